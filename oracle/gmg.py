@@ -1,0 +1,198 @@
+"""Geometric multigrid with the patchwise Vanka smoother (oracle; test infrastructure only).
+
+Follows Sec. 4: vertex patches P_l^m (Eq. 4.9), the patch index sets
+Z_l(P) and the dof map (Eq. 4.10), the local Vanka operator
+S_P(d) = R_P d + omega A_P^{-1} R_P (b_l - A_l d) with the principal
+submatrix A_P (Def. 4.2, Eqs. 4.11-4.13), the smoothing steps with averaging
+(Algorithm 4.1), prolongation by interpolation and restriction by its
+transpose, J pre- and post-smoothing steps on levels l = 1..L and a direct
+solve on level 0.
+
+Readings:
+
+* Z_l(P) ("all degrees of freedom linked to the patch"): the degrees of
+  freedom whose basis function is supported in the closed patch, i.e. the
+  nodes of the patch that do not lie on the part of the patch boundary
+  interior to the domain; all k+1 time nodes and all fields (v, u, p).
+  The reading where every node of every patch cell is included is
+  available as ``support=False``.
+* Level operators are rediscretisations of Problem 3.1 on each level.
+* Smoothing: Algorithm 4.1 starts from d = 0 for the pre-smoothing of each
+  level; post-smoothing starts from the corrected iterate.  The residual in
+  S_P uses the iterate of the start of the sweep (d is only overwritten
+  after the patch loop).
+* The coarse direct solve is a dense LU with partial pivoting.
+"""
+import itertools
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .space import BoxMesh, NodalSpace, SpatialOps, Material
+from .slab import Temporal, slab_matrix
+
+
+def _axis_range(a_lo, a_hi, at_lo_bdry, at_hi_bdry):
+    lo = a_lo if at_lo_bdry else a_lo + 1
+    hi = a_hi if at_hi_bdry else a_hi - 1
+    return range(lo, hi + 1)
+
+
+def patch_nodes(space, vertex, support=True):
+    """Global node indices of the scalar space ``space`` belonging to the
+    vertex patch at lattice vertex ``vertex`` (multi-index)."""
+    mesh, m = space.mesh, space.m
+    ranges = []
+    for i in range(mesh.dim):
+        c0 = max(vertex[i] - 1, 0)
+        c1 = min(vertex[i], mesh.n[i] - 1)
+        a_lo, a_hi = m * c0, m * (c1 + 1)
+        if support:
+            # an end node of the range is shared with a cell outside the patch
+            # unless that side of the patch lies on the domain boundary
+            ranges.append(_axis_range(a_lo, a_hi, c0 == 0, c1 == mesh.n[i] - 1))
+        else:
+            ranges.append(range(a_lo, a_hi + 1))
+    out = []
+    for a in itertools.product(*ranges[::-1]):
+        out.append(space.node_index(a[::-1]))
+    return np.array(out, int)
+
+
+def patch_dofs(ops, temporal, vertex, support=True):
+    """Global slab indices (paper ordering) of Z_l(P) for one vertex patch."""
+    un = patch_nodes(ops.Vs, vertex, support)
+    pn = patch_nodes(ops.Qs, vertex, support)
+    d, R, n_s = ops.d, ops.R, ops.n_s
+    vec = np.array([I * d + c for I in un for c in range(d)], int)
+    out = []
+    for a in range(temporal.q):
+        base = a * n_s
+        out.append(base + vec)
+        out.append(base + R + vec)
+        out.append(base + 2 * R + pn)
+    return np.concatenate(out)
+
+
+def vertices(mesh):
+    dims = mesh.n + 1
+    for idx in range(int(np.prod(dims))):
+        v, t = [], idx
+        for i in range(mesh.dim):
+            v.append(t % dims[i])
+            t //= dims[i]
+        yield tuple(v)
+
+
+def prolongation_scalar(coarse, fine):
+    """Interpolation of the coarse Q_m space into the nested fine one:
+    P[f, c] = coarse basis function c evaluated at fine node f."""
+    xf = fine.node_coords()
+    cm_ = coarse.mesh
+    rows, cols, vals = [], [], []
+    for f, x in enumerate(xf):
+        cell = []
+        for i in range(cm_.dim):
+            c = int(np.floor((x[i] - cm_.lo[i]) / cm_.h[i] + 1e-12))
+            cell.append(min(max(c, 0), cm_.n[i] - 1))
+        xr = (x - (cm_.lo + cm_.h * np.array(cell))) / cm_.h
+        phi, _ = coarse.basis(xr[None, :])
+        nodes = coarse.cell_nodes(tuple(cell))
+        for j, nd in enumerate(nodes):
+            if abs(phi[0, j]) > 1e-14:
+                rows.append(f)
+                cols.append(nd)
+                vals.append(phi[0, j])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(fine.nnodes, coarse.nnodes))
+
+
+def slab_prolongation(coarse_ops, fine_ops, temporal):
+    """I_q (x) blockdiag(P_u (x) I_d, P_u (x) I_d, P_p); time is not coarsened."""
+    d = fine_ops.d
+    Pu = prolongation_scalar(coarse_ops.Vs, fine_ops.Vs)
+    Pp = prolongation_scalar(coarse_ops.Qs, fine_ops.Qs)
+    Pv = sp.kron(Pu, sp.identity(d))
+    blk = sp.block_diag([Pv, Pv, Pp])
+    return sp.kron(sp.identity(temporal.q), blk, format="csr")
+
+
+class Level:
+    def __init__(self, ops, A, temporal, support=True):
+        self.ops, self.A = ops, A
+        self.patches = []
+        self.inverses = []
+        self.support = support
+        self.temporal = temporal
+
+    def build_patches(self):
+        A = self.A.tocsr()
+        for v in vertices(self.ops.mesh):
+            idx = patch_dofs(self.ops, self.temporal, v, self.support)
+            AP = A[idx][:, idx].toarray()
+            self.patches.append(idx)
+            self.inverses.append(np.linalg.inv(AP))
+
+
+def smooth(level, b, d, omega, nsweeps):
+    """Algorithm 4.1, literally: per sweep reset counters p and accumulator z,
+    apply every local Vanka operator to the current iterate, accumulate the
+    extended patch results, then d = z / p."""
+    A = level.A
+    n = A.shape[0]
+    for _ in range(nsweeps):
+        p = np.zeros(n, dtype=np.int64)
+        z = np.zeros(n)
+        res = b - A @ d  # S_P applies to the iterate of the start of the sweep
+        for idx, Ainv in zip(level.patches, level.inverses):
+            y = d[idx] + omega * (Ainv @ res[idx])
+            z[idx] += y
+            p[idx] += 1
+        if np.any(p == 0):
+            raise RuntimeError("a degree of freedom belongs to no patch")
+        d = z / p
+    return d
+
+
+class Hierarchy:
+    """Levels 0..L of the GMG method for one slab problem."""
+
+    def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material_fine, bc_u, bc_p, tau,
+                 omega=0.7, nsweeps=1, support=True, hf="measure"):
+        self.temporal = Temporal(k)
+        self.omega, self.nsweeps = omega, nsweeps
+        meshes = [BoxMesh(dim, lo, hi, n_fine, hf)]
+        mats = [material_fine]
+        for _ in range(n_levels - 1):
+            mats.append(mats[-1].coarsen(meshes[-1]))
+            meshes.append(meshes[-1].coarsen())
+        meshes, mats = meshes[::-1], mats[::-1]  # level 0 = coarsest
+        self.levels = []
+        for mesh, mat in zip(meshes, mats):
+            ops = SpatialOps(mesh, r, mat, bc_u, bc_p)
+            A = slab_matrix(ops, self.temporal, tau)
+            self.levels.append(Level(ops, A, self.temporal, support))
+        self.P = [None] + [slab_prolongation(self.levels[l - 1].ops, self.levels[l].ops,
+                                             self.temporal) for l in range(1, n_levels)]
+        for lev in self.levels[1:]:
+            lev.build_patches()
+        self.coarse_lu = sla.lu_factor(self.levels[0].A.toarray())
+
+    @property
+    def fine(self):
+        return self.levels[-1]
+
+    def vcycle(self, b, l=None):
+        """One V-cycle for A_l d = b from d = 0."""
+        if l is None:
+            l = len(self.levels) - 1
+        if l == 0:
+            return sla.lu_solve(self.coarse_lu, b)
+        lev = self.levels[l]
+        d = np.zeros_like(b)
+        d = smooth(lev, b, d, self.omega, self.nsweeps)
+        r = b - lev.A @ d
+        bc = self.P[l].T @ r
+        dc = self.vcycle(bc, l - 1)
+        d = d + self.P[l] @ dc
+        d = smooth(lev, b, d, self.omega, self.nsweeps)
+        return d
