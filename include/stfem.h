@@ -1,0 +1,247 @@
+/*
+ * stfem.h -- C ABI of the GB300 space-time FEM solver for dynamic
+ * poro-/thermoelasticity (arXiv 2303.06742): flexible GMRES preconditioned by
+ * a geometric-multigrid V-cycle with the patchwise Vanka smoother.
+ *
+ * Problem solved (Sec. 3, Problem 3.1; Sec. 4, Problem 4.1): on each time
+ * slab I_n = (t_{n-1}, t_n] the dG(k) / Taylor-Hood Q_r^d / Q_{r-1}
+ * discretisation of Eq. 1.1 (first-order form Eq. 3.1, Nitsche boundary
+ * terms Eqs. 3.2-3.3) gives A_n X_n = F_n (Eq. 4.5).
+ *
+ * Vector layout ("paper order", Eq. 4.4), used by every vector argument:
+ *   X = (V_1, U_1, P_1, ..., V_q, U_q, P_q),  q = k + 1 Radau nodes of I_n,
+ *   V_a, U_a: R = d * n_u entries, index node * d + component (node-major),
+ *   P_a:      S = n_p entries,
+ *   n_u = prod_i (r N_i + 1), n_p = prod_i ((r-1) N_i + 1) lattice nodes of the
+ *   Q_r and Q_{r-1} spaces, numbered lexicographically with x fastest; the
+ *   nodal basis uses Gauss-Lobatto support points on each cell.
+ *   A slab vector has N_slab = q (2R + S) entries; a "state" (the solution at
+ *   one time point) has 2R + S entries ordered (V, U, P).
+ *   Row blocks of A_n are ordered (u-equation, v-equation, p-equation) per
+ *   test time node, the u-equation multiplied by rho (Eq. 4.7).
+ *
+ * Memory: every vector argument is a DEVICE pointer (cudaMalloc / torch CUDA
+ * memory) to FP64 data, owned by the caller, unless the name ends in _host.
+ * The handle owns all memory it allocates and frees it in stfem_destroy.
+ * All work is issued on the handle's stream (stfem_set_stream); calls return
+ * after the stream has been synchronised unless stated otherwise.
+ *
+ * Errors: every int-returning call returns STFEM_OK (0), a positive soft
+ * status (STFEM_NOT_CONVERGED) or a negative error code; the message of the
+ * last error is available from stfem_last_error().  No call throws.
+ */
+#ifndef STFEM_H
+#define STFEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STFEM_OK 0
+#define STFEM_NOT_CONVERGED 1
+#define STFEM_ERR_ARG (-1)
+#define STFEM_ERR_CUDA (-2)
+#define STFEM_ERR_SINGULAR_PATCH (-3)
+#define STFEM_ERR_BREAKDOWN (-4)
+#define STFEM_ERR_STATE (-5)
+#define STFEM_ERR_OOM (-6)
+
+#define STFEM_BC_DIRICHLET 0 /* homogeneous Dirichlet, imposed by Nitsche's method */
+#define STFEM_BC_NEUMANN 1   /* natural condition; data from the problem id */
+
+#define STFEM_PROBLEM_NONE 0            /* f = g = 0, zero boundary data */
+#define STFEM_PROBLEM_SIN 1             /* u = phi sin t (1,..,1), p = phi cos t, phi = prod sin(pi x_i) */
+#define STFEM_PROBLEM_PULSE 2           /* 3D: traction (0,0,-sin(pi t/0.05)) on [0.75,1.25]^2 of the top face */
+#define STFEM_PROBLEM_PAPER_EOC 3       /* Eq. 5.1, omega_1 = omega_2 = pi (2D) */
+#define STFEM_PROBLEM_PAPER_SUPERCONV 4 /* Eq. 5.3, omega_1 = 40 pi, omega_2 = 10 pi (2D) */
+
+#define STFEM_FP64 0  /* every step in FP64 */
+#define STFEM_MIXED 1 /* V-cycle (level operators, patch inverses, transfers) in FP32 inside FP64 FGMRES */
+
+#define STFEM_HF_MEASURE 0 /* h_F = |K|_d, the cell measure (Sec. 3, literal) */
+#define STFEM_HF_LENGTH 1  /* h_F = |K|_d^(1/d) */
+
+/* Level operators of the multigrid hierarchy (the paper does not state them):
+ * Galerkin products A_{l-1} = P_l^T A_l P_l of the finest slab matrix, or a
+ * rediscretisation of Problem 3.1 on each level with the mean of the fine
+ * cells' coefficients. */
+#define STFEM_COARSE_GALERKIN 0
+#define STFEM_COARSE_REDISCRETIZE 1
+
+typedef struct stfem_ctx *stfem_h;
+
+/* Uniform box mesh [lo, hi] with n_cells[i] cells per axis on the finest
+ * level; n_levels levels obtained by halving (each n_cells[i] must be
+ * divisible by 2^(n_levels-1)); level 0 is the coarsest (Sec. 2). */
+typedef struct {
+  int dim;          /* 2 or 3 */
+  double lo[3], hi[3];
+  int n_cells[3];
+  int n_levels;     /* >= 1 */
+  int hf_mode;      /* STFEM_HF_MEASURE (default reading) or STFEM_HF_LENGTH */
+  int coarse_op;    /* STFEM_COARSE_GALERKIN (default) or STFEM_COARSE_REDISCRETIZE */
+} stfem_mesh;
+
+/* r: displacement degree (Q_r^d / Q_{r-1} Taylor-Hood, r >= 2, Eq. 2.5);
+ * k: temporal degree of dG(k) (k+1 right Gauss-Radau nodes, Eq. 2.4), 0..4. */
+typedef struct {
+  int r;
+  int k;
+} stfem_degrees;
+
+/* Coefficients of Eq. 1.1 with isotropic C (lambda, mu) and K = kappa I.
+ * The *_cell arrays (host, may be NULL) give per-cell values on the finest
+ * mesh, cells numbered lexicographically with x fastest; coarse cells take
+ * the arithmetic mean of their children. */
+typedef struct {
+  double rho, alpha, c0;
+  double lambda, mu, kappa;
+  const double *lambda_cell_host;
+  const double *mu_cell_host;
+  const double *kappa_cell_host;
+} stfem_material;
+
+/* Boundary conditions per box face f = 2*axis + side (side 0: x_axis = lo,
+ * side 1: x_axis = hi); problem: STFEM_PROBLEM_* (source terms, Neumann data,
+ * initial values); t0: initial time of the march. */
+typedef struct {
+  int bc_u[6];
+  int bc_p[6];
+  int problem;
+  double t0;
+} stfem_bcs;
+
+/* GMG parameters (Sec. 4): damping omega of the Vanka operator (Eq. 4.11;
+ * the paper uses 0.7), n_sweeps pre- and post-smoothing steps of
+ * Algorithm 4.1 per level, precision STFEM_FP64 or STFEM_MIXED. */
+typedef struct {
+  double omega;
+  int n_sweeps;
+  int precision;
+} stfem_gmg_params;
+
+/* Builds the mesh hierarchy, spatial matrices of every level (Eqs. 3.2-3.3),
+ * temporal matrices (Eq. 2.4) and transfers, and uploads them to the current
+ * CUDA device.  tau: time step.  Returns a new handle in *out.
+ * Errors: STFEM_ERR_ARG for invalid sizes/degrees, STFEM_ERR_CUDA/OOM. */
+int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                const stfem_bcs *bcs, double tau, stfem_h *out);
+
+/* Builds the vertex patches of every level l >= 1 (Eq. 4.9), extracts and
+ * inverts the patch matrices A_P in FP64 (Def. 4.2, Eq. 4.13), inverts the
+ * coarse matrix A_0 (dense, partial pivoting) and uploads everything.
+ * Once per handle (STFEM_ERR_STATE otherwise).  STFEM_ERR_SINGULAR_PATCH if a
+ * patch matrix has a zero pivot. */
+int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p);
+
+/* Issue all work on this CUDA stream (cudaStream_t passed as void*; NULL =
+ * the legacy default stream). */
+int stfem_set_stream(stfem_h h, void *stream);
+
+/* Sizes: *n_slab = q (2R+S) of level l (l = -1: finest), *n_state = 2R+S,
+ * *n_patches of level l, *inv_bytes = bytes of the stored patch inverses of
+ * level l in the current precision. */
+int stfem_level_info(stfem_h h, int level, long long *n_slab, long long *n_state,
+                     long long *n_patches, long long *inv_bytes);
+
+/* y = A_l x on level l in the precision that level uses inside the V-cycle
+ * (FP64 for STFEM_FP64, FP32 for STFEM_MIXED; fine-level FGMRES products are
+ * FP64 always when level = -1). x, y: device, n_slab FP64. */
+int stfem_apply(stfem_h h, int level, const double *x, double *y);
+
+/* n_sweeps averaged Vanka smoothing steps of Algorithm 4.1 on level l >= 1
+ * for A_l d = b, in the level's precision.  zero_init != 0 starts from d = 0
+ * (Algorithm 4.1's initialisation) and ignores d's input. */
+int stfem_smooth(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init);
+
+/* Restriction b_{l-1} = P_l^T r_l and prolongation-add d_l += P_l d_{l-1}
+ * between level l and l-1 (interpolation of nested spaces, Sec. 4); time is
+ * not coarsened. */
+int stfem_restrict(stfem_h h, int level, const double *r_fine, double *b_coarse);
+int stfem_prolongate_add(stfem_h h, int level, const double *d_coarse, double *d_fine);
+
+/* x = A_0^{-1} b on the coarsest level (FP64 explicit inverse from a dense
+ * LU with partial pivoting). */
+int stfem_coarse_solve(stfem_h h, const double *b, double *x);
+
+/* One V-cycle from d = 0 for A_L d = b on the finest level (the
+ * preconditioner of each FGMRES iteration, Sec. 4). */
+int stfem_vcycle(stfem_h h, const double *b, double *d);
+
+/* Flexible GMRES(restart) for A_n x = rhs (Sec. 4) on the finest level,
+ * right-preconditioned by one V-cycle per iteration, classical Gram-Schmidt
+ * applied twice.  x: in = initial guess x0, out = solution.  Stops when the
+ * least-squares residual satisfies |g_{j+1}| <= tol ||rhs - A x0|| and the
+ * recomputed true residual confirms it, or after max_it iterations.
+ * *iters: iterations done; *rel_res: final true ||rhs - A x|| / ||rhs - A x0||.
+ * Returns STFEM_OK, STFEM_NOT_CONVERGED or STFEM_ERR_BREAKDOWN (NaN/Inf). */
+int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart, int max_it,
+               int *iters, double *rel_res);
+
+/* History |g_j| / ||rhs - A x0|| of the last slab_solve (j = 0..iters) into
+ * hist_host (capacity cap); *n = number of entries written. */
+int stfem_solve_history(stfem_h h, double *hist_host, int cap, int *n);
+
+/* State at t0 by nodal interpolation of the problem's initial values
+ * (zero for STFEM_PROBLEM_NONE / PULSE).  state: device, 2R+S. */
+int stfem_initial_state(stfem_h h, double *state);
+
+/* Right-hand side F_n of slab n (0-based, I_n = (t0 + n tau, t0 + (n+1) tau])
+ * from the problem's data at the Radau nodes and the previous end state
+ * prev_state (device, 2R+S) (Eq. 3.5, Eq. 4.5).  rhs: device, n_slab. */
+int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs);
+
+/* March n_slabs slabs from slab index first_slab: for each slab, build F_n,
+ * take x0 = previous end state at every time node, solve with tol, restart,
+ * max_it as slab_solve, and continue from the end state (value at the last
+ * Radau node, t_n).  state: device, 2R+S, in = state at t_{first_slab}
+ * (resume point), out = state at the end.  iters_host: per-slab iteration
+ * counts (may be NULL).  Returns the worst status over the slabs. */
+int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int restart,
+          int max_it, int *iters_host);
+
+/* ---- Host-side inspection of the setup (no GPU needed; for tests) ----
+ * These rebuild the hierarchy on the host from the same arguments as
+ * stfem_setup and return what the GPU path would upload.  Two-call pattern:
+ * with NULL output arrays only the sizes are returned.  Arrays are host
+ * memory owned by the caller.  Errors as stfem_setup (message via
+ * stfem_last_error(NULL)). */
+
+/* Slab matrix A_l of level l (l = -1: finest) in CSR form, paper order
+ * (Eqs. 4.4-4.7): A_l = Dt (x) S1 + diag(W) (x) S2, expanded. */
+int stfem_host_level_matrix(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                            const stfem_bcs *bcs, double tau, int level, long long *n, long long *nnz,
+                            long long *rowptr_host, int *col_host, double *val_host);
+
+/* Vertex patches of level l >= 1 (Eq. 4.9): patch p holds the slab indices
+ * dofs_host[off_host[p] .. off_host[p+1]) (all time nodes and fields). */
+int stfem_host_patch_dofs(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                          const stfem_bcs *bcs, double tau, int level, long long *n_patches, long long *total,
+                          long long *off_host, int *dofs_host);
+
+/* Scalar interpolation from level l-1 to l (field 0: Q_r nodes, field 1:
+ * Q_{r-1} nodes) in CSR form (rows: fine nodes). */
+int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                            const stfem_bcs *bcs, double tau, int level, int field, long long *nrows,
+                            long long *ncols, long long *nnz, long long *rowptr_host, int *col_host,
+                            double *val_host);
+
+/* Right Gauss-Radau nodes t[q] and weights w[q] on [-1,1], chi_a(-1) and
+ * Dt[b*q+a] (row-major) for dG(k), q = k+1 (Eq. 2.4). */
+int stfem_host_temporal(int k, double *t_host, double *w_host, double *chi_host, double *Dt_host);
+
+/* Message of the last error on this handle (or of the last failed
+ * stfem_setup when h is NULL). */
+const char *stfem_last_error(stfem_h h);
+
+/* Message of the last failed stfem_host_* call on this thread. */
+const char *stfem_host_last_error(void);
+
+/* Frees every resource of the handle.  NULL is ignored. */
+void stfem_destroy(stfem_h h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STFEM_H */

@@ -1,0 +1,62 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle.
+
+Only data: problem sizes, coefficients and random draws.  No arithmetic of
+the method lives here.  Workload shapes follow the paper's setting (Sec. 5:
+unit boxes, uniform refinement, Taylor-Hood pairs, dG(k) slabs) at the
+sizes of the benchmarked configurations.
+"""
+import numpy as np
+
+SEED = 20230312
+
+
+def lame_from_young(E, nu):
+    return E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+
+
+def case(name, seed=SEED):
+    """Keyword arguments of a problem instance (for paper_2303_06742_gb300.Problem
+    and for the oracle's Instance), by name."""
+    rng = np.random.default_rng(seed)
+    if name == "c1_2d_q2_k1_8":  # 2D unit square 8x8, Q2/Q1, k=1, 3 levels
+        return dict(dim=2, n=8, levels=3, r=2, k=1, tau=0.01, slabs=10, rho=1.0, alpha=1.0, c0=1.0,
+                    lam=1.0, mu=1.0, kappa=1.0, problem="sin", tol=1e-10)
+    if name == "c2_2d_q3_k2_64":  # 2D 64x64, 5 levels, Q3/Q2, k=2, random materials
+        lam = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        mu = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        kap = np.exp(rng.standard_normal(64 * 64))
+        return dict(dim=2, n=64, levels=5, r=3, k=2, tau=1e-3, slabs=20, rho=1.0, alpha=1.0, c0=1e-2,
+                    lam=lam, mu=mu, kappa_cell=kap, problem="sin", tol=1e-8)
+    if name == "c2_small_2d_q3_k2_8":  # same recipe, 8x8 / 3 levels (oracle-sized)
+        lam = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        mu = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        kap = np.exp(rng.standard_normal(8 * 8))
+        return dict(dim=2, n=8, levels=3, r=3, k=2, tau=1e-3, slabs=3, rho=1.0, alpha=1.0, c0=1e-2,
+                    lam=lam, mu=mu, kappa_cell=kap, problem="sin", tol=1e-8)
+    if name == "c3_small_3d_q2_k1_4":  # thermoelastic set, 3D 4^3, 2 levels
+        return dict(dim=3, n=4, levels=2, r=2, k=1, tau=1e-2, slabs=2, rho=1.0, alpha=0.5, c0=1.0,
+                    lam=2.0, mu=1.0, kappa=0.1, problem="sin", tol=1e-8)
+    if name == "c3_3d_q2_k1_16":
+        return dict(dim=3, n=16, levels=4, r=2, k=1, tau=1e-2, slabs=10, rho=1.0, alpha=0.5, c0=1.0,
+                    lam=2.0, mu=1.0, kappa=0.1, problem="sin", tol=1e-8)
+    if name == "c5_small_3d_pulse":  # layered box [0,2]^2 x [0,1], 4x4x2 cells
+        n = (4, 4, 2)
+        kap, mu = layered(n, 1.0)
+        return dict(dim=3, n=n, levels=2, r=2, k=1, tau=5e-3, slabs=2, lo=[0, 0, 0], hi=[2, 2, 1],
+                    rho=1.0, alpha=1.0, c0=1.0, lam=1.0, mu_cell=mu, kappa_cell=kap, problem="pulse",
+                    bc_u=[1, 1, 1, 1, 0, 1], bc_p=[1, 1, 1, 1, 1, 0], tol=1e-8)
+    raise KeyError(name)
+
+
+def layered(n, top_z_split):
+    """Two horizontal layers split at z = 0.5: lower kappa = 1, mu = 1; upper
+    kappa = 1e-3, mu = 10 (per cell, cells lexicographic with x fastest)."""
+    nx, ny, nz = n
+    kap = np.empty(nx * ny * nz)
+    mu = np.empty(nx * ny * nz)
+    for z in range(nz):
+        upper = (z + 0.5) / nz * top_z_split > 0.5
+        sl = slice(z * nx * ny, (z + 1) * nx * ny)
+        kap[sl] = 1e-3 if upper else 1.0
+        mu[sl] = 10.0 if upper else 1.0
+    return kap, mu

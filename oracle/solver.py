@@ -17,9 +17,10 @@ class Instance:
     """One problem: a GMG hierarchy, the data problem and the time step."""
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
-                 problem, t0=0.0, omega=0.7, nsweeps=1, support=True, hf="measure"):
+                 problem, t0=0.0, omega=0.7, nsweeps=1, support=True, hf="measure",
+                 coarse="galerkin"):
         self.h = Hierarchy(dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
-                           omega, nsweeps, support, hf)
+                           omega, nsweeps, support, hf, coarse)
         self.prob, self.tau, self.t0 = problem, tau, t0
         self.tmp = self.h.temporal
         self.ops = self.h.fine.ops

@@ -1,0 +1,290 @@
+"""GB300 GMRES-GMG solver for space-time FEM of dynamic poro-/thermoelasticity.
+
+Thin Python binding of the C ABI in ``include/stfem.h`` (arXiv 2303.06742):
+argument marshalling only.  Every step of the solver runs in the CUDA kernels
+of ``libstfem.so``; importing this package fails loudly when the library has
+not been built (``python -m paper_2303_06742_gb300.build``).
+
+Vectors passed to the device calls are CUDA float64 tensors (or any object
+with ``data_ptr()``) in the paper's slab ordering (Eq. 4.4).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstfem.so")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_ARG, ERR_CUDA, ERR_SINGULAR_PATCH, ERR_BREAKDOWN, ERR_STATE, ERR_OOM = -1, -2, -3, -4, -5, -6
+DIRICHLET, NEUMANN = 0, 1
+PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPERCONV = 0, 1, 2, 3, 4
+FP64, MIXED = 0, 1
+HF_MEASURE, HF_LENGTH = 0, 1
+COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
+
+
+class StfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("stfem error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("n_cells", C.c_int * 3), ("n_levels", C.c_int), ("hf_mode", C.c_int),
+                ("coarse_op", C.c_int)]
+
+
+class Degrees(C.Structure):
+    _fields_ = [("r", C.c_int), ("k", C.c_int)]
+
+
+class Material(C.Structure):
+    _fields_ = [("rho", C.c_double), ("alpha", C.c_double), ("c0", C.c_double),
+                ("lambda_", C.c_double), ("mu", C.c_double), ("kappa", C.c_double),
+                ("lambda_cell_host", C.POINTER(C.c_double)), ("mu_cell_host", C.POINTER(C.c_double)),
+                ("kappa_cell_host", C.POINTER(C.c_double))]
+
+
+class BCs(C.Structure):
+    _fields_ = [("bc_u", C.c_int * 6), ("bc_p", C.c_int * 6), ("problem", C.c_int), ("t0", C.c_double)]
+
+
+class GmgParams(C.Structure):
+    _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libstfem.so is not built; run `python -m paper_2303_06742_gb300.build` "
+                          "(or __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    pI, pD, pLL = C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_longlong)
+    sig = {
+        "stfem_setup": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material), C.POINTER(BCs), D,
+                        C.POINTER(P)],
+        "stfem_gmg_setup": [P, C.POINTER(GmgParams)],
+        "stfem_set_stream": [P, P],
+        "stfem_level_info": [P, I, pLL, pLL, pLL, pLL],
+        "stfem_apply": [P, I, P, P],
+        "stfem_smooth": [P, I, P, P, I, I],
+        "stfem_restrict": [P, I, P, P],
+        "stfem_prolongate_add": [P, I, P, P],
+        "stfem_coarse_solve": [P, P, P],
+        "stfem_vcycle": [P, P, P],
+        "slab_solve": [P, P, P, D, I, I, pI, pD],
+        "stfem_solve_history": [P, pD, I, pI],
+        "stfem_initial_state": [P, P],
+        "stfem_slab_rhs": [P, I, P, P],
+        "march": [P, I, I, P, D, I, I, pI],
+        "stfem_host_level_matrix": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
+                                    C.POINTER(BCs), D, I, pLL, pLL, pLL, pI, pD],
+        "stfem_host_patch_dofs": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
+                                  C.POINTER(BCs), D, I, pLL, pLL, pLL, pI],
+        "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
+                                    C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pLL, pI, pD],
+        "stfem_host_temporal": [I, pD, pD, pD, pD],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.stfem_last_error.argtypes = [P]
+    lib.stfem_last_error.restype = C.c_char_p
+    lib.stfem_host_last_error.argtypes = []
+    lib.stfem_host_last_error.restype = C.c_char_p
+    lib.stfem_destroy.argtypes = [P]
+    lib.stfem_destroy.restype = None
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(int(t))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Problem:
+    """Arguments of stfem_setup as plain Python values."""
+
+    def __init__(self, dim, n_cells, n_levels, r, k, tau, lo=None, hi=None, rho=1.0, alpha=1.0, c0=1.0,
+                 lam=1.0, mu=1.0, kappa=1.0, lam_cell=None, mu_cell=None, kappa_cell=None,
+                 bc_u=None, bc_p=None, problem=PROBLEM_NONE, t0=0.0, hf_mode=HF_MEASURE,
+                 coarse_op=COARSE_GALERKIN):
+        self.dim = dim
+        lo = list(lo) if lo is not None else [0.0] * dim
+        hi = list(hi) if hi is not None else [1.0] * dim
+        n_cells = list(n_cells) if hasattr(n_cells, "__len__") else [n_cells] * dim
+        self.mesh = Mesh(dim, (C.c_double * 3)(*(lo + [0.0] * (3 - dim))),
+                         (C.c_double * 3)(*(hi + [1.0] * (3 - dim))),
+                         (C.c_int * 3)(*(n_cells + [1] * (3 - dim))), n_levels, hf_mode, coarse_op)
+        self.deg = Degrees(r, k)
+        self._cells = []
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._cells.append(a)
+            return _dptr(a)
+
+        self.mat = Material(rho, alpha, c0, lam, mu, kappa, arr(lam_cell), arr(mu_cell), arr(kappa_cell))
+        bc_u = list(bc_u) if bc_u is not None else [DIRICHLET] * (2 * dim)
+        bc_p = list(bc_p) if bc_p is not None else [DIRICHLET] * (2 * dim)
+        self.bcs = BCs((C.c_int * 6)(*(bc_u + [0] * (6 - len(bc_u)))),
+                       (C.c_int * 6)(*(bc_p + [0] * (6 - len(bc_p)))), problem, t0)
+        self.tau = tau
+        self.r, self.k, self.q = r, k, k + 1
+
+    def args(self):
+        return (C.byref(self.mesh), C.byref(self.deg), C.byref(self.mat), C.byref(self.bcs),
+                C.c_double(self.tau))
+
+
+def _host_check(rc):
+    if rc < 0:
+        raise StfemError(rc, lib.stfem_host_last_error().decode())
+
+
+def host_level_matrix(prob, level=-1):
+    """Slab matrix of a level as built by the host setup: (indptr, indices, data, n)."""
+    n, nnz = C.c_longlong(), C.c_longlong()
+    _host_check(lib.stfem_host_level_matrix(*prob.args(), level, C.byref(n), C.byref(nnz), None, None, None))
+    rp = np.zeros(n.value + 1, np.int64)
+    ci = np.zeros(nnz.value, np.int32)
+    va = np.zeros(nnz.value, np.float64)
+    _host_check(lib.stfem_host_level_matrix(*prob.args(), level, C.byref(n), C.byref(nnz),
+                                            rp.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                            ci.ctypes.data_as(C.POINTER(C.c_int)), _dptr(va)))
+    return rp, ci, va, n.value
+
+
+def host_patch_dofs(prob, level=-1):
+    """List of per-patch slab index arrays of a level (vertex order, x fastest)."""
+    npch, tot = C.c_longlong(), C.c_longlong()
+    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, C.byref(npch), C.byref(tot), None, None))
+    off = np.zeros(npch.value + 1, np.int64)
+    dofs = np.zeros(tot.value, np.int32)
+    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, C.byref(npch), C.byref(tot),
+                                          off.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                          dofs.ctypes.data_as(C.POINTER(C.c_int))))
+    return [dofs[off[i]:off[i + 1]] for i in range(npch.value)]
+
+
+def host_prolongation(prob, level, field):
+    nr, nc, nnz = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _host_check(lib.stfem_host_prolongation(*prob.args(), level, field, C.byref(nr), C.byref(nc),
+                                            C.byref(nnz), None, None, None))
+    rp = np.zeros(nr.value + 1, np.int64)
+    ci = np.zeros(nnz.value, np.int32)
+    va = np.zeros(nnz.value, np.float64)
+    _host_check(lib.stfem_host_prolongation(*prob.args(), level, field, C.byref(nr), C.byref(nc),
+                                            C.byref(nnz), rp.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                            ci.ctypes.data_as(C.POINTER(C.c_int)), _dptr(va)))
+    return rp, ci, va, (nr.value, nc.value)
+
+
+def host_temporal(k):
+    q = k + 1
+    t, w, chi, Dt = (np.zeros(q), np.zeros(q), np.zeros(q), np.zeros(q * q))
+    _host_check(lib.stfem_host_temporal(k, _dptr(t), _dptr(w), _dptr(chi), _dptr(Dt)))
+    return t, w, chi, Dt.reshape(q, q)
+
+
+class Solver:
+    """Handle of one problem instance on the current CUDA device."""
+
+    def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None):
+        self.prob = prob
+        h = C.c_void_p()
+        rc = lib.stfem_setup(*prob.args(), C.byref(h))
+        if rc < 0:
+            raise StfemError(rc, lib.stfem_last_error(None).decode())
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision))))
+        self.precision = precision
+        n_slab, n_state = C.c_longlong(), C.c_longlong()
+        self._check(lib.stfem_level_info(self.h, -1, C.byref(n_slab), C.byref(n_state), None, None))
+        self.n_slab, self.n_state = n_slab.value, n_state.value
+
+    def _check(self, rc):
+        if rc < 0:
+            raise StfemError(rc, lib.stfem_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.stfem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self._check(lib.stfem_set_stream(self.h, C.c_void_p(s)))
+
+    def level_info(self, level=-1):
+        vals = [C.c_longlong() for _ in range(4)]
+        self._check(lib.stfem_level_info(self.h, level, *[C.byref(v) for v in vals]))
+        return dict(n_slab=vals[0].value, n_state=vals[1].value, n_patches=vals[2].value,
+                    inv_bytes=vals[3].value)
+
+    def apply(self, level, x, y):
+        self._check(lib.stfem_apply(self.h, level, _ptr(x), _ptr(y)))
+
+    def smooth(self, level, b, d, n_sweeps=1, zero_init=True):
+        self._check(lib.stfem_smooth(self.h, level, _ptr(b), _ptr(d), n_sweeps, int(bool(zero_init))))
+
+    def restrict(self, level, r_fine, b_coarse):
+        self._check(lib.stfem_restrict(self.h, level, _ptr(r_fine), _ptr(b_coarse)))
+
+    def prolongate_add(self, level, d_coarse, d_fine):
+        self._check(lib.stfem_prolongate_add(self.h, level, _ptr(d_coarse), _ptr(d_fine)))
+
+    def coarse_solve(self, b, x):
+        self._check(lib.stfem_coarse_solve(self.h, _ptr(b), _ptr(x)))
+
+    def vcycle(self, b, d):
+        self._check(lib.stfem_vcycle(self.h, _ptr(b), _ptr(d)))
+
+    def slab_solve(self, rhs, x, tol=1e-8, restart=30, max_it=500):
+        it, rr = C.c_int(), C.c_double()
+        rc = self._check(lib.slab_solve(self.h, _ptr(rhs), _ptr(x), tol, restart, max_it, C.byref(it),
+                                        C.byref(rr)))
+        return rc, it.value, rr.value
+
+    def history(self, cap=4096):
+        buf = np.zeros(cap)
+        n = C.c_int()
+        self._check(lib.stfem_solve_history(self.h, _dptr(buf), cap, C.byref(n)))
+        return buf[:n.value].copy()
+
+    def initial_state(self, state):
+        self._check(lib.stfem_initial_state(self.h, _ptr(state)))
+
+    def slab_rhs(self, slab, prev_state, rhs):
+        self._check(lib.stfem_slab_rhs(self.h, slab, _ptr(prev_state), _ptr(rhs)))
+
+    def march(self, first_slab, n_slabs, state, tol=1e-8, restart=30, max_it=500):
+        iters = (C.c_int * max(n_slabs, 1))()
+        rc = self._check(lib.march(self.h, first_slab, n_slabs, _ptr(state), tol, restart, max_it, iters))
+        return rc, list(iters)[:n_slabs]

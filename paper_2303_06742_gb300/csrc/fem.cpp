@@ -1,0 +1,1155 @@
+// Host-side setup of the space-time FE hierarchy (arXiv 2303.06742).
+//
+// Secs. 2-3: Taylor-Hood Q_r^d / Q_{r-1} spaces on uniform box meshes, the
+// forms A_gamma, C, B_gamma with Nitsche terms (Eqs. 3.2-3.3), right
+// Gauss-Radau dG(k) in time (Eq. 2.4).  Sec. 4: vertex patches (Eq. 4.9),
+// principal-submatrix patch inverses (Def. 4.2, Eq. 4.13), interpolation
+// transfers, coarse direct solve.
+//
+// Readings (the paper is silent or garbled there):
+//  * h_F = |K|_d literally (Sec. 3), or |K|_d^{1/d} on request;
+//  * gamma_a = 5e4 r (r+1), gamma_b = r (r-1) / 2;
+//  * element integrals by Gauss-Legendre with r+2 points per direction;
+//  * coarse-level coefficients are the mean of the fine children;
+//  * patch dof set: dofs whose basis support lies in the closed patch.
+#include "fem.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <atomic>
+#include <array>
+
+namespace stfem {
+
+// ---------------------------------------------------------------- quadrature
+static void legendre(int n, double x, double *p, double *dp) {
+  // P_n and P_n' by the three-term recurrence and P'_{j+1} = P'_{j-1} + (2j+1) P_j
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (n == 0) {
+    *p = 1.0;
+    *dp = 0.0;
+    return;
+  }
+  for (int j = 1; j < n; ++j) {
+    double p2 = ((2 * j + 1) * x * p1 - j * p0) / (j + 1);
+    double d2 = d0 + (2 * j + 1) * p1;
+    p0 = p1;
+    p1 = p2;
+    d0 = d1;
+    d1 = d2;
+  }
+  *p = p1;
+  *dp = d1;
+}
+
+Rule gauss01(int n) {
+  Rule r;
+  r.x.resize(n);
+  r.w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(n, x, &p, &dp);
+      double dx = p / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double p, dp;
+    legendre(n, x, &p, &dp);
+    r.x[n - 1 - i] = 0.5 * (x + 1.0);
+    r.w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return r;
+}
+
+std::vector<double> lobatto01(int r) {
+  std::vector<double> x(r + 1);
+  x[0] = -1.0;
+  x[r] = 1.0;
+  for (int i = 1; i < r; ++i) {
+    double z = -std::cos(M_PI * i / r);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(r, z, &p, &dp);
+      double d2 = (2.0 * z * dp - r * (r + 1.0) * p) / (1.0 - z * z); // P_r''
+      double dz = dp / d2;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  for (auto &v : x) v = 0.5 * (v + 1.0);
+  return x;
+}
+
+Rule radau_right(int n) {
+  // interior nodes: zeros of P_{n-1} - P_n in (-1, 1) by bracketing and
+  // bisection; weights (1 + x) / (n^2 P_{n-1}(x)^2), end weight 2 / n^2.
+  Rule r;
+  auto f = [n](double x) {
+    double a, da, b, db;
+    legendre(n - 1, x, &a, &da);
+    legendre(n, x, &b, &db);
+    return a - b;
+  };
+  const int M = 20000;
+  double xa = -1.0, fa = f(xa);
+  for (int i = 1; i <= M && (int)r.x.size() < n - 1; ++i) {
+    double xb = -1.0 + 1.999 * i / M, fb = f(xb);
+    if (fa == 0.0) {
+      r.x.push_back(xa);
+    } else if (fa * fb < 0.0) {
+      double lo = xa, hi = xb, flo = fa;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi), fm = f(mid);
+        if ((fm < 0) == (flo < 0)) {
+          lo = mid;
+          flo = fm;
+        } else {
+          hi = mid;
+        }
+      }
+      r.x.push_back(0.5 * (lo + hi));
+    }
+    xa = xb;
+    fa = fb;
+  }
+  for (double x : r.x) {
+    double a, da;
+    legendre(n - 1, x, &a, &da);
+    r.w.push_back((1.0 + x) / (double(n) * n * a * a));
+  }
+  r.x.push_back(1.0);
+  r.w.push_back(2.0 / (double(n) * n));
+  return r;
+}
+
+void lagrange(const std::vector<double> &nodes, double x, double *val, double *der) {
+  const int n = (int)nodes.size();
+  for (int i = 0; i < n; ++i) {
+    double den = 1.0, num = 1.0, d = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      den *= nodes[i] - nodes[j];
+      // product rule: d/dx prod_j (x - x_j) = sum_l prod_{j != l} (x - x_j)
+      d = d * (x - nodes[j]) + num;
+      num *= x - nodes[j];
+    }
+    val[i] = num / den;
+    der[i] = d / den;
+  }
+}
+
+Temporal make_temporal(int k) {
+  Temporal T;
+  T.k = k;
+  T.q = k + 1;
+  Rule r = radau_right(T.q);
+  T.t = r.x;
+  T.w = r.w;
+  T.chi_m1.resize(T.q);
+  std::vector<double> v(T.q), d(T.q);
+  lagrange(T.t, -1.0, T.chi_m1.data(), d.data());
+  T.Dt.assign(T.q * T.q, 0.0);
+  for (int b = 0; b < T.q; ++b) {
+    lagrange(T.t, T.t[b], v.data(), d.data());
+    for (int a = 0; a < T.q; ++a)
+      T.Dt[b * T.q + a] = T.w[b] * d[a] + T.chi_m1[a] * T.chi_m1[b];
+  }
+  return T;
+}
+
+// ---------------------------------------------------------------- mesh
+Box make_box(int dim, const double *lo, const double *hi, const int *n, int hf_mode) {
+  Box b;
+  b.dim = dim;
+  b.vol = 1.0;
+  b.ncell = 1;
+  for (int i = 0; i < 3; ++i) {
+    b.lo[i] = i < dim ? lo[i] : 0.0;
+    b.hi[i] = i < dim ? hi[i] : 1.0;
+    b.n[i] = i < dim ? n[i] : 1;
+    b.h[i] = (b.hi[i] - b.lo[i]) / b.n[i];
+    if (i < dim) {
+      b.vol *= b.h[i];
+      b.ncell *= b.n[i];
+    }
+  }
+  b.hF = hf_mode == 1 ? std::pow(b.vol, 1.0 / dim) : b.vol;
+  return b;
+}
+
+Coef coarsen(const Coef &f, const Box &fb) {
+  Coef c;
+  c.rho = f.rho;
+  c.alpha = f.alpha;
+  c.c0 = f.c0;
+  int nc[3] = {1, 1, 1};
+  for (int i = 0; i < fb.dim; ++i) nc[i] = fb.n[i] / 2;
+  long ncc = (long)nc[0] * nc[1] * nc[2];
+  c.lam.assign(ncc, 0.0);
+  c.mu.assign(ncc, 0.0);
+  c.kap.assign(ncc, 0.0);
+  const int nchild = 1 << fb.dim;
+  for (int z = 0; z < nc[2]; ++z)
+    for (int y = 0; y < nc[1]; ++y)
+      for (int x = 0; x < nc[0]; ++x) {
+        long ci = x + (long)nc[0] * (y + (long)nc[1] * z);
+        for (int ch = 0; ch < nchild; ++ch) {
+          int fx = 2 * x + (ch & 1), fy = fb.dim > 1 ? 2 * y + ((ch >> 1) & 1) : 0,
+              fz = fb.dim > 2 ? 2 * z + ((ch >> 2) & 1) : 0;
+          long fi = fx + (long)fb.n[0] * (fy + (long)fb.n[1] * fz);
+          c.lam[ci] += f.lam[fi] / nchild;
+          c.mu[ci] += f.mu[fi] / nchild;
+          c.kap[ci] += f.kap[fi] / nchild;
+        }
+      }
+  return c;
+}
+
+Lattice make_lattice(const Box &b, int m) {
+  Lattice L;
+  L.dim = b.dim;
+  L.m = m;
+  L.nnodes = 1;
+  for (int i = 0; i < 3; ++i) {
+    L.dims[i] = i < b.dim ? m * b.n[i] + 1 : 1;
+    L.nnodes *= L.dims[i];
+  }
+  L.ref = lobatto01(m);
+  return L;
+}
+
+void cells_of(int a, int m, int ncell, int *c_lo, int *c_hi) {
+  if (a % m == 0) {
+    *c_lo = std::max(a / m - 1, 0);
+    *c_hi = std::min(a / m, ncell - 1);
+  } else {
+    *c_lo = *c_hi = a / m;
+  }
+}
+
+// ---------------------------------------------------------------- assembly
+namespace {
+
+inline void unflatten(long idx, const int *dims, int dim, int *a) {
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      a[i] = (int)(idx % dims[i]);
+      idx /= dims[i];
+    } else {
+      a[i] = 0;
+    }
+  }
+}
+
+inline long flatten(const int *a, const int *dims) {
+  return a[0] + (long)dims[0] * (a[1] + (long)dims[1] * a[2]);
+}
+
+// Neighbour box of a node (lattice coordinate a with degree m_row) inside the
+// lattice of degree m_col: the nodes of all cells holding the node.
+struct NbrBox {
+  int lo[3], ext[3];
+  long size;
+};
+
+inline NbrBox nbr_box(const int *a, int m_row, int m_col, const Box &b) {
+  NbrBox nb;
+  nb.size = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < b.dim) {
+      int clo, chi;
+      cells_of(a[i], m_row, b.n[i], &clo, &chi);
+      nb.lo[i] = m_col * clo;
+      nb.ext[i] = m_col * (chi + 1) - nb.lo[i] + 1;
+    } else {
+      nb.lo[i] = 0;
+      nb.ext[i] = 1;
+    }
+    nb.size *= nb.ext[i];
+  }
+  return nb;
+}
+
+inline long nbr_pos(const NbrBox &nb, const int *a) {
+  return (a[0] - nb.lo[0]) + (long)nb.ext[0] * ((a[1] - nb.lo[1]) + (long)nb.ext[1] * (a[2] - nb.lo[2]));
+}
+
+// Node-level matrix with a fixed number of values per entry.
+struct NodeMat {
+  std::vector<long> rowptr;
+  std::vector<double> val; // nvals per entry
+  int nvals = 1;
+};
+
+NodeMat make_nodemat(const Lattice &row, const Lattice &colL, const Box &b, int nvals) {
+  NodeMat M;
+  M.nvals = nvals;
+  M.rowptr.resize(row.nnodes + 1);
+  M.rowptr[0] = 0;
+  int a[3];
+  for (long i = 0; i < row.nnodes; ++i) {
+    unflatten(i, row.dims, b.dim, a);
+    M.rowptr[i + 1] = M.rowptr[i] + nbr_box(a, row.m, colL.m, b).size;
+  }
+  M.val.assign(M.rowptr[row.nnodes] * nvals, 0.0);
+  return M;
+}
+
+// Tensor-product reference data of one scalar space at a set of points.
+struct RefData {
+  int nloc = 0, npts = 0, dim = 2;
+  std::vector<double> phi;  // [pt][loc]
+  std::vector<double> dphi; // [pt][loc][dim], physical derivatives
+  std::vector<int> loc;     // [loc][3] local lattice offsets
+};
+
+RefData ref_data(const Lattice &L, const Box &b, const std::vector<std::array<double, 3>> &pts) {
+  RefData R;
+  R.dim = b.dim;
+  const int m1 = L.m + 1;
+  R.nloc = 1;
+  for (int i = 0; i < b.dim; ++i) R.nloc *= m1;
+  R.npts = (int)pts.size();
+  R.loc.resize(R.nloc * 3);
+  for (int l = 0; l < R.nloc; ++l) {
+    int t = l;
+    for (int i = 0; i < 3; ++i) {
+      if (i < b.dim) {
+        R.loc[l * 3 + i] = t % m1;
+        t /= m1;
+      } else {
+        R.loc[l * 3 + i] = 0;
+      }
+    }
+  }
+  R.phi.assign((size_t)R.npts * R.nloc, 0.0);
+  R.dphi.assign((size_t)R.npts * R.nloc * b.dim, 0.0);
+  std::vector<double> v(m1), d(m1);
+  for (int q = 0; q < R.npts; ++q) {
+    double vals[3][16] = {}, ders[3][16] = {};
+    for (int i = 0; i < b.dim; ++i) {
+      lagrange(L.ref, pts[q][i], v.data(), d.data());
+      for (int j = 0; j < m1; ++j) {
+        vals[i][j] = v[j];
+        ders[i][j] = d[j] / b.h[i];
+      }
+    }
+    for (int l = 0; l < R.nloc; ++l) {
+      double p = 1.0;
+      for (int i = 0; i < b.dim; ++i) p *= vals[i][R.loc[l * 3 + i]];
+      R.phi[(size_t)q * R.nloc + l] = p;
+      for (int j = 0; j < b.dim; ++j) {
+        double g = 1.0;
+        for (int i = 0; i < b.dim; ++i) g *= (i == j) ? ders[i][R.loc[l * 3 + i]] : vals[i][R.loc[l * 3 + i]];
+        R.dphi[((size_t)q * R.nloc + l) * b.dim + j] = g;
+      }
+    }
+  }
+  return R;
+}
+
+std::vector<std::array<double, 3>> cell_points(const Box &b, int nq, std::vector<double> *w) {
+  Rule g = gauss01(nq);
+  std::vector<std::array<double, 3>> pts;
+  w->clear();
+  int nz = b.dim > 2 ? nq : 1, ny = b.dim > 1 ? nq : 1;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nq; ++x) {
+        pts.push_back({g.x[x], b.dim > 1 ? g.x[y] : 0.0, b.dim > 2 ? g.x[z] : 0.0});
+        double ww = g.w[x] * (b.dim > 1 ? g.w[y] : 1.0) * (b.dim > 2 ? g.w[z] : 1.0);
+        w->push_back(ww * b.vol);
+      }
+  return pts;
+}
+
+std::vector<std::array<double, 3>> face_points(const Box &b, int nq, int ax, int side,
+                                               std::vector<double> *w) {
+  Rule g = gauss01(nq);
+  std::vector<std::array<double, 3>> pts;
+  w->clear();
+  int other[2], no = 0;
+  for (int i = 0; i < b.dim; ++i)
+    if (i != ax) other[no++] = i;
+  double area = b.vol / b.h[ax];
+  int n1 = no > 1 ? nq : 1;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < nq; ++i) {
+      std::array<double, 3> p = {0, 0, 0};
+      p[ax] = side;
+      p[other[0]] = g.x[i];
+      if (no > 1) p[other[1]] = g.x[j];
+      pts.push_back(p);
+      w->push_back(g.w[i] * (no > 1 ? g.w[j] : 1.0) * area);
+    }
+  return pts;
+}
+
+} // namespace
+
+Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
+  Level L;
+  L.box = b;
+  L.r = r;
+  L.coef = coef;
+  L.U = make_lattice(b, r);
+  L.P = make_lattice(b, r - 1);
+  const int d = b.dim;
+  L.R = (long)d * L.U.nnodes;
+  L.S = L.P.nnodes;
+  L.ns = 2 * L.R + L.S;
+  const double gam_a = 5.0e4 * r * (r + 1), gam_b = 0.5 * r * (r - 1);
+  const double alpha = coef.alpha;
+
+  // reference element data
+  std::vector<double> wq;
+  auto pts = cell_points(b, r + 2, &wq);
+  RefData RU = ref_data(L.U, b, pts), RP = ref_data(L.P, b, pts);
+  const int nu = RU.nloc, np = RP.nloc, nq = RU.npts, du = nu * d;
+  // unit-coefficient element matrices
+  std::vector<double> Mu(nu * nu, 0), Kmu(du * du, 0), Klam(du * du, 0), Cv(np * du, 0), Bv(np * np, 0),
+      Mp(np * np, 0);
+  for (int q = 0; q < nq; ++q) {
+    const double W = wq[q];
+    const double *pu = &RU.phi[(size_t)q * nu], *gu = &RU.dphi[(size_t)q * nu * d];
+    const double *pp = &RP.phi[(size_t)q * np], *gp = &RP.dphi[(size_t)q * np * d];
+    for (int i = 0; i < nu; ++i)
+      for (int j = 0; j < nu; ++j) {
+        Mu[i * nu + j] += W * pu[i] * pu[j];
+        double gg = 0;
+        for (int a = 0; a < d; ++a) gg += gu[i * d + a] * gu[j * d + a];
+        for (int c = 0; c < d; ++c)
+          for (int cp = 0; cp < d; ++cp) {
+            int I = i * d + c, J = j * d + cp;
+            Kmu[I * du + J] += W * ((c == cp ? gg : 0.0) + gu[j * d + c] * gu[i * d + cp]);
+            Klam[I * du + J] += W * gu[i * d + c] * gu[j * d + cp];
+          }
+      }
+    for (int s = 0; s < np; ++s)
+      for (int j = 0; j < nu; ++j)
+        for (int cp = 0; cp < d; ++cp) Cv[s * du + j * d + cp] += -alpha * W * gu[j * d + cp] * pp[s];
+    for (int rr = 0; rr < np; ++rr)
+      for (int s = 0; s < np; ++s) {
+        double gg = 0;
+        for (int a = 0; a < d; ++a) gg += gp[s * d + a] * gp[rr * d + a];
+        Bv[rr * np + s] += W * gg;
+        Mp[rr * np + s] += W * pp[rr] * pp[s];
+      }
+  }
+  // face matrices, per face id
+  struct FaceMats {
+    std::vector<double> Kmu, Klam, Kpen, C, B, Bpen;
+  };
+  std::vector<FaceMats> F(2 * d);
+  for (int ax = 0; ax < d; ++ax)
+    for (int side = 0; side < 2; ++side) {
+      FaceMats &fm = F[2 * ax + side];
+      fm.Kmu.assign(du * du, 0);
+      fm.Klam.assign(du * du, 0);
+      fm.Kpen.assign(du * du, 0);
+      fm.C.assign(np * du, 0);
+      fm.B.assign(np * np, 0);
+      fm.Bpen.assign(np * np, 0);
+      std::vector<double> wf;
+      auto fp = face_points(b, r + 2, ax, side, &wf);
+      RefData FU = ref_data(L.U, b, fp), FP = ref_data(L.P, b, fp);
+      double n[3] = {0, 0, 0};
+      n[ax] = side ? 1.0 : -1.0;
+      for (int q = 0; q < (int)fp.size(); ++q) {
+        const double W = wf[q];
+        const double *pu = &FU.phi[(size_t)q * nu], *gu = &FU.dphi[(size_t)q * nu * d];
+        const double *pp = &FP.phi[(size_t)q * np], *gp = &FP.dphi[(size_t)q * np * d];
+        for (int i = 0; i < nu; ++i) {
+          double dni = 0;
+          for (int a = 0; a < d; ++a) dni += gu[i * d + a] * n[a];
+          for (int j = 0; j < nu; ++j) {
+            double dnj = 0;
+            for (int a = 0; a < d; ++a) dnj += gu[j * d + a] * n[a];
+            for (int c = 0; c < d; ++c)
+              for (int cp = 0; cp < d; ++cp) {
+                int I = i * d + c, J = j * d + cp;
+                double delta = (c == cp) ? 1.0 : 0.0;
+                // -<sigma(psi_J) n, psi_I> - <psi_J, sigma(psi_I) n>
+                fm.Kmu[I * du + J] += -W * pu[i] * (delta * dnj + gu[j * d + c] * n[cp]) -
+                                      W * pu[j] * (delta * dni + gu[i * d + cp] * n[c]);
+                fm.Klam[I * du + J] += -W * pu[i] * gu[j * d + cp] * n[c] - W * pu[j] * gu[i * d + c] * n[cp];
+                fm.Kpen[I * du + J] += delta * (gam_a / b.hF) * W * pu[i] * pu[j];
+              }
+          }
+        }
+        for (int s = 0; s < np; ++s)
+          for (int j = 0; j < nu; ++j)
+            for (int cp = 0; cp < d; ++cp) fm.C[s * du + j * d + cp] += alpha * W * pu[j] * n[cp] * pp[s];
+        for (int rr = 0; rr < np; ++rr) {
+          double dnr = 0;
+          for (int a = 0; a < d; ++a) dnr += gp[rr * d + a] * n[a];
+          for (int s = 0; s < np; ++s) {
+            double dns = 0;
+            for (int a = 0; a < d; ++a) dns += gp[s * d + a] * n[a];
+            fm.B[rr * np + s] += -W * (dns * pp[rr] + pp[s] * dnr);
+            fm.Bpen[rr * np + s] += (gam_b / b.hF) * W * pp[s] * pp[rr];
+          }
+        }
+      }
+    }
+
+  // node-level matrices
+  NodeMat UU = make_nodemat(L.U, L.U, b, 1 + d * d); // M, K[c][c']
+  NodeMat UP = make_nodemat(L.U, L.P, b, d);         // C^T: C[s][(I,c)]
+  NodeMat PU = make_nodemat(L.P, L.U, b, d);         // C[s][(J,c')]
+  NodeMat PP = make_nodemat(L.P, L.P, b, 2);         // Mp, B
+  std::vector<double> Ke(du * du), Ce(np * du), Be(np * np);
+  int cm[3];
+  for (long c = 0; c < b.ncell; ++c) {
+    unflatten(c, b.n, d, cm);
+    const double lam = coef.lam[c], mu = coef.mu[c], kap = coef.kap[c];
+    for (int i = 0; i < du * du; ++i) Ke[i] = lam * Klam[i] + mu * Kmu[i];
+    for (int i = 0; i < np * du; ++i) Ce[i] = Cv[i];
+    for (int i = 0; i < np * np; ++i) Be[i] = kap * Bv[i];
+    for (int ax = 0; ax < d; ++ax)
+      for (int side = 0; side < 2; ++side) {
+        bool on = side ? (cm[ax] == b.n[ax] - 1) : (cm[ax] == 0);
+        if (!on) continue;
+        int f = 2 * ax + side;
+        if (bc.bc_u[f] == 0) {
+          for (int i = 0; i < du * du; ++i) Ke[i] += lam * F[f].Klam[i] + mu * F[f].Kmu[i] + F[f].Kpen[i];
+          for (int i = 0; i < np * du; ++i) Ce[i] += F[f].C[i];
+        }
+        if (bc.bc_p[f] == 0)
+          for (int i = 0; i < np * np; ++i) Be[i] += kap * F[f].B[i] + F[f].Bpen[i];
+      }
+    // global lattice coordinates of local nodes
+    int gu_[216][3], gp_[216][3];
+    long giu[216], gip[216];
+    for (int l = 0; l < nu; ++l) {
+      for (int i = 0; i < 3; ++i) gu_[l][i] = (i < d) ? r * cm[i] + RU.loc[l * 3 + i] : 0;
+      giu[l] = flatten(gu_[l], L.U.dims);
+    }
+    for (int l = 0; l < np; ++l) {
+      for (int i = 0; i < 3; ++i) gp_[l][i] = (i < d) ? (r - 1) * cm[i] + RP.loc[l * 3 + i] : 0;
+      gip[l] = flatten(gp_[l], L.P.dims);
+    }
+    for (int i = 0; i < nu; ++i) {
+      NbrBox nbu = nbr_box(gu_[i], r, r, b), nbp = nbr_box(gu_[i], r, r - 1, b);
+      for (int j = 0; j < nu; ++j) {
+        long e = UU.rowptr[giu[i]] + nbr_pos(nbu, gu_[j]);
+        double *v = &UU.val[e * UU.nvals];
+        v[0] += Mu[i * nu + j];
+        for (int c = 0; c < d; ++c)
+          for (int cp = 0; cp < d; ++cp) v[1 + c * d + cp] += Ke[(i * d + c) * du + j * d + cp];
+      }
+      for (int s = 0; s < np; ++s) {
+        long e = UP.rowptr[giu[i]] + nbr_pos(nbp, gp_[s]);
+        for (int c = 0; c < d; ++c) UP.val[e * d + c] += Ce[s * du + i * d + c];
+      }
+    }
+    for (int s = 0; s < np; ++s) {
+      NbrBox nbu = nbr_box(gp_[s], r - 1, r, b), nbp = nbr_box(gp_[s], r - 1, r - 1, b);
+      for (int j = 0; j < nu; ++j) {
+        long e = PU.rowptr[gip[s]] + nbr_pos(nbu, gu_[j]);
+        for (int cp = 0; cp < d; ++cp) PU.val[e * d + cp] += Ce[s * du + j * d + cp];
+      }
+      for (int t = 0; t < np; ++t) {
+        long e = PP.rowptr[gip[s]] + nbr_pos(nbp, gp_[t]);
+        PP.val[e * 2 + 0] += Mp[s * np + t];
+        PP.val[e * 2 + 1] += Be[s * np + t];
+      }
+    }
+  }
+
+  // expand to the spatial system CSR (rows u-eq, v-eq, p-eq; cols V, U, P)
+  const double rho = coef.rho, c0 = coef.c0;
+  const long R = L.R, S = L.S, ns = L.ns;
+  L.rowptr.assign(ns + 1, 0);
+  int a[3];
+  for (long I = 0; I < L.U.nnodes; ++I) {
+    long nnu = UU.rowptr[I + 1] - UU.rowptr[I], nnp = UP.rowptr[I + 1] - UP.rowptr[I];
+    for (int c = 0; c < d; ++c) {
+      L.rowptr[I * d + c + 1] = 2 * nnu;
+      L.rowptr[R + I * d + c + 1] = nnu + d * nnu + nnp;
+    }
+  }
+  for (long s = 0; s < S; ++s)
+    L.rowptr[2 * R + s + 1] = d * (PU.rowptr[s + 1] - PU.rowptr[s]) + (PP.rowptr[s + 1] - PP.rowptr[s]);
+  for (long i = 0; i < ns; ++i) L.rowptr[i + 1] += L.rowptr[i];
+  const long nnz = L.rowptr[ns];
+  L.col.resize(nnz);
+  L.v1.assign(nnz, 0.0);
+  L.v2.assign(nnz, 0.0);
+  for (long I = 0; I < L.U.nnodes; ++I) {
+    unflatten(I, L.U.dims, d, a);
+    NbrBox nbu = nbr_box(a, r, r, b), nbp = nbr_box(a, r, r - 1, b);
+    std::vector<long> Jn(nbu.size), Sn(nbp.size);
+    long t = 0;
+    for (int z = 0; z < nbu.ext[2]; ++z)
+      for (int y = 0; y < nbu.ext[1]; ++y)
+        for (int x = 0; x < nbu.ext[0]; ++x) {
+          int aj[3] = {nbu.lo[0] + x, nbu.lo[1] + y, nbu.lo[2] + z};
+          Jn[t++] = flatten(aj, L.U.dims);
+        }
+    t = 0;
+    for (int z = 0; z < nbp.ext[2]; ++z)
+      for (int y = 0; y < nbp.ext[1]; ++y)
+        for (int x = 0; x < nbp.ext[0]; ++x) {
+          int aj[3] = {nbp.lo[0] + x, nbp.lo[1] + y, nbp.lo[2] + z};
+          Sn[t++] = flatten(aj, L.P.dims);
+        }
+    const double *uu = &UU.val[UU.rowptr[I] * UU.nvals];
+    const double *up = &UP.val[UP.rowptr[I] * d];
+    for (int c = 0; c < d; ++c) {
+      // u-equation row (multiplied by rho): -rho M on V (W), rho M on U (Dt)
+      long e = L.rowptr[I * d + c];
+      for (long j = 0; j < nbu.size; ++j, ++e) {
+        L.col[e] = (int)(Jn[j] * d + c);
+        L.v2[e] = -rho * uu[j * UU.nvals];
+      }
+      for (long j = 0; j < nbu.size; ++j, ++e) {
+        L.col[e] = (int)(R + Jn[j] * d + c);
+        L.v1[e] = rho * uu[j * UU.nvals];
+      }
+      // v-equation row: rho M on V (Dt), K on U (W), C^T on P (W)
+      e = L.rowptr[R + I * d + c];
+      for (long j = 0; j < nbu.size; ++j, ++e) {
+        L.col[e] = (int)(Jn[j] * d + c);
+        L.v1[e] = rho * uu[j * UU.nvals];
+      }
+      for (long j = 0; j < nbu.size; ++j)
+        for (int cp = 0; cp < d; ++cp, ++e) {
+          L.col[e] = (int)(R + Jn[j] * d + cp);
+          L.v2[e] = uu[j * UU.nvals + 1 + c * d + cp];
+        }
+      for (long s = 0; s < nbp.size; ++s, ++e) {
+        L.col[e] = (int)(2 * R + Sn[s]);
+        L.v2[e] = up[s * d + c];
+      }
+    }
+  }
+  for (long s = 0; s < S; ++s) {
+    unflatten(s, L.P.dims, d, a);
+    NbrBox nbu = nbr_box(a, r - 1, r, b), nbp = nbr_box(a, r - 1, r - 1, b);
+    long e = L.rowptr[2 * R + s];
+    const double *pu = &PU.val[PU.rowptr[s] * d];
+    const double *pp = &PP.val[PP.rowptr[s] * 2];
+    long t = 0;
+    for (int z = 0; z < nbu.ext[2]; ++z)
+      for (int y = 0; y < nbu.ext[1]; ++y)
+        for (int x = 0; x < nbu.ext[0]; ++x, ++t) {
+          int aj[3] = {nbu.lo[0] + x, nbu.lo[1] + y, nbu.lo[2] + z};
+          long J = flatten(aj, L.U.dims);
+          for (int cp = 0; cp < d; ++cp, ++e) {
+            L.col[e] = (int)(J * d + cp);
+            L.v2[e] = -pu[t * d + cp];
+          }
+        }
+    t = 0;
+    for (int z = 0; z < nbp.ext[2]; ++z)
+      for (int y = 0; y < nbp.ext[1]; ++y)
+        for (int x = 0; x < nbp.ext[0]; ++x, ++t, ++e) {
+          int aj[3] = {nbp.lo[0] + x, nbp.lo[1] + y, nbp.lo[2] + z};
+          L.col[e] = (int)(2 * R + flatten(aj, L.P.dims));
+          L.v1[e] = c0 * pp[t * 2 + 0];
+          L.v2[e] = pp[t * 2 + 1];
+        }
+  }
+  return L;
+}
+
+// ---------------------------------------------------------------- transfers
+CSR prolongation(const Lattice &cl, const Box &cb, const Lattice &fl, const Box &fb) {
+  CSR P;
+  P.nrows = fl.nnodes;
+  P.ncols = cl.nnodes;
+  P.rowptr.assign(P.nrows + 1, 0);
+  const int m = fl.m, d = fb.dim;
+  std::vector<double> v(m + 1), dd(m + 1);
+  int a[3];
+  for (long f = 0; f < fl.nnodes; ++f) {
+    unflatten(f, fl.dims, d, a);
+    double w1[3][16];
+    int base[3];
+    for (int i = 0; i < 3; ++i) {
+      if (i < d) {
+        int cf = std::min(a[i] / m, fb.n[i] - 1);
+        int loc = a[i] - m * cf;
+        int cc = cf / 2;
+        double xi = ((cf % 2) + fl.ref[loc]) / 2.0;
+        lagrange(cl.ref, xi, v.data(), dd.data());
+        for (int j = 0; j <= m; ++j) w1[i][j] = v[j];
+        base[i] = m * cc;
+      } else {
+        w1[i][0] = 1.0;
+        base[i] = 0;
+      }
+    }
+    int ez = d > 2 ? m + 1 : 1, ey = d > 1 ? m + 1 : 1;
+    for (int z = 0; z < ez; ++z)
+      for (int y = 0; y < ey; ++y)
+        for (int x = 0; x <= m; ++x) {
+          double w = w1[0][x] * w1[1][y] * w1[2][z];
+          if (std::fabs(w) <= 1e-14) continue;
+          int ac[3] = {base[0] + x, base[1] + y, base[2] + z};
+          P.col.push_back((int)flatten(ac, cl.dims));
+          P.val.push_back(w);
+        }
+    P.rowptr[f + 1] = (int)P.col.size();
+  }
+  (void)cb;
+  return P;
+}
+
+CSR transpose(const CSR &a) {
+  CSR t;
+  t.nrows = a.ncols;
+  t.ncols = a.nrows;
+  t.rowptr.assign(t.nrows + 1, 0);
+  for (int c : a.col) t.rowptr[c + 1]++;
+  for (long i = 0; i < t.nrows; ++i) t.rowptr[i + 1] += t.rowptr[i];
+  t.col.resize(a.col.size());
+  t.val.resize(a.val.size());
+  std::vector<int> pos(t.rowptr.begin(), t.rowptr.end() - 1);
+  for (long r = 0; r < a.nrows; ++r)
+    for (int e = a.rowptr[r]; e < a.rowptr[r + 1]; ++e) {
+      int p = pos[a.col[e]]++;
+      t.col[p] = (int)r;
+      t.val[p] = a.val[e];
+    }
+  return t;
+}
+
+void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
+  const int d = F.box.dim;
+  const long Rf = F.R, Rc = Cl->R, nsf = F.ns, nsc = Cl->ns;
+  // spatial prolongation P_s (rows fine, cols coarse)
+  std::vector<long> pptr(nsf + 1, 0);
+  std::vector<int> pcol;
+  std::vector<double> pval;
+  for (long i = 0; i < nsf; ++i) {
+    if (i < 2 * Rf) {
+      const long blk = i / Rf, rem = i % Rf, node = rem / d;
+      const int comp = (int)(rem % d);
+      for (int e = Pu.rowptr[node]; e < Pu.rowptr[node + 1]; ++e) {
+        pcol.push_back((int)(blk * Rc + (long)Pu.col[e] * d + comp));
+        pval.push_back(Pu.val[e]);
+      }
+    } else {
+      const long node = i - 2 * Rf;
+      for (int e = Pp.rowptr[node]; e < Pp.rowptr[node + 1]; ++e) {
+        pcol.push_back((int)(2 * Rc + Pp.col[e]));
+        pval.push_back(Pp.val[e]);
+      }
+    }
+    pptr[i + 1] = (long)pcol.size();
+  }
+  // P_s^T (rows coarse)
+  std::vector<long> tptr(nsc + 1, 0);
+  for (int c : pcol) tptr[c + 1]++;
+  for (long i = 0; i < nsc; ++i) tptr[i + 1] += tptr[i];
+  std::vector<int> tcol(pcol.size());
+  std::vector<double> tval(pcol.size());
+  {
+    std::vector<long> fill(tptr.begin(), tptr.end() - 1);
+    for (long i = 0; i < nsf; ++i)
+      for (long e = pptr[i]; e < pptr[i + 1]; ++e) {
+        long p = fill[pcol[e]]++;
+        tcol[p] = (int)i;
+        tval[p] = pval[e];
+      }
+  }
+  // AP = S P_s (rows fine), two value arrays
+  std::vector<long> aptr(nsf + 1, 0);
+  std::vector<std::vector<int>> acol_t;
+  std::vector<std::vector<double>> a1_t, a2_t;
+  const int nt = n_threads();
+  std::vector<std::vector<int>> rows_col(nsf);
+  std::vector<std::vector<double>> rows_v1(nsf), rows_v2(nsf);
+  {
+    std::atomic<long> next(0);
+    auto work = [&]() {
+      std::vector<double> acc1(nsc, 0.0), acc2(nsc, 0.0);
+      std::vector<char> mark(nsc, 0);
+      std::vector<int> touched;
+      for (;;) {
+        const long i0 = next.fetch_add(256);
+        if (i0 >= nsf) break;
+        for (long i = i0; i < std::min(nsf, i0 + 256); ++i) {
+          touched.clear();
+          for (int e = F.rowptr[i]; e < F.rowptr[i + 1]; ++e) {
+            const int j = F.col[e];
+            const double x1 = F.v1[e], x2 = F.v2[e];
+            for (long f = pptr[j]; f < pptr[j + 1]; ++f) {
+              const int J = pcol[f];
+              if (!mark[J]) {
+                mark[J] = 1;
+                touched.push_back(J);
+                acc1[J] = acc2[J] = 0.0;
+              }
+              acc1[J] += x1 * pval[f];
+              acc2[J] += x2 * pval[f];
+            }
+          }
+          std::sort(touched.begin(), touched.end());
+          rows_col[i] = touched;
+          rows_v1[i].resize(touched.size());
+          rows_v2[i].resize(touched.size());
+          for (size_t t = 0; t < touched.size(); ++t) {
+            rows_v1[i][t] = acc1[touched[t]];
+            rows_v2[i][t] = acc2[touched[t]];
+            mark[touched[t]] = 0;
+          }
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(work);
+    for (auto &t : th) t.join();
+  }
+  // C = P_s^T AP (rows coarse)
+  std::vector<std::vector<int>> ccol(nsc);
+  std::vector<std::vector<double>> cv1(nsc), cv2(nsc);
+  {
+    std::atomic<long> next(0);
+    auto work = [&]() {
+      std::vector<double> acc1(nsc, 0.0), acc2(nsc, 0.0);
+      std::vector<char> mark(nsc, 0);
+      std::vector<int> touched;
+      for (;;) {
+        const long I0 = next.fetch_add(64);
+        if (I0 >= nsc) break;
+        for (long I = I0; I < std::min(nsc, I0 + 64); ++I) {
+          touched.clear();
+          for (long e = tptr[I]; e < tptr[I + 1]; ++e) {
+            const int i = tcol[e];
+            const double w = tval[e];
+            const std::vector<int> &rc = rows_col[i];
+            for (size_t t = 0; t < rc.size(); ++t) {
+              const int J = rc[t];
+              if (!mark[J]) {
+                mark[J] = 1;
+                touched.push_back(J);
+                acc1[J] = acc2[J] = 0.0;
+              }
+              acc1[J] += w * rows_v1[i][t];
+              acc2[J] += w * rows_v2[i][t];
+            }
+          }
+          std::sort(touched.begin(), touched.end());
+          ccol[I] = touched;
+          cv1[I].resize(touched.size());
+          cv2[I].resize(touched.size());
+          for (size_t t = 0; t < touched.size(); ++t) {
+            cv1[I][t] = acc1[touched[t]];
+            cv2[I][t] = acc2[touched[t]];
+            mark[touched[t]] = 0;
+          }
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(work);
+    for (auto &t : th) t.join();
+  }
+  Cl->rowptr.assign(nsc + 1, 0);
+  for (long I = 0; I < nsc; ++I) Cl->rowptr[I + 1] = Cl->rowptr[I] + (int)ccol[I].size();
+  Cl->col.resize(Cl->rowptr[nsc]);
+  Cl->v1.resize(Cl->rowptr[nsc]);
+  Cl->v2.resize(Cl->rowptr[nsc]);
+  for (long I = 0; I < nsc; ++I) {
+    std::copy(ccol[I].begin(), ccol[I].end(), Cl->col.begin() + Cl->rowptr[I]);
+    std::copy(cv1[I].begin(), cv1[I].end(), Cl->v1.begin() + Cl->rowptr[I]);
+    std::copy(cv2[I].begin(), cv2[I].end(), Cl->v2.begin() + Cl->rowptr[I]);
+  }
+}
+
+// ---------------------------------------------------------------- patches
+int n_threads() {
+  unsigned n = std::thread::hardware_concurrency();
+  return n ? (int)n : 4;
+}
+
+bool invert(double *a, int n) {
+  std::vector<int> piv(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(a[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::fabs(a[(size_t)i * n + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+    double *rk = a + (size_t)k * n;
+    const double inv = 1.0 / rk[k];
+    rk[k] = 1.0;
+    for (int j = 0; j < n; ++j) rk[j] *= inv;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      double *ri = a + (size_t)i * n;
+      const double f = ri[k];
+      if (f == 0.0) continue;
+      ri[k] = 0.0;
+      for (int j = 0; j < n; ++j) ri[j] -= f * rk[j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k)
+      for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + k], a[(size_t)i * n + piv[k]]);
+  return true;
+}
+
+static void patch_axis(int v, int m, int ncell, int *lo, int *hi) {
+  int c0 = std::max(v - 1, 0), c1 = std::min(v, ncell - 1);
+  int alo = m * c0, ahi = m * (c1 + 1);
+  *lo = (c0 == 0) ? alo : alo + 1;
+  *hi = (c1 == ncell - 1) ? ahi : ahi - 1;
+}
+
+int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out, std::string *err,
+                  bool invert_them) {
+  const Box &b = L.box;
+  const int d = b.dim, q = T.q;
+  int vdims[3] = {1, 1, 1};
+  long nv = 1;
+  for (int i = 0; i < d; ++i) {
+    vdims[i] = b.n[i] + 1;
+    nv *= vdims[i];
+  }
+  Patches &P = *out;
+  P = Patches();
+  P.npatch = nv;
+  P.size.resize(nv);
+  P.ld.resize(nv);
+  P.dof_off.resize(nv + 1);
+  P.inv_off.resize(nv + 1);
+  std::vector<std::vector<int>> spatial(nv);
+  int v[3];
+  for (long p = 0; p < nv; ++p) {
+    unflatten(p, vdims, d, v);
+    int ulo[3] = {0, 0, 0}, uhi[3] = {0, 0, 0}, plo[3] = {0, 0, 0}, phi[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) {
+      patch_axis(v[i], L.r, b.n[i], &ulo[i], &uhi[i]);
+      patch_axis(v[i], L.r - 1, b.n[i], &plo[i], &phi[i]);
+    }
+    std::vector<long> un, pn;
+    for (int z = ulo[2]; z <= uhi[2]; ++z)
+      for (int y = ulo[1]; y <= uhi[1]; ++y)
+        for (int x = ulo[0]; x <= uhi[0]; ++x) {
+          int a[3] = {x, y, z};
+          un.push_back(flatten(a, L.U.dims));
+        }
+    for (int z = plo[2]; z <= phi[2]; ++z)
+      for (int y = plo[1]; y <= phi[1]; ++y)
+        for (int x = plo[0]; x <= phi[0]; ++x) {
+          int a[3] = {x, y, z};
+          pn.push_back(flatten(a, L.P.dims));
+        }
+    std::vector<int> &sp = spatial[p];
+    for (long I : un)
+      for (int c = 0; c < d; ++c) sp.push_back((int)(I * d + c));
+    for (long I : un)
+      for (int c = 0; c < d; ++c) sp.push_back((int)(L.R + I * d + c));
+    for (long s : pn) sp.push_back((int)(2 * L.R + s));
+    P.size[p] = (int)sp.size() * q;
+  }
+  P.dof_off[0] = 0;
+  P.inv_off[0] = 0;
+  for (long p = 0; p < nv; ++p) {
+    int C = P.size[p];
+    P.ld[p] = (C + vec - 1) / vec * vec;
+    P.dof_off[p + 1] = P.dof_off[p] + C;
+    P.inv_off[p + 1] = P.inv_off[p] + (long long)C * P.ld[p];
+  }
+  P.dofs.resize(P.dof_off[nv]);
+  if (invert_them) P.inv.assign(P.inv_off[nv], 0.0);
+  for (long p = 0; p < nv; ++p) {
+    const std::vector<int> &sp = spatial[p];
+    long long o = P.dof_off[p];
+    for (int a = 0; a < q; ++a)
+      for (size_t m = 0; m < sp.size(); ++m) P.dofs[o++] = (int)(a * L.ns + sp[m]);
+  }
+  if (!invert_them) return 0;
+  // extract and invert in parallel
+  std::atomic<long> next(0);
+  std::atomic<long> bad(-1);
+  auto work = [&]() {
+    std::vector<int> loc(L.ns, -1);
+    std::vector<double> S1, S2, A;
+    for (;;) {
+      long p = next.fetch_add(1);
+      if (p >= nv) break;
+      const std::vector<int> &sp = spatial[p];
+      const int Cs = (int)sp.size(), C = Cs * q;
+      for (int m = 0; m < Cs; ++m) loc[sp[m]] = m;
+      S1.assign((size_t)Cs * Cs, 0.0);
+      S2.assign((size_t)Cs * Cs, 0.0);
+      for (int m = 0; m < Cs; ++m) {
+        int g = sp[m];
+        for (int e = L.rowptr[g]; e < L.rowptr[g + 1]; ++e) {
+          int lc = loc[L.col[e]];
+          if (lc < 0) continue;
+          S1[(size_t)m * Cs + lc] = L.v1[e];
+          S2[(size_t)m * Cs + lc] = L.v2[e];
+        }
+      }
+      for (int m = 0; m < Cs; ++m) loc[sp[m]] = -1;
+      A.assign((size_t)C * C, 0.0);
+      for (int bb = 0; bb < q; ++bb)
+        for (int aa = 0; aa < q; ++aa) {
+          const double dt = T.Dt[bb * q + aa], w = (aa == bb) ? 0.5 * tau * T.w[bb] : 0.0;
+          for (int m = 0; m < Cs; ++m)
+            for (int mp = 0; mp < Cs; ++mp)
+              A[(size_t)(bb * Cs + m) * C + aa * Cs + mp] = dt * S1[(size_t)m * Cs + mp] + w * S2[(size_t)m * Cs + mp];
+        }
+      if (!invert(A.data(), C)) {
+        bad.store(p);
+        continue;
+      }
+      double *dst = &P.inv[P.inv_off[p]];
+      const int ld = P.ld[p];
+      for (int i = 0; i < C; ++i)
+        for (int j = 0; j < C; ++j) dst[(size_t)j * ld + i] = A[(size_t)i * C + j];
+    }
+  };
+  int nt = std::min<long>(n_threads(), nv);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(work);
+  for (auto &t : th) t.join();
+  if (bad.load() >= 0) {
+    if (err) *err = "singular patch matrix (patch " + std::to_string(bad.load()) + ")";
+    return -1;
+  }
+  return 0;
+}
+
+std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau) {
+  const long ns = L.ns, N = ns * T.q;
+  std::vector<double> A((size_t)N * N, 0.0);
+  for (int bb = 0; bb < T.q; ++bb)
+    for (int aa = 0; aa < T.q; ++aa) {
+      const double dt = T.Dt[bb * T.q + aa], w = (aa == bb) ? 0.5 * tau * T.w[bb] : 0.0;
+      for (long i = 0; i < ns; ++i)
+        for (int e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e)
+          A[(size_t)(bb * ns + i) * N + aa * ns + L.col[e]] += dt * L.v1[e] + w * L.v2[e];
+    }
+  return A;
+}
+
+int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                    const stfem_bcs *bcs, double tau, std::vector<Level> *levels, std::vector<CSR> *Pu,
+                    std::vector<CSR> *Pp, std::string *err) {
+  if (!mesh || !deg || !mat || !bcs) {
+    *err = "null argument";
+    return STFEM_ERR_ARG;
+  }
+  const int d = mesh->dim;
+  if (d != 2 && d != 3) {
+    *err = "dim must be 2 or 3";
+    return STFEM_ERR_ARG;
+  }
+  if (deg->r < 2 || deg->r > 5 || (d == 3 && deg->r > 3) || deg->k < 0 || deg->k > 4) {
+    *err = "unsupported degrees (need 2 <= r <= 5 (r <= 3 in 3D), 0 <= k <= 4)";
+    return STFEM_ERR_ARG;
+  }
+  if (mesh->n_levels < 1 || mesh->n_levels > 12 || !(tau > 0.0)) {
+    *err = "invalid n_levels or tau";
+    return STFEM_ERR_ARG;
+  }
+  if (mesh->hf_mode != STFEM_HF_MEASURE && mesh->hf_mode != STFEM_HF_LENGTH) {
+    *err = "invalid hf_mode";
+    return STFEM_ERR_ARG;
+  }
+  if (mesh->coarse_op != STFEM_COARSE_GALERKIN && mesh->coarse_op != STFEM_COARSE_REDISCRETIZE) {
+    *err = "invalid coarse_op";
+    return STFEM_ERR_ARG;
+  }
+  for (int i = 0; i < d; ++i) {
+    if (mesh->n_cells[i] < 1 || (mesh->n_cells[i] % (1 << (mesh->n_levels - 1))) != 0 ||
+        !(mesh->hi[i] > mesh->lo[i])) {
+      *err = "n_cells must be positive and divisible by 2^(n_levels-1), and hi > lo";
+      return STFEM_ERR_ARG;
+    }
+  }
+  const int pid = bcs->problem;
+  if (pid < 0 || pid > 4 || (pid == STFEM_PROBLEM_PULSE && d != 3) ||
+      ((pid == STFEM_PROBLEM_PAPER_EOC || pid == STFEM_PROBLEM_PAPER_SUPERCONV) && d != 2)) {
+    *err = "unsupported problem id for this dimension";
+    return STFEM_ERR_ARG;
+  }
+  BCs bc;
+  for (int f = 0; f < 6; ++f) {
+    bc.bc_u[f] = f < 2 * d ? bcs->bc_u[f] : 0;
+    bc.bc_p[f] = f < 2 * d ? bcs->bc_p[f] : 0;
+    if (f < 2 * d) {
+      if ((bc.bc_u[f] != 0 && bc.bc_u[f] != 1) || (bc.bc_p[f] != 0 && bc.bc_p[f] != 1)) {
+        *err = "boundary condition flags must be 0 or 1";
+        return STFEM_ERR_ARG;
+      }
+      if (pid != STFEM_PROBLEM_NONE && pid != STFEM_PROBLEM_PULSE && (bc.bc_u[f] || bc.bc_p[f])) {
+        *err = "manufactured problems need Dirichlet conditions on every face";
+        return STFEM_ERR_ARG;
+      }
+    }
+  }
+  const int nlev = mesh->n_levels;
+  std::vector<Box> boxes(nlev);
+  std::vector<Coef> coefs(nlev);
+  Box fine = make_box(d, mesh->lo, mesh->hi, mesh->n_cells, mesh->hf_mode);
+  Coef c;
+  c.rho = mat->rho;
+  c.alpha = mat->alpha;
+  c.c0 = mat->c0;
+  c.lam.resize(fine.ncell);
+  c.mu.resize(fine.ncell);
+  c.kap.resize(fine.ncell);
+  for (long i = 0; i < fine.ncell; ++i) {
+    c.lam[i] = mat->lambda_cell_host ? mat->lambda_cell_host[i] : mat->lambda;
+    c.mu[i] = mat->mu_cell_host ? mat->mu_cell_host[i] : mat->mu;
+    c.kap[i] = mat->kappa_cell_host ? mat->kappa_cell_host[i] : mat->kappa;
+  }
+  boxes[nlev - 1] = fine;
+  coefs[nlev - 1] = c;
+  for (int l = nlev - 2; l >= 0; --l) {
+    coefs[l] = coarsen(coefs[l + 1], boxes[l + 1]);
+    int nc[3];
+    for (int i = 0; i < 3; ++i) nc[i] = i < d ? boxes[l + 1].n[i] / 2 : 1;
+    boxes[l] = make_box(d, mesh->lo, mesh->hi, nc, mesh->hf_mode);
+  }
+  levels->assign(nlev, Level());
+  const bool galerkin_ops = mesh->coarse_op == STFEM_COARSE_GALERKIN;
+  for (int l = 0; l < nlev; ++l) {
+    if (galerkin_ops && l < nlev - 1) {
+      // sizes only; the matrix comes from the Galerkin product below
+      Level &Lv = (*levels)[l];
+      Lv.box = boxes[l];
+      Lv.r = deg->r;
+      Lv.coef = coefs[l];
+      Lv.U = make_lattice(boxes[l], deg->r);
+      Lv.P = make_lattice(boxes[l], deg->r - 1);
+      Lv.R = (long)d * Lv.U.nnodes;
+      Lv.S = Lv.P.nnodes;
+      Lv.ns = 2 * Lv.R + Lv.S;
+    } else {
+      (*levels)[l] = assemble_level(boxes[l], deg->r, coefs[l], bc);
+    }
+  }
+  Pu->assign(nlev, CSR());
+  Pp->assign(nlev, CSR());
+  for (int l = 1; l < nlev; ++l) {
+    (*Pu)[l] = prolongation((*levels)[l - 1].U, boxes[l - 1], (*levels)[l].U, boxes[l]);
+    (*Pp)[l] = prolongation((*levels)[l - 1].P, boxes[l - 1], (*levels)[l].P, boxes[l]);
+  }
+  if (galerkin_ops)
+    for (int l = nlev - 1; l >= 1; --l) galerkin((*levels)[l], (*Pu)[l], (*Pp)[l], &(*levels)[l - 1]);
+  return STFEM_OK;
+}
+
+} // namespace stfem

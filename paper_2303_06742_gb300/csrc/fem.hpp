@@ -1,0 +1,123 @@
+// Host-side setup of the space-time FE hierarchy (arXiv 2303.06742, Secs. 2-4).
+// Builds, per multigrid level, the spatial system matrix whose Kronecker
+// combination with the temporal matrices gives the slab matrix of Problem 4.1,
+// plus transfers, vertex patches, patch inverses and the coarse inverse.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stfem.h"
+
+namespace stfem {
+
+struct Rule {
+  std::vector<double> x, w;
+};
+
+Rule gauss01(int n);                  // n-point Gauss-Legendre on [0,1]
+std::vector<double> lobatto01(int r); // r+1 Gauss-Lobatto points on [0,1]
+Rule radau_right(int n);              // n-point right Gauss-Radau on [-1,1] (Eq. 2.4)
+// Lagrange basis on `nodes` at x: values val[i], derivatives der[i].
+void lagrange(const std::vector<double> &nodes, double x, double *val, double *der);
+
+// dG(k) temporal data: Radau nodes/weights on [-1,1], chi_a(-1) and
+// Dt[b*q+a] = w_b chi_a'(t_b) + chi_a(-1) chi_b(-1).
+struct Temporal {
+  int k = 0, q = 1;
+  std::vector<double> t, w, chi_m1, Dt;
+};
+Temporal make_temporal(int k);
+
+struct Box {
+  int dim = 2;
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  int n[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  double vol = 1, hF = 1;
+  long ncell = 1;
+};
+Box make_box(int dim, const double *lo, const double *hi, const int *n, int hf_mode);
+
+struct Coef {
+  double rho = 1, alpha = 1, c0 = 1;
+  std::vector<double> lam, mu, kap; // per cell of the level
+};
+Coef coarsen(const Coef &fine, const Box &fine_box);
+
+struct BCs {
+  int bc_u[6] = {0, 0, 0, 0, 0, 0};
+  int bc_p[6] = {0, 0, 0, 0, 0, 0};
+};
+
+// A scalar Lagrange lattice space Q_m on a box.
+struct Lattice {
+  int dim = 2, m = 1;
+  int dims[3] = {1, 1, 1};
+  long nnodes = 1;
+  std::vector<double> ref; // Gauss-Lobatto points on [0,1]
+};
+Lattice make_lattice(const Box &b, int m);
+// Range of cells (along one axis) whose closure holds lattice coordinate a.
+void cells_of(int a, int m, int ncell, int *c_lo, int *c_hi);
+
+// Spatial system matrix of one level: rows (u-eq, v-eq, p-eq), columns
+// (V, U, P); entry (v1, v2) multiplies Dt and W respectively, so that
+// (A x)_b = sum_a Dt[b,a] S1 x_a + W_b S2 x_b.
+struct Level {
+  Box box;
+  int r = 2;
+  Lattice U, P;
+  long R = 0, S = 0, ns = 0;
+  Coef coef;
+  std::vector<int> rowptr, col;
+  std::vector<double> v1, v2;
+  // per lattice node: spatial position, for initial values and loads
+};
+
+Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc);
+
+// Scalar interpolation coarse Q_m -> fine Q_m (fine rows), CSR.
+struct CSR {
+  long nrows = 0, ncols = 0;
+  std::vector<int> rowptr, col;
+  std::vector<double> val;
+};
+CSR prolongation(const Lattice &coarse, const Box &cbox, const Lattice &fine, const Box &fbox);
+CSR transpose(const CSR &a);
+// Galerkin product P_s^T S P_s of the spatial system of `fine` (both value
+// arrays), P_s = blockdiag(Pu (x) I_d, Pu (x) I_d, Pp); fills the matrix of
+// `coarse` (whose sizes must be set).
+void galerkin(const Level &fine, const CSR &Pu, const CSR &Pp, Level *coarse);
+
+// Vertex patches of a level (reading: dofs whose support lies in the closed
+// patch), with the patch matrices inverted in FP64.
+struct Patches {
+  long npatch = 0;
+  std::vector<int> size;          // C_P
+  std::vector<long long> dof_off; // offset into dofs
+  std::vector<int> dofs;          // global slab indices (paper order)
+  std::vector<long long> inv_off; // offset (elements) into inv
+  std::vector<double> inv;        // column-major A_P^{-1}, leading dim ld(C_P)
+  std::vector<int> ld;
+};
+// vec: elements per 16-byte vector of the storage type (2 for FP64, 4 for FP32).
+// invert_them = false only builds the dof lists.
+int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out,
+                  std::string *err, bool invert_them = true);
+
+// Dense row-major slab matrix of a level (for the coarse solve).
+std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau);
+// In-place Gauss-Jordan inverse with partial pivoting of a row-major n x n
+// matrix. Returns false on a zero pivot.
+bool invert(double *a, int n);
+
+int n_threads();
+
+// Validates the ABI arguments and builds every level (finest last) and the
+// scalar transfers Pu[l], Pp[l] from level l-1 to l (index 0 unused).
+int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                    const stfem_bcs *bcs, double tau, std::vector<Level> *levels, std::vector<CSR> *Pu,
+                    std::vector<CSR> *Pp, std::string *err);
+
+} // namespace stfem

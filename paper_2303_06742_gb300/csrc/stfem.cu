@@ -1,0 +1,1417 @@
+// GB300 (sm_103a) implementation of the GMRES-GMG solver for the space-time
+// FEM of dynamic poro-/thermoelasticity (arXiv 2303.06742) behind the C ABI
+// declared in include/stfem.h.
+//
+// Data layout in HBM: slab vectors in the paper's order (Eq. 4.4), time node
+// outermost, so that each spatial row of the Kronecker SpMV reads the q time
+// values of a column with q coalesced gathers.  Each level holds one spatial
+// CSR with two values per entry (coefficients of Dt and of W), the patch dof
+// lists and the patch inverses stored column-major (a thread owns VEC
+// consecutive rows and streams the inverse with 16-byte loads), and an inverse
+// map dof -> (patch, local row) for the deterministic averaged update.
+#include "../../include/stfem.h"
+#include "fem.hpp"
+#include "kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace stfem_dev;
+
+namespace {
+
+// ============================================================ device helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- SpMV
+// y_b = sum_a Dt[b,a] S1 x_a + W_b S2 x_b   (mode 0)
+// y_b = rhs_b - (...)                        (mode 1)
+// G lanes cooperate on one spatial row.
+template <typename T, int Q, int G>
+__global__ void __launch_bounds__(256) k_spmv(long ns, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                              const T *__restrict__ v1, const T *__restrict__ v2, TimeCoef<T> tc,
+                                              const T *__restrict__ x, const T *__restrict__ rhs,
+                                              T *__restrict__ y, int mode) {
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long row = gid / G;
+  const int lane = threadIdx.x % G;
+  const bool valid = row < ns;
+  T s1[Q], s2[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) s1[a] = s2[a] = T(0);
+  if (valid) {
+    const int e1 = rowptr[row + 1];
+    for (int e = rowptr[row] + lane; e < e1; e += G) {
+      const int c = col[e];
+      const T a1 = v1[e], a2 = v2[e];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T xv = x[(long)a * ns + c];
+        s1[a] += a1 * xv;
+        s2[a] += a2 * xv;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      s1[a] += __shfl_xor_sync(0xffffffffu, s1[a], o);
+      s2[a] += __shfl_xor_sync(0xffffffffu, s2[a], o);
+    }
+  }
+  if (valid && lane < Q) {
+    // lane b writes time node b
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      if (b != lane) continue;
+      T acc = tc.W[b] * s2[b];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) acc += tc.Dt[b * Q + a] * s1[a];
+      const long o = (long)b * ns + row;
+      y[o] = mode ? rhs[o] - acc : acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Vanka
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void fma_vec(T *acc, const typename Vec16<T>::type &a, T r);
+template <>
+__device__ __forceinline__ void fma_vec<float>(float *acc, const float4 &a, float r) {
+  acc[0] += a.x * r;
+  acc[1] += a.y * r;
+  acc[2] += a.z * r;
+  acc[3] += a.w * r;
+}
+template <>
+__device__ __forceinline__ void fma_vec<double>(double *acc, const double2 &a, double r) {
+  acc[0] += a.x * r;
+  acc[1] += a.y * r;
+}
+
+// y_P = A_P^{-1} R_P res for every patch P of the level (one CTA per patch).
+// The inverse is column-major with leading dimension ld_P (multiple of VEC);
+// a thread owns VEC consecutive rows and loops over the columns, so a warp
+// streams 32 x 16 contiguous bytes per column.
+template <typename T>
+__global__ void __launch_bounds__(512) k_patch_apply(const int *__restrict__ psize, const long long *__restrict__ pdoff,
+                                                     const int *__restrict__ pdofs, const long long *__restrict__ pioff,
+                                                     const int *__restrict__ pld, const T *__restrict__ pinv,
+                                                     const T *__restrict__ res, T *__restrict__ y) {
+  using V = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  extern __shared__ unsigned char smem_raw[];
+  T *rs = reinterpret_cast<T *>(smem_raw);
+  const long p = blockIdx.x;
+  const int C = psize[p];
+  const long long doff = pdoff[p];
+  for (int j = threadIdx.x; j < C; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
+  __syncthreads();
+  const T *A = pinv + pioff[p];
+  const int ld = pld[p];
+  for (int row0 = VEC * threadIdx.x; row0 < C; row0 += VEC * blockDim.x) {
+    T acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+    const V *col0 = reinterpret_cast<const V *>(A + row0);
+    const long stride = ld / VEC;
+    int j = 0;
+    for (; j + 4 <= C; j += 4) {
+      const V a0 = __ldcs(col0 + (long)(j + 0) * stride);
+      const V a1 = __ldcs(col0 + (long)(j + 1) * stride);
+      const V a2 = __ldcs(col0 + (long)(j + 2) * stride);
+      const V a3 = __ldcs(col0 + (long)(j + 3) * stride);
+      fma_vec<T>(acc, a0, rs[j + 0]);
+      fma_vec<T>(acc, a1, rs[j + 1]);
+      fma_vec<T>(acc, a2, rs[j + 2]);
+      fma_vec<T>(acc, a3, rs[j + 3]);
+    }
+    for (; j < C; ++j) fma_vec<T>(acc, __ldcs(col0 + (long)j * stride), rs[j]);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      if (row0 + v < C) y[doff + row0 + v] = acc[v];
+  }
+}
+
+// d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
+// scale = omega / (number of patches holding the dof): Algorithm 4.1's
+// d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).
+template <typename T>
+__global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *__restrict__ ipos,
+                               const T *__restrict__ scale, const T *__restrict__ y, T *__restrict__ d, int zero) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T acc = T(0);
+  for (int e = iptr[i]; e < iptr[i + 1]; ++e) acc += y[ipos[e]];
+  d[i] = (zero ? T(0) : d[i]) + scale[i] * acc;
+}
+
+// ---------------------------------------------------------------- transfers
+// out[a, block, node] = sum_k M[node, k] in[a, block, k] for the scalar
+// operator of the block's space (Q_r for the V/U blocks, Q_{r-1} for P).
+// add != 0 accumulates into out.
+template <typename T>
+__global__ void k_transfer(long n_out, long ns_out, long R_out, long ns_in, long R_in, int d, const int *__restrict__ up,
+                           const int *__restrict__ uc, const T *__restrict__ uv, const int *__restrict__ pp,
+                           const int *__restrict__ pc, const T *__restrict__ pv, const T *__restrict__ in,
+                           T *__restrict__ out, int add) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const long a = i / ns_out, m = i % ns_out;
+  const T *src = in + a * ns_in;
+  T acc = T(0);
+  if (m < 2 * R_out) {
+    const long blk = m / R_out, rem = m % R_out;
+    const long node = rem / d;
+    const int comp = (int)(rem % d);
+    const T *s = src + blk * R_in + comp;
+    for (int e = up[node]; e < up[node + 1]; ++e) acc += uv[e] * s[(long)uc[e] * d];
+  } else {
+    const long node = m - 2 * R_out;
+    const T *s = src + 2 * R_in;
+    for (int e = pp[node]; e < pp[node + 1]; ++e) acc += pv[e] * s[pc[e]];
+  }
+  out[i] = add ? out[i] + acc : acc;
+}
+
+// ---------------------------------------------------------------- coarse
+// x = Ainv b with a dense FP64 inverse (one warp per row).
+template <typename T>
+__global__ void k_coarse(long n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x) {
+  const long row = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  const double *a = Ainv + row * n;
+  for (long j = lane; j < n; j += 32) acc += a[j] * (double)b[j];
+  acc = warp_sum(acc);
+  if (lane == 0) x[row] = (T)acc;
+}
+
+template <typename A, typename B>
+__global__ void k_convert(long n, const A *__restrict__ a, B *__restrict__ b) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// ---------------------------------------------------------------- BLAS-1 (FP64)
+constexpr int DOT_BLOCKS = 608; // 4 x 152 SMs
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_NV = 8;
+
+// partial[v][block] = sum over the block's share of V_v . w  (v < k)
+__global__ void __launch_bounds__(DOT_THREADS) k_multidot(int k, const double *__restrict__ V, long ldV,
+                                                          const double *__restrict__ w, long n,
+                                                          double *__restrict__ partial) {
+  const int v0 = blockIdx.y * DOT_NV;
+  double acc[DOT_NV];
+#pragma unroll
+  for (int t = 0; t < DOT_NV; ++t) acc[t] = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int t = 0; t < DOT_NV; ++t)
+      if (v0 + t < k) acc[t] += V[(long)(v0 + t) * ldV + i] * wi;
+  }
+  __shared__ double sm[DOT_NV][DOT_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < DOT_NV; ++t) {
+    const double s = warp_sum(acc[t]);
+    if (lane == 0) sm[t][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int t = 0; t < DOT_NV; ++t) {
+      double s = lane < DOT_THREADS / 32 ? sm[t][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0 && v0 + t < k) partial[(long)(v0 + t) * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// out[v] = sum_b partial[v][b] in a fixed order (one block per v).
+__global__ void k_reduce_partials(int nb, const double *__restrict__ partial, double *__restrict__ out) {
+  __shared__ double sm[32];
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(long)v * nb + b];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) out[v] = t;
+  }
+}
+
+// w -= sum_v h[v] V_v
+__global__ void k_multiaxpy(int k, const double *__restrict__ V, long ldV, const double *__restrict__ h,
+                            double *__restrict__ w, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int v = 0; v < k; ++v) acc += h[v] * V[(long)v * ldV + i];
+  w[i] -= acc;
+}
+
+// dst = src / *div  (or src / div_host when div == nullptr)
+__global__ void k_div(long n, const double *__restrict__ src, double *__restrict__ dst, const double *div,
+                      double div_host) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = div ? *div : div_host;
+  dst[i] = src[i] / s;
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
+// previous Givens rotations applied, a new rotation for (H_jj, H_{j+1,j})
+// and the update of g.  status = {|g_{j+1}|, h_{j+1,j}}.
+__global__ void k_givens(int j, int m1, const double *__restrict__ h1, const double *__restrict__ h2,
+                         const double *__restrict__ hn2, double *__restrict__ H, double *__restrict__ cs,
+                         double *__restrict__ sn, double *__restrict__ g, double *__restrict__ hnorm,
+                         double *__restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double col[MAXM + 1];
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(*hn2);
+  col[j + 1] = hn;
+  *hnorm = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double rho = hypot(a, b);
+  cs[j] = a / rho;
+  sn[j] = b / rho;
+  col[j] = rho;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  for (int i = 0; i <= j + 1; ++i) H[(long)j * m1 + i] = col[i];
+  status[0] = fabs(g[j + 1]);
+  status[1] = hn;
+}
+
+// Back substitution H(0:k,0:k) y = g(0:k).
+__global__ void k_backsolve(int k, int m1, const double *__restrict__ H, const double *__restrict__ g,
+                            double *__restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int l = i + 1; l < k; ++l) s += H[(long)l * m1 + i] * y[l];
+    y[i] = (g[i] - s) / H[(long)i * m1 + i];
+  }
+}
+
+template <typename TZ>
+__global__ void k_update_x(long n, int k, const TZ *__restrict__ Z, long ldZ, const double *__restrict__ y,
+                           double *__restrict__ x) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < k; ++j) acc += (double)Z[(long)j * ldZ + i] * y[j];
+  x[i] += acc;
+}
+
+__global__ void k_set(double *p, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+__global__ void k_repeat(long ns, int q, const double *__restrict__ state, double *__restrict__ x) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns * q) return;
+  x[i] = state[i % ns];
+}
+
+// ---------------------------------------------------------------- problem data
+__device__ void node_coord(const GeomDev &g, int deg, const int *dims, const double *ref, long idx, double *x) {
+  for (int i = 0; i < 3; ++i) {
+    if (i < g.dim) {
+      const int a = (int)(idx % dims[i]);
+      idx /= dims[i];
+      const int c = min(a / deg, g.n[i] - 1);
+      x[i] = g.lo[i] + g.h[i] * (c + ref[a - deg * c]);
+    } else {
+      x[i] = 0.0;
+    }
+  }
+}
+
+// Built-in manufactured solutions (homogeneous on the boundary of the unit box)
+// and their sources rho f = rho u_tt - div sigma(u) + alpha grad p,
+// g = c0 p_t + alpha div u_t - kappa lap p (Eq. 1.1), derived by hand.
+__device__ void dev_fields(const ProbDev &P, const double *x, double t, double *u, double *v, double *p) {
+  const int d = P.dim;
+  for (int i = 0; i < 3; ++i) u[i] = v[i] = 0.0;
+  *p = 0.0;
+  if (P.id == STFEM_PROBLEM_SIN) {
+    double phi = 1.0;
+    for (int i = 0; i < d; ++i) phi *= sin(M_PI * x[i]);
+    for (int i = 0; i < d; ++i) {
+      u[i] = phi * sin(t);
+      v[i] = phi * cos(t);
+    }
+    *p = phi * cos(t);
+  } else if (P.id == STFEM_PROBLEM_PAPER_EOC) {
+    const double w1 = M_PI, w2 = M_PI;
+    const double T0 = sin(w1 * t * t), T1 = 2.0 * w1 * t * cos(w1 * t * t);
+    const double psi = sin(w2 * x[0]) * sin(w2 * x[1]);
+    u[0] = u[1] = T0 * psi;
+    v[0] = v[1] = T1 * psi;
+    *p = T0 * psi;
+  } else if (P.id == STFEM_PROBLEM_PAPER_SUPERCONV) {
+    const double w1 = 40.0 * M_PI, w2 = 10.0 * M_PI;
+    const double X = x[0], Y = x[1];
+    const double Ax = X * X * (X - 1) * (X - 1), Ay = Y * Y * (Y - 1) * (Y - 1);
+    const double Bx = (X - 1) * X * (2 * X - 1), By = (Y - 1) * Y * (2 * Y - 1);
+    u[0] = -2.0 * Ax * By * sin(w1 * t);
+    u[1] = 2.0 * Bx * Ay * sin(w1 * t);
+    v[0] = -2.0 * Ax * By * w1 * cos(w1 * t);
+    v[1] = 2.0 * Bx * Ay * w1 * cos(w1 * t);
+    *p = -2.0 * Ax * By * sin(w2 * t);
+  }
+}
+
+__device__ void dev_source(const ProbDev &P, const double *x, double t, double lam, double mu, double kap, double *rf,
+                           double *g) {
+  const int d = P.dim;
+  for (int i = 0; i < 3; ++i) rf[i] = 0.0;
+  *g = 0.0;
+  if (P.id == STFEM_PROBLEM_SIN) {
+    double s[3], c[3];
+    for (int i = 0; i < d; ++i) {
+      s[i] = sin(M_PI * x[i]);
+      c[i] = cos(M_PI * x[i]);
+    }
+    double phi = 1.0;
+    for (int i = 0; i < d; ++i) phi *= s[i];
+    const double pi2 = M_PI * M_PI;
+    double dphi[3];
+    for (int i = 0; i < d; ++i) {
+      double pr = M_PI * c[i];
+      for (int k = 0; k < d; ++k)
+        if (k != i) pr *= s[k];
+      dphi[i] = pr;
+    }
+    for (int i = 0; i < d; ++i) {
+      double hsum = 0.0; // sum_j d_i d_j phi
+      for (int j = 0; j < d; ++j) {
+        if (j == i) {
+          hsum += -pi2 * phi;
+        } else {
+          double pr = pi2 * c[i] * c[j];
+          for (int k = 0; k < d; ++k)
+            if (k != i && k != j) pr *= s[k];
+          hsum += pr;
+        }
+      }
+      rf[i] = -P.rho * phi * sin(t) + d * pi2 * mu * phi * sin(t) - (mu + lam) * sin(t) * hsum +
+              P.alpha * cos(t) * dphi[i];
+    }
+    double div = 0.0;
+    for (int j = 0; j < d; ++j) div += dphi[j];
+    *g = -P.c0 * phi * sin(t) + P.alpha * cos(t) * div + kap * d * pi2 * phi * cos(t);
+  } else if (P.id == STFEM_PROBLEM_PAPER_EOC) {
+    const double w1 = M_PI, w2 = M_PI;
+    const double T0 = sin(w1 * t * t), T1 = 2.0 * w1 * t * cos(w1 * t * t),
+                 T2 = 2.0 * w1 * cos(w1 * t * t) - 4.0 * w1 * w1 * t * t * sin(w1 * t * t);
+    const double sx = sin(w2 * x[0]), sy = sin(w2 * x[1]), cx = cos(w2 * x[0]), cy = cos(w2 * x[1]);
+    const double psi = sx * sy, cc = cx * cy, w22 = w2 * w2;
+    const double base = P.rho * T2 * psi + 2.0 * mu * w22 * T0 * psi + (mu + lam) * w22 * T0 * (psi - cc);
+    rf[0] = base + P.alpha * T0 * w2 * cx * sy;
+    rf[1] = base + P.alpha * T0 * w2 * sx * cy;
+    *g = P.c0 * T1 * psi + P.alpha * T1 * w2 * (cx * sy + sx * cy) + 2.0 * kap * w22 * T0 * psi;
+  } else if (P.id == STFEM_PROBLEM_PAPER_SUPERCONV) {
+    const double w1 = 40.0 * M_PI, w2 = 10.0 * M_PI;
+    const double X = x[0], Y = x[1];
+    const double Ax = X * X * (X - 1) * (X - 1), Ay = Y * Y * (Y - 1) * (Y - 1);
+    const double Bx = (X - 1) * X * (2 * X - 1), By = (Y - 1) * Y * (2 * Y - 1);
+    const double A2x = 12 * X * X - 12 * X + 2, A2y = 12 * Y * Y - 12 * Y + 2;
+    const double B1y = 6 * Y * Y - 6 * Y + 1, B2x = 12 * X - 6, B2y = 12 * Y - 6;
+    const double A1x = 2.0 * Bx; // A' = 2B
+    const double s1 = sin(w1 * t), s2 = sin(w2 * t), c2 = cos(w2 * t);
+    rf[0] = 2.0 * P.rho * w1 * w1 * Ax * By * s1 + 2.0 * mu * (A2x * By + Ax * B2y) * s1 - 2.0 * P.alpha * A1x * By * s2;
+    rf[1] = -2.0 * P.rho * w1 * w1 * Bx * Ay * s1 - 2.0 * mu * (B2x * Ay + Bx * A2y) * s1 - 2.0 * P.alpha * Ax * B1y * s2;
+    *g = -2.0 * P.c0 * w2 * Ax * By * c2 + 2.0 * kap * (A2x * By + Ax * B2y) * s2;
+  }
+}
+
+// z-component of the traction t_N on the top face for the pulse problem
+__device__ double dev_top_traction(const ProbDev &P, const double *x, double t) {
+  if (P.id != STFEM_PROBLEM_PULSE) return 0.0;
+  if (x[0] >= 0.75 && x[0] <= 1.25 && x[1] >= 0.75 && x[1] <= 1.25) return -sin(M_PI * t / 0.05);
+  return 0.0;
+}
+
+// state = nodal interpolation of (v, u, p) at time t
+__global__ void k_interp(GeomDev g, ProbDev P, double t, long R, long S, double *__restrict__ state) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * R + S) return;
+  double x[3], u[3], v[3], p;
+  if (i < 2 * R) {
+    const long rem = i % R;
+    node_coord(g, g.r, g.udims, g.refU, rem / g.dim, x);
+    dev_fields(P, x, t, u, v, &p);
+    state[i] = (i < R) ? v[rem % g.dim] : u[rem % g.dim];
+  } else {
+    node_coord(g, g.r - 1, g.pdims, g.refP, i - 2 * R, x);
+    dev_fields(P, x, t, u, v, &p);
+    state[i] = p;
+  }
+}
+
+// Slab right-hand side (Eq. 3.5 / Eq. 4.5):
+// rhs[b, m] = chi_b(-1) (S1 state)[m] + W_b * load_m(t_b), load = 0 on u-rows,
+// F = <rho f, psi> - <t_N, psi>_{Gamma_N} on v-rows, G = <g, xi> on p-rows.
+// Node-centric gather over the cells holding the node (deterministic).
+__global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double> tc, const double *chi,
+                      const double *tnode, double t_prev, double tau, long R, long S,
+                      const double *__restrict__ ys, double *__restrict__ out) {
+  const long ns = 2 * R + S;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)q * ns) return;
+  const int b = (int)(i / ns);
+  const long m = i % ns;
+  double val = chi[b] * ys[m];
+  if (m >= R && P.id != STFEM_PROBLEM_NONE) {
+    const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
+    const int d = g.dim;
+    const bool urow = m < 2 * R;
+    const int deg = urow ? g.r : g.r - 1;
+    const int *dims = urow ? g.udims : g.pdims;
+    const long node = urow ? (m - R) / d : m - 2 * R;
+    const int comp = urow ? (int)((m - R) % d) : 0;
+    int a[3] = {0, 0, 0}, clo[3] = {0, 0, 0}, chi_[3] = {0, 0, 0};
+    long t = node;
+    for (int k = 0; k < d; ++k) {
+      a[k] = (int)(t % dims[k]);
+      t /= dims[k];
+      if (a[k] % deg == 0) {
+        clo[k] = max(a[k] / deg - 1, 0);
+        chi_[k] = min(a[k] / deg, g.n[k] - 1);
+      } else {
+        clo[k] = chi_[k] = a[k] / deg;
+      }
+    }
+    const int nl = urow ? L.nlu : L.nlp;
+    const double *phi = urow ? L.phiU : L.phiP;
+    double load = 0.0;
+    for (int cz = clo[2]; cz <= chi_[2]; ++cz)
+      for (int cy = clo[1]; cy <= chi_[1]; ++cy)
+        for (int cx = clo[0]; cx <= chi_[0]; ++cx) {
+          const int cc[3] = {cx, cy, cz};
+          int li = 0, stride = 1;
+          for (int k = 0; k < d; ++k) {
+            li += (a[k] - deg * cc[k]) * stride;
+            stride *= deg + 1;
+          }
+          const long cell = cx + (long)g.n[0] * (cy + (long)g.n[1] * cz);
+          const double lam = L.lam[cell], mu = L.mu[cell], kap = L.kap[cell];
+          for (int qq = 0; qq < L.nq; ++qq) {
+            double x[3];
+            for (int k = 0; k < 3; ++k) x[k] = g.lo[k] + g.h[k] * (cc[k] + L.qx[qq * 3 + k]);
+            double rf[3], gg;
+            dev_source(P, x, tb, lam, mu, kap, rf, &gg);
+            load += L.qw[qq] * (urow ? rf[comp] : gg) * phi[qq * nl + li];
+          }
+          // Neumann traction on the top face (pulse problem)
+          if (urow && L.top_neumann && comp == d - 1 && cc[d - 1] == g.n[d - 1] - 1 &&
+              a[d - 1] == deg * g.n[d - 1]) {
+            for (int qq = 0; qq < L.nqf; ++qq) {
+              double x[3];
+              for (int k = 0; k < 3; ++k) x[k] = g.lo[k] + g.h[k] * (cc[k] + L.fx[qq * 3 + k]);
+              load += -L.fw[qq] * dev_top_traction(P, x, tb) * L.fphiU[qq * L.nlu + li];
+            }
+          }
+        }
+    val += tc.W[b] * load;
+  }
+  out[i] = val;
+}
+
+// ============================================================ host side
+inline int grid_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+template <typename T>
+struct DLevel {
+  long ns = 0, N = 0, R = 0, S = 0;
+  long long nnz = 0;
+  int *rowptr = nullptr, *col = nullptr;
+  T *v1 = nullptr, *v2 = nullptr;
+  // patches
+  long npatch = 0;
+  int maxC = 0;
+  int *psize = nullptr, *pld = nullptr, *pdofs = nullptr;
+  long long *pdoff = nullptr, *pioff = nullptr;
+  T *pinv = nullptr;
+  long long inv_elems = 0, sumC = 0;
+  int *iptr = nullptr, *ipos = nullptr;
+  T *scale = nullptr, *ybuf = nullptr;
+  // work vectors
+  T *b = nullptr, *d = nullptr, *r = nullptr;
+  // transfer from level l-1 (valid for l >= 1): P rows fine, R rows coarse
+  int *Pu_p = nullptr, *Pu_c = nullptr, *Pp_p = nullptr, *Pp_c = nullptr;
+  int *Ru_p = nullptr, *Ru_c = nullptr, *Rp_p = nullptr, *Rp_c = nullptr;
+  T *Pu_v = nullptr, *Pp_v = nullptr, *Ru_v = nullptr, *Rp_v = nullptr;
+};
+
+} // namespace
+
+struct stfem_ctx {
+  std::string err;
+  cudaStream_t stream = 0;
+  int dim = 2, r = 2, k = 1, q = 2, nlev = 1;
+  double tau = 0.01, t0 = 0.0;
+  int problem = 0;
+  stfem::Temporal T;
+  std::vector<stfem::Level> hl;
+  std::vector<stfem::CSR> Pu, Pp; // index l: from l-1 to l
+  ProbDev prob{};
+  GeomDev geom{}; // finest level
+  // FP64 operators of every level (built by stfem_setup)
+  std::vector<DLevel<double>> L64;
+  // FP32 V-cycle levels (built by gmg_setup in STFEM_MIXED)
+  std::vector<DLevel<float>> L32;
+  int precision = -1;
+  double omega = 0.7;
+  int nsweeps = 1;
+  double *coarse_inv = nullptr;
+  // FGMRES workspace
+  int mcap = 0;
+  double *V = nullptr, *Zd = nullptr, *w = nullptr, *rvec = nullptr, *zt = nullptr;
+  float *Zf = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *hn2 = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
+         *y = nullptr, *hnorm = nullptr, *partial = nullptr, *status = nullptr;
+  double *status_host = nullptr;
+  // march buffers and load tables
+  double *rhs = nullptr, *xs = nullptr, *ys = nullptr, *chi = nullptr, *tnode = nullptr;
+  LoadTables lt{};
+  std::vector<double> hist;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+std::string g_setup_err;
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                                   \
+      return e_ == cudaErrorMemoryAllocation ? STFEM_ERR_OOM : STFEM_ERR_CUDA;                       \
+    }                                                                                                \
+  } while (0)
+
+#define CKR(expr)                                                                                    \
+  do {                                                                                               \
+    int rc_ = (expr);                                                                                \
+    if (rc_ < 0) return rc_;                                                                         \
+  } while (0)
+
+template <typename T>
+int dalloc(stfem_h h, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  CK(cudaMalloc((void **)p, n * sizeof(T)));
+  h->allocs.push_back((void *)*p);
+  return 0;
+}
+
+template <typename T, typename S>
+int upload(stfem_h h, T **p, const std::vector<S> &src) {
+  CKR(dalloc(h, p, src.size()));
+  if (src.empty()) return 0;
+  std::vector<T> tmp(src.begin(), src.end());
+  CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+template <typename T>
+TimeCoef<T> time_coef(const stfem::Temporal &Tm, double tau) {
+  TimeCoef<T> tc{};
+  tc.q = Tm.q;
+  for (int i = 0; i < Tm.q * Tm.q; ++i) tc.Dt[i] = (T)Tm.Dt[i];
+  for (int b = 0; b < Tm.q; ++b) tc.W[b] = (T)(0.5 * tau * Tm.w[b]);
+  return tc;
+}
+
+template <typename T, int Q>
+void launch_spmv_q(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+                   int mode) {
+  constexpr int G = 8;
+  const long threads = L.ns * G;
+  k_spmv<T, Q, G><<<grid_for(threads, 256), 256, 0, s>>>(L.ns, L.rowptr, L.col, L.v1, L.v2, tc, x, rhs, y, mode);
+}
+
+template <typename T>
+void launch_spmv(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+                 int mode) {
+  switch (tc.q) {
+  case 1: launch_spmv_q<T, 1>(s, L, tc, x, rhs, y, mode); break;
+  case 2: launch_spmv_q<T, 2>(s, L, tc, x, rhs, y, mode); break;
+  case 3: launch_spmv_q<T, 3>(s, L, tc, x, rhs, y, mode); break;
+  case 4: launch_spmv_q<T, 4>(s, L, tc, x, rhs, y, mode); break;
+  default: launch_spmv_q<T, 5>(s, L, tc, x, rhs, y, mode); break;
+  }
+}
+
+template <typename T>
+int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
+  D.ns = L.ns;
+  D.N = L.ns * q;
+  D.R = L.R;
+  D.S = L.S;
+  D.nnz = (long long)L.col.size();
+  CKR(upload(h, &D.rowptr, L.rowptr));
+  CKR(upload(h, &D.col, L.col));
+  CKR(upload(h, &D.v1, L.v1));
+  CKR(upload(h, &D.v2, L.v2));
+  CKR(dalloc(h, &D.b, D.N));
+  CKR(dalloc(h, &D.d, D.N));
+  CKR(dalloc(h, &D.r, D.N));
+  return 0;
+}
+
+template <typename T>
+int upload_transfer(stfem_h h, DLevel<T> &D, const stfem::CSR &Pu, const stfem::CSR &Pp) {
+  stfem::CSR Ru = stfem::transpose(Pu), Rp = stfem::transpose(Pp);
+  CKR(upload(h, &D.Pu_p, Pu.rowptr));
+  CKR(upload(h, &D.Pu_c, Pu.col));
+  CKR(upload(h, &D.Pu_v, Pu.val));
+  CKR(upload(h, &D.Pp_p, Pp.rowptr));
+  CKR(upload(h, &D.Pp_c, Pp.col));
+  CKR(upload(h, &D.Pp_v, Pp.val));
+  CKR(upload(h, &D.Ru_p, Ru.rowptr));
+  CKR(upload(h, &D.Ru_c, Ru.col));
+  CKR(upload(h, &D.Ru_v, Ru.val));
+  CKR(upload(h, &D.Rp_p, Rp.rowptr));
+  CKR(upload(h, &D.Rp_c, Rp.col));
+  CKR(upload(h, &D.Rp_v, Rp.val));
+  return 0;
+}
+
+template <typename T>
+int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omega) {
+  D.npatch = P.npatch;
+  D.maxC = *std::max_element(P.size.begin(), P.size.end());
+  D.inv_elems = (long long)P.inv.size();
+  D.sumC = (long long)P.dofs.size();
+  CKR(upload(h, &D.psize, P.size));
+  CKR(upload(h, &D.pld, P.ld));
+  CKR(upload(h, &D.pdofs, P.dofs));
+  CKR(upload(h, &D.pdoff, P.dof_off));
+  CKR(upload(h, &D.pioff, P.inv_off));
+  CKR(upload(h, &D.pinv, P.inv));
+  CKR(dalloc(h, &D.ybuf, P.dofs.size()));
+  // inverse map dof -> positions in ybuf, in patch order
+  std::vector<int> cnt(D.N + 1, 0);
+  for (int dof : P.dofs) cnt[dof + 1]++;
+  for (long i = 0; i < D.N; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> pos(P.dofs.size());
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (size_t e = 0; e < P.dofs.size(); ++e) pos[fill[P.dofs[e]]++] = (int)e;
+  std::vector<double> scale(D.N);
+  for (long i = 0; i < D.N; ++i) {
+    int c = cnt[i + 1] - cnt[i];
+    if (c == 0) {
+      h->err = "a degree of freedom belongs to no patch";
+      return STFEM_ERR_STATE;
+    }
+    scale[i] = omega / c;
+  }
+  CKR(upload(h, &D.iptr, cnt));
+  CKR(upload(h, &D.ipos, pos));
+  CKR(upload(h, &D.scale, scale));
+  return 0;
+}
+
+// ---------------------------------------------------------------- V-cycle
+template <typename T>
+std::vector<DLevel<T>> &levels(stfem_h h);
+template <>
+std::vector<DLevel<double>> &levels<double>(stfem_h h) {
+  return h->L64;
+}
+template <>
+std::vector<DLevel<float>> &levels<float>(stfem_h h) {
+  return h->L32;
+}
+
+template <typename T>
+void smooth(stfem_h h, int l, int nsw, bool zero_init) {
+  DLevel<T> &L = levels<T>(h)[l];
+  const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
+  cudaStream_t s = h->stream;
+  for (int it = 0; it < nsw; ++it) {
+    const bool zero = zero_init && it == 0;
+    const T *res = L.b;
+    if (!zero) {
+      launch_spmv<T>(s, L, tc, L.d, L.b, L.r, 1);
+      res = L.r;
+    }
+    constexpr int VEC = Vec16<T>::n;
+    int threads = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
+    threads = std::min(std::max(threads, 32), 512);
+    k_patch_apply<T><<<(unsigned)L.npatch, threads, L.maxC * sizeof(T), s>>>(L.psize, L.pdoff, L.pdofs, L.pioff,
+                                                                              L.pld, L.pinv, res, L.ybuf);
+    k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d, zero ? 1 : 0);
+  }
+}
+
+template <typename T>
+void restrict_to(stfem_h h, int l, const T *rf, T *bc) {
+  DLevel<T> &F = levels<T>(h)[l];
+  DLevel<T> &C = levels<T>(h)[l - 1];
+  k_transfer<T><<<grid_for(C.N, 256), 256, 0, h->stream>>>(C.N, C.ns, C.R, F.ns, F.R, h->dim, F.Ru_p, F.Ru_c, F.Ru_v,
+                                                            F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
+}
+
+template <typename T>
+void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
+  DLevel<T> &F = levels<T>(h)[l];
+  DLevel<T> &C = levels<T>(h)[l - 1];
+  k_transfer<T><<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.N, F.ns, F.R, C.ns, C.R, h->dim, F.Pu_p, F.Pu_c, F.Pu_v,
+                                                            F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
+}
+
+template <typename T>
+void coarse(stfem_h h, const T *b, T *x) {
+  const long n = levels<T>(h)[0].N;
+  k_coarse<T><<<grid_for(n * 32, 256), 256, 0, h->stream>>>(n, h->coarse_inv, b, x);
+}
+
+// V-cycle on level l for A_l d_l = b_l (both in the level's buffers), d from 0.
+template <typename T>
+void vcycle(stfem_h h, int l) {
+  std::vector<DLevel<T>> &Ls = levels<T>(h);
+  if (l == 0) {
+    coarse<T>(h, Ls[0].b, Ls[0].d);
+    return;
+  }
+  DLevel<T> &L = Ls[l];
+  const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
+  smooth<T>(h, l, h->nsweeps, true);
+  launch_spmv<T>(h->stream, L, tc, L.d, L.b, L.r, 1);
+  restrict_to<T>(h, l, L.r, Ls[l - 1].b);
+  vcycle<T>(h, l - 1);
+  prolongate_add<T>(h, l, Ls[l - 1].d, L.d);
+  smooth<T>(h, l, h->nsweeps, false);
+}
+
+// z = M^{-1} v with one V-cycle in the GMG precision; v, z FP64 (z may be FP32 storage)
+int precondition(stfem_h h, const double *v, double *zd, float *zf) {
+  const int L = h->nlev - 1;
+  cudaStream_t s = h->stream;
+  if (h->precision == STFEM_FP64) {
+    DLevel<double> &F = h->L64[L];
+    CK(cudaMemcpyAsync(F.b, v, F.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    vcycle<double>(h, L);
+    CK(cudaMemcpyAsync(zd, F.d, F.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    DLevel<float> &F = h->L32[L];
+    k_convert<double, float><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, v, F.b);
+    vcycle<float>(h, L);
+    if (zf) CK(cudaMemcpyAsync(zf, F.d, F.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (zd) k_convert<float, double><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, F.d, zd);
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+// dots out[0..k) = V_v . w on device (deterministic two-stage reduction)
+void multidot(stfem_h h, int k, const double *V, long ldV, const double *w, long n, double *out) {
+  dim3 grid(DOT_BLOCKS, (k + DOT_NV - 1) / DOT_NV);
+  k_multidot<<<grid, DOT_THREADS, 0, h->stream>>>(k, V, ldV, w, n, h->partial);
+  k_reduce_partials<<<k, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+}
+
+int read_scalar(stfem_h h, const double *dev, double *host) {
+  CK(cudaMemcpyAsync(h->status_host, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *host = h->status_host[0];
+  return 0;
+}
+
+int ensure_workspace(stfem_h h, int m) {
+  if (m <= h->mcap) return 0;
+  if (m > MAXM) {
+    h->err = "restart length above the supported maximum";
+    return STFEM_ERR_ARG;
+  }
+  const long N = h->L64.back().N;
+  CKR(dalloc(h, &h->V, (size_t)(m + 1) * N));
+  if (h->precision == STFEM_MIXED) {
+    CKR(dalloc(h, &h->Zf, (size_t)m * N));
+  } else {
+    CKR(dalloc(h, &h->Zd, (size_t)m * N));
+  }
+  CKR(dalloc(h, &h->H, (size_t)(m + 1) * m));
+  CKR(dalloc(h, &h->cs, m));
+  CKR(dalloc(h, &h->sn, m));
+  CKR(dalloc(h, &h->g, m + 1));
+  CKR(dalloc(h, &h->y, m));
+  CKR(dalloc(h, &h->h1, m + 1));
+  CKR(dalloc(h, &h->h2, m + 1));
+  h->mcap = m;
+  return 0;
+}
+
+int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it, int *iters, double *relres) {
+  CKR(ensure_workspace(h, m));
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  cudaStream_t s = h->stream;
+  const int nb = grid_for(N, 256);
+  h->hist.clear();
+  *iters = 0;
+  *relres = 0.0;
+  launch_spmv<double>(s, F, tc, x, b, h->rvec, 1);
+  multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
+  double beta0sq;
+  CKR(read_scalar(h, h->hn2, &beta0sq));
+  const double beta0 = std::sqrt(beta0sq);
+  h->hist.push_back(1.0);
+  if (!std::isfinite(beta0)) {
+    h->err = "initial residual is not finite";
+    return STFEM_ERR_BREAKDOWN;
+  }
+  if (beta0 == 0.0) return STFEM_OK;
+  double beta = beta0;
+  int it = 0;
+  const int m1 = m + 1;
+  for (;;) {
+    k_div<<<nb, 256, 0, s>>>(N, h->rvec, h->V, nullptr, beta);
+    k_set<<<1, 1, 0, s>>>(h->g, beta);
+    int jlast = -1;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double *vj = h->V + (long)j * N;
+      double *zj = nullptr;
+      if (h->precision == STFEM_FP64) {
+        zj = h->Zd + (long)j * N;
+        CKR(precondition(h, vj, zj, nullptr));
+      } else {
+        CKR(precondition(h, vj, h->zt, h->Zf + (long)j * N));
+        zj = h->zt;
+      }
+      double *w = h->w;
+      launch_spmv<double>(s, F, tc, zj, nullptr, w, 0);
+      // classical Gram-Schmidt, applied twice
+      multidot(h, j + 1, h->V, N, w, N, h->h1);
+      k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
+      multidot(h, j + 1, h->V, N, w, N, h->h2);
+      k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
+      multidot(h, 1, w, N, w, N, h->hn2);
+      k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);
+      CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CK(cudaGetLastError());
+      const double res = h->status_host[0], hn = h->status_host[1];
+      if (!std::isfinite(res) || !std::isfinite(hn)) {
+        h->err = "FGMRES breakdown: non-finite Hessenberg entry";
+        *iters = it;
+        return STFEM_ERR_BREAKDOWN;
+      }
+      if (hn > 0.0) k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
+      ++it;
+      jlast = j;
+      h->hist.push_back(res / beta0);
+      if (res <= tol * beta0 || it >= max_it || hn == 0.0) {
+        stop = true;
+        break;
+      }
+    }
+    const int kk = jlast + 1;
+    k_backsolve<<<1, 1, 0, s>>>(kk, m1, h->H, h->g, h->y);
+    if (h->precision == STFEM_FP64)
+      k_update_x<double><<<nb, 256, 0, s>>>(N, kk, h->Zd, N, h->y, x);
+    else
+      k_update_x<float><<<nb, 256, 0, s>>>(N, kk, h->Zf, N, h->y, x);
+    launch_spmv<double>(s, F, tc, x, b, h->rvec, 1);
+    multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
+    double rr;
+    CKR(read_scalar(h, h->hn2, &rr));
+    const double res = std::sqrt(rr);
+    *iters = it;
+    *relres = res / beta0;
+    if (!std::isfinite(res)) {
+      h->err = "FGMRES breakdown: non-finite residual";
+      return STFEM_ERR_BREAKDOWN;
+    }
+    if (res <= tol * beta0) return STFEM_OK;
+    if (it >= max_it) return STFEM_NOT_CONVERGED;
+    (void)stop;
+    beta = res;
+  }
+}
+
+int check_level(stfem_h h, int level, bool allow_fine_alias) {
+  if (level == -1 && allow_fine_alias) return 0;
+  if (level < 0 || level >= h->nlev) {
+    h->err = "level out of range";
+    return STFEM_ERR_ARG;
+  }
+  return 0;
+}
+
+int require_gmg(stfem_h h) {
+  if (h->precision < 0) {
+    h->err = "stfem_gmg_setup has not been called";
+    return STFEM_ERR_STATE;
+  }
+  return 0;
+}
+
+// copy an FP64 ABI vector into a level buffer of type T (and back)
+template <typename T>
+void to_level(stfem_h h, const double *src, T *dst, long n) {
+  k_convert<double, T><<<grid_for(n, 256), 256, 0, h->stream>>>(n, src, dst);
+}
+template <typename T>
+void from_level(stfem_h h, const T *src, double *dst, long n) {
+  k_convert<T, double><<<grid_for(n, 256), 256, 0, h->stream>>>(n, src, dst);
+}
+
+template <typename T>
+int apply_t(stfem_h h, int level, const double *x, double *y) {
+  DLevel<T> &L = levels<T>(h)[level];
+  const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
+  to_level<T>(h, x, L.d, L.N);
+  launch_spmv<T>(h->stream, L, tc, L.d, nullptr, L.r, 0);
+  from_level<T>(h, L.r, y, L.N);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+template <typename T>
+int smooth_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init) {
+  DLevel<T> &L = levels<T>(h)[level];
+  to_level<T>(h, b, L.b, L.N);
+  if (!zero_init) to_level<T>(h, d, L.d, L.N);
+  smooth<T>(h, level, nsw, zero_init != 0);
+  from_level<T>(h, L.d, d, L.N);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+template <typename T>
+int transfer_t(stfem_h h, int level, const double *in, double *out, bool restrict_dir) {
+  std::vector<DLevel<T>> &Ls = levels<T>(h);
+  DLevel<T> &F = Ls[level], &C = Ls[level - 1];
+  if (restrict_dir) {
+    to_level<T>(h, in, F.r, F.N);
+    restrict_to<T>(h, level, F.r, C.b);
+    from_level<T>(h, C.b, out, C.N);
+  } else {
+    to_level<T>(h, in, C.d, C.N);
+    to_level<T>(h, out, F.d, F.N);
+    prolongate_add<T>(h, level, C.d, F.d);
+    from_level<T>(h, F.d, out, F.N);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int build_load_tables(stfem_h h) {
+  const stfem::Level &L = h->hl.back();
+  const stfem::Box &b = L.box;
+  const int d = b.dim, nq1 = h->r + 2;
+  stfem::Rule g = stfem::gauss01(nq1);
+  std::vector<double> qx, qw, fx, fw;
+  int nz = d > 2 ? nq1 : 1, ny = d > 1 ? nq1 : 1;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nq1; ++x) {
+        qx.push_back(g.x[x]);
+        qx.push_back(d > 1 ? g.x[y] : 0.0);
+        qx.push_back(d > 2 ? g.x[z] : 0.0);
+        qw.push_back(g.w[x] * (d > 1 ? g.w[y] : 1.0) * (d > 2 ? g.w[z] : 1.0) * b.vol);
+      }
+  if (d == 3) {
+    const double area = b.h[0] * b.h[1];
+    for (int y = 0; y < nq1; ++y)
+      for (int x = 0; x < nq1; ++x) {
+        fx.push_back(g.x[x]);
+        fx.push_back(g.x[y]);
+        fx.push_back(1.0);
+        fw.push_back(g.w[x] * g.w[y] * area);
+      }
+  }
+  auto tab = [&](const stfem::Lattice &lat, const std::vector<double> &pts) {
+    const int m1 = lat.m + 1;
+    int nl = 1;
+    for (int i = 0; i < d; ++i) nl *= m1;
+    const int np = (int)pts.size() / 3;
+    std::vector<double> out((size_t)np * nl);
+    std::vector<double> v(m1), dv(m1);
+    for (int qq = 0; qq < np; ++qq) {
+      double vals[3][16];
+      for (int i = 0; i < d; ++i) {
+        stfem::lagrange(lat.ref, pts[qq * 3 + i], v.data(), dv.data());
+        for (int j = 0; j < m1; ++j) vals[i][j] = v[j];
+      }
+      for (int l = 0; l < nl; ++l) {
+        int t = l;
+        double p = 1.0;
+        for (int i = 0; i < d; ++i) {
+          p *= vals[i][t % m1];
+          t /= m1;
+        }
+        out[(size_t)qq * nl + l] = p;
+      }
+    }
+    return out;
+  };
+  std::vector<double> phiU = tab(L.U, qx), phiP = tab(L.P, qx);
+  std::vector<double> fphiU = d == 3 ? tab(L.U, fx) : std::vector<double>(1, 0.0);
+  int nlu = 1, nlp = 1;
+  for (int i = 0; i < d; ++i) {
+    nlu *= h->r + 1;
+    nlp *= h->r;
+  }
+  LoadTables &lt = h->lt;
+  lt.nq = (int)qw.size();
+  lt.nlu = nlu;
+  lt.nlp = nlp;
+  lt.nqf = (int)fw.size();
+  double *p;
+  CKR(upload(h, &p, qx)); lt.qx = p;
+  CKR(upload(h, &p, qw)); lt.qw = p;
+  CKR(upload(h, &p, phiU)); lt.phiU = p;
+  CKR(upload(h, &p, phiP)); lt.phiP = p;
+  CKR(upload(h, &p, fx.empty() ? std::vector<double>(3, 0.0) : fx)); lt.fx = p;
+  CKR(upload(h, &p, fw.empty() ? std::vector<double>(1, 0.0) : fw)); lt.fw = p;
+  CKR(upload(h, &p, fphiU)); lt.fphiU = p;
+  CKR(upload(h, &p, L.coef.lam)); lt.lam = p;
+  CKR(upload(h, &p, L.coef.mu)); lt.mu = p;
+  CKR(upload(h, &p, L.coef.kap)); lt.kap = p;
+  return 0;
+}
+
+int fail_setup(stfem_h h, int rc) {
+  g_setup_err = h->err;
+  stfem_destroy(h);
+  return rc;
+}
+
+} // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat, const stfem_bcs *bcs,
+                double tau, stfem_h *out) {
+  if (!out) {
+    g_setup_err = "null argument";
+    return STFEM_ERR_ARG;
+  }
+  *out = nullptr;
+  stfem_h h = new stfem_ctx();
+  {
+    int rc0 = stfem::build_hierarchy(mesh, deg, mat, bcs, tau, &h->hl, &h->Pu, &h->Pp, &h->err);
+    if (rc0 < 0) return fail_setup(h, rc0);
+  }
+  const int d = mesh->dim;
+  const int pid = bcs->problem;
+  h->dim = d;
+  h->r = deg->r;
+  h->k = deg->k;
+  h->q = deg->k + 1;
+  h->nlev = mesh->n_levels;
+  h->tau = tau;
+  h->t0 = bcs->t0;
+  h->problem = pid;
+  h->T = stfem::make_temporal(deg->k);
+  // upload FP64 operators
+  h->L64.resize(h->nlev);
+  int rc;
+  for (int l = 0; l < h->nlev; ++l) {
+    if ((rc = upload_level_matrix(h, h->L64[l], h->hl[l], h->q)) < 0) return fail_setup(h, rc);
+    if (l >= 1 && (rc = upload_transfer(h, h->L64[l], h->Pu[l], h->Pp[l])) < 0) return fail_setup(h, rc);
+  }
+  // geometry and problem of the finest level
+  const stfem::Level &F = h->hl.back();
+  GeomDev &g = h->geom;
+  g.dim = d;
+  g.r = h->r;
+  for (int i = 0; i < 3; ++i) {
+    g.lo[i] = F.box.lo[i];
+    g.h[i] = F.box.h[i];
+    g.n[i] = F.box.n[i];
+    g.udims[i] = F.U.dims[i];
+    g.pdims[i] = F.P.dims[i];
+  }
+  for (int i = 0; i < 8; ++i) {
+    g.refU[i] = i < (int)F.U.ref.size() ? F.U.ref[i] : 0.0;
+    g.refP[i] = i < (int)F.P.ref.size() ? F.P.ref[i] : 0.0;
+  }
+  h->prob.id = pid;
+  h->prob.dim = d;
+  h->prob.rho = mat->rho;
+  h->prob.alpha = mat->alpha;
+  h->prob.c0 = mat->c0;
+  if ((rc = build_load_tables(h)) < 0) return fail_setup(h, rc);
+  h->lt.top_neumann = (d == 3 && bcs->bc_u[5] == 1) ? 1 : 0;
+  const long N = h->L64.back().N;
+  if ((rc = dalloc(h, &h->w, N)) < 0 || (rc = dalloc(h, &h->rvec, N)) < 0 || (rc = dalloc(h, &h->zt, N)) < 0 ||
+      (rc = dalloc(h, &h->rhs, N)) < 0 || (rc = dalloc(h, &h->xs, N)) < 0 ||
+      (rc = dalloc(h, &h->ys, F.ns)) < 0 || (rc = dalloc(h, &h->hn2, 1)) < 0 ||
+      (rc = dalloc(h, &h->hnorm, 1)) < 0 || (rc = dalloc(h, &h->status, 4)) < 0 ||
+      (rc = dalloc(h, &h->partial, (size_t)DOT_BLOCKS * (MAXM + 1))) < 0 ||
+      (rc = upload(h, &h->chi, h->T.chi_m1)) < 0 || (rc = upload(h, &h->tnode, h->T.t)) < 0)
+    return fail_setup(h, rc);
+  if (cudaHostAlloc((void **)&h->status_host, 4 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+    h->err = "cudaHostAlloc failed";
+    return fail_setup(h, STFEM_ERR_CUDA);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    h->err = "device error during setup";
+    return fail_setup(h, STFEM_ERR_CUDA);
+  }
+  *out = h;
+  return STFEM_OK;
+}
+
+int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
+  if (!h || !p) return STFEM_ERR_ARG;
+  if (!(p->omega > 0.0) || p->n_sweeps < 1 || (p->precision != STFEM_FP64 && p->precision != STFEM_MIXED)) {
+    h->err = "invalid GMG parameters";
+    return STFEM_ERR_ARG;
+  }
+  if (h->precision >= 0) {
+    h->err = "stfem_gmg_setup may only be called once per handle";
+    return STFEM_ERR_STATE;
+  }
+  h->omega = p->omega;
+  h->nsweeps = p->n_sweeps;
+  h->precision = p->precision;
+  const bool mixed = p->precision == STFEM_MIXED;
+  if (mixed) {
+    h->L32.resize(h->nlev);
+    for (int l = 0; l < h->nlev; ++l) {
+      CKR(upload_level_matrix(h, h->L32[l], h->hl[l], h->q));
+      if (l >= 1) CKR(upload_transfer(h, h->L32[l], h->Pu[l], h->Pp[l]));
+    }
+  }
+  for (int l = 1; l < h->nlev; ++l) {
+    stfem::Patches P;
+    std::string err;
+    if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err) < 0) {
+      h->err = err + " on level " + std::to_string(l);
+      return STFEM_ERR_SINGULAR_PATCH;
+    }
+    if (mixed)
+      CKR(upload_patches(h, h->L32[l], P, h->omega));
+    else
+      CKR(upload_patches(h, h->L64[l], P, h->omega));
+  }
+  std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
+  const int n0 = (int)(h->hl[0].ns * h->q);
+  if (!stfem::invert(A0.data(), n0)) {
+    h->err = "singular coarse matrix";
+    return STFEM_ERR_SINGULAR_PATCH;
+  }
+  CKR(upload(h, &h->coarse_inv, A0));
+  CK(cudaDeviceSynchronize());
+  return STFEM_OK;
+}
+
+int stfem_set_stream(stfem_h h, void *stream) {
+  if (!h) return STFEM_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return STFEM_OK;
+}
+
+int stfem_level_info(stfem_h h, int level, long long *n_slab, long long *n_state, long long *n_patches,
+                     long long *inv_bytes) {
+  if (!h) return STFEM_ERR_ARG;
+  if (level == -1) level = h->nlev - 1;
+  CKR(check_level(h, level, false));
+  const stfem::Level &L = h->hl[level];
+  if (n_slab) *n_slab = L.ns * h->q;
+  if (n_state) *n_state = L.ns;
+  long long np = 0, ib = 0;
+  if (h->precision == STFEM_MIXED && level >= 1) {
+    np = h->L32[level].npatch;
+    ib = h->L32[level].inv_elems * 4;
+  } else if (h->precision == STFEM_FP64 && level >= 1) {
+    np = h->L64[level].npatch;
+    ib = h->L64[level].inv_elems * 8;
+  }
+  if (n_patches) *n_patches = np;
+  if (inv_bytes) *inv_bytes = ib;
+  return STFEM_OK;
+}
+
+int stfem_apply(stfem_h h, int level, const double *x, double *y) {
+  if (!h || !x || !y) return STFEM_ERR_ARG;
+  CKR(check_level(h, level, true));
+  if (level == -1 || h->precision != STFEM_MIXED) return apply_t<double>(h, level == -1 ? h->nlev - 1 : level, x, y);
+  return apply_t<float>(h, level, x, y);
+}
+
+int stfem_smooth(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init) {
+  if (!h || !b || !d || n_sweeps < 1) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  CKR(check_level(h, level, false));
+  if (level < 1) {
+    h->err = "smoothing is defined on levels >= 1";
+    return STFEM_ERR_ARG;
+  }
+  if (h->precision == STFEM_MIXED) return smooth_t<float>(h, level, b, d, n_sweeps, zero_init);
+  return smooth_t<double>(h, level, b, d, n_sweeps, zero_init);
+}
+
+int stfem_restrict(stfem_h h, int level, const double *r_fine, double *b_coarse) {
+  if (!h || !r_fine || !b_coarse) return STFEM_ERR_ARG;
+  CKR(check_level(h, level, false));
+  if (level < 1) return STFEM_ERR_ARG;
+  if (h->precision == STFEM_MIXED) return transfer_t<float>(h, level, r_fine, b_coarse, true);
+  return transfer_t<double>(h, level, r_fine, b_coarse, true);
+}
+
+int stfem_prolongate_add(stfem_h h, int level, const double *d_coarse, double *d_fine) {
+  if (!h || !d_coarse || !d_fine) return STFEM_ERR_ARG;
+  CKR(check_level(h, level, false));
+  if (level < 1) return STFEM_ERR_ARG;
+  if (h->precision == STFEM_MIXED) return transfer_t<float>(h, level, d_coarse, d_fine, false);
+  return transfer_t<double>(h, level, d_coarse, d_fine, false);
+}
+
+int stfem_coarse_solve(stfem_h h, const double *b, double *x) {
+  if (!h || !b || !x) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  coarse<double>(h, b, x);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return STFEM_OK;
+}
+
+int stfem_vcycle(stfem_h h, const double *b, double *d) {
+  if (!h || !b || !d) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  CKR(precondition(h, b, d, nullptr));
+  CK(cudaStreamSynchronize(h->stream));
+  return STFEM_OK;
+}
+
+int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart, int max_it, int *iters,
+               double *rel_res) {
+  if (!h || !rhs || !x || restart < 1 || max_it < 0 || !(tol >= 0.0)) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  int it = 0;
+  double rr = 0.0;
+  int rc = fgmres(h, rhs, x, tol, restart, max_it, &it, &rr);
+  if (iters) *iters = it;
+  if (rel_res) *rel_res = rr;
+  return rc;
+}
+
+int stfem_solve_history(stfem_h h, double *hist_host, int cap, int *n) {
+  if (!h || !n) return STFEM_ERR_ARG;
+  int m = std::min<int>(cap, (int)h->hist.size());
+  for (int i = 0; i < m && hist_host; ++i) hist_host[i] = h->hist[i];
+  *n = m;
+  return STFEM_OK;
+}
+
+int stfem_initial_state(stfem_h h, double *state) {
+  if (!h || !state) return STFEM_ERR_ARG;
+  const stfem::Level &F = h->hl.back();
+  k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, h->t0, F.R, F.S, state);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return STFEM_OK;
+}
+
+static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) {
+  DLevel<double> &F = h->L64.back();
+  const stfem::Level &HF = h->hl.back();
+  TimeCoef<double> one{};
+  one.q = 1;
+  one.Dt[0] = 1.0;
+  one.W[0] = 0.0;
+  launch_spmv<double>(h->stream, F, one, prev, nullptr, h->ys, 0); // S1 * state
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  const double t_prev = h->t0 + slab * h->tau;
+  k_rhs<<<grid_for(F.N, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode, t_prev,
+                                                   h->tau, HF.R, HF.S, h->ys, rhs);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs) {
+  if (!h || !prev_state || !rhs || slab < 0) return STFEM_ERR_ARG;
+  CKR(slab_rhs_async(h, slab, prev_state, rhs));
+  CK(cudaStreamSynchronize(h->stream));
+  return STFEM_OK;
+}
+
+int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int restart, int max_it,
+          int *iters_host) {
+  if (!h || !state || n_slabs < 0 || first_slab < 0) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  DLevel<double> &F = h->L64.back();
+  int worst = STFEM_OK;
+  for (int n = 0; n < n_slabs; ++n) {
+    CKR(slab_rhs_async(h, first_slab + n, state, h->rhs));
+    k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, state, h->xs);
+    int it = 0;
+    double rr = 0.0;
+    int rc = fgmres(h, h->rhs, h->xs, tol, restart, max_it, &it, &rr);
+    if (iters_host) iters_host[n] = it;
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+    CK(cudaMemcpyAsync(state, h->xs + (long)(h->q - 1) * F.ns, F.ns * sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return worst;
+}
+
+const char *stfem_last_error(stfem_h h) { return h ? h->err.c_str() : g_setup_err.c_str(); }
+
+void stfem_destroy(stfem_h h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  delete h;
+}
+
+} // extern "C"

@@ -1,0 +1,131 @@
+"""The C++ host setup of the CUDA path against the oracle (CPU, no GPU).
+
+The two sides share no code: the C++ setup has its own quadrature (Legendre
+recurrences, Newton / bisection), index-form element matrices, structured
+sparsity and Gauss-Jordan inverses.  Matching them checks the assembly that
+the kernels later consume.
+"""
+import re
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+stfem = pytest.importorskip("paper_2303_06742_gb300")
+
+from oracle.space import BoxMesh, Material, SpatialOps
+from oracle.slab import Temporal, slab_matrix
+from oracle.gmg import vertices, patch_dofs, prolongation_scalar
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, re.M):
+                names.add(m.group(1))
+    assert {"stfem_setup", "stfem_gmg_setup", "slab_solve", "march", "stfem_destroy"} <= names
+    for n in names:
+        assert hasattr(stfem.lib, n), n
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_temporal_matches_oracle(k):
+    t, w, chi, Dt = stfem.host_temporal(k)
+    T = Temporal(k)
+    assert np.allclose(t, T.t, atol=1e-14)
+    assert np.allclose(w, T.w, atol=1e-14)
+    assert np.allclose(chi, T.chi_m1, atol=1e-12)
+    assert np.allclose(Dt, T.Dt, atol=1e-11 * max(1.0, np.abs(T.Dt).max()))
+
+
+CASES = [
+    # dim, n, levels, r, k, lo, hi, bc_u, bc_p, hf
+    (2, 4, 2, 2, 1, [0, 0], [1, 1], [1, 1, 1, 1], [1, 1, 1, 1], "measure"),
+    (2, 4, 2, 2, 1, [0, 0], [1, 2], [0, 1, 0, 0], [1, 0, 0, 1], "measure"),
+    (2, 4, 2, 3, 2, [0, 0], [1, 1], [0, 0, 0, 0], [0, 0, 0, 0], "length"),
+    (3, 2, 2, 2, 1, [0, 0, 0], [2, 2, 1], [0, 1, 1, 1, 0, 1], [1, 1, 1, 1, 1, 0], "measure"),
+]
+
+
+def _pair(case, seed=0, coarse_op=0):
+    dim, n, L, r, k, lo, hi, bcu, bcp, hf = case
+    rng = np.random.default_rng(seed)
+    nc = n ** dim
+    lam = rng.uniform(0.5, 5.0, nc)
+    mu = rng.uniform(0.5, 5.0, nc)
+    kap = np.exp(rng.standard_normal(nc))
+    tau = 0.013
+    prob = stfem.Problem(dim, n, L, r, k, tau, lo=lo, hi=hi, rho=1.3, alpha=0.8, c0=0.2,
+                         lam_cell=lam, mu_cell=mu, kappa_cell=kap, bc_u=bcu, bc_p=bcp,
+                         hf_mode=stfem.HF_MEASURE if hf == "measure" else stfem.HF_LENGTH,
+                         coarse_op=coarse_op)
+    meshes = [BoxMesh(dim, lo, hi, [n] * dim, hf)]
+    mats = [Material(1.3, 0.8, 0.2, lam, mu, kap)]
+    for _ in range(L - 1):
+        mats.append(mats[-1].coarsen(meshes[-1]))
+        meshes.append(meshes[-1].coarsen())
+    ops = [SpatialOps(m, r, mt, bcu, bcp) for m, mt in zip(meshes[::-1], mats[::-1])]
+    return prob, ops, Temporal(k), tau
+
+
+@pytest.mark.parametrize("coarse", ["rediscretize", "galerkin"])
+@pytest.mark.parametrize("case", CASES)
+def test_level_matrices_match_oracle(case, coarse):
+    from oracle.gmg import slab_prolongation
+    prob, ops, T, tau = _pair(case, coarse_op=stfem.COARSE_GALERKIN if coarse == "galerkin"
+                              else stfem.COARSE_REDISCRETIZE)
+    mats = [slab_matrix(o, T, tau) for o in ops]
+    if coarse == "galerkin":
+        for l in range(len(ops) - 1, 0, -1):
+            P = slab_prolongation(ops[l - 1], ops[l], T)
+            mats[l - 1] = (P.T @ mats[l] @ P).tocsr()
+    for level, o in enumerate(ops):
+        rp, ci, va, n = stfem.host_level_matrix(prob, level)
+        A = sp.csr_matrix((va, ci, rp), shape=(n, n))
+        B = mats[level]
+        assert A.shape == B.shape
+        # row-wise relative error: Nitsche penalties dominate the largest
+        # entries, so a global scale would hide errors in interior rows
+        scale = np.asarray(abs(B).max(axis=1).todense()).ravel()
+        D = sp.diags(1.0 / scale)
+        diff = abs(D @ (A - B)).max()
+        assert diff <= 1e-12, (level, diff)
+        # and the sparsity patterns agree up to exact zeros
+        assert abs(D @ (abs(A) - abs(B))).max() <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_patch_sets_match_oracle(case):
+    prob, ops, T, tau = _pair(case)
+    for level in range(1, len(ops)):
+        host = stfem.host_patch_dofs(prob, level)
+        ora = [patch_dofs(ops[level], T, v) for v in vertices(ops[level].mesh)]
+        assert len(host) == len(ora)
+        for a, b in zip(host, ora):
+            assert np.array_equal(np.sort(a), np.sort(b))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_prolongations_match_oracle(case):
+    prob, ops, T, tau = _pair(case)
+    for level in range(1, len(ops)):
+        for field, (sc, sf) in enumerate([(ops[level - 1].Vs, ops[level].Vs), (ops[level - 1].Qs, ops[level].Qs)]):
+            rp, ci, va, shape = stfem.host_prolongation(prob, level, field)
+            A = sp.csr_matrix((va, ci, rp), shape=shape)
+            B = prolongation_scalar(sc, sf)
+            assert abs(A - B).max() < 1e-13
+
+
+def test_setup_rejects_bad_arguments():
+    bad = stfem.Problem(2, 6, 3, 2, 1, 0.01)  # 6 not divisible by 4
+    with pytest.raises(stfem.StfemError):
+        stfem.host_level_matrix(bad)
+    bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, bc_u=[1, 0, 0, 0], problem=stfem.PROBLEM_SIN)
+    with pytest.raises(stfem.StfemError):
+        stfem.host_level_matrix(bad)
