@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Benchmark of the GMRES-GMG space-time solver (arXiv 2303.06742) on GB300.
+
+Metric: slab solves per second (with p50/p99 latency per slab solve) of the
+march of a 2D 64x64 Q3/Q2 dG(2) problem (5 GMG levels, tau = 1e-3, lognormal
+per-cell permeability, log-uniform Lame parameters, c0 = 1e-2), solved to a
+relative residual of 1e-8 with the FP32 V-cycle inside FP64 flexible GMRES;
+the plain FP64 path is measured beside it.  One step = one slab of the march:
+right-hand side assembly plus a full FGMRES-GMG solve (all hot-path steps).
+The GMG hierarchy and patch inverses are built once before the timed region
+and stay resident (setup time is reported separately).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU: independent replicas, one instance per rank, no collective on the
+data path ("scaling": "weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_2d_q3_k2_64"
+WORKLOAD_DESC = ("2D unit square 64x64, 5 GMG levels, Q3^2/Q2 Taylor-Hood, dG(2) (3 Radau nodes), "
+                 "tau=1e-3, lambda/mu log-uniform [0.5,50], kappa lognormal per cell (sigma=1), c0=1e-2, "
+                 "alpha=1, manufactured sine solution, Dirichlet (Nitsche) on all faces; "
+                 "N_slab=496,911; FGMRES(30) to 1e-8 relative")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_leg(workload, out_path, mode, steps=0, warmup=0):
+    """Runs the oracle (test infrastructure) in this process on the host cores.
+
+    mode "solve": set up, time one full slab solve (slab 0), save the solution.
+    mode "reference": set up, one full solve for the iteration count, then
+    `warmup`+`steps` samples of two FGMRES iterations each.
+    """
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import inputs
+    from _cases import oracle_instance
+    from oracle.slab import repeat_state
+    c = inputs.case(workload)
+    t0 = time.perf_counter()
+    O = oracle_instance(c)
+    t_setup = time.perf_counter() - t0
+    st0 = O.initial_state()
+    b = O.rhs(0, st0)
+    x0 = repeat_state(O.ops, O.tmp, st0)
+    t0 = time.perf_counter()
+    x, it, rel, _ = O.solve(b, x0, c["tol"])
+    t_solve = time.perf_counter() - t0
+    res = dict(setup_s=t_setup, solve_s=t_solve, iters=it, rel=rel)
+    if mode == "solve":
+        np.save(out_path + ".npy", x)
+    else:
+        samples = []
+        for i in range(warmup + steps):
+            t0 = time.perf_counter()
+            O.solve(b, x0, 0.0, restart=30, max_it=2)
+            if i >= warmup:
+                samples.append((time.perf_counter() - t0) / 2.0)
+        res["per_iter_s"] = samples
+    with open(out_path, "w") as f:
+        json.dump(res, f)
+
+
+def run_oracle_subprocess(workload, mode, steps=0, warmup=0):
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", path, "--workload", workload,
+           "--steps", str(steps), "--warmup", str(warmup), "--impl", "reference" if mode == "reference" else "ours"]
+    subprocess.run(cmd, check=True, env=env)
+    with open(path) as f:
+        res = json.load(f)
+    os.unlink(path)
+    sol = None
+    if os.path.exists(path + ".npy"):
+        import numpy as np
+        sol = np.load(path + ".npy")
+        os.unlink(path + ".npy")
+    return res, sol
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = [l for ts, l in self.lines if t0 - 0.25 <= ts <= t1 + 0.25] or [l for _, l in self.lines]
+        for line in rows:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("stfem.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2303_06742_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(workload, precision):
+    """Per-launch DRAM bytes of the patch-apply kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    key = "%s/%s/patch_apply" % (workload, precision)
+    r = rec.get(key)
+    if not r or r.get("source_hash") != kernel_source_hash():
+        return None
+    return r.get("bytes_per_launch")
+
+
+def pct(vals, q):
+    v = sorted(vals)
+    if not v:
+        return None
+    i = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[i]
+
+
+# ------------------------------------------------------------------ GPU arm
+def make_solver(c, precision, stream):
+    import paper_2303_06742_gb300 as st
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _cases import gpu_problem
+    return st.Solver(gpu_problem(c), precision=precision, stream=stream)
+
+
+def time_march(S, torch, stream, state, first, steps, tol, profile=False):
+    """Marches `steps` slabs one by one; returns per-step device ms, iterations."""
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    iters = []
+    if profile:
+        S.profile(True)
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for i in range(steps):
+            rc, it = S.march(first + i, 1, state, tol=tol)
+            if rc != 0:
+                raise RuntimeError("march returned %d at slab %d" % (rc, first + i))
+            iters.append(it[0])
+            evs[i + 1].record(stream)
+    stream.synchronize()
+    ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    return ms, iters
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import paper_2303_06742_gb300 as st
+    import inputs
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    c = inputs.case(args.workload)
+    tol = c["tol"]
+    stream = torch.cuda.Stream()
+    K, W = args.steps, args.warmup
+
+    # ---- mixed precision (headline)
+    t0 = time.perf_counter()
+    S = make_solver(c, st.MIXED, stream)
+    setup_s = time.perf_counter() - t0
+    state = torch.zeros(S.n_state, dtype=torch.float64, device="cuda")
+    S.initial_state(state)
+    # slab 0 solution for the error against the oracle
+    x_slab0 = None
+    with torch.cuda.stream(stream):
+        rhs0 = torch.zeros(S.n_slab, dtype=torch.float64, device="cuda")
+        S.slab_rhs(0, state, rhs0)
+        x_slab0 = state.repeat(S.prob.q)
+        rc0, it0, rel0 = S.slab_solve(rhs0, x_slab0, tol=tol)
+    stream.synchronize()
+    x_slab0_host = x_slab0.cpu().numpy()
+    launches0 = S.launch_count()
+    time_march(S, torch, stream, state, 0, W, tol)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    ms, iters = time_march(S, torch, stream, state, W, K, tol, profile=True)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    prof = S.profile_read()
+    S.profile(False)
+    launches = sum(v["launches"] for v in prof.values())
+    total_ms = sum(ms)
+    clk = clocks.stop(tw0, tw1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = K * world / (total_ms / 1000.0)
+
+    # ---- end to end through the public call with host buffers
+    E = min(K, 5)
+    n = S.n_slab
+    rhs_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    x0_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    with torch.cuda.stream(stream):
+        rd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        S.slab_rhs(W + K, state, rd)
+        rhs_h.copy_(rd)
+        x0_h.copy_(state.repeat(S.prob.q))
+    stream.synchronize()
+    rhs_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    x_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e_ev[0].record(stream)
+        for _ in range(E):
+            rhs_d.copy_(rhs_h, non_blocking=True)
+            x_d.copy_(x0_h, non_blocking=True)
+            S.slab_solve(rhs_d, x_d, tol=tol)
+            x_h.copy_(x_d, non_blocking=True)
+        e_ev[1].record(stream)
+    stream.synchronize()
+    e2e_ms = e_ev[0].elapsed_time(e_ev[1])
+    e2e_value = E * world / (e2e_ms / 1000.0)
+    info = {l: S.level_info(l) for l in range(c["levels"])}
+    S.close()
+
+    # ---- plain FP64 path beside it
+    fp64 = None
+    if not args.no_fp64:
+        t0 = time.perf_counter()
+        S64 = make_solver(c, st.FP64, stream)
+        setup64 = time.perf_counter() - t0
+        st64 = torch.zeros(S64.n_state, dtype=torch.float64, device="cuda")
+        S64.initial_state(st64)
+        K64 = min(K, 5)
+        time_march(S64, torch, stream, st64, 0, min(W, 2), tol)
+        ms64, it64 = time_march(S64, torch, stream, st64, min(W, 2), K64, tol)
+        fp64 = {"value": K64 / (sum(ms64) / 1000.0), "unit": "slab solves/s", "steps": K64,
+                "p50_ms": pct(ms64, 50), "p99_ms": pct(ms64, 99), "iters_per_slab": it64, "setup_s": setup64}
+        S64.close()
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel (patch-inverse apply)
+    pa = prof["patch_apply"]
+    peak, peak_kind = peak_hbm()
+    achieved = pa["bytes"] / (pa["ms"] / 1000.0) / 1e9 if pa["ms"] > 0 else None
+    traffic = dram_traffic(args.workload, "mixed")
+    roof = {"kernel": "k_patch_apply<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
+            "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"]}
+    breakdown = {k: {"ms": v["ms"], "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-30),
+                     "launches": v["launches"],
+                     "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
+                 for k, v in prof.items()}
+
+    # ---- oracle on the host cores (bounded sample: one slab solve)
+    cpu = None
+    err_vs_oracle = None
+    if not args.no_cpu_baseline:
+        res, sol = run_oracle_subprocess(args.workload, "solve")
+        cpu = {"value": 1.0 / res["solve_s"], "unit": "slab solves/s", "cores": 1, "kind": "oracle",
+               "sample": "one full slab solve (slab 0, FGMRES-GMG to %g, %d iterations) of the same workload; "
+                         "oracle setup (%.1f s) excluded as on the GPU" % (tol, res["iters"], res["setup_s"])}
+        if sol is not None:
+            err_vs_oracle = float(np.abs(x_slab0_host - sol).max() / np.abs(sol).max())
+
+    out = {
+        "metric": "slab solves/s",
+        "value": value,
+        "unit": "slab solves/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": total_ms / K,
+        "p50_ms": pct(ms, 50),
+        "p99_ms": pct(ms, 99),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "FP32 V-cycle inside FP64 FGMRES",
+                   "tol": tol, "restart": 30, "omega": 0.7, "sweeps": 1,
+                   "l2": "inputs larger than L2: %.2f GB of FP32 patch inverses streamed per sweep set"
+                         % (sum(v["inv_bytes"] for v in info.values()) / 1e9),
+                   "levels": info, "parallelism": "replicas" if world > 1 else "single"},
+        "iters_per_slab": iters,
+        "first_slab": {"iters": it0, "rel_res": rel0, "err_vs_fp64_oracle": err_vs_oracle},
+        "setup_s": setup_s,
+        "roofline": roof,
+        "breakdown": breakdown,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "slab solves/s", "steps": E,
+                "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+        "fp64": fp64,
+        "speedup_mixed_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import inputs
+    c = inputs.case(args.workload)
+    res, _ = run_oracle_subprocess(args.workload, "reference", steps=args.steps, warmup=args.warmup)
+    per_iter = res["per_iter_s"]
+    iters = res["iters"]
+    t_slab = statistics.mean(per_iter) * iters
+    value = 1.0 / t_slab
+    samples_ms = [p * iters * 1000.0 for p in per_iter]
+    out = {
+        "impl": "reference",
+        "metric": "slab solves/s",
+        "value": value,
+        "unit": "slab solves/s",
+        "n_gpus": 0,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_slab * 1000.0,
+        "p50_ms": pct(samples_ms, 50),
+        "p99_ms": pct(samples_ms, 99),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "FP64 (oracle)", "tol": c["tol"]},
+        "cpu_baseline": {"value": value, "unit": "slab solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: 2 FGMRES-GMG iterations of slab 0, scaled by the %d iterations "
+                                   "of a full slab solve; oracle setup (%.1f s) excluded" % (iters, res["setup_s"])},
+        "e2e": {"value": value, "unit": "slab solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.cpu_leg:
+        oracle_leg(args.workload, args.cpu_leg, "reference" if args.impl == "reference" else "solve",
+                   args.steps, args.warmup)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

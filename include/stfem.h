@@ -200,6 +200,33 @@ int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs);
 int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int restart,
           int max_it, int *iters_host);
 
+/* ---- Launch accounting ----
+ * Kernel classes of the hot path, for the roofline of each step. */
+#define STFEM_KCLASS_SPMV 0        /* space-time Kronecker SpMV / residual (Eq. 4.7) */
+#define STFEM_KCLASS_PATCH_APPLY 1 /* y_P = A_P^{-1} R_P r for every patch (Eq. 4.11) */
+#define STFEM_KCLASS_UPDATE 2      /* averaged scatter d += omega D^{-1} sum E_P y_P (Algorithm 4.1) */
+#define STFEM_KCLASS_TRANSFER 3    /* restriction / prolongation */
+#define STFEM_KCLASS_COARSE 4      /* coarse direct solve */
+#define STFEM_KCLASS_BLAS1 5       /* Arnoldi dots, axpys, scaling, solution update */
+#define STFEM_KCLASS_RHS 6         /* slab right-hand side */
+#define STFEM_KCLASS_OTHER 7       /* conversions, Givens, reductions, copies */
+#define STFEM_KCLASS_COUNT 8
+
+/* enable != 0 resets the counters and brackets every later kernel launch of
+ * the handle with CUDA events on its stream; 0 stops recording (counters are
+ * also reset).  Launch counts and algorithmic bytes/flops are always counted. */
+int stfem_profile(stfem_h h, int enable);
+
+/* Totals of one kernel class since the last stfem_profile call: launches,
+ * summed device time of the launches in ms (only while profiling), and the
+ * algorithmic bytes and flops of those launches (data each launch must move
+ * at least once / arithmetic it must do, from the sizes of the structures). */
+int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, double *bytes,
+                       double *flops);
+
+/* Number of kernels the handle has launched since it was created. */
+int stfem_launch_count(stfem_h h, long long *n);
+
 /* ---- Host-side inspection of the setup (no GPU needed; for tests) ----
  * These rebuild the hierarchy on the host from the same arguments as
  * stfem_setup and return what the GPU path would upload.  Two-call pattern:

@@ -403,7 +403,7 @@ class SpatialOps:
                     Fe = -np.einsum("q,qi,qc->ic", wf, ph, tN)
                     for li, I in enumerate(un):
                         F[I * d:(I + 1) * d] += Fe[li]
-                else:
+                elif not prob.zero_trace:
                     uD = prob.u(Xfp, t)  # (nqf, d)
                     vD = prob.v(Xfp, t)
                     Pv = self._vector_vals(ph)
@@ -420,7 +420,7 @@ class SpatialOps:
                 if self.bc_p[fid] == NEUMANN:
                     pN = prob.p_flux(Xfp, t, n, kap)
                     G[pn] += -np.einsum("q,q,qr->r", wf, pN, ps)
-                else:
+                elif not prob.zero_trace:
                     pD = prob.p(Xfp, t)
                     dn = kap * np.einsum("qsa,a->qs", dps, n)
                     G[pn] += -np.einsum("q,q,qs->s", wf, pD, dn)

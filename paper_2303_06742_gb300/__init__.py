@@ -3,7 +3,8 @@
 Thin Python binding of the C ABI in ``include/stfem.h`` (arXiv 2303.06742):
 argument marshalling only.  Every step of the solver runs in the CUDA kernels
 of ``libstfem.so``; importing this package fails loudly when the library has
-not been built (``python -m paper_2303_06742_gb300.build``).
+not been built (``python paper_2303_06742_gb300/build.py`` or
+``__graft_entry__.build()``).
 
 Vectors passed to the device calls are CUDA float64 tensors (or any object
 with ``data_ptr()``) in the paper's slab ordering (Eq. 4.4).
@@ -24,6 +25,7 @@ PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPER
 FP64, MIXED = 0, 1
 HF_MEASURE, HF_LENGTH = 0, 1
 COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
+KCLASSES = ["spmv", "patch_apply", "update", "transfer", "coarse", "blas1", "rhs", "other"]
 
 
 class StfemError(RuntimeError):
@@ -59,7 +61,7 @@ class GmgParams(C.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libstfem.so is not built; run `python -m paper_2303_06742_gb300.build` "
+        raise ImportError("libstfem.so is not built; run `python paper_2303_06742_gb300/build.py` "
                           "(or __graft_entry__.build())")
     lib = C.CDLL(LIB_PATH)
     P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
@@ -88,6 +90,9 @@ def _load():
         "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pLL, pI, pD],
         "stfem_host_temporal": [I, pD, pD, pD, pD],
+        "stfem_profile": [P, I],
+        "stfem_profile_read": [P, I, pLL, pD, pD, pD],
+        "stfem_launch_count": [P, pLL],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -283,6 +288,23 @@ class Solver:
 
     def slab_rhs(self, slab, prev_state, rhs):
         self._check(lib.stfem_slab_rhs(self.h, slab, _ptr(prev_state), _ptr(rhs)))
+
+    def profile(self, enable=True):
+        self._check(lib.stfem_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{class: dict(launches, ms, bytes, flops)} since the last profile() call."""
+        out = {}
+        for i, name in enumerate(KCLASSES):
+            n, ms, by, fl = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+            self._check(lib.stfem_profile_read(self.h, i, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+            out[name] = dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+        return out
+
+    def launch_count(self):
+        n = C.c_longlong()
+        self._check(lib.stfem_launch_count(self.h, C.byref(n)))
+        return n.value
 
     def march(self, first_slab, n_slabs, state, tol=1e-8, restart=30, max_it=500):
         iters = (C.c_int * max(n_slabs, 1))()

@@ -577,6 +577,8 @@ struct DLevel {
   long long inv_elems = 0, sumC = 0;
   int *iptr = nullptr, *ipos = nullptr;
   T *scale = nullptr, *ybuf = nullptr;
+  double patch_bytes = 0.0, patch_flops = 0.0; // algorithmic, per patch-apply launch
+  double transfer_bytes = 0.0, transfer_nnz = 0.0;
   // work vectors
   T *b = nullptr, *d = nullptr, *r = nullptr;
   // transfer from level l-1 (valid for l >= 1): P rows fine, R rows coarse
@@ -618,6 +620,16 @@ struct stfem_ctx {
   LoadTables lt{};
   std::vector<double> hist;
   std::vector<void *> allocs;
+  // launch accounting: totals per kernel class; event pairs when profiling
+  long long launches = 0;
+  bool prof = false;
+  struct KStat {
+    long long launches = 0;
+    double bytes = 0.0, flops = 0.0, ms = 0.0;
+  } kstat[STFEM_KCLASS_COUNT];
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  std::vector<std::pair<int, size_t>> pending; // (class, index of start event)
 };
 
 namespace {
@@ -638,6 +650,34 @@ std::string g_setup_err;
     int rc_ = (expr);                                                                                \
     if (rc_ < 0) return rc_;                                                                         \
   } while (0)
+
+// Counts a kernel launch of class kc with its algorithmic bytes/flops and,
+// when profiling is on, brackets it with a pair of events on the stream.
+struct Launch {
+  stfem_h h;
+  int kc;
+  Launch(stfem_h h_, int kc_, double bytes, double flops) : h(h_), kc(kc_) {
+    h->launches++;
+    h->kstat[kc].launches++;
+    h->kstat[kc].bytes += bytes;
+    h->kstat[kc].flops += flops;
+    if (h->prof) record();
+  }
+  ~Launch() {
+    if (h->prof) record();
+  }
+  void record() {
+    if (h->evnext >= h->evpool.size()) {
+      for (int i = 0; i < 1024; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->evpool.push_back(e);
+      }
+    }
+    if (h->evnext % 2 == 0) h->pending.push_back({kc, h->evnext});
+    cudaEventRecord(h->evpool[h->evnext++], h->stream);
+  }
+};
 
 template <typename T>
 int dalloc(stfem_h h, T **p, size_t n) {
@@ -674,9 +714,21 @@ void launch_spmv_q(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, co
   k_spmv<T, Q, G><<<grid_for(threads, 256), 256, 0, s>>>(L.ns, L.rowptr, L.col, L.v1, L.v2, tc, x, rhs, y, mode);
 }
 
+// algorithmic bytes of one Kronecker SpMV: the matrix once, x and y (and rhs) once
 template <typename T>
-void launch_spmv(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+double spmv_bytes(const DLevel<T> &L, int q, int mode) {
+  return (double)L.nnz * (4.0 + 2.0 * sizeof(T)) + (L.ns + 1) * 4.0 + (double)q * L.ns * sizeof(T) * (mode ? 3 : 2);
+}
+template <typename T>
+double spmv_flops(const DLevel<T> &L, int q) {
+  return 4.0 * L.nnz * q + 2.0 * L.ns * q * (q + 1);
+}
+
+template <typename T>
+void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
                  int mode) {
+  Launch G_(h, STFEM_KCLASS_SPMV, spmv_bytes(L, tc.q, mode), spmv_flops(L, tc.q));
+  cudaStream_t s = h->stream;
   switch (tc.q) {
   case 1: launch_spmv_q<T, 1>(s, L, tc, x, rhs, y, mode); break;
   case 2: launch_spmv_q<T, 2>(s, L, tc, x, rhs, y, mode); break;
@@ -718,6 +770,10 @@ int upload_transfer(stfem_h h, DLevel<T> &D, const stfem::CSR &Pu, const stfem::
   CKR(upload(h, &D.Rp_p, Rp.rowptr));
   CKR(upload(h, &D.Rp_c, Rp.col));
   CKR(upload(h, &D.Rp_v, Rp.val));
+  // multiply-adds of one slab transfer: q time nodes x (2d copies of the Q_r
+  // operator + the Q_{r-1} operator); the operator itself is read once
+  D.transfer_nnz = (double)h->q * (2.0 * h->dim * Pu.col.size() + Pp.col.size());
+  D.transfer_bytes = (double)(Pu.col.size() + Pp.col.size()) * (4.0 + sizeof(T));
   return 0;
 }
 
@@ -727,6 +783,15 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
   D.maxC = *std::max_element(P.size.begin(), P.size.end());
   D.inv_elems = (long long)P.inv.size();
   D.sumC = (long long)P.dofs.size();
+  // algorithmic bytes of one patch-apply launch: every inverse once (C_P^2
+  // entries), the dof index, the gathered residual and the result per row
+  D.patch_bytes = 0.0;
+  D.patch_flops = 0.0;
+  for (long p = 0; p < P.npatch; ++p) {
+    const double C = P.size[p];
+    D.patch_bytes += C * C * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
+    D.patch_flops += 2.0 * C * C;
+  }
   CKR(upload(h, &D.psize, P.size));
   CKR(upload(h, &D.pld, P.ld));
   CKR(upload(h, &D.pdofs, P.dofs));
@@ -777,15 +842,23 @@ void smooth(stfem_h h, int l, int nsw, bool zero_init) {
     const bool zero = zero_init && it == 0;
     const T *res = L.b;
     if (!zero) {
-      launch_spmv<T>(s, L, tc, L.d, L.b, L.r, 1);
+      launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1);
       res = L.r;
     }
     constexpr int VEC = Vec16<T>::n;
     int threads = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
     threads = std::min(std::max(threads, 32), 512);
-    k_patch_apply<T><<<(unsigned)L.npatch, threads, L.maxC * sizeof(T), s>>>(L.psize, L.pdoff, L.pdofs, L.pioff,
-                                                                              L.pld, L.pinv, res, L.ybuf);
-    k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d, zero ? 1 : 0);
+    {
+      Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
+      k_patch_apply<T><<<(unsigned)L.npatch, threads, L.maxC * sizeof(T), s>>>(L.psize, L.pdoff, L.pdofs, L.pioff,
+                                                                                L.pld, L.pinv, res, L.ybuf);
+    }
+    {
+      Launch G_(h, STFEM_KCLASS_UPDATE,
+                (double)L.N * (4.0 + 3.0 * sizeof(T)) + (double)L.sumC * (4.0 + sizeof(T)), (double)L.sumC + 2.0 * L.N);
+      k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d,
+                                                           zero ? 1 : 0);
+    }
   }
 }
 
@@ -793,6 +866,7 @@ template <typename T>
 void restrict_to(stfem_h h, int l, const T *rf, T *bc) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
+  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
   k_transfer<T><<<grid_for(C.N, 256), 256, 0, h->stream>>>(C.N, C.ns, C.R, F.ns, F.R, h->dim, F.Ru_p, F.Ru_c, F.Ru_v,
                                                             F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
 }
@@ -801,6 +875,7 @@ template <typename T>
 void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
+  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
   k_transfer<T><<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.N, F.ns, F.R, C.ns, C.R, h->dim, F.Pu_p, F.Pu_c, F.Pu_v,
                                                             F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
 }
@@ -808,6 +883,7 @@ void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
 template <typename T>
 void coarse(stfem_h h, const T *b, T *x) {
   const long n = levels<T>(h)[0].N;
+  Launch G_(h, STFEM_KCLASS_COARSE, (double)n * n * 8.0 + 2.0 * n * sizeof(T), 2.0 * n * n);
   k_coarse<T><<<grid_for(n * 32, 256), 256, 0, h->stream>>>(n, h->coarse_inv, b, x);
 }
 
@@ -822,7 +898,7 @@ void vcycle(stfem_h h, int l) {
   DLevel<T> &L = Ls[l];
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
   smooth<T>(h, l, h->nsweeps, true);
-  launch_spmv<T>(h->stream, L, tc, L.d, L.b, L.r, 1);
+  launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1);
   restrict_to<T>(h, l, L.r, Ls[l - 1].b);
   vcycle<T>(h, l - 1);
   prolongate_add<T>(h, l, Ls[l - 1].d, L.d);
@@ -840,10 +916,16 @@ int precondition(stfem_h h, const double *v, double *zd, float *zf) {
     CK(cudaMemcpyAsync(zd, F.d, F.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
     DLevel<float> &F = h->L32[L];
-    k_convert<double, float><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, v, F.b);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, F.N * 12.0, 0.0);
+      k_convert<double, float><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, v, F.b);
+    }
     vcycle<float>(h, L);
     if (zf) CK(cudaMemcpyAsync(zf, F.d, F.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    if (zd) k_convert<float, double><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, F.d, zd);
+    if (zd) {
+      Launch G_(h, STFEM_KCLASS_OTHER, F.N * 12.0, 0.0);
+      k_convert<float, double><<<grid_for(F.N, 256), 256, 0, s>>>(F.N, F.d, zd);
+    }
   }
   CK(cudaGetLastError());
   return 0;
@@ -852,8 +934,14 @@ int precondition(stfem_h h, const double *v, double *zd, float *zf) {
 // dots out[0..k) = V_v . w on device (deterministic two-stage reduction)
 void multidot(stfem_h h, int k, const double *V, long ldV, const double *w, long n, double *out) {
   dim3 grid(DOT_BLOCKS, (k + DOT_NV - 1) / DOT_NV);
-  k_multidot<<<grid, DOT_THREADS, 0, h->stream>>>(k, V, ldV, w, n, h->partial);
-  k_reduce_partials<<<k, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(k + 1) * n * 8.0, 2.0 * k * n);
+    k_multidot<<<grid, DOT_THREADS, 0, h->stream>>>(k, V, ldV, w, n, h->partial);
+  }
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)k * DOT_BLOCKS * 8.0, (double)k * DOT_BLOCKS);
+    k_reduce_partials<<<k, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+  }
 }
 
 int read_scalar(stfem_h h, const double *dev, double *host) {
@@ -897,7 +985,7 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
   h->hist.clear();
   *iters = 0;
   *relres = 0.0;
-  launch_spmv<double>(s, F, tc, x, b, h->rvec, 1);
+  launch_spmv<double>(h, F, tc, x, b, h->rvec, 1);
   multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
   double beta0sq;
   CKR(read_scalar(h, h->hn2, &beta0sq));
@@ -912,8 +1000,14 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
   int it = 0;
   const int m1 = m + 1;
   for (;;) {
-    k_div<<<nb, 256, 0, s>>>(N, h->rvec, h->V, nullptr, beta);
-    k_set<<<1, 1, 0, s>>>(h->g, beta);
+    {
+      Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+      k_div<<<nb, 256, 0, s>>>(N, h->rvec, h->V, nullptr, beta);
+    }
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, 8.0, 0.0);
+      k_set<<<1, 1, 0, s>>>(h->g, beta);
+    }
     int jlast = -1;
     bool stop = false;
     for (int j = 0; j < m; ++j) {
@@ -927,14 +1021,23 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
         zj = h->zt;
       }
       double *w = h->w;
-      launch_spmv<double>(s, F, tc, zj, nullptr, w, 0);
+      launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
       // classical Gram-Schmidt, applied twice
       multidot(h, j + 1, h->V, N, w, N, h->h1);
-      k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
+      {
+        Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
+        k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
+      }
       multidot(h, j + 1, h->V, N, w, N, h->h2);
-      k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
+      {
+        Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
+        k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
+      }
       multidot(h, 1, w, N, w, N, h->hn2);
-      k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);
+      {
+        Launch G_(h, STFEM_KCLASS_OTHER, (double)(4 * j + 8) * 8.0, (double)(6 * j + 10));
+        k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);
+      }
       CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       CK(cudaGetLastError());
@@ -944,7 +1047,10 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
         *iters = it;
         return STFEM_ERR_BREAKDOWN;
       }
-      if (hn > 0.0) k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
+      if (hn > 0.0) {
+        Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+        k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
+      }
       ++it;
       jlast = j;
       h->hist.push_back(res / beta0);
@@ -954,12 +1060,19 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
       }
     }
     const int kk = jlast + 1;
-    k_backsolve<<<1, 1, 0, s>>>(kk, m1, h->H, h->g, h->y);
-    if (h->precision == STFEM_FP64)
-      k_update_x<double><<<nb, 256, 0, s>>>(N, kk, h->Zd, N, h->y, x);
-    else
-      k_update_x<float><<<nb, 256, 0, s>>>(N, kk, h->Zf, N, h->y, x);
-    launch_spmv<double>(s, F, tc, x, b, h->rvec, 1);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, (double)kk * kk * 8.0, (double)kk * kk);
+      k_backsolve<<<1, 1, 0, s>>>(kk, m1, h->H, h->g, h->y);
+    }
+    {
+      Launch G_(h, STFEM_KCLASS_BLAS1, (double)N * (16.0 + kk * (h->precision == STFEM_FP64 ? 8.0 : 4.0)),
+                2.0 * kk * N);
+      if (h->precision == STFEM_FP64)
+        k_update_x<double><<<nb, 256, 0, s>>>(N, kk, h->Zd, N, h->y, x);
+      else
+        k_update_x<float><<<nb, 256, 0, s>>>(N, kk, h->Zf, N, h->y, x);
+    }
+    launch_spmv<double>(h, F, tc, x, b, h->rvec, 1);
     multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
     double rr;
     CKR(read_scalar(h, h->hn2, &rr));
@@ -997,10 +1110,12 @@ int require_gmg(stfem_h h) {
 // copy an FP64 ABI vector into a level buffer of type T (and back)
 template <typename T>
 void to_level(stfem_h h, const double *src, T *dst, long n) {
+  Launch G_(h, STFEM_KCLASS_OTHER, n * (8.0 + sizeof(T)), 0.0);
   k_convert<double, T><<<grid_for(n, 256), 256, 0, h->stream>>>(n, src, dst);
 }
 template <typename T>
 void from_level(stfem_h h, const T *src, double *dst, long n) {
+  Launch G_(h, STFEM_KCLASS_OTHER, n * (8.0 + sizeof(T)), 0.0);
   k_convert<T, double><<<grid_for(n, 256), 256, 0, h->stream>>>(n, src, dst);
 }
 
@@ -1009,7 +1124,7 @@ int apply_t(stfem_h h, int level, const double *x, double *y) {
   DLevel<T> &L = levels<T>(h)[level];
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
   to_level<T>(h, x, L.d, L.N);
-  launch_spmv<T>(h->stream, L, tc, L.d, nullptr, L.r, 0);
+  launch_spmv<T>(h, L, tc, L.d, nullptr, L.r, 0);
   from_level<T>(h, L.r, y, L.N);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
@@ -1353,7 +1468,10 @@ int stfem_solve_history(stfem_h h, double *hist_host, int cap, int *n) {
 int stfem_initial_state(stfem_h h, double *state) {
   if (!h || !state) return STFEM_ERR_ARG;
   const stfem::Level &F = h->hl.back();
-  k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, h->t0, F.R, F.S, state);
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, F.ns * 8.0, 0.0);
+    k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, h->t0, F.R, F.S, state);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return STFEM_OK;
@@ -1366,9 +1484,10 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) 
   one.q = 1;
   one.Dt[0] = 1.0;
   one.W[0] = 0.0;
-  launch_spmv<double>(h->stream, F, one, prev, nullptr, h->ys, 0); // S1 * state
+  launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0); // S1 * state
   const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
   const double t_prev = h->t0 + slab * h->tau;
+  Launch G_(h, STFEM_KCLASS_RHS, (double)F.N * 16.0, 0.0);
   k_rhs<<<grid_for(F.N, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode, t_prev,
                                                    h->tau, HF.R, HF.S, h->ys, rhs);
   CK(cudaGetLastError());
@@ -1390,7 +1509,10 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
   int worst = STFEM_OK;
   for (int n = 0; n < n_slabs; ++n) {
     CKR(slab_rhs_async(h, first_slab + n, state, h->rhs));
-    k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, state, h->xs);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, F.N * 8.0 + F.ns * 8.0, 0.0);
+      k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, state, h->xs);
+    }
     int it = 0;
     double rr = 0.0;
     int rc = fgmres(h, h->rhs, h->xs, tol, restart, max_it, &it, &rr);
@@ -1404,12 +1526,49 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
   return worst;
 }
 
+int stfem_profile(stfem_h h, int enable) {
+  if (!h) return STFEM_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  h->prof = enable != 0;
+  for (auto &k : h->kstat) k = stfem_ctx::KStat();
+  h->pending.clear();
+  h->evnext = 0;
+  return STFEM_OK;
+}
+
+int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, double *bytes, double *flops) {
+  if (!h || kclass < 0 || kclass >= STFEM_KCLASS_COUNT) return STFEM_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  // resolve recorded event pairs into per-class times
+  for (const auto &pe : h->pending) {
+    float t = 0.f;
+    if (pe.second + 1 < h->evnext &&
+        cudaEventElapsedTime(&t, h->evpool[pe.second], h->evpool[pe.second + 1]) == cudaSuccess)
+      h->kstat[pe.first].ms += t;
+  }
+  h->pending.clear();
+  h->evnext = 0;
+  const auto &k = h->kstat[kclass];
+  if (launches) *launches = k.launches;
+  if (ms) *ms = k.ms;
+  if (bytes) *bytes = k.bytes;
+  if (flops) *flops = k.flops;
+  return STFEM_OK;
+}
+
+int stfem_launch_count(stfem_h h, long long *n) {
+  if (!h || !n) return STFEM_ERR_ARG;
+  *n = h->launches;
+  return STFEM_OK;
+}
+
 const char *stfem_last_error(stfem_h h) { return h ? h->err.c_str() : g_setup_err.c_str(); }
 
 void stfem_destroy(stfem_h h) {
   if (!h) return;
   cudaDeviceSynchronize();
   for (void *p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
 }

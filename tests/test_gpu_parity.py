@@ -9,8 +9,9 @@ Floating-point tolerances (FP64 mode):
 * operator applications, transfers: 1e-13 relative (sums of O(100) products);
 * anything that applies an explicit inverse (patch, coarse): the inverses are
   computed by different algorithms (LAPACK LU in the oracle, Gauss-Jordan on
-  the host here), so they agree to about cond(A_P) eps; with the Nitsche
-  penalty cond(A_P) reaches ~1e6-1e8, giving the 1e-8 relative bound;
+  the host here), so they agree to about cond(A) eps; smoothers and V-cycles
+  are held to 1e-11, the coarse solve (larger, worse-conditioned matrix) to
+  1e-10;
 * FGMRES iterates and march states: the benchmark spec's bound of 1e-10 relative is
   applied to the solution of each solve (tol 1e-10 problems); residual
   histories agree to 1e-6 relative.
@@ -94,7 +95,7 @@ def test_coarse_solve(name):
     S.coarse_solve(dev(b), x)
     err = _rel(host(x), sla.lu_solve(O.h.coarse_lu, b))
     print(name, "coarse", err)
-    assert err < 1e-8
+    assert err < 1e-10
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -115,7 +116,7 @@ def test_smoother_every_level(name):
         ref = smooth(lev, b, d0.copy(), 0.7, 2)
         e2 = _rel(host(d), ref)
         print(name, "smooth level", l, e1, e2)
-        assert e1 < 1e-8 and e2 < 1e-8
+        assert e1 < 1e-11 and e2 < 1e-11
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -127,7 +128,7 @@ def test_vcycle(name):
     S.vcycle(dev(b), d)
     err = _rel(host(d), O.h.vcycle(b))
     print(name, "vcycle", err)
-    assert err < 1e-8
+    assert err < 1e-11
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -148,7 +149,7 @@ def test_initial_state_and_rhs(name):
         ref = O.rhs(n, prev_t)
         err = _rel(host(rhs), ref)
         print(name, "rhs", n, err)
-        assert err < 1e-12
+        assert err < 1e-13
 
 
 @pytest.mark.parametrize("name", CASES)
