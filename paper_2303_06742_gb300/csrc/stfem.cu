@@ -35,52 +35,143 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------- SpMV
-// y_b = sum_a Dt[b,a] S1 x_a + W_b S2 x_b   (mode 0)
-// y_b = rhs_b - (...)                        (mode 1)
-// G lanes cooperate on one spatial row.
-template <typename T, int Q, int G>
-__global__ void __launch_bounds__(256) k_spmv(long ns, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                              const T *__restrict__ v1, const T *__restrict__ v2, TimeCoef<T> tc,
-                                              const T *__restrict__ x, const T *__restrict__ rhs,
-                                              T *__restrict__ y, int mode) {
+// y_b = sum_a Dt[b,a] S1 x_a + W_b S2 x_b (mode 0) or rhs_b - (...) (mode 1):
+// the slab operator A_n = Dt (x) S1 + W (x) S2 of Eq. 4.7.
+// Node-block form of the same operator.  For a displacement node I with
+// neighbours J (shared cell) and pressure neighbours s:
+//   u-eq_b[I,c] = sum_a Dt[b,a] (Mr U_a)[I,c] - W_b (Mr V_b)[I,c]
+//   v-eq_b[I,c] = sum_a Dt[b,a] (Mr V_a)[I,c] + W_b ((K U_b)[I,c] + (Ct P_b)[I,c])
+// and for a pressure node s
+//   p-eq_b[s]   = sum_a Dt[b,a] (Mp0 P_a)[s] + W_b ((B P_b)[s] + (Cn V_b)[s])
+// with Mr = rho M (scalar), K (d x d per pair), Ct = C^T (d per pair),
+// Mp0 = c0 Mp, Cn = -C (d per pair).  G lanes per node.
+template <typename T>
+struct NodeBlockDev {
+  long nu, np;
+  const int *uu_ptr, *uu_col;
+  const T *uu_m, *uu_k;
+  const int *up_ptr, *up_col;
+  const T *up_c;
+  const int *pu_ptr, *pu_col;
+  const T *pu_c;
+  const int *pp_ptr, *pp_col;
+  const T *pp_m, *pp_b;
+};
+
+template <typename T, int Q, int D, int G>
+__global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
+                                                 const T *__restrict__ x, const T *__restrict__ rhs,
+                                                 T *__restrict__ y, int mode) {
+  constexpr int NA = 4 * Q * D;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long row = gid / G;
+  const long node = gid / G;
   const int lane = threadIdx.x % G;
-  const bool valid = row < ns;
-  T s1[Q], s2[Q];
+  T acc[NA];
 #pragma unroll
-  for (int a = 0; a < Q; ++a) s1[a] = s2[a] = T(0);
-  if (valid) {
-    const int e1 = rowptr[row + 1];
-    for (int e = rowptr[row] + lane; e < e1; e += G) {
-      const int c = col[e];
-      const T a1 = v1[e], a2 = v2[e];
+  for (int i = 0; i < NA; ++i) acc[i] = T(0);
+  const bool is_u = node < A.nu;
+  const bool is_p = !is_u && node < A.nu + A.np;
+  if (is_u) {
+    // acc layout: [0] Mr U, [1] Mr V, [2] K U, [3] Ct P; each Q x D
+    const int e1 = A.uu_ptr[node + 1];
+    for (int e = A.uu_ptr[node] + lane; e < e1; e += G) {
+      const long J = A.uu_col[e];
+      const T m = A.uu_m[e];
+      T k[D * D];
+#pragma unroll
+      for (int i = 0; i < D * D; ++i) k[i] = A.uu_k[(long)e * D * D + i];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        const T xv = x[(long)a * ns + c];
-        s1[a] += a1 * xv;
-        s2[a] += a2 * xv;
+        T v[D], u[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          v[c] = x[(long)a * ns + J * D + c];
+          u[c] = x[(long)a * ns + R + J * D + c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          acc[(0 * Q + a) * D + c] += m * u[c];
+          acc[(1 * Q + a) * D + c] += m * v[c];
+          T kk = T(0);
+#pragma unroll
+          for (int cp = 0; cp < D; ++cp) kk += k[c * D + cp] * u[cp];
+          acc[(2 * Q + a) * D + c] += kk;
+        }
+      }
+    }
+    const int f1 = A.up_ptr[node + 1];
+    for (int e = A.up_ptr[node] + lane; e < f1; e += G) {
+      const long sI = A.up_col[e];
+      T ct[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T pv = x[(long)a * ns + 2 * R + sI];
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[(3 * Q + a) * D + c] += ct[c] * pv;
+      }
+    }
+  } else if (is_p) {
+    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V
+    const long sI = node - A.nu;
+    const int e1 = A.pp_ptr[sI + 1];
+    for (int e = A.pp_ptr[sI] + lane; e < e1; e += G) {
+      const long s2 = A.pp_col[e];
+      const T m = A.pp_m[e], bb = A.pp_b[e];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T pv = x[(long)a * ns + 2 * R + s2];
+        acc[a] += m * pv;
+        acc[Q + a] += bb * pv;
+      }
+    }
+    const int f1 = A.pu_ptr[sI + 1];
+    for (int e = A.pu_ptr[sI] + lane; e < f1; e += G) {
+      const long J = A.pu_col[e];
+      T cn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        T t = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + J * D + c];
+        acc[2 * Q + a] += t;
       }
     }
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      s1[a] += __shfl_xor_sync(0xffffffffu, s1[a], o);
-      s2[a] += __shfl_xor_sync(0xffffffffu, s2[a], o);
-    }
+    for (int i = 0; i < NA; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
   }
-  if (valid && lane < Q) {
-    // lane b writes time node b
+  if (is_u) {
+    // outputs: (eq in {u, v}) x Q x D, output o written by lane o % G
+#pragma unroll
+    for (int o = 0; o < 2 * Q * D; ++o) {
+      if (o % G != lane) continue;
+      const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
+      T val = T(0);
+#pragma unroll
+      for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[(eq * Q + a) * D + c];
+      if (eq == 0)
+        val -= tc.W[b] * acc[(1 * Q + b) * D + c];
+      else
+        val += tc.W[b] * (acc[(2 * Q + b) * D + c] + acc[(3 * Q + b) * D + c]);
+      const long oi = (long)b * ns + eq * R + node * D + c;
+      y[oi] = mode ? rhs[oi] - val : val;
+    }
+  } else if (is_p) {
+    const long sI = node - A.nu;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
-      if (b != lane) continue;
-      T acc = tc.W[b] * s2[b];
+      if (b % G != lane) continue;
+      T val = tc.W[b] * (acc[Q + b] + acc[2 * Q + b]);
 #pragma unroll
-      for (int a = 0; a < Q; ++a) acc += tc.Dt[b * Q + a] * s1[a];
-      const long o = (long)b * ns + row;
-      y[o] = mode ? rhs[o] - acc : acc;
+      for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
+      const long oi = (long)b * ns + 2 * R + sI;
+      y[oi] = mode ? rhs[oi] - val : val;
     }
   }
 }
@@ -116,45 +207,66 @@ __device__ __forceinline__ void fma_vec<double>(double *acc, const double2 &a, d
 
 // y_P = A_P^{-1} R_P res for every patch P of the level (one CTA per patch).
 // The inverse is column-major with leading dimension ld_P (multiple of VEC);
-// a thread owns VEC consecutive rows and loops over the columns, so a warp
-// streams 32 x 16 contiguous bytes per column.
-template <typename T>
-__global__ void __launch_bounds__(512) k_patch_apply(const int *__restrict__ psize, const long long *__restrict__ pdoff,
-                                                     const int *__restrict__ pdofs, const long long *__restrict__ pioff,
-                                                     const int *__restrict__ pld, const T *__restrict__ pinv,
-                                                     const T *__restrict__ res, T *__restrict__ y) {
+// thread (tr, tj) owns VEC consecutive rows starting at VEC*tr and the
+// columns j = tj, tj + J, ...: each warp streams 32 x 16 contiguous bytes per
+// column.  With J > 1 (levels with few patches) the J partial sums are added
+// in a fixed order through shared memory, so the result is deterministic.
+template <typename T, int J>
+__global__ void __launch_bounds__(1024) k_patch_apply(const int *__restrict__ psize,
+                                                      const long long *__restrict__ pdoff,
+                                                      const int *__restrict__ pdofs,
+                                                      const long long *__restrict__ pioff,
+                                                      const int *__restrict__ pld, const T *__restrict__ pinv,
+                                                      const T *__restrict__ res, T *__restrict__ y) {
   using V = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
-  extern __shared__ unsigned char smem_raw[];
-  T *rs = reinterpret_cast<T *>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int RT = blockDim.x / J;
+  const int tr = threadIdx.x % RT, tj = threadIdx.x / RT;
   const long p = blockIdx.x;
   const int C = psize[p];
   const long long doff = pdoff[p];
+  T *red = reinterpret_cast<T *>(smem_raw);             // [J][RT][VEC]
+  T *rs = red + (J > 1 ? (size_t)J * RT * VEC : 0);     // [C]
   for (int j = threadIdx.x; j < C; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
   __syncthreads();
   const T *A = pinv + pioff[p];
-  const int ld = pld[p];
-  for (int row0 = VEC * threadIdx.x; row0 < C; row0 += VEC * blockDim.x) {
+  const long stride = pld[p] / VEC;
+  for (int base = 0; base < C; base += VEC * RT) {
+    const int row0 = base + VEC * tr;
     T acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = T(0);
-    const V *col0 = reinterpret_cast<const V *>(A + row0);
-    const long stride = ld / VEC;
-    int j = 0;
-    for (; j + 4 <= C; j += 4) {
-      const V a0 = __ldcs(col0 + (long)(j + 0) * stride);
-      const V a1 = __ldcs(col0 + (long)(j + 1) * stride);
-      const V a2 = __ldcs(col0 + (long)(j + 2) * stride);
-      const V a3 = __ldcs(col0 + (long)(j + 3) * stride);
-      fma_vec<T>(acc, a0, rs[j + 0]);
-      fma_vec<T>(acc, a1, rs[j + 1]);
-      fma_vec<T>(acc, a2, rs[j + 2]);
-      fma_vec<T>(acc, a3, rs[j + 3]);
-    }
-    for (; j < C; ++j) fma_vec<T>(acc, __ldcs(col0 + (long)j * stride), rs[j]);
+    if (row0 < C) {
+      const V *col0 = reinterpret_cast<const V *>(A + row0);
+      int j = tj;
+      for (; j + 7 * J < C; j += 8 * J) {
+        V a[8];
 #pragma unroll
-    for (int v = 0; v < VEC; ++v)
-      if (row0 + v < C) y[doff + row0 + v] = acc[v];
+        for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) fma_vec<T>(acc, a[u], rs[j + u * J]);
+      }
+      for (; j < C; j += J) fma_vec<T>(acc, __ldcs(col0 + (long)j * stride), rs[j]);
+    }
+    if (J > 1) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) red[((size_t)tj * RT + tr) * VEC + v] = acc[v];
+      __syncthreads();
+      if (tj == 0 && row0 < C) {
+        for (int t = 1; t < J; ++t)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[v] += red[((size_t)t * RT + tr) * VEC + v];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          if (row0 + v < C) y[doff + row0 + v] = acc[v];
+      }
+      __syncthreads();
+    } else if (row0 < C) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        if (row0 + v < C) y[doff + row0 + v] = acc[v];
+    }
   }
 }
 
@@ -172,31 +284,45 @@ __global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *
 }
 
 // ---------------------------------------------------------------- transfers
-// out[a, block, node] = sum_k M[node, k] in[a, block, k] for the scalar
-// operator of the block's space (Q_r for the V/U blocks, Q_{r-1} for P).
-// add != 0 accumulates into out.
-template <typename T>
-__global__ void k_transfer(long n_out, long ns_out, long R_out, long ns_in, long R_in, int d, const int *__restrict__ up,
-                           const int *__restrict__ uc, const T *__restrict__ uv, const int *__restrict__ pp,
-                           const int *__restrict__ pc, const T *__restrict__ pv, const T *__restrict__ in,
-                           T *__restrict__ out, int add) {
+// out[a, blk, node*d + c] (+)= sum_e M[node, e] in[a, blk, col_e*d + c] for the
+// vector blocks blk = V, U (scalar operator of the Q_r space) and
+// out[a, P, node] (+)= sum_e Mp[node, e] in[a, P, col_e] (Q_{r-1} space), for
+// every time node a.  One thread per output node.
+template <typename T, int D>
+__global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_out, long ns_in, long R_in,
+                           const int *__restrict__ up, const int *__restrict__ uc, const T *__restrict__ uv,
+                           const int *__restrict__ pp, const int *__restrict__ pc, const T *__restrict__ pv,
+                           const T *__restrict__ in, T *__restrict__ out, int add) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_out) return;
-  const long a = i / ns_out, m = i % ns_out;
-  const T *src = in + a * ns_in;
-  T acc = T(0);
-  if (m < 2 * R_out) {
-    const long blk = m / R_out, rem = m % R_out;
-    const long node = rem / d;
-    const int comp = (int)(rem % d);
-    const T *s = src + blk * R_in + comp;
-    for (int e = up[node]; e < up[node + 1]; ++e) acc += uv[e] * s[(long)uc[e] * d];
-  } else {
-    const long node = m - 2 * R_out;
-    const T *s = src + 2 * R_in;
-    for (int e = pp[node]; e < pp[node + 1]; ++e) acc += pv[e] * s[pc[e]];
+  if (i < nu_out) {
+    const int e0 = up[i], e1 = up[i + 1];
+    for (int a = 0; a < q; ++a)
+      for (int blk = 0; blk < 2; ++blk) {
+        T acc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = T(0);
+        const T *src = in + (long)a * ns_in + blk * R_in;
+        for (int e = e0; e < e1; ++e) {
+          const T w = uv[e];
+          const T *sp = src + (long)uc[e] * D;
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[c] += w * sp[c];
+        }
+        T *dst = out + (long)a * ns_out + blk * R_out + i * D;
+#pragma unroll
+        for (int c = 0; c < D; ++c) dst[c] = add ? dst[c] + acc[c] : acc[c];
+      }
+  } else if (i < nu_out + np_out) {
+    const long node = i - nu_out;
+    const int e0 = pp[node], e1 = pp[node + 1];
+    for (int a = 0; a < q; ++a) {
+      T acc = T(0);
+      const T *src = in + (long)a * ns_in + 2 * R_in;
+      for (int e = e0; e < e1; ++e) acc += pv[e] * src[pc[e]];
+      T *dst = out + (long)a * ns_out + 2 * R_out + node;
+      *dst = add ? *dst + acc : acc;
+    }
   }
-  out[i] = add ? out[i] + acc : acc;
 }
 
 // ---------------------------------------------------------------- coarse
@@ -490,13 +616,43 @@ __global__ void k_interp(GeomDev g, ProbDev P, double t, long R, long S, double 
   }
 }
 
+// Source values rho f (d components) and g at every (time node b, cell,
+// quadrature point) of the finest level: src[((b * ncell + cell) * nq + qp) * 4 + c].
+__global__ void k_src_eval(GeomDev g, ProbDev P, LoadTables L, int q, const double *tnode, double t_prev, double tau,
+                           long ncell, double *__restrict__ src) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)q * ncell * L.nq) return;
+  const int qp = (int)(i % L.nq);
+  const long cell = (i / L.nq) % ncell;
+  const int b = (int)(i / ((long)L.nq * ncell));
+  const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
+  long t = cell;
+  double x[3];
+  for (int k = 0; k < 3; ++k) {
+    int c = 0;
+    if (k < g.dim) {
+      c = (int)(t % g.n[k]);
+      t /= g.n[k];
+    }
+    x[k] = g.lo[k] + g.h[k] * (c + L.qx[qp * 3 + k]);
+  }
+  double rf[3], gg;
+  dev_source(P, x, tb, L.lam[cell], L.mu[cell], L.kap[cell], rf, &gg);
+  double *o = src + i * 4;
+  o[0] = rf[0];
+  o[1] = rf[1];
+  o[2] = rf[2];
+  o[3] = gg;
+}
+
 // Slab right-hand side (Eq. 3.5 / Eq. 4.5):
 // rhs[b, m] = chi_b(-1) (S1 state)[m] + W_b * load_m(t_b), load = 0 on u-rows,
 // F = <rho f, psi> - <t_N, psi>_{Gamma_N} on v-rows, G = <g, xi> on p-rows.
-// Node-centric gather over the cells holding the node (deterministic).
+// Node-centric gather over the cells holding the node (deterministic), from
+// the source values precomputed by k_src_eval.
 __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double> tc, const double *chi,
                       const double *tnode, double t_prev, double tau, long R, long S,
-                      const double *__restrict__ ys, double *__restrict__ out) {
+                      const double *__restrict__ src, const double *__restrict__ ys, double *__restrict__ out) {
   const long ns = 2 * R + S;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)q * ns) return;
@@ -510,7 +666,7 @@ __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double
     const int deg = urow ? g.r : g.r - 1;
     const int *dims = urow ? g.udims : g.pdims;
     const long node = urow ? (m - R) / d : m - 2 * R;
-    const int comp = urow ? (int)((m - R) % d) : 0;
+    const int comp = urow ? (int)((m - R) % d) : 3;
     int a[3] = {0, 0, 0}, clo[3] = {0, 0, 0}, chi_[3] = {0, 0, 0};
     long t = node;
     for (int k = 0; k < d; ++k) {
@@ -525,6 +681,7 @@ __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double
     }
     const int nl = urow ? L.nlu : L.nlp;
     const double *phi = urow ? L.phiU : L.phiP;
+    const long ncell = (long)g.n[0] * g.n[1] * g.n[2];
     double load = 0.0;
     for (int cz = clo[2]; cz <= chi_[2]; ++cz)
       for (int cy = clo[1]; cy <= chi_[1]; ++cy)
@@ -536,14 +693,8 @@ __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double
             stride *= deg + 1;
           }
           const long cell = cx + (long)g.n[0] * (cy + (long)g.n[1] * cz);
-          const double lam = L.lam[cell], mu = L.mu[cell], kap = L.kap[cell];
-          for (int qq = 0; qq < L.nq; ++qq) {
-            double x[3];
-            for (int k = 0; k < 3; ++k) x[k] = g.lo[k] + g.h[k] * (cc[k] + L.qx[qq * 3 + k]);
-            double rf[3], gg;
-            dev_source(P, x, tb, lam, mu, kap, rf, &gg);
-            load += L.qw[qq] * (urow ? rf[comp] : gg) * phi[qq * nl + li];
-          }
+          const double *sv = src + (((long)b * ncell + cell) * L.nq) * 4 + comp;
+          for (int qq = 0; qq < L.nq; ++qq) load += L.qw[qq] * sv[qq * 4] * phi[qq * nl + li];
           // Neumann traction on the top face (pulse problem)
           if (urow && L.top_neumann && comp == d - 1 && cc[d - 1] == g.n[d - 1] - 1 &&
               a[d - 1] == deg * g.n[d - 1]) {
@@ -566,8 +717,9 @@ template <typename T>
 struct DLevel {
   long ns = 0, N = 0, R = 0, S = 0;
   long long nnz = 0;
-  int *rowptr = nullptr, *col = nullptr;
-  T *v1 = nullptr, *v2 = nullptr;
+  // node-block operator (see k_spmv_nb)
+  NodeBlockDev<T> nb{};
+  double nb_bytes = 0.0, nb_flops = 0.0;
   // patches
   long npatch = 0;
   int maxC = 0;
@@ -616,7 +768,7 @@ struct stfem_ctx {
          *y = nullptr, *hnorm = nullptr, *partial = nullptr, *status = nullptr;
   double *status_host = nullptr;
   // march buffers and load tables
-  double *rhs = nullptr, *xs = nullptr, *ys = nullptr, *chi = nullptr, *tnode = nullptr;
+  double *rhs = nullptr, *xs = nullptr, *ys = nullptr, *chi = nullptr, *tnode = nullptr, *src = nullptr;
   LoadTables lt{};
   std::vector<double> hist;
   std::vector<void *> allocs;
@@ -706,36 +858,166 @@ TimeCoef<T> time_coef(const stfem::Temporal &Tm, double tau) {
   return tc;
 }
 
-template <typename T, int Q>
-void launch_spmv_q(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
-                   int mode) {
-  constexpr int G = 8;
-  const long threads = L.ns * G;
-  k_spmv<T, Q, G><<<grid_for(threads, 256), 256, 0, s>>>(L.ns, L.rowptr, L.col, L.v1, L.v2, tc, x, rhs, y, mode);
+template <typename T, int Q, int D>
+void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+                    int mode) {
+  constexpr int G = 4;
+  const long threads = (L.nb.nu + L.nb.np) * G;
+  k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256), 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode);
 }
 
-// algorithmic bytes of one Kronecker SpMV: the matrix once, x and y (and rhs) once
+template <typename T, int Q>
+void launch_spmv_q(cudaStream_t s, int d, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs,
+                   T *y, int mode) {
+  if (d == 2)
+    launch_spmv_qd<T, Q, 2>(s, L, tc, x, rhs, y, mode);
+  else
+    launch_spmv_qd<T, Q, 3>(s, L, tc, x, rhs, y, mode);
+}
+
+// algorithmic bytes of one Kronecker SpMV: the node-block operator once, x and y
+// (and rhs) once
 template <typename T>
 double spmv_bytes(const DLevel<T> &L, int q, int mode) {
-  return (double)L.nnz * (4.0 + 2.0 * sizeof(T)) + (L.ns + 1) * 4.0 + (double)q * L.ns * sizeof(T) * (mode ? 3 : 2);
-}
-template <typename T>
-double spmv_flops(const DLevel<T> &L, int q) {
-  return 4.0 * L.nnz * q + 2.0 * L.ns * q * (q + 1);
+  return L.nb_bytes + (double)q * L.ns * sizeof(T) * (mode ? 3 : 2);
 }
 
 template <typename T>
 void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
                  int mode) {
-  Launch G_(h, STFEM_KCLASS_SPMV, spmv_bytes(L, tc.q, mode), spmv_flops(L, tc.q));
+  Launch G_(h, STFEM_KCLASS_SPMV, spmv_bytes(L, tc.q, mode), L.nb_flops * tc.q);
   cudaStream_t s = h->stream;
+  const int d = h->dim;
   switch (tc.q) {
-  case 1: launch_spmv_q<T, 1>(s, L, tc, x, rhs, y, mode); break;
-  case 2: launch_spmv_q<T, 2>(s, L, tc, x, rhs, y, mode); break;
-  case 3: launch_spmv_q<T, 3>(s, L, tc, x, rhs, y, mode); break;
-  case 4: launch_spmv_q<T, 4>(s, L, tc, x, rhs, y, mode); break;
-  default: launch_spmv_q<T, 5>(s, L, tc, x, rhs, y, mode); break;
+  case 1: launch_spmv_q<T, 1>(s, d, L, tc, x, rhs, y, mode); break;
+  case 2: launch_spmv_q<T, 2>(s, d, L, tc, x, rhs, y, mode); break;
+  case 3: launch_spmv_q<T, 3>(s, d, L, tc, x, rhs, y, mode); break;
+  case 4: launch_spmv_q<T, 4>(s, d, L, tc, x, rhs, y, mode); break;
+  default: launch_spmv_q<T, 5>(s, d, L, tc, x, rhs, y, mode); break;
   }
+}
+
+// Node-block arrays of a level, decoded from the spatial system CSR (whose
+// blocks have the structure of Eq. 4.7); checks that structure.
+struct NodeBlockHost {
+  long nu = 0, np = 0;
+  std::vector<int> uu_ptr, uu_col, up_ptr, up_col, pu_ptr, pu_col, pp_ptr, pp_col;
+  std::vector<double> uu_m, uu_k, up_c, pu_c, pp_m, pp_b;
+};
+
+int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *err) {
+  NodeBlockHost &H = *out;
+  const long R = L.R, S = L.S, nu = R / d, np = S;
+  H.nu = nu;
+  H.np = np;
+  H.uu_ptr.assign(nu + 1, 0);
+  H.up_ptr.assign(nu + 1, 0);
+  H.pu_ptr.assign(np + 1, 0);
+  H.pp_ptr.assign(np + 1, 0);
+  double scale = 0.0;
+  for (double v : L.v1) scale = std::max(scale, std::fabs(v));
+  for (double v : L.v2) scale = std::max(scale, std::fabs(v));
+  const double tol = 1e-12 * scale;
+  std::vector<int> pos(nu, -1);
+  for (long I = 0; I < nu; ++I) {
+    // u-equation row (I, 0): the U block holds rho M_IJ in v1
+    const long ru = I * d;
+    const int first = (int)H.uu_col.size();
+    for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
+      const long c = L.col[e];
+      if (c >= R && c < 2 * R && (c - R) % d == 0) {
+        pos[(c - R) / d] = (int)H.uu_col.size() - first;
+        H.uu_col.push_back((int)((c - R) / d));
+        H.uu_m.push_back(L.v1[e]);
+      }
+    }
+    const int cnt = (int)H.uu_col.size() - first;
+    H.uu_ptr[I + 1] = (int)H.uu_col.size();
+    H.uu_k.resize(H.uu_col.size() * d * d, 0.0);
+    // v-equation rows (I, c): U block -> K[c][c'] in v2, P block -> C^T in v2
+    std::vector<int> pcols;
+    for (int c = 0; c < d; ++c) {
+      const long rv = R + I * d + c;
+      int pk = 0;
+      for (int e = L.rowptr[rv]; e < L.rowptr[rv + 1]; ++e) {
+        const long col = L.col[e];
+        if (col < R) {
+          const long J = col / d;
+          if (col % d != c || pos[J] < 0 || std::fabs(L.v1[e] - H.uu_m[first + pos[J]]) > tol ||
+              std::fabs(L.v2[e]) > tol) {
+            *err = "unexpected structure in the v-equation rows";
+            return STFEM_ERR_STATE;
+          }
+        } else if (col < 2 * R) {
+          const long J = (col - R) / d;
+          const int cp = (int)((col - R) % d);
+          if (pos[J] < 0 || std::fabs(L.v1[e]) > tol) {
+            *err = "unexpected structure in the elasticity block";
+            return STFEM_ERR_STATE;
+          }
+          H.uu_k[((size_t)first + pos[J]) * d * d + c * d + cp] = L.v2[e];
+        } else {
+          if (c == 0) {
+            pcols.push_back((int)(col - 2 * R));
+            for (int cc = 0; cc < d; ++cc) H.up_c.push_back(0.0);
+          }
+          if (pk >= (int)pcols.size() || pcols[pk] != (int)(col - 2 * R)) {
+            *err = "unexpected pressure coupling pattern";
+            return STFEM_ERR_STATE;
+          }
+          H.up_c[(H.up_col.size() + pk) * d + c] = L.v2[e];
+          ++pk;
+        }
+      }
+    }
+    for (int sc : pcols) H.up_col.push_back(sc);
+    H.up_ptr[I + 1] = (int)H.up_col.size();
+    // the u-equation's V block must be -rho M (times W)
+    for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
+      const long c = L.col[e];
+      if (c < R) {
+        const long J = c / d;
+        if (pos[J] < 0 || std::fabs(L.v2[e] + H.uu_m[first + pos[J]]) > tol || std::fabs(L.v1[e]) > tol) {
+          *err = "unexpected structure in the u-equation rows";
+          return STFEM_ERR_STATE;
+        }
+      }
+    }
+    for (int t = first; t < first + cnt; ++t) pos[H.uu_col[t]] = -1;
+  }
+  for (long sI = 0; sI < np; ++sI) {
+    const long rp = 2 * R + sI;
+    std::vector<double> cn;
+    std::vector<int> jl;
+    for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
+      const long col = L.col[e];
+      if (col < R) {
+        const long J = col / d;
+        const int c = (int)(col % d);
+        if (jl.empty() || jl.back() != (int)J) {
+          jl.push_back((int)J);
+          for (int cc = 0; cc < d; ++cc) cn.push_back(0.0);
+        }
+        cn[(jl.size() - 1) * d + c] = L.v2[e];
+        if (std::fabs(L.v1[e]) > tol) {
+          *err = "unexpected structure in the p-equation rows";
+          return STFEM_ERR_STATE;
+        }
+      } else if (col >= 2 * R) {
+        H.pp_col.push_back((int)(col - 2 * R));
+        H.pp_m.push_back(L.v1[e]);
+        H.pp_b.push_back(L.v2[e]);
+      } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
+        *err = "p-equation couples to U";
+        return STFEM_ERR_STATE;
+      }
+    }
+    for (size_t t = 0; t < jl.size(); ++t) H.pu_col.push_back(jl[t]);
+    H.pu_c.insert(H.pu_c.end(), cn.begin(), cn.end());
+    H.pu_ptr[sI + 1] = (int)H.pu_col.size();
+    H.pp_ptr[sI + 1] = (int)H.pp_col.size();
+  }
+  return 0;
 }
 
 template <typename T>
@@ -744,11 +1026,37 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   D.N = L.ns * q;
   D.R = L.R;
   D.S = L.S;
+  NodeBlockHost H;
+  std::string err;
+  if (node_block(L, h->dim, &H, &err) < 0) {
+    h->err = err;
+    return STFEM_ERR_STATE;
+  }
+  const int d = h->dim;
+  NodeBlockDev<T> &nb = D.nb;
+  nb.nu = H.nu;
+  nb.np = H.np;
+  int *ip;
+  T *tp;
+  CKR(upload(h, &ip, H.uu_ptr)); nb.uu_ptr = ip;
+  CKR(upload(h, &ip, H.uu_col)); nb.uu_col = ip;
+  CKR(upload(h, &tp, H.uu_m)); nb.uu_m = tp;
+  CKR(upload(h, &tp, H.uu_k)); nb.uu_k = tp;
+  CKR(upload(h, &ip, H.up_ptr)); nb.up_ptr = ip;
+  CKR(upload(h, &ip, H.up_col)); nb.up_col = ip;
+  CKR(upload(h, &tp, H.up_c)); nb.up_c = tp;
+  CKR(upload(h, &ip, H.pu_ptr)); nb.pu_ptr = ip;
+  CKR(upload(h, &ip, H.pu_col)); nb.pu_col = ip;
+  CKR(upload(h, &tp, H.pu_c)); nb.pu_c = tp;
+  CKR(upload(h, &ip, H.pp_ptr)); nb.pp_ptr = ip;
+  CKR(upload(h, &ip, H.pp_col)); nb.pp_col = ip;
+  CKR(upload(h, &tp, H.pp_m)); nb.pp_m = tp;
+  CKR(upload(h, &tp, H.pp_b)); nb.pp_b = tp;
+  const double nuu = H.uu_col.size(), nup = H.up_col.size(), npu = H.pu_col.size(), npp = H.pp_col.size();
+  D.nb_bytes = (nuu * (1 + d * d) + nup * d + npu * d + npp * 2) * sizeof(T) + (nuu + nup + npu + npp) * 4.0 +
+               (2.0 * H.nu + 2.0 * H.np + 4) * 4.0;
+  D.nb_flops = 2.0 * (nuu * (2 * d + d * d) + nup * d + npu * d + npp * 2);
   D.nnz = (long long)L.col.size();
-  CKR(upload(h, &D.rowptr, L.rowptr));
-  CKR(upload(h, &D.col, L.col));
-  CKR(upload(h, &D.v1, L.v1));
-  CKR(upload(h, &D.v2, L.v2));
   CKR(dalloc(h, &D.b, D.N));
   CKR(dalloc(h, &D.d, D.N));
   CKR(dalloc(h, &D.r, D.N));
@@ -833,6 +1141,29 @@ std::vector<DLevel<float>> &levels<float>(stfem_h h) {
   return h->L32;
 }
 
+// Launch shape of the patch apply: RT row threads cover the largest patch
+// (VEC rows each); J column groups per patch when the level has too few
+// patches to keep the 152 SMs streaming (about 2^18 resident threads).
+template <typename T>
+void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res) {
+  constexpr int VEC = Vec16<T>::n;
+  int RT = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
+  RT = std::min(std::max(RT, 32), 1024);
+  int J = 1;
+  const double target = 152.0 * 1536.0;
+  while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
+  const size_t smem = (size_t)L.maxC * sizeof(T) + (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
+  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
+  const unsigned grid = (unsigned)L.npatch;
+  cudaStream_t s = h->stream;
+  switch (J) {
+  case 1: k_patch_apply<T, 1><<<grid, RT, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
+  case 2: k_patch_apply<T, 2><<<grid, RT * 2, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
+  case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
+  default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
+  }
+}
+
 template <typename T>
 void smooth(stfem_h h, int l, int nsw, bool zero_init) {
   DLevel<T> &L = levels<T>(h)[l];
@@ -845,14 +1176,7 @@ void smooth(stfem_h h, int l, int nsw, bool zero_init) {
       launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1);
       res = L.r;
     }
-    constexpr int VEC = Vec16<T>::n;
-    int threads = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
-    threads = std::min(std::max(threads, 32), 512);
-    {
-      Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
-      k_patch_apply<T><<<(unsigned)L.npatch, threads, L.maxC * sizeof(T), s>>>(L.psize, L.pdoff, L.pdofs, L.pioff,
-                                                                                L.pld, L.pinv, res, L.ybuf);
-    }
+    launch_patch_apply<T>(h, L, res);
     {
       Launch G_(h, STFEM_KCLASS_UPDATE,
                 (double)L.N * (4.0 + 3.0 * sizeof(T)) + (double)L.sumC * (4.0 + sizeof(T)), (double)L.sumC + 2.0 * L.N);
@@ -867,8 +1191,13 @@ void restrict_to(stfem_h h, int l, const T *rf, T *bc) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
-  k_transfer<T><<<grid_for(C.N, 256), 256, 0, h->stream>>>(C.N, C.ns, C.R, F.ns, F.R, h->dim, F.Ru_p, F.Ru_c, F.Ru_v,
-                                                            F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
+  const long nu = C.R / h->dim, np = C.S;
+  if (h->dim == 2)
+    k_transfer<T, 2><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+                                                                     F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
+  else
+    k_transfer<T, 3><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+                                                                     F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
 }
 
 template <typename T>
@@ -876,8 +1205,13 @@ void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
-  k_transfer<T><<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.N, F.ns, F.R, C.ns, C.R, h->dim, F.Pu_p, F.Pu_c, F.Pu_v,
-                                                            F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
+  const long nu = F.R / h->dim, np = F.S;
+  if (h->dim == 2)
+    k_transfer<T, 2><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+                                                                     F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
+  else
+    k_transfer<T, 3><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+                                                                     F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
 }
 
 template <typename T>
@@ -1306,6 +1640,7 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
   if ((rc = dalloc(h, &h->w, N)) < 0 || (rc = dalloc(h, &h->rvec, N)) < 0 || (rc = dalloc(h, &h->zt, N)) < 0 ||
       (rc = dalloc(h, &h->rhs, N)) < 0 || (rc = dalloc(h, &h->xs, N)) < 0 ||
       (rc = dalloc(h, &h->ys, F.ns)) < 0 || (rc = dalloc(h, &h->hn2, 1)) < 0 ||
+      (rc = dalloc(h, &h->src, (size_t)h->q * F.box.ncell * h->lt.nq * 4)) < 0 ||
       (rc = dalloc(h, &h->hnorm, 1)) < 0 || (rc = dalloc(h, &h->status, 4)) < 0 ||
       (rc = dalloc(h, &h->partial, (size_t)DOT_BLOCKS * (MAXM + 1))) < 0 ||
       (rc = upload(h, &h->chi, h->T.chi_m1)) < 0 || (rc = upload(h, &h->tnode, h->T.t)) < 0)
@@ -1487,9 +1822,16 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) 
   launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0); // S1 * state
   const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
   const double t_prev = h->t0 + slab * h->tau;
-  Launch G_(h, STFEM_KCLASS_RHS, (double)F.N * 16.0, 0.0);
+  const long ncell = HF.box.ncell;
+  const long nsrc = (long)h->q * ncell * h->lt.nq;
+  if (h->prob.id != STFEM_PROBLEM_NONE) {
+    Launch G_(h, STFEM_KCLASS_RHS, (double)nsrc * 32.0, 0.0);
+    k_src_eval<<<grid_for(nsrc, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, h->tnode, t_prev, h->tau,
+                                                           ncell, h->src);
+  }
+  Launch G_(h, STFEM_KCLASS_RHS, (double)F.N * 16.0 + (double)nsrc * 32.0, 0.0);
   k_rhs<<<grid_for(F.N, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode, t_prev,
-                                                   h->tau, HF.R, HF.S, h->ys, rhs);
+                                                   h->tau, HF.R, HF.S, h->src, h->ys, rhs);
   CK(cudaGetLastError());
   return 0;
 }
