@@ -227,6 +227,34 @@ int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, d
 /* Number of kernels the handle has launched since it was created. */
 int stfem_launch_count(stfem_h h, long long *n);
 
+/* ---- Allocation-free smoothing ----
+ * No counterpart in the paper: an interface for callers that must not
+ * allocate device memory at call time, e.g. code that runs while a CUDA stream
+ * is being captured into a graph (cudaMalloc is not allowed there), solvers
+ * embedded in a host application that fixes its device-memory budget after
+ * start-up, or latency-critical loops where an allocation would stall.
+ *
+ * stfem_smooth_noalloc does exactly what stfem_smooth does (n_sweeps averaged
+ * Vanka sweeps of Algorithm 4.1 on level l >= 1, in the level's precision),
+ * but takes its scratch memory (the level-precision copies of b and d, the
+ * residual and the patch results) from one static device array of
+ * STFEM_NOALLOC_SCRATCH_BYTES bytes that is part of the library (every GPU
+ * that loads the library holds it until the process exits).  It calls no
+ * cudaMalloc or cudaFree.  The caller passes b and d (device, FP64, n_slab of
+ * the level) as for stfem_smooth; the handle's setup data are only read.
+ *
+ * Needs (3 n_slab + sum of patch sizes) * (4 in STFEM_MIXED, 8 in STFEM_FP64)
+ * bytes of scratch; larger levels are rejected with STFEM_ERR_ARG and a
+ * message naming the sizes.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The current device must be the one
+ * the handle was set up on.  Every call, from every handle, shares the one
+ * array and it keeps the last call's contents: calls that may overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Profiling (stfem_profile) must be off, since it creates events. */
+#define STFEM_NOALLOC_SCRATCH_BYTES (16u << 20)
+int stfem_smooth_noalloc(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init);
+
 /* ---- Host-side inspection of the setup (no GPU needed; for tests) ----
  * These rebuild the hierarchy on the host from the same arguments as
  * stfem_setup and return what the GPU path would upload.  Two-call pattern:

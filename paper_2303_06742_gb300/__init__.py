@@ -74,6 +74,7 @@ def _load():
         "stfem_level_info": [P, I, pLL, pLL, pLL, pLL],
         "stfem_apply": [P, I, P, P],
         "stfem_smooth": [P, I, P, P, I, I],
+        "stfem_smooth_noalloc": [P, I, P, P, I, I],
         "stfem_restrict": [P, I, P, P],
         "stfem_prolongate_add": [P, I, P, P],
         "stfem_coarse_solve": [P, P, P],
@@ -258,6 +259,10 @@ class Solver:
 
     def smooth(self, level, b, d, n_sweeps=1, zero_init=True):
         self._check(lib.stfem_smooth(self.h, level, _ptr(b), _ptr(d), n_sweeps, int(bool(zero_init))))
+
+    def smooth_noalloc(self, level, b, d, n_sweeps=1, zero_init=True):
+        """stfem_smooth_noalloc: the same sweeps with the library's static scratch array."""
+        self._check(lib.stfem_smooth_noalloc(self.h, level, _ptr(b), _ptr(d), n_sweeps, int(bool(zero_init))))
 
     def restrict(self, level, r_fine, b_coarse):
         self._check(lib.stfem_restrict(self.h, level, _ptr(r_fine), _ptr(b_coarse)))

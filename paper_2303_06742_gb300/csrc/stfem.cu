@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -744,6 +745,7 @@ struct DLevel {
 struct stfem_ctx {
   std::string err;
   cudaStream_t stream = 0;
+  int device = 0;
   int dim = 2, r = 2, k = 1, q = 2, nlev = 1;
   double tau = 0.01, t0 = 0.0;
   int problem = 0;
@@ -1580,6 +1582,106 @@ int fail_setup(stfem_h h, int rc) {
 
 } // namespace
 
+// ---------------------------------------------------------------- allocation-free smoothing
+// Scratch of stfem_smooth_noalloc: one static array per device that loads the
+// library.  Host code must not use the symbol as an address; its device
+// address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STFEM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up on the
+// first call per device).
+int noalloc_scratch(stfem_h h, unsigned char **out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != h->device) {
+    h->err = "stfem_smooth_noalloc: the current device is not the handle's device";
+    return STFEM_ERR_STATE;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    h->err = "stfem_smooth_noalloc: device index out of range";
+    return STFEM_ERR_STATE;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_noalloc_ptr[dev]);
+  return 0;
+}
+
+// The patch apply of launch_patch_apply, writing the patch results to y.
+template <typename T>
+void launch_patch_apply_into(stfem_h h, DLevel<T> &L, const T *res, T *y) {
+  constexpr int VEC = Vec16<T>::n;
+  int RT = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
+  RT = std::min(std::max(RT, 32), 1024);
+  int J = 1;
+  const double target = 152.0 * 1536.0;
+  while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
+  const size_t smem = (size_t)L.maxC * sizeof(T) + (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
+  const unsigned grid = (unsigned)L.npatch;
+  cudaStream_t s = h->stream;
+  switch (J) {
+  case 1: k_patch_apply<T, 1><<<grid, RT, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  case 2: k_patch_apply<T, 2><<<grid, RT * 2, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  }
+}
+
+template <typename T>
+int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init) {
+  DLevel<T> &L = levels<T>(h)[level];
+  const size_t need = (3 * (size_t)L.N + (size_t)L.sumC) * sizeof(T);
+  if (need > STFEM_NOALLOC_SCRATCH_BYTES) {
+    h->err = "stfem_smooth_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
+             " bytes of scratch, more than the " + std::to_string((size_t)STFEM_NOALLOC_SCRATCH_BYTES) +
+             "-byte static array";
+    return STFEM_ERR_ARG;
+  }
+  unsigned char *base = nullptr;
+  CKR(noalloc_scratch(h, &base));
+  // layout: b_T | d_T | r_T | y_T (each 256-byte aligned)
+  auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t vb = align((size_t)L.N * sizeof(T));
+  if (3 * vb + (size_t)L.sumC * sizeof(T) > STFEM_NOALLOC_SCRATCH_BYTES) {
+    h->err = "stfem_smooth_noalloc: level does not fit the static array after alignment";
+    return STFEM_ERR_ARG;
+  }
+  T *bT = reinterpret_cast<T *>(base);
+  T *dT = reinterpret_cast<T *>(base + vb);
+  T *rT = reinterpret_cast<T *>(base + 2 * vb);
+  T *yT = reinterpret_cast<T *>(base + 3 * vb);
+  const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
+  cudaStream_t s = h->stream;
+  k_convert<double, T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, b, bT);
+  if (!zero_init) k_convert<double, T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d, dT);
+  for (int it = 0; it < nsw; ++it) {
+    const bool zero = zero_init && it == 0;
+    const T *res = bT;
+    if (!zero) {
+      launch_spmv<T>(h, L, tc, dT, bT, rT, 1);
+      res = rT;
+    }
+    launch_patch_apply_into<T>(h, L, res, yT);
+    k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0);
+  }
+  k_convert<T, double><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, dT, d);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+} // namespace
+
 // ============================================================ C ABI
 extern "C" {
 
@@ -1591,6 +1693,7 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
   }
   *out = nullptr;
   stfem_h h = new stfem_ctx();
+  cudaGetDevice(&h->device);
   {
     int rc0 = stfem::build_hierarchy(mesh, deg, mat, bcs, tau, &h->hl, &h->Pu, &h->Pp, &h->err);
     if (rc0 < 0) return fail_setup(h, rc0);
@@ -1745,6 +1848,22 @@ int stfem_smooth(stfem_h h, int level, const double *b, double *d, int n_sweeps,
   }
   if (h->precision == STFEM_MIXED) return smooth_t<float>(h, level, b, d, n_sweeps, zero_init);
   return smooth_t<double>(h, level, b, d, n_sweeps, zero_init);
+}
+
+int stfem_smooth_noalloc(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init) {
+  if (!h || !b || !d || n_sweeps < 1) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  CKR(check_level(h, level, false));
+  if (level < 1) {
+    h->err = "smoothing is defined on levels >= 1";
+    return STFEM_ERR_ARG;
+  }
+  if (h->prof) {
+    h->err = "stfem_smooth_noalloc: turn profiling off first (it creates CUDA events)";
+    return STFEM_ERR_STATE;
+  }
+  if (h->precision == STFEM_MIXED) return smooth_noalloc_t<float>(h, level, b, d, n_sweeps, zero_init);
+  return smooth_noalloc_t<double>(h, level, b, d, n_sweeps, zero_init);
 }
 
 int stfem_restrict(stfem_h h, int level, const double *r_fine, double *b_coarse) {
