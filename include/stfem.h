@@ -111,13 +111,28 @@ typedef struct {
   double t0;
 } stfem_bcs;
 
+/* Storage of the patch inverses A_P^{-1} (Eq. 4.11):
+ * DENSE: the explicit C_P x C_P inverse of each patch matrix.
+ * TIME_DIAGONAL: A_P = Dt (x) S1_P + W (x) S2_P (Eq. 4.7 restricted to the
+ * patch) is inverted through the eigen-decomposition W^{-1} Dt = V L V^{-1}:
+ * A_P^{-1} = (V (x) I) blockdiag((l_a S1_P + S2_P)^{-1}) (V^{-1} W^{-1} (x) I),
+ * one real block per real eigenvalue and one complex block per conjugate
+ * pair: q C_s^2 stored reals instead of q^2 C_s^2 (C_s = C_P / q).  The same
+ * operator up to rounding.  AUTO: DENSE for STFEM_FP64, TIME_DIAGONAL for
+ * STFEM_MIXED. */
+#define STFEM_PATCH_AUTO 0
+#define STFEM_PATCH_DENSE 1
+#define STFEM_PATCH_TIME_DIAGONAL 2
+
 /* GMG parameters (Sec. 4): damping omega of the Vanka operator (Eq. 4.11;
  * the paper uses 0.7), n_sweeps pre- and post-smoothing steps of
- * Algorithm 4.1 per level, precision STFEM_FP64 or STFEM_MIXED. */
+ * Algorithm 4.1 per level, precision STFEM_FP64 or STFEM_MIXED, patch_form
+ * STFEM_PATCH_*. */
 typedef struct {
   double omega;
   int n_sweeps;
   int precision;
+  int patch_form;
 } stfem_gmg_params;
 
 /* Builds the mesh hierarchy, spatial matrices of every level (Eqs. 3.2-3.3),

@@ -25,6 +25,7 @@ PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPER
 FP64, MIXED = 0, 1
 HF_MEASURE, HF_LENGTH = 0, 1
 COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
+PATCH_AUTO, PATCH_DENSE, PATCH_TIME_DIAGONAL = 0, 1, 2
 KCLASSES = ["spmv", "patch_apply", "update", "transfer", "coarse", "blas1", "rhs", "other"]
 
 
@@ -56,7 +57,7 @@ class BCs(C.Structure):
 
 
 class GmgParams(C.Structure):
-    _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int)]
+    _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int), ("patch_form", C.c_int)]
 
 
 def _load():
@@ -213,7 +214,7 @@ def host_temporal(k):
 class Solver:
     """Handle of one problem instance on the current CUDA device."""
 
-    def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None):
+    def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None, patch_form=PATCH_AUTO):
         self.prob = prob
         h = C.c_void_p()
         rc = lib.stfem_setup(*prob.args(), C.byref(h))
@@ -222,7 +223,7 @@ class Solver:
         self.h = h
         if stream is not None:
             self.set_stream(stream)
-        self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision))))
+        self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision, patch_form))))
         self.precision = precision
         n_slab, n_state = C.c_longlong(), C.c_longlong()
         self._check(lib.stfem_level_info(self.h, -1, C.byref(n_slab), C.byref(n_state), None, None))

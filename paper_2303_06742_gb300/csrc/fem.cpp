@@ -20,6 +20,7 @@
 #include <thread>
 #include <atomic>
 #include <array>
+#include <complex>
 
 namespace stfem {
 
@@ -906,6 +907,191 @@ bool invert(double *a, int n) {
   return true;
 }
 
+// Gauss-Jordan inverse with partial pivoting for complex row-major matrices.
+static bool invert_complex(std::complex<double> *a, int n) {
+  std::vector<int> piv(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::abs(a[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::abs(a[(size_t)i * n + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+    std::complex<double> *rk = a + (size_t)k * n;
+    const std::complex<double> inv = 1.0 / rk[k];
+    rk[k] = 1.0;
+    for (int j = 0; j < n; ++j) rk[j] *= inv;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      std::complex<double> *ri = a + (size_t)i * n;
+      const std::complex<double> f = ri[k];
+      if (f == 0.0) continue;
+      ri[k] = 0.0;
+      for (int j = 0; j < n; ++j) ri[j] -= f * rk[j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k)
+      for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + k], a[(size_t)i * n + piv[k]]);
+  return true;
+}
+
+bool time_diag(const Temporal &Tm, double tau, TimeDiag *out, std::string *err) {
+  typedef std::complex<double> cd;
+  const int q = Tm.q;
+  // T = W^{-1} Dt
+  std::vector<double> A(q * q);
+  for (int b = 0; b < q; ++b)
+    for (int a = 0; a < q; ++a) A[b * q + a] = Tm.Dt[b * q + a] / (0.5 * tau * Tm.w[b]);
+  // characteristic polynomial (Faddeev-LeVerrier): p(x) = x^q + c[q-1] x^{q-1} + ... + c[0]
+  std::vector<double> c(q + 1, 0.0), M(q * q, 0.0), AM(q * q);
+  c[q] = 1.0;
+  for (int k = 1; k <= q; ++k) {
+    // M_k = A M_{k-1} + c_{q-k+1} I ; c_{q-k} = -tr(A M_k) / k
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        double sacc = 0.0;
+        for (int l = 0; l < q; ++l) sacc += A[i * q + l] * M[l * q + j];
+        AM[i * q + j] = sacc;
+      }
+    for (int i = 0; i < q * q; ++i) M[i] = AM[i];
+    for (int i = 0; i < q; ++i) M[i * q + i] += c[q - k + 1];
+    double tr = 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int l = 0; l < q; ++l) tr += A[i * q + l] * M[l * q + i];
+    c[q - k] = -tr / k;
+  }
+  // roots by Durand-Kerner (Weierstrass) iteration
+  auto poly = [&](cd x) {
+    cd v = 1.0;
+    for (int k = q - 1; k >= 0; --k) v = v * x + c[k];
+    return v;
+  };
+  double rad = 0.0;
+  for (int k = 0; k < q; ++k) rad = std::max(rad, std::abs(c[k]));
+  rad = 1.0 + rad;
+  std::vector<cd> z(q);
+  for (int i = 0; i < q; ++i) z[i] = std::polar(0.5 * rad, 2.0 * M_PI * i / q + 0.4);
+  for (int it = 0; it < 2000; ++it) {
+    double delta = 0.0;
+    for (int i = 0; i < q; ++i) {
+      cd den = 1.0;
+      for (int j = 0; j < q; ++j)
+        if (j != i) den *= (z[i] - z[j]);
+      const cd dz = poly(z[i]) / den;
+      z[i] -= dz;
+      delta = std::max(delta, std::abs(dz) / std::max(1.0, std::abs(z[i])));
+    }
+    if (delta < 1e-15) break;
+  }
+  // classify: real slots, then one member (Im > 0) of each conjugate pair
+  std::vector<cd> slots;
+  int nr = 0, nc = 0;
+  std::vector<bool> used(q, false);
+  for (int i = 0; i < q; ++i)
+    if (std::fabs(z[i].imag()) <= 1e-9 * std::max(1.0, std::abs(z[i]))) {
+      slots.push_back(cd(z[i].real(), 0.0));
+      used[i] = true;
+      ++nr;
+    }
+  for (int i = 0; i < q; ++i)
+    if (!used[i] && z[i].imag() > 0) {
+      slots.push_back(z[i]);
+      ++nc;
+    }
+  if (nr + 2 * nc != q) {
+    *err = "time matrix eigenvalues are not real or conjugate pairs";
+    return false;
+  }
+  // eigenvectors by inverse iteration with a perturbed shift
+  std::vector<cd> Vf(q * q); // full V, columns: slots then conjugates of complex slots
+  std::vector<cd> lamf(q);
+  int col = 0;
+  auto eigvec = [&](cd lam, std::vector<cd> &v) {
+    std::vector<cd> B(q * q);
+    const cd mu = lam * (1.0 + 1e-11) + cd(1e-13, 0.0);
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) B[i * q + j] = A[i * q + j] - (i == j ? mu : 0.0);
+    if (!invert_complex(B.data(), q)) return false;
+    v.assign(q, cd(1.0, 0.3));
+    for (int it = 0; it < 3; ++it) {
+      std::vector<cd> w(q, 0.0);
+      for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) w[i] += B[i * q + j] * v[j];
+      // normalise: largest component = 1
+      int im = 0;
+      for (int i = 1; i < q; ++i)
+        if (std::abs(w[i]) > std::abs(w[im])) im = i;
+      const cd s0 = w[im];
+      for (int i = 0; i < q; ++i) v[i] = w[i] / s0;
+    }
+    return true;
+  };
+  for (int sidx = 0; sidx < nr + nc; ++sidx) {
+    std::vector<cd> v;
+    if (!eigvec(slots[sidx], v)) {
+      *err = "eigenvector iteration failed";
+      return false;
+    }
+    if (sidx < nr)
+      for (auto &x : v) x = cd(x.real(), 0.0);
+    for (int i = 0; i < q; ++i) Vf[i * q + col] = v[i];
+    lamf[col] = slots[sidx];
+    ++col;
+  }
+  for (int sidx = nr; sidx < nr + nc; ++sidx) {
+    for (int i = 0; i < q; ++i) Vf[i * q + col] = std::conj(Vf[i * q + sidx]);
+    lamf[col] = std::conj(slots[sidx]);
+    ++col;
+  }
+  std::vector<cd> Vi(Vf);
+  if (!invert_complex(Vi.data(), q)) {
+    *err = "eigenvector matrix is singular";
+    return false;
+  }
+  // check V diag(lam) V^{-1} = T
+  double e = 0.0, sc = 0.0;
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      cd sacc = 0.0;
+      for (int l = 0; l < q; ++l) sacc += Vf[i * q + l] * lamf[l] * Vi[l * q + j];
+      e = std::max(e, std::abs(sacc - A[i * q + j]));
+      sc = std::max(sc, std::fabs(A[i * q + j]));
+    }
+  if (e > 1e-10 * sc) {
+    *err = "time matrix is not diagonalisable to working accuracy";
+    return false;
+  }
+  TimeDiag &D = *out;
+  D.q = q;
+  D.nr = nr;
+  D.nc = nc;
+  const int ns = nr + nc;
+  D.lam.resize(2 * ns);
+  D.Vmat.resize(2 * q * ns);
+  D.Umat.resize(2 * ns * q);
+  for (int a = 0; a < ns; ++a) {
+    D.lam[2 * a] = lamf[a].real();
+    D.lam[2 * a + 1] = lamf[a].imag();
+    for (int b = 0; b < q; ++b) {
+      D.Vmat[2 * (b * ns + a)] = Vf[b * q + a].real();
+      D.Vmat[2 * (b * ns + a) + 1] = Vf[b * q + a].imag();
+      // U = V^{-1} W^{-1}
+      const cd u = Vi[a * q + b] / (0.5 * tau * Tm.w[b]);
+      D.Umat[2 * (a * q + b)] = u.real();
+      D.Umat[2 * (a * q + b) + 1] = u.imag();
+    }
+  }
+  return true;
+}
+
 static void patch_axis(int v, int m, int ncell, int *lo, int *hi) {
   int c0 = std::max(v - 1, 0), c1 = std::min(v, ncell - 1);
   int alo = m * c0, ahi = m * (c1 + 1);
@@ -914,7 +1100,7 @@ static void patch_axis(int v, int m, int ncell, int *lo, int *hi) {
 }
 
 int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out, std::string *err,
-                  bool invert_them) {
+                  bool invert_them, const TimeDiag *td) {
   const Box &b = L.box;
   const int d = b.dim, q = T.q;
   int vdims[3] = {1, 1, 1};
@@ -962,11 +1148,21 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
   }
   P.dof_off[0] = 0;
   P.inv_off[0] = 0;
+  P.form = td ? 1 : 0;
+  P.cs.resize(nv);
   for (long p = 0; p < nv; ++p) {
     int C = P.size[p];
-    P.ld[p] = (C + vec - 1) / vec * vec;
+    const int Cs = C / q;
+    P.cs[p] = Cs;
     P.dof_off[p + 1] = P.dof_off[p] + C;
-    P.inv_off[p + 1] = P.inv_off[p] + (long long)C * P.ld[p];
+    if (td) {
+      const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+      P.ld[p] = ldR;
+      P.inv_off[p + 1] = P.inv_off[p] + (long long)td->nr * Cs * ldR + (long long)td->nc * Cs * ldC;
+    } else {
+      P.ld[p] = (C + vec - 1) / vec * vec;
+      P.inv_off[p + 1] = P.inv_off[p] + (long long)C * P.ld[p];
+    }
   }
   P.dofs.resize(P.dof_off[nv]);
   if (invert_them) P.inv.assign(P.inv_off[nv], 0.0);
@@ -1001,6 +1197,40 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
         }
       }
       for (int m = 0; m < Cs; ++m) loc[sp[m]] = -1;
+      if (td) {
+        double *dst = &P.inv[P.inv_off[p]];
+        const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+        bool ok = true;
+        for (int a = 0; a < td->nr && ok; ++a) {
+          const double lam = td->lam[2 * a];
+          A.assign((size_t)Cs * Cs, 0.0);
+          for (size_t i = 0; i < (size_t)Cs * Cs; ++i) A[i] = lam * S1[i] + S2[i];
+          if (!invert(A.data(), Cs)) {
+            ok = false;
+            break;
+          }
+          for (int i = 0; i < Cs; ++i)
+            for (int j = 0; j < Cs; ++j) dst[(size_t)j * ldR + i] = A[(size_t)i * Cs + j];
+          dst += (size_t)Cs * ldR;
+        }
+        for (int a = td->nr; a < td->nr + td->nc && ok; ++a) {
+          const std::complex<double> lam(td->lam[2 * a], td->lam[2 * a + 1]);
+          std::vector<std::complex<double>> Z((size_t)Cs * Cs);
+          for (size_t i = 0; i < (size_t)Cs * Cs; ++i) Z[i] = lam * S1[i] + S2[i];
+          if (!invert_complex(Z.data(), Cs)) {
+            ok = false;
+            break;
+          }
+          for (int i = 0; i < Cs; ++i)
+            for (int j = 0; j < Cs; ++j) {
+              dst[(size_t)j * ldC + 2 * i] = Z[(size_t)i * Cs + j].real();
+              dst[(size_t)j * ldC + 2 * i + 1] = Z[(size_t)i * Cs + j].imag();
+            }
+          dst += (size_t)Cs * ldC;
+        }
+        if (!ok) bad.store(p);
+        continue;
+      }
       A.assign((size_t)C * C, 0.0);
       for (int bb = 0; bb < q; ++bb)
         for (int aa = 0; aa < q; ++aa) {

@@ -90,8 +90,28 @@ CSR transpose(const CSR &a);
 // `coarse` (whose sizes must be set).
 void galerkin(const Level &fine, const CSR &Pu, const CSR &Pp, Level *coarse);
 
+// Eigen-decomposition of W^{-1} Dt = V diag(lam) V^{-1} used by the
+// time-diagonal form of the patch inverses.  Slots: the nr real eigenvalues
+// first, then one member (Im > 0) of each of the nc complex-conjugate pairs.
+// U = V^{-1} W^{-1}; rows/columns are given for the slots only (the partner of
+// a pair is the complex conjugate).  All arrays row-major, complex as (re, im).
+struct TimeDiag {
+  int q = 0, nr = 0, nc = 0;
+  std::vector<double> lam;  // [slot][2]
+  std::vector<double> Vmat; // [b][slot][2]: V[b][a]
+  std::vector<double> Umat; // [slot][b][2]: U[a][b]
+};
+// Fails (returns false) when W^{-1} Dt is not diagonalisable to 1e-10.
+bool time_diag(const Temporal &T, double tau, TimeDiag *out, std::string *err);
+
 // Vertex patches of a level (reading: dofs whose support lies in the closed
 // patch), with the patch matrices inverted in FP64.
+//
+// form 0 (dense): per patch the column-major C x C inverse, leading dim ld.
+// form 1 (time-diagonal): per patch, for each real slot the column-major
+// (lam S1_P + S2_P)^{-1} (Cs x Cs, leading dim ldR = ceil(Cs/4)*4), then for each
+// complex slot the same for complex lam with (re, im) interleaved per row
+// (leading dim ldC = 2*ceil(Cs/2)*2 reals).
 struct Patches {
   long npatch = 0;
   std::vector<int> size;          // C_P
@@ -100,11 +120,14 @@ struct Patches {
   std::vector<long long> inv_off; // offset (elements) into inv
   std::vector<double> inv;        // column-major A_P^{-1}, leading dim ld(C_P)
   std::vector<int> ld;
+  int form = 0;
+  std::vector<int> cs;            // spatial size Cs of each patch (form 1)
 };
 // vec: elements per 16-byte vector of the storage type (2 for FP64, 4 for FP32).
-// invert_them = false only builds the dof lists.
+// invert_them = false only builds the dof lists.  td != nullptr selects the
+// time-diagonal form.
 int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out,
-                  std::string *err, bool invert_them = true);
+                  std::string *err, bool invert_them = true, const TimeDiag *td = nullptr);
 
 // Dense row-major slab matrix of a level (for the coarse solve).
 std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau);

@@ -271,6 +271,142 @@ __global__ void __launch_bounds__(1024) k_patch_apply(const int *__restrict__ ps
   }
 }
 
+// Time-diagonal form of the same product.  With W^{-1} Dt = V diag(lam) V^{-1}
+// (q x q) the patch matrix Dt (x) S1_P + W (x) S2_P has the inverse
+//   A_P^{-1} = (V (x) I) blockdiag_a (lam_a S1_P + S2_P)^{-1} (V^{-1} W^{-1} (x) I),
+// and a complex-conjugate pair of eigenvalues shares one complex block.  Per
+// patch the kernel (1) gathers r_P, (2) mixes the q time blocks with
+// U = V^{-1} W^{-1}, (3) multiplies each slot by its stored inverse (real
+// slots: VEC rows per thread; complex slots: VEC/2 rows, (re, im) interleaved),
+// (4) mixes back with V (a conjugate pair contributes 2 Re(V z)).
+template <typename T>
+struct DiagCoef {
+  int nr, nc;
+  T U[2 * MAXQ * MAXQ]; // U[(a * q + b) * 2 + {re, im}] for the slots a
+  T V[2 * MAXQ * MAXQ]; // V[(b * ns + a) * 2 + {re, im}]
+};
+
+template <typename T, int J, int Q>
+__global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict__ pcs,
+                                                           const long long *__restrict__ pdoff,
+                                                           const int *__restrict__ pdofs,
+                                                           const long long *__restrict__ pioff,
+                                                           const T *__restrict__ pinv, const T *__restrict__ res,
+                                                           T *__restrict__ y, DiagCoef<T> dc, int maxCs) {
+  using Vv = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int CR = VEC / 2; // complex rows per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int RT = blockDim.x / J;
+  const int tr = threadIdx.x % RT, tj = threadIdx.x / RT;
+  const long p = blockIdx.x;
+  const int Cs = pcs[p], C = Q * Cs;
+  const long long doff = pdoff[p];
+  const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  T *red = reinterpret_cast<T *>(smem_raw);
+  T *rs = red + (J > 1 ? (size_t)J * RT * VEC : 0);
+  T *rt = rs + (size_t)Q * maxCs;
+  T *z = rt + (size_t)nrow * maxCs;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
+  __syncthreads();
+  for (int m = threadIdx.x; m < Cs; m += blockDim.x) {
+    for (int a = 0; a < ns; ++a) {
+      T re = T(0), im = T(0);
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const T r = rs[b * Cs + m];
+        re += dc.U[(a * Q + b) * 2] * r;
+        im += dc.U[(a * Q + b) * 2 + 1] * r;
+      }
+      if (a < nr) {
+        rt[a * Cs + m] = re;
+      } else {
+        rt[(nr + 2 * (a - nr)) * Cs + m] = re;
+        rt[(nr + 2 * (a - nr) + 1) * Cs + m] = im;
+      }
+    }
+  }
+  __syncthreads();
+  const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
+  const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+  const T *Ab = pinv + pioff[p];
+  T vals[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) vals[v] = T(0);
+  int role = -1, slot = 0, m0 = 0;
+  if (tr < nr * nRr) {
+    role = 0;
+    slot = tr / nRr;
+    m0 = VEC * (tr % nRr);
+    const Vv *col0 = reinterpret_cast<const Vv *>(Ab + (size_t)slot * Cs * ldR + m0);
+    const T *x = rt + slot * Cs;
+    const long stride = ldR / VEC;
+    int j = tj;
+    for (; j + 7 * J < Cs; j += 8 * J) {
+      Vv a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) fma_vec<T>(vals, a[u], x[j + u * J]);
+    }
+    for (; j < Cs; j += J) fma_vec<T>(vals, __ldcs(col0 + (long)j * stride), x[j]);
+  } else if (tr < nr * nRr + nc * nCr) {
+    role = 1;
+    const int t2 = tr - nr * nRr;
+    slot = t2 / nCr;
+    m0 = CR * (t2 % nCr);
+    const T *A = Ab + (size_t)nr * Cs * ldR + (size_t)slot * Cs * ldC + 2 * m0;
+    const T *xr = rt + (nr + 2 * slot) * Cs, *xi = xr + Cs;
+    const long stride = ldC / VEC;
+    const Vv *col0 = reinterpret_cast<const Vv *>(A);
+    for (int j = tj; j < Cs; j += J) {
+      const Vv a = __ldcs(col0 + (long)j * stride);
+      const T *av = reinterpret_cast<const T *>(&a);
+      const T ar = xr[j], ai = xi[j];
+#pragma unroll
+      for (int i = 0; i < CR; ++i) {
+        vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+        vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+      }
+    }
+  }
+  if (J > 1) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) red[((size_t)tj * RT + tr) * VEC + v] = vals[v];
+    __syncthreads();
+    if (tj == 0)
+      for (int t = 1; t < J; ++t)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) vals[v] += red[((size_t)t * RT + tr) * VEC + v];
+  }
+  if (tj == 0) {
+    if (role == 0) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        if (m0 + v < Cs) z[slot * Cs + m0 + v] = vals[v];
+    } else if (role == 1) {
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+        if (m0 + i < Cs) {
+          z[(nr + 2 * slot) * Cs + m0 + i] = vals[2 * i];
+          z[(nr + 2 * slot + 1) * Cs + m0 + i] = vals[2 * i + 1];
+        }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < C; idx += blockDim.x) {
+    const int b = idx / Cs, m = idx - b * Cs;
+    T val = T(0);
+    for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * z[a * Cs + m];
+    for (int c = 0; c < nc; ++c) {
+      const int a = nr + c;
+      val += T(2) * (dc.V[(b * ns + a) * 2] * z[(nr + 2 * c) * Cs + m] -
+                     dc.V[(b * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
+    }
+    y[doff + idx] = val;
+  }
+}
+
 // d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
 // scale = omega / (number of patches holding the dof): Algorithm 4.1's
 // d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).
@@ -287,42 +423,42 @@ __global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *
 // ---------------------------------------------------------------- transfers
 // out[a, blk, node*d + c] (+)= sum_e M[node, e] in[a, blk, col_e*d + c] for the
 // vector blocks blk = V, U (scalar operator of the Q_r space) and
-// out[a, P, node] (+)= sum_e Mp[node, e] in[a, P, col_e] (Q_{r-1} space), for
-// every time node a.  One thread per output node.
+// out[a, P, node] (+)= sum_e Mp[node, e] in[a, P, col_e] (Q_{r-1} space).
+// One thread per (time node, block, output node): the d components of a node
+// are contiguous, so each operator entry feeds D loads from one segment.
 template <typename T, int D>
 __global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_out, long ns_in, long R_in,
                            const int *__restrict__ up, const int *__restrict__ uc, const T *__restrict__ uv,
                            const int *__restrict__ pp, const int *__restrict__ pc, const T *__restrict__ pv,
                            const T *__restrict__ in, T *__restrict__ out, int add) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nu_out) {
-    const int e0 = up[i], e1 = up[i + 1];
-    for (int a = 0; a < q; ++a)
-      for (int blk = 0; blk < 2; ++blk) {
-        T acc[D];
+  const long nuq = 2 * nu_out * q;
+  if (i < nuq) {
+    const long node = i % nu_out;
+    const long ab = i / nu_out; // a * 2 + blk
+    const int a = (int)(ab >> 1), blk = (int)(ab & 1);
+    T acc[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = T(0);
-        const T *src = in + (long)a * ns_in + blk * R_in;
-        for (int e = e0; e < e1; ++e) {
-          const T w = uv[e];
-          const T *sp = src + (long)uc[e] * D;
+    for (int c = 0; c < D; ++c) acc[c] = T(0);
+    const T *src = in + (long)a * ns_in + blk * R_in;
+    for (int e = up[node]; e < up[node + 1]; ++e) {
+      const T w = uv[e];
+      const T *sp = src + (long)uc[e] * D;
 #pragma unroll
-          for (int c = 0; c < D; ++c) acc[c] += w * sp[c];
-        }
-        T *dst = out + (long)a * ns_out + blk * R_out + i * D;
-#pragma unroll
-        for (int c = 0; c < D; ++c) dst[c] = add ? dst[c] + acc[c] : acc[c];
-      }
-  } else if (i < nu_out + np_out) {
-    const long node = i - nu_out;
-    const int e0 = pp[node], e1 = pp[node + 1];
-    for (int a = 0; a < q; ++a) {
-      T acc = T(0);
-      const T *src = in + (long)a * ns_in + 2 * R_in;
-      for (int e = e0; e < e1; ++e) acc += pv[e] * src[pc[e]];
-      T *dst = out + (long)a * ns_out + 2 * R_out + node;
-      *dst = add ? *dst + acc : acc;
+      for (int c = 0; c < D; ++c) acc[c] += w * sp[c];
     }
+    T *dst = out + (long)a * ns_out + blk * R_out + node * D;
+#pragma unroll
+    for (int c = 0; c < D; ++c) dst[c] = add ? dst[c] + acc[c] : acc[c];
+  } else if (i < nuq + np_out * q) {
+    const long j = i - nuq;
+    const long node = j % np_out;
+    const int a = (int)(j / np_out);
+    T acc = T(0);
+    const T *src = in + (long)a * ns_in + 2 * R_in;
+    for (int e = pp[node]; e < pp[node + 1]; ++e) acc += pv[e] * src[pc[e]];
+    T *dst = out + (long)a * ns_out + 2 * R_out + node;
+    *dst = add ? *dst + acc : acc;
   }
 }
 
@@ -731,6 +867,10 @@ struct DLevel {
   int *iptr = nullptr, *ipos = nullptr;
   T *scale = nullptr, *ybuf = nullptr;
   double patch_bytes = 0.0, patch_flops = 0.0; // algorithmic, per patch-apply launch
+  int form = 0;       // 0 dense inverses, 1 time-diagonal form
+  int *pcs = nullptr; // spatial patch size Cs (form 1)
+  int maxCs = 0;
+  DiagCoef<T> dc{};
   double transfer_bytes = 0.0, transfer_nnz = 0.0;
   // work vectors
   T *b = nullptr, *d = nullptr, *r = nullptr;
@@ -1088,9 +1228,21 @@ int upload_transfer(stfem_h h, DLevel<T> &D, const stfem::CSR &Pu, const stfem::
 }
 
 template <typename T>
+void set_diag(DLevel<T> &D, const stfem::TimeDiag &td) {
+  D.dc = DiagCoef<T>{};
+  D.dc.nr = td.nr;
+  D.dc.nc = td.nc;
+  for (size_t i = 0; i < td.Umat.size() && i < 2 * MAXQ * MAXQ; ++i) D.dc.U[i] = (T)td.Umat[i];
+  for (size_t i = 0; i < td.Vmat.size() && i < 2 * MAXQ * MAXQ; ++i) D.dc.V[i] = (T)td.Vmat[i];
+}
+
+template <typename T>
 int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omega) {
   D.npatch = P.npatch;
   D.maxC = *std::max_element(P.size.begin(), P.size.end());
+  D.form = P.form;
+  D.maxCs = *std::max_element(P.cs.begin(), P.cs.end());
+  CKR(upload(h, &D.pcs, P.cs));
   D.inv_elems = (long long)P.inv.size();
   D.sumC = (long long)P.dofs.size();
   // algorithmic bytes of one patch-apply launch: every inverse once (C_P^2
@@ -1099,8 +1251,19 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
   D.patch_flops = 0.0;
   for (long p = 0; p < P.npatch; ++p) {
     const double C = P.size[p];
-    D.patch_bytes += C * C * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
-    D.patch_flops += 2.0 * C * C;
+    const double stored = (double)(P.inv_off[p + 1] - P.inv_off[p]);
+    if (P.form == 1) {
+      // algorithmic: the slot inverses once (Cs^2 per real slot, 2 Cs^2 per
+      // complex slot; padding excluded) plus the per-row traffic
+      const double Cs = P.cs[p];
+      const double q = C / Cs, nr = D.dc.nr, nc = D.dc.nc;
+      D.patch_bytes += (nr + 2.0 * nc) * Cs * Cs * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
+      D.patch_flops += (2.0 * nr + 8.0 * nc) * Cs * Cs + 4.0 * q * C;
+    } else {
+      D.patch_bytes += C * C * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
+      D.patch_flops += 2.0 * C * C;
+    }
+    (void)stored;
   }
   CKR(upload(h, &D.psize, P.size));
   CKR(upload(h, &D.pld, P.ld));
@@ -1144,26 +1307,60 @@ std::vector<DLevel<float>> &levels<float>(stfem_h h) {
 }
 
 // Launch shape of the patch apply: RT row threads cover the largest patch
-// (VEC rows each); J column groups per patch when the level has too few
-// patches to keep the 152 SMs streaming (about 2^18 resident threads).
+// (VEC rows each, or the slot rows of the time-diagonal form); J column groups
+// per patch when the level has too few patches to keep the 152 SMs streaming
+// (about 2^18 resident threads).
+template <typename T, int Q>
+void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t smem, const T *res, T *y) {
+  const unsigned grid = (unsigned)L.npatch;
+  switch (J) {
+  case 1: k_patch_apply_diag<T, 1, Q><<<grid, RT, smem, s>>>(L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, L.dc, L.maxCs); break;
+  case 2: k_patch_apply_diag<T, 2, Q><<<grid, RT * 2, smem, s>>>(L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, L.dc, L.maxCs); break;
+  case 4: k_patch_apply_diag<T, 4, Q><<<grid, RT * 4, smem, s>>>(L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, L.dc, L.maxCs); break;
+  default: k_patch_apply_diag<T, 8, Q><<<grid, RT * 8, smem, s>>>(L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, L.dc, L.maxCs); break;
+  }
+}
+
 template <typename T>
-void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res) {
+void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   constexpr int VEC = Vec16<T>::n;
-  int RT = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
+  int rows;
+  if (L.form == 1)
+    rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
+  else
+    rows = (L.maxC + VEC - 1) / VEC;
+  int RT = (rows + 31) / 32 * 32;
   RT = std::min(std::max(RT, 32), 1024);
   int J = 1;
   const double target = 152.0 * 1536.0;
   while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
-  const size_t smem = (size_t)L.maxC * sizeof(T) + (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
-  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
-  const unsigned grid = (unsigned)L.npatch;
+  size_t smem = (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
   cudaStream_t s = h->stream;
-  switch (J) {
-  case 1: k_patch_apply<T, 1><<<grid, RT, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
-  case 2: k_patch_apply<T, 2><<<grid, RT * 2, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
-  case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
-  default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, L.ybuf); break;
+  const unsigned grid = (unsigned)L.npatch;
+  if (L.form == 1) {
+    smem += (size_t)(h->q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
+    switch (h->q) {
+    case 1: launch_patch_diag_q<T, 1>(s, L, RT, J, smem, res, y); break;
+    case 2: launch_patch_diag_q<T, 2>(s, L, RT, J, smem, res, y); break;
+    case 3: launch_patch_diag_q<T, 3>(s, L, RT, J, smem, res, y); break;
+    case 4: launch_patch_diag_q<T, 4>(s, L, RT, J, smem, res, y); break;
+    default: launch_patch_diag_q<T, 5>(s, L, RT, J, smem, res, y); break;
+    }
+    return;
   }
+  smem += (size_t)L.maxC * sizeof(T);
+  switch (J) {
+  case 1: k_patch_apply<T, 1><<<grid, RT, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  case 2: k_patch_apply<T, 2><<<grid, RT * 2, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
+  }
+}
+
+template <typename T>
+void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res) {
+  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
+  launch_patch_apply_to<T>(h, L, res, L.ybuf);
 }
 
 template <typename T>
@@ -1193,12 +1390,12 @@ void restrict_to(stfem_h h, int l, const T *rf, T *bc) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
-  const long nu = C.R / h->dim, np = C.S;
+  const long nu = C.R / h->dim, np = C.S, nt = (2 * nu + np) * h->q;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+    k_transfer<T, 2><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
                                                                      F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
   else
-    k_transfer<T, 3><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+    k_transfer<T, 3><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
                                                                      F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
 }
 
@@ -1207,12 +1404,12 @@ void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
-  const long nu = F.R / h->dim, np = F.S;
+  const long nu = F.R / h->dim, np = F.S, nt = (2 * nu + np) * h->q;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+    k_transfer<T, 2><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
                                                                      F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
   else
-    k_transfer<T, 3><<<grid_for(nu + np, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+    k_transfer<T, 3><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
                                                                      F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
 }
 
@@ -1617,26 +1814,6 @@ int noalloc_scratch(stfem_h h, unsigned char **out) {
   return 0;
 }
 
-// The patch apply of launch_patch_apply, writing the patch results to y.
-template <typename T>
-void launch_patch_apply_into(stfem_h h, DLevel<T> &L, const T *res, T *y) {
-  constexpr int VEC = Vec16<T>::n;
-  int RT = ((L.maxC + VEC - 1) / VEC + 31) / 32 * 32;
-  RT = std::min(std::max(RT, 32), 1024);
-  int J = 1;
-  const double target = 152.0 * 1536.0;
-  while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
-  const size_t smem = (size_t)L.maxC * sizeof(T) + (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
-  const unsigned grid = (unsigned)L.npatch;
-  cudaStream_t s = h->stream;
-  switch (J) {
-  case 1: k_patch_apply<T, 1><<<grid, RT, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
-  case 2: k_patch_apply<T, 2><<<grid, RT * 2, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
-  case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
-  default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
-  }
-}
-
 template <typename T>
 int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init) {
   DLevel<T> &L = levels<T>(h)[level];
@@ -1671,7 +1848,7 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
       launch_spmv<T>(h, L, tc, dT, bT, rT, 1);
       res = rT;
     }
-    launch_patch_apply_into<T>(h, L, res, yT);
+    launch_patch_apply_to<T>(h, L, res, yT);
     k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0);
   }
   k_convert<T, double><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, dT, d);
@@ -1762,7 +1939,8 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
 
 int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
   if (!h || !p) return STFEM_ERR_ARG;
-  if (!(p->omega > 0.0) || p->n_sweeps < 1 || (p->precision != STFEM_FP64 && p->precision != STFEM_MIXED)) {
+  if (!(p->omega > 0.0) || p->n_sweeps < 1 || (p->precision != STFEM_FP64 && p->precision != STFEM_MIXED) ||
+      p->patch_form < STFEM_PATCH_AUTO || p->patch_form > STFEM_PATCH_TIME_DIAGONAL) {
     h->err = "invalid GMG parameters";
     return STFEM_ERR_ARG;
   }
@@ -1781,17 +1959,31 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       if (l >= 1) CKR(upload_transfer(h, h->L32[l], h->Pu[l], h->Pp[l]));
     }
   }
+  int form = p->patch_form;
+  if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
+  stfem::TimeDiag td;
+  if (form == STFEM_PATCH_TIME_DIAGONAL) {
+    std::string err;
+    if (!stfem::time_diag(h->T, h->tau, &td, &err)) {
+      h->err = "time-diagonal patch form: " + err;
+      return STFEM_ERR_STATE;
+    }
+  }
   for (int l = 1; l < h->nlev; ++l) {
     stfem::Patches P;
     std::string err;
-    if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err) < 0) {
+    if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err, true,
+                             form == STFEM_PATCH_TIME_DIAGONAL ? &td : nullptr) < 0) {
       h->err = err + " on level " + std::to_string(l);
       return STFEM_ERR_SINGULAR_PATCH;
     }
-    if (mixed)
+    if (mixed) {
+      set_diag(h->L32[l], td);
       CKR(upload_patches(h, h->L32[l], P, h->omega));
-    else
+    } else {
+      set_diag(h->L64[l], td);
       CKR(upload_patches(h, h->L64[l], P, h->omega));
+    }
   }
   std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
   const int n0 = (int)(h->hl[0].ns * h->q);

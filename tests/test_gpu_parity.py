@@ -35,12 +35,12 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def pair(name, precision=0):
-    key = (name, precision)
+def pair(name, precision=0, patch_form=0):
+    key = (name, precision, patch_form)
     if key not in _cache:
         import paper_2303_06742_gb300 as st
         c = case(name)
-        S = st.Solver(gpu_problem(c), precision=precision)
+        S = st.Solver(gpu_problem(c), precision=precision, patch_form=patch_form)
         O = oracle_instance(c)
         _cache[key] = (c, S, O)
     return _cache[key]
@@ -211,3 +211,23 @@ def test_mixed_precision_solve(name):
     assert rc == 0 and rel <= tol
     r0 = np.linalg.norm(b - O.A @ x0)
     assert np.linalg.norm(b - O.A @ xg) <= 1.01 * tol * r0
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("precision,patch_form,tol", [(0, 2, 1e-10), (1, 1, 1e-4), (1, 2, 1e-4)])
+def test_smoother_patch_forms(name, precision, patch_form, tol):
+    """Time-diagonal patch inverses (FP64: to rounding of the eigen-decomposition)
+    and both FP32 forms of the mixed mode against the oracle's smoother."""
+    from oracle.gmg import smooth
+    c, S, O = pair(name, precision=precision, patch_form=patch_form)
+    rng = np.random.default_rng(8)
+    for l in range(1, len(O.h.levels)):
+        lev = O.h.levels[l]
+        b = rng.standard_normal(lev.A.shape[0])
+        d0 = rng.standard_normal(lev.A.shape[0])
+        d = dev(d0)
+        S.smooth(l, dev(b), d, n_sweeps=2, zero_init=False)
+        ref = smooth(lev, b, d0.copy(), 0.7, 2)
+        err = _rel(host(d), ref)
+        print(name, "smooth form", precision, patch_form, "level", l, err)
+        assert err < tol
