@@ -25,6 +25,14 @@
 
 using namespace stfem_dev;
 
+// Launch-shape tuning of the patch apply (compile-time constants).
+#ifndef STFEM_DIAG_UNROLL_COMPLEX
+#define STFEM_DIAG_UNROLL_COMPLEX 0
+#endif
+#ifndef STFEM_PATCH_THREADS_PER_SM
+#define STFEM_PATCH_THREADS_PER_SM 4096
+#endif
+
 namespace {
 
 // ============================================================ device helpers
@@ -75,29 +83,40 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
   if (is_u) {
     // acc layout: [0] Mr U, [1] Mr V, [2] K U, [3] Ct P; each Q x D
     const int e1 = A.uu_ptr[node + 1];
-    for (int e = A.uu_ptr[node] + lane; e < e1; e += G) {
-      const long J = A.uu_col[e];
-      const T m = A.uu_m[e];
-      T k[D * D];
+    // two neighbours per trip: their matrix and vector loads are independent
+    for (int e0 = A.uu_ptr[node] + lane; e0 < e1; e0 += 2 * G) {
+      const bool two = e0 + G < e1;
+      const int eb[2] = {e0, two ? e0 + G : e0};
+      long J[2];
+      T m[2], k[2][D * D];
 #pragma unroll
-      for (int i = 0; i < D * D; ++i) k[i] = A.uu_k[(long)e * D * D + i];
+      for (int t = 0; t < 2; ++t) {
+        J[t] = A.uu_col[eb[t]];
+        m[t] = (t == 0 || two) ? A.uu_m[eb[t]] : T(0);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) k[t][i] = (t == 0 || two) ? A.uu_k[(long)eb[t] * D * D + i] : T(0);
+      }
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        T v[D], u[D];
+        T v[2][D], u[2][D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          v[c] = x[(long)a * ns + J * D + c];
-          u[c] = x[(long)a * ns + R + J * D + c];
-        }
+        for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          acc[(0 * Q + a) * D + c] += m * u[c];
-          acc[(1 * Q + a) * D + c] += m * v[c];
-          T kk = T(0);
+          for (int c = 0; c < D; ++c) {
+            v[t][c] = x[(long)a * ns + J[t] * D + c];
+            u[t][c] = x[(long)a * ns + R + J[t] * D + c];
+          }
 #pragma unroll
-          for (int cp = 0; cp < D; ++cp) kk += k[c * D + cp] * u[cp];
-          acc[(2 * Q + a) * D + c] += kk;
-        }
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            acc[(0 * Q + a) * D + c] += m[t] * u[t][c];
+            acc[(1 * Q + a) * D + c] += m[t] * v[t][c];
+            T kk = T(0);
+#pragma unroll
+            for (int cp = 0; cp < D; ++cp) kk += k[t][c * D + cp] * u[t][cp];
+            acc[(2 * Q + a) * D + c] += kk;
+          }
       }
     }
     const int f1 = A.up_ptr[node + 1];
@@ -359,7 +378,23 @@ __global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict
     const T *xr = rt + (nr + 2 * slot) * Cs, *xi = xr + Cs;
     const long stride = ldC / VEC;
     const Vv *col0 = reinterpret_cast<const Vv *>(A);
-    for (int j = tj; j < Cs; j += J) {
+    int j = tj;
+    for (; STFEM_DIAG_UNROLL_COMPLEX && j + 7 * J < Cs; j += 8 * J) {
+      Vv a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T *av = reinterpret_cast<const T *>(&a[u]);
+        const T ar = xr[j + u * J], ai = xi[j + u * J];
+#pragma unroll
+        for (int i = 0; i < CR; ++i) {
+          vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+          vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+        }
+      }
+    }
+    for (; j < Cs; j += J) {
       const Vv a = __ldcs(col0 + (long)j * stride);
       const T *av = reinterpret_cast<const T *>(&a);
       const T ar = xr[j], ai = xi[j];
@@ -404,6 +439,247 @@ __global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict
                      dc.V[(b * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
     }
     y[doff + idx] = val;
+  }
+}
+
+// ---------------------------------------------------------------- bulk-copy streaming
+// Helpers for the asynchronous bulk copy (cp.async.bulk) of contiguous global
+// data into shared memory, completed on an mbarrier (transaction bytes).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(smem_addr(bar)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+// Waits until the phase of the given parity has completed, for at most
+// `limit` clock cycles; false on timeout (the caller then aborts).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+constexpr int STREAM_STAGES = 4;
+constexpr int STREAM_CHUNK = 16384;                 // bytes per shared-memory stage
+constexpr long long STREAM_WAIT_LIMIT = 4000000000LL; // clock cycles (about 2 s)
+constexpr int STREAM_HEADER = STREAM_STAGES * STREAM_CHUNK + 2 * STREAM_STAGES * 8 + 16;
+
+// Time-diagonal patch apply (see k_patch_apply_diag) with the inverse blocks
+// streamed by bulk copies.  Persistent CTAs take patches p = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  The last warp is the producer: one lane walks
+// the (patch, slot, column chunk) sequence and copies each chunk (contiguous,
+// 16-byte aligned, a multiple of 16 bytes) into a ring of STREAM_STAGES
+// shared stages.  The other warps gather and mix the residual, consume the
+// chunks of their slot rows from shared memory, and mix the result back.
+// Every wait is bounded; on a timeout the CTA sets *err, the producer waits
+// (bounded) for its copies still in flight, and the CTA returns.
+template <typename T, int Q>
+__global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const int *__restrict__ pcs,
+                                                             const long long *__restrict__ pdoff,
+                                                             const int *__restrict__ pdofs,
+                                                             const long long *__restrict__ pioff,
+                                                             const T *__restrict__ pinv, const T *__restrict__ res,
+                                                             T *__restrict__ y, DiagCoef<T> dc, int maxCs,
+                                                             int *__restrict__ err) {
+  using Vv = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int CR = VEC / 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *stage = smem_raw;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STREAM_STAGES * STREAM_CHUNK);
+  uint64_t *empty = full + STREAM_STAGES;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + STREAM_STAGES);
+  const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  T *rs = reinterpret_cast<T *>(smem_raw + STREAM_HEADER);
+  T *rt = rs + (size_t)Q * maxCs;
+  T *z = rt + (size_t)nrow * maxCs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwc = (blockDim.x >> 5) - 1; // consumer warps
+  const int nct = nwc * 32;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STREAM_STAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], nwc);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == nwc) {
+    // ---------------- producer
+    if (lane != 0) return;
+    long long it = 0;
+    bool ok = true;
+    for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
+      const int Cs = pcs[p];
+      const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+      const T *base = pinv + pioff[p];
+      for (int sl = 0; sl < ns && ok; ++sl) {
+        const int ld = sl < nr ? ldR : ldC;
+        const T *sb = base + (sl < nr ? (size_t)sl * Cs * ldR : (size_t)nr * Cs * ldR + (size_t)(sl - nr) * Cs * ldC);
+        const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
+        for (int j0 = 0; j0 < Cs; j0 += K) {
+          const int st = (int)(it % STREAM_STAGES);
+          if (it >= STREAM_STAGES &&
+              !mbar_wait(&empty[st], (uint32_t)(((it / STREAM_STAGES) - 1) & 1), STREAM_WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          if (*abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t bytes = (uint32_t)(min(K, Cs - j0) * ld * (int)sizeof(T));
+          mbar_arrive_expect_tx(&full[st], bytes);
+          bulk_copy_g2s(stage + (size_t)st * STREAM_CHUNK, sb + (size_t)j0 * ld, bytes, &full[st]);
+          ++it;
+        }
+      }
+    }
+    if (!ok) {
+      atomicExch(err, 1);
+      *abort_flag = 1;
+      // copies still in flight must land before the CTA exits
+      for (long long k = (it > STREAM_STAGES ? it - STREAM_STAGES : 0); k < it; ++k)
+        mbar_wait(&full[k % STREAM_STAGES], (uint32_t)((k / STREAM_STAGES) & 1), STREAM_WAIT_LIMIT);
+    }
+    return;
+  }
+
+  // ---------------- consumers (threads 0 .. nct-1)
+  const int tid = threadIdx.x;
+  long long it = 0;
+  for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+    // all consumers pass the same barriers, so they all see the flag and
+    // leave together (no barrier is left waiting)
+    consumer_sync(nct);
+    if (*abort_flag) return;
+    const int Cs = pcs[p], C = Q * Cs;
+    const long long doff = pdoff[p];
+    for (int j = tid; j < C; j += nct) rs[j] = res[pdofs[doff + j]];
+    consumer_sync(nct);
+    for (int m = tid; m < Cs; m += nct) {
+      for (int a = 0; a < ns; ++a) {
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          const T r = rs[b * Cs + m];
+          re += dc.U[(a * Q + b) * 2] * r;
+          im += dc.U[(a * Q + b) * 2 + 1] * r;
+        }
+        if (a < nr) {
+          rt[a * Cs + m] = re;
+        } else {
+          rt[(nr + 2 * (a - nr)) * Cs + m] = re;
+          rt[(nr + 2 * (a - nr) + 1) * Cs + m] = im;
+        }
+      }
+    }
+    consumer_sync(nct);
+    const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
+    const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+    int role = -1, slot = 0, m0 = 0;
+    if (tid < nr * nRr) {
+      role = 0;
+      slot = tid / nRr;
+      m0 = VEC * (tid % nRr);
+    } else if (tid < nr * nRr + nc * nCr) {
+      role = 1;
+      const int t2 = tid - nr * nRr;
+      slot = t2 / nCr;
+      m0 = CR * (t2 % nCr);
+    }
+    T vals[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) vals[v] = T(0);
+    for (int sl = 0; sl < ns; ++sl) {
+      const int ld = sl < nr ? ldR : ldC;
+      const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
+      for (int j0 = 0; j0 < Cs; j0 += K) {
+        const int st = (int)(it % STREAM_STAGES);
+        bool ready = !*abort_flag;
+        if (ready && !mbar_wait(&full[st], (uint32_t)((it / STREAM_STAGES) & 1), STREAM_WAIT_LIMIT)) {
+          atomicExch(err, 2);
+          *abort_flag = 1;
+          ready = false;
+        }
+        const int ncol = ready ? min(K, Cs - j0) : 0;
+        const T *sbuf = reinterpret_cast<const T *>(stage + (size_t)st * STREAM_CHUNK);
+        if (sl < nr) {
+          if (role == 0 && slot == sl) {
+            const T *x = rt + sl * Cs + j0;
+            for (int j = 0; j < ncol; ++j)
+              fma_vec<T>(vals, *reinterpret_cast<const Vv *>(sbuf + (size_t)j * ld + m0), x[j]);
+          }
+        } else if (role == 1 && slot == sl - nr) {
+          const T *xr = rt + (nr + 2 * slot) * Cs + j0, *xi = xr + Cs;
+          for (int j = 0; j < ncol; ++j) {
+            const Vv a = *reinterpret_cast<const Vv *>(sbuf + (size_t)j * ld + 2 * m0);
+            const T *av = reinterpret_cast<const T *>(&a);
+            const T ar = xr[j], ai = xi[j];
+#pragma unroll
+            for (int i = 0; i < CR; ++i) {
+              vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+              vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        ++it;
+      }
+    }
+    if (role == 0) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        if (m0 + v < Cs) z[slot * Cs + m0 + v] = vals[v];
+    } else if (role == 1) {
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+        if (m0 + i < Cs) {
+          z[(nr + 2 * slot) * Cs + m0 + i] = vals[2 * i];
+          z[(nr + 2 * slot + 1) * Cs + m0 + i] = vals[2 * i + 1];
+        }
+    }
+    consumer_sync(nct);
+    for (int idx = tid; idx < C; idx += nct) {
+      const int b = idx / Cs, m = idx - b * Cs;
+      T val = T(0);
+      for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * z[a * Cs + m];
+      for (int c = 0; c < nc; ++c) {
+        const int a = nr + c;
+        val += T(2) * (dc.V[(b * ns + a) * 2] * z[(nr + 2 * c) * Cs + m] -
+                       dc.V[(b * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
+      }
+      y[doff + idx] = val;
+    }
+    consumer_sync(nct);
   }
 }
 
@@ -909,6 +1185,7 @@ struct stfem_ctx {
   double *h1 = nullptr, *h2 = nullptr, *hn2 = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
          *y = nullptr, *hnorm = nullptr, *partial = nullptr, *status = nullptr;
   double *status_host = nullptr;
+  int *dev_err = nullptr; // set by kernels whose bounded waits timed out
   // march buffers and load tables
   double *rhs = nullptr, *xs = nullptr, *ys = nullptr, *chi = nullptr, *tnode = nullptr, *src = nullptr;
   LoadTables lt{};
@@ -1321,6 +1598,35 @@ void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t sme
   }
 }
 
+// Shape of the streaming time-diagonal patch apply: one consumer thread per
+// row block of the largest patch (rounded to warps) plus a producer warp;
+// shared memory = stages + the per-patch vectors; as many CTAs per SM as
+// shared memory allows (at most 3), at most one CTA per patch.
+template <typename T>
+void stream_shape(const DLevel<T> &L, int q, int *threads, size_t *smem, int *grid) {
+  constexpr int VEC = Vec16<T>::n;
+  const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
+  const int nwc = std::max(1, (rows + 31) / 32);
+  *threads = 32 * (nwc + 1);
+  *smem = (size_t)STREAM_HEADER + (size_t)(q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
+  const int per_sm = std::max(1, std::min(3, (int)((227u * 1024u) / *smem)));
+  *grid = (int)std::min<long>(L.npatch, 152L * per_sm);
+}
+
+template <typename T, int Q>
+void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
+  static bool attr_set = false;
+  int threads, grid;
+  size_t smem;
+  stream_shape(L, Q, &threads, &smem, &grid);
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_patch_apply_stream<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  k_patch_apply_stream<T, Q><<<grid, threads, smem, h->stream>>>((int)L.npatch, L.pcs, L.pdoff, L.pdofs, L.pioff,
+                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err);
+}
+
 template <typename T>
 void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   constexpr int VEC = Vec16<T>::n;
@@ -1329,22 +1635,22 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
     rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
   else
     rows = (L.maxC + VEC - 1) / VEC;
-  int RT = (rows + 31) / 32 * 32;
-  RT = std::min(std::max(RT, 32), 1024);
+  // the dense kernel loops over row blocks, so it can cap RT; the
+  // time-diagonal one needs every row block resident (checked at setup)
+  const int RT = L.form == 1 ? std::max((rows + 31) / 32 * 32, 32) : std::min(std::max((rows + 31) / 32 * 32, 32), 512);
   int J = 1;
-  const double target = 152.0 * 1536.0;
+  const double target = 152.0 * STFEM_PATCH_THREADS_PER_SM;
   while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
   size_t smem = (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
   cudaStream_t s = h->stream;
   const unsigned grid = (unsigned)L.npatch;
   if (L.form == 1) {
-    smem += (size_t)(h->q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
     switch (h->q) {
-    case 1: launch_patch_diag_q<T, 1>(s, L, RT, J, smem, res, y); break;
-    case 2: launch_patch_diag_q<T, 2>(s, L, RT, J, smem, res, y); break;
-    case 3: launch_patch_diag_q<T, 3>(s, L, RT, J, smem, res, y); break;
-    case 4: launch_patch_diag_q<T, 4>(s, L, RT, J, smem, res, y); break;
-    default: launch_patch_diag_q<T, 5>(s, L, RT, J, smem, res, y); break;
+    case 1: launch_patch_stream_q<T, 1>(h, L, res, y); break;
+    case 2: launch_patch_stream_q<T, 2>(h, L, res, y); break;
+    case 3: launch_patch_stream_q<T, 3>(h, L, res, y); break;
+    case 4: launch_patch_stream_q<T, 4>(h, L, res, y); break;
+    default: launch_patch_stream_q<T, 5>(h, L, res, y); break;
     }
     return;
   }
@@ -1355,6 +1661,25 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
   default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
   }
+}
+
+// Row threads a patch needs: the time-diagonal kernel gives each thread one
+// row block; a single CTA (no column split) holds at most 512 threads.
+template <typename T>
+int check_patch_shape(stfem_h h, const DLevel<T> &L) {
+  constexpr int VEC = Vec16<T>::n;
+  if (L.form != 1) return 0;
+  const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
+  int threads, grid;
+  size_t smem;
+  stream_shape(L, h->q, &threads, &smem, &grid);
+  const size_t widest_column = (size_t)2 * ((L.maxCs + 1) / 2 * 2) * sizeof(T); // complex slot column
+  if (rows > 992 || smem > 227u * 1024u || widest_column > (size_t)STREAM_CHUNK) {
+    h->err = "patches too large for the time-diagonal form (" + std::to_string(rows) + " row threads, " +
+             std::to_string(smem) + " bytes of shared memory); use STFEM_PATCH_DENSE";
+    return STFEM_ERR_ARG;
+  }
+  return 0;
 }
 
 template <typename T>
@@ -1623,6 +1948,18 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
   }
 }
 
+// A bounded wait inside a kernel timed out (reported through h->dev_err).
+int check_dev_err(stfem_h h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e) {
+    h->err = "a bounded wait in the streaming patch apply timed out (code " + std::to_string(e) + ")";
+    return STFEM_ERR_CUDA;
+  }
+  return 0;
+}
+
 int check_level(stfem_h h, int level, bool allow_fine_alias) {
   if (level == -1 && allow_fine_alias) return 0;
   if (level < 0 || level >= h->nlev) {
@@ -1673,6 +2010,7 @@ int smooth_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero
   from_level<T>(h, L.d, d, L.N);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
+  CKR(check_dev_err(h));
   return 0;
 }
 
@@ -1854,6 +2192,7 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   k_convert<T, double><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, dT, d);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  CKR(check_dev_err(h));
   return 0;
 }
 
@@ -1922,6 +2261,7 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
       (rc = dalloc(h, &h->ys, F.ns)) < 0 || (rc = dalloc(h, &h->hn2, 1)) < 0 ||
       (rc = dalloc(h, &h->src, (size_t)h->q * F.box.ncell * h->lt.nq * 4)) < 0 ||
       (rc = dalloc(h, &h->hnorm, 1)) < 0 || (rc = dalloc(h, &h->status, 4)) < 0 ||
+      (rc = dalloc(h, &h->dev_err, 1)) < 0 ||
       (rc = dalloc(h, &h->partial, (size_t)DOT_BLOCKS * (MAXM + 1))) < 0 ||
       (rc = upload(h, &h->chi, h->T.chi_m1)) < 0 || (rc = upload(h, &h->tnode, h->T.t)) < 0)
     return fail_setup(h, rc);
@@ -1929,7 +2269,7 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
     h->err = "cudaHostAlloc failed";
     return fail_setup(h, STFEM_ERR_CUDA);
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     h->err = "device error during setup";
     return fail_setup(h, STFEM_ERR_CUDA);
   }
@@ -1980,9 +2320,11 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
     if (mixed) {
       set_diag(h->L32[l], td);
       CKR(upload_patches(h, h->L32[l], P, h->omega));
+      CKR(check_patch_shape(h, h->L32[l]));
     } else {
       set_diag(h->L64[l], td);
       CKR(upload_patches(h, h->L64[l], P, h->omega));
+      CKR(check_patch_shape(h, h->L64[l]));
     }
   }
   std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
@@ -2088,6 +2430,7 @@ int stfem_vcycle(stfem_h h, const double *b, double *d) {
   CKR(require_gmg(h));
   CKR(precondition(h, b, d, nullptr));
   CK(cudaStreamSynchronize(h->stream));
+  CKR(check_dev_err(h));
   return STFEM_OK;
 }
 
@@ -2100,6 +2443,7 @@ int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart,
   int rc = fgmres(h, rhs, x, tol, restart, max_it, &it, &rr);
   if (iters) *iters = it;
   if (rel_res) *rel_res = rr;
+  CKR(check_dev_err(h));
   return rc;
 }
 
@@ -2176,6 +2520,7 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
                        h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
+  CKR(check_dev_err(h));
   return worst;
 }
 
