@@ -509,13 +509,13 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char *stage = smem_raw;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + STREAM_STAGES * STREAM_CHUNK);
+  extern __shared__ __align__(128) unsigned char smem_stream[];
+  unsigned char *stage = smem_stream;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_stream + STREAM_STAGES * STREAM_CHUNK);
   uint64_t *empty = full + STREAM_STAGES;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + STREAM_STAGES);
   const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
-  T *rs = reinterpret_cast<T *>(smem_raw + STREAM_HEADER);
+  T *rs = reinterpret_cast<T *>(smem_stream + STREAM_HEADER);
   T *rt = rs + (size_t)Q * maxCs;
   T *z = rt + (size_t)nrow * maxCs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1200,6 +1200,15 @@ struct stfem_ctx {
   } kstat[STFEM_KCLASS_COUNT];
   std::vector<cudaEvent_t> evpool;
   size_t evnext = 0;
+  // one captured CUDA graph per FGMRES iteration index j (same buffers every
+  // solve), with the launch accounting of its kernels
+  struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    KStat delta[STFEM_KCLASS_COUNT];
+  };
+  std::vector<GraphRec> graphs;
+  bool use_graphs = true;
   std::vector<std::pair<int, size_t>> pending; // (class, index of start event)
 };
 
@@ -1615,14 +1624,9 @@ void stream_shape(const DLevel<T> &L, int q, int *threads, size_t *smem, int *gr
 
 template <typename T, int Q>
 void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
-  static bool attr_set = false;
   int threads, grid;
   size_t smem;
   stream_shape(L, Q, &threads, &smem, &grid);
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_patch_apply_stream<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_set = true;
-  }
   k_patch_apply_stream<T, Q><<<grid, threads, smem, h->stream>>>((int)L.npatch, L.pcs, L.pdoff, L.pdofs, L.pioff,
                                                                  L.pinv, res, y, L.dc, L.maxCs, h->dev_err);
 }
@@ -1661,6 +1665,19 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   case 4: k_patch_apply<T, 4><<<grid, RT * 4, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
   default: k_patch_apply<T, 8><<<grid, RT * 8, smem, s>>>(L.psize, L.pdoff, L.pdofs, L.pioff, L.pld, L.pinv, res, y); break;
   }
+}
+
+// Opts the streaming kernels in to 227 KB of dynamic shared memory (done at
+// setup, never during a graph capture).
+int prepare_stream_kernels(stfem_h h) {
+#define STFEM_SMEM_ATTR(T, Q)                                                                            \
+  CK(cudaFuncSetAttribute(k_patch_apply_stream<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
+  STFEM_SMEM_ATTR(float, 1); STFEM_SMEM_ATTR(float, 2); STFEM_SMEM_ATTR(float, 3);
+  STFEM_SMEM_ATTR(float, 4); STFEM_SMEM_ATTR(float, 5);
+  STFEM_SMEM_ATTR(double, 1); STFEM_SMEM_ATTR(double, 2); STFEM_SMEM_ATTR(double, 3);
+  STFEM_SMEM_ATTR(double, 4); STFEM_SMEM_ATTR(double, 5);
+#undef STFEM_SMEM_ATTR
+  return 0;
 }
 
 // Row threads a patch needs: the time-diagonal kernel gives each thread one
@@ -1830,6 +1847,108 @@ int ensure_workspace(stfem_h h, int m) {
   CKR(dalloc(h, &h->h1, m + 1));
   CKR(dalloc(h, &h->h2, m + 1));
   h->mcap = m;
+  for (auto &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.assign(m, stfem_ctx::GraphRec());
+  return 0;
+}
+
+// All work of FGMRES iteration j (Sec. 4): z_j = M^{-1} v_j (one V-cycle),
+// w = A z_j, classical Gram-Schmidt twice, Givens update, copy of the status
+// {|g_{j+1}|, h_{j+1,j}} to pinned host memory, and v_{j+1} = w / h_{j+1,j}
+// (unused when the host stops at j).  Only stream-ordered work: it can be
+// captured into a graph.
+int enqueue_iteration(stfem_h h, int j, int m1) {
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  cudaStream_t s = h->stream;
+  const int nb = grid_for(N, 256);
+  double *vj = h->V + (long)j * N;
+  double *zj = nullptr;
+  if (h->precision == STFEM_FP64) {
+    zj = h->Zd + (long)j * N;
+    CKR(precondition(h, vj, zj, nullptr));
+  } else {
+    CKR(precondition(h, vj, h->zt, h->Zf + (long)j * N));
+    zj = h->zt;
+  }
+  double *w = h->w;
+  launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
+  // classical Gram-Schmidt, applied twice
+  multidot(h, j + 1, h->V, N, w, N, h->h1);
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
+    k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
+  }
+  multidot(h, j + 1, h->V, N, w, N, h->h2);
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
+    k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
+  }
+  multidot(h, 1, w, N, w, N, h->hn2);
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)(4 * j + 8) * 8.0, (double)(6 * j + 10));
+    k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);
+  }
+  CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (j + 1 < m1) {
+    Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+    k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
+  }
+  return 0;
+}
+
+// Runs iteration j from its captured graph (captured on first use), or
+// eagerly when profiling (per-launch events) or on the legacy stream.
+int run_iteration(stfem_h h, int j, int m1) {
+  const bool graphs = h->use_graphs && !h->prof && h->stream != 0 && j < (int)h->graphs.size();
+  if (!graphs) return enqueue_iteration(h, j, m1);
+  stfem_ctx::GraphRec &g = h->graphs[j];
+  if (!g.exec) {
+    stfem_ctx::KStat before[STFEM_KCLASS_COUNT];
+    for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) before[k] = h->kstat[k];
+    const long long l0 = h->launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->use_graphs = false;
+      return enqueue_iteration(h, j, m1);
+    }
+    const int rc = enqueue_iteration(h, j, m1);
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    if (rc < 0) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess || cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      g.exec = nullptr;
+      h->use_graphs = false;
+      for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) h->kstat[k] = before[k];
+      h->launches = l0;
+      return enqueue_iteration(h, j, m1);
+    }
+    cudaGraphDestroy(graph);
+    // the capture only recorded the launches: keep their accounting with the
+    // graph and count them when it runs
+    for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) {
+      g.delta[k].launches = h->kstat[k].launches - before[k].launches;
+      g.delta[k].bytes = h->kstat[k].bytes - before[k].bytes;
+      g.delta[k].flops = h->kstat[k].flops - before[k].flops;
+      h->kstat[k] = before[k];
+    }
+    g.launches = h->launches - l0;
+    h->launches = l0;
+  }
+  CK(cudaGraphLaunch(g.exec, h->stream));
+  for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) {
+    h->kstat[k].launches += g.delta[k].launches;
+    h->kstat[k].bytes += g.delta[k].bytes;
+    h->kstat[k].flops += g.delta[k].flops;
+  }
+  h->launches += g.launches;
   return 0;
 }
 
@@ -1869,34 +1988,7 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
     int jlast = -1;
     bool stop = false;
     for (int j = 0; j < m; ++j) {
-      double *vj = h->V + (long)j * N;
-      double *zj = nullptr;
-      if (h->precision == STFEM_FP64) {
-        zj = h->Zd + (long)j * N;
-        CKR(precondition(h, vj, zj, nullptr));
-      } else {
-        CKR(precondition(h, vj, h->zt, h->Zf + (long)j * N));
-        zj = h->zt;
-      }
-      double *w = h->w;
-      launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
-      // classical Gram-Schmidt, applied twice
-      multidot(h, j + 1, h->V, N, w, N, h->h1);
-      {
-        Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
-        k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
-      }
-      multidot(h, j + 1, h->V, N, w, N, h->h2);
-      {
-        Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
-        k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
-      }
-      multidot(h, 1, w, N, w, N, h->hn2);
-      {
-        Launch G_(h, STFEM_KCLASS_OTHER, (double)(4 * j + 8) * 8.0, (double)(6 * j + 10));
-        k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);
-      }
-      CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CKR(run_iteration(h, j, m1));
       CK(cudaStreamSynchronize(s));
       CK(cudaGetLastError());
       const double res = h->status_host[0], hn = h->status_host[1];
@@ -1904,10 +1996,6 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
         h->err = "FGMRES breakdown: non-finite Hessenberg entry";
         *iters = it;
         return STFEM_ERR_BREAKDOWN;
-      }
-      if (hn > 0.0) {
-        Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
-        k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
       }
       ++it;
       jlast = j;
@@ -2301,6 +2389,7 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
   }
   int form = p->patch_form;
   if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
+  CKR(prepare_stream_kernels(h));
   stfem::TimeDiag td;
   if (form == STFEM_PATCH_TIME_DIAGONAL) {
     std::string err;
@@ -2567,6 +2656,8 @@ void stfem_destroy(stfem_h h) {
   cudaDeviceSynchronize();
   for (void *p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  for (auto &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
 }

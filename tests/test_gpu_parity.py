@@ -231,3 +231,31 @@ def test_smoother_patch_forms(name, precision, patch_form, tol):
         err = _rel(host(d), ref)
         print(name, "smooth form", precision, patch_form, "level", l, err)
         assert err < tol
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_march_on_stream_uses_graphs(name, precision):
+    """On a non-default stream every FGMRES iteration runs from a captured CUDA
+    graph; the march must match the oracle as the eager path does, and the
+    launch accounting must keep counting the replayed kernels."""
+    import paper_2303_06742_gb300 as st
+    c = case(name)
+    O = pair(name)[2]
+    stream = torch.cuda.Stream()
+    S = st.Solver(gpu_problem(c), precision=precision, stream=stream)
+    st_ref, its_ref = O.march(2, 1e-10)
+    s = dev(np.zeros(S.n_state))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        S.initial_state(s)
+        l0 = S.launch_count()
+        rc, it = S.march(0, 2, s, tol=1e-10)
+        l1 = S.launch_count()
+    stream.synchronize()
+    err = _rel(host(s), np.concatenate(st_ref))
+    print(name, "graph march", precision, it, its_ref, err, l1 - l0)
+    assert rc == 0
+    assert err < (1e-9 if precision == 0 else 1e-7)
+    assert l1 - l0 > 20 * sum(it)
+    S.close()
