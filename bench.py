@@ -183,7 +183,7 @@ def kernel_source_hash():
 def dram_traffic(workload, precision):
     """Per-launch DRAM bytes of the patch-apply kernel from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "traffic_k_patch_apply_stream_%s.json" % workload)
     try:
         with open(p) as f:
             rec = json.load(f)
