@@ -30,10 +30,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "c2_2d_q3_k2_64"
-WORKLOAD_DESC = ("2D unit square 64x64, 5 GMG levels, Q3^2/Q2 Taylor-Hood, dG(2) (3 Radau nodes), "
-                 "tau=1e-3, lambda/mu log-uniform [0.5,50], kappa lognormal per cell (sigma=1), c0=1e-2, "
-                 "alpha=1, manufactured sine solution, Dirichlet (Nitsche) on all faces; "
-                 "N_slab=496,911; FGMRES(30) to 1e-8 relative")
+WORKLOAD_DESCS = {
+    "c2_2d_q3_k2_64": ("2D unit square 64x64, 5 GMG levels, Q3^2/Q2 Taylor-Hood, dG(2) (3 Radau nodes), "
+                       "tau=1e-3, lambda/mu log-uniform [0.5,50], kappa lognormal per cell (sigma=1), c0=1e-2, "
+                       "alpha=1, manufactured sine solution, Dirichlet (Nitsche) on all faces; "
+                       "N_slab=496,911; FGMRES(30) to 1e-8 relative"),
+    "c3_3d_q2_k1_16": ("3D unit cube 16^3, 4 GMG levels, Q2^3/Q1 Taylor-Hood, dG(1), tau=1e-2, thermoelastic "
+                       "set (alpha=0.5, c0=1, kappa=0.1, lambda=2, mu=1), manufactured sine solution, Dirichlet "
+                       "on all faces; N_slab=441,070; one right-hand side; FGMRES(30) to 1e-8 relative"),
+}
 
 
 def parse():
@@ -343,7 +348,7 @@ def gpu_arm(args):
     peak, peak_kind = peak_hbm()
     achieved = pa["bytes"] / (pa["ms"] / 1000.0) / 1e9 if pa["ms"] > 0 else None
     traffic = dram_traffic(args.workload, "mixed")
-    roof = {"kernel": "k_patch_apply_stream<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+    roof = {"kernel": "k_patch_apply_stream<float>", "workload": args.workload, "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
             "traffic": traffic,
             "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
@@ -381,7 +386,8 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": "FP32 V-cycle inside FP64 FGMRES",
+        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload),
+                   "precision": "FP32 V-cycle inside FP64 FGMRES",
                    "tol": tol, "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
                    "l2": "inputs larger than L2: %.2f GB of FP32 patch inverses streamed per sweep set"
                          % (sum(v["inv_bytes"] for v in info.values()) / 1e9),
@@ -431,7 +437,8 @@ def reference_arm(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": "FP64 (oracle)", "tol": c["tol"]},
+        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "precision": "FP64 (oracle)",
+                   "tol": c["tol"]},
         "cpu_baseline": {"value": value, "unit": "slab solves/s", "cores": 1, "kind": "oracle",
                          "sample": "each step: 2 FGMRES-GMG iterations of slab 0, scaled by the %d iterations "
                                    "of a full slab solve; oracle setup (%.1f s) excluded" % (iters, res["setup_s"])},

@@ -795,6 +795,56 @@ __global__ void __launch_bounds__(DOT_THREADS) k_multidot(int k, const double *_
   }
 }
 
+// w <- w - sum_v h[v] V_v, fused with the block partial sums of the next
+// Gram-Schmidt quantity: mode 0, partial[v][block] = V_v . w_new (v < k);
+// mode 1, partial[0][block] = w_new . w_new.  KB >= k bounds the register
+// accumulators.
+template <int KB>
+__global__ void __launch_bounds__(DOT_THREADS) k_axpy_dot(int k, const double *__restrict__ V, long ldV,
+                                                          const double *__restrict__ h, double *__restrict__ w,
+                                                          long n, double *__restrict__ partial, int mode) {
+  double acc[KB];
+#pragma unroll
+  for (int t = 0; t < KB; ++t) acc[t] = 0.0;
+  double hv[KB];
+#pragma unroll
+  for (int t = 0; t < KB; ++t) hv[t] = t < k ? h[t] : 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double vi[KB];
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      vi[t] = t < k ? V[(long)t * ldV + i] : 0.0;
+      s += hv[t] * vi[t];
+    }
+    const double wn = w[i] - s;
+    w[i] = wn;
+    if (mode == 0) {
+#pragma unroll
+      for (int t = 0; t < KB; ++t) acc[t] += vi[t] * wn;
+    } else {
+      acc[0] += wn * wn;
+    }
+  }
+  __shared__ double sm[KB][DOT_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nout = mode == 0 ? k : 1;
+#pragma unroll
+  for (int t = 0; t < KB; ++t) {
+    const double sv = warp_sum(acc[t]);
+    if (lane == 0) sm[t][warp] = sv;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      double sv = lane < DOT_THREADS / 32 ? sm[t][lane] : 0.0;
+      sv = warp_sum(sv);
+      if (lane == 0 && t < nout) partial[(long)t * gridDim.x + blockIdx.x] = sv;
+    }
+  }
+}
+
 // out[v] = sum_b partial[v][b] in a fixed order (one block per v).
 __global__ void k_reduce_partials(int nb, const double *__restrict__ partial, double *__restrict__ out) {
   __shared__ double sm[32];
@@ -1286,10 +1336,18 @@ TimeCoef<T> time_coef(const stfem::Temporal &Tm, double tau) {
   return tc;
 }
 
+// Lanes per node: the FP64 instance is bound by the FP64 pipe, so fewer lanes
+// (fewer FP64 shuffle-reduction adds); the FP32 instances are latency-bound,
+// so more lanes for the long 3D rows (up to 125 neighbours).
+template <typename T, int D>
+struct SpmvLanes {
+  static constexpr int G = sizeof(T) == 8 ? 2 : (D == 3 ? 8 : 4);
+};
+
 template <typename T, int Q, int D>
 void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
                     int mode) {
-  constexpr int G = 4;
+  constexpr int G = SpmvLanes<T, D>::G;
   const long threads = (L.nb.nu + L.nb.np) * G;
   k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256), 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode);
 }
@@ -1819,6 +1877,28 @@ void multidot(stfem_h h, int k, const double *V, long ldV, const double *w, long
   }
 }
 
+// w <- w - V h (k vectors), then out = V^T w (mode 0, k values) or
+// out = w . w (mode 1): one pass over V and w, fixed-order reduction.
+void axpy_dot(stfem_h h, int k, const double *V, long ldV, const double *hvec, double *w, long n, double *out,
+              int mode) {
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(k + 2) * n * 8.0, 2.0 * k * n * (mode == 0 ? 2 : 1) + 2.0 * n);
+    if (k <= 8)
+      k_axpy_dot<8><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+    else if (k <= 16)
+      k_axpy_dot<16><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+    else if (k <= 24)
+      k_axpy_dot<24><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+    else
+      k_axpy_dot<32><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+  }
+  {
+    const int nout = mode == 0 ? k : 1;
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)nout * DOT_BLOCKS * 8.0, (double)nout * DOT_BLOCKS);
+    k_reduce_partials<<<nout, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+  }
+}
+
 int read_scalar(stfem_h h, const double *dev, double *host) {
   CK(cudaMemcpyAsync(h->status_host, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1875,18 +1955,11 @@ int enqueue_iteration(stfem_h h, int j, int m1) {
   }
   double *w = h->w;
   launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
-  // classical Gram-Schmidt, applied twice
+  // classical Gram-Schmidt, applied twice: h1 = V^T w; w -= V h1 and
+  // h2 = V^T w in one pass; w -= V h2 and ||w||^2 in one pass
   multidot(h, j + 1, h->V, N, w, N, h->h1);
-  {
-    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
-    k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h1, w, N);
-  }
-  multidot(h, j + 1, h->V, N, w, N, h->h2);
-  {
-    Launch G_(h, STFEM_KCLASS_BLAS1, (double)(j + 3) * N * 8.0, 2.0 * (j + 1) * N);
-    k_multiaxpy<<<nb, 256, 0, s>>>(j + 1, h->V, N, h->h2, w, N);
-  }
-  multidot(h, 1, w, N, w, N, h->hn2);
+  axpy_dot(h, j + 1, h->V, N, h->h1, w, N, h->h2, 0);
+  axpy_dot(h, j + 1, h->V, N, h->h2, w, N, h->hn2, 1);
   {
     Launch G_(h, STFEM_KCLASS_OTHER, (double)(4 * j + 8) * 8.0, (double)(6 * j + 10));
     k_givens<<<1, 1, 0, s>>>(j, m1, h->h1, h->h2, h->hn2, h->H, h->cs, h->sn, h->g, h->hnorm, h->status);

@@ -257,5 +257,5 @@ def test_march_on_stream_uses_graphs(name, precision):
     print(name, "graph march", precision, it, its_ref, err, l1 - l0)
     assert rc == 0
     assert err < (1e-9 if precision == 0 else 1e-7)
-    assert l1 - l0 > 20 * sum(it)
+    assert l1 - l0 > 10 * sum(it)  # replayed kernels are counted
     S.close()
