@@ -57,15 +57,61 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 struct NodeBlockDev {
   long nu, np;
-  const int *uu_ptr, *uu_col;
-  const T *uu_m, *uu_k;
-  const int *up_ptr, *up_col;
-  const T *up_c;
-  const int *pu_ptr, *pu_col;
-  const T *pu_c;
-  const int *pp_ptr, *pp_col;
-  const T *pp_m, *pp_b;
+  int r;                       // displacement degree (pressure degree r - 1)
+  int n[3];                    // cells per axis of the level
+  int udims[3], pdims[3];      // lattice sizes of Q_r and Q_{r-1}
+  const int *uu_ptr, *up_ptr, *pu_ptr, *pp_ptr;
+  const T *uu_m, *uu_k, *up_c, *pu_c, *pp_m, *pp_b;
 };
+
+// Neighbour box of a node: the lattice nodes (degree m_col) of all cells that
+// hold the node (lattice coordinate a, degree m_row).  Every level operator
+// couples exactly within this box, so neighbour addresses are computed, not
+// loaded.
+struct Box3 {
+  int lo[3], ext[3];
+};
+
+__device__ __forceinline__ Box3 node_box(const int *a, int m_row, int m_col, const int *ncell, int dim) {
+  Box3 b;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      int clo, chi;
+      if (a[i] % m_row == 0) {
+        clo = max(a[i] / m_row - 1, 0);
+        chi = min(a[i] / m_row, ncell[i] - 1);
+      } else {
+        clo = chi = a[i] / m_row;
+      }
+      b.lo[i] = m_col * clo;
+      b.ext[i] = m_col * (chi + 1) - b.lo[i] + 1;
+    } else {
+      b.lo[i] = 0;
+      b.ext[i] = 1;
+    }
+  }
+  return b;
+}
+
+__device__ __forceinline__ long box_node(const Box3 &b, int e, const int *dims) {
+  const int ex = e % b.ext[0];
+  const int t = e / b.ext[0];
+  const int ey = t % b.ext[1], ez = t / b.ext[1];
+  return (long)(b.lo[0] + ex) + (long)dims[0] * ((b.lo[1] + ey) + (long)dims[1] * (b.lo[2] + ez));
+}
+
+__device__ __forceinline__ void lattice_coords(long idx, const int *dims, int dim, int *a) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      a[i] = (int)(idx % dims[i]);
+      idx /= dims[i];
+    } else {
+      a[i] = 0;
+    }
+  }
+}
 
 template <typename T, int Q, int D, int G>
 __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
@@ -82,16 +128,19 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
   const bool is_p = !is_u && node < A.nu + A.np;
   if (is_u) {
     // acc layout: [0] Mr U, [1] Mr V, [2] K U, [3] Ct P; each Q x D
-    const int e1 = A.uu_ptr[node + 1];
+    int a[3];
+    lattice_coords(node, A.udims, D, a);
+    const Box3 bu = node_box(a, A.r, A.r, A.n, D);
+    const int base = A.uu_ptr[node], e1 = A.uu_ptr[node + 1];
     // two neighbours per trip: their matrix and vector loads are independent
-    for (int e0 = A.uu_ptr[node] + lane; e0 < e1; e0 += 2 * G) {
+    for (int e0 = base + lane; e0 < e1; e0 += 2 * G) {
       const bool two = e0 + G < e1;
       const int eb[2] = {e0, two ? e0 + G : e0};
       long J[2];
       T m[2], k[2][D * D];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        J[t] = A.uu_col[eb[t]];
+        J[t] = box_node(bu, eb[t] - base, A.udims);
         m[t] = (t == 0 || two) ? A.uu_m[eb[t]] : T(0);
 #pragma unroll
         for (int i = 0; i < D * D; ++i) k[t][i] = (t == 0 || two) ? A.uu_k[(long)eb[t] * D * D + i] : T(0);
@@ -119,9 +168,10 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
           }
       }
     }
-    const int f1 = A.up_ptr[node + 1];
-    for (int e = A.up_ptr[node] + lane; e < f1; e += G) {
-      const long sI = A.up_col[e];
+    const Box3 bp = node_box(a, A.r, A.r - 1, A.n, D);
+    const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long sI = box_node(bp, e - f0, A.pdims);
       T ct[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
@@ -135,9 +185,12 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
   } else if (is_p) {
     // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V
     const long sI = node - A.nu;
-    const int e1 = A.pp_ptr[sI + 1];
-    for (int e = A.pp_ptr[sI] + lane; e < e1; e += G) {
-      const long s2 = A.pp_col[e];
+    int a[3];
+    lattice_coords(sI, A.pdims, D, a);
+    const Box3 bp = node_box(a, A.r - 1, A.r - 1, A.n, D);
+    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
+    for (int e = e0p + lane; e < e1; e += G) {
+      const long s2 = box_node(bp, e - e0p, A.pdims);
       const T m = A.pp_m[e], bb = A.pp_b[e];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
@@ -146,9 +199,10 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
         acc[Q + a] += bb * pv;
       }
     }
-    const int f1 = A.pu_ptr[sI + 1];
-    for (int e = A.pu_ptr[sI] + lane; e < f1; e += G) {
-      const long J = A.pu_col[e];
+    const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
+    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long J = box_node(bu, e - f0, A.udims);
       T cn[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
@@ -1383,125 +1437,177 @@ void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *
   }
 }
 
-// Node-block arrays of a level, decoded from the spatial system CSR (whose
-// blocks have the structure of Eq. 4.7); checks that structure.
+// Node-block arrays of a level in box order, decoded from the spatial system
+// CSR (whose blocks have the structure of Eq. 4.7).  Every entry must lie in
+// the node's neighbour box (checked); box positions without an entry are
+// stored as zeros.
 struct NodeBlockHost {
   long nu = 0, np = 0;
-  std::vector<int> uu_ptr, uu_col, up_ptr, up_col, pu_ptr, pu_col, pp_ptr, pp_col;
+  std::vector<int> uu_ptr, up_ptr, pu_ptr, pp_ptr;
   std::vector<double> uu_m, uu_k, up_c, pu_c, pp_m, pp_b;
 };
+
+struct HostBox {
+  int lo[3], ext[3];
+  long size;
+};
+
+static HostBox host_box(const int *a, int m_row, int m_col, const int *ncell, int dim) {
+  HostBox b;
+  b.size = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      int clo, chi;
+      stfem::cells_of(a[i], m_row, ncell[i], &clo, &chi);
+      b.lo[i] = m_col * clo;
+      b.ext[i] = m_col * (chi + 1) - b.lo[i] + 1;
+    } else {
+      b.lo[i] = 0;
+      b.ext[i] = 1;
+    }
+    b.size *= b.ext[i];
+  }
+  return b;
+}
+
+// position of lattice node j (flat index in `dims`) in box b, or -1
+static long box_pos(const HostBox &b, long j, const int *dims, int dim) {
+  long pos = 0, stride = 1;
+  for (int i = 0; i < 3; ++i) {
+    int c = 0;
+    if (i < dim) {
+      c = (int)(j % dims[i]);
+      j /= dims[i];
+    }
+    const int o = c - b.lo[i];
+    if (o < 0 || o >= b.ext[i]) return -1;
+    pos += o * stride;
+    stride *= b.ext[i];
+  }
+  return pos;
+}
+
+static void coords_of(long idx, const int *dims, int dim, int *a) {
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      a[i] = (int)(idx % dims[i]);
+      idx /= dims[i];
+    } else {
+      a[i] = 0;
+    }
+  }
+}
 
 int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *err) {
   NodeBlockHost &H = *out;
   const long R = L.R, S = L.S, nu = R / d, np = S;
+  const int r = L.r;
+  const int *ud = L.U.dims, *pd = L.P.dims, *nc = L.box.n;
   H.nu = nu;
   H.np = np;
   H.uu_ptr.assign(nu + 1, 0);
   H.up_ptr.assign(nu + 1, 0);
   H.pu_ptr.assign(np + 1, 0);
   H.pp_ptr.assign(np + 1, 0);
+  int a[3];
+  for (long I = 0; I < nu; ++I) {
+    coords_of(I, ud, d, a);
+    H.uu_ptr[I + 1] = H.uu_ptr[I] + (int)host_box(a, r, r, nc, d).size;
+    H.up_ptr[I + 1] = H.up_ptr[I] + (int)host_box(a, r, r - 1, nc, d).size;
+  }
+  for (long sI = 0; sI < np; ++sI) {
+    coords_of(sI, pd, d, a);
+    H.pu_ptr[sI + 1] = H.pu_ptr[sI] + (int)host_box(a, r - 1, r, nc, d).size;
+    H.pp_ptr[sI + 1] = H.pp_ptr[sI] + (int)host_box(a, r - 1, r - 1, nc, d).size;
+  }
+  H.uu_m.assign(H.uu_ptr[nu], 0.0);
+  H.uu_k.assign((size_t)H.uu_ptr[nu] * d * d, 0.0);
+  H.up_c.assign((size_t)H.up_ptr[nu] * d, 0.0);
+  H.pu_c.assign((size_t)H.pu_ptr[np] * d, 0.0);
+  H.pp_m.assign(H.pp_ptr[np], 0.0);
+  H.pp_b.assign(H.pp_ptr[np], 0.0);
   double scale = 0.0;
   for (double v : L.v1) scale = std::max(scale, std::fabs(v));
   for (double v : L.v2) scale = std::max(scale, std::fabs(v));
   const double tol = 1e-12 * scale;
-  std::vector<int> pos(nu, -1);
+  auto bad = [&](const char *what) {
+    *err = std::string("level operator does not have the expected block/box structure: ") + what;
+    return STFEM_ERR_STATE;
+  };
   for (long I = 0; I < nu; ++I) {
-    // u-equation row (I, 0): the U block holds rho M_IJ in v1
-    const long ru = I * d;
-    const int first = (int)H.uu_col.size();
-    for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
-      const long c = L.col[e];
-      if (c >= R && c < 2 * R && (c - R) % d == 0) {
-        pos[(c - R) / d] = (int)H.uu_col.size() - first;
-        H.uu_col.push_back((int)((c - R) / d));
-        H.uu_m.push_back(L.v1[e]);
+    coords_of(I, ud, d, a);
+    const HostBox bu = host_box(a, r, r, nc, d), bp = host_box(a, r, r - 1, nc, d);
+    for (int c = 0; c < d; ++c) {
+      // u-equation row (I, c): V block -rho M (W), U block rho M (Dt), same component
+      const long ru = I * d + c;
+      for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
+        const long col = L.col[e];
+        if (col >= 2 * R) {
+          if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) return bad("u-equation couples to P");
+          continue;
+        }
+        const long blk = col / R, rem = col % R, J = rem / d;
+        const long pos = box_pos(bu, J, ud, d);
+        if (pos < 0 || rem % d != c) return bad("u-equation entry outside the box");
+        const size_t at = (size_t)H.uu_ptr[I] + pos;
+        if (blk == 1) {
+          if (c == 0) H.uu_m[at] = L.v1[e];
+          else if (std::fabs(L.v1[e] - H.uu_m[at]) > tol) return bad("u-equation mass differs between components");
+          if (std::fabs(L.v2[e]) > tol) return bad("u-equation U block has a W part");
+        } else if (std::fabs(L.v1[e]) > tol) {
+          return bad("u-equation V block has a Dt part");
+        }
       }
     }
-    const int cnt = (int)H.uu_col.size() - first;
-    H.uu_ptr[I + 1] = (int)H.uu_col.size();
-    H.uu_k.resize(H.uu_col.size() * d * d, 0.0);
-    // v-equation rows (I, c): U block -> K[c][c'] in v2, P block -> C^T in v2
-    std::vector<int> pcols;
     for (int c = 0; c < d; ++c) {
+      const long ru = I * d + c;
+      for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
+        const long col = L.col[e];
+        if (col < R) {
+          const size_t at = (size_t)H.uu_ptr[I] + box_pos(bu, col / d, ud, d);
+          if (std::fabs(L.v2[e] + H.uu_m[at]) > tol) return bad("u-equation V block is not -rho M");
+        }
+      }
+      // v-equation row (I, c)
       const long rv = R + I * d + c;
-      int pk = 0;
       for (int e = L.rowptr[rv]; e < L.rowptr[rv + 1]; ++e) {
         const long col = L.col[e];
         if (col < R) {
-          const long J = col / d;
-          if (col % d != c || pos[J] < 0 || std::fabs(L.v1[e] - H.uu_m[first + pos[J]]) > tol ||
-              std::fabs(L.v2[e]) > tol) {
-            *err = "unexpected structure in the v-equation rows";
-            return STFEM_ERR_STATE;
-          }
+          const long pos = box_pos(bu, col / d, ud, d);
+          if (pos < 0 || col % d != c) return bad("v-equation V entry outside the box");
+          if (std::fabs(L.v1[e] - H.uu_m[(size_t)H.uu_ptr[I] + pos]) > tol || std::fabs(L.v2[e]) > tol)
+            return bad("v-equation V block is not rho M");
         } else if (col < 2 * R) {
-          const long J = (col - R) / d;
-          const int cp = (int)((col - R) % d);
-          if (pos[J] < 0 || std::fabs(L.v1[e]) > tol) {
-            *err = "unexpected structure in the elasticity block";
-            return STFEM_ERR_STATE;
-          }
-          H.uu_k[((size_t)first + pos[J]) * d * d + c * d + cp] = L.v2[e];
+          const long pos = box_pos(bu, (col - R) / d, ud, d);
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("elasticity entry outside the box");
+          H.uu_k[((size_t)H.uu_ptr[I] + pos) * d * d + c * d + (col - R) % d] = L.v2[e];
         } else {
-          if (c == 0) {
-            pcols.push_back((int)(col - 2 * R));
-            for (int cc = 0; cc < d; ++cc) H.up_c.push_back(0.0);
-          }
-          if (pk >= (int)pcols.size() || pcols[pk] != (int)(col - 2 * R)) {
-            *err = "unexpected pressure coupling pattern";
-            return STFEM_ERR_STATE;
-          }
-          H.up_c[(H.up_col.size() + pk) * d + c] = L.v2[e];
-          ++pk;
+          const long pos = box_pos(bp, col - 2 * R, pd, d);
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("coupling entry outside the box");
+          H.up_c[((size_t)H.up_ptr[I] + pos) * d + c] = L.v2[e];
         }
       }
     }
-    for (int sc : pcols) H.up_col.push_back(sc);
-    H.up_ptr[I + 1] = (int)H.up_col.size();
-    // the u-equation's V block must be -rho M (times W)
-    for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
-      const long c = L.col[e];
-      if (c < R) {
-        const long J = c / d;
-        if (pos[J] < 0 || std::fabs(L.v2[e] + H.uu_m[first + pos[J]]) > tol || std::fabs(L.v1[e]) > tol) {
-          *err = "unexpected structure in the u-equation rows";
-          return STFEM_ERR_STATE;
-        }
-      }
-    }
-    for (int t = first; t < first + cnt; ++t) pos[H.uu_col[t]] = -1;
   }
   for (long sI = 0; sI < np; ++sI) {
+    coords_of(sI, pd, d, a);
+    const HostBox bu = host_box(a, r - 1, r, nc, d), bp = host_box(a, r - 1, r - 1, nc, d);
     const long rp = 2 * R + sI;
-    std::vector<double> cn;
-    std::vector<int> jl;
     for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
       const long col = L.col[e];
       if (col < R) {
-        const long J = col / d;
-        const int c = (int)(col % d);
-        if (jl.empty() || jl.back() != (int)J) {
-          jl.push_back((int)J);
-          for (int cc = 0; cc < d; ++cc) cn.push_back(0.0);
-        }
-        cn[(jl.size() - 1) * d + c] = L.v2[e];
-        if (std::fabs(L.v1[e]) > tol) {
-          *err = "unexpected structure in the p-equation rows";
-          return STFEM_ERR_STATE;
-        }
+        const long pos = box_pos(bu, col / d, ud, d);
+        if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("p-equation V entry outside the box");
+        H.pu_c[((size_t)H.pu_ptr[sI] + pos) * d + col % d] = L.v2[e];
       } else if (col >= 2 * R) {
-        H.pp_col.push_back((int)(col - 2 * R));
-        H.pp_m.push_back(L.v1[e]);
-        H.pp_b.push_back(L.v2[e]);
+        const long pos = box_pos(bp, col - 2 * R, pd, d);
+        if (pos < 0) return bad("p-equation P entry outside the box");
+        H.pp_m[(size_t)H.pp_ptr[sI] + pos] = L.v1[e];
+        H.pp_b[(size_t)H.pp_ptr[sI] + pos] = L.v2[e];
       } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
-        *err = "p-equation couples to U";
-        return STFEM_ERR_STATE;
+        return bad("p-equation couples to U");
       }
     }
-    for (size_t t = 0; t < jl.size(); ++t) H.pu_col.push_back(jl[t]);
-    H.pu_c.insert(H.pu_c.end(), cn.begin(), cn.end());
-    H.pu_ptr[sI + 1] = (int)H.pu_col.size();
-    H.pp_ptr[sI + 1] = (int)H.pp_col.size();
   }
   return 0;
 }
@@ -1522,25 +1628,26 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   NodeBlockDev<T> &nb = D.nb;
   nb.nu = H.nu;
   nb.np = H.np;
+  nb.r = L.r;
+  for (int i = 0; i < 3; ++i) {
+    nb.n[i] = L.box.n[i];
+    nb.udims[i] = L.U.dims[i];
+    nb.pdims[i] = L.P.dims[i];
+  }
   int *ip;
   T *tp;
   CKR(upload(h, &ip, H.uu_ptr)); nb.uu_ptr = ip;
-  CKR(upload(h, &ip, H.uu_col)); nb.uu_col = ip;
   CKR(upload(h, &tp, H.uu_m)); nb.uu_m = tp;
   CKR(upload(h, &tp, H.uu_k)); nb.uu_k = tp;
   CKR(upload(h, &ip, H.up_ptr)); nb.up_ptr = ip;
-  CKR(upload(h, &ip, H.up_col)); nb.up_col = ip;
   CKR(upload(h, &tp, H.up_c)); nb.up_c = tp;
   CKR(upload(h, &ip, H.pu_ptr)); nb.pu_ptr = ip;
-  CKR(upload(h, &ip, H.pu_col)); nb.pu_col = ip;
   CKR(upload(h, &tp, H.pu_c)); nb.pu_c = tp;
   CKR(upload(h, &ip, H.pp_ptr)); nb.pp_ptr = ip;
-  CKR(upload(h, &ip, H.pp_col)); nb.pp_col = ip;
   CKR(upload(h, &tp, H.pp_m)); nb.pp_m = tp;
   CKR(upload(h, &tp, H.pp_b)); nb.pp_b = tp;
-  const double nuu = H.uu_col.size(), nup = H.up_col.size(), npu = H.pu_col.size(), npp = H.pp_col.size();
-  D.nb_bytes = (nuu * (1 + d * d) + nup * d + npu * d + npp * 2) * sizeof(T) + (nuu + nup + npu + npp) * 4.0 +
-               (2.0 * H.nu + 2.0 * H.np + 4) * 4.0;
+  const double nuu = H.uu_m.size(), nup = H.up_c.size() / d, npu = H.pu_c.size() / d, npp = H.pp_m.size();
+  D.nb_bytes = (nuu * (1 + d * d) + nup * d + npu * d + npp * 2) * sizeof(T) + (2.0 * H.nu + 2.0 * H.np + 4) * 4.0;
   D.nb_flops = 2.0 * (nuu * (2 * d + d * d) + nup * d + npu * d + npp * 2);
   D.nnz = (long long)L.col.size();
   CKR(dalloc(h, &D.b, D.N));
