@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--sweeps", type=int, default=1, help="pre- and post-smoothing sweeps per level")
+    p.add_argument("--requests", type=int, default=64, help="requests of the serving workload")
+    p.add_argument("--workers", type=int, default=8, help="concurrent requests of the serving workload")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -447,8 +449,57 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ serving arm
+def serving_arm(args):
+    """Serving stream: requests arrive by a Poisson process and are admitted by
+    HBM footprint; reports slab throughput, request and slab latencies."""
+    import torch
+    import paper_2303_06742_gb300 as st
+    import inputs
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _cases import gpu_problem
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = inputs.serving_stream(args.requests)
+    probs = [gpu_problem(c) for c in reqs]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    S = st.Server(hbm_budget=budget, n_workers=args.workers)
+    t0 = time.perf_counter()
+    ids = []
+    for p, c in zip(probs, reqs):
+        wait = c["arrival"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(S.submit(p, c["slabs"], tol=c["tol"]))
+    res = [S.result(i) for i in ids]
+    makespan = max(r[0]["t_done"] for r in res) - min(r[0]["t_submit"] for r in res)
+    S.close()
+    if rank != 0:
+        return
+    slabs = sum(r[0]["n_slabs"] for r in res)
+    lat = [r[0]["t_done"] - r[0]["t_submit"] for r in res]
+    setup = [r[0]["t_ready"] - r[0]["t_admit"] for r in res]
+    slab_ms = [x for r in res for x in r[2]]
+    print(json.dumps({
+        "metric": "slab solves/s", "value": slabs / makespan, "unit": "slab solves/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving stream: %d 2D requests, Poisson arrivals (mean 2 ms), meshes "
+                               "{16,32,64,128}^2, (Q2/Q1,k=1) or (Q3/Q2,k=2), 5-50 slabs, random materials; "
+                               "%d workers, HBM budget %.0f GB" % (len(reqs), args.workers, budget / 1e9)},
+        "requests": len(reqs), "slabs": slabs, "makespan_s": makespan,
+        "request_latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+        "slab_latency_ms": {"p50": pct(slab_ms, 50), "p99": pct(slab_ms, 99)},
+        "setup_s": {"p50": pct(setup, 50), "p99": pct(setup, 99)},
+        "status": sorted(set(r[0]["status"] for r in res)),
+    }))
+
+
 def main():
     args = parse()
+    if args.workload == "serving" and not args.cpu_leg:
+        serving_arm(args)
+        return
     if args.cpu_leg:
         oracle_leg(args.workload, args.cpu_leg, "reference" if args.impl == "reference" else "solve",
                    args.steps, args.warmup)

@@ -242,6 +242,67 @@ int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, d
 /* Number of kernels the handle has launched since it was created. */
 int stfem_launch_count(stfem_h h, long long *n);
 
+/* Device bytes the handle has allocated (matrices, patch inverses, Krylov
+ * and level work vectors). */
+int stfem_footprint_bytes(stfem_h h, long long *bytes);
+
+/* Upper estimate of the device bytes of a handle for these arguments, after
+ * stfem_gmg_setup with `gmg` and FGMRES restart `restart`, computed from the
+ * sizes alone (no setup, no GPU).  Used to admit requests by HBM footprint. */
+int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_gmg_params *gmg,
+                         int restart, long long *bytes);
+
+/* ---- Serving loop ----
+ * A request is one march (slabs 0..n_slabs-1 from the initial state of its
+ * problem).  Requests are submitted as they arrive; the server admits them
+ * in arrival order, skipping over requests that do not fit, while the sum of
+ * the footprint estimates of running requests stays within the HBM budget
+ * and a worker is free.  Each worker thread owns one handle and one CUDA
+ * stream at a time, so admitted requests run concurrently on the device, each
+ * keeping its GMG hierarchy and Krylov state resident until its march ends.
+ * Results are bitwise the same as a request run alone (all kernels are
+ * deterministic and handles share nothing on the device).  Host arrays of the
+ * request are copied at submit.  Times are seconds since the server was
+ * created. */
+typedef struct stfem_server_ctx *stfem_server;
+
+typedef struct {
+  stfem_mesh mesh;
+  stfem_degrees deg;
+  stfem_material mat; /* per-cell arrays are copied at submit */
+  stfem_bcs bcs;
+  double tau;
+  stfem_gmg_params gmg;
+  int n_slabs;
+  double tol;
+  int restart;
+  int max_it;
+} stfem_request;
+
+typedef struct {
+  int status;             /* worst march status, or a negative error code */
+  int n_slabs;
+  long long n_state;      /* length of the end state */
+  long long footprint;    /* estimate used for admission */
+  long long device_bytes; /* bytes the handle actually allocated */
+  int iters_total;
+  double t_submit, t_admit, t_ready, t_done; /* ready = setup finished */
+} stfem_result;
+
+/* n_workers concurrent requests at most; hbm_budget bytes of footprint. */
+int stfem_server_create(long long hbm_budget, int n_workers, stfem_server *out);
+/* Queues a request; *id identifies it.  STFEM_ERR_ARG if its footprint
+ * estimate exceeds the whole budget. */
+int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id);
+/* Waits up to timeout_s seconds (< 0: forever) for request id.  Returns
+ * STFEM_OK when done (info filled; end_state_host, if not NULL, receives the
+ * n_state end state; slab_ms_host, if not NULL, the n_slabs per-slab times),
+ * STFEM_NOT_CONVERGED if still running at the timeout. */
+int stfem_server_result(stfem_server s, long long id, double timeout_s, stfem_result *info,
+                        double *end_state_host, double *slab_ms_host);
+/* Waits for all requests, stops the workers and frees everything. */
+void stfem_server_destroy(stfem_server s);
+
 /* ---- Allocation-free smoothing ----
  * No counterpart in the paper: an interface for callers that must not
  * allocate device memory at call time, e.g. code that runs while a CUDA stream
@@ -274,8 +335,8 @@ int stfem_smooth_noalloc(stfem_h h, int level, const double *b, double *d, int n
  * These rebuild the hierarchy on the host from the same arguments as
  * stfem_setup and return what the GPU path would upload.  Two-call pattern:
  * with NULL output arrays only the sizes are returned.  Arrays are host
- * memory owned by the caller.  Errors as stfem_setup (message via
- * stfem_last_error(NULL)). */
+ * memory owned by the caller.  Error codes as stfem_setup; the message is
+ * available from stfem_host_last_error() on the calling thread. */
 
 /* Slab matrix A_l of level l (l = -1: finest) in CSR form, paper order
  * (Eqs. 4.4-4.7): A_l = Dt (x) S1 + diag(W) (x) S2, expanded. */
@@ -300,8 +361,8 @@ int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, co
  * Dt[b*q+a] (row-major) for dG(k), q = k+1 (Eq. 2.4). */
 int stfem_host_temporal(int k, double *t_host, double *w_host, double *chi_host, double *Dt_host);
 
-/* Message of the last error on this handle (or of the last failed
- * stfem_setup when h is NULL). */
+/* Message of the last error on this handle (or, when h is NULL, of the last
+ * failed stfem_setup made by the calling thread). */
 const char *stfem_last_error(stfem_h h);
 
 /* Message of the last failed stfem_host_* call on this thread. */

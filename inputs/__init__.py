@@ -60,3 +60,28 @@ def layered(n, top_z_split):
         kap[sl] = 1e-3 if upper else 1.0
         mu[sl] = 10.0 if upper else 1.0
     return kap, mu
+
+
+def serving_stream(n_requests=256, seed=SEED, mean_gap_s=2e-3, meshes=(16, 32, 64, 128),
+                   degrees=((2, 1), (3, 2)), slabs=(5, 50)):
+    """Request stream of the serving workload: Poisson arrivals (exponential
+    gaps, mean 2 ms), square 2D meshes drawn uniformly from `meshes` (GMG down
+    to 4x4), (r, k) uniformly from `degrees`, the slab count uniform in
+    `slabs`, materials drawn as for the 64x64 workload (lambda, mu
+    log-uniform in [0.5, 50] per request, kappa lognormal per cell,
+    c0 = 1e-2, tau = 1e-3), the sine manufactured solution, tol 1e-8."""
+    rng = np.random.default_rng(seed + 4)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += float(rng.exponential(mean_gap_s))
+        n = int(rng.choice(meshes))
+        r, k = degrees[int(rng.integers(len(degrees)))]
+        levels = int(round(np.log2(n / 4))) + 1
+        lam = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        mu = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+        kap = np.exp(rng.standard_normal(n * n))
+        out.append(dict(arrival=t, dim=2, n=n, levels=levels, r=r, k=k, tau=1e-3,
+                        slabs=int(rng.integers(slabs[0], slabs[1] + 1)), rho=1.0, alpha=1.0, c0=1e-2,
+                        lam=lam, mu=mu, kappa_cell=kap, problem="sin", tol=1e-8))
+    return out

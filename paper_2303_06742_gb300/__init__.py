@@ -60,6 +60,19 @@ class GmgParams(C.Structure):
     _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int), ("patch_form", C.c_int)]
 
 
+class Request(C.Structure):
+    _fields_ = [("mesh", Mesh), ("deg", Degrees), ("mat", Material), ("bcs", BCs), ("tau", C.c_double),
+                ("gmg", GmgParams), ("n_slabs", C.c_int), ("tol", C.c_double), ("restart", C.c_int),
+                ("max_it", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_slabs", C.c_int), ("n_state", C.c_longlong),
+                ("footprint", C.c_longlong), ("device_bytes", C.c_longlong), ("iters_total", C.c_int),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_ready", C.c_double),
+                ("t_done", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libstfem.so is not built; run `python paper_2303_06742_gb300/build.py` "
@@ -93,6 +106,11 @@ def _load():
                                     C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pLL, pI, pD],
         "stfem_host_temporal": [I, pD, pD, pD, pD],
         "stfem_profile": [P, I],
+        "stfem_footprint_bytes": [P, pLL],
+        "stfem_estimate_bytes": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(GmgParams), I, pLL],
+        "stfem_server_create": [LL, I, C.POINTER(P)],
+        "stfem_server_submit": [P, C.POINTER(Request), pLL],
+        "stfem_server_result": [P, LL, D, C.POINTER(Result), pD, pD],
         "stfem_profile_read": [P, I, pLL, pD, pD, pD],
         "stfem_launch_count": [P, pLL],
     }
@@ -106,6 +124,8 @@ def _load():
     lib.stfem_host_last_error.restype = C.c_char_p
     lib.stfem_destroy.argtypes = [P]
     lib.stfem_destroy.restype = None
+    lib.stfem_server_destroy.argtypes = [P]
+    lib.stfem_server_destroy.restype = None
     return lib
 
 
@@ -307,6 +327,11 @@ class Solver:
             out[name] = dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
         return out
 
+    def footprint_bytes(self):
+        n = C.c_longlong()
+        self._check(lib.stfem_footprint_bytes(self.h, C.byref(n)))
+        return n.value
+
     def launch_count(self):
         n = C.c_longlong()
         self._check(lib.stfem_launch_count(self.h, C.byref(n)))
@@ -316,3 +341,59 @@ class Solver:
         iters = (C.c_int * max(n_slabs, 1))()
         rc = self._check(lib.march(self.h, first_slab, n_slabs, _ptr(state), tol, restart, max_it, iters))
         return rc, list(iters)[:n_slabs]
+
+
+def estimate_bytes(prob, precision=FP64, patch_form=PATCH_AUTO, restart=30, n_sweeps=1, omega=0.7):
+    n = C.c_longlong()
+    _host_check(lib.stfem_estimate_bytes(C.byref(prob.mesh), C.byref(prob.deg),
+                                         C.byref(GmgParams(omega, n_sweeps, precision, patch_form)), restart,
+                                         C.byref(n)))
+    return n.value
+
+
+class Server:
+    """The serving loop: requests (marches) admitted by HBM footprint and run
+    concurrently by `n_workers` threads, each with its own handle and stream."""
+
+    def __init__(self, hbm_budget, n_workers):
+        s = C.c_void_p()
+        rc = lib.stfem_server_create(int(hbm_budget), int(n_workers), C.byref(s))
+        if rc < 0:
+            raise StfemError(rc, "server creation failed")
+        self.s = s
+        self._keep = {}
+
+    def submit(self, prob, n_slabs, tol=1e-8, precision=MIXED, restart=30, max_it=500, omega=0.7, n_sweeps=1,
+               patch_form=PATCH_AUTO):
+        req = Request(prob.mesh, prob.deg, prob.mat, prob.bcs, prob.tau,
+                      GmgParams(omega, n_sweeps, precision, patch_form), n_slabs, tol, restart, max_it)
+        i = C.c_longlong()
+        rc = lib.stfem_server_submit(self.s, C.byref(req), C.byref(i))
+        if rc < 0:
+            raise StfemError(rc, "request rejected (footprint above the budget or bad arguments)")
+        return i.value
+
+    def result(self, rid, timeout=-1.0):
+        """(info dict, end state, per-slab ms) once the request is done; None on timeout."""
+        info = Result()
+        rc = lib.stfem_server_result(self.s, rid, float(timeout), C.byref(info), None, None)
+        if rc == NOT_CONVERGED:
+            return None
+        if rc < 0:
+            raise StfemError(rc, "unknown request")
+        state = np.zeros(info.n_state)
+        slab = np.zeros(max(info.n_slabs, 1))
+        lib.stfem_server_result(self.s, rid, -1.0, C.byref(info), _dptr(state), _dptr(slab))
+        d = {f: getattr(info, f) for f, _ in Result._fields_}
+        return d, state, slab[:info.n_slabs]
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib.stfem_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -27,18 +27,19 @@ def _nvcc():
 def commands():
     nvcc = _nvcc()
     inc = "-I" + os.path.join(ROOT, "include")
-    cxx = ["g++", "-O3", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function", inc, "-c"]
+    cxx = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Wall", "-Wno-unused-function", inc, "-c"]
     objs = []
     cmds = []
-    for src in ("fem.cpp", "host_api.cpp"):
+    cuda_inc = "-I" + os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
+    for src in ("fem.cpp", "host_api.cpp", "server.cpp"):
         o = os.path.join(OUT, src + ".o")
-        cmds.append(cxx + [os.path.join(CSRC, src), "-o", o])
+        cmds.append(cxx[:-1] + [cuda_inc, "-c", os.path.join(CSRC, src), "-o", o])
         objs.append(o)
     o = os.path.join(OUT, "stfem.cu.o")
     cmds.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", inc,
                  "-c", os.path.join(CSRC, "stfem.cu"), "-o", o])
     objs.append(o)
-    link = [nvcc, ARCH, "-shared", "-o", LIB] + objs + ["-lpthread"]
+    link = [nvcc, ARCH, "-shared", "-o", LIB] + objs + ["-lpthread", "-lgomp"]
     return cmds, link
 
 

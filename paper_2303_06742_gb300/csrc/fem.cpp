@@ -874,6 +874,9 @@ int n_threads() {
 
 bool invert(double *a, int n) {
   std::vector<int> piv(n);
+  // large matrices (the coarse level): the row updates of each pivot step
+  // run in parallel; patch matrices are inverted one per thread instead
+  const bool par = n >= 512;
   for (int k = 0; k < n; ++k) {
     int p = k;
     double best = std::fabs(a[(size_t)k * n + k]);
@@ -892,6 +895,7 @@ bool invert(double *a, int n) {
     const double inv = 1.0 / rk[k];
     rk[k] = 1.0;
     for (int j = 0; j < n; ++j) rk[j] *= inv;
+#pragma omp parallel for schedule(static) if (par)
     for (int i = 0; i < n; ++i) {
       if (i == k) continue;
       double *ri = a + (size_t)i * n;

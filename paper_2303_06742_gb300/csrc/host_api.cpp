@@ -3,6 +3,8 @@
 // the setup can be checked without a GPU.
 #include "fem.hpp"
 
+#include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -107,6 +109,102 @@ int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, co
     col[i] = P.col[i];
     val[i] = P.val[i];
   }
+  return STFEM_OK;
+}
+
+// Upper estimate of a handle's device bytes from the sizes alone: every
+// array stfem_setup and stfem_gmg_setup allocate, with the neighbour boxes
+// and patch sizes counted exactly per node / per vertex and the largest
+// possible box for the level operators.
+int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_gmg_params *gmg,
+                         int restart, long long *bytes) {
+  if (!mesh || !deg || !gmg || !bytes || restart < 1) {
+    g_host_err = "null argument";
+    return STFEM_ERR_ARG;
+  }
+  const int d = mesh->dim, r = deg->r, q = deg->k + 1, L = mesh->n_levels;
+  if ((d != 2 && d != 3) || r < 2 || q < 1 || q > 5 || L < 1) {
+    g_host_err = "invalid sizes";
+    return STFEM_ERR_ARG;
+  }
+  const bool mixed = gmg->precision == STFEM_MIXED;
+  int form = gmg->patch_form;
+  if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
+  const double sp = mixed ? 4.0 : 8.0; // V-cycle precision
+  const int vec = mixed ? 4 : 2;
+  const int nr = q % 2, nc = q / 2;
+  double total = 0.0;
+  long nfine[3] = {1, 1, 1};
+  for (int i = 0; i < d; ++i) nfine[i] = mesh->n_cells[i];
+  double Nfine = 0.0, ns_fine = 0.0, ncell_fine = 1.0;
+  for (int l = L - 1; l >= 0; --l) {
+    long n[3] = {1, 1, 1};
+    double nu = 1, np = 1, nv = 1, ncell = 1;
+    for (int i = 0; i < d; ++i) {
+      n[i] = nfine[i] >> (L - 1 - l);
+      nu *= r * n[i] + 1;
+      np *= (r - 1) * n[i] + 1;
+      nv *= n[i] + 1;
+      ncell *= n[i];
+    }
+    const double ns = 2.0 * d * nu + np, N = q * ns;
+    if (l == L - 1) {
+      Nfine = N;
+      ns_fine = ns;
+      ncell_fine = ncell;
+    }
+    // node-block operator (largest boxes): FP64 always, FP32 copy in mixed mode
+    const double b1 = std::pow(2 * r + 1, d), b2 = std::pow(2 * r - 1, d);
+    const double mat = nu * b1 * (1 + d * d) + nu * b2 * d + np * b1 * d + np * b2 * 2;
+    total += mat * 8.0 + (nu + np + 2) * 8.0 + 3.0 * N * 8.0;
+    if (mixed) total += mat * 4.0 + (nu + np + 2) * 8.0 + 3.0 * N * 4.0;
+    // transfers to the next coarser level (P and P^T, both precisions)
+    if (l >= 1) {
+      const double tr = (nu * std::pow(r + 1, d) + np * std::pow(r, d)) * 2.0;
+      total += tr * (4.0 + 8.0) + 2.0 * (nu + np + 2) * 4.0;
+      if (mixed) total += tr * (4.0 + 4.0) + 2.0 * (nu + np + 2) * 4.0;
+    }
+    // patches (levels >= 1): exact patch sizes per vertex
+    if (l >= 1) {
+      auto axis_nodes = [](long v, long ncl, int m) {
+        const long c0 = std::max(v - 1, 0L), c1 = std::min(v, ncl - 1);
+        const long alo = m * c0, ahi = m * (c1 + 1);
+        const long lo = (c0 == 0) ? alo : alo + 1, hi = (c1 == ncl - 1) ? ahi : ahi - 1;
+        return (double)(hi - lo + 1);
+      };
+      double inv = 0.0, sumC = 0.0;
+      long vx = n[0] + 1, vy = d > 1 ? n[1] + 1 : 1, vz = d > 2 ? n[2] + 1 : 1;
+      for (long z = 0; z < vz; ++z)
+        for (long y = 0; y < vy; ++y)
+          for (long x = 0; x < vx; ++x) {
+            double u = axis_nodes(x, n[0], r), pp = axis_nodes(x, n[0], r - 1);
+            if (d > 1) {
+              u *= axis_nodes(y, n[1], r);
+              pp *= axis_nodes(y, n[1], r - 1);
+            }
+            if (d > 2) {
+              u *= axis_nodes(z, n[2], r);
+              pp *= axis_nodes(z, n[2], r - 1);
+            }
+            const double Cs = 2.0 * d * u + pp, C = q * Cs;
+            sumC += C;
+            if (form == STFEM_PATCH_TIME_DIAGONAL) {
+              const double ldR = std::ceil(Cs / 4.0) * 4.0, ldC = 2.0 * std::ceil(Cs / 2.0) * 2.0;
+              inv += nr * Cs * ldR + nc * Cs * ldC;
+            } else {
+              inv += C * std::ceil(C / vec) * vec;
+            }
+          }
+      total += inv * sp + sumC * (4.0 + sp + 4.0) + nv * (4 + 4 + 8 + 8 + 4) + (N + 1) * 4.0 + N * sp;
+    }
+    if (l == 0) total += N * N * 8.0; // dense coarse inverse
+  }
+  // Krylov workspace and march buffers
+  const double m = restart;
+  total += (m + 1) * Nfine * 8.0 + m * Nfine * (mixed ? 4.0 : 8.0) + 5.0 * Nfine * 8.0 + ns_fine * 8.0;
+  total += 608.0 * 65 * 8.0 + ncell_fine * q * std::pow(r + 2, d) * 4 * 8.0;
+  total += 3.0 * ncell_fine * 8.0 + 64.0 * 1024.0; // coefficients, tables, scalars
+  *bytes = (long long)(total * 1.05) + (1LL << 20);
   return STFEM_OK;
 }
 

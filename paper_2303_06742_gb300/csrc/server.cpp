@@ -1,0 +1,221 @@
+// Serving loop of the C ABI (include/stfem.h): requests (one march each) are
+// admitted by HBM footprint and run concurrently, one handle and one CUDA
+// stream per worker thread.
+#include "../../include/stfem.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct Request {
+  long long id = 0;
+  stfem_request req{};
+  std::vector<double> lam, mu, kap; // copies of the per-cell arrays
+  long long footprint = 0;
+  stfem_result info{};
+  std::vector<double> end_state;
+  std::vector<double> slab_ms;
+  bool done = false;
+};
+
+} // namespace
+
+struct stfem_server_ctx {
+  long long budget = 0, used = 0;
+  int n_workers = 1, running = 0;
+  bool stop = false;
+  long long next_id = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> pending;
+  std::map<long long, std::shared_ptr<Request>> all;
+  std::vector<std::thread> workers;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+// Runs one request on this thread's own stream and handle.
+void run_request(stfem_server s, Request &R) {
+  stfem_request q = R.req;
+  q.mat.lambda_cell_host = R.lam.empty() ? nullptr : R.lam.data();
+  q.mat.mu_cell_host = R.mu.empty() ? nullptr : R.mu.data();
+  q.mat.kappa_cell_host = R.kap.empty() ? nullptr : R.kap.data();
+  int status = STFEM_OK;
+  cudaStream_t stream = nullptr;
+  stfem_h h = nullptr;
+  double *state = nullptr;
+  long long n_slab = 0, n_state = 0;
+  R.slab_ms.assign(q.n_slabs, 0.0);
+  do {
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+      status = STFEM_ERR_CUDA;
+      break;
+    }
+    if ((status = stfem_setup(&q.mesh, &q.deg, &q.mat, &q.bcs, q.tau, &h)) < 0) break;
+    stfem_set_stream(h, stream);
+    if ((status = stfem_gmg_setup(h, &q.gmg)) < 0) break;
+    stfem_level_info(h, -1, &n_slab, &n_state, nullptr, nullptr);
+    if (cudaMalloc((void **)&state, n_state * sizeof(double)) != cudaSuccess) {
+      status = STFEM_ERR_OOM;
+      break;
+    }
+    if ((status = stfem_initial_state(h, state)) < 0) break;
+    R.info.t_ready = s->now();
+    int worst = STFEM_OK, iters_total = 0;
+    for (int n = 0; n < q.n_slabs; ++n) {
+      const double t = s->now();
+      int it = 0;
+      const int rc = march(h, n, 1, state, q.tol, q.restart, q.max_it, &it);
+      R.slab_ms[n] = 1000.0 * (s->now() - t);
+      iters_total += it;
+      if (rc < 0) {
+        worst = rc;
+        break;
+      }
+      worst = std::max(worst, rc);
+    }
+    status = worst;
+    R.info.iters_total = iters_total;
+    R.end_state.assign(n_state, 0.0);
+    if (cudaMemcpyAsync(R.end_state.data(), state, n_state * sizeof(double), cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      status = STFEM_ERR_CUDA;
+    long long bytes = 0;
+    stfem_footprint_bytes(h, &bytes);
+    R.info.device_bytes = bytes + n_state * (long long)sizeof(double);
+  } while (false);
+  if (state) cudaFree(state);
+  if (h) stfem_destroy(h);
+  if (stream) cudaStreamDestroy(stream);
+  R.info.status = status;
+  R.info.n_slabs = q.n_slabs;
+  R.info.n_state = n_state;
+}
+
+void worker(stfem_server s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    std::shared_ptr<Request> R;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      for (;;) {
+        if (s->stop && s->pending.empty()) return;
+        // first request in arrival order that fits the remaining budget
+        auto it = std::find_if(s->pending.begin(), s->pending.end(), [&](const std::shared_ptr<Request> &r) {
+          return s->used + r->footprint <= s->budget;
+        });
+        if (it != s->pending.end()) {
+          R = *it;
+          s->pending.erase(it);
+          s->used += R->footprint;
+          ++s->running;
+          R->info.t_admit = s->now();
+          break;
+        }
+        s->cv_work.wait(lock);
+      }
+    }
+    run_request(s, *R);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      R->info.t_done = s->now();
+      R->done = true;
+      s->used -= R->footprint;
+      --s->running;
+    }
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+  }
+}
+
+} // namespace
+
+extern "C" {
+
+int stfem_server_create(long long hbm_budget, int n_workers, stfem_server *out) {
+  if (!out || hbm_budget <= 0 || n_workers < 1 || n_workers > 256) return STFEM_ERR_ARG;
+  stfem_server s = new stfem_server_ctx();
+  s->budget = hbm_budget;
+  s->n_workers = n_workers;
+  s->t0 = std::chrono::steady_clock::now();
+  cudaGetDevice(&s->device);
+  for (int i = 0; i < n_workers; ++i) s->workers.emplace_back(worker, s);
+  *out = s;
+  return STFEM_OK;
+}
+
+int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id) {
+  if (!s || !req || !id || req->n_slabs < 0) return STFEM_ERR_ARG;
+  auto R = std::make_shared<Request>();
+  R->req = *req;
+  long ncell = 1;
+  for (int i = 0; i < req->mesh.dim && i < 3; ++i) ncell *= req->mesh.n_cells[i];
+  if (req->mat.lambda_cell_host) R->lam.assign(req->mat.lambda_cell_host, req->mat.lambda_cell_host + ncell);
+  if (req->mat.mu_cell_host) R->mu.assign(req->mat.mu_cell_host, req->mat.mu_cell_host + ncell);
+  if (req->mat.kappa_cell_host) R->kap.assign(req->mat.kappa_cell_host, req->mat.kappa_cell_host + ncell);
+  const int rc = stfem_estimate_bytes(&req->mesh, &req->deg, &req->gmg, req->restart, &R->footprint);
+  if (rc < 0) return rc;
+  R->info.footprint = R->footprint;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (R->footprint > s->budget) return STFEM_ERR_ARG;
+    R->id = s->next_id++;
+    R->info.t_submit = s->now();
+    s->all[R->id] = R;
+    s->pending.push_back(R);
+    *id = R->id;
+  }
+  s->cv_work.notify_one();
+  return STFEM_OK;
+}
+
+int stfem_server_result(stfem_server s, long long id, double timeout_s, stfem_result *info, double *end_state_host,
+                        double *slab_ms_host) {
+  if (!s) return STFEM_ERR_ARG;
+  std::shared_ptr<Request> R;
+  {
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return STFEM_ERR_ARG;
+    R = it->second;
+    auto ready = [&] { return R->done; };
+    if (timeout_s < 0)
+      s->cv_done.wait(lock, ready);
+    else if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready))
+      return STFEM_NOT_CONVERGED;
+  }
+  if (info) *info = R->info;
+  if (end_state_host) std::copy(R->end_state.begin(), R->end_state.end(), end_state_host);
+  if (slab_ms_host) std::copy(R->slab_ms.begin(), R->slab_ms.end(), slab_ms_host);
+  return STFEM_OK;
+}
+
+void stfem_server_destroy(stfem_server s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto &t : s->workers) t.join();
+  delete s;
+}
+
+} // extern "C"

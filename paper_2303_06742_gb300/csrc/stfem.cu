@@ -1295,6 +1295,7 @@ struct stfem_ctx {
   LoadTables lt{};
   std::vector<double> hist;
   std::vector<void *> allocs;
+  long long device_bytes = 0; // sum of the handle's allocations
   // launch accounting: totals per kernel class; event pairs when profiling
   long long launches = 0;
   bool prof = false;
@@ -1318,7 +1319,9 @@ struct stfem_ctx {
 
 namespace {
 
-std::string g_setup_err;
+// message of the last failed stfem_setup of the calling thread (setups of
+// concurrent requests run on different threads)
+thread_local std::string g_setup_err;
 
 #define CK(call)                                                                                     \
   do {                                                                                               \
@@ -1369,6 +1372,7 @@ int dalloc(stfem_h h, T **p, size_t n) {
   if (n == 0) n = 1;
   CK(cudaMalloc((void **)p, n * sizeof(T)));
   h->allocs.push_back((void *)*p);
+  h->device_bytes += (long long)(n * sizeof(T));
   return 0;
 }
 
@@ -2820,6 +2824,12 @@ int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, d
   if (ms) *ms = k.ms;
   if (bytes) *bytes = k.bytes;
   if (flops) *flops = k.flops;
+  return STFEM_OK;
+}
+
+int stfem_footprint_bytes(stfem_h h, long long *bytes) {
+  if (!h || !bytes) return STFEM_ERR_ARG;
+  *bytes = h->device_bytes;
   return STFEM_OK;
 }
 

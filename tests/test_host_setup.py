@@ -129,3 +129,23 @@ def test_setup_rejects_bad_arguments():
     bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, bc_u=[1, 0, 0, 0], problem=stfem.PROBLEM_SIN)
     with pytest.raises(stfem.StfemError):
         stfem.host_level_matrix(bad)
+
+
+@pytest.mark.parametrize("name", ["c1_2d_q2_k1_8", "c3_small_3d_q2_k1_4"])
+def test_footprint_estimate_covers_the_patch_inverses(name):
+    """The admission estimate of the serving loop (no setup, sizes only) must
+    hold at least the patch inverses that setup stores: sum over levels >= 1
+    and patches of C_P^2 values (C_P from the host patch lists), in either
+    precision.  A smaller mesh must estimate less."""
+    import inputs
+    from _cases import gpu_problem
+    c = dict(inputs.case(name))
+    prob = gpu_problem(c)
+    for precision, size in ((stfem.FP64, 8), (stfem.MIXED, 4)):
+        est = stfem.estimate_bytes(prob, precision)
+        inv = 0
+        for level in range(1, c["levels"]):
+            inv += sum(len(p) ** 2 for p in stfem.host_patch_dofs(prob, level)) * size
+        assert est >= inv > 0
+    c_small = dict(c, n=c["n"] // 2, levels=c["levels"] - 1)
+    assert stfem.estimate_bytes(gpu_problem(c_small), stfem.MIXED) < stfem.estimate_bytes(prob, stfem.MIXED)
