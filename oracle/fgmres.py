@@ -13,21 +13,23 @@ Readings:
 * Stopping: |g_{j+1}| <= tol * ||b - A x_0|| (relative to the residual of the
   initial guess of this solve); at each restart and at the end the true
   residual is recomputed and the solve only stops when it satisfies the same
-  bound or the iteration budget is spent.
+  bound or the iteration budget is spent.  ``absolute=True`` takes the
+  paper's own rule of Sec. 5, the bound tol on the residual itself.
 * Givens rotation for (a, b): rho = hypot(a, b), c = a / rho, s = b / rho,
   applied as [c s; -s c].
 """
 import numpy as np
 
 
-def fgmres(apply_A, b, x0, precond, tol, restart=30, max_it=500):
+def fgmres(apply_A, b, x0, precond, tol, restart=30, max_it=500, absolute=False):
     """Returns (x, iterations, final relative true residual, history of |g|/beta0)."""
     x = np.array(x0, dtype=float, copy=True)
     r = b - apply_A(x)
     beta0 = float(np.linalg.norm(r))
     hist = [1.0]
-    if beta0 == 0.0:
-        return x, 0, 0.0, hist
+    bound = tol if absolute else tol * beta0
+    if beta0 == 0.0 or beta0 <= bound:
+        return x, 0, (1.0 if beta0 > 0.0 else 0.0), hist
     it = 0
     n = b.shape[0]
     m = restart
@@ -69,7 +71,7 @@ def fgmres(apply_A, b, x0, precond, tol, restart=30, max_it=500):
             it += 1
             jlast = j
             hist.append(abs(g[j + 1]) / beta0)
-            if abs(g[j + 1]) <= tol * beta0 or it >= max_it or hn == 0.0:
+            if abs(g[j + 1]) <= bound or it >= max_it or hn == 0.0:
                 break
         k = jlast + 1
         y = np.zeros(k)
@@ -78,5 +80,5 @@ def fgmres(apply_A, b, x0, precond, tol, restart=30, max_it=500):
         x = x + Z[:k].T @ y
         r = b - apply_A(x)
         res = float(np.linalg.norm(r))
-        if res <= tol * beta0 or it >= max_it:
+        if res <= bound or it >= max_it:
             return x, it, res / beta0, hist

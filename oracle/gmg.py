@@ -27,6 +27,18 @@ Readings:
   S_P uses the iterate of the start of the sweep (d is only overwritten
   after the patch loop).
 * The coarse direct solve is a dense LU with partial pivoting.
+
+Variants for the ablations of Sec. 4 (the introduction reports that an
+elementwise Vanka smoother fails to damp the high frequencies; Remark 4.3
+reports that the averaging of Algorithm 4.1 is essential):
+
+* ``patches="cell"``: one patch per cell, holding every node of the closed
+  cell (under the support reading a cell would hold its interior nodes
+  only and the vertices would belong to no patch).
+* ``averaging=False``: the patch results overwrite one another in patch
+  order instead of being averaged, i.e. z[Z(P)] = y_P in the loop over P
+  and d = z afterwards; the residual is still the one of the start of the
+  sweep.
 """
 import itertools
 import numpy as np
@@ -79,6 +91,38 @@ def patch_dofs(ops, temporal, vertex, support=True):
     return np.concatenate(out)
 
 
+def cell_patch_nodes(space, cell):
+    """Every node of the scalar space ``space`` on the closed cell ``cell``."""
+    m = space.m
+    ranges = [range(m * cell[i], m * (cell[i] + 1) + 1) for i in range(space.mesh.dim)]
+    return np.array([space.node_index(a[::-1]) for a in itertools.product(*ranges[::-1])], int)
+
+
+def cell_patch_dofs(ops, temporal, cell):
+    """Global slab indices (paper ordering) of the cell patch of ``cell``."""
+    un = cell_patch_nodes(ops.Vs, cell)
+    pn = cell_patch_nodes(ops.Qs, cell)
+    d, R, n_s = ops.d, ops.R, ops.n_s
+    vec = np.array([I * d + c for I in un for c in range(d)], int)
+    out = []
+    for a in range(temporal.q):
+        base = a * n_s
+        out.append(base + vec)
+        out.append(base + R + vec)
+        out.append(base + 2 * R + pn)
+    return np.concatenate(out)
+
+
+def cells(mesh):
+    """Cell multi-indices, x fastest."""
+    for idx in range(int(np.prod(mesh.n))):
+        c, t = [], idx
+        for i in range(mesh.dim):
+            c.append(t % mesh.n[i])
+            t //= mesh.n[i]
+        yield tuple(c)
+
+
 def vertices(mesh):
     dims = mesh.n + 1
     for idx in range(int(np.prod(dims))):
@@ -122,26 +166,33 @@ def slab_prolongation(coarse_ops, fine_ops, temporal):
 
 
 class Level:
-    def __init__(self, ops, A, temporal, support=True):
+    def __init__(self, ops, A, temporal, support=True, patches="vertex"):
+        if patches not in ("vertex", "cell"):
+            raise ValueError("patches must be 'vertex' or 'cell'")
         self.ops, self.A = ops, A
         self.patches = []
         self.inverses = []
         self.support = support
+        self.kind = patches
         self.temporal = temporal
 
     def build_patches(self):
         A = self.A.tocsr()
-        for v in vertices(self.ops.mesh):
-            idx = patch_dofs(self.ops, self.temporal, v, self.support)
+        if self.kind == "vertex":
+            sets = [patch_dofs(self.ops, self.temporal, v, self.support) for v in vertices(self.ops.mesh)]
+        else:
+            sets = [cell_patch_dofs(self.ops, self.temporal, c) for c in cells(self.ops.mesh)]
+        for idx in sets:
             AP = A[idx][:, idx].toarray()
             self.patches.append(idx)
             self.inverses.append(np.linalg.inv(AP))
 
 
-def smooth(level, b, d, omega, nsweeps):
+def smooth(level, b, d, omega, nsweeps, averaging=True):
     """Algorithm 4.1, literally: per sweep reset counters p and accumulator z,
     apply every local Vanka operator to the current iterate, accumulate the
-    extended patch results, then d = z / p."""
+    extended patch results, then d = z / p.  With ``averaging=False`` the
+    patch results overwrite z in patch order and d = z."""
     A = level.A
     n = A.shape[0]
     for _ in range(nsweeps):
@@ -150,8 +201,12 @@ def smooth(level, b, d, omega, nsweeps):
         res = b - A @ d  # S_P applies to the iterate of the start of the sweep
         for idx, Ainv in zip(level.patches, level.inverses):
             y = d[idx] + omega * (Ainv @ res[idx])
-            z[idx] += y
-            p[idx] += 1
+            if averaging:
+                z[idx] += y
+                p[idx] += 1
+            else:
+                z[idx] = y
+                p[idx] = 1
         if np.any(p == 0):
             raise RuntimeError("a degree of freedom belongs to no patch")
         d = z / p
@@ -162,9 +217,11 @@ class Hierarchy:
     """Levels 0..L of the GMG method for one slab problem."""
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material_fine, bc_u, bc_p, tau,
-                 omega=0.7, nsweeps=1, support=True, hf="measure", coarse="galerkin"):
+                 omega=0.7, nsweeps=1, support=True, hf="measure", coarse="galerkin",
+                 patches="vertex", averaging=True):
         self.temporal = Temporal(k)
         self.omega, self.nsweeps = omega, nsweeps
+        self.averaging = averaging
         meshes = [BoxMesh(dim, lo, hi, n_fine, hf)]
         mats = [material_fine]
         for _ in range(n_levels - 1):
@@ -175,7 +232,7 @@ class Hierarchy:
         for mesh, mat in zip(meshes, mats):
             ops = SpatialOps(mesh, r, mat, bc_u, bc_p)
             A = slab_matrix(ops, self.temporal, tau)
-            self.levels.append(Level(ops, A, self.temporal, support))
+            self.levels.append(Level(ops, A, self.temporal, support, patches))
         self.P = [None] + [slab_prolongation(self.levels[l - 1].ops, self.levels[l].ops,
                                              self.temporal) for l in range(1, n_levels)]
         if coarse == "galerkin":
@@ -199,10 +256,10 @@ class Hierarchy:
             return sla.lu_solve(self.coarse_lu, b)
         lev = self.levels[l]
         d = np.zeros_like(b)
-        d = smooth(lev, b, d, self.omega, self.nsweeps)
+        d = smooth(lev, b, d, self.omega, self.nsweeps, self.averaging)
         r = b - lev.A @ d
         bc = self.P[l].T @ r
         dc = self.vcycle(bc, l - 1)
         d = d + self.P[l] @ dc
-        d = smooth(lev, b, d, self.omega, self.nsweeps)
+        d = smooth(lev, b, d, self.omega, self.nsweeps, self.averaging)
         return d

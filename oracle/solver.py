@@ -18,9 +18,10 @@ class Instance:
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
                  problem, t0=0.0, omega=0.7, nsweeps=1, support=True, hf="measure",
-                 coarse="galerkin"):
+                 coarse="galerkin", patches="vertex", averaging=True, absolute=False):
         self.h = Hierarchy(dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
-                           omega, nsweeps, support, hf, coarse)
+                           omega, nsweeps, support, hf, coarse, patches, averaging)
+        self.absolute = absolute
         self.prob, self.tau, self.t0 = problem, tau, t0
         self.tmp = self.h.temporal
         self.ops = self.h.fine.ops
@@ -35,7 +36,7 @@ class Instance:
         return slab_rhs(self.ops, self.tmp, self.tau, t_prev, self.prob, prev)
 
     def solve(self, b, x0, tol, restart=30, max_it=500):
-        return fgmres(lambda x: self.A @ x, b, x0, self.h.vcycle, tol, restart, max_it)
+        return fgmres(lambda x: self.A @ x, b, x0, self.h.vcycle, tol, restart, max_it, self.absolute)
 
     def march(self, n_slabs, tol, restart=30, max_it=500, state=None, on_slab=None):
         state = self.initial_state() if state is None else state

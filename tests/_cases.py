@@ -22,7 +22,8 @@ def gpu_problem(c, hf_mode=0):
                       t0=c.get("t0", 0.0), hf_mode=hf_mode)
 
 
-def oracle_instance(c, omega=0.7, nsweeps=1, hf="measure"):
+def oracle_instance(c, omega=0.7, nsweeps=1, hf="measure", **variant):
+    """``variant``: patches, averaging, absolute (oracle.solver.Instance)."""
     from oracle.space import Material
     from oracle.solver import Instance
     from oracle import problems as P
@@ -48,7 +49,7 @@ def oracle_instance(c, omega=0.7, nsweeps=1, hf="measure"):
     bcu = c.get("bc_u") or [0] * (2 * d)
     bcp = c.get("bc_p") or [0] * (2 * d)
     return Instance(d, lo, hi, n, c["levels"], c["r"], c["k"], mat, bcu, bcp, c["tau"], prob,
-                    t0=c.get("t0", 0.0), omega=omega, nsweeps=nsweeps, hf=hf)
+                    t0=c.get("t0", 0.0), omega=omega, nsweeps=nsweeps, hf=hf, **variant)
 
 
 def case(name):

@@ -160,3 +160,100 @@ def test_energy_decays_without_data():
         E.append(energy(st))
     assert all(e2 <= e1 * (1 + 1e-10) for e1, e2 in zip(E, E[1:]))
     assert E[-1] < E[0]
+
+
+def _level_kind(dim, n, r, k, patches, tau=0.01):
+    mesh = BoxMesh(dim, [0.0] * dim, [1.0] * dim, [n] * dim)
+    mat = Material.uniform(mesh, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    ops = SpatialOps(mesh, r, mat, [0] * (2 * dim), [0] * (2 * dim))
+    T = Temporal(k)
+    lev = Level(ops, slab_matrix(ops, T, tau), T, patches=patches)
+    lev.build_patches()
+    return lev
+
+
+@pytest.mark.parametrize("dim,r,k", [(2, 2, 1), (3, 2, 0)])
+def test_cell_patches_sizes_multiplicities_and_one_cell_exactness(dim, r, k):
+    """Cell patches hold q (2d (r+1)^d + r^d) dofs each; a u-node at a lattice
+    vertex interior to the domain lies in 2^d of them, a node inside a cell in
+    one.  On a single cell the one patch is the whole system, so a sweep is
+    d + omega A^{-1} (b - A d) with or without averaging."""
+    lev = _level_kind(dim, 3, r, k, "cell")
+    q, ops = k + 1, lev.ops
+    assert len(lev.patches) == 3 ** dim
+    assert all(len(p) == q * (2 * dim * (r + 1) ** dim + r ** dim) for p in lev.patches)
+    cnt = np.zeros(lev.A.shape[0], int)
+    for p in lev.patches:
+        cnt[p] += 1
+    vtx = ops.Vs.node_index([r] * dim)  # lattice vertex (1, .., 1)
+    mid = ops.Vs.node_index([1] * dim)  # inside cell (0, .., 0)
+    assert cnt[vtx * dim] == 2 ** dim and cnt[mid * dim] == 1
+    one = _level_kind(dim, 1, r, k, "cell")
+    n = one.A.shape[0]
+    rng = np.random.default_rng(5)
+    xs, d0 = rng.standard_normal(n), rng.standard_normal(n)
+    b = one.A @ xs
+    for averaging in (True, False):
+        d1 = smooth(one, b, d0.copy(), 0.7, 1, averaging)
+        assert np.linalg.norm(d1 - xs - 0.3 * (d0 - xs)) < 1e-8 * np.linalg.norm(d0 - xs)
+
+
+@pytest.mark.parametrize("patches", ["vertex", "cell"])
+def test_overwrite_takes_each_dofs_last_patch(patches):
+    """Without averaging (Remark 4.3's comparison) a dof ends with the local
+    update of the highest-numbered patch that holds it: computed here per dof
+    from that owner patch alone and compared with the sequential loop."""
+    lev = _level_kind(2, 3, 2, 1, patches)
+    n = lev.A.shape[0]
+    rng = np.random.default_rng(6)
+    b, d = rng.standard_normal(n), rng.standard_normal(n)
+    seq = smooth(lev, b, d.copy(), 0.7, 1, averaging=False)
+    owner = np.full(n, -1)
+    for m, idx in enumerate(lev.patches):
+        owner[idx] = np.maximum(owner[idx], m)
+    res = b - lev.A @ d
+    ref = np.empty(n)
+    for i in range(n):
+        idx = lev.patches[owner[i]]
+        loc = int(np.nonzero(idx == i)[0][0])
+        ref[i] = d[i] + 0.7 * (lev.inverses[owner[i]][loc] @ res[idx])
+    assert np.allclose(seq, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert not np.allclose(seq, smooth(lev, b, d.copy(), 0.7, 1, averaging=True))
+
+
+def test_absolute_stop_equals_the_matching_relative_stop():
+    """Stopping on ||r|| <= t is stopping on ||r|| <= (t / ||r_0||) ||r_0||:
+    both runs take the same iterations and return the same iterate, and the
+    final true residual is below t."""
+    rng = np.random.default_rng(7)
+    N = 60
+    A = np.eye(N) * 4 + rng.standard_normal((N, N)) * 0.5
+    b = rng.standard_normal(N)
+    x0 = np.zeros(N)
+    beta0 = np.linalg.norm(b)
+    t = 1e-6
+    xa, ita, _, _ = fgmres(lambda v: A @ v, b, x0, lambda v: v, t, restart=10, absolute=True)
+    xr, itr, _, _ = fgmres(lambda v: A @ v, b, x0, lambda v: v, t / beta0, restart=10)
+    assert ita == itr and np.array_equal(xa, xr)
+    assert np.linalg.norm(b - A @ xa) <= t
+    x1, it1, _, _ = fgmres(lambda v: A @ v, b, x0, lambda v: v, 2 * beta0, absolute=True)
+    assert it1 == 0 and np.array_equal(x1, x0)
+
+
+def test_elementwise_vanka_is_weaker_under_pressure_coupling():
+    """The introduction reports that cell-wise Vanka fails to damp the high
+    frequencies because the pressure dofs couple across cells; with c0 = 0
+    and a small permeability (2D 16x16, Q2/Q1, k = 1, tau = 0.1) the cell
+    patches need clearly more FGMRES-GMG iterations than vertex patches."""
+    mesh = BoxMesh(2, [0, 0], [1, 1], [16, 16])
+    mat = Material.uniform(mesh, 1.0, 1.0, 0.0, 1.0, 1.0, 1e-3)
+    prob = sin_problem(2, 1.0, 1.0, 0.0)
+    its = {}
+    for patches in ("vertex", "cell"):
+        H = Hierarchy(2, [0, 0], [1, 1], [16, 16], 3, 2, 1, mat, [0] * 4, [0] * 4, 0.1, patches=patches)
+        ops, T = H.fine.ops, H.temporal
+        st = interpolate_state(ops, prob, 0.0)
+        b = slab_rhs(ops, T, 0.1, 0.0, prob, st)
+        _, its[patches], rel, _ = fgmres(lambda v: H.fine.A @ v, b, repeat_state(ops, T, st), H.vcycle, 1e-8)
+        assert rel <= 1e-8
+    assert its["cell"] >= 1.5 * its["vertex"]
