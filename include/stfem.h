@@ -124,15 +124,40 @@ typedef struct {
 #define STFEM_PATCH_DENSE 1
 #define STFEM_PATCH_TIME_DIAGONAL 2
 
+/* Patch sets of the smoother.  VERTEX: the vertex patches of Eq. 4.9 (the
+ * method).  CELL: one patch per cell holding every node of the closed cell,
+ * the elementwise Vanka smoother that the introduction reports to fail on
+ * this system (an ablation). */
+#define STFEM_PATCHES_VERTEX 0
+#define STFEM_PATCHES_CELL 1
+
+/* Combination of the patch results in a sweep.  AVERAGE: Algorithm 4.1,
+ * the mean of the results of all patches holding a dof.  OVERWRITE: the
+ * results overwrite one another in patch order (the last patch holding a
+ * dof wins), the variant Remark 4.3 compares against (an ablation). */
+#define STFEM_UPDATE_AVERAGE 0
+#define STFEM_UPDATE_OVERWRITE 1
+
+/* Most right-hand sides one batched call solves together. */
+#define STFEM_MAX_RHS 8
+
 /* GMG parameters (Sec. 4): damping omega of the Vanka operator (Eq. 4.11;
  * the paper uses 0.7), n_sweeps pre- and post-smoothing steps of
- * Algorithm 4.1 per level, precision STFEM_FP64 or STFEM_MIXED, patch_form
- * STFEM_PATCH_*. */
+ * Algorithm 4.1 per level (the paper's J_max, 4 in its experiments),
+ * precision STFEM_FP64 or STFEM_MIXED, patch_form STFEM_PATCH_*,
+ * patch_kind STFEM_PATCHES_*, update STFEM_UPDATE_*, n_rhs the most
+ * right-hand sides the batched calls (slab_solve_batch, march_batch,
+ * stfem_vcycle_batch) will be given (0 or 1: none; at most STFEM_MAX_RHS);
+ * the level work vectors are allocated with that many columns.  A
+ * zero-initialised tail (patch_form .. n_rhs) selects the defaults. */
 typedef struct {
   double omega;
   int n_sweeps;
   int precision;
   int patch_form;
+  int patch_kind;
+  int update;
+  int n_rhs;
 } stfem_gmg_params;
 
 /* Builds the mesh hierarchy, spatial matrices of every level (Eqs. 3.2-3.3),
@@ -148,6 +173,13 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
  * Once per handle (STFEM_ERR_STATE otherwise).  STFEM_ERR_SINGULAR_PATCH if a
  * patch matrix has a zero pivot. */
 int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p);
+
+/* Stopping rule of slab_solve, march and stfem_solve_history: RELATIVE
+ * (default) stops on ||b - A x|| <= tol ||b - A x0||; ABSOLUTE stops on
+ * ||b - A x|| <= tol, the rule of the paper's experiments (Sec. 5, 1e-8). */
+#define STFEM_STOP_RELATIVE 0
+#define STFEM_STOP_ABSOLUTE 1
+int stfem_set_stop(stfem_h h, int mode);
 
 /* Issue all work on this CUDA stream (cudaStream_t passed as void*; NULL =
  * the legacy default stream). */
@@ -239,6 +271,28 @@ int stfem_profile(stfem_h h, int enable);
 int stfem_profile_read(stfem_h h, int kclass, long long *launches, double *ms, double *bytes,
                        double *flops);
 
+/* ---- Several right-hand sides ----
+ * n_rhs (<= the n_rhs given to stfem_gmg_setup) systems with the same slab
+ * matrix, in columns of length n_slab (device, column c at offset
+ * c * n_slab; states: column stride n_state).  Each column is solved as the
+ * single-column call would solve it (same stopping rule, its own Krylov
+ * space), but all columns are preconditioned by one V-cycle that reads each
+ * patch inverse and level operator once per sweep for all of them.
+ * iters_host[c] / rel_res_host[c] per column (march_batch: iters_host
+ * [n_slabs][n_rhs]).  The return value is the worst column's status. */
+int slab_solve_batch(stfem_h h, int n_rhs, const double *rhs, double *x, double tol, int restart, int max_it,
+                     int *iters_host, double *rel_res_host);
+/* n_rhs independent marches of the handle's problem, column c with its data
+ * taken at time t0_host[c] + slab * tau (its own initial time; the
+ * handle's t0 is ignored), from the states in `state` (updated in place). */
+int march_batch(stfem_h h, int n_rhs, const double *t0_host, int first_slab, int n_slabs, double *state,
+                double tol, int restart, int max_it, int *iters_host);
+/* d = M^{-1} b for n_rhs columns (one batched V-cycle, as stfem_vcycle). */
+int stfem_vcycle_batch(stfem_h h, int n_rhs, const double *b, double *d);
+/* Nodal interpolant of the problem's exact state at time t (as
+ * stfem_initial_state, which takes t = t0). */
+int stfem_initial_state_at(stfem_h h, double t, double *state);
+
 /* Number of kernels the handle has launched since it was created. */
 int stfem_launch_count(stfem_h h, long long *n);
 
@@ -287,6 +341,7 @@ typedef struct {
   long long device_bytes; /* bytes the handle actually allocated */
   int iters_total;
   double t_submit, t_admit, t_ready, t_done; /* ready = setup finished */
+  char error[160]; /* message of the failure (status < 0), else empty */
 } stfem_result;
 
 /* n_workers concurrent requests at most; hbm_budget bytes of footprint. */
@@ -344,11 +399,12 @@ int stfem_host_level_matrix(const stfem_mesh *mesh, const stfem_degrees *deg, co
                             const stfem_bcs *bcs, double tau, int level, long long *n, long long *nnz,
                             long long *rowptr_host, int *col_host, double *val_host);
 
-/* Vertex patches of level l >= 1 (Eq. 4.9): patch p holds the slab indices
+/* Patches of level l >= 1 of kind patch_kind (STFEM_PATCHES_*; vertex
+ * patches: Eq. 4.9): patch p holds the slab indices
  * dofs_host[off_host[p] .. off_host[p+1]) (all time nodes and fields). */
 int stfem_host_patch_dofs(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
-                          const stfem_bcs *bcs, double tau, int level, long long *n_patches, long long *total,
-                          long long *off_host, int *dofs_host);
+                          const stfem_bcs *bcs, double tau, int level, int patch_kind, long long *n_patches,
+                          long long *total, long long *off_host, int *dofs_host);
 
 /* Scalar interpolation from level l-1 to l (field 0: Q_r nodes, field 1:
  * Q_{r-1} nodes) in CSR form (rows: fine nodes). */

@@ -26,6 +26,9 @@ FP64, MIXED = 0, 1
 HF_MEASURE, HF_LENGTH = 0, 1
 COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
 PATCH_AUTO, PATCH_DENSE, PATCH_TIME_DIAGONAL = 0, 1, 2
+PATCHES_VERTEX, PATCHES_CELL = 0, 1
+UPDATE_AVERAGE, UPDATE_OVERWRITE = 0, 1
+STOP_RELATIVE, STOP_ABSOLUTE = 0, 1
 KCLASSES = ["spmv", "patch_apply", "update", "transfer", "coarse", "blas1", "rhs", "other"]
 
 
@@ -57,7 +60,8 @@ class BCs(C.Structure):
 
 
 class GmgParams(C.Structure):
-    _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int), ("patch_form", C.c_int)]
+    _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int), ("patch_form", C.c_int),
+                ("patch_kind", C.c_int), ("update", C.c_int), ("n_rhs", C.c_int)]
 
 
 class Request(C.Structure):
@@ -70,7 +74,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("n_slabs", C.c_int), ("n_state", C.c_longlong),
                 ("footprint", C.c_longlong), ("device_bytes", C.c_longlong), ("iters_total", C.c_int),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_ready", C.c_double),
-                ("t_done", C.c_double)]
+                ("t_done", C.c_double), ("error", C.c_char * 160)]
 
 
 def _load():
@@ -98,14 +102,19 @@ def _load():
         "stfem_initial_state": [P, P],
         "stfem_slab_rhs": [P, I, P, P],
         "march": [P, I, I, P, D, I, I, pI],
+        "slab_solve_batch": [P, I, P, P, D, I, I, pI, pD],
+        "march_batch": [P, I, pD, I, I, P, D, I, I, pI],
+        "stfem_vcycle_batch": [P, I, P, P],
+        "stfem_initial_state_at": [P, D, P],
         "stfem_host_level_matrix": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, pLL, pLL, pLL, pI, pD],
         "stfem_host_patch_dofs": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
-                                  C.POINTER(BCs), D, I, pLL, pLL, pLL, pI],
+                                  C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pI],
         "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pLL, pI, pD],
         "stfem_host_temporal": [I, pD, pD, pD, pD],
         "stfem_profile": [P, I],
+        "stfem_set_stop": [P, I],
         "stfem_footprint_bytes": [P, pLL],
         "stfem_estimate_bytes": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(GmgParams), I, pLL],
         "stfem_server_create": [LL, I, C.POINTER(P)],
@@ -199,13 +208,14 @@ def host_level_matrix(prob, level=-1):
     return rp, ci, va, n.value
 
 
-def host_patch_dofs(prob, level=-1):
-    """List of per-patch slab index arrays of a level (vertex order, x fastest)."""
+def host_patch_dofs(prob, level=-1, patch_kind=PATCHES_VERTEX):
+    """List of per-patch slab index arrays of a level (vertex or cell order, x fastest)."""
     npch, tot = C.c_longlong(), C.c_longlong()
-    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, C.byref(npch), C.byref(tot), None, None))
+    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, patch_kind, C.byref(npch), C.byref(tot), None,
+                                          None))
     off = np.zeros(npch.value + 1, np.int64)
     dofs = np.zeros(tot.value, np.int32)
-    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, C.byref(npch), C.byref(tot),
+    _host_check(lib.stfem_host_patch_dofs(*prob.args(), level, patch_kind, C.byref(npch), C.byref(tot),
                                           off.ctypes.data_as(C.POINTER(C.c_longlong)),
                                           dofs.ctypes.data_as(C.POINTER(C.c_int))))
     return [dofs[off[i]:off[i + 1]] for i in range(npch.value)]
@@ -234,7 +244,8 @@ def host_temporal(k):
 class Solver:
     """Handle of one problem instance on the current CUDA device."""
 
-    def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None, patch_form=PATCH_AUTO):
+    def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None, patch_form=PATCH_AUTO,
+                 patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE, stop=STOP_RELATIVE, n_rhs=0):
         self.prob = prob
         h = C.c_void_p()
         rc = lib.stfem_setup(*prob.args(), C.byref(h))
@@ -243,7 +254,9 @@ class Solver:
         self.h = h
         if stream is not None:
             self.set_stream(stream)
-        self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision, patch_form))))
+        self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision, patch_form,
+                                                                  patch_kind, update, n_rhs))))
+        self.set_stop(stop)
         self.precision = precision
         n_slab, n_state = C.c_longlong(), C.c_longlong()
         self._check(lib.stfem_level_info(self.h, -1, C.byref(n_slab), C.byref(n_state), None, None))
@@ -264,6 +277,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_stop(self, mode):
+        """STOP_RELATIVE (default) or STOP_ABSOLUTE (tol bounds the residual itself)."""
+        self._check(lib.stfem_set_stop(self.h, int(mode)))
 
     def set_stream(self, stream):
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
@@ -342,11 +359,35 @@ class Solver:
         rc = self._check(lib.march(self.h, first_slab, n_slabs, _ptr(state), tol, restart, max_it, iters))
         return rc, list(iters)[:n_slabs]
 
+    def slab_solve_batch(self, n_rhs, rhs, x, tol=1e-8, restart=30, max_it=500):
+        """n_rhs columns (column stride n_slab); returns (status, iterations, relative residuals)."""
+        it = np.zeros(n_rhs, np.int32)
+        rr = np.zeros(n_rhs)
+        rc = self._check(lib.slab_solve_batch(self.h, n_rhs, _ptr(rhs), _ptr(x), tol, restart, max_it,
+                                              it.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rr)))
+        return rc, it.tolist(), rr
 
-def estimate_bytes(prob, precision=FP64, patch_form=PATCH_AUTO, restart=30, n_sweeps=1, omega=0.7):
+    def march_batch(self, t0s, first_slab, n_slabs, state, tol=1e-8, restart=30, max_it=500):
+        """len(t0s) marches (states column stride n_state); iterations [n_slabs][n_rhs]."""
+        t0 = np.ascontiguousarray(t0s, dtype=np.float64)
+        it = np.zeros((max(n_slabs, 1), len(t0)), np.int32)
+        rc = self._check(lib.march_batch(self.h, len(t0), _dptr(t0), first_slab, n_slabs, _ptr(state), tol,
+                                         restart, max_it, it.ctypes.data_as(C.POINTER(C.c_int))))
+        return rc, it[:n_slabs]
+
+    def vcycle_batch(self, n_rhs, b, d):
+        self._check(lib.stfem_vcycle_batch(self.h, n_rhs, _ptr(b), _ptr(d)))
+
+    def initial_state_at(self, t, state):
+        self._check(lib.stfem_initial_state_at(self.h, float(t), _ptr(state)))
+
+
+def estimate_bytes(prob, precision=FP64, patch_form=PATCH_AUTO, restart=30, n_sweeps=1, omega=0.7,
+                   patch_kind=PATCHES_VERTEX):
     n = C.c_longlong()
     _host_check(lib.stfem_estimate_bytes(C.byref(prob.mesh), C.byref(prob.deg),
-                                         C.byref(GmgParams(omega, n_sweeps, precision, patch_form)), restart,
+                                         C.byref(GmgParams(omega, n_sweeps, precision, patch_form, patch_kind,
+                                                           UPDATE_AVERAGE)), restart,
                                          C.byref(n)))
     return n.value
 
@@ -364,9 +405,10 @@ class Server:
         self._keep = {}
 
     def submit(self, prob, n_slabs, tol=1e-8, precision=MIXED, restart=30, max_it=500, omega=0.7, n_sweeps=1,
-               patch_form=PATCH_AUTO):
+               patch_form=PATCH_AUTO, patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE):
         req = Request(prob.mesh, prob.deg, prob.mat, prob.bcs, prob.tau,
-                      GmgParams(omega, n_sweeps, precision, patch_form), n_slabs, tol, restart, max_it)
+                      GmgParams(omega, n_sweeps, precision, patch_form, patch_kind, update), n_slabs, tol,
+                      restart, max_it)
         i = C.c_longlong()
         rc = lib.stfem_server_submit(self.s, C.byref(req), C.byref(i))
         if rc < 0:
@@ -385,6 +427,7 @@ class Server:
         slab = np.zeros(max(info.n_slabs, 1))
         lib.stfem_server_result(self.s, rid, -1.0, C.byref(info), _dptr(state), _dptr(slab))
         d = {f: getattr(info, f) for f, _ in Result._fields_}
+        d["error"] = d["error"].decode(errors="replace")
         return d, state, slab[:info.n_slabs]
 
     def close(self):

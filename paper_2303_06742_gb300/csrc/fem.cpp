@@ -1104,13 +1104,14 @@ static void patch_axis(int v, int m, int ncell, int *lo, int *hi) {
 }
 
 int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out, std::string *err,
-                  bool invert_them, const TimeDiag *td) {
+                  bool invert_them, const TimeDiag *td, int kind) {
   const Box &b = L.box;
   const int d = b.dim, q = T.q;
+  // patch centres: lattice vertices (kind 0) or cells (kind 1), x fastest
   int vdims[3] = {1, 1, 1};
   long nv = 1;
   for (int i = 0; i < d; ++i) {
-    vdims[i] = b.n[i] + 1;
+    vdims[i] = kind == 1 ? b.n[i] : b.n[i] + 1;
     nv *= vdims[i];
   }
   Patches &P = *out;
@@ -1126,8 +1127,15 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
     unflatten(p, vdims, d, v);
     int ulo[3] = {0, 0, 0}, uhi[3] = {0, 0, 0}, plo[3] = {0, 0, 0}, phi[3] = {0, 0, 0};
     for (int i = 0; i < d; ++i) {
-      patch_axis(v[i], L.r, b.n[i], &ulo[i], &uhi[i]);
-      patch_axis(v[i], L.r - 1, b.n[i], &plo[i], &phi[i]);
+      if (kind == 1) {
+        ulo[i] = L.r * v[i];
+        uhi[i] = L.r * (v[i] + 1);
+        plo[i] = (L.r - 1) * v[i];
+        phi[i] = (L.r - 1) * (v[i] + 1);
+      } else {
+        patch_axis(v[i], L.r, b.n[i], &ulo[i], &uhi[i]);
+        patch_axis(v[i], L.r - 1, b.n[i], &plo[i], &phi[i]);
+      }
     }
     std::vector<long> un, pn;
     for (int z = ulo[2]; z <= uhi[2]; ++z)

@@ -125,9 +125,10 @@ struct Patches {
 };
 // vec: elements per 16-byte vector of the storage type (2 for FP64, 4 for FP32).
 // invert_them = false only builds the dof lists.  td != nullptr selects the
-// time-diagonal form.
+// time-diagonal form.  kind 0: vertex patches (Eq. 4.9, nodes supported in
+// the closed patch); kind 1: cell patches (every node of the closed cell).
 int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out,
-                  std::string *err, bool invert_them = true, const TimeDiag *td = nullptr);
+                  std::string *err, bool invert_them = true, const TimeDiag *td = nullptr, int kind = 0);
 
 // Dense row-major slab matrix of a level (for the coarse solve).
 std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau);

@@ -62,8 +62,12 @@ int stfem_host_level_matrix(const stfem_mesh *mesh, const stfem_degrees *deg, co
 }
 
 int stfem_host_patch_dofs(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
-                          const stfem_bcs *bcs, double tau, int level, long long *n_patches, long long *total,
-                          long long *off, int *dofs) {
+                          const stfem_bcs *bcs, double tau, int level, int patch_kind, long long *n_patches,
+                          long long *total, long long *off, int *dofs) {
+  if (patch_kind != STFEM_PATCHES_VERTEX && patch_kind != STFEM_PATCHES_CELL) {
+    g_host_err = "unknown patch kind";
+    return STFEM_ERR_ARG;
+  }
   std::vector<stfem::Level> L;
   std::vector<stfem::CSR> Pu, Pp;
   int rc = build(mesh, deg, mat, bcs, tau, &L, &Pu, &Pp);
@@ -75,7 +79,8 @@ int stfem_host_patch_dofs(const stfem_mesh *mesh, const stfem_degrees *deg, cons
   }
   stfem::Patches P;
   std::string err;
-  if (stfem::build_patches(L[level], stfem::make_temporal(deg->k), tau, 1, &P, &err, false) < 0) {
+  if (stfem::build_patches(L[level], stfem::make_temporal(deg->k), tau, 1, &P, &err, false, nullptr,
+                           patch_kind) < 0) {
     g_host_err = err;
     return STFEM_ERR_SINGULAR_PATCH;
   }
@@ -164,16 +169,19 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
       total += tr * (4.0 + 8.0) + 2.0 * (nu + np + 2) * 4.0;
       if (mixed) total += tr * (4.0 + 4.0) + 2.0 * (nu + np + 2) * 4.0;
     }
-    // patches (levels >= 1): exact patch sizes per vertex
+    // patches (levels >= 1): exact patch sizes per vertex (or per cell)
     if (l >= 1) {
-      auto axis_nodes = [](long v, long ncl, int m) {
+      const bool cellk = gmg->patch_kind == STFEM_PATCHES_CELL;
+      auto axis_nodes = [cellk](long v, long ncl, int m) {
+        if (cellk) return (double)(m + 1);
         const long c0 = std::max(v - 1, 0L), c1 = std::min(v, ncl - 1);
         const long alo = m * c0, ahi = m * (c1 + 1);
         const long lo = (c0 == 0) ? alo : alo + 1, hi = (c1 == ncl - 1) ? ahi : ahi - 1;
         return (double)(hi - lo + 1);
       };
       double inv = 0.0, sumC = 0.0;
-      long vx = n[0] + 1, vy = d > 1 ? n[1] + 1 : 1, vz = d > 2 ? n[2] + 1 : 1;
+      const long e = cellk ? 0 : 1;
+      long vx = n[0] + e, vy = d > 1 ? n[1] + e : 1, vz = d > 2 ? n[2] + e : 1;
       for (long z = 0; z < vz; ++z)
         for (long y = 0; y < vy; ++y)
           for (long x = 0; x < vx; ++x) {

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -61,13 +62,17 @@ void run_request(stfem_server s, Request &R) {
   stfem_h h = nullptr;
   double *state = nullptr;
   long long n_slab = 0, n_state = 0;
+  std::string msg;
   R.slab_ms.assign(q.n_slabs, 0.0);
   do {
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
       status = STFEM_ERR_CUDA;
       break;
     }
-    if ((status = stfem_setup(&q.mesh, &q.deg, &q.mat, &q.bcs, q.tau, &h)) < 0) break;
+    if ((status = stfem_setup(&q.mesh, &q.deg, &q.mat, &q.bcs, q.tau, &h)) < 0) {
+      msg = stfem_last_error(nullptr);
+      break;
+    }
     stfem_set_stream(h, stream);
     if ((status = stfem_gmg_setup(h, &q.gmg)) < 0) break;
     stfem_level_info(h, -1, &n_slab, &n_state, nullptr, nullptr);
@@ -101,6 +106,8 @@ void run_request(stfem_server s, Request &R) {
     stfem_footprint_bytes(h, &bytes);
     R.info.device_bytes = bytes + n_state * (long long)sizeof(double);
   } while (false);
+  if (status < 0 && msg.empty()) msg = h ? stfem_last_error(h) : "CUDA stream or state allocation failed";
+  std::snprintf(R.info.error, sizeof(R.info.error), "%s", status < 0 ? msg.c_str() : "");
   if (state) cudaFree(state);
   if (h) stfem_destroy(h);
   if (stream) cudaStreamDestroy(stream);

@@ -116,9 +116,16 @@ __device__ __forceinline__ void lattice_coords(long idx, const int *dims, int di
 template <typename T, int Q, int D, int G>
 __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
                                                  const T *__restrict__ x, const T *__restrict__ rhs,
-                                                 T *__restrict__ y, int mode) {
+                                                 T *__restrict__ y, int mode, int nb, long cstride) {
   constexpr int NA = 4 * Q * D;
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  // nb right-hand sides (column stride cstride): consecutive CTAs take the
+  // same nodes of different columns, so the node blocks are read from DRAM
+  // about once and from L2 by the other columns
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  x += (long)col * cstride;
+  y += (long)col * cstride;
+  if (rhs) rhs += (long)col * cstride;
   const long node = gid / G;
   const int lane = threadIdx.x % G;
   T acc[NA];
@@ -742,9 +749,13 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
 // d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).
 template <typename T>
 __global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *__restrict__ ipos,
-                               const T *__restrict__ scale, const T *__restrict__ y, T *__restrict__ d, int zero) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                               const T *__restrict__ scale, const T *__restrict__ y, T *__restrict__ d, int zero,
+                               int nb, long ystride) {
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  y += (long)col * ystride;
+  d += (long)col * N;
   T acc = T(0);
   for (int e = iptr[i]; e < iptr[i + 1]; ++e) acc += y[ipos[e]];
   d[i] = (zero ? T(0) : d[i]) + scale[i] * acc;
@@ -760,8 +771,12 @@ template <typename T, int D>
 __global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_out, long ns_in, long R_in,
                            const int *__restrict__ up, const int *__restrict__ uc, const T *__restrict__ uv,
                            const int *__restrict__ pp, const int *__restrict__ pc, const T *__restrict__ pv,
-                           const T *__restrict__ in, T *__restrict__ out, int add) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                           const T *__restrict__ in, T *__restrict__ out, int add, int nb, long in_stride,
+                           long out_stride) {
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  in += (long)col * in_stride;
+  out += (long)col * out_stride;
   const long nuq = 2 * nu_out * q;
   if (i < nuq) {
     const long node = i % nu_out;
@@ -795,10 +810,14 @@ __global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_
 // ---------------------------------------------------------------- coarse
 // x = Ainv b with a dense FP64 inverse (one warp per row).
 template <typename T>
-__global__ void k_coarse(long n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x) {
-  const long row = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void k_coarse(long n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x,
+                         int nb) {
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long row = ((long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
+  b += (long)col * n;
+  x += (long)col * n;
   double acc = 0.0;
   const double *a = Ainv + row * n;
   for (long j = lane; j < n; j += 32) acc += a[j] * (double)b[j];
@@ -810,6 +829,14 @@ template <typename A, typename B>
 __global__ void k_convert(long n, const A *__restrict__ a, B *__restrict__ b) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (B)a[i];
+}
+
+// b[c * sb + i] = a[c * sa + i] for nb columns of n entries (with conversion)
+template <typename A, typename B>
+__global__ void k_copy_cols(long n, int nb, const A *__restrict__ a, long sa, B *__restrict__ b, long sb) {
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  if (i < n) b[(long)col * sb + i] = (B)a[(long)col * sa + i];
 }
 
 // ---------------------------------------------------------------- BLAS-1 (FP64)
@@ -931,7 +958,7 @@ __global__ void k_div(long n, const double *__restrict__ src, double *__restrict
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double s = div ? *div : div_host;
-  dst[i] = src[i] / s;
+  dst[i] = s != 0.0 ? src[i] / s : 0.0; // a zero column (finished right-hand side) stays zero
 }
 
 // Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
@@ -954,8 +981,8 @@ __global__ void k_givens(int j, int m1, const double *__restrict__ h1, const dou
   }
   const double a = col[j], b = col[j + 1];
   const double rho = hypot(a, b);
-  cs[j] = a / rho;
-  sn[j] = b / rho;
+  cs[j] = rho != 0.0 ? a / rho : 1.0;
+  sn[j] = rho != 0.0 ? b / rho : 0.0;
   col[j] = rho;
   col[j + 1] = 0.0;
   g[j + 1] = -sn[j] * g[j];
@@ -1252,8 +1279,9 @@ struct DLevel {
   int maxCs = 0;
   DiagCoef<T> dc{};
   double transfer_bytes = 0.0, transfer_nnz = 0.0;
-  // work vectors
+  // work vectors: ncols columns of N (b, d, r) and of sumC (ybuf)
   T *b = nullptr, *d = nullptr, *r = nullptr;
+  int ncols = 1;
   // transfer from level l-1 (valid for l >= 1): P rows fine, R rows coarse
   int *Pu_p = nullptr, *Pu_c = nullptr, *Pp_p = nullptr, *Pp_c = nullptr;
   int *Ru_p = nullptr, *Ru_c = nullptr, *Rp_p = nullptr, *Rp_c = nullptr;
@@ -1281,6 +1309,8 @@ struct stfem_ctx {
   int precision = -1;
   double omega = 0.7;
   int nsweeps = 1;
+  int patch_kind = STFEM_PATCHES_VERTEX, update = STFEM_UPDATE_AVERAGE;
+  int stop = STFEM_STOP_RELATIVE;
   double *coarse_inv = nullptr;
   // FGMRES workspace
   int mcap = 0;
@@ -1315,6 +1345,20 @@ struct stfem_ctx {
   std::vector<GraphRec> graphs;
   bool use_graphs = true;
   std::vector<std::pair<int, size_t>> pending; // (class, index of start event)
+  // several right-hand sides solved together: one FGMRES per column, all
+  // columns preconditioned by one batched V-cycle
+  int nrhs_cap = 1;
+  struct Batch {
+    int nb = 0, m = 0;
+    long sw = 0; // stride of the per-column small arrays
+    double *V = nullptr, *Zd = nullptr, *zt = nullptr, *w = nullptr, *rvec = nullptr, *rhs = nullptr,
+           *xs = nullptr;
+    float *Zf = nullptr;
+    double *small = nullptr;  // per column: H, cs, sn, g, y, h1, h2, hnorm
+    double *norms = nullptr;  // [nb] squared norms, then [nb][2] statuses
+    double *host = nullptr;   // pinned copy of norms
+    std::vector<GraphRec> graphs;
+  } bt;
 };
 
 namespace {
@@ -1404,19 +1448,20 @@ struct SpmvLanes {
 
 template <typename T, int Q, int D>
 void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
-                    int mode) {
+                    int mode, int nb) {
   constexpr int G = SpmvLanes<T, D>::G;
   const long threads = (L.nb.nu + L.nb.np) * G;
-  k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256), 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode);
+  k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode, nb,
+                                                                    L.N);
 }
 
 template <typename T, int Q>
 void launch_spmv_q(cudaStream_t s, int d, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs,
-                   T *y, int mode) {
+                   T *y, int mode, int nb) {
   if (d == 2)
-    launch_spmv_qd<T, Q, 2>(s, L, tc, x, rhs, y, mode);
+    launch_spmv_qd<T, Q, 2>(s, L, tc, x, rhs, y, mode, nb);
   else
-    launch_spmv_qd<T, Q, 3>(s, L, tc, x, rhs, y, mode);
+    launch_spmv_qd<T, Q, 3>(s, L, tc, x, rhs, y, mode, nb);
 }
 
 // algorithmic bytes of one Kronecker SpMV: the node-block operator once, x and y
@@ -1426,18 +1471,20 @@ double spmv_bytes(const DLevel<T> &L, int q, int mode) {
   return L.nb_bytes + (double)q * L.ns * sizeof(T) * (mode ? 3 : 2);
 }
 
+// nb > 1: nb columns of x, rhs, y with column stride L.N
 template <typename T>
 void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
-                 int mode) {
-  Launch G_(h, STFEM_KCLASS_SPMV, spmv_bytes(L, tc.q, mode), L.nb_flops * tc.q);
+                 int mode, int nb = 1) {
+  Launch G_(h, STFEM_KCLASS_SPMV, L.nb_bytes + (spmv_bytes(L, tc.q, mode) - L.nb_bytes) * nb,
+            L.nb_flops * tc.q * nb);
   cudaStream_t s = h->stream;
   const int d = h->dim;
   switch (tc.q) {
-  case 1: launch_spmv_q<T, 1>(s, d, L, tc, x, rhs, y, mode); break;
-  case 2: launch_spmv_q<T, 2>(s, d, L, tc, x, rhs, y, mode); break;
-  case 3: launch_spmv_q<T, 3>(s, d, L, tc, x, rhs, y, mode); break;
-  case 4: launch_spmv_q<T, 4>(s, d, L, tc, x, rhs, y, mode); break;
-  default: launch_spmv_q<T, 5>(s, d, L, tc, x, rhs, y, mode); break;
+  case 1: launch_spmv_q<T, 1>(s, d, L, tc, x, rhs, y, mode, nb); break;
+  case 2: launch_spmv_q<T, 2>(s, d, L, tc, x, rhs, y, mode, nb); break;
+  case 3: launch_spmv_q<T, 3>(s, d, L, tc, x, rhs, y, mode, nb); break;
+  case 4: launch_spmv_q<T, 4>(s, d, L, tc, x, rhs, y, mode, nb); break;
+  default: launch_spmv_q<T, 5>(s, d, L, tc, x, rhs, y, mode, nb); break;
   }
 }
 
@@ -1692,7 +1739,7 @@ void set_diag(DLevel<T> &D, const stfem::TimeDiag &td) {
 }
 
 template <typename T>
-int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omega) {
+int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omega, int update) {
   D.npatch = P.npatch;
   D.maxC = *std::max_element(P.size.begin(), P.size.end());
   D.form = P.form;
@@ -1741,11 +1788,30 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
       h->err = "a degree of freedom belongs to no patch";
       return STFEM_ERR_STATE;
     }
-    scale[i] = omega / c;
+    scale[i] = update == STFEM_UPDATE_OVERWRITE ? omega : omega / c;
+  }
+  if (update == STFEM_UPDATE_OVERWRITE) {
+    // the last patch holding a dof (positions are in patch order) wins
+    std::vector<int> last(D.N);
+    for (long i = 0; i < D.N; ++i) last[i] = pos[cnt[i + 1] - 1];
+    pos.swap(last);
+    for (long i = 0; i <= D.N; ++i) cnt[i] = (int)i;
   }
   CKR(upload(h, &D.iptr, cnt));
   CKR(upload(h, &D.ipos, pos));
   CKR(upload(h, &D.scale, scale));
+  return 0;
+}
+
+// Level work vectors with nb columns (b, d, r of N; the patch results of sumC).
+template <typename T>
+int ensure_columns(stfem_h h, DLevel<T> &D, int nb) {
+  if (D.ncols >= nb) return 0;
+  CKR(dalloc(h, &D.b, (size_t)nb * D.N));
+  CKR(dalloc(h, &D.d, (size_t)nb * D.N));
+  CKR(dalloc(h, &D.r, (size_t)nb * D.N));
+  if (D.sumC > 0) CKR(dalloc(h, &D.ybuf, (size_t)nb * D.sumC));
+  D.ncols = nb;
   return 0;
 }
 
@@ -1868,14 +1934,16 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
   return 0;
 }
 
+// nb columns: res with column stride L.N, results with column stride L.sumC
 template <typename T>
-void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res) {
-  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes, L.patch_flops);
-  launch_patch_apply_to<T>(h, L, res, L.ybuf);
+void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res, int nb = 1) {
+  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes * nb, L.patch_flops * nb);
+  for (int c = 0; c < nb; ++c) launch_patch_apply_to<T>(h, L, res + (long)c * L.N, L.ybuf + (long)c * L.sumC);
 }
 
+// nsw sweeps of Algorithm 4.1 on level l for nb columns of the level buffers
 template <typename T>
-void smooth(stfem_h h, int l, int nsw, bool zero_init) {
+void smooth(stfem_h h, int l, int nsw, bool zero_init, int nb = 1) {
   DLevel<T> &L = levels<T>(h)[l];
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
   cudaStream_t s = h->stream;
@@ -1883,70 +1951,78 @@ void smooth(stfem_h h, int l, int nsw, bool zero_init) {
     const bool zero = zero_init && it == 0;
     const T *res = L.b;
     if (!zero) {
-      launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1);
+      launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1, nb);
       res = L.r;
     }
-    launch_patch_apply<T>(h, L, res);
+    launch_patch_apply<T>(h, L, res, nb);
     {
       Launch G_(h, STFEM_KCLASS_UPDATE,
-                (double)L.N * (4.0 + 3.0 * sizeof(T)) + (double)L.sumC * (4.0 + sizeof(T)), (double)L.sumC + 2.0 * L.N);
-      k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d,
-                                                           zero ? 1 : 0);
+                ((double)L.N * (4.0 + 3.0 * sizeof(T)) + (double)L.sumC * (4.0 + sizeof(T))) * nb,
+                ((double)L.sumC + 2.0 * L.N) * nb);
+      k_vanka_update<T><<<grid_for(L.N, 256) * nb, 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d,
+                                                                zero ? 1 : 0, nb, L.sumC);
     }
   }
 }
 
 template <typename T>
-void restrict_to(stfem_h h, int l, const T *rf, T *bc) {
+void restrict_to(stfem_h h, int l, const T *rf, T *bc, int nb = 1) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
-  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
+  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) * nb + F.transfer_bytes,
+            2.0 * F.transfer_nnz * nb);
   const long nu = C.R / h->dim, np = C.S, nt = (2 * nu + np) * h->q;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
-                                                                     F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
+    k_transfer<T, 2><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+                                                                          F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf,
+                                                                          bc, 0, nb, F.N, C.N);
   else
-    k_transfer<T, 3><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
-                                                                     F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0);
+    k_transfer<T, 3><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
+                                                                          F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf,
+                                                                          bc, 0, nb, F.N, C.N);
 }
 
 template <typename T>
-void prolongate_add(stfem_h h, int l, const T *dc, T *df) {
+void prolongate_add(stfem_h h, int l, const T *dc, T *df, int nb = 1) {
   DLevel<T> &F = levels<T>(h)[l];
   DLevel<T> &C = levels<T>(h)[l - 1];
-  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) + F.transfer_bytes, 2.0 * F.transfer_nnz);
+  Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) * nb + F.transfer_bytes,
+            2.0 * F.transfer_nnz * nb);
   const long nu = F.R / h->dim, np = F.S, nt = (2 * nu + np) * h->q;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
-                                                                     F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
+    k_transfer<T, 2><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+                                                                          F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc,
+                                                                          df, 1, nb, C.N, F.N);
   else
-    k_transfer<T, 3><<<grid_for(nt, 128), 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
-                                                                     F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1);
+    k_transfer<T, 3><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
+                                                                          F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc,
+                                                                          df, 1, nb, C.N, F.N);
 }
 
 template <typename T>
-void coarse(stfem_h h, const T *b, T *x) {
+void coarse(stfem_h h, const T *b, T *x, int nb = 1) {
   const long n = levels<T>(h)[0].N;
-  Launch G_(h, STFEM_KCLASS_COARSE, (double)n * n * 8.0 + 2.0 * n * sizeof(T), 2.0 * n * n);
-  k_coarse<T><<<grid_for(n * 32, 256), 256, 0, h->stream>>>(n, h->coarse_inv, b, x);
+  Launch G_(h, STFEM_KCLASS_COARSE, (double)n * n * 8.0 + 2.0 * n * sizeof(T) * nb, 2.0 * n * n * nb);
+  k_coarse<T><<<grid_for(n * 32, 256) * nb, 256, 0, h->stream>>>(n, h->coarse_inv, b, x, nb);
 }
 
-// V-cycle on level l for A_l d_l = b_l (both in the level's buffers), d from 0.
+// V-cycle on level l for A_l d_l = b_l (both in the level's buffers), d from
+// 0; nb columns (column stride N of each level) at once.
 template <typename T>
-void vcycle(stfem_h h, int l) {
+void vcycle(stfem_h h, int l, int nb = 1) {
   std::vector<DLevel<T>> &Ls = levels<T>(h);
   if (l == 0) {
-    coarse<T>(h, Ls[0].b, Ls[0].d);
+    coarse<T>(h, Ls[0].b, Ls[0].d, nb);
     return;
   }
   DLevel<T> &L = Ls[l];
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
-  smooth<T>(h, l, h->nsweeps, true);
-  launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1);
-  restrict_to<T>(h, l, L.r, Ls[l - 1].b);
-  vcycle<T>(h, l - 1);
-  prolongate_add<T>(h, l, Ls[l - 1].d, L.d);
-  smooth<T>(h, l, h->nsweeps, false);
+  smooth<T>(h, l, h->nsweeps, true, nb);
+  launch_spmv<T>(h, L, tc, L.d, L.b, L.r, 1, nb);
+  restrict_to<T>(h, l, L.r, Ls[l - 1].b, nb);
+  vcycle<T>(h, l - 1, nb);
+  prolongate_add<T>(h, l, Ls[l - 1].d, L.d, nb);
+  smooth<T>(h, l, h->nsweeps, false, nb);
 }
 
 // z = M^{-1} v with one V-cycle in the GMG precision; v, z FP64 (z may be FP32 storage)
@@ -2083,12 +2159,14 @@ int enqueue_iteration(stfem_h h, int j, int m1) {
   return 0;
 }
 
-// Runs iteration j from its captured graph (captured on first use), or
-// eagerly when profiling (per-launch events) or on the legacy stream.
-int run_iteration(stfem_h h, int j, int m1) {
-  const bool graphs = h->use_graphs && !h->prof && h->stream != 0 && j < (int)h->graphs.size();
-  if (!graphs) return enqueue_iteration(h, j, m1);
-  stfem_ctx::GraphRec &g = h->graphs[j];
+// Runs the work enqueue() issues from its captured graph gv[j] (captured on
+// first use), or eagerly when profiling (per-launch events) or on the legacy
+// stream.
+template <typename F>
+int run_captured(stfem_h h, std::vector<stfem_ctx::GraphRec> &gv, int j, F enqueue) {
+  const bool graphs = h->use_graphs && !h->prof && h->stream != 0 && j < (int)gv.size();
+  if (!graphs) return enqueue();
+  stfem_ctx::GraphRec &g = gv[j];
   if (!g.exec) {
     stfem_ctx::KStat before[STFEM_KCLASS_COUNT];
     for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) before[k] = h->kstat[k];
@@ -2097,9 +2175,9 @@ int run_iteration(stfem_h h, int j, int m1) {
     if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       h->use_graphs = false;
-      return enqueue_iteration(h, j, m1);
+      return enqueue();
     }
-    const int rc = enqueue_iteration(h, j, m1);
+    const int rc = enqueue();
     const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
     if (rc < 0) {
       if (graph) cudaGraphDestroy(graph);
@@ -2112,7 +2190,7 @@ int run_iteration(stfem_h h, int j, int m1) {
       h->use_graphs = false;
       for (int k = 0; k < STFEM_KCLASS_COUNT; ++k) h->kstat[k] = before[k];
       h->launches = l0;
-      return enqueue_iteration(h, j, m1);
+      return enqueue();
     }
     cudaGraphDestroy(graph);
     // the capture only recorded the launches: keep their accounting with the
@@ -2136,6 +2214,10 @@ int run_iteration(stfem_h h, int j, int m1) {
   return 0;
 }
 
+int run_iteration(stfem_h h, int j, int m1) {
+  return run_captured(h, h->graphs, j, [&]() { return enqueue_iteration(h, j, m1); });
+}
+
 int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it, int *iters, double *relres) {
   CKR(ensure_workspace(h, m));
   DLevel<double> &F = h->L64.back();
@@ -2156,7 +2238,11 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
     h->err = "initial residual is not finite";
     return STFEM_ERR_BREAKDOWN;
   }
-  if (beta0 == 0.0) return STFEM_OK;
+  const double bound = h->stop == STFEM_STOP_ABSOLUTE ? tol : tol * beta0;
+  if (beta0 == 0.0 || beta0 <= bound) {
+    *relres = beta0 > 0.0 ? 1.0 : 0.0;
+    return STFEM_OK;
+  }
   double beta = beta0;
   int it = 0;
   const int m1 = m + 1;
@@ -2184,7 +2270,7 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
       ++it;
       jlast = j;
       h->hist.push_back(res / beta0);
-      if (res <= tol * beta0 || it >= max_it || hn == 0.0) {
+      if (res <= bound || it >= max_it || hn == 0.0) {
         stop = true;
         break;
       }
@@ -2213,11 +2299,265 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
       h->err = "FGMRES breakdown: non-finite residual";
       return STFEM_ERR_BREAKDOWN;
     }
-    if (res <= tol * beta0) return STFEM_OK;
+    if (res <= bound) return STFEM_OK;
     if (it >= max_it) return STFEM_NOT_CONVERGED;
     (void)stop;
     beta = res;
   }
+}
+
+// ---------------------------------------------------------------- several right-hand sides
+// Columns c = 0..nb-1 of the batch: one flexible GMRES per column (its own
+// Krylov basis, Hessenberg matrix and rotations), all columns advanced in
+// lockstep so that the V-cycle preconditions the nb vectors v_j together
+// (the patch inverses and level operators are read once per sweep for all
+// columns).  A column that has met its bound keeps iterating harmlessly until
+// the others finish the cycle; it uses only its first k_c iterations.
+struct BatchCol {
+  double *V, *H, *cs, *sn, *g, *y, *h1, *h2, *hnorm, *hn2, *status;
+};
+
+BatchCol batch_col(stfem_h h, int c) {
+  stfem_ctx::Batch &B = h->bt;
+  const long N = h->L64.back().N;
+  const int m = B.m, m1 = m + 1;
+  double *sm = B.small + (long)c * B.sw;
+  BatchCol k;
+  k.V = B.V + (long)c * m1 * N;
+  k.H = sm;
+  k.cs = k.H + (long)m1 * m;
+  k.sn = k.cs + m;
+  k.g = k.sn + m;
+  k.y = k.g + m1;
+  k.h1 = k.y + m;
+  k.h2 = k.h1 + m1;
+  k.hnorm = k.h2 + m1;
+  k.hn2 = B.norms + c;
+  k.status = B.norms + h->nrhs_cap + 2 * c;
+  return k;
+}
+
+int ensure_batch_workspace(stfem_h h, int m) {
+  stfem_ctx::Batch &B = h->bt;
+  if (m > MAXM) {
+    h->err = "restart length above the supported maximum";
+    return STFEM_ERR_ARG;
+  }
+  if (m <= B.m) return 0;
+  const long N = h->L64.back().N;
+  const int nb = h->nrhs_cap, m1 = m + 1;
+  CKR(dalloc(h, &B.V, (size_t)nb * m1 * N));
+  if (h->precision == STFEM_MIXED) {
+    CKR(dalloc(h, &B.Zf, (size_t)nb * m * N));
+  } else {
+    CKR(dalloc(h, &B.Zd, (size_t)nb * m * N));
+  }
+  CKR(dalloc(h, &B.zt, (size_t)nb * N));
+  CKR(dalloc(h, &B.w, (size_t)nb * N));
+  CKR(dalloc(h, &B.rvec, (size_t)nb * N));
+  if (!B.rhs) {
+    CKR(dalloc(h, &B.rhs, (size_t)nb * N));
+    CKR(dalloc(h, &B.xs, (size_t)nb * N));
+  }
+  B.sw = (long)m1 * m + 2L * m + m1 + m + 2L * m1 + 1;
+  CKR(dalloc(h, &B.small, (size_t)nb * B.sw));
+  if (!B.norms) {
+    CKR(dalloc(h, &B.norms, (size_t)3 * nb));
+    CK(cudaHostAlloc((void **)&B.host, (size_t)3 * nb * sizeof(double), cudaHostAllocDefault));
+  }
+  B.m = m;
+  for (auto &g : B.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  B.graphs.assign(m, stfem_ctx::GraphRec());
+  B.nb = 0;
+  return 0;
+}
+
+// Same as enqueue_iteration, for nb columns: one batched V-cycle and one
+// batched SpMV, then CGS2 and the Givens update per column; the statuses of
+// all columns are copied to pinned memory at once.
+int enqueue_iteration_batch(stfem_h h, int j, int m1, int nb) {
+  stfem_ctx::Batch &B = h->bt;
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  const int m = m1 - 1;
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  cudaStream_t s = h->stream;
+  const int nbk = grid_for(N, 256);
+  const int L = h->nlev - 1;
+  const double *vj = B.V + (long)j * N; // column stride m1 * N
+  const double *zsp = nullptr;          // z_j of all columns, column stride N, FP64
+  if (h->precision == STFEM_FP64) {
+    DLevel<double> &G = h->L64[L];
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 16.0 * nb, 0.0);
+      k_copy_cols<double, double><<<nbk * nb, 256, 0, s>>>(N, nb, vj, (long)m1 * N, G.b, N);
+    }
+    vcycle<double>(h, L, nb);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 16.0 * nb, 0.0);
+      k_copy_cols<double, double><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.Zd + (long)j * N, (long)m * N);
+    }
+    zsp = G.d;
+  } else {
+    DLevel<float> &G = h->L32[L];
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * nb, 0.0);
+      k_copy_cols<double, float><<<nbk * nb, 256, 0, s>>>(N, nb, vj, (long)m1 * N, G.b, N);
+    }
+    vcycle<float>(h, L, nb);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 8.0 * nb, 0.0);
+      k_copy_cols<float, float><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.Zf + (long)j * N, (long)m * N);
+    }
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * nb, 0.0);
+      k_copy_cols<float, double><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.zt, N);
+    }
+    zsp = B.zt;
+  }
+  launch_spmv<double>(h, F, tc, zsp, nullptr, B.w, 0, nb);
+  for (int c = 0; c < nb; ++c) {
+    const BatchCol k = batch_col(h, c);
+    double *w = B.w + (long)c * N;
+    multidot(h, j + 1, k.V, N, w, N, k.h1);
+    axpy_dot(h, j + 1, k.V, N, k.h1, w, N, k.h2, 0);
+    axpy_dot(h, j + 1, k.V, N, k.h2, w, N, k.hn2, 1);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, (double)(4 * j + 8) * 8.0, (double)(6 * j + 10));
+      k_givens<<<1, 1, 0, s>>>(j, m1, k.h1, k.h2, k.hn2, k.H, k.cs, k.sn, k.g, k.hnorm, k.status);
+    }
+  }
+  CK(cudaMemcpyAsync(B.host + h->nrhs_cap, B.norms + h->nrhs_cap, 2 * (size_t)nb * sizeof(double),
+                     cudaMemcpyDeviceToHost, s));
+  if (j + 1 < m1)
+    for (int c = 0; c < nb; ++c) {
+      const BatchCol k = batch_col(h, c);
+      Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+      k_div<<<nbk, 256, 0, s>>>(N, B.w + (long)c * N, k.V + (long)(j + 1) * N, k.hnorm, 0.0);
+    }
+  return 0;
+}
+
+// r = b - A x for nb columns and ||r_c||^2 -> host[c]
+int batch_residuals(stfem_h h, int nb, const double *b, const double *x) {
+  stfem_ctx::Batch &B = h->bt;
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  launch_spmv<double>(h, F, tc, x, b, B.rvec, 1, nb);
+  for (int c = 0; c < nb; ++c) multidot(h, 1, B.rvec + (long)c * N, N, B.rvec + (long)c * N, N, B.norms + c);
+  CK(cudaMemcpyAsync(B.host, B.norms, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return 0;
+}
+
+// Flexible GMRES(m) for nb right-hand sides (device, column stride N):
+// every column is solved as by fgmres() alone (same stopping rule per
+// column); iters[c], relres[c] per column.  Returns the worst status.
+int fgmres_batch(stfem_h h, int nb, const double *b, double *x, double tol, int m, int max_it, int *iters,
+                 double *relres) {
+  CKR(ensure_batch_workspace(h, m));
+  stfem_ctx::Batch &B = h->bt;
+  if (B.nb != nb) { // graphs hold the column count in their launches
+    for (auto &g : B.graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    B.graphs.assign(B.m, stfem_ctx::GraphRec());
+    B.nb = nb;
+  }
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  cudaStream_t s = h->stream;
+  const int nbk = grid_for(N, 256);
+  const int m1 = m + 1;
+  std::vector<double> beta0(nb), bound(nb), beta(nb);
+  std::vector<int> active(nb, 0), it(nb, 0), kk(nb, 0), done(nb, 0);
+  CKR(batch_residuals(h, nb, b, x));
+  int worst = STFEM_OK;
+  for (int c = 0; c < nb; ++c) {
+    beta0[c] = std::sqrt(B.host[c]);
+    if (!std::isfinite(beta0[c])) {
+      h->err = "initial residual is not finite";
+      return STFEM_ERR_BREAKDOWN;
+    }
+    bound[c] = h->stop == STFEM_STOP_ABSOLUTE ? tol : tol * beta0[c];
+    active[c] = beta0[c] > 0.0 && beta0[c] > bound[c];
+    beta[c] = beta0[c];
+    iters[c] = 0;
+    relres[c] = beta0[c] > 0.0 && !active[c] ? 1.0 : 0.0;
+  }
+  for (;;) {
+    int nact = 0;
+    for (int c = 0; c < nb; ++c) nact += active[c];
+    if (nact == 0) break;
+    for (int c = 0; c < nb; ++c) {
+      const BatchCol k = batch_col(h, c);
+      const double bc = active[c] ? beta[c] : 0.0; // finished columns run on zeros
+      {
+        Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+        k_div<<<nbk, 256, 0, s>>>(N, B.rvec + (long)c * N, k.V, nullptr, bc);
+      }
+      {
+        Launch G_(h, STFEM_KCLASS_OTHER, 8.0, 0.0);
+        k_set<<<1, 1, 0, s>>>(k.g, bc);
+      }
+      done[c] = !active[c];
+      kk[c] = 0;
+    }
+    for (int j = 0; j < m; ++j) {
+      CKR(run_captured(h, B.graphs, j, [&]() { return enqueue_iteration_batch(h, j, m1, nb); }));
+      CK(cudaStreamSynchronize(s));
+      CK(cudaGetLastError());
+      bool all = true;
+      for (int c = 0; c < nb; ++c) {
+        if (done[c]) continue;
+        const double res = B.host[h->nrhs_cap + 2 * c], hn = B.host[h->nrhs_cap + 2 * c + 1];
+        if (!std::isfinite(res) || !std::isfinite(hn)) {
+          h->err = "FGMRES breakdown: non-finite Hessenberg entry in column " + std::to_string(c);
+          return STFEM_ERR_BREAKDOWN;
+        }
+        ++it[c];
+        kk[c] = j + 1;
+        if (res <= bound[c] || it[c] >= max_it || hn == 0.0) done[c] = 1;
+        all = all && done[c];
+      }
+      if (all) break;
+    }
+    for (int c = 0; c < nb; ++c) {
+      if (!active[c] || kk[c] == 0) continue;
+      const BatchCol k = batch_col(h, c);
+      {
+        Launch G_(h, STFEM_KCLASS_OTHER, (double)kk[c] * kk[c] * 8.0, (double)kk[c] * kk[c]);
+        k_backsolve<<<1, 1, 0, s>>>(kk[c], m1, k.H, k.g, k.y);
+      }
+      Launch G_(h, STFEM_KCLASS_BLAS1, (double)N * (16.0 + kk[c] * (h->precision == STFEM_FP64 ? 8.0 : 4.0)),
+                2.0 * kk[c] * N);
+      if (h->precision == STFEM_FP64)
+        k_update_x<double><<<nbk, 256, 0, s>>>(N, kk[c], B.Zd + (long)c * m * N, N, k.y, x + (long)c * N);
+      else
+        k_update_x<float><<<nbk, 256, 0, s>>>(N, kk[c], B.Zf + (long)c * m * N, N, k.y, x + (long)c * N);
+    }
+    CKR(batch_residuals(h, nb, b, x));
+    for (int c = 0; c < nb; ++c) {
+      if (!active[c]) continue;
+      const double res = std::sqrt(B.host[c]);
+      if (!std::isfinite(res)) {
+        h->err = "FGMRES breakdown: non-finite residual in column " + std::to_string(c);
+        return STFEM_ERR_BREAKDOWN;
+      }
+      iters[c] = it[c];
+      relres[c] = res / beta0[c];
+      beta[c] = res;
+      if (res <= bound[c]) {
+        active[c] = 0;
+      } else if (it[c] >= max_it) {
+        active[c] = 0;
+        worst = STFEM_NOT_CONVERGED;
+      }
+    }
+  }
+  return worst;
 }
 
 // A bounded wait inside a kernel timed out (reported through h->dev_err).
@@ -2459,7 +2799,8 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
       res = rT;
     }
     launch_patch_apply_to<T>(h, L, res, yT);
-    k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0);
+    k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0, 1,
+                                                         L.sumC);
   }
   k_convert<T, double><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, dT, d);
   CK(cudaGetLastError());
@@ -2541,7 +2882,10 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
     h->err = "cudaHostAlloc failed";
     return fail_setup(h, STFEM_ERR_CUDA);
   }
-  if (cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  // uploads went through the legacy stream: wait for them there (no
+  // device-wide synchronisation, which would also wait for, and can disturb
+  // the graph captures of, handles run by other threads)
+  if (cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     h->err = "device error during setup";
     return fail_setup(h, STFEM_ERR_CUDA);
   }
@@ -2552,7 +2896,10 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
 int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
   if (!h || !p) return STFEM_ERR_ARG;
   if (!(p->omega > 0.0) || p->n_sweeps < 1 || (p->precision != STFEM_FP64 && p->precision != STFEM_MIXED) ||
-      p->patch_form < STFEM_PATCH_AUTO || p->patch_form > STFEM_PATCH_TIME_DIAGONAL) {
+      p->patch_form < STFEM_PATCH_AUTO || p->patch_form > STFEM_PATCH_TIME_DIAGONAL ||
+      (p->patch_kind != STFEM_PATCHES_VERTEX && p->patch_kind != STFEM_PATCHES_CELL) ||
+      (p->update != STFEM_UPDATE_AVERAGE && p->update != STFEM_UPDATE_OVERWRITE) || p->n_rhs < 0 ||
+      p->n_rhs > STFEM_MAX_RHS) {
     h->err = "invalid GMG parameters";
     return STFEM_ERR_ARG;
   }
@@ -2562,6 +2909,9 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
   }
   h->omega = p->omega;
   h->nsweeps = p->n_sweeps;
+  h->patch_kind = p->patch_kind;
+  h->update = p->update;
+  h->nrhs_cap = std::max(1, p->n_rhs);
   h->precision = p->precision;
   const bool mixed = p->precision == STFEM_MIXED;
   if (mixed) {
@@ -2586,17 +2936,17 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
     stfem::Patches P;
     std::string err;
     if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err, true,
-                             form == STFEM_PATCH_TIME_DIAGONAL ? &td : nullptr) < 0) {
+                             form == STFEM_PATCH_TIME_DIAGONAL ? &td : nullptr, h->patch_kind) < 0) {
       h->err = err + " on level " + std::to_string(l);
       return STFEM_ERR_SINGULAR_PATCH;
     }
     if (mixed) {
       set_diag(h->L32[l], td);
-      CKR(upload_patches(h, h->L32[l], P, h->omega));
+      CKR(upload_patches(h, h->L32[l], P, h->omega, h->update));
       CKR(check_patch_shape(h, h->L32[l]));
     } else {
       set_diag(h->L64[l], td);
-      CKR(upload_patches(h, h->L64[l], P, h->omega));
+      CKR(upload_patches(h, h->L64[l], P, h->omega, h->update));
       CKR(check_patch_shape(h, h->L64[l]));
     }
   }
@@ -2607,7 +2957,24 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
     return STFEM_ERR_SINGULAR_PATCH;
   }
   CKR(upload(h, &h->coarse_inv, A0));
-  CK(cudaDeviceSynchronize());
+  if (h->nrhs_cap > 1)
+    for (int l = 0; l < h->nlev; ++l) {
+      if (mixed)
+        CKR(ensure_columns(h, h->L32[l], h->nrhs_cap));
+      else
+        CKR(ensure_columns(h, h->L64[l], h->nrhs_cap));
+    }
+  CK(cudaStreamSynchronize(0)); // uploads of the legacy stream (see stfem_setup)
+  return STFEM_OK;
+}
+
+int stfem_set_stop(stfem_h h, int mode) {
+  if (!h) return STFEM_ERR_ARG;
+  if (mode != STFEM_STOP_RELATIVE && mode != STFEM_STOP_ABSOLUTE) {
+    h->err = "unknown stopping rule";
+    return STFEM_ERR_ARG;
+  }
+  h->stop = mode;
   return STFEM_OK;
 }
 
@@ -2720,6 +3087,55 @@ int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart,
   return rc;
 }
 
+int slab_solve_batch(stfem_h h, int n_rhs, const double *rhs, double *x, double tol, int restart, int max_it,
+                     int *iters_host, double *rel_res_host) {
+  if (!h || !rhs || !x || !iters_host || !rel_res_host || restart < 1 || max_it < 0 || !(tol >= 0.0))
+    return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  if (n_rhs < 1 || n_rhs > h->nrhs_cap) {
+    h->err = "n_rhs must be between 1 and the n_rhs given to stfem_gmg_setup";
+    return STFEM_ERR_ARG;
+  }
+  const int rc = fgmres_batch(h, n_rhs, rhs, x, tol, restart, max_it, iters_host, rel_res_host);
+  CK(cudaStreamSynchronize(h->stream));
+  CKR(check_dev_err(h));
+  return rc;
+}
+
+int stfem_vcycle_batch(stfem_h h, int n_rhs, const double *b, double *d) {
+  if (!h || !b || !d) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  if (n_rhs < 1 || n_rhs > h->nrhs_cap) {
+    h->err = "n_rhs must be between 1 and the n_rhs given to stfem_gmg_setup";
+    return STFEM_ERR_ARG;
+  }
+  const int L = h->nlev - 1;
+  const long N = h->L64.back().N;
+  const int nbk = grid_for(N, 256);
+  cudaStream_t s = h->stream;
+  if (h->precision == STFEM_FP64) {
+    DLevel<double> &G = h->L64[L];
+    CK(cudaMemcpyAsync(G.b, b, (size_t)n_rhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    vcycle<double>(h, L, n_rhs);
+    CK(cudaMemcpyAsync(d, G.d, (size_t)n_rhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    DLevel<float> &G = h->L32[L];
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * n_rhs, 0.0);
+      k_copy_cols<double, float><<<nbk * n_rhs, 256, 0, s>>>(N, n_rhs, b, N, G.b, N);
+    }
+    vcycle<float>(h, L, n_rhs);
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * n_rhs, 0.0);
+      k_copy_cols<float, double><<<nbk * n_rhs, 256, 0, s>>>(N, n_rhs, G.d, N, d, N);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  CKR(check_dev_err(h));
+  return STFEM_OK;
+}
+
 int stfem_solve_history(stfem_h h, double *hist_host, int cap, int *n) {
   if (!h || !n) return STFEM_ERR_ARG;
   int m = std::min<int>(cap, (int)h->hist.size());
@@ -2728,19 +3144,21 @@ int stfem_solve_history(stfem_h h, double *hist_host, int cap, int *n) {
   return STFEM_OK;
 }
 
-int stfem_initial_state(stfem_h h, double *state) {
+int stfem_initial_state_at(stfem_h h, double t, double *state) {
   if (!h || !state) return STFEM_ERR_ARG;
   const stfem::Level &F = h->hl.back();
   {
     Launch G_(h, STFEM_KCLASS_OTHER, F.ns * 8.0, 0.0);
-    k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, h->t0, F.R, F.S, state);
+    k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, t, F.R, F.S, state);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return STFEM_OK;
 }
 
-static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) {
+int stfem_initial_state(stfem_h h, double *state) { return stfem_initial_state_at(h, h ? h->t0 : 0.0, state); }
+
+static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs, double t0) {
   DLevel<double> &F = h->L64.back();
   const stfem::Level &HF = h->hl.back();
   TimeCoef<double> one{};
@@ -2749,7 +3167,7 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) 
   one.W[0] = 0.0;
   launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0); // S1 * state
   const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
-  const double t_prev = h->t0 + slab * h->tau;
+  const double t_prev = t0 + slab * h->tau;
   const long ncell = HF.box.ncell;
   const long nsrc = (long)h->q * ncell * h->lt.nq;
   if (h->prob.id != STFEM_PROBLEM_NONE) {
@@ -2766,7 +3184,7 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs) 
 
 int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs) {
   if (!h || !prev_state || !rhs || slab < 0) return STFEM_ERR_ARG;
-  CKR(slab_rhs_async(h, slab, prev_state, rhs));
+  CKR(slab_rhs_async(h, slab, prev_state, rhs, h->t0));
   CK(cudaStreamSynchronize(h->stream));
   return STFEM_OK;
 }
@@ -2778,7 +3196,7 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
   DLevel<double> &F = h->L64.back();
   int worst = STFEM_OK;
   for (int n = 0; n < n_slabs; ++n) {
-    CKR(slab_rhs_async(h, first_slab + n, state, h->rhs));
+    CKR(slab_rhs_async(h, first_slab + n, state, h->rhs, h->t0));
     {
       Launch G_(h, STFEM_KCLASS_OTHER, F.N * 8.0 + F.ns * 8.0, 0.0);
       k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, state, h->xs);
@@ -2791,6 +3209,42 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
     if (rc > worst) worst = rc;
     CK(cudaMemcpyAsync(state, h->xs + (long)(h->q - 1) * F.ns, F.ns * sizeof(double), cudaMemcpyDeviceToDevice,
                        h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CKR(check_dev_err(h));
+  return worst;
+}
+
+int march_batch(stfem_h h, int n_rhs, const double *t0_host, int first_slab, int n_slabs, double *state,
+                double tol, int restart, int max_it, int *iters_host) {
+  if (!h || !t0_host || !state || n_slabs < 0 || first_slab < 0 || restart < 1 || max_it < 0 || !(tol >= 0.0))
+    return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  if (n_rhs < 1 || n_rhs > h->nrhs_cap) {
+    h->err = "n_rhs must be between 1 and the n_rhs given to stfem_gmg_setup";
+    return STFEM_ERR_ARG;
+  }
+  CKR(ensure_batch_workspace(h, restart));
+  stfem_ctx::Batch &B = h->bt;
+  DLevel<double> &F = h->L64.back();
+  int worst = STFEM_OK;
+  std::vector<int> it(n_rhs);
+  std::vector<double> rr(n_rhs);
+  for (int n = 0; n < n_slabs; ++n) {
+    for (int c = 0; c < n_rhs; ++c) {
+      double *st = state + (long)c * F.ns;
+      CKR(slab_rhs_async(h, first_slab + n, st, B.rhs + (long)c * F.N, t0_host[c]));
+      Launch G_(h, STFEM_KCLASS_OTHER, F.N * 8.0 + F.ns * 8.0, 0.0);
+      k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, st, B.xs + (long)c * F.N);
+    }
+    const int rc = fgmres_batch(h, n_rhs, B.rhs, B.xs, tol, restart, max_it, it.data(), rr.data());
+    if (iters_host)
+      for (int c = 0; c < n_rhs; ++c) iters_host[(long)n * n_rhs + c] = it[c];
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+    for (int c = 0; c < n_rhs; ++c)
+      CK(cudaMemcpyAsync(state + (long)c * F.ns, B.xs + (long)c * F.N + (long)(h->q - 1) * F.ns,
+                         F.ns * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
   CKR(check_dev_err(h));
@@ -2843,12 +3297,16 @@ const char *stfem_last_error(stfem_h h) { return h ? h->err.c_str() : g_setup_er
 
 void stfem_destroy(stfem_h h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  // every entry point has synchronised its stream before returning; cudaFree
+  // waits for the device work that may still use the memory
   for (void *p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (auto &g : h->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto &g : h->bt.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->bt.host) cudaFreeHost(h->bt.host);
   delete h;
 }
 

@@ -63,7 +63,7 @@ def test_admission_by_footprint():
     ids = [S.submit(p, c["slabs"], tol=c["tol"]) for p, c in zip(probs, reqs)]
     res = [S.result(i)[0] for i in ids]
     S.close()
-    assert all(r["status"] == 0 for r in res)
+    assert all(r["status"] == 0 for r in res), [(r["status"], r["error"]) for r in res]
     spans = sorted((r["t_admit"], r["t_done"], r["footprint"]) for r in res)
     for a in spans:  # at any admission time the running footprints fit the budget
         running = sum(f for (s0, s1, f) in spans if s0 <= a[0] < s1)

@@ -16,7 +16,7 @@ stfem = pytest.importorskip("paper_2303_06742_gb300")
 
 from oracle.space import BoxMesh, Material, SpatialOps
 from oracle.slab import Temporal, slab_matrix
-from oracle.gmg import vertices, patch_dofs, prolongation_scalar
+from oracle.gmg import vertices, patch_dofs, prolongation_scalar, cells, cell_patch_dofs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -106,6 +106,17 @@ def test_patch_sets_match_oracle(case):
     for level in range(1, len(ops)):
         host = stfem.host_patch_dofs(prob, level)
         ora = [patch_dofs(ops[level], T, v) for v in vertices(ops[level].mesh)]
+        assert len(host) == len(ora)
+        for a, b in zip(host, ora):
+            assert np.array_equal(np.sort(a), np.sort(b))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_cell_patch_sets_match_oracle(case):
+    prob, ops, T, tau = _pair(case)
+    for level in range(1, len(ops)):
+        host = stfem.host_patch_dofs(prob, level, stfem.PATCHES_CELL)
+        ora = [cell_patch_dofs(ops[level], T, c) for c in cells(ops[level].mesh)]
         assert len(host) == len(ora)
         for a, b in zip(host, ora):
             assert np.array_equal(np.sort(a), np.sort(b))
