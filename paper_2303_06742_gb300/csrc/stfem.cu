@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace stfem_dev;
@@ -744,6 +745,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
   }
 }
 
+#include "tc_patch.cuh"
+
 // d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
 // scale = omega / (number of patches holding the dof): Algorithm 4.1's
 // d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).
@@ -1274,6 +1277,13 @@ struct DLevel {
   int *iptr = nullptr, *ipos = nullptr;
   T *scale = nullptr, *ybuf = nullptr;
   double patch_bytes = 0.0, patch_flops = 0.0; // algorithmic, per patch-apply launch
+  double patch_inv_bytes = 0.0;                 // the inverse part of patch_bytes
+  // tensor-core layout of the time-diagonal inverses (FP32 levels of
+  // handles set up for several right-hand sides)
+  int tc = 0, tc_nst = 0;
+  uint32_t tc_cols = 0;
+  long long *ptoff = nullptr;
+  float *ptile = nullptr;
   int form = 0;       // 0 dense inverses, 1 time-diagonal form
   int *pcs = nullptr; // spatial patch size Cs (form 1)
   int maxCs = 0;
@@ -1760,9 +1770,11 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
       const double Cs = P.cs[p];
       const double q = C / Cs, nr = D.dc.nr, nc = D.dc.nc;
       D.patch_bytes += (nr + 2.0 * nc) * Cs * Cs * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
+      D.patch_inv_bytes += (nr + 2.0 * nc) * Cs * Cs * sizeof(T);
       D.patch_flops += (2.0 * nr + 8.0 * nc) * Cs * Cs + 4.0 * q * C;
     } else {
       D.patch_bytes += C * C * sizeof(T) + C * (4.0 + 2.0 * sizeof(T)) + 24.0;
+      D.patch_inv_bytes += C * C * sizeof(T);
       D.patch_flops += 2.0 * C * C;
     }
     (void)stored;
@@ -1812,6 +1824,68 @@ int ensure_columns(stfem_h h, DLevel<T> &D, int nb) {
   CKR(dalloc(h, &D.r, (size_t)nb * D.N));
   if (D.sumC > 0) CKR(dalloc(h, &D.ybuf, (size_t)nb * D.sumC));
   D.ncols = nb;
+  return 0;
+}
+
+// Tensor-core layout of the time-diagonal inverses of an FP32 level (see
+// tc_patch.cuh): per patch and slot a, A(m, k) in K blocks of 8, row groups
+// of 8, K cores of 4; real slot A = Z_a, complex slot A = [Re Z_a | Im Z_a];
+// rows padded to Cs8, K to Cs8 or 2 Cs8, with zeros.
+int upload_tc_tiles(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
+  const int nr = D.dc.nr, nc = D.dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  const int c8max = tcp::cs8(D.maxCs);
+  if (c8max * 32 > tcp::STAGE) {
+    h->err = "patches too large for the tensor-core patch apply";
+    return STFEM_ERR_ARG;
+  }
+  const size_t fixed = tcp::smem_bytes(0, D.maxCs, nrow);
+  const int nst = (int)std::min<size_t>(tcp::MAXSTAGES, (227u * 1024u - std::min<size_t>(fixed, 227u * 1024u)) /
+                                                            tcp::STAGE);
+  if (nst < 2) {
+    h->err = "patches too large for the tensor-core patch apply (shared memory)";
+    return STFEM_ERR_ARG;
+  }
+  const int ntile = (c8max + 127) / 128;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(16 * ntile)) cols *= 2;
+  std::vector<long long> off(P.npatch + 1, 0);
+  for (long p = 0; p < P.npatch; ++p) {
+    const long long c8 = tcp::cs8(P.cs[p]);
+    long long n = 0;
+    for (int a = 0; a < ns; ++a) n += (long long)tcp::kext(a, nr, (int)c8) * c8;
+    off[p + 1] = off[p] + n;
+  }
+  std::vector<float> tile((size_t)off[P.npatch], 0.f);
+  for (long p = 0; p < P.npatch; ++p) {
+    const int Cs = P.cs[p], c8 = tcp::cs8(Cs);
+    const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+    const double *inv = P.inv.data() + P.inv_off[p];
+    float *t = tile.data() + off[p];
+    for (int a = 0; a < ns; ++a) {
+      const int K = tcp::kext(a, nr, c8);
+      auto at = [&](int m, int k) -> float & {
+        return t[(size_t)(k / 8) * c8 * 8 + ((m / 8) * 2 + (k % 8) / 4) * 32 + (m % 8) * 4 + (k % 4)];
+      };
+      if (a < nr) {
+        const double *z = inv + (size_t)a * Cs * ldR;
+        for (int j = 0; j < Cs; ++j)
+          for (int m = 0; m < Cs; ++m) at(m, j) = (float)z[(size_t)j * ldR + m];
+      } else {
+        const double *z = inv + (size_t)nr * Cs * ldR + (size_t)(a - nr) * Cs * ldC;
+        for (int j = 0; j < Cs; ++j)
+          for (int m = 0; m < Cs; ++m) {
+            at(m, j) = (float)z[(size_t)j * ldC + 2 * m];
+            at(m, c8 + j) = (float)z[(size_t)j * ldC + 2 * m + 1];
+          }
+      }
+      t += (size_t)K * c8;
+    }
+  }
+  CKR(upload(h, &D.ptoff, off));
+  CKR(upload(h, &D.ptile, tile));
+  D.tc = 1;
+  D.tc_nst = nst;
+  D.tc_cols = cols;
   return 0;
 }
 
@@ -1912,6 +1986,11 @@ int prepare_stream_kernels(stfem_h h) {
   STFEM_SMEM_ATTR(double, 1); STFEM_SMEM_ATTR(double, 2); STFEM_SMEM_ATTR(double, 3);
   STFEM_SMEM_ATTR(double, 4); STFEM_SMEM_ATTR(double, 5);
 #undef STFEM_SMEM_ATTR
+  CK(cudaFuncSetAttribute(k_patch_apply_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(cudaFuncSetAttribute(k_patch_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(cudaFuncSetAttribute(k_patch_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(cudaFuncSetAttribute(k_patch_apply_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CK(cudaFuncSetAttribute(k_patch_apply_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   return 0;
 }
 
@@ -1934,10 +2013,35 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
   return 0;
 }
 
-// nb columns: res with column stride L.N, results with column stride L.sumC
+template <int Q>
+void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, int nb) {
+  const size_t smem = tcp::smem_bytes(L.tc_nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
+  const int grid = (int)std::min<long>(L.npatch, 152L);
+  k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)L.npatch, nb, L.pcs, L.pdoff, L.pdofs, L.ptoff,
+                                                             L.ptile, res, L.N, L.ybuf, L.sumC, L.dc, L.maxCs,
+                                                             L.tc_nst, L.tc_cols, h->dev_err);
+}
+
+// nb columns: res with column stride L.N, results with column stride
+// L.sumC.  Algorithmic bytes: the inverses once, the per-row traffic per
+// column (the tensor-core kernel reads each inverse once for all columns;
+// without it the columns are applied one after another).
 template <typename T>
 void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res, int nb = 1) {
-  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_bytes * nb, L.patch_flops * nb);
+  Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_inv_bytes + (L.patch_bytes - L.patch_inv_bytes) * nb,
+            L.patch_flops * nb);
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.tc) {
+      switch (h->q) {
+      case 1: launch_patch_tc_q<1>(h, L, res, nb); break;
+      case 2: launch_patch_tc_q<2>(h, L, res, nb); break;
+      case 3: launch_patch_tc_q<3>(h, L, res, nb); break;
+      case 4: launch_patch_tc_q<4>(h, L, res, nb); break;
+      default: launch_patch_tc_q<5>(h, L, res, nb); break;
+      }
+      return;
+    }
+  }
   for (int c = 0; c < nb; ++c) launch_patch_apply_to<T>(h, L, res + (long)c * L.N, L.ybuf + (long)c * L.sumC);
 }
 
@@ -2944,6 +3048,7 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       set_diag(h->L32[l], td);
       CKR(upload_patches(h, h->L32[l], P, h->omega, h->update));
       CKR(check_patch_shape(h, h->L32[l]));
+      if (h->nrhs_cap > 1 && form == STFEM_PATCH_TIME_DIAGONAL) CKR(upload_tc_tiles(h, h->L32[l], P));
     } else {
       set_diag(h->L64[l], td);
       CKR(upload_patches(h, h->L64[l], P, h->omega, h->update));

@@ -1,0 +1,358 @@
+// Batched time-diagonal patch apply on the 5th-generation tensor cores
+// (tcgen05, TF32 operands, FP32 accumulators in tensor memory), for nb <= 8
+// right-hand sides that share the patch inverses (Algorithm 4.1, line 6, with
+// A_P^{-1} in the time-diagonal form: y = (V (x) I) blockdiag(Z_a) (U (x) I) r).
+//
+// Included by stfem.cu after the bulk-copy / mbarrier helpers.
+//
+// Per patch and slot a the product z_a = Z_a x_a is one GEMM D = A B with
+//   real slot:    A = Z_a (Cs x Cs),            B = [X | 0]            (N = 16)
+//   complex slot: A = [Re Z_a | Im Z_a] (Cs x 2Cs), B = [[Xr, Xi], [-Xi, Xr]]
+// so that D = [Re z | Im z] (column n < 8: right-hand side n, real part;
+// n >= 8: imaginary part).  A is stored at setup in the canonical K-major
+// layout without swizzle (8 x 16-byte core matrices; per K-block of 8 values
+// the row groups of 8 rows, each holding its two K cores), so a contiguous
+// bulk copy lands in shared memory ready for the MMA descriptors: rows padded
+// to Cs8 = 8 ceil(Cs / 8), K to Cs8 (real) or 2 Cs8 (complex), with zeros.
+//
+// Warp roles (320 threads): warp 0 streams A through a ring of stages
+// (cp.async.bulk, mbarrier transaction counts); warp 1 owns the tensor
+// memory and one lane issues the MMAs; warps 2..9 gather and transform the
+// residual columns, write B, read D back (tcgen05.ld) and mix the result back
+// to the time nodes.  Every wait is bounded (clock64); on a timeout the CTA
+// sets *err and every role leaves at its next uniform decision point after
+// draining its own copies / MMAs.
+
+namespace tcp {
+
+constexpr int THREADS = 320;
+constexpr int NCONS = 256; // consumer threads (warps 2..9)
+constexpr int STAGE = 16384;
+constexpr int SLACK = 4096; // the last M tile of a K block reads up to 4 KB past it
+constexpr int MAXSTAGES = 8;
+constexpr long long WAIT = 4000000000LL;
+constexpr uint32_t IDESC = (1u << 4)         // D: FP32
+                           | (2u << 7)       // A: TF32
+                           | (2u << 10)      // B: TF32
+                           | ((16u >> 3) << 17) // N = 16
+                           | ((128u >> 4) << 24); // M = 128
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46); // descriptor version 1, no swizzle, base offset 0
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+               "l"(a), "l"(b), "r"(IDESC), "r"(accum)
+               : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+               " [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                 "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 2, %0;" ::"r"(NCONS) : "memory"); }
+
+__host__ __device__ __forceinline__ int cs8(int cs) { return (cs + 7) / 8 * 8; }
+// K extent of slot a (real slots first)
+__host__ __device__ __forceinline__ int kext(int a, int nr, int c8) { return a < nr ? c8 : 2 * c8; }
+// K blocks per stage copy
+__host__ __device__ __forceinline__ int kpb(int c8) { return STAGE / (c8 * 32); }
+
+struct Smem {
+  unsigned char *stage; // MAXSTAGES * STAGE + SLACK (nst used)
+  float *B;             // 16 x Kmax, core layout [kb][n group][k core]
+  float *xt;            // [slot rows (nr + 2 nc)][8][maxCs]: transformed residual, then z
+  uint64_t *full, *empty, *bfull, *afull, *aempty, *drain;
+  uint32_t *tmem;
+  volatile int *flag; // [0] abort, [1] consumer decision
+};
+
+__device__ __forceinline__ Smem carve(unsigned char *base, int nst, int maxCs, int nrow) {
+  Smem s;
+  size_t o = 0;
+  s.stage = base + o;
+  o += (size_t)nst * STAGE + SLACK;
+  s.B = reinterpret_cast<float *>(base + o);
+  o += (size_t)16 * 2 * cs8(maxCs) * sizeof(float);
+  s.xt = reinterpret_cast<float *>(base + o);
+  o += (size_t)nrow * 8 * maxCs * sizeof(float);
+  o = (o + 7) / 8 * 8;
+  s.full = reinterpret_cast<uint64_t *>(base + o);
+  s.empty = s.full + MAXSTAGES;
+  s.bfull = s.empty + MAXSTAGES;
+  s.afull = s.bfull + 1;
+  s.aempty = s.afull + 1;
+  s.drain = s.aempty + 1;
+  s.tmem = reinterpret_cast<uint32_t *>(s.drain + 1);
+  s.flag = reinterpret_cast<volatile int *>(s.tmem + 2);
+  return s;
+}
+
+__host__ __device__ inline size_t smem_bytes(int nst, int maxCs, int nrow) {
+  size_t o = (size_t)nst * STAGE + SLACK + (size_t)16 * 2 * cs8(maxCs) * sizeof(float) +
+             (size_t)nrow * 8 * maxCs * sizeof(float);
+  o = (o + 7) / 8 * 8;
+  return o + (2 * MAXSTAGES + 4) * 8 + 16;
+}
+
+} // namespace tcp
+
+template <int Q>
+__global__ void __launch_bounds__(tcp::THREADS, 1)
+    k_patch_apply_tc(int npatch, int nb, const int *__restrict__ pcs, const long long *__restrict__ pdoff,
+                     const int *__restrict__ pdofs, const long long *__restrict__ ptoff,
+                     const float *__restrict__ ptile, const float *__restrict__ res, long rstride,
+                     float *__restrict__ y, long ystride, DiagCoef<float> dc, int maxCs, int nst, uint32_t tcols,
+                     int *__restrict__ err) {
+  using namespace tcp;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  const Smem S = carve(smem_tc, nst, maxCs, nrow);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < nst; ++st) {
+      mbar_init(&S.full[st], 1);
+      mbar_init(&S.empty[st], 1);
+    }
+    mbar_init(S.bfull, 1);
+    mbar_init(S.afull, 1);
+    mbar_init(S.aempty, 1);
+    mbar_init(S.drain, 1);
+    S.flag[0] = 0;
+    S.flag[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(S.tmem)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *S.tmem;
+
+  if (warp == 0) {
+    // ---------------- producer: the A stages of every (patch, slot)
+    if (lane == 0) {
+      long long it = 0;
+      bool ok = true;
+      for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
+        const int c8 = cs8(pcs[p]), per = kpb(c8);
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(ptile + ptoff[p]);
+        for (int a = 0; a < ns && ok; ++a) {
+          const int nkb = kext(a, nr, c8) / 8;
+          for (int kb = 0; kb < nkb; kb += per) {
+            const int st = (int)(it % nst);
+            if (it >= nst && !mbar_wait(&S.empty[st], (uint32_t)(((it / nst) - 1) & 1), WAIT)) {
+              ok = false;
+              break;
+            }
+            if (S.flag[0]) {
+              ok = false;
+              break;
+            }
+            const uint32_t bytes = (uint32_t)(min(per, nkb - kb) * c8 * 32);
+            mbar_arrive_expect_tx(&S.full[st], bytes);
+            bulk_copy_g2s(S.stage + (size_t)st * STAGE, src, bytes, &S.full[st]);
+            src += bytes;
+            ++it;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 3);
+        S.flag[0] = 1;
+        for (long long k = (it > nst ? it - nst : 0); k < it; ++k)
+          mbar_wait(&S.full[k % nst], (uint32_t)((k / nst) & 1), WAIT);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      long long it = 0, nslot = 0;
+      bool ok = true;
+      const uint32_t bbase = smem_addr(S.B);
+      for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
+        const int c8 = cs8(pcs[p]), per = kpb(c8), ntile = (c8 + 127) / 128;
+        for (int a = 0; a < ns && ok; ++a, ++nslot) {
+          // B of this slot written; D free (its previous contents read back)
+          if (!mbar_wait(S.bfull, (uint32_t)(nslot & 1), WAIT) ||
+              (nslot > 0 && !mbar_wait(S.aempty, (uint32_t)((nslot - 1) & 1), WAIT)) || S.flag[0]) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const int nkb = kext(a, nr, c8) / 8;
+          for (int kb = 0; kb < nkb; kb += per) {
+            const int st = (int)(it % nst);
+            if (!mbar_wait(&S.full[st], (uint32_t)((it / nst) & 1), WAIT)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t sbase = smem_addr(S.stage + (size_t)st * STAGE);
+            const int nk = min(per, nkb - kb);
+            for (int j = 0; j < nk; ++j) {
+              const uint64_t bd = sdesc(bbase + (uint32_t)(kb + j) * 512u, 128u, 256u);
+              for (int mt = 0; mt < ntile; ++mt) {
+                const uint64_t ad = sdesc(sbase + (uint32_t)(j * c8 * 32 + mt * 4096), 128u, 256u);
+                mma_tf32(tbase + (uint32_t)(mt * 16), ad, bd, (kb + j) > 0 ? 1u : 0u);
+              }
+            }
+            commit(&S.empty[st]); // stage free once these MMAs have read it
+            ++it;
+          }
+          if (!ok) break;
+          commit(S.afull);
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 4);
+        S.flag[0] = 1;
+      }
+      // every MMA issued has completed before tensor memory is released
+      commit(S.drain);
+      mbar_wait(S.drain, 0u, WAIT);
+    }
+  } else {
+    // ---------------- consumers (threads 64 .. 319)
+    const int tid = threadIdx.x - 64;
+    const int cw = tid >> 5;          // consumer warp 0..7
+    const int quarter = warp & 3;     // tensor-memory lanes 32 quarter .. +31
+    const int group = cw >> 2;        // tiles mt = group, group + 2, ...
+    long long nslot = 0;
+    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+      // uniform decision to go on
+      cons_sync();
+      if (tid == 0) S.flag[1] = S.flag[0];
+      cons_sync();
+      if (S.flag[1]) break;
+      const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+      const long long doff = pdoff[p];
+      // gather the nb residual columns and transform to the slots:
+      // xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot
+      for (int idx = tid; idx < 8 * Cs; idx += NCONS) {
+        const int c = idx / Cs, m = idx - c * Cs;
+        float r[Q];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) r[b] = c < nb ? res[(long)c * rstride + pdofs[doff + b * Cs + m]] : 0.f;
+        for (int a = 0; a < ns; ++a) {
+          float re = 0.f, im = 0.f;
+#pragma unroll
+          for (int b = 0; b < Q; ++b) {
+            re += dc.U[(a * Q + b) * 2] * r[b];
+            im += dc.U[(a * Q + b) * 2 + 1] * r[b];
+          }
+          if (a < nr) {
+            S.xt[((size_t)a * 8 + c) * maxCs + m] = re;
+          } else {
+            const int row = nr + 2 * (a - nr);
+            S.xt[((size_t)row * 8 + c) * maxCs + m] = re;
+            S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m] = im;
+          }
+        }
+      }
+      cons_sync();
+      bool stop = false;
+      for (int a = 0; a < ns; ++a, ++nslot) {
+        // B of slot a (the previous slot's MMAs have completed: afull waited)
+        const int K = kext(a, nr, c8);
+        const bool cplx = a >= nr;
+        const int row = cplx ? nr + 2 * (a - nr) : a;
+        for (int idx = tid; idx < 16 * K; idx += NCONS) {
+          const int k = idx >> 4, n = idx & 15;
+          float v = 0.f;
+          if (!cplx) {
+            if (n < 8 && k < Cs) v = S.xt[((size_t)row * 8 + n) * maxCs + k];
+          } else {
+            const int kk = k < c8 ? k : k - c8;
+            if (kk < Cs) {
+              const float xr = S.xt[((size_t)row * 8 + (n & 7)) * maxCs + kk];
+              const float xi = S.xt[((size_t)(row + 1) * 8 + (n & 7)) * maxCs + kk];
+              v = k < c8 ? (n < 8 ? xr : xi) : (n < 8 ? -xi : xr);
+            }
+          }
+          const int kb = k >> 3, kc = (k >> 2) & 1, e = k & 3, ng = n >> 3, rr = n & 7;
+          S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4 + e] = v;
+        }
+        fence_async_smem();
+        cons_sync();
+        if (tid == 0) mbar_arrive(S.bfull);
+        // D of slot a complete
+        if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nslot & 1), WAIT) ? 0 : 1;
+        cons_sync();
+        if (S.flag[1]) {
+          if (tid == 0) {
+            atomicExch(err, 5);
+            S.flag[0] = 1;
+          }
+          stop = true;
+          break;
+        }
+        fence_after();
+        for (int mt = group; mt < ntile; mt += 2) {
+          float v[16];
+          __syncwarp();
+          ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
+          const int m = mt * 128 + quarter * 32 + lane;
+          if (m < Cs) {
+            if (!cplx) {
+              for (int c = 0; c < nb; ++c) S.xt[((size_t)row * 8 + c) * maxCs + m] = v[c];
+            } else {
+              for (int c = 0; c < nb; ++c) {
+                S.xt[((size_t)row * 8 + c) * maxCs + m] = v[c];
+                S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m] = v[8 + c];
+              }
+            }
+          }
+        }
+        fence_before();
+        cons_sync();
+        if (tid == 0) mbar_arrive(S.aempty);
+      }
+      if (stop) break;
+      // back to the time nodes: y[c][b][m]
+      for (int idx = tid; idx < nb * Q * Cs; idx += NCONS) {
+        const int c = idx / (Q * Cs), rem = idx - c * Q * Cs, b = rem / Cs, m = rem - b * Cs;
+        float val = 0.f;
+        for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * S.xt[((size_t)a * 8 + c) * maxCs + m];
+        for (int cc = 0; cc < nc; ++cc) {
+          const int a = nr + cc, row = nr + 2 * cc;
+          val += 2.f * (dc.V[(b * ns + a) * 2] * S.xt[((size_t)row * 8 + c) * maxCs + m] -
+                        dc.V[(b * ns + a) * 2 + 1] * S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m]);
+        }
+        y[(long)c * ystride + doff + rem] = val;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(tcols) : "memory");
+  }
+}

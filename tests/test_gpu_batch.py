@@ -38,10 +38,11 @@ def _solver(c, precision, nb):
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2.5e-3)])
 def test_vcycle_batch_columns(name, precision, tol):
     """Each column of the batched V-cycle equals the oracle's V-cycle of that
-    column, and (FP64) is bitwise the single-column V-cycle."""
+    column (MIXED: the tensor-core patch apply, TF32 bound of test_gpu_tc),
+    and is bitwise the single-column V-cycle of the same handle."""
     c = case(name)
     O = oracle_instance(c)
     S = _solver(c, precision, 4)
@@ -57,10 +58,7 @@ def test_vcycle_batch_columns(name, precision, tol):
         assert err < tol
         d1 = dev(np.zeros(n))
         S.vcycle(dev(B[k]), d1)
-        if precision == 0:
-            assert np.array_equal(host(d1), D[k])
-        else:
-            assert _rel(host(d1), D[k]) < 1e-5
+        assert np.array_equal(host(d1), D[k])
     S.close()
 
 
