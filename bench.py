@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--sweeps", type=int, default=1, help="pre- and post-smoothing sweeps per level")
     p.add_argument("--requests", type=int, default=64, help="requests of the serving workload")
     p.add_argument("--workers", type=int, default=8, help="concurrent requests of the serving workload")
+    p.add_argument("--rhs", type=int, default=1,
+                   help="right-hand sides solved together (marches from t0 = 0, 0.1, ...): >1 times the "
+                        "batched path with the tensor-core patch apply")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -449,6 +452,147 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ batched right-hand sides
+def batch_arm(args):
+    """n_rhs marches of the workload's operator (data phases t0 = 0.1 c) solved
+    together: one step = one slab of every march (n_rhs slab solves), through
+    march_batch with the tensor-core patch apply.  The same marches solved
+    one after another on the single-column path are timed beside it."""
+    import numpy as np
+    import torch
+    import paper_2303_06742_gb300 as st
+    import inputs
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _cases import gpu_problem
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    c = inputs.case(args.workload)
+    nb, tol, K, W = args.rhs, c["tol"], args.steps, args.warmup
+    t0s = [0.1 * k for k in range(nb)]
+    stream = torch.cuda.Stream()
+    ts = time.perf_counter()
+    S = st.Solver(gpu_problem(c), precision=st.MIXED, stream=stream, n_sweeps=args.sweeps, n_rhs=nb)
+    setup_s = time.perf_counter() - ts
+    states = torch.zeros((nb, S.n_state), dtype=torch.float64, device="cuda")
+    for k, t0 in enumerate(t0s):
+        S.initial_state_at(t0, states[k])
+
+    def run(first, steps, profile=False):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        its = []
+        if profile:
+            S.profile(True)
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for i in range(steps):
+                rc, it = S.march_batch(t0s, first + i, 1, states, tol=tol)
+                if rc != 0:
+                    raise RuntimeError("march_batch returned %d" % rc)
+                its.append(it[0].tolist())
+                evs[i + 1].record(stream)
+        stream.synchronize()
+        return [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)], its
+
+    run(0, W)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    l0 = S.launch_count()
+    ms, its = run(W, K)
+    torch.cuda.synchronize()
+    launches = S.launch_count() - l0
+    tw1 = time.time()
+    clk = clocks.stop(tw0, tw1)
+    total_ms = sum(ms)
+    KP = min(K, 3)
+    run(W + K, KP, profile=True)
+    prof = S.profile_read()
+    S.profile(False)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = K * nb * world / (total_ms / 1000.0)
+
+    # end to end: every step copies the nb right-hand sides and initial
+    # guesses from pinned host memory and the solutions back
+    E = min(K, 3)
+    n = S.n_slab
+    rhs_h = torch.empty((nb, n), dtype=torch.float64, pin_memory=True)
+    x0_h = torch.empty((nb, n), dtype=torch.float64, pin_memory=True)
+    x_h = torch.empty((nb, n), dtype=torch.float64, pin_memory=True)
+    with torch.cuda.stream(stream):
+        rd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for k in range(nb):
+            S.slab_rhs(0, states[k], rd)
+            rhs_h[k].copy_(rd)
+            x0_h[k].copy_(states[k].repeat(S.prob.q))
+    stream.synchronize()
+    rhs_d = torch.empty((nb, n), dtype=torch.float64, device="cuda")
+    x_d = torch.empty((nb, n), dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for _ in range(E):
+            rhs_d.copy_(rhs_h, non_blocking=True)
+            x_d.copy_(x0_h, non_blocking=True)
+            S.slab_solve_batch(nb, rhs_d, x_d, tol=tol)
+            x_h.copy_(x_d, non_blocking=True)
+        ev[1].record(stream)
+    stream.synchronize()
+    e2e_value = E * nb * world / (ev[0].elapsed_time(ev[1]) / 1000.0)
+    S.close()
+
+    # the same marches one after another on the single-column FP32 path
+    S1 = st.Solver(gpu_problem(c), precision=st.MIXED, stream=stream, n_sweeps=args.sweeps)
+    one = []
+    for k, t0 in enumerate(t0s[:min(nb, 2)]):
+        st1 = torch.zeros(S1.n_state, dtype=torch.float64, device="cuda")
+        S1.initial_state_at(t0, st1)
+        time_march(S1, torch, stream, st1, 0, 2, tol)
+        ms1, _ = time_march(S1, torch, stream, st1, 2, min(K, 4), tol)
+        one += ms1
+    S1.close()
+    single = 1000.0 / (sum(one) / len(one))
+    if rank != 0:
+        return
+    pa = prof["patch_apply"]
+    peak, peak_kind = peak_hbm()
+    achieved = pa["bytes"] / (pa["ms"] / 1000.0) / 1e9 if pa["ms"] > 0 else None
+    breakdown = {k: {"ms": v["ms"], "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-30),
+                     "launches": v["launches"]} for k, v in prof.items()}
+    print(json.dumps({
+        "metric": "slab solves/s", "value": value, "unit": "slab solves/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": total_ms / K, "p50_ms": pct(ms, 50), "p99_ms": pct(ms, 99),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload) + "; %d right-hand sides "
+                   "(marches from t0 = 0, 0.1, ..) solved together, one step = one slab of each" % nb,
+                   "precision": "TF32 tensor-core patch apply, FP32 V-cycle, FP64 FGMRES", "tol": tol,
+                   "l2": "no flush: the patch inverses streamed per sweep exceed L2"},
+        "iters_per_slab": its, "setup_s": setup_s,
+        "e2e": {"value": e2e_value, "unit": "slab solves/s", "h2d_bytes_per_step": 2 * nb * n * 8,
+                "d2h_bytes_per_step": nb * n * 8},
+        "single_column_path": {"value": single, "unit": "slab solves/s",
+                               "note": "same operator, one march at a time, FP32 CUDA-core patch apply"},
+        "roofline": {"kernel": "k_patch_apply_tc", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+                     "traffic": None, "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
+                     "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"]},
+        "breakdown": breakdown, "gpu_launches": launches, "clocks": clk,
+    }))
+
+
 # ------------------------------------------------------------------ serving arm
 def serving_arm(args):
     """Serving stream: requests arrive by a Poisson process and are admitted by
@@ -495,10 +639,71 @@ def serving_arm(args):
     }))
 
 
+# ------------------------------------------------------------------ pulse march served with 3D requests
+def served_pulse_arm(args):
+    """The layered 3D 32^3 pulse march (40 slabs, 3.37 M unknowns per slab)
+    served together with 16 concurrent 3D 16^3 marches (10 slabs each), all
+    submitted at time 0 to the serving loop (one worker per request).  The
+    big march is also run alone for its uncontended slab latency."""
+    import torch
+    import paper_2303_06742_gb300 as st
+    import inputs
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _cases import gpu_problem
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = inputs.served_with_pulse()
+    probs = [gpu_problem(c) for c in reqs]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    tw0 = time.time()
+    S = st.Server(hbm_budget=budget, n_workers=len(reqs))
+    ids = [S.submit(p, c["slabs"], tol=c["tol"]) for p, c in zip(probs, reqs)]
+    res = [S.result(i) for i in ids]
+    S.close()
+    tw1 = time.time()
+    clk = clocks.stop(tw0, tw1)
+    A = st.Server(hbm_budget=budget, n_workers=1)
+    alone = A.result(A.submit(probs[0], reqs[0]["slabs"], tol=reqs[0]["tol"]))
+    A.close()
+    big, small = res[0], res[1:]
+    march_s = [r[0]["t_done"] - r[0]["t_ready"] for r in res]
+    t_first = min(r[0]["t_ready"] for r in res)
+    t_last = max(r[0]["t_done"] for r in res)
+    slabs = sum(r[0]["n_slabs"] for r in res)
+    print(json.dumps({
+        "metric": "slab solves/s", "value": slabs / (t_last - t_first), "unit": "slab solves/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "3D [0,2]^2x[0,1] 32^3 layered pulse (Q2^3/Q1, dG(1), 4 levels, tau 5e-3, "
+                               "40 slabs, 3,367,374 unknowns per slab) served with 16 concurrent 3D 16^3 "
+                               "thermoelastic marches (10 slabs each); FP32 V-cycle in FP64 FGMRES, tol 1e-8; "
+                               "value = all slabs over the time from the first finished setup to the last "
+                               "finished march"},
+        "status": sorted(set(r[0]["status"] for r in res)),
+        "pulse": {"slab_latency_ms": {"p50": pct(list(big[2]), 50), "p99": pct(list(big[2]), 99)},
+                  "march_s": march_s[0], "setup_s": big[0]["t_ready"] - big[0]["t_admit"],
+                  "iters_total": big[0]["iters_total"], "device_bytes": big[0]["device_bytes"],
+                  "alone_slab_latency_ms": {"p50": pct(list(alone[2]), 50), "p99": pct(list(alone[2]), 99)},
+                  "alone_march_s": alone[0]["t_done"] - alone[0]["t_ready"]},
+        "small": {"march_s": {"p50": pct(march_s[1:], 50), "p99": pct(march_s[1:], 99)},
+                  "slab_latency_ms": {"p50": pct([x for r in small for x in r[2]], 50),
+                                      "p99": pct([x for r in small for x in r[2]], 99)},
+                  "setup_s": {"p50": pct([r[0]["t_ready"] - r[0]["t_admit"] for r in small], 50)}},
+        "clocks": clk,
+    }))
+
+
 def main():
     args = parse()
     if args.workload == "serving" and not args.cpu_leg:
         serving_arm(args)
+        return
+    if args.workload == "pulse_served" and not args.cpu_leg:
+        served_pulse_arm(args)
+        return
+    if args.rhs > 1 and not args.cpu_leg and args.impl != "reference":
+        batch_arm(args)
         return
     if args.cpu_leg:
         oracle_leg(args.workload, args.cpu_leg, "reference" if args.impl == "reference" else "solve",

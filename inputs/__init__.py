@@ -45,7 +45,23 @@ def case(name, seed=SEED):
         return dict(dim=3, n=n, levels=2, r=2, k=1, tau=5e-3, slabs=2, lo=[0, 0, 0], hi=[2, 2, 1],
                     rho=1.0, alpha=1.0, c0=1.0, lam=1.0, mu_cell=mu, kappa_cell=kap, problem="pulse",
                     bc_u=[1, 1, 1, 1, 0, 1], bc_p=[1, 1, 1, 1, 1, 0], tol=1e-8)
+    if name == "c5_3d_pulse_32":  # layered box [0,2]^2 x [0,1], 32^3 cells, 4 levels
+        n = (32, 32, 32)
+        kap, mu = layered(n, 1.0)
+        return dict(dim=3, n=n, levels=4, r=2, k=1, tau=5e-3, slabs=40, lo=[0, 0, 0], hi=[2, 2, 1],
+                    rho=1.0, alpha=1.0, c0=1.0, lam=1.0, mu_cell=mu, kappa_cell=kap, problem="pulse",
+                    bc_u=[1, 1, 1, 1, 0, 1], bc_p=[1, 1, 1, 1, 1, 0], tol=1e-8)
     raise KeyError(name)
+
+
+def served_with_pulse(n_small=16):
+    """The layered 32^3 pulse march (40 slabs) submitted together with
+    n_small 3D 16^3 thermoelastic marches (10 slabs each, data phases
+    t0 = 0.05 i), all at time 0."""
+    out = [dict(case("c5_3d_pulse_32"), arrival=0.0)]
+    for i in range(n_small):
+        out.append(dict(case("c3_3d_q2_k1_16"), t0=0.05 * i, arrival=0.0))
+    return out
 
 
 def layered(n, top_z_split):

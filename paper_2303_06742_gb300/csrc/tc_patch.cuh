@@ -243,17 +243,11 @@ __global__ void __launch_bounds__(tcp::THREADS, 1)
     const int cw = tid >> 5;          // consumer warp 0..7
     const int quarter = warp & 3;     // tensor-memory lanes 32 quarter .. +31
     const int group = cw >> 2;        // tiles mt = group, group + 2, ...
-    long long nslot = 0;
-    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
-      // uniform decision to go on
-      cons_sync();
-      if (tid == 0) S.flag[1] = S.flag[0];
-      cons_sync();
-      if (S.flag[1]) break;
-      const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+    // gather the nb residual columns of patch p and transform them to the
+    // slots: xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot
+    auto gather = [&](int p) {
+      const int Cs = pcs[p];
       const long long doff = pdoff[p];
-      // gather the nb residual columns and transform to the slots:
-      // xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot
       for (int idx = tid; idx < 8 * Cs; idx += NCONS) {
         const int c = idx / Cs, m = idx - c * Cs;
         float r[Q];
@@ -275,29 +269,92 @@ __global__ void __launch_bounds__(tcp::THREADS, 1)
           }
         }
       }
+    };
+    // B operand of slot a from xt (see the layout above)
+    auto write_b = [&](int a, int Cs, int c8) {
+      const int K = kext(a, nr, c8);
+      const bool cplx = a >= nr;
+      const int row = cplx ? nr + 2 * (a - nr) : a;
+      for (int idx = tid; idx < 16 * K; idx += NCONS) {
+        const int k = idx >> 4, n = idx & 15;
+        float v = 0.f;
+        if (!cplx) {
+          if (n < 8 && k < Cs) v = S.xt[((size_t)row * 8 + n) * maxCs + k];
+        } else {
+          const int kk = k < c8 ? k : k - c8;
+          if (kk < Cs) {
+            const float xr = S.xt[((size_t)row * 8 + (n & 7)) * maxCs + kk];
+            const float xi = S.xt[((size_t)(row + 1) * 8 + (n & 7)) * maxCs + kk];
+            v = k < c8 ? (n < 8 ? xr : xi) : (n < 8 ? -xi : xr);
+          }
+        }
+        const int kb = k >> 3, kc = (k >> 2) & 1, e = k & 3, ng = n >> 3, rr = n & 7;
+        S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4 + e] = v;
+      }
+    };
+    long long nslot = 0;
+    if (ns == 1) {
+      // One slot per patch (dG(0) or dG(1)): the next patch is gathered while
+      // the MMAs of this one run, and the epilogue mixes D straight back to
+      // the time nodes (y = V z, complex: 2 Re(V z)).
+      const bool cplx = nc == 1;
+      if (blockIdx.x < npatch) gather(blockIdx.x);
+      for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++nslot) {
+        cons_sync(); // xt of patch p complete
+        if (tid == 0) S.flag[1] = S.flag[0];
+        cons_sync();
+        if (S.flag[1]) break;
+        const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+        const long long doff = pdoff[p];
+        write_b(0, Cs, c8);
+        fence_async_smem();
+        cons_sync();
+        if (tid == 0) mbar_arrive(S.bfull);
+        if (p + (int)gridDim.x < npatch) gather(p + gridDim.x);
+        if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nslot & 1), WAIT) ? 0 : 1;
+        cons_sync();
+        if (S.flag[1]) {
+          if (tid == 0) {
+            atomicExch(err, 5);
+            S.flag[0] = 1;
+          }
+          break;
+        }
+        fence_after();
+        for (int mt = group; mt < ntile; mt += 2) {
+          float v[16];
+          __syncwarp();
+          ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
+          const int m = mt * 128 + quarter * 32 + lane;
+          if (m < Cs)
+            for (int c = 0; c < nb; ++c)
+#pragma unroll
+              for (int b = 0; b < Q; ++b) {
+                const float vr = dc.V[b * 2], vi = dc.V[b * 2 + 1];
+                y[(long)c * ystride + doff + b * Cs + m] = cplx ? 2.f * (vr * v[c] - vi * v[8 + c]) : vr * v[c];
+              }
+        }
+        fence_before();
+        cons_sync();
+        if (tid == 0) mbar_arrive(S.aempty);
+      }
+    } else
+    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+      // uniform decision to go on
+      cons_sync();
+      if (tid == 0) S.flag[1] = S.flag[0];
+      cons_sync();
+      if (S.flag[1]) break;
+      const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+      const long long doff = pdoff[p];
+      gather(p);
       cons_sync();
       bool stop = false;
       for (int a = 0; a < ns; ++a, ++nslot) {
         // B of slot a (the previous slot's MMAs have completed: afull waited)
-        const int K = kext(a, nr, c8);
         const bool cplx = a >= nr;
         const int row = cplx ? nr + 2 * (a - nr) : a;
-        for (int idx = tid; idx < 16 * K; idx += NCONS) {
-          const int k = idx >> 4, n = idx & 15;
-          float v = 0.f;
-          if (!cplx) {
-            if (n < 8 && k < Cs) v = S.xt[((size_t)row * 8 + n) * maxCs + k];
-          } else {
-            const int kk = k < c8 ? k : k - c8;
-            if (kk < Cs) {
-              const float xr = S.xt[((size_t)row * 8 + (n & 7)) * maxCs + kk];
-              const float xi = S.xt[((size_t)(row + 1) * 8 + (n & 7)) * maxCs + kk];
-              v = k < c8 ? (n < 8 ? xr : xi) : (n < 8 ? -xi : xr);
-            }
-          }
-          const int kb = k >> 3, kc = (k >> 2) & 1, e = k & 3, ng = n >> 3, rr = n & 7;
-          S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4 + e] = v;
-        }
+        write_b(a, Cs, c8);
         fence_async_smem();
         cons_sync();
         if (tid == 0) mbar_arrive(S.bfull);
