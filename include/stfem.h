@@ -287,6 +287,15 @@ int slab_solve_batch(stfem_h h, int n_rhs, const double *rhs, double *x, double 
  * handle's t0 is ignored), from the states in `state` (updated in place). */
 int march_batch(stfem_h h, int n_rhs, const double *t0_host, int first_slab, int n_slabs, double *state,
                 double tol, int restart, int max_it, int *iters_host);
+/* y = A x with the finest slab matrix as the FGMRES iterations apply it to
+ * their preconditioned vectors: STFEM_FP64 in FP64; STFEM_MIXED with x
+ * rounded to FP32 (the V-cycle output is FP32) and the product formed in
+ * double-float arithmetic on the FP32 pipes (matrix values split into float
+ * pairs, sums as unevaluated float pairs; relative error about n 2^-48 of
+ * sum_j |a_ij x_j| per row).  x, y: device, n_slab FP64.  No counterpart in
+ * the paper beyond the product itself (Eq. 4.7). */
+int stfem_apply_krylov(stfem_h h, const double *x, double *y);
+
 /* d = M^{-1} b for n_rhs columns (one batched V-cycle, as stfem_vcycle). */
 int stfem_vcycle_batch(stfem_h h, int n_rhs, const double *b, double *d);
 /* Nodal interpolant of the problem's exact state at time t (as

@@ -105,6 +105,7 @@ def _load():
         "slab_solve_batch": [P, I, P, P, D, I, I, pI, pD],
         "march_batch": [P, I, pD, I, I, P, D, I, I, pI],
         "stfem_vcycle_batch": [P, I, P, P],
+        "stfem_apply_krylov": [P, P, P],
         "stfem_initial_state_at": [P, D, P],
         "stfem_host_level_matrix": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, pLL, pLL, pLL, pI, pD],
@@ -374,6 +375,10 @@ class Solver:
         rc = self._check(lib.march_batch(self.h, len(t0), _dptr(t0), first_slab, n_slabs, _ptr(state), tol,
                                          restart, max_it, it.ctypes.data_as(C.POINTER(C.c_int))))
         return rc, it[:n_slabs]
+
+    def apply_krylov(self, x, y):
+        """y = A x as the FGMRES iterations form it (MIXED: double-float on FP32-rounded x)."""
+        self._check(lib.stfem_apply_krylov(self.h, _ptr(x), _ptr(y)))
 
     def vcycle_batch(self, n_rhs, b, d):
         self._check(lib.stfem_vcycle_batch(self.h, n_rhs, _ptr(b), _ptr(d)))

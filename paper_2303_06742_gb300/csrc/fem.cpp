@@ -911,14 +911,16 @@ bool invert(double *a, int n) {
   return true;
 }
 
-// Gauss-Jordan inverse with partial pivoting for complex row-major matrices.
-static bool invert_complex(std::complex<double> *a, int n) {
+// Gauss-Jordan inverse with partial pivoting of a complex row-major matrix
+// held as separate real and imaginary parts (contiguous rows vectorise);
+// the elimination updates two rows per pass over the pivot row.
+static bool invert_complex(double *re, double *im, int n) {
   std::vector<int> piv(n);
   for (int k = 0; k < n; ++k) {
     int p = k;
-    double best = std::abs(a[(size_t)k * n + k]);
+    double best = std::hypot(re[(size_t)k * n + k], im[(size_t)k * n + k]);
     for (int i = k + 1; i < n; ++i) {
-      double v = std::abs(a[(size_t)i * n + k]);
+      const double v = std::hypot(re[(size_t)i * n + k], im[(size_t)i * n + k]);
       if (v > best) {
         best = v;
         p = i;
@@ -927,23 +929,72 @@ static bool invert_complex(std::complex<double> *a, int n) {
     if (!(best > 0.0) || !std::isfinite(best)) return false;
     piv[k] = p;
     if (p != k)
-      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
-    std::complex<double> *rk = a + (size_t)k * n;
-    const std::complex<double> inv = 1.0 / rk[k];
-    rk[k] = 1.0;
-    for (int j = 0; j < n; ++j) rk[j] *= inv;
-    for (int i = 0; i < n; ++i) {
-      if (i == k) continue;
-      std::complex<double> *ri = a + (size_t)i * n;
-      const std::complex<double> f = ri[k];
-      if (f == 0.0) continue;
-      ri[k] = 0.0;
-      for (int j = 0; j < n; ++j) ri[j] -= f * rk[j];
+      for (int j = 0; j < n; ++j) {
+        std::swap(re[(size_t)k * n + j], re[(size_t)p * n + j]);
+        std::swap(im[(size_t)k * n + j], im[(size_t)p * n + j]);
+      }
+    double *kr = re + (size_t)k * n, *ki = im + (size_t)k * n;
+    const double dr = kr[k], di = ki[k], den = dr * dr + di * di, ir = dr / den, ii = -di / den;
+    kr[k] = 1.0;
+    ki[k] = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double x = kr[j], y = ki[j];
+      kr[j] = x * ir - y * ii;
+      ki[j] = x * ii + y * ir;
     }
+    int rows[2], nrow = 0;
+    auto eliminate = [&](int cnt) {
+      if (cnt == 2) {
+        double *ar = re + (size_t)rows[0] * n, *ai = im + (size_t)rows[0] * n;
+        double *br = re + (size_t)rows[1] * n, *bi = im + (size_t)rows[1] * n;
+        const double fr = ar[k], fi = ai[k], gr = br[k], gi = bi[k];
+        ar[k] = ai[k] = br[k] = bi[k] = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double x = kr[j], y = ki[j];
+          ar[j] -= fr * x - fi * y;
+          ai[j] -= fr * y + fi * x;
+          br[j] -= gr * x - gi * y;
+          bi[j] -= gr * y + gi * x;
+        }
+      } else if (cnt == 1) {
+        double *ar = re + (size_t)rows[0] * n, *ai = im + (size_t)rows[0] * n;
+        const double fr = ar[k], fi = ai[k];
+        ar[k] = ai[k] = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double x = kr[j], y = ki[j];
+          ar[j] -= fr * x - fi * y;
+          ai[j] -= fr * y + fi * x;
+        }
+      }
+    };
+    for (int i = 0; i < n; ++i) {
+      if (i == k || (re[(size_t)i * n + k] == 0.0 && im[(size_t)i * n + k] == 0.0)) continue;
+      rows[nrow++] = i;
+      if (nrow == 2) {
+        eliminate(2);
+        nrow = 0;
+      }
+    }
+    eliminate(nrow);
   }
   for (int k = n - 1; k >= 0; --k)
     if (piv[k] != k)
-      for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + k], a[(size_t)i * n + piv[k]]);
+      for (int i = 0; i < n; ++i) {
+        std::swap(re[(size_t)i * n + k], re[(size_t)i * n + piv[k]]);
+        std::swap(im[(size_t)i * n + k], im[(size_t)i * n + piv[k]]);
+      }
+  return true;
+}
+
+// The same for a std::complex array (the small q x q matrices of time_diag).
+static bool invert_complex(std::complex<double> *a, int n) {
+  std::vector<double> re((size_t)n * n), im((size_t)n * n);
+  for (size_t i = 0; i < (size_t)n * n; ++i) {
+    re[i] = a[i].real();
+    im[i] = a[i].imag();
+  }
+  if (!invert_complex(re.data(), im.data(), n)) return false;
+  for (size_t i = 0; i < (size_t)n * n; ++i) a[i] = std::complex<double>(re[i], im[i]);
   return true;
 }
 
@@ -1190,7 +1241,7 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
   std::atomic<long> bad(-1);
   auto work = [&]() {
     std::vector<int> loc(L.ns, -1);
-    std::vector<double> S1, S2, A;
+    std::vector<double> S1, S2, A, Zr, Zi;
     for (;;) {
       long p = next.fetch_add(1);
       if (p >= nv) break;
@@ -1226,17 +1277,21 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
           dst += (size_t)Cs * ldR;
         }
         for (int a = td->nr; a < td->nr + td->nc && ok; ++a) {
-          const std::complex<double> lam(td->lam[2 * a], td->lam[2 * a + 1]);
-          std::vector<std::complex<double>> Z((size_t)Cs * Cs);
-          for (size_t i = 0; i < (size_t)Cs * Cs; ++i) Z[i] = lam * S1[i] + S2[i];
-          if (!invert_complex(Z.data(), Cs)) {
+          const double lr = td->lam[2 * a], li = td->lam[2 * a + 1];
+          Zr.resize((size_t)Cs * Cs);
+          Zi.resize((size_t)Cs * Cs);
+          for (size_t i = 0; i < (size_t)Cs * Cs; ++i) {
+            Zr[i] = lr * S1[i] + S2[i];
+            Zi[i] = li * S1[i];
+          }
+          if (!invert_complex(Zr.data(), Zi.data(), Cs)) {
             ok = false;
             break;
           }
           for (int i = 0; i < Cs; ++i)
             for (int j = 0; j < Cs; ++j) {
-              dst[(size_t)j * ldC + 2 * i] = Z[(size_t)i * Cs + j].real();
-              dst[(size_t)j * ldC + 2 * i + 1] = Z[(size_t)i * Cs + j].imag();
+              dst[(size_t)j * ldC + 2 * i] = Zr[(size_t)i * Cs + j];
+              dst[(size_t)j * ldC + 2 * i + 1] = Zi[(size_t)i * Cs + j];
             }
           dst += (size_t)Cs * ldC;
         }

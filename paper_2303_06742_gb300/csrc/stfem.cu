@@ -30,6 +30,11 @@ using namespace stfem_dev;
 #ifndef STFEM_DIAG_UNROLL_COMPLEX
 #define STFEM_DIAG_UNROLL_COMPLEX 0
 #endif
+#ifndef STFEM_STREAM_MIN_PATCHES
+// time-diagonal levels with fewer patches use the one-CTA-per-patch kernel
+// with column groups (more loads in flight per patch) instead of streaming
+#define STFEM_STREAM_MIN_PATCHES 0
+#endif
 #ifndef STFEM_PATCH_THREADS_PER_SM
 #define STFEM_PATCH_THREADS_PER_SM 4096
 #endif
@@ -254,6 +259,167 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
       for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
       const long oi = (long)b * ns + 2 * R + sI;
       y[oi] = mode ? rhs[oi] - val : val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- double-float SpMV
+// y = A x for an FP64 operator whose every value a is held as the float pair
+// (hi, lo), hi = fl32(a), lo = fl32(a - hi) (a = hi + lo to about 2^-48),
+// applied to a vector that is exactly representable in FP32 (the output of
+// the FP32 V-cycle).  Products and sums run on the FP32 pipes in double-float
+// arithmetic: hi * x is split exactly with an FMA, lo * x is added to the
+// error term, and the running sum is kept as an unevaluated pair (hi, lo)
+// updated by Knuth's TwoSum.  The relative error of a row is about
+// n 2^-48 of the sum of |a_j x_j| (FP64: n 2^-53), while the FP32 pipes run
+// GB300's rate for FP32, far above its FP64 rate.  The Q time-node mixing
+// of Eq. 4.7 at the end is FP64.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_madd(DF &acc, float2 a, float x) {
+  const float p = a.x * x;
+  float e = fmaf(a.x, x, -p); // exact: a.x * x = p + e
+  e = fmaf(a.y, x, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float err = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += err + e;
+}
+
+__device__ __forceinline__ void df_add(DF &acc, float bh, float bl) {
+  const float s = acc.hi + bh;
+  const float bb = s - acc.hi;
+  const float err = (acc.hi - (s - bb)) + (bh - bb);
+  acc.hi = s;
+  acc.lo += err + bl;
+}
+
+__device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+template <int Q, int D, int G>
+__global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns, long R, TimeCoef<double> tc,
+                                                 const float *__restrict__ x, double *__restrict__ y, int nb,
+                                                 long cstride) {
+  constexpr int NA = 4 * Q * D;
+  const int col = (int)(blockIdx.x % (unsigned)nb);
+  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  x += (long)col * cstride;
+  y += (long)col * cstride;
+  const long node = gid / G;
+  const int lane = threadIdx.x % G;
+  DF acc[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) acc[i] = DF{0.f, 0.f};
+  const bool is_u = node < A.nu;
+  const bool is_p = !is_u && node < A.nu + A.np;
+  if (is_u) {
+    // acc layout as in k_spmv_nb: [0] M U, [1] M V, [2] K U, [3] Ct P
+    int a[3];
+    lattice_coords(node, A.udims, D, a);
+    const Box3 bu = node_box(a, A.r, A.r, A.n, D);
+    const int base = A.uu_ptr[node], e1 = A.uu_ptr[node + 1];
+    for (int e = base + lane; e < e1; e += G) {
+      const long J = box_node(bu, e - base, A.udims);
+      const float2 m = A.uu_m[e];
+      float2 k[D * D];
+#pragma unroll
+      for (int i = 0; i < D * D; ++i) k[i] = A.uu_k[(long)e * D * D + i];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        float v[D], u[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          v[c] = x[(long)t * ns + J * D + c];
+          u[c] = x[(long)t * ns + R + J * D + c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          df_madd(acc[(0 * Q + t) * D + c], m, u[c]);
+          df_madd(acc[(1 * Q + t) * D + c], m, v[c]);
+#pragma unroll
+          for (int cp = 0; cp < D; ++cp) df_madd(acc[(2 * Q + t) * D + c], k[c * D + cp], u[cp]);
+        }
+      }
+    }
+    const Box3 bp = node_box(a, A.r, A.r - 1, A.n, D);
+    const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long sI = box_node(bp, e - f0, A.pdims);
+      float2 ct[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const float pv = x[(long)t * ns + 2 * R + sI];
+#pragma unroll
+        for (int c = 0; c < D; ++c) df_madd(acc[(3 * Q + t) * D + c], ct[c], pv);
+      }
+    }
+  } else if (is_p) {
+    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V
+    const long sI = node - A.nu;
+    int a[3];
+    lattice_coords(sI, A.pdims, D, a);
+    const Box3 bp = node_box(a, A.r - 1, A.r - 1, A.n, D);
+    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
+    for (int e = e0p + lane; e < e1; e += G) {
+      const long s2 = box_node(bp, e - e0p, A.pdims);
+      const float2 m = A.pp_m[e], bb = A.pp_b[e];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const float pv = x[(long)t * ns + 2 * R + s2];
+        df_madd(acc[t], m, pv);
+        df_madd(acc[Q + t], bb, pv);
+      }
+    }
+    const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
+    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long J = box_node(bu, e - f0, A.udims);
+      float2 cn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
+#pragma unroll
+      for (int t = 0; t < Q; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + J * D + c]);
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float bh = __shfl_xor_sync(0xffffffffu, acc[i].hi, o);
+      const float bl = __shfl_xor_sync(0xffffffffu, acc[i].lo, o);
+      df_add(acc[i], bh, bl);
+    }
+  }
+  if (is_u) {
+#pragma unroll
+    for (int o = 0; o < 2 * Q * D; ++o) {
+      if (o % G != lane) continue;
+      const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
+      double val = 0.0;
+#pragma unroll
+      for (int t = 0; t < Q; ++t) val += tc.Dt[b * Q + t] * df_val(acc[(eq * Q + t) * D + c]);
+      if (eq == 0)
+        val -= tc.W[b] * df_val(acc[(1 * Q + b) * D + c]);
+      else
+        val += tc.W[b] * (df_val(acc[(2 * Q + b) * D + c]) + df_val(acc[(3 * Q + b) * D + c]));
+      y[(long)b * ns + eq * R + node * D + c] = val;
+    }
+  } else if (is_p) {
+    const long sI = node - A.nu;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      if (b % G != lane) continue;
+      double val = tc.W[b] * (df_val(acc[Q + b]) + df_val(acc[2 * Q + b]));
+#pragma unroll
+      for (int t = 0; t < Q; ++t) val += tc.Dt[b * Q + t] * df_val(acc[t]);
+      y[(long)b * ns + 2 * R + sI] = val;
     }
   }
 }
@@ -1266,6 +1432,9 @@ struct DLevel {
   long long nnz = 0;
   // node-block operator (see k_spmv_nb)
   NodeBlockDev<T> nb{};
+  // the same values as float pairs (see k_spmv_df; finest FP64 level, MIXED)
+  NodeBlockDev<float2> nbdf{};
+  bool has_df = false;
   double nb_bytes = 0.0, nb_flops = 0.0;
   // patches
   long npatch = 0;
@@ -1498,6 +1667,35 @@ void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *
   }
 }
 
+template <int Q, int D>
+void launch_spmv_df_qd(cudaStream_t s, const DLevel<double> &L, const TimeCoef<double> &tc, const float *x,
+                       double *y, int nb) {
+  constexpr int G = D == 3 ? 8 : 4;
+  const long threads = (L.nb.nu + L.nb.np) * G;
+  k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, tc, x, y, nb, L.N);
+}
+
+// y = A x on the finest FP64 level in double-float arithmetic, x FP32 (nb
+// columns, stride L.N): the FGMRES operator of the MIXED mode
+void launch_spmv_df(stfem_h h, const DLevel<double> &L, const TimeCoef<double> &tc, const float *x, double *y,
+                    int nb = 1) {
+  Launch G_(h, STFEM_KCLASS_SPMV, L.nb_bytes + (double)tc.q * L.ns * 12.0 * nb, L.nb_flops * tc.q * nb);
+  cudaStream_t s = h->stream;
+#define STFEM_DF_Q(Q)                                                                                  \
+  if (h->dim == 2)                                                                                     \
+    launch_spmv_df_qd<Q, 2>(s, L, tc, x, y, nb);                                                       \
+  else                                                                                                 \
+    launch_spmv_df_qd<Q, 3>(s, L, tc, x, y, nb);
+  switch (tc.q) {
+  case 1: STFEM_DF_Q(1) break;
+  case 2: STFEM_DF_Q(2) break;
+  case 3: STFEM_DF_Q(3) break;
+  case 4: STFEM_DF_Q(4) break;
+  default: STFEM_DF_Q(5) break;
+  }
+#undef STFEM_DF_Q
+}
+
 // Node-block arrays of a level in box order, decoded from the spatial system
 // CSR (whose blocks have the structure of Eq. 4.7).  Every entry must lie in
 // the node's neighbour box (checked); box positions without an entry are
@@ -1714,6 +1912,47 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   CKR(dalloc(h, &D.b, D.N));
   CKR(dalloc(h, &D.d, D.N));
   CKR(dalloc(h, &D.r, D.N));
+  return 0;
+}
+
+// Float-pair copy (hi = fl32(a), lo = fl32(a - hi)) of the node-block values
+// of an FP64 level, for the double-float SpMV.
+int upload_level_df(stfem_h h, DLevel<double> &D, const stfem::Level &L) {
+  NodeBlockHost H;
+  std::string err;
+  if (node_block(L, h->dim, &H, &err) < 0) {
+    h->err = err;
+    return STFEM_ERR_STATE;
+  }
+  auto split = [](const std::vector<double> &v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+    }
+    return o;
+  };
+  NodeBlockDev<float2> &nb = D.nbdf;
+  nb.nu = D.nb.nu;
+  nb.np = D.nb.np;
+  nb.r = D.nb.r;
+  for (int i = 0; i < 3; ++i) {
+    nb.n[i] = D.nb.n[i];
+    nb.udims[i] = D.nb.udims[i];
+    nb.pdims[i] = D.nb.pdims[i];
+  }
+  nb.uu_ptr = D.nb.uu_ptr;
+  nb.up_ptr = D.nb.up_ptr;
+  nb.pu_ptr = D.nb.pu_ptr;
+  nb.pp_ptr = D.nb.pp_ptr;
+  float2 *fp;
+  CKR(upload(h, &fp, split(H.uu_m))); nb.uu_m = fp;
+  CKR(upload(h, &fp, split(H.uu_k))); nb.uu_k = fp;
+  CKR(upload(h, &fp, split(H.up_c))); nb.up_c = fp;
+  CKR(upload(h, &fp, split(H.pu_c))); nb.pu_c = fp;
+  CKR(upload(h, &fp, split(H.pp_m))); nb.pp_m = fp;
+  CKR(upload(h, &fp, split(H.pp_b))); nb.pp_b = fp;
+  D.has_df = true;
   return 0;
 }
 
@@ -1957,6 +2196,17 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   size_t smem = (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
   cudaStream_t s = h->stream;
   const unsigned grid = (unsigned)L.npatch;
+  if (L.form == 1 && L.npatch < STFEM_STREAM_MIN_PATCHES) {
+    smem += (size_t)(h->q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
+    switch (h->q) {
+    case 1: launch_patch_diag_q<T, 1>(s, L, RT, J, smem, res, y); break;
+    case 2: launch_patch_diag_q<T, 2>(s, L, RT, J, smem, res, y); break;
+    case 3: launch_patch_diag_q<T, 3>(s, L, RT, J, smem, res, y); break;
+    case 4: launch_patch_diag_q<T, 4>(s, L, RT, J, smem, res, y); break;
+    default: launch_patch_diag_q<T, 5>(s, L, RT, J, smem, res, y); break;
+    }
+    return;
+  }
   if (L.form == 1) {
     switch (h->q) {
     case 1: launch_patch_stream_q<T, 1>(h, L, res, y); break;
@@ -2236,16 +2486,19 @@ int enqueue_iteration(stfem_h h, int j, int m1) {
   cudaStream_t s = h->stream;
   const int nb = grid_for(N, 256);
   double *vj = h->V + (long)j * N;
-  double *zj = nullptr;
+  double *w = h->w;
   if (h->precision == STFEM_FP64) {
-    zj = h->Zd + (long)j * N;
+    double *zj = h->Zd + (long)j * N;
     CKR(precondition(h, vj, zj, nullptr));
+    launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
+  } else if (F.has_df) {
+    // z_j is the FP32 V-cycle output: exact in FP32, so A z_j in double-float
+    CKR(precondition(h, vj, nullptr, h->Zf + (long)j * N));
+    launch_spmv_df(h, F, tc, h->Zf + (long)j * N, w);
   } else {
     CKR(precondition(h, vj, h->zt, h->Zf + (long)j * N));
-    zj = h->zt;
+    launch_spmv<double>(h, F, tc, h->zt, nullptr, w, 0);
   }
-  double *w = h->w;
-  launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
   // classical Gram-Schmidt, applied twice: h1 = V^T w; w -= V h1 and
   // h2 = V^T w in one pass; w -= V h2 and ||w||^2 in one pass
   multidot(h, j + 1, h->V, N, w, N, h->h1);
@@ -2514,13 +2767,17 @@ int enqueue_iteration_batch(stfem_h h, int j, int m1, int nb) {
       Launch G_(h, STFEM_KCLASS_OTHER, N * 8.0 * nb, 0.0);
       k_copy_cols<float, float><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.Zf + (long)j * N, (long)m * N);
     }
-    {
-      Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * nb, 0.0);
-      k_copy_cols<float, double><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.zt, N);
+    if (F.has_df) {
+      launch_spmv_df(h, F, tc, G.d, B.w, nb);
+    } else {
+      {
+        Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0 * nb, 0.0);
+        k_copy_cols<float, double><<<nbk * nb, 256, 0, s>>>(N, nb, G.d, N, B.zt, N);
+      }
+      zsp = B.zt;
     }
-    zsp = B.zt;
   }
-  launch_spmv<double>(h, F, tc, zsp, nullptr, B.w, 0, nb);
+  if (zsp) launch_spmv<double>(h, F, tc, zsp, nullptr, B.w, 0, nb);
   for (int c = 0; c < nb; ++c) {
     const BatchCol k = batch_col(h, c);
     double *w = B.w + (long)c * N;
@@ -3024,6 +3281,7 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       CKR(upload_level_matrix(h, h->L32[l], h->hl[l], h->q));
       if (l >= 1) CKR(upload_transfer(h, h->L32[l], h->Pu[l], h->Pp[l]));
     }
+    CKR(upload_level_df(h, h->L64.back(), h->hl.back()));
   }
   int form = p->patch_form;
   if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
@@ -3205,6 +3463,26 @@ int slab_solve_batch(stfem_h h, int n_rhs, const double *rhs, double *x, double 
   CK(cudaStreamSynchronize(h->stream));
   CKR(check_dev_err(h));
   return rc;
+}
+
+int stfem_apply_krylov(stfem_h h, const double *x, double *y) {
+  if (!h || !x || !y) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  DLevel<double> &F = h->L64.back();
+  const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
+  if (h->precision == STFEM_MIXED && F.has_df) {
+    float *xf = h->L32.back().b; // V-cycle input buffer, free between calls
+    {
+      Launch G_(h, STFEM_KCLASS_OTHER, F.N * 12.0, 0.0);
+      k_convert<double, float><<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.N, x, xf);
+    }
+    launch_spmv_df(h, F, tc, xf, y);
+  } else {
+    launch_spmv<double>(h, F, tc, x, nullptr, y, 0);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return STFEM_OK;
 }
 
 int stfem_vcycle_batch(stfem_h h, int n_rhs, const double *b, double *d) {

@@ -259,3 +259,26 @@ def test_march_on_stream_uses_graphs(name, precision):
     assert err < (1e-9 if precision == 0 else 1e-7)
     assert l1 - l0 > 10 * sum(it)  # replayed kernels are counted
     S.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_double_float_krylov_operator(name):
+    """MIXED: the FGMRES product A z (z from the FP32 V-cycle) is formed in
+    double-float arithmetic.  Against the oracle's FP64 product with the same
+    FP32-rounded vector: per row |error| <= 1e-12 sum_j |a_ij x_j| (the
+    double-float bound n 2^-48 with n <= 250 terms is 9e-13)."""
+    c, S, O = pair(name, precision=1)
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal(O.A.shape[0]).astype(np.float32).astype(np.float64)
+    y = dev(np.zeros_like(x))
+    S.apply_krylov(dev(x), y)
+    ref = O.A @ x
+    scale = abs(O.A) @ abs(x)
+    err = float(np.max(np.abs(host(y) - ref) / np.maximum(scale, 1e-300)))
+    print(name, "double-float product", err)
+    assert err < 1e-12
+    # the FP64 mode applies the FP64 product
+    c64, S64, _ = pair(name)
+    y64 = dev(np.zeros_like(x))
+    S64.apply_krylov(dev(x), y64)
+    assert float(np.max(np.abs(host(y64) - ref) / np.maximum(scale, 1e-300))) < 1e-14
