@@ -148,8 +148,12 @@ typedef struct {
  * patch_kind STFEM_PATCHES_*, update STFEM_UPDATE_*, n_rhs the most
  * right-hand sides the batched calls (slab_solve_batch, march_batch,
  * stfem_vcycle_batch) will be given (0 or 1: none; at most STFEM_MAX_RHS);
- * the level work vectors are allocated with that many columns.  A
- * zero-initialised tail (patch_form .. n_rhs) selects the defaults. */
+ * the level work vectors are allocated with that many columns.
+ * factor_host: 1 inverts the time-diagonal patch blocks on the host (threaded
+ * FP64 Gauss-Jordan) instead of on the device (default: FP64 Gauss-Jordan
+ * with partial pivoting on the GPU, C_s <= 512).  The dense form is always
+ * inverted on the host.  A zero-initialised tail (patch_form .. factor_host)
+ * selects the defaults. */
 typedef struct {
   double omega;
   int n_sweeps;
@@ -158,6 +162,7 @@ typedef struct {
   int patch_kind;
   int update;
   int n_rhs;
+  int factor_host;
 } stfem_gmg_params;
 
 /* Builds the mesh hierarchy, spatial matrices of every level (Eqs. 3.2-3.3),

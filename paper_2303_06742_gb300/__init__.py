@@ -61,7 +61,7 @@ class BCs(C.Structure):
 
 class GmgParams(C.Structure):
     _fields_ = [("omega", C.c_double), ("n_sweeps", C.c_int), ("precision", C.c_int), ("patch_form", C.c_int),
-                ("patch_kind", C.c_int), ("update", C.c_int), ("n_rhs", C.c_int)]
+                ("patch_kind", C.c_int), ("update", C.c_int), ("n_rhs", C.c_int), ("factor_host", C.c_int)]
 
 
 class Request(C.Structure):
@@ -246,7 +246,7 @@ class Solver:
     """Handle of one problem instance on the current CUDA device."""
 
     def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None, patch_form=PATCH_AUTO,
-                 patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE, stop=STOP_RELATIVE, n_rhs=0):
+                 patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE, stop=STOP_RELATIVE, n_rhs=0, factor_host=0):
         self.prob = prob
         h = C.c_void_p()
         rc = lib.stfem_setup(*prob.args(), C.byref(h))
@@ -256,7 +256,7 @@ class Solver:
         if stream is not None:
             self.set_stream(stream)
         self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision, patch_form,
-                                                                  patch_kind, update, n_rhs))))
+                                                                  patch_kind, update, n_rhs, factor_host))))
         self.set_stop(stop)
         self.precision = precision
         n_slab, n_state = C.c_longlong(), C.c_longlong()

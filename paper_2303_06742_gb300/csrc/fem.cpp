@@ -1327,6 +1327,41 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
   return 0;
 }
 
+void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, std::vector<double> *out,
+                          std::vector<long long> *off) {
+  (void)q;
+  off->assign(p1 - p0 + 1, 0);
+  for (long p = p0; p < p1; ++p) (*off)[p - p0 + 1] = (*off)[p - p0] + 2LL * P.cs[p] * P.cs[p];
+  out->assign((size_t)off->back(), 0.0);
+  std::atomic<long> next(p0);
+  auto work = [&]() {
+    std::vector<int> loc(L.ns, -1);
+    for (;;) {
+      const long p = next.fetch_add(1);
+      if (p >= p1) break;
+      const int Cs = P.cs[p];
+      // time node 0 of the patch dof list: the spatial indices
+      const int *sp = P.dofs.data() + P.dof_off[p];
+      for (int m = 0; m < Cs; ++m) loc[sp[m]] = m;
+      double *S1 = out->data() + (*off)[p - p0], *S2 = S1 + (size_t)Cs * Cs;
+      for (int m = 0; m < Cs; ++m) {
+        const int g = sp[m];
+        for (int e = L.rowptr[g]; e < L.rowptr[g + 1]; ++e) {
+          const int lc = loc[L.col[e]];
+          if (lc < 0) continue;
+          S1[(size_t)m * Cs + lc] = L.v1[e];
+          S2[(size_t)m * Cs + lc] = L.v2[e];
+        }
+      }
+      for (int m = 0; m < Cs; ++m) loc[sp[m]] = -1;
+    }
+  };
+  const int nt = (int)std::min<long>(n_threads(), std::max(1L, p1 - p0));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(work);
+  for (auto &t : th) t.join();
+}
+
 std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau) {
   const long ns = L.ns, N = ns * T.q;
   std::vector<double> A((size_t)N * N, 0.0);

@@ -130,6 +130,13 @@ struct Patches {
 int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patches *out,
                   std::string *err, bool invert_them = true, const TimeDiag *td = nullptr, int kind = 0);
 
+// The spatial patch blocks S1_P, S2_P (row-major C_s x C_s each, S2 right
+// after S1) of patches p0 .. p1-1 of a level whose dof lists P holds (built
+// with invert_them = false), for inversion on the device; off[p - p0] is
+// the offset of patch p's S1 in out.  Threaded.
+void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, std::vector<double> *out,
+                          std::vector<long long> *off);
+
 // Dense row-major slab matrix of a level (for the coarse solve).
 std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau);
 // In-place Gauss-Jordan inverse with partial pivoting of a row-major n x n

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <climits>
 #include <vector>
 
 using namespace stfem_dev;
@@ -712,16 +713,17 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-constexpr int STREAM_STAGES = 4;
+constexpr int STREAM_STAGES = 4;                    // most stages of the ring (runtime: nst)
 constexpr int STREAM_CHUNK = 16384;                 // bytes per shared-memory stage
 constexpr long long STREAM_WAIT_LIMIT = 4000000000LL; // clock cycles (about 2 s)
-constexpr int STREAM_HEADER = STREAM_STAGES * STREAM_CHUNK + 2 * STREAM_STAGES * 8 + 16;
+// shared-memory bytes before the per-patch vectors: the ring, the barriers
+__host__ __device__ constexpr int stream_header(int nst) { return nst * STREAM_CHUNK + 2 * STREAM_STAGES * 8 + 16; }
 
 // Time-diagonal patch apply (see k_patch_apply_diag) with the inverse blocks
 // streamed by bulk copies.  Persistent CTAs take patches p = blockIdx.x,
 // blockIdx.x + gridDim.x, ...  The last warp is the producer: one lane walks
 // the (patch, slot, column chunk) sequence and copies each chunk (contiguous,
-// 16-byte aligned, a multiple of 16 bytes) into a ring of STREAM_STAGES
+// 16-byte aligned, a multiple of 16 bytes) into a ring of nst <= STREAM_STAGES
 // shared stages.  The other warps gather and mix the residual, consume the
 // chunks of their slot rows from shared memory, and mix the result back.
 // Every wait is bounded; on a timeout the CTA sets *err, the producer waits
@@ -733,24 +735,24 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
                                                              const long long *__restrict__ pioff,
                                                              const T *__restrict__ pinv, const T *__restrict__ res,
                                                              T *__restrict__ y, DiagCoef<T> dc, int maxCs,
-                                                             int *__restrict__ err) {
+                                                             int *__restrict__ err, int nst) {
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
   extern __shared__ __align__(128) unsigned char smem_stream[];
   unsigned char *stage = smem_stream;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_stream + STREAM_STAGES * STREAM_CHUNK);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_stream + nst * STREAM_CHUNK);
   uint64_t *empty = full + STREAM_STAGES;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + STREAM_STAGES);
   const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
-  T *rs = reinterpret_cast<T *>(smem_stream + STREAM_HEADER);
+  T *rs = reinterpret_cast<T *>(smem_stream + stream_header(nst));
   T *rt = rs + (size_t)Q * maxCs;
   T *z = rt + (size_t)nrow * maxCs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwc = (blockDim.x >> 5) - 1; // consumer warps
   const int nct = nwc * 32;
   if (threadIdx.x == 0) {
-    for (int st = 0; st < STREAM_STAGES; ++st) {
+    for (int st = 0; st < nst; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], nwc);
     }
@@ -773,9 +775,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
         const T *sb = base + (sl < nr ? (size_t)sl * Cs * ldR : (size_t)nr * Cs * ldR + (size_t)(sl - nr) * Cs * ldC);
         const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
         for (int j0 = 0; j0 < Cs; j0 += K) {
-          const int st = (int)(it % STREAM_STAGES);
-          if (it >= STREAM_STAGES &&
-              !mbar_wait(&empty[st], (uint32_t)(((it / STREAM_STAGES) - 1) & 1), STREAM_WAIT_LIMIT)) {
+          const int st = (int)(it % nst);
+          if (it >= nst && !mbar_wait(&empty[st], (uint32_t)(((it / nst) - 1) & 1), STREAM_WAIT_LIMIT)) {
             ok = false;
             break;
           }
@@ -794,8 +795,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
       atomicExch(err, 1);
       *abort_flag = 1;
       // copies still in flight must land before the CTA exits
-      for (long long k = (it > STREAM_STAGES ? it - STREAM_STAGES : 0); k < it; ++k)
-        mbar_wait(&full[k % STREAM_STAGES], (uint32_t)((k / STREAM_STAGES) & 1), STREAM_WAIT_LIMIT);
+      for (long long k = (it > nst ? it - nst : 0); k < it; ++k)
+        mbar_wait(&full[k % nst], (uint32_t)((k / nst) & 1), STREAM_WAIT_LIMIT);
     }
     return;
   }
@@ -850,9 +851,9 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
       const int ld = sl < nr ? ldR : ldC;
       const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
       for (int j0 = 0; j0 < Cs; j0 += K) {
-        const int st = (int)(it % STREAM_STAGES);
+        const int st = (int)(it % nst);
         bool ready = !*abort_flag;
-        if (ready && !mbar_wait(&full[st], (uint32_t)((it / STREAM_STAGES) & 1), STREAM_WAIT_LIMIT)) {
+        if (ready && !mbar_wait(&full[st], (uint32_t)((it / nst) & 1), STREAM_WAIT_LIMIT)) {
           atomicExch(err, 2);
           *abort_flag = 1;
           ready = false;
@@ -912,6 +913,7 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
 }
 
 #include "tc_patch.cuh"
+#include "patch_factor.cuh"
 
 // d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
 // scale = omega / (number of patches holding the dof): Algorithm 4.1's
@@ -2023,7 +2025,11 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
   CKR(upload(h, &D.pdofs, P.dofs));
   CKR(upload(h, &D.pdoff, P.dof_off));
   CKR(upload(h, &D.pioff, P.inv_off));
-  CKR(upload(h, &D.pinv, P.inv));
+  if (P.inv.empty() && P.inv_off.back() > 0) {
+    CKR(dalloc(h, &D.pinv, (size_t)P.inv_off.back())); // factorised on the device
+  } else {
+    CKR(upload(h, &D.pinv, P.inv));
+  }
   CKR(dalloc(h, &D.ybuf, P.dofs.size()));
   // inverse map dof -> positions in ybuf, in patch order
   std::vector<int> cnt(D.N + 1, 0);
@@ -2054,6 +2060,147 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
   return 0;
 }
 
+// Stages of the tensor-core kernel's ring: as many as fit next to the fixed
+// shared memory when STFEM_TC_CTAS_PER_SM CTAs share an SM (at most 8).
+#ifndef STFEM_TC_CTAS_PER_SM
+#define STFEM_TC_CTAS_PER_SM 1
+#endif
+static int tc_stages(size_t fixed) {
+  const size_t per_cta = (227u * 1024u) / STFEM_TC_CTAS_PER_SM - 1024u;
+  if (fixed >= per_cta) return 0;
+  return (int)std::min<size_t>(tcp::MAXSTAGES, (per_cta - fixed) / tcp::STAGE);
+}
+
+// Time-diagonal patch inverses of a level computed on the device (see
+// patch_factor.cuh): the host extracts S1_P, S2_P in batches of at most
+// about 1 GB, the device forms lam_a S1_P + S2_P per slot and inverts it in
+// FP64 straight into the level's storage.
+template <typename T>
+int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem::Patches &P,
+                     const stfem::TimeDiag &td) {
+  const int ns = td.nr + td.nc;
+  if (D.maxCs > 512) {
+    h->err = "patches too large for the device factorisation";
+    return STFEM_ERR_ARG;
+  }
+  double *lam = nullptr, *blocks = nullptr, *scratch = nullptr;
+  long long *boff = nullptr, *bad = nullptr;
+  std::vector<double> lamh(td.lam.begin(), td.lam.end());
+  lamh.resize(2 * ns, 0.0);
+  const long scr_stride = 2L * D.maxCs * D.maxCs;
+  const long long limit = 1LL << 30;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(608, limit / (scr_stride * 8)));
+  int rc = 0;
+  do {
+    if (cudaMalloc((void **)&lam, lamh.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&scratch, (size_t)grid * scr_stride * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&bad, sizeof(long long)) != cudaSuccess) {
+      h->err = "device factorisation: out of memory";
+      rc = STFEM_ERR_OOM;
+      break;
+    }
+    const long long none = LLONG_MAX;
+    cudaMemcpy(lam, lamh.data(), lamh.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(bad, &none, sizeof(long long), cudaMemcpyHostToDevice);
+    size_t cap_blocks = 0, cap_off = 0;
+    std::vector<double> hb;
+    std::vector<long long> ho;
+    for (long p0 = 0; p0 < P.npatch && rc == 0;) {
+      long p1 = p0;
+      long long bytes = 0;
+      while (p1 < P.npatch && (p1 == p0 || bytes + 16LL * P.cs[p1] * P.cs[p1] <= limit)) {
+        bytes += 16LL * P.cs[p1] * P.cs[p1];
+        ++p1;
+      }
+      stfem::extract_patch_blocks(L, P, h->q, p0, p1, &hb, &ho);
+      if (hb.size() > cap_blocks) {
+        if (blocks) cudaFree(blocks);
+        blocks = nullptr;
+        if (cudaMalloc((void **)&blocks, hb.size() * sizeof(double)) != cudaSuccess) {
+          h->err = "device factorisation: out of memory";
+          rc = STFEM_ERR_OOM;
+          break;
+        }
+        cap_blocks = hb.size();
+      }
+      if (ho.size() > cap_off) {
+        if (boff) cudaFree(boff);
+        boff = nullptr;
+        if (cudaMalloc((void **)&boff, ho.size() * sizeof(long long)) != cudaSuccess) {
+          h->err = "device factorisation: out of memory";
+          rc = STFEM_ERR_OOM;
+          break;
+        }
+        cap_off = ho.size();
+      }
+      if (cudaMemcpy(blocks, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(boff, ho.data(), ho.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->err = "device factorisation: copy failed";
+        rc = STFEM_ERR_CUDA;
+        break;
+      }
+      const long items = (p1 - p0) * ns;
+      k_patch_factor<T><<<(int)std::min<long>(grid, items), PF_THREADS>>>(p0, p1 - p0, td.nr, td.nc, lam, D.pcs,
+                                                                          boff, blocks, D.pioff, D.pinv, scratch,
+                                                                          scr_stride, bad);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
+        h->err = "device factorisation kernel failed";
+        rc = STFEM_ERR_CUDA;
+        break;
+      }
+      p0 = p1;
+    }
+    if (rc == 0) {
+      long long b = none;
+      cudaMemcpy(&b, bad, sizeof(long long), cudaMemcpyDeviceToHost);
+      if (b != none) {
+        h->err = "singular patch matrix (patch " + std::to_string(b) + ")";
+        rc = STFEM_ERR_SINGULAR_PATCH;
+      }
+    }
+  } while (false);
+  if (lam) cudaFree(lam);
+  if (blocks) cudaFree(blocks);
+  if (boff) cudaFree(boff);
+  if (scratch) cudaFree(scratch);
+  if (bad) cudaFree(bad);
+  return rc;
+}
+
+// Tensor-core tiles from device-resident FP32 inverses.
+int build_tc_tiles_device(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
+  const int nr = D.dc.nr, nc = D.dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  const int c8max = tcp::cs8(D.maxCs);
+  if (c8max * 32 > tcp::STAGE) {
+    h->err = "patches too large for the tensor-core patch apply";
+    return STFEM_ERR_ARG;
+  }
+  const size_t fixed = tcp::smem_bytes(0, D.maxCs, nrow);
+  const int nst = tc_stages(fixed);
+  if (nst < 2) {
+    h->err = "patches too large for the tensor-core patch apply (shared memory)";
+    return STFEM_ERR_ARG;
+  }
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(16 * ((c8max + 127) / 128))) cols *= 2;
+  std::vector<long long> off(P.npatch + 1, 0);
+  for (long p = 0; p < P.npatch; ++p) {
+    const long long c8 = tcp::cs8(P.cs[p]);
+    long long n = 0;
+    for (int a = 0; a < ns; ++a) n += (long long)tcp::kext(a, nr, (int)c8) * c8;
+    off[p + 1] = off[p] + n;
+  }
+  CKR(upload(h, &D.ptoff, off));
+  CKR(dalloc(h, &D.ptile, (size_t)off[P.npatch]));
+  k_build_tc_tiles<<<(unsigned)P.npatch, 256>>>(D.pcs, D.pioff, D.pinv, D.ptoff, D.ptile, nr, nc);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(0));
+  D.tc = 1;
+  D.tc_nst = nst;
+  D.tc_cols = cols;
+  return 0;
+}
+
 // Level work vectors with nb columns (b, d, r of N; the patch results of sumC).
 template <typename T>
 int ensure_columns(stfem_h h, DLevel<T> &D, int nb) {
@@ -2078,8 +2225,7 @@ int upload_tc_tiles(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
     return STFEM_ERR_ARG;
   }
   const size_t fixed = tcp::smem_bytes(0, D.maxCs, nrow);
-  const int nst = (int)std::min<size_t>(tcp::MAXSTAGES, (227u * 1024u - std::min<size_t>(fixed, 227u * 1024u)) /
-                                                            tcp::STAGE);
+  const int nst = tc_stages(fixed);
   if (nst < 2) {
     h->err = "patches too large for the tensor-core patch apply (shared memory)";
     return STFEM_ERR_ARG;
@@ -2159,24 +2305,29 @@ void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t sme
 // row block of the largest patch (rounded to warps) plus a producer warp;
 // shared memory = stages + the per-patch vectors; as many CTAs per SM as
 // shared memory allows (at most 3), at most one CTA per patch.
+// Ring shape (measured on GB300 with both bench workloads): 2D patches (few
+// consumer warps per CTA) run best with 2 stages and up to 5 CTAs per SM,
+// 3D patches with 4 stages and up to 3.
 template <typename T>
-void stream_shape(const DLevel<T> &L, int q, int *threads, size_t *smem, int *grid) {
+void stream_shape(const DLevel<T> &L, int q, int dim, int *threads, size_t *smem, int *grid, int *nst) {
   constexpr int VEC = Vec16<T>::n;
   const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
   const int nwc = std::max(1, (rows + 31) / 32);
   *threads = 32 * (nwc + 1);
-  *smem = (size_t)STREAM_HEADER + (size_t)(q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
-  const int per_sm = std::max(1, std::min(3, (int)((227u * 1024u) / *smem)));
+  *nst = dim == 2 ? 2 : STREAM_STAGES;
+  const int cap = dim == 2 ? 5 : 3;
+  *smem = (size_t)stream_header(*nst) + (size_t)(q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
+  const int per_sm = std::max(1, std::min(cap, (int)((227u * 1024u) / *smem)));
   *grid = (int)std::min<long>(L.npatch, 152L * per_sm);
 }
 
 template <typename T, int Q>
 void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
-  int threads, grid;
+  int threads, grid, nst;
   size_t smem;
-  stream_shape(L, Q, &threads, &smem, &grid);
+  stream_shape(L, Q, h->dim, &threads, &smem, &grid, &nst);
   k_patch_apply_stream<T, Q><<<grid, threads, smem, h->stream>>>((int)L.npatch, L.pcs, L.pdoff, L.pdofs, L.pioff,
-                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err);
+                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err, nst);
 }
 
 template <typename T>
@@ -2251,9 +2402,9 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
   constexpr int VEC = Vec16<T>::n;
   if (L.form != 1) return 0;
   const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
-  int threads, grid;
+  int threads, grid, nst;
   size_t smem;
-  stream_shape(L, h->q, &threads, &smem, &grid);
+  stream_shape(L, h->q, h->dim, &threads, &smem, &grid, &nst);
   const size_t widest_column = (size_t)2 * ((L.maxCs + 1) / 2 * 2) * sizeof(T); // complex slot column
   if (rows > 992 || smem > 227u * 1024u || widest_column > (size_t)STREAM_CHUNK) {
     h->err = "patches too large for the time-diagonal form (" + std::to_string(rows) + " row threads, " +
@@ -2266,7 +2417,7 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
 template <int Q>
 void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, int nb) {
   const size_t smem = tcp::smem_bytes(L.tc_nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
-  const int grid = (int)std::min<long>(L.npatch, 152L);
+  const int grid = (int)std::min<long>(L.npatch, 152L * STFEM_TC_CTAS_PER_SM);
   k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)L.npatch, nb, L.pcs, L.pdoff, L.pdofs, L.ptoff,
                                                              L.ptile, res, L.N, L.ybuf, L.sumC, L.dc, L.maxCs,
                                                              L.tc_nst, L.tc_cols, h->dev_err);
@@ -3294,10 +3445,12 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       return STFEM_ERR_STATE;
     }
   }
+  // time-diagonal inverses are factorised on the device unless asked otherwise
+  const bool dev_factor = form == STFEM_PATCH_TIME_DIAGONAL && !p->factor_host;
   for (int l = 1; l < h->nlev; ++l) {
     stfem::Patches P;
     std::string err;
-    if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err, true,
+    if (stfem::build_patches(h->hl[l], h->T, h->tau, mixed ? 4 : 2, &P, &err, !dev_factor,
                              form == STFEM_PATCH_TIME_DIAGONAL ? &td : nullptr, h->patch_kind) < 0) {
       h->err = err + " on level " + std::to_string(l);
       return STFEM_ERR_SINGULAR_PATCH;
@@ -3306,11 +3459,14 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       set_diag(h->L32[l], td);
       CKR(upload_patches(h, h->L32[l], P, h->omega, h->update));
       CKR(check_patch_shape(h, h->L32[l]));
-      if (h->nrhs_cap > 1 && form == STFEM_PATCH_TIME_DIAGONAL) CKR(upload_tc_tiles(h, h->L32[l], P));
+      if (dev_factor) CKR(factor_on_device(h, h->L32[l], h->hl[l], P, td));
+      if (h->nrhs_cap > 1 && form == STFEM_PATCH_TIME_DIAGONAL)
+        CKR(dev_factor ? build_tc_tiles_device(h, h->L32[l], P) : upload_tc_tiles(h, h->L32[l], P));
     } else {
       set_diag(h->L64[l], td);
       CKR(upload_patches(h, h->L64[l], P, h->omega, h->update));
       CKR(check_patch_shape(h, h->L64[l]));
+      if (dev_factor) CKR(factor_on_device(h, h->L64[l], h->hl[l], P, td));
     }
   }
   std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
