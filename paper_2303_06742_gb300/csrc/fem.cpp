@@ -872,11 +872,9 @@ int n_threads() {
   return n ? (int)n : 4;
 }
 
-bool invert(double *a, int n) {
+static bool invert_unblocked(double *a, int n) {
   std::vector<int> piv(n);
-  // large matrices (the coarse level): the row updates of each pivot step
-  // run in parallel; patch matrices are inverted one per thread instead
-  const bool par = n >= 512;
+  const bool par = false;
   for (int k = 0; k < n; ++k) {
     int p = k;
     double best = std::fabs(a[(size_t)k * n + k]);
@@ -910,6 +908,124 @@ bool invert(double *a, int n) {
       for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + k], a[(size_t)i * n + piv[k]]);
   return true;
 }
+
+// Blocked Gauss-Jordan inverse (delayed updates) for large matrices (the
+// coarse level): the same eliminations and pivots as invert_unblocked, in
+// panels of PB columns.  Inside a panel the panel columns of every row are
+// updated at once; the other columns of the panel's pivot rows are brought up
+// to date when the row becomes the pivot; all remaining updates of a panel are
+// applied at its end as one rank-PB product, threaded and register-blocked,
+// so the matrix is swept once per panel instead of once per pivot.
+static bool invert_blocked(double *a, int n) {
+  constexpr int PB = 64;
+  const bool par = n >= 2048; // threads only for the coarse level (patch workers are threads already)
+  std::vector<int> piv(n);
+  std::vector<double> F((size_t)n * PB), R((size_t)PB * n);
+  for (int k0 = 0; k0 < n; k0 += PB) {
+    const int k1 = std::min(n, k0 + PB), b = k1 - k0;
+    std::fill(F.begin(), F.end(), 0.0);
+    for (int k = k0; k < k1; ++k) {
+      const int kk = k - k0;
+      int p = k;
+      double best = std::fabs(a[(size_t)k * n + k]);
+      for (int i = k + 1; i < n; ++i) {
+        const double v = std::fabs(a[(size_t)i * n + k]);
+        if (v > best) {
+          best = v;
+          p = i;
+        }
+      }
+      if (!(best > 0.0) || !std::isfinite(best)) return false;
+      piv[k] = p;
+      if (p != k) {
+        for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+        for (int j = 0; j < PB; ++j) std::swap(F[(size_t)k * PB + j], F[(size_t)p * PB + j]);
+      }
+      double *rk = a + (size_t)k * n;
+      // pending updates of this panel's earlier steps on row k, outside the panel
+      for (int q2 = 0; q2 < kk; ++q2) {
+        const double f = F[(size_t)k * PB + q2];
+        if (f == 0.0) continue;
+        const double *rq = a + (size_t)(k0 + q2) * n;
+#pragma omp parallel for schedule(static) if (par && n >= 4096)
+        for (int j = 0; j < n; ++j)
+          if (j < k0 || j >= k1) rk[j] -= f * rq[j];
+        F[(size_t)k * PB + q2] = 0.0;
+      }
+      const double inv = 1.0 / rk[k];
+      rk[k] = 1.0;
+      for (int j = 0; j < n; ++j) rk[j] *= inv;
+      // the panel columns of every other row; the multipliers are kept
+#pragma omp parallel for schedule(static) if (par)
+      for (int i = 0; i < n; ++i) {
+        if (i == k) continue;
+        double *ri = a + (size_t)i * n;
+        const double f = ri[k];
+        if (f == 0.0) continue;
+        F[(size_t)i * PB + kk] = f;
+        ri[k] = 0.0;
+        for (int j = k0; j < k1; ++j) ri[j] -= f * rk[j];
+      }
+    }
+    // the panel's pivot rows outside the panel, as they were at their steps
+    for (int q2 = 0; q2 < b; ++q2)
+      std::copy(a + (size_t)(k0 + q2) * n, a + (size_t)(k0 + q2 + 1) * n, R.begin() + (size_t)q2 * n);
+    // rows -= F R outside the panel: four rows per pass over a column tile
+    const int nblk = (n + 3) / 4;
+#pragma omp parallel for schedule(dynamic, 4) if (par)
+    for (int ib = 0; ib < nblk; ++ib) {
+      const int i0 = ib * 4, ni = std::min(4, n - i0);
+      for (int j0 = 0; j0 < n; j0 += 512) {
+        const int j1 = std::min(n, j0 + 512);
+        for (int q2 = 0; q2 < b; ++q2) {
+          double f[4] = {0.0, 0.0, 0.0, 0.0};
+          bool any = false;
+          for (int t = 0; t < ni; ++t) {
+            f[t] = F[(size_t)(i0 + t) * PB + q2];
+            any = any || f[t] != 0.0;
+          }
+          if (!any) continue;
+          const double *rq = R.data() + (size_t)q2 * n;
+          // the tile without the panel columns: [j0, ja) and [jb, j1)
+          const int ja = std::min(j1, std::max(j0, k0)), jb = std::max(j0, std::min(j1, k1));
+          if (ni == 4) {
+            double *r0 = a + (size_t)i0 * n, *r1 = r0 + n, *r2 = r1 + n, *r3 = r2 + n;
+            const double f0 = f[0], f1 = f[1], f2 = f[2], f3 = f[3];
+            for (int j = j0; j < ja; ++j) {
+              const double x = rq[j];
+              r0[j] -= f0 * x;
+              r1[j] -= f1 * x;
+              r2[j] -= f2 * x;
+              r3[j] -= f3 * x;
+            }
+            for (int j = jb; j < j1; ++j) {
+              const double x = rq[j];
+              r0[j] -= f0 * x;
+              r1[j] -= f1 * x;
+              r2[j] -= f2 * x;
+              r3[j] -= f3 * x;
+            }
+          } else {
+            for (int t = 0; t < ni; ++t) {
+              double *ri = a + (size_t)(i0 + t) * n;
+              const double ft = f[t];
+              for (int j = j0; j < ja; ++j) ri[j] -= ft * rq[j];
+              for (int j = jb; j < j1; ++j) ri[j] -= ft * rq[j];
+            }
+          }
+        }
+      }
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k)
+      for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + k], a[(size_t)i * n + piv[k]]);
+  return true;
+}
+
+// Patch matrices (small, one per thread) take the unblocked form; the coarse
+// level (large) the blocked one.
+bool invert(double *a, int n) { return n >= 512 ? invert_blocked(a, n) : invert_unblocked(a, n); }
 
 // Gauss-Jordan inverse with partial pivoting of a complex row-major matrix
 // held as separate real and imaginary parts (contiguous rows vectorise);

@@ -6,9 +6,10 @@
 // slot; (re, im) interleaved per row, ld = 2 * 2 ceil(Cs/2) for a complex
 // slot), rounded to the storage type.  Included by stfem.cu.
 //
-// One CTA per (patch, slot) item at a time (persistent grid); the working
-// matrix lives in a global scratch block of the CTA (L2-resident: the
-// matrices of all CTAs in flight fit in L2), planar real / imaginary parts.
+// Persistent CTAs take (patch, slot) items from an atomic counter (patch
+// sizes vary, so a static split would leave CTAs idle); the working matrix
+// lives in a global scratch block of the CTA (L2-resident: the matrices of
+// all CTAs in flight fit in L2), planar real / imaginary parts.
 // No waits: every step ends at __syncthreads.  A zero or non-finite pivot
 // marks the patch in *bad (the smallest such index wins) and the item stops.
 
@@ -19,15 +20,21 @@ __global__ void __launch_bounds__(PF_THREADS)
     k_patch_factor(long p0, long np, int nr, int nc, const double *__restrict__ lam, const int *__restrict__ pcs,
                    const long long *__restrict__ boff, const double *__restrict__ blocks,
                    const long long *__restrict__ pioff, T *__restrict__ pinv, double *__restrict__ scratch,
-                   long scr_stride, long long *__restrict__ bad) {
+                   long scr_stride, long long *__restrict__ bad, unsigned long long *__restrict__ next) {
   __shared__ double fr[512], fi[512]; // column k before the elimination (Cs <= 512)
   __shared__ double red_v[PF_THREADS];
   __shared__ int red_i[PF_THREADS];
   __shared__ int piv[512];
   __shared__ int stop;
+  __shared__ long long take;
   const int ns = nr + nc;
   double *Zr = scratch + (long)blockIdx.x * scr_stride;
-  for (long item = blockIdx.x; item < np * ns; item += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) take = (long long)atomicAdd(next, 1ull);
+    __syncthreads();
+    const long item = (long)take;
+    __syncthreads();
+    if (item >= np * ns) break;
     const long pl = item / ns;  // patch within the batch
     const int a = (int)(item - pl * ns);
     const long p = p0 + pl;

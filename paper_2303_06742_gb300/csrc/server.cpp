@@ -69,7 +69,8 @@ void run_request(stfem_server s, Request &R) {
       status = STFEM_ERR_CUDA;
       break;
     }
-    if ((status = stfem_setup(&q.mesh, &q.deg, &q.mat, &q.bcs, q.tau, &h)) < 0) {
+    status = stfem_setup(&q.mesh, &q.deg, &q.mat, &q.bcs, q.tau, &h);
+    if (status < 0) {
       msg = stfem_last_error(nullptr);
       break;
     }

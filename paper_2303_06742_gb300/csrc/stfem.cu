@@ -300,8 +300,27 @@ __device__ __forceinline__ void df_add(DF &acc, float bh, float bl) {
 
 __device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
 
+// acc += c * a for a float-pair coefficient c and a double-float value a
+__device__ __forceinline__ void df_fma(DF &acc, float2 c, const DF &a) {
+  const float p = c.x * a.hi;
+  float e = fmaf(c.x, a.hi, -p);
+  e = fmaf(c.x, a.lo, e);
+  e = fmaf(c.y, a.hi, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float err = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += err + e;
+}
+
+// Dt and W of Eq. 4.7 as float pairs (for the double-float time mixing)
+struct TimeCoefDF {
+  int q;
+  float2 Dt[MAXQ * MAXQ], W[MAXQ], mW[MAXQ];
+};
+
 template <int Q, int D, int G>
-__global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns, long R, TimeCoef<double> tc,
+__global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns, long R, TimeCoefDF tc,
                                                  const float *__restrict__ x, double *__restrict__ y, int nb,
                                                  long cstride) {
   constexpr int NA = 4 * Q * D;
@@ -398,29 +417,35 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
       df_add(acc[i], bh, bl);
     }
   }
+  // time-node mixing of Eq. 4.7 in double-float as well; one conversion to
+  // FP64 per output
   if (is_u) {
 #pragma unroll
     for (int o = 0; o < 2 * Q * D; ++o) {
       if (o % G != lane) continue;
       const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
-      double val = 0.0;
+      DF val{0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < Q; ++t) val += tc.Dt[b * Q + t] * df_val(acc[(eq * Q + t) * D + c]);
-      if (eq == 0)
-        val -= tc.W[b] * df_val(acc[(1 * Q + b) * D + c]);
-      else
-        val += tc.W[b] * (df_val(acc[(2 * Q + b) * D + c]) + df_val(acc[(3 * Q + b) * D + c]));
-      y[(long)b * ns + eq * R + node * D + c] = val;
+      for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[(eq * Q + t) * D + c]);
+      if (eq == 0) {
+        df_fma(val, tc.mW[b], acc[(1 * Q + b) * D + c]);
+      } else {
+        df_fma(val, tc.W[b], acc[(2 * Q + b) * D + c]);
+        df_fma(val, tc.W[b], acc[(3 * Q + b) * D + c]);
+      }
+      y[(long)b * ns + eq * R + node * D + c] = df_val(val);
     }
   } else if (is_p) {
     const long sI = node - A.nu;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
       if (b % G != lane) continue;
-      double val = tc.W[b] * (df_val(acc[Q + b]) + df_val(acc[2 * Q + b]));
+      DF val{0.f, 0.f};
+      df_fma(val, tc.W[b], acc[Q + b]);
+      df_fma(val, tc.W[b], acc[2 * Q + b]);
 #pragma unroll
-      for (int t = 0; t < Q; ++t) val += tc.Dt[b * Q + t] * df_val(acc[t]);
-      y[(long)b * ns + 2 * R + sI] = val;
+      for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[t]);
+      y[(long)b * ns + 2 * R + sI] = df_val(val);
     }
   }
 }
@@ -1674,7 +1699,18 @@ void launch_spmv_df_qd(cudaStream_t s, const DLevel<double> &L, const TimeCoef<d
                        double *y, int nb) {
   constexpr int G = D == 3 ? 8 : 4;
   const long threads = (L.nb.nu + L.nb.np) * G;
-  k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, tc, x, y, nb, L.N);
+  TimeCoefDF td{};
+  td.q = tc.q;
+  auto pair = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
+  for (int i = 0; i < tc.q * tc.q; ++i) td.Dt[i] = pair(tc.Dt[i]);
+  for (int b = 0; b < tc.q; ++b) {
+    td.W[b] = pair(tc.W[b]);
+    td.mW[b] = pair(-tc.W[b]);
+  }
+  k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
 }
 
 // y = A x on the finest FP64 level in double-float arithmetic, x FP32 (nb
@@ -2063,7 +2099,7 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
 // Stages of the tensor-core kernel's ring: as many as fit next to the fixed
 // shared memory when STFEM_TC_CTAS_PER_SM CTAs share an SM (at most 8).
 #ifndef STFEM_TC_CTAS_PER_SM
-#define STFEM_TC_CTAS_PER_SM 1
+#define STFEM_TC_CTAS_PER_SM 2
 #endif
 static int tc_stages(size_t fixed) {
   const size_t per_cta = (227u * 1024u) / STFEM_TC_CTAS_PER_SM - 1024u;
@@ -2074,7 +2110,9 @@ static int tc_stages(size_t fixed) {
 // Time-diagonal patch inverses of a level computed on the device (see
 // patch_factor.cuh): the host extracts S1_P, S2_P in batches of at most
 // about 1 GB, the device forms lam_a S1_P + S2_P per slot and inverts it in
-// FP64 straight into the level's storage.
+// FP64 straight into the level's storage, on a lowest-priority stream of the
+// setup: when factorisation CTAs retire, kernels of other handles (the
+// marches of concurrent requests) get the SMs first.
 template <typename T>
 int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem::Patches &P,
                      const stfem::TimeDiag &td) {
@@ -2085,6 +2123,8 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
   }
   double *lam = nullptr, *blocks = nullptr, *scratch = nullptr;
   long long *boff = nullptr, *bad = nullptr;
+  unsigned long long *next = nullptr;
+  cudaStream_t fs = nullptr;
   std::vector<double> lamh(td.lam.begin(), td.lam.end());
   lamh.resize(2 * ns, 0.0);
   const long scr_stride = 2L * D.maxCs * D.maxCs;
@@ -2092,9 +2132,13 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
   const int grid = (int)std::max<long long>(1, std::min<long long>(608, limit / (scr_stride * 8)));
   int rc = 0;
   do {
-    if (cudaMalloc((void **)&lam, lamh.size() * sizeof(double)) != cudaSuccess ||
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&fs, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+        cudaMalloc((void **)&lam, lamh.size() * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void **)&scratch, (size_t)grid * scr_stride * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&bad, sizeof(long long)) != cudaSuccess) {
+        cudaMalloc((void **)&bad, sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void **)&next, sizeof(unsigned long long)) != cudaSuccess) {
       h->err = "device factorisation: out of memory";
       rc = STFEM_ERR_OOM;
       break;
@@ -2133,17 +2177,25 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
         }
         cap_off = ho.size();
       }
+      // cudaMemcpy from pageable memory may return before its DMA has landed;
+      // it is ordered only with the legacy stream, so wait there before the
+      // factorisation stream reads the batch (and the earlier uploads)
       if (cudaMemcpy(blocks, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMemcpy(boff, ho.data(), ho.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+          cudaMemcpy(boff, ho.data(), ho.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaStreamSynchronize(0) != cudaSuccess) {
         h->err = "device factorisation: copy failed";
         rc = STFEM_ERR_CUDA;
         break;
       }
       const long items = (p1 - p0) * ns;
-      k_patch_factor<T><<<(int)std::min<long>(grid, items), PF_THREADS>>>(p0, p1 - p0, td.nr, td.nc, lam, D.pcs,
-                                                                          boff, blocks, D.pioff, D.pinv, scratch,
-                                                                          scr_stride, bad);
-      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
+      if (cudaMemsetAsync(next, 0, sizeof(unsigned long long), fs) != cudaSuccess) {
+        h->err = "device factorisation: memset failed";
+        rc = STFEM_ERR_CUDA;
+        break;
+      }
+      k_patch_factor<T><<<(int)std::min<long>(grid, items), PF_THREADS, 0, fs>>>(
+          p0, p1 - p0, td.nr, td.nc, lam, D.pcs, boff, blocks, D.pioff, D.pinv, scratch, scr_stride, bad, next);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(fs) != cudaSuccess) {
         h->err = "device factorisation kernel failed";
         rc = STFEM_ERR_CUDA;
         break;
@@ -2159,11 +2211,14 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
       }
     }
   } while (false);
+  if (fs) cudaStreamSynchronize(fs);
   if (lam) cudaFree(lam);
   if (blocks) cudaFree(blocks);
   if (boff) cudaFree(boff);
   if (scratch) cudaFree(scratch);
   if (bad) cudaFree(bad);
+  if (next) cudaFree(next);
+  if (fs) cudaStreamDestroy(fs);
   return rc;
 }
 
