@@ -209,6 +209,20 @@ def dram_traffic(workload, precision):
     return r.get("bytes_per_launch")
 
 
+def job_throughput(units_per_rank, total_ms, world, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units in its own total_ms; the job took the slowest rank's
+    time, so value = units_per_rank * world / max over ranks of the time.
+    Returns (value in units/s, the max time in ms).  The only collective is
+    this one MAX reduction of a timing scalar; the solves exchange nothing."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return units_per_rank * world / (total_ms / 1000.0), total_ms
+
+
 def pct(vals, q):
     v = sorted(vals)
     if not v:
@@ -298,11 +312,7 @@ def gpu_arm(args):
     _, _ = time_march(S, torch, stream, state, W + K, KP, tol, profile=True)
     prof = S.profile_read()
     S.profile(False)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = K * world / (total_ms / 1000.0)
+    value, total_ms = job_throughput(K, total_ms, world, dist)
 
     # ---- end to end through the public call with host buffers
     E = min(K, 5)
@@ -520,11 +530,7 @@ def batch_arm(args):
     run(W + K, KP, profile=True)
     prof = S.profile_read()
     S.profile(False)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = K * nb * world / (total_ms / 1000.0)
+    value, total_ms = job_throughput(K * nb, total_ms, world, dist)
 
     # end to end: every step copies the nb right-hand sides and initial
     # guesses from pinned host memory and the solutions back
