@@ -36,6 +36,15 @@ using namespace stfem_dev;
 // with column groups (more loads in flight per patch) instead of streaming
 #define STFEM_STREAM_MIN_PATCHES 0
 #endif
+// lanes per output of the restriction (rows of P^T hold up to (2r+1)^d
+// entries) and of the prolongation (rows of P: up to (r+1)^d); measured on
+// both bench workloads: 8 lanes for the restriction took 5% off a 2D slab
+#ifndef STFEM_RESTRICT_LANES
+#define STFEM_RESTRICT_LANES 8
+#endif
+#ifndef STFEM_PROLONG_LANES
+#define STFEM_PROLONG_LANES 1
+#endif
 #ifndef STFEM_PATCH_THREADS_PER_SM
 #define STFEM_PATCH_THREADS_PER_SM 4096
 #endif
@@ -963,43 +972,63 @@ __global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *
 // out[a, P, node] (+)= sum_e Mp[node, e] in[a, P, col_e] (Q_{r-1} space).
 // One thread per (time node, block, output node): the d components of a node
 // are contiguous, so each operator entry feeds D loads from one segment.
-template <typename T, int D>
+template <typename T, int D, int G>
 __global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_out, long ns_in, long R_in,
                            const int *__restrict__ up, const int *__restrict__ uc, const T *__restrict__ uv,
                            const int *__restrict__ pp, const int *__restrict__ pc, const T *__restrict__ pv,
                            const T *__restrict__ in, T *__restrict__ out, int add, int nb, long in_stride,
                            long out_stride) {
+  // G lanes per output (the long rows of P^T in the restriction), reduced by
+  // xor-shuffles in a fixed order; every lane of the warp takes part in the
+  // shuffles (lanes without an output carry zeros)
   const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  const long i = gid / G;
+  const int lane = (int)(gid % G);
   in += (long)col * in_stride;
   out += (long)col * out_stride;
   const long nuq = 2 * nu_out * q;
-  if (i < nuq) {
-    const long node = i % nu_out;
-    const long ab = i / nu_out; // a * 2 + blk
-    const int a = (int)(ab >> 1), blk = (int)(ab & 1);
-    T acc[D];
+  T acc[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = T(0);
+  for (int c = 0; c < D; ++c) acc[c] = T(0);
+  int kind = 0;
+  long node = 0;
+  int a = 0, blk = 0;
+  if (i < nuq) {
+    kind = 1;
+    node = i % nu_out;
+    const long ab = i / nu_out; // a * 2 + blk
+    a = (int)(ab >> 1);
+    blk = (int)(ab & 1);
     const T *src = in + (long)a * ns_in + blk * R_in;
-    for (int e = up[node]; e < up[node + 1]; ++e) {
+    for (int e = up[node] + lane; e < up[node + 1]; e += G) {
       const T w = uv[e];
       const T *sp = src + (long)uc[e] * D;
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[c] += w * sp[c];
     }
+  } else if (i < nuq + np_out * q) {
+    kind = 2;
+    const long j = i - nuq;
+    node = j % np_out;
+    a = (int)(j / np_out);
+    const T *src = in + (long)a * ns_in + 2 * R_in;
+    for (int e = pp[node] + lane; e < pp[node + 1]; e += G) acc[0] += pv[e] * src[pc[e]];
+  }
+  if (G > 1) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
+  }
+  if (lane != 0) return;
+  if (kind == 1) {
     T *dst = out + (long)a * ns_out + blk * R_out + node * D;
 #pragma unroll
     for (int c = 0; c < D; ++c) dst[c] = add ? dst[c] + acc[c] : acc[c];
-  } else if (i < nuq + np_out * q) {
-    const long j = i - nuq;
-    const long node = j % np_out;
-    const int a = (int)(j / np_out);
-    T acc = T(0);
-    const T *src = in + (long)a * ns_in + 2 * R_in;
-    for (int e = pp[node]; e < pp[node + 1]; ++e) acc += pv[e] * src[pc[e]];
+  } else if (kind == 2) {
     T *dst = out + (long)a * ns_out + 2 * R_out + node;
-    *dst = add ? *dst + acc : acc;
+    *dst = add ? *dst + acc[0] : acc[0];
   }
 }
 
@@ -2531,15 +2560,15 @@ void restrict_to(stfem_h h, int l, const T *rf, T *bc, int nb = 1) {
   DLevel<T> &C = levels<T>(h)[l - 1];
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + F.N) * sizeof(T) * nb + F.transfer_bytes,
             2.0 * F.transfer_nnz * nb);
+  // restriction: rows of P^T are long, STFEM_RESTRICT_LANES lanes per output
   const long nu = C.R / h->dim, np = C.S, nt = (2 * nu + np) * h->q;
+  constexpr int GR = STFEM_RESTRICT_LANES;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
-                                                                          F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf,
-                                                                          bc, 0, nb, F.N, C.N);
+    k_transfer<T, 2, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
+        nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
   else
-    k_transfer<T, 3><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p,
-                                                                          F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf,
-                                                                          bc, 0, nb, F.N, C.N);
+    k_transfer<T, 3, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
+        nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
 }
 
 template <typename T>
@@ -2549,14 +2578,13 @@ void prolongate_add(stfem_h h, int l, const T *dc, T *df, int nb = 1) {
   Launch G_(h, STFEM_KCLASS_TRANSFER, (double)(C.N + 2 * F.N) * sizeof(T) * nb + F.transfer_bytes,
             2.0 * F.transfer_nnz * nb);
   const long nu = F.R / h->dim, np = F.S, nt = (2 * nu + np) * h->q;
+  constexpr int GP = STFEM_PROLONG_LANES;
   if (h->dim == 2)
-    k_transfer<T, 2><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
-                                                                          F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc,
-                                                                          df, 1, nb, C.N, F.N);
+    k_transfer<T, 2, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
+        nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
   else
-    k_transfer<T, 3><<<grid_for(nt, 128) * nb, 128, 0, h->stream>>>(nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p,
-                                                                          F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc,
-                                                                          df, 1, nb, C.N, F.N);
+    k_transfer<T, 3, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
+        nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
 }
 
 template <typename T>
