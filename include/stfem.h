@@ -431,6 +431,13 @@ int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, co
  * Dt[b*q+a] (row-major) for dG(k), q = k+1 (Eq. 2.4). */
 int stfem_host_temporal(int k, double *t_host, double *w_host, double *chi_host, double *Dt_host);
 
+/* In-place inverse of the row-major n x n host matrix a_host by the
+ * Gauss-Jordan elimination with partial pivoting (first largest modulus)
+ * that setup uses for the coarse level (Sec. 4: direct solve on level 0);
+ * blocked with delayed updates for n >= 512.  STFEM_ERR_SINGULAR_PATCH on a
+ * zero pivot. */
+int stfem_host_invert(int n, double *a_host);
+
 /* Message of the last error on this handle (or, when h is NULL, of the last
  * failed stfem_setup made by the calling thread). */
 const char *stfem_last_error(stfem_h h);

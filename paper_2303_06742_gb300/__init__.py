@@ -114,6 +114,7 @@ def _load():
         "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pLL, pI, pD],
         "stfem_host_temporal": [I, pD, pD, pD, pD],
+        "stfem_host_invert": [I, pD],
         "stfem_profile": [P, I],
         "stfem_set_stop": [P, I],
         "stfem_footprint_bytes": [P, pLL],
@@ -233,6 +234,13 @@ def host_prolongation(prob, level, field):
                                             C.byref(nnz), rp.ctypes.data_as(C.POINTER(C.c_longlong)),
                                             ci.ctypes.data_as(C.POINTER(C.c_int)), _dptr(va)))
     return rp, ci, va, (nr.value, nc.value)
+
+
+def host_invert(a):
+    """Inverse of a square matrix by the host Gauss-Jordan elimination of the coarse level."""
+    a = np.ascontiguousarray(a, dtype=np.float64).copy()
+    _host_check(lib.stfem_host_invert(a.shape[0], _dptr(a)))
+    return a
 
 
 def host_temporal(k):

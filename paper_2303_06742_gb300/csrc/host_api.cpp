@@ -21,6 +21,18 @@ extern "C" {
 
 const char *stfem_host_last_error(void) { return g_host_err.c_str(); }
 
+int stfem_host_invert(int n, double *a) {
+  if (n < 1 || !a) {
+    g_host_err = "invalid arguments";
+    return STFEM_ERR_ARG;
+  }
+  if (!stfem::invert(a, n)) {
+    g_host_err = "zero pivot";
+    return STFEM_ERR_SINGULAR_PATCH;
+  }
+  return STFEM_OK;
+}
+
 int stfem_host_level_matrix(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
                             const stfem_bcs *bcs, double tau, int level, long long *n, long long *nnz,
                             long long *rowptr, int *col, double *val) {
