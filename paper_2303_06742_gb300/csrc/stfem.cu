@@ -1506,6 +1506,9 @@ struct DLevel {
   // tensor-core layout of the time-diagonal inverses (FP32 levels of
   // handles set up for several right-hand sides)
   int tc = 0, tc_nst = 0;
+  // ring shape of the streaming patch apply picked by autotune_stream (0: by
+  // dimension)
+  int tune_nst = 0, tune_cap = 0;
   uint32_t tc_cols = 0;
   long long *ptoff = nullptr;
   float *ptile = nullptr;
@@ -2399,7 +2402,11 @@ void stream_shape(const DLevel<T> &L, int q, int dim, int *threads, size_t *smem
   const int nwc = std::max(1, (rows + 31) / 32);
   *threads = 32 * (nwc + 1);
   *nst = dim == 2 ? 2 : STREAM_STAGES;
-  const int cap = dim == 2 ? 5 : 3;
+  int cap = dim == 2 ? 5 : 3;
+  if (L.tune_nst > 0) {
+    *nst = L.tune_nst;
+    cap = L.tune_cap;
+  }
   *smem = (size_t)stream_header(*nst) + (size_t)(q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
   const int per_sm = std::max(1, std::min(cap, (int)((227u * 1024u) / *smem)));
   *grid = (int)std::min<long>(L.npatch, 152L * per_sm);
@@ -2476,6 +2483,56 @@ int prepare_stream_kernels(stfem_h h) {
   CK(cudaFuncSetAttribute(k_patch_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  return 0;
+}
+
+// Autotuner of the streaming patch apply: times the candidate ring shapes
+// (stages per CTA x CTAs per SM) on the level's own inverses and keeps the
+// fastest.  The shape changes only how patches are spread over CTAs, never
+// the arithmetic of a patch, so results do not depend on the choice.
+template <typename T>
+int autotune_stream(stfem_h h, DLevel<T> &L) {
+  if (L.form != 1 || L.tc || L.npatch == 0) return 0;
+  static const int cand[][2] = {{2, 5}, {3, 4}, {4, 3}};
+  cudaStream_t ts = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStream_t saved = h->stream;
+  h->stream = ts;
+  cudaMemsetAsync(L.r, 0, (size_t)L.N * sizeof(T), ts);
+  float best = 1e30f;
+  int bn = 0, bc = 0;
+  for (const auto &c : cand) {
+    L.tune_nst = c[0];
+    L.tune_cap = c[1];
+    int threads, grid, nst;
+    size_t smem;
+    stream_shape(L, h->q, h->dim, &threads, &smem, &grid, &nst);
+    if (smem > 227u * 1024u) continue;
+    for (int w = 0; w < 2; ++w) launch_patch_apply_to<T>(h, L, L.r, L.ybuf);
+    cudaEventRecord(e0, ts);
+    for (int t = 0; t < 5; ++t) launch_patch_apply_to<T>(h, L, L.r, L.ybuf);
+    cudaEventRecord(e1, ts);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bn = c[0];
+      bc = c[1];
+    }
+  }
+  h->stream = saved;
+  L.tune_nst = bn;
+  L.tune_cap = bc;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
+  CK(e);
+  CK(cudaGetLastError());
   return 0;
 }
 
@@ -3552,6 +3609,13 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       if (dev_factor) CKR(factor_on_device(h, h->L64[l], h->hl[l], P, td));
     }
   }
+  for (int l = 1; l < h->nlev; ++l) {
+    if (mixed)
+      CKR(autotune_stream(h, h->L32[l]));
+    else
+      CKR(autotune_stream(h, h->L64[l]));
+  }
+  CKR(check_dev_err(h));
   std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
   const int n0 = (int)(h->hl[0].ns * h->q);
   if (!stfem::invert(A0.data(), n0)) {
