@@ -1,7 +1,8 @@
 // Batched time-diagonal patch apply on the 5th-generation tensor cores
 // (tcgen05, TF32 operands, FP32 accumulators in tensor memory), for nb <= 8
-// right-hand sides that share the patch inverses (Algorithm 4.1, line 6, with
-// A_P^{-1} in the time-diagonal form: y = (V (x) I) blockdiag(Z_a) (U (x) I) r).
+// right-hand sides that share the patch inverses: the local Vanka solves of
+// Algorithm 4.1 with A_P^{-1} in the time-diagonal form
+// y = (V (x) I) blockdiag(Z_a) (U (x) I) r.
 //
 // Included by stfem.cu after the bulk-copy / mbarrier helpers.
 //
