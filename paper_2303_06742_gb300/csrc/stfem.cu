@@ -2064,7 +2064,7 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
   D.form = P.form;
   D.maxCs = *std::max_element(P.cs.begin(), P.cs.end());
   CKR(upload(h, &D.pcs, P.cs));
-  D.inv_elems = (long long)P.inv.size();
+  D.inv_elems = (long long)P.inv_off.back(); // stored inverse entries (host- or device-factorised)
   D.sumC = (long long)P.dofs.size();
   // algorithmic bytes of one patch-apply launch: every inverse once (C_P^2
   // entries), the dof index, the gathered residual and the result per row
