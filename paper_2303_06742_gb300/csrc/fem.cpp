@@ -283,7 +283,7 @@ inline long nbr_pos(const NbrBox &nb, const int *a) {
 // Node-level matrix with a fixed number of values per entry.
 struct NodeMat {
   std::vector<long> rowptr;
-  std::vector<double> val; // nvals per entry
+  hvec<double> val; // nvals per entry
   int nvals = 1;
 };
 
@@ -297,7 +297,11 @@ NodeMat make_nodemat(const Lattice &row, const Lattice &colL, const Box &b, int 
     unflatten(i, row.dims, b.dim, a);
     M.rowptr[i + 1] = M.rowptr[i] + nbr_box(a, row.m, colL.m, b).size;
   }
-  M.val.assign(M.rowptr[row.nnodes] * nvals, 0.0);
+  const long nv = M.rowptr[row.nnodes] * nvals;
+  M.val.resize(nv);
+  double *v = M.val.data();
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < nv; ++i) v[i] = 0.0;
   return M;
 }
 
@@ -504,9 +508,26 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
   NodeMat UP = make_nodemat(L.U, L.P, b, d);         // C^T: C[s][(I,c)]
   NodeMat PU = make_nodemat(L.P, L.U, b, d);         // C[s][(J,c')]
   NodeMat PP = make_nodemat(L.P, L.P, b, 2);         // Mp, B
+  // cells in 2^d colour classes by the parity of their coordinates: cells of
+  // one class share no node, so a class is scattered in parallel
+  std::vector<std::vector<long>> colour(1 << d);
+  {
+    int cc[3];
+    for (long c = 0; c < b.ncell; ++c) {
+      unflatten(c, b.n, d, cc);
+      int k = 0;
+      for (int i = 0; i < d; ++i) k |= (cc[i] & 1) << i;
+      colour[k].push_back(c);
+    }
+  }
+  for (const std::vector<long> &cells : colour) {
+#pragma omp parallel
+  {
   std::vector<double> Ke(du * du), Ce(np * du), Be(np * np);
   int cm[3];
-  for (long c = 0; c < b.ncell; ++c) {
+#pragma omp for schedule(dynamic, 16)
+  for (long ci = 0; ci < (long)cells.size(); ++ci) {
+    const long c = cells[ci];
     unflatten(c, b.n, d, cm);
     const double lam = coef.lam[c], mu = coef.mu[c], kap = coef.kap[c];
     for (int i = 0; i < du * du; ++i) Ke[i] = lam * Klam[i] + mu * Kmu[i];
@@ -562,6 +583,8 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
       }
     }
   }
+  }
+  }
 
   // expand to the spatial system CSR (rows u-eq, v-eq, p-eq; cols V, U, P)
   const double rho = coef.rho, c0 = coef.c0;
@@ -580,9 +603,13 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
   for (long i = 0; i < ns; ++i) L.rowptr[i + 1] += L.rowptr[i];
   const long nnz = L.rowptr[ns];
   L.col.resize(nnz);
-  L.v1.assign(nnz, 0.0);
-  L.v2.assign(nnz, 0.0);
+  L.v1.resize(nnz);
+  L.v2.resize(nnz);
+  // rows are disjoint ranges of the CSR: threaded, and every entry of col, v1
+  // and v2 is written once here (the arrays start uninitialised)
+#pragma omp parallel for schedule(dynamic, 64)
   for (long I = 0; I < L.U.nnodes; ++I) {
+    int a[3];
     unflatten(I, L.U.dims, d, a);
     NbrBox nbu = nbr_box(a, r, r, b), nbp = nbr_box(a, r, r - 1, b);
     std::vector<long> Jn(nbu.size), Sn(nbp.size);
@@ -607,30 +634,37 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
       long e = L.rowptr[I * d + c];
       for (long j = 0; j < nbu.size; ++j, ++e) {
         L.col[e] = (int)(Jn[j] * d + c);
+        L.v1[e] = 0.0;
         L.v2[e] = -rho * uu[j * UU.nvals];
       }
       for (long j = 0; j < nbu.size; ++j, ++e) {
         L.col[e] = (int)(R + Jn[j] * d + c);
         L.v1[e] = rho * uu[j * UU.nvals];
+        L.v2[e] = 0.0;
       }
       // v-equation row: rho M on V (Dt), K on U (W), C^T on P (W)
       e = L.rowptr[R + I * d + c];
       for (long j = 0; j < nbu.size; ++j, ++e) {
         L.col[e] = (int)(Jn[j] * d + c);
         L.v1[e] = rho * uu[j * UU.nvals];
+        L.v2[e] = 0.0;
       }
       for (long j = 0; j < nbu.size; ++j)
         for (int cp = 0; cp < d; ++cp, ++e) {
           L.col[e] = (int)(R + Jn[j] * d + cp);
+          L.v1[e] = 0.0;
           L.v2[e] = uu[j * UU.nvals + 1 + c * d + cp];
         }
       for (long s = 0; s < nbp.size; ++s, ++e) {
         L.col[e] = (int)(2 * R + Sn[s]);
+        L.v1[e] = 0.0;
         L.v2[e] = up[s * d + c];
       }
     }
   }
+#pragma omp parallel for schedule(dynamic, 64)
   for (long s = 0; s < S; ++s) {
+    int a[3];
     unflatten(s, L.P.dims, d, a);
     NbrBox nbu = nbr_box(a, r - 1, r, b), nbp = nbr_box(a, r - 1, r - 1, b);
     long e = L.rowptr[2 * R + s];
@@ -644,6 +678,7 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
           long J = flatten(aj, L.U.dims);
           for (int cp = 0; cp < d; ++cp, ++e) {
             L.col[e] = (int)(J * d + cp);
+            L.v1[e] = 0.0;
             L.v2[e] = -pu[t * d + cp];
           }
         }
@@ -859,6 +894,7 @@ void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
   Cl->col.resize(Cl->rowptr[nsc]);
   Cl->v1.resize(Cl->rowptr[nsc]);
   Cl->v2.resize(Cl->rowptr[nsc]);
+#pragma omp parallel for schedule(dynamic, 256)
   for (long I = 0; I < nsc; ++I) {
     std::copy(ccol[I].begin(), ccol[I].end(), Cl->col.begin() + Cl->rowptr[I]);
     std::copy(cv1[I].begin(), cv1[I].end(), Cl->v1.begin() + Cl->rowptr[I]);

@@ -4,12 +4,32 @@
 // plus transfers, vertex patches, patch inverses and the coarse inverse.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <type_traits>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/stfem.h"
 
 namespace stfem {
+
+// Allocator whose value-less construct leaves the element uninitialised, so
+// that resize() of a large array costs no serial write: the threaded loop that
+// fills it touches its pages first.
+template <class T> struct uninit_alloc : std::allocator<T> {
+  template <class U> struct rebind {
+    using other = uninit_alloc<U>;
+  };
+  uninit_alloc() = default;
+  template <class U> uninit_alloc(const uninit_alloc<U> &) noexcept {}
+  template <class U> void construct(U *p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new ((void *)p) U;
+  }
+  template <class U, class... A> void construct(U *p, A &&...a) { ::new ((void *)p) U(std::forward<A>(a)...); }
+};
+template <class T> using hvec = std::vector<T, uninit_alloc<T>>;
 
 struct Rule {
   std::vector<double> x, w;
@@ -70,8 +90,9 @@ struct Level {
   Lattice U, P;
   long R = 0, S = 0, ns = 0;
   Coef coef;
-  std::vector<int> rowptr, col;
-  std::vector<double> v1, v2;
+  std::vector<int> rowptr;
+  hvec<int> col;
+  hvec<double> v1, v2;
   // per lattice node: spatial position, for initial values and loads
 };
 
