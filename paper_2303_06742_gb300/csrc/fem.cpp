@@ -796,19 +796,23 @@ void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
         tval[p] = pval[e];
       }
   }
-  // AP = S P_s (rows fine), two value arrays
-  std::vector<long> aptr(nsf + 1, 0);
-  std::vector<std::vector<int>> acol_t;
-  std::vector<std::vector<double>> a1_t, a2_t;
+  // AP = S P_s (rows fine), two value arrays.  Each worker appends the rows
+  // it builds to buffers of its own; a row is found by (worker, offset).
   const int nt = n_threads();
-  std::vector<std::vector<int>> rows_col(nsf);
-  std::vector<std::vector<double>> rows_v1(nsf), rows_v2(nsf);
+  struct RowBuf {
+    hvec<int> col;
+    hvec<double> v1, v2;
+  };
+  std::vector<RowBuf> apb(nt);
+  std::vector<int> ap_who(nsf), ap_len(nsf);
+  std::vector<long> ap_at(nsf);
   {
     std::atomic<long> next(0);
-    auto work = [&]() {
-      std::vector<double> acc1(nsc, 0.0), acc2(nsc, 0.0);
+    auto work = [&](int w) {
+      std::vector<double> acc(2 * nsc, 0.0); // (S1, S2) parts side by side
       std::vector<char> mark(nsc, 0);
       std::vector<int> touched;
+      RowBuf &o = apb[w];
       for (;;) {
         const long i0 = next.fetch_add(256);
         if (i0 >= nsf) break;
@@ -822,37 +826,40 @@ void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
               if (!mark[J]) {
                 mark[J] = 1;
                 touched.push_back(J);
-                acc1[J] = acc2[J] = 0.0;
+                acc[2 * J] = acc[2 * J + 1] = 0.0;
               }
-              acc1[J] += x1 * pval[f];
-              acc2[J] += x2 * pval[f];
+              acc[2 * J] += x1 * pval[f];
+              acc[2 * J + 1] += x2 * pval[f];
             }
           }
           std::sort(touched.begin(), touched.end());
-          rows_col[i] = touched;
-          rows_v1[i].resize(touched.size());
-          rows_v2[i].resize(touched.size());
-          for (size_t t = 0; t < touched.size(); ++t) {
-            rows_v1[i][t] = acc1[touched[t]];
-            rows_v2[i][t] = acc2[touched[t]];
-            mark[touched[t]] = 0;
+          ap_who[i] = w;
+          ap_at[i] = (long)o.col.size();
+          ap_len[i] = (int)touched.size();
+          for (const int J : touched) {
+            o.col.push_back(J);
+            o.v1.push_back(acc[2 * J]);
+            o.v2.push_back(acc[2 * J + 1]);
+            mark[J] = 0;
           }
         }
       }
     };
     std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(work);
+    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
     for (auto &t : th) t.join();
   }
-  // C = P_s^T AP (rows coarse)
-  std::vector<std::vector<int>> ccol(nsc);
-  std::vector<std::vector<double>> cv1(nsc), cv2(nsc);
+  // C = P_s^T AP (rows coarse), the same way
+  std::vector<RowBuf> cb(nt);
+  std::vector<int> c_who(nsc), c_len(nsc);
+  std::vector<long> c_at(nsc);
   {
     std::atomic<long> next(0);
-    auto work = [&]() {
-      std::vector<double> acc1(nsc, 0.0), acc2(nsc, 0.0);
+    auto work = [&](int w) {
+      std::vector<double> acc(2 * nsc, 0.0);
       std::vector<char> mark(nsc, 0);
       std::vector<int> touched;
+      RowBuf &o = cb[w];
       for (;;) {
         const long I0 = next.fetch_add(64);
         if (I0 >= nsc) break;
@@ -860,45 +867,50 @@ void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
           touched.clear();
           for (long e = tptr[I]; e < tptr[I + 1]; ++e) {
             const int i = tcol[e];
-            const double w = tval[e];
-            const std::vector<int> &rc = rows_col[i];
-            for (size_t t = 0; t < rc.size(); ++t) {
+            const double wgt = tval[e];
+            const RowBuf &a = apb[ap_who[i]];
+            const int *rc = a.col.data() + ap_at[i];
+            const double *r1 = a.v1.data() + ap_at[i], *r2 = a.v2.data() + ap_at[i];
+            for (int t = 0; t < ap_len[i]; ++t) {
               const int J = rc[t];
               if (!mark[J]) {
                 mark[J] = 1;
                 touched.push_back(J);
-                acc1[J] = acc2[J] = 0.0;
+                acc[2 * J] = acc[2 * J + 1] = 0.0;
               }
-              acc1[J] += w * rows_v1[i][t];
-              acc2[J] += w * rows_v2[i][t];
+              acc[2 * J] += wgt * r1[t];
+              acc[2 * J + 1] += wgt * r2[t];
             }
           }
           std::sort(touched.begin(), touched.end());
-          ccol[I] = touched;
-          cv1[I].resize(touched.size());
-          cv2[I].resize(touched.size());
-          for (size_t t = 0; t < touched.size(); ++t) {
-            cv1[I][t] = acc1[touched[t]];
-            cv2[I][t] = acc2[touched[t]];
-            mark[touched[t]] = 0;
+          c_who[I] = w;
+          c_at[I] = (long)o.col.size();
+          c_len[I] = (int)touched.size();
+          for (const int J : touched) {
+            o.col.push_back(J);
+            o.v1.push_back(acc[2 * J]);
+            o.v2.push_back(acc[2 * J + 1]);
+            mark[J] = 0;
           }
         }
       }
     };
     std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(work);
+    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
     for (auto &t : th) t.join();
   }
   Cl->rowptr.assign(nsc + 1, 0);
-  for (long I = 0; I < nsc; ++I) Cl->rowptr[I + 1] = Cl->rowptr[I] + (int)ccol[I].size();
+  for (long I = 0; I < nsc; ++I) Cl->rowptr[I + 1] = Cl->rowptr[I] + c_len[I];
   Cl->col.resize(Cl->rowptr[nsc]);
   Cl->v1.resize(Cl->rowptr[nsc]);
   Cl->v2.resize(Cl->rowptr[nsc]);
 #pragma omp parallel for schedule(dynamic, 256)
   for (long I = 0; I < nsc; ++I) {
-    std::copy(ccol[I].begin(), ccol[I].end(), Cl->col.begin() + Cl->rowptr[I]);
-    std::copy(cv1[I].begin(), cv1[I].end(), Cl->v1.begin() + Cl->rowptr[I]);
-    std::copy(cv2[I].begin(), cv2[I].end(), Cl->v2.begin() + Cl->rowptr[I]);
+    const RowBuf &a = cb[c_who[I]];
+    const long at = c_at[I], to = Cl->rowptr[I];
+    std::copy(a.col.begin() + at, a.col.begin() + at + c_len[I], Cl->col.begin() + to);
+    std::copy(a.v1.begin() + at, a.v1.begin() + at + c_len[I], Cl->v1.begin() + to);
+    std::copy(a.v2.begin() + at, a.v2.begin() + at + c_len[I], Cl->v2.begin() + to);
   }
 }
 
@@ -1479,12 +1491,12 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
   return 0;
 }
 
-void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, std::vector<double> *out,
+void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, hvec<double> *out,
                           std::vector<long long> *off) {
   (void)q;
   off->assign(p1 - p0 + 1, 0);
   for (long p = p0; p < p1; ++p) (*off)[p - p0 + 1] = (*off)[p - p0] + 2LL * P.cs[p] * P.cs[p];
-  out->assign((size_t)off->back(), 0.0);
+  out->resize((size_t)off->back()); // zeroed patch by patch by the workers
   std::atomic<long> next(p0);
   auto work = [&]() {
     std::vector<int> loc(L.ns, -1);
@@ -1496,6 +1508,7 @@ void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long
       const int *sp = P.dofs.data() + P.dof_off[p];
       for (int m = 0; m < Cs; ++m) loc[sp[m]] = m;
       double *S1 = out->data() + (*off)[p - p0], *S2 = S1 + (size_t)Cs * Cs;
+      std::fill(S1, S1 + 2 * (size_t)Cs * Cs, 0.0);
       for (int m = 0; m < Cs; ++m) {
         const int g = sp[m];
         for (int e = L.rowptr[g]; e < L.rowptr[g + 1]; ++e) {

@@ -155,7 +155,7 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
 // after S1) of patches p0 .. p1-1 of a level whose dof lists P holds (built
 // with invert_them = false), for inversion on the device; off[p - p0] is
 // the offset of patch p's S1 in out.  Threaded.
-void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, std::vector<double> *out,
+void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, hvec<double> *out,
                           std::vector<long long> *off);
 
 // Dense row-major slab matrix of a level (for the coarse solve).

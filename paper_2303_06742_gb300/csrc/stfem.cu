@@ -23,6 +23,7 @@
 #include <string>
 #include <type_traits>
 #include <climits>
+#include <future>
 #include <vector>
 
 using namespace stfem_dev;
@@ -2179,16 +2180,23 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
     cudaMemcpy(lam, lamh.data(), lamh.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(bad, &none, sizeof(long long), cudaMemcpyHostToDevice);
     size_t cap_blocks = 0, cap_off = 0;
-    std::vector<double> hb;
+    stfem::hvec<double> hb;
     std::vector<long long> ho;
-    for (long p0 = 0; p0 < P.npatch && rc == 0;) {
-      long p1 = p0;
+    // batches of at most `limit` bytes of blocks; the host extracts batch
+    // b + 1 while the device factorises batch b (the host buffers are free
+    // once their copy has landed; the device buffers once the kernel is done)
+    auto batch_end = [&](long b0) {
+      long b1 = b0;
       long long bytes = 0;
-      while (p1 < P.npatch && (p1 == p0 || bytes + 16LL * P.cs[p1] * P.cs[p1] <= limit)) {
-        bytes += 16LL * P.cs[p1] * P.cs[p1];
-        ++p1;
+      while (b1 < P.npatch && (b1 == b0 || bytes + 16LL * P.cs[b1] * P.cs[b1] <= limit)) {
+        bytes += 16LL * P.cs[b1] * P.cs[b1];
+        ++b1;
       }
-      stfem::extract_patch_blocks(L, P, h->q, p0, p1, &hb, &ho);
+      return b1;
+    };
+    long p0 = 0, p1 = batch_end(0);
+    if (P.npatch > 0) stfem::extract_patch_blocks(L, P, h->q, p0, p1, &hb, &ho);
+    while (p0 < P.npatch && rc == 0) {
       if (hb.size() > cap_blocks) {
         if (blocks) cudaFree(blocks);
         blocks = nullptr;
@@ -2211,7 +2219,8 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
       }
       // cudaMemcpy from pageable memory may return before its DMA has landed;
       // it is ordered only with the legacy stream, so wait there before the
-      // factorisation stream reads the batch (and the earlier uploads)
+      // factorisation stream reads the batch (and the earlier uploads), and
+      // before the host buffer is refilled
       if (cudaMemcpy(blocks, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
           cudaMemcpy(boff, ho.data(), ho.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
           cudaStreamSynchronize(0) != cudaSuccess) {
@@ -2227,12 +2236,16 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
       }
       k_patch_factor<T><<<(int)std::min<long>(grid, items), PF_THREADS, 0, fs>>>(
           p0, p1 - p0, td.nr, td.nc, lam, D.pcs, boff, blocks, D.pioff, D.pinv, scratch, scr_stride, bad, next);
-      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(fs) != cudaSuccess) {
+      const bool launched = cudaGetLastError() == cudaSuccess;
+      const long q0 = p1, q1 = q0 < P.npatch ? batch_end(q0) : q0;
+      if (launched && q0 < P.npatch) stfem::extract_patch_blocks(L, P, h->q, q0, q1, &hb, &ho);
+      if (!launched || cudaStreamSynchronize(fs) != cudaSuccess) {
         h->err = "device factorisation kernel failed";
         rc = STFEM_ERR_CUDA;
         break;
       }
-      p0 = p1;
+      p0 = q0;
+      p1 = q1;
     }
     if (rc == 0) {
       long long b = none;
@@ -3585,6 +3598,15 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       return STFEM_ERR_STATE;
     }
   }
+  // the coarse inverse (host, FP64) is computed while the patches are set up
+  // (host extraction, device factorisation); nothing writes level 0 meanwhile,
+  // and an early return waits for it in the future's destructor
+  const int n0 = (int)(h->hl[0].ns * h->q);
+  std::vector<double> A0;
+  std::future<bool> coarse = std::async(std::launch::async, [&]() {
+    A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
+    return stfem::invert(A0.data(), n0);
+  });
   // time-diagonal inverses are factorised on the device unless asked otherwise
   const bool dev_factor = form == STFEM_PATCH_TIME_DIAGONAL && !p->factor_host;
   for (int l = 1; l < h->nlev; ++l) {
@@ -3616,9 +3638,7 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       CKR(autotune_stream(h, h->L64[l]));
   }
   CKR(check_dev_err(h));
-  std::vector<double> A0 = stfem::dense_slab(h->hl[0], h->T, h->tau);
-  const int n0 = (int)(h->hl[0].ns * h->q);
-  if (!stfem::invert(A0.data(), n0)) {
+  if (!coarse.get()) {
     h->err = "singular coarse matrix";
     return STFEM_ERR_SINGULAR_PATCH;
   }
