@@ -56,12 +56,14 @@ def parse():
     p.add_argument("--rhs", type=int, default=1,
                    help="right-hand sides solved together (marches from t0 = 0, 0.1, ...): >1 times the "
                         "batched path with the tensor-core patch apply")
+    p.add_argument("--form", default="3.1", choices=["3.1", "B.1"],
+                   help="slab problem: Problem 3.1 (default) or Problem B.1 of Appendix B")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_leg(workload, out_path, mode, steps=0, warmup=0):
+def oracle_leg(workload, out_path, mode, steps=0, warmup=0, form="3.1"):
     """Runs the oracle (test infrastructure) in this process on the host cores.
 
     mode "solve": set up, time one full slab solve (slab 0), save the solution.
@@ -75,7 +77,7 @@ def oracle_leg(workload, out_path, mode, steps=0, warmup=0):
     from oracle.slab import repeat_state
     c = inputs.case(workload)
     t0 = time.perf_counter()
-    O = oracle_instance(c)
+    O = oracle_instance(c, form=form)
     t_setup = time.perf_counter() - t0
     st0 = O.initial_state()
     b = O.rhs(0, st0)
@@ -98,7 +100,7 @@ def oracle_leg(workload, out_path, mode, steps=0, warmup=0):
         json.dump(res, f)
 
 
-def run_oracle_subprocess(workload, mode, steps=0, warmup=0):
+def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1"):
     fd, path = tempfile.mkstemp(suffix=".json")
     os.close(fd)
     env = dict(os.environ)
@@ -106,7 +108,8 @@ def run_oracle_subprocess(workload, mode, steps=0, warmup=0):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", path, "--workload", workload,
-           "--steps", str(steps), "--warmup", str(warmup), "--impl", "reference" if mode == "reference" else "ours"]
+           "--steps", str(steps), "--warmup", str(warmup), "--impl", "reference" if mode == "reference" else "ours",
+           "--form", form]
     subprocess.run(cmd, check=True, env=env)
     with open(path) as f:
         res = json.load(f)
@@ -232,11 +235,12 @@ def pct(vals, q):
 
 
 # ------------------------------------------------------------------ GPU arm
-def make_solver(c, precision, stream, sweeps=1):
+def make_solver(c, precision, stream, sweeps=1, form="3.1"):
     import paper_2303_06742_gb300 as st
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from _cases import gpu_problem
-    return st.Solver(gpu_problem(c), precision=precision, stream=stream, n_sweeps=sweeps)
+    f = st.FORM_PROBLEM_B_1 if form == "B.1" else st.FORM_PROBLEM_3_1
+    return st.Solver(gpu_problem(c, form=f), precision=precision, stream=stream, n_sweeps=sweeps)
 
 
 def time_march(S, torch, stream, state, first, steps, tol, profile=False):
@@ -278,7 +282,7 @@ def gpu_arm(args):
 
     # ---- mixed precision (headline)
     t0 = time.perf_counter()
-    S = make_solver(c, st.MIXED, stream, args.sweeps)
+    S = make_solver(c, st.MIXED, stream, args.sweeps, args.form)
     setup_s = time.perf_counter() - t0
     state = torch.zeros(S.n_state, dtype=torch.float64, device="cuda")
     S.initial_state(state)
@@ -348,7 +352,7 @@ def gpu_arm(args):
     fp64 = None
     if not args.no_fp64:
         t0 = time.perf_counter()
-        S64 = make_solver(c, st.FP64, stream, args.sweeps)
+        S64 = make_solver(c, st.FP64, stream, args.sweeps, args.form)
         setup64 = time.perf_counter() - t0
         st64 = torch.zeros(S64.n_state, dtype=torch.float64, device="cuda")
         S64.initial_state(st64)
@@ -382,7 +386,7 @@ def gpu_arm(args):
     cpu = None
     err_vs_oracle = None
     if not args.no_cpu_baseline:
-        res, sol = run_oracle_subprocess(args.workload, "solve")
+        res, sol = run_oracle_subprocess(args.workload, "solve", form=args.form)
         cpu = {"value": 1.0 / res["solve_s"], "unit": "slab solves/s", "cores": 1, "kind": "oracle",
                "sample": "one full slab solve (slab 0, FGMRES-GMG to %g, %d iterations) of the same workload; "
                          "oracle setup (%.1f s) excluded as on the GPU" % (tol, res["iters"], res["setup_s"])}
@@ -406,6 +410,7 @@ def gpu_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload),
                    "precision": "FP32 V-cycle inside FP64 FGMRES",
+                   "form": "Problem %s" % args.form,
                    "tol": tol, "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
                    "l2": "inputs larger than L2: %.2f GB of FP32 patch inverses streamed per sweep set"
                          % (sum(v["inv_bytes"] for v in info.values()) / 1e9),
@@ -433,7 +438,8 @@ def reference_arm(args):
         return
     import inputs
     c = inputs.case(args.workload)
-    res, _ = run_oracle_subprocess(args.workload, "reference", steps=args.steps, warmup=args.warmup)
+    res, _ = run_oracle_subprocess(args.workload, "reference", steps=args.steps, warmup=args.warmup,
+                                   form=args.form)
     per_iter = res["per_iter_s"]
     iters = res["iters"]
     t_slab = statistics.mean(per_iter) * iters
@@ -456,6 +462,7 @@ def reference_arm(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "precision": "FP64 (oracle)",
+                   "form": "Problem %s" % args.form,
                    "tol": c["tol"]},
         "cpu_baseline": {"value": value, "unit": "slab solves/s", "cores": 1, "kind": "oracle",
                          "sample": "each step: 2 FGMRES-GMG iterations of slab 0, scaled by the %d iterations "
@@ -716,7 +723,7 @@ def main():
         return
     if args.cpu_leg:
         oracle_leg(args.workload, args.cpu_leg, "reference" if args.impl == "reference" else "solve",
-                   args.steps, args.warmup)
+                   args.steps, args.warmup, args.form)
         return
     if args.impl == "reference":
         reference_arm(args)

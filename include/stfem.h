@@ -82,11 +82,25 @@ typedef struct {
   int coarse_op;    /* STFEM_COARSE_GALERKIN (default) or STFEM_COARSE_REDISCRETIZE */
 } stfem_mesh;
 
+/* The discrete slab problem (the pressure equation differs):
+ * PROBLEM_3_1: Problem 3.1 (Eq. 3.5c tests -C(v, psi): the pressure row couples
+ *   -C to V with the time mass W).
+ * PROBLEM_B_1: Problem B.1 of Appendix B (tests -C(d_t u, psi) and adds the
+ *   jump of alpha div u, less its normal trace on Gamma_D^u, at t_{n-1}: the
+ *   pressure row couples -C to U through Dt).  Its previous-slab coupling takes
+ *   the volume part -alpha <div u^-, xi> alone plus the data term
+ *   -alpha <u_D(t_{n-1}) . n, xi>_{Gamma_D^u}, which is zero for every built-in
+ *   problem (all have homogeneous traces). */
+#define STFEM_FORM_PROBLEM_3_1 0
+#define STFEM_FORM_PROBLEM_B_1 1
+
 /* r: displacement degree (Q_r^d / Q_{r-1} Taylor-Hood, r >= 2, Eq. 2.5);
- * k: temporal degree of dG(k) (k+1 right Gauss-Radau nodes, Eq. 2.4), 0..4. */
+ * k: temporal degree of dG(k) (k+1 right Gauss-Radau nodes, Eq. 2.4), 0..4;
+ * form: STFEM_FORM_PROBLEM_3_1 (0, default) or STFEM_FORM_PROBLEM_B_1. */
 typedef struct {
   int r;
   int k;
+  int form;
 } stfem_degrees;
 
 /* Coefficients of Eq. 1.1 with isotropic C (lambda, mu) and K = kappa I.

@@ -218,7 +218,7 @@ class Hierarchy:
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material_fine, bc_u, bc_p, tau,
                  omega=0.7, nsweeps=1, support=True, hf="measure", coarse="galerkin",
-                 patches="vertex", averaging=True):
+                 patches="vertex", averaging=True, form="3.1"):
         self.temporal = Temporal(k)
         self.omega, self.nsweeps = omega, nsweeps
         self.averaging = averaging
@@ -231,7 +231,7 @@ class Hierarchy:
         self.levels = []
         for mesh, mat in zip(meshes, mats):
             ops = SpatialOps(mesh, r, mat, bc_u, bc_p)
-            A = slab_matrix(ops, self.temporal, tau)
+            A = slab_matrix(ops, self.temporal, tau, form)
             self.levels.append(Level(ops, A, self.temporal, support, patches))
         self.P = [None] + [slab_prolongation(self.levels[l - 1].ops, self.levels[l].ops,
                                              self.temporal) for l in range(1, n_levels)]

@@ -10,12 +10,24 @@ chi-hat the reference basis:
   (independent of tau, because d/dt = (2/tau) d/dt-hat);
 * Q_n(chi_a chi_b) = (tau/2) w-hat_b delta_ab =: W[b] delta_ab.
 
+Two slab problems (``form``):
+
+* ``"3.1"`` (default): the main-text Problem 3.1, whose pressure equation
+  (Eq. 3.5c) tests -C(v, psi); its row couples -C to the V column with the
+  time mass W.
+* ``"B.1"``: Problem B.1 of Appendix B, whose pressure equation tests
+  -C(d_t u, psi) and adds the jump of alpha div u (minus its normal trace on
+  Gamma_D^u) at t_{n-1}.  The time derivative and that jump combine into
+  Dt, so the row couples -C to the U column with Dt: S1 gains -C and S2
+  loses it.  Its previous-slab coupling is c0 Mp P^- + alpha <div u^-, xi>
+  - alpha <u_D(t_{n-1}) . n, xi>_{Gamma_D^u}, i.e. -Cvol U^- with the
+  volume part of C alone, and the boundary term takes the data u_D, not u^-.
+
 Readings:
 
-* Which slab problem: the main-text Problem 3.1 (v-coupled pressure
-  equation), whose pressure row couples -C to the V column.  The printed
-  block matrix (4.7) places -C under the U column, which matches neither
-  Problem 3.1 nor Problem B.1 literally.
+* The printed block matrix (4.7) places -C under the U column; its printed
+  C_{a,b} (Eq. 4.8) has the time mass of Problem 3.1.  Each form here is
+  derived from its own weak form instead.
 * Index convention: rows are test functions (time node b, space index i),
   columns trial functions (time node a, space index j), derived from the
   weak form; the block layout and the multiplication of Eq. 3.1a by rho
@@ -53,18 +65,34 @@ class Temporal:
         return v
 
 
-def spatial_blocks(ops):
+FORMS = ("3.1", "B.1")
+
+
+def _check_form(form):
+    if form not in FORMS:
+        raise ValueError("form must be one of %s" % (FORMS,))
+
+
+def spatial_blocks(ops, form="3.1"):
     """S1 (multiplies Dt) and S2 (multiplies W) as n_s x n_s block matrices.
 
-    Rows (u-eq, v-eq, p-eq), columns (V, U, P):
+    Rows (u-eq, v-eq, p-eq), columns (V, U, P).  Problem 3.1:
       S1 = [[0, rho M, 0], [rho M, 0, 0], [0, 0, c0 Mp]]
       S2 = [[-rho M, 0, 0], [0, K, C^T], [-C, 0, B]]
+    Problem B.1: S1 = [[0, rho M, 0], [rho M, 0, 0], [0, -C, c0 Mp]],
+      S2 = [[-rho M, 0, 0], [0, K, C^T], [0, 0, B]].
     """
+    _check_form(form)
     rho, c0 = ops.mat.rho, ops.mat.c0
     M, Mp, K, C, B = ops.M, ops.Mp, ops.K, ops.C, ops.B
-    S1 = sp.bmat([[None, rho * M, None], [rho * M, None, None], [None, None, c0 * Mp]],
-                 format="csr")
-    S2 = sp.bmat([[-rho * M, None, None], [None, K, C.T], [-C, None, B]], format="csr")
+    if form == "3.1":
+        S1 = sp.bmat([[None, rho * M, None], [rho * M, None, None], [None, None, c0 * Mp]],
+                     format="csr")
+        S2 = sp.bmat([[-rho * M, None, None], [None, K, C.T], [-C, None, B]], format="csr")
+    else:
+        S1 = sp.bmat([[None, rho * M, None], [rho * M, None, None], [None, -C, c0 * Mp]],
+                     format="csr")
+        S2 = sp.bmat([[-rho * M, None, None], [None, K, C.T], [None, None, B]], format="csr")
     # keep the zero blocks of the right shape
     n = ops.n_s
     S1 = sp.csr_matrix(S1, shape=(n, n))
@@ -72,17 +100,19 @@ def spatial_blocks(ops):
     return S1, S2
 
 
-def slab_matrix(ops, temporal, tau):
+def slab_matrix(ops, temporal, tau, form="3.1"):
     """A_n = Dt (x) S1 + diag(W) (x) S2 in the paper's ordering (Eqs. 4.6-4.7)."""
-    S1, S2 = spatial_blocks(ops)
+    S1, S2 = spatial_blocks(ops, form)
     A = sp.kron(sp.csr_matrix(temporal.Dt), S1) + sp.kron(sp.diags(temporal.W(tau)), S2)
     return A.tocsr()
 
 
-def slab_matrix_direct(ops, temporal, tau, nqt=None):
+def slab_matrix_direct(ops, temporal, tau, nqt=None, form="3.1"):
     """The same matrix assembled block by block from the time integrals of
-    Eq. 3.5, using an independent Gauss rule in time (exact for the
-    polynomial integrands), for checking the Kronecker form."""
+    Eq. 3.5 (Problem B.1: of its pressure equation), using an independent
+    Gauss rule in time (exact for the polynomial integrands), for checking
+    the Kronecker form."""
+    _check_form(form)
     q = temporal.q
     nqt = nqt or (temporal.k + 2)
     x, w = gauss_legendre(nqt)
@@ -96,22 +126,29 @@ def slab_matrix_direct(ops, temporal, tau, nqt=None):
             # int_{I_n} chi_a' chi_b dt = sum w chi-hat_a' chi-hat_b (tau/2 * 2/tau)
             d_ab = np.sum(w * dchi[:, a] * chi[:, b]) + temporal.chi_m1[a] * temporal.chi_m1[b]
             m_ab = 0.5 * tau * np.sum(w * chi[:, a] * chi[:, b])
+            if form == "3.1":  # Q_n(-C(v, psi))
+                p_v, p_u = -m_ab * C, None
+            else:  # Q_n(-C(d_t u, psi)) plus the jump of -C(u, psi) at t_{n-1}
+                p_v, p_u = None, -d_ab * C
             blk = sp.bmat([
                 [-rho * m_ab * M, rho * d_ab * M, None],
                 [rho * d_ab * M, m_ab * K, m_ab * C.T],
-                [-m_ab * C, None, c0 * d_ab * Mp + m_ab * B]], format="csr")
+                [p_v, p_u, c0 * d_ab * Mp + m_ab * B]], format="csr")
             blocks[b][a] = sp.csr_matrix(blk, shape=(2 * R + S, 2 * R + S))
     return sp.bmat(blocks, format="csr")
 
 
-def slab_rhs(ops, temporal, tau, t_prev, prob, prev):
+def slab_rhs(ops, temporal, tau, t_prev, prob, prev, form="3.1"):
     """F_n of Eq. 4.5: Radau-quadrature loads plus the coupling to the
     previous slab's end state ``prev`` = (V, U, P) at t_{n-1} (Eq. 3.5).
 
     u-eq (multiplied by rho): rho chi_b(-1) M U^-
     v-eq: (tau/2) w_b F(t_b) + rho chi_b(-1) M V^-
-    p-eq: (tau/2) w_b G(t_b) + c0 chi_b(-1) Mp P^-
+    p-eq: (tau/2) w_b G(t_b) + c0 chi_b(-1) Mp P^-                  (3.1)
+          (tau/2) w_b G(t_b) + chi_b(-1) (c0 Mp P^- - Cvol U^-
+                  - alpha <u_D(t_{n-1}) . n, xi>_{Gamma_D^u})        (B.1)
     """
+    _check_form(form)
     R, S, n_s = ops.R, ops.S, ops.n_s
     Vm, Um, Pm = prev
     rho, c0 = ops.mat.rho, ops.mat.c0
@@ -119,6 +156,9 @@ def slab_rhs(ops, temporal, tau, t_prev, prob, prev):
     MU = ops.M @ Um
     MV = ops.M @ Vm
     MP = ops.Mp @ Pm
+    if form == "B.1":  # the whole pressure coupling, multiplied by chi_b(-1) below
+        MP = c0 * MP - ops.Cvol @ Um - ops.normal_trace_load(prob, t_prev)
+        c0 = 1.0
     out = np.zeros(temporal.q * n_s)
     for b in range(temporal.q):
         tb = t_prev + 0.5 * tau * (temporal.t[b] + 1.0)

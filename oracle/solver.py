@@ -18,9 +18,11 @@ class Instance:
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
                  problem, t0=0.0, omega=0.7, nsweeps=1, support=True, hf="measure",
-                 coarse="galerkin", patches="vertex", averaging=True, absolute=False):
+                 coarse="galerkin", patches="vertex", averaging=True, absolute=False,
+                 form="3.1"):
         self.h = Hierarchy(dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
-                           omega, nsweeps, support, hf, coarse, patches, averaging)
+                           omega, nsweeps, support, hf, coarse, patches, averaging, form)
+        self.form = form
         self.absolute = absolute
         self.prob, self.tau, self.t0 = problem, tau, t0
         self.tmp = self.h.temporal
@@ -33,7 +35,7 @@ class Instance:
     def rhs(self, n, prev):
         """F_n for slab n = 0, 1, ... given the previous end state."""
         t_prev = self.t0 + n * self.tau
-        return slab_rhs(self.ops, self.tmp, self.tau, t_prev, self.prob, prev)
+        return slab_rhs(self.ops, self.tmp, self.tau, t_prev, self.prob, prev, self.form)
 
     def solve(self, b, x0, tol, restart=30, max_it=500):
         return fgmres(lambda x: self.A @ x, b, x0, self.h.vcycle, tol, restart, max_it, self.absolute)

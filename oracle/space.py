@@ -216,6 +216,8 @@ class SpatialOps:
     Mp  : scalar Q_{r-1} mass
     K   : A_gamma(psi_j, psi_i) incl. Nitsche terms, R x R, R = d * nu
     C   : C(psi_j, xi_s) stored as C[s, j], S x R
+    Cvol: its volume part -alpha <div psi_j, xi_s> alone (the previous-slab
+          coupling of Problem B.1 needs it)
     B   : B_gamma(xi_s, xi_r) incl. Nitsche terms, S x S
     Row index = test function, column index = trial function.
     """
@@ -257,7 +259,7 @@ class SpatialOps:
         return P
 
     def _elem_u(self, lam, mu, faces_D):
-        """Element K, C, Mu for one cell (shared geometry; per-cell lam, mu)."""
+        """Element K, C, Cvol, Mu for one cell (shared geometry; per-cell lam, mu)."""
         mesh, d = self.mesh, self.d
         X, w = cell_rule(d, self.nq)
         w = w * mesh.vol
@@ -271,6 +273,7 @@ class SpatialOps:
         K = np.einsum("q,qjab,qiab->ij", w, sig, eps)
         div = np.trace(G, axis1=2, axis2=3)
         C = -self.mat.alpha * np.einsum("q,qs,qj->sj", w, psi, div)
+        Cvol = C.copy()
         Mu = np.einsum("q,qi,qj->ij", w, phi, phi)
         for ax, side, fid in faces_D:
             Xf, wf = face_rule(d, self.nq, ax, side)
@@ -292,7 +295,7 @@ class SpatialOps:
             K += (self.gamma_a / mesh.hF) * np.einsum("q,qja,qia->ij", wf, Pv, Pv)
             pn = np.einsum("qja,a->qj", Pv, n)
             C += self.mat.alpha * np.einsum("q,qs,qj->sj", wf, ps, pn)
-        return K, C, Mu
+        return K, C, Cvol, Mu
 
     def _elem_p(self, kappa, faces_D):
         mesh, d = self.mesh, self.d
@@ -318,7 +321,7 @@ class SpatialOps:
     def _assemble(self):
         mesh, d = self.mesh, self.d
         cache_u, cache_p = {}, {}
-        rows = {k: [] for k in ("K", "C", "Mu", "B", "Mp")}
+        rows = {k: [] for k in ("K", "C", "Cvol", "Mu", "B", "Mp")}
         cols = {k: [] for k in rows}
         vals = {k: [] for k in rows}
 
@@ -339,17 +342,19 @@ class SpatialOps:
             kp = (kap, fp)
             if kp not in cache_p:
                 cache_p[kp] = self._elem_p(kap, fp)
-            K, C, Mu = cache_u[ku]
+            K, C, Cvol, Mu = cache_u[ku]
             B, Mp = cache_p[kp]
             un = self.Vs.cell_nodes(cm)
             pn = self.Qs.cell_nodes(cm)
             uvec = np.array([i * d + cc for i in un for cc in range(d)], int)
             add("K", uvec, uvec, K)
             add("C", pn, uvec, C)
+            add("Cvol", pn, uvec, Cvol)
             add("Mu", un, un, Mu)
             add("B", pn, pn, B)
             add("Mp", pn, pn, Mp)
-        shapes = {"K": (self.R, self.R), "C": (self.S, self.R), "Mu": (self.nu, self.nu),
+        shapes = {"K": (self.R, self.R), "C": (self.S, self.R), "Cvol": (self.S, self.R),
+                  "Mu": (self.nu, self.nu),
                   "B": (self.S, self.S), "Mp": (self.S, self.S)}
         for key in rows:
             M = sp.coo_matrix((np.concatenate(vals[key]), (np.concatenate(rows[key]),
@@ -426,3 +431,26 @@ class SpatialOps:
                     G[pn] += -np.einsum("q,q,qs->s", wf, pD, dn)
                     G[pn] += (self.gamma_b / mesh.hF) * np.einsum("q,q,qs->s", wf, pD, ps)
         return F, G
+
+    def normal_trace_load(self, prob, t):
+        """alpha <u_D(t) . n, xi_r> over the Dirichlet faces of u: the data term
+        of the previous-slab coupling in the pressure equation of Problem B.1
+        (zero when the exact solution vanishes on the boundary)."""
+        out = np.zeros(self.S)
+        if prob is None or prob.zero_trace:
+            return out
+        mesh, d = self.mesh, self.d
+        for c, cm in mesh.cells():
+            x0 = mesh.lo + mesh.h * np.array(cm)
+            pn = self.Qs.cell_nodes(cm)
+            for ax, side, fid in boundary_faces(mesh, cm):
+                if self.bc_u[fid] != DIRICHLET:
+                    continue
+                Xf, wf = face_rule(d, self.nq, ax, side)
+                wf = wf * (mesh.vol / mesh.h[ax])
+                ps, _ = self.Qs.basis(Xf)
+                n = np.zeros(d)
+                n[ax] = 1.0 if side == 1 else -1.0
+                uD = prob.u(x0[None, :] + Xf * mesh.h[None, :], t)
+                out[pn] += self.mat.alpha * np.einsum("q,q,qr->r", wf, uD @ n, ps)
+        return out

@@ -397,8 +397,9 @@ std::vector<std::array<double, 3>> face_points(const Box &b, int nq, int ax, int
 
 } // namespace
 
-Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
+Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int form) {
   Level L;
+  L.form = form;
   L.box = b;
   L.r = r;
   L.coef = coef;
@@ -508,6 +509,9 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
   NodeMat UP = make_nodemat(L.U, L.P, b, d);         // C^T: C[s][(I,c)]
   NodeMat PU = make_nodemat(L.P, L.U, b, d);         // C[s][(J,c')]
   NodeMat PP = make_nodemat(L.P, L.P, b, 2);         // Mp, B
+  const bool b1 = form == STFEM_FORM_PROBLEM_B_1;
+  NodeMat PUv; // volume part of C (Problem B.1 only)
+  if (b1) PUv = make_nodemat(L.P, L.U, b, d);
   // cells in 2^d colour classes by the parity of their coordinates: cells of
   // one class share no node, so a class is scattered in parallel
   std::vector<std::vector<long>> colour(1 << d);
@@ -575,6 +579,8 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
       for (int j = 0; j < nu; ++j) {
         long e = PU.rowptr[gip[s]] + nbr_pos(nbu, gu_[j]);
         for (int cp = 0; cp < d; ++cp) PU.val[e * d + cp] += Ce[s * du + j * d + cp];
+        if (b1)
+          for (int cp = 0; cp < d; ++cp) PUv.val[e * d + cp] += Cv[s * du + j * d + cp];
       }
       for (int t = 0; t < np; ++t) {
         long e = PP.rowptr[gip[s]] + nbr_pos(nbp, gp_[t]);
@@ -677,9 +683,15 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
           int aj[3] = {nbu.lo[0] + x, nbu.lo[1] + y, nbu.lo[2] + z};
           long J = flatten(aj, L.U.dims);
           for (int cp = 0; cp < d; ++cp, ++e) {
-            L.col[e] = (int)(J * d + cp);
-            L.v1[e] = 0.0;
-            L.v2[e] = -pu[t * d + cp];
+            if (b1) { // -C on U through Dt (Problem B.1)
+              L.col[e] = (int)(R + J * d + cp);
+              L.v1[e] = -pu[t * d + cp];
+              L.v2[e] = 0.0;
+            } else { // -C on V through W (Problem 3.1)
+              L.col[e] = (int)(J * d + cp);
+              L.v1[e] = 0.0;
+              L.v2[e] = -pu[t * d + cp];
+            }
           }
         }
     t = 0;
@@ -691,6 +703,10 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc) {
           L.v1[e] = c0 * pp[t * 2 + 0];
           L.v2[e] = pp[t * 2 + 1];
         }
+  }
+  if (b1) {
+    L.cvol.resize(PUv.val.size());
+    for (size_t i = 0; i < PUv.val.size(); ++i) L.cvol[i] = -PUv.val[i];
   }
   return L;
 }
@@ -1568,6 +1584,10 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
     *err = "invalid coarse_op";
     return STFEM_ERR_ARG;
   }
+  if (deg->form != STFEM_FORM_PROBLEM_3_1 && deg->form != STFEM_FORM_PROBLEM_B_1) {
+    *err = "invalid form";
+    return STFEM_ERR_ARG;
+  }
   for (int i = 0; i < d; ++i) {
     if (mesh->n_cells[i] < 1 || (mesh->n_cells[i] % (1 << (mesh->n_levels - 1))) != 0 ||
         !(mesh->hi[i] > mesh->lo[i])) {
@@ -1628,6 +1648,7 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
       Level &Lv = (*levels)[l];
       Lv.box = boxes[l];
       Lv.r = deg->r;
+      Lv.form = deg->form;
       Lv.coef = coefs[l];
       Lv.U = make_lattice(boxes[l], deg->r);
       Lv.P = make_lattice(boxes[l], deg->r - 1);
@@ -1635,7 +1656,7 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
       Lv.S = Lv.P.nnodes;
       Lv.ns = 2 * Lv.R + Lv.S;
     } else {
-      (*levels)[l] = assemble_level(boxes[l], deg->r, coefs[l], bc);
+      (*levels)[l] = assemble_level(boxes[l], deg->r, coefs[l], bc, deg->form);
     }
   }
   Pu->assign(nlev, CSR());

@@ -93,10 +93,17 @@ struct Level {
   std::vector<int> rowptr;
   hvec<int> col;
   hvec<double> v1, v2;
+  // STFEM_FORM_PROBLEM_3_1: the p-equation couples -C to V (in v2);
+  // STFEM_FORM_PROBLEM_B_1: to U (in v1).  For B.1 an assembled level also
+  // keeps -Cvol, the volume part of the same coupling, per pressure node over
+  // its displacement neighbour box (d values per neighbour, the order of the
+  // p-rows' entries): the previous-slab coupling of Problem B.1 uses it.
+  int form = 0;
+  std::vector<double> cvol;
   // per lattice node: spatial position, for initial values and loads
 };
 
-Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc);
+Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc, int form = 0);
 
 // Scalar interpolation coarse Q_m -> fine Q_m (fine rows), CSR.
 struct CSR {

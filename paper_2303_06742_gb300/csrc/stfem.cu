@@ -69,12 +69,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 //   v-eq_b[I,c] = sum_a Dt[b,a] (Mr V_a)[I,c] + W_b ((K U_b)[I,c] + (Ct P_b)[I,c])
 // and for a pressure node s
 //   p-eq_b[s]   = sum_a Dt[b,a] (Mp0 P_a)[s] + W_b ((B P_b)[s] + (Cn V_b)[s])
+// (Problem 3.1), or with Problem B.1 (pcouple = 1)
+//   p-eq_b[s]   = sum_a Dt[b,a] ((Mp0 P_a)[s] + (Cn U_a)[s]) + W_b (B P_b)[s]
 // with Mr = rho M (scalar), K (d x d per pair), Ct = C^T (d per pair),
 // Mp0 = c0 Mp, Cn = -C (d per pair).  G lanes per node.
 template <typename T>
 struct NodeBlockDev {
   long nu, np;
   int r;                       // displacement degree (pressure degree r - 1)
+  int pcouple;                 // 0: Cn on V through W (3.1); 1: on U through Dt (B.1)
   int n[3];                    // cells per axis of the level
   int udims[3], pdims[3];      // lattice sizes of Q_r and Q_{r-1}
   const int *uu_ptr, *up_ptr, *pu_ptr, *pp_ptr;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
       }
     }
   } else if (is_p) {
-    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V
+    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
     const long sI = node - A.nu;
     int a[3];
     lattice_coords(sI, A.pdims, D, a);
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
     }
     const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
     const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    const long uoff = A.pcouple ? R : 0; // the V or the U block of x
     for (int e = f0 + lane; e < f1; e += G) {
       const long J = box_node(bu, e - f0, A.udims);
       T cn[D];
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
       for (int a = 0; a < Q; ++a) {
         T t = T(0);
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + J * D + c];
+        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
         acc[2 * Q + a] += t;
       }
     }
@@ -265,9 +269,16 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
       if (b % G != lane) continue;
-      T val = tc.W[b] * (acc[Q + b] + acc[2 * Q + b]);
+      T val;
+      if (A.pcouple) {
+        val = tc.W[b] * acc[Q + b];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
+        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * (acc[a] + acc[2 * Q + a]);
+      } else {
+        val = tc.W[b] * (acc[Q + b] + acc[2 * Q + b]);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
+      }
       const long oi = (long)b * ns + 2 * R + sI;
       y[oi] = mode ? rhs[oi] - val : val;
     }
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
       }
     }
   } else if (is_p) {
-    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V
+    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
     const long sI = node - A.nu;
     int a[3];
     lattice_coords(sI, A.pdims, D, a);
@@ -407,6 +418,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
     }
     const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
     const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    const long uoff = A.pcouple ? R : 0; // the V or the U block of x
     for (int e = f0 + lane; e < f1; e += G) {
       const long J = box_node(bu, e - f0, A.udims);
       float2 cn[D];
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
 #pragma unroll
       for (int t = 0; t < Q; ++t)
 #pragma unroll
-        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + J * D + c]);
+        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + uoff + J * D + c]);
     }
   }
 #pragma unroll
@@ -452,9 +464,12 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
       if (b % G != lane) continue;
       DF val{0.f, 0.f};
       df_fma(val, tc.W[b], acc[Q + b]);
-      df_fma(val, tc.W[b], acc[2 * Q + b]);
+      if (!A.pcouple) df_fma(val, tc.W[b], acc[2 * Q + b]);
 #pragma unroll
       for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[t]);
+      if (A.pcouple)
+#pragma unroll
+        for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[2 * Q + t]);
       y[(long)b * ns + 2 * R + sI] = df_val(val);
     }
   }
@@ -1491,6 +1506,8 @@ struct DLevel {
   NodeBlockDev<T> nb{};
   // the same values as float pairs (see k_spmv_df; finest FP64 level, MIXED)
   NodeBlockDev<float2> nbdf{};
+  // Problem B.1: -Cvol in the layout of nb.pu_c (assembled levels)
+  const T *pu_cvol = nullptr;
   bool has_df = false;
   double nb_bytes = 0.0, nb_flops = 0.0;
   // patches
@@ -1832,6 +1849,7 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
   NodeBlockHost &H = *out;
   const long R = L.R, S = L.S, nu = R / d, np = S;
   const int r = L.r;
+  const bool b1 = L.form == STFEM_FORM_PROBLEM_B_1;
   const int *ud = L.U.dims, *pd = L.P.dims, *nc = L.box.n;
   H.nu = nu;
   H.np = np;
@@ -1925,17 +1943,21 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
     const long rp = 2 * R + sI;
     for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
       const long col = L.col[e];
-      if (col < R) {
+      if (!b1 && col < R) { // Problem 3.1: -C on V through W
         const long pos = box_pos(bu, col / d, ud, d);
         if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("p-equation V entry outside the box");
         H.pu_c[((size_t)H.pu_ptr[sI] + pos) * d + col % d] = L.v2[e];
+      } else if (b1 && col >= R && col < 2 * R) { // Problem B.1: -C on U through Dt
+        const long pos = box_pos(bu, (col - R) / d, ud, d);
+        if (pos < 0 || std::fabs(L.v2[e]) > tol) return bad("p-equation U entry outside the box");
+        H.pu_c[((size_t)H.pu_ptr[sI] + pos) * d + (col - R) % d] = L.v1[e];
       } else if (col >= 2 * R) {
         const long pos = box_pos(bp, col - 2 * R, pd, d);
         if (pos < 0) return bad("p-equation P entry outside the box");
         H.pp_m[(size_t)H.pp_ptr[sI] + pos] = L.v1[e];
         H.pp_b[(size_t)H.pp_ptr[sI] + pos] = L.v2[e];
       } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
-        return bad("p-equation couples to U");
+        return bad(b1 ? "p-equation couples to V" : "p-equation couples to U");
       }
     }
   }
@@ -1959,6 +1981,7 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   nb.nu = H.nu;
   nb.np = H.np;
   nb.r = L.r;
+  nb.pcouple = L.form == STFEM_FORM_PROBLEM_B_1 ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     nb.n[i] = L.box.n[i];
     nb.udims[i] = L.U.dims[i];
@@ -1976,6 +1999,15 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   CKR(upload(h, &ip, H.pp_ptr)); nb.pp_ptr = ip;
   CKR(upload(h, &tp, H.pp_m)); nb.pp_m = tp;
   CKR(upload(h, &tp, H.pp_b)); nb.pp_b = tp;
+  if (std::is_same<T, double>::value && nb.pcouple && !L.cvol.empty()) {
+    // Problem B.1's previous-slab coupling: -Cvol in the layout of pu_c
+    if (L.cvol.size() != H.pu_c.size()) {
+      h->err = "volume coupling does not match the node-block layout";
+      return STFEM_ERR_STATE;
+    }
+    CKR(upload(h, &tp, L.cvol));
+    D.pu_cvol = tp;
+  }
   const double nuu = H.uu_m.size(), nup = H.up_c.size() / d, npu = H.pu_c.size() / d, npp = H.pp_m.size();
   D.nb_bytes = (nuu * (1 + d * d) + nup * d + npu * d + npp * 2) * sizeof(T) + (2.0 * H.nu + 2.0 * H.np + 4) * 4.0;
   D.nb_flops = 2.0 * (nuu * (2 * d + d * d) + nup * d + npu * d + npp * 2);
@@ -2007,6 +2039,7 @@ int upload_level_df(stfem_h h, DLevel<double> &D, const stfem::Level &L) {
   nb.nu = D.nb.nu;
   nb.np = D.nb.np;
   nb.r = D.nb.r;
+  nb.pcouple = D.nb.pcouple;
   for (int i = 0; i < 3; ++i) {
     nb.n[i] = D.nb.n[i];
     nb.udims[i] = D.nb.udims[i];
@@ -3871,7 +3904,22 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs, 
   one.q = 1;
   one.Dt[0] = 1.0;
   one.W[0] = 0.0;
-  launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0); // S1 * state
+  if (F.nb.pcouple) {
+    // Problem B.1: the pressure row couples to the previous state through
+    // c0 Mp P^- + alpha <div u^-, xi>, i.e. the volume part of -C alone (the
+    // data term -alpha <u_D . n, xi> is zero for the built-in problems); the
+    // launch takes its arguments by value, so the swap lasts for it alone
+    if (!F.pu_cvol) {
+      h->err = "Problem B.1 needs the volume coupling of the finest level";
+      return STFEM_ERR_STATE;
+    }
+    const double *pu_c = F.nb.pu_c;
+    F.nb.pu_c = F.pu_cvol;
+    launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0);
+    F.nb.pu_c = pu_c;
+  } else {
+    launch_spmv<double>(h, F, one, prev, nullptr, h->ys, 0); // S1 * state
+  }
   const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
   const double t_prev = t0 + slab * h->tau;
   const long ncell = HF.box.ncell;

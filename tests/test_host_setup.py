@@ -53,7 +53,7 @@ CASES = [
 ]
 
 
-def _pair(case, seed=0, coarse_op=0):
+def _pair(case, seed=0, coarse_op=0, form=0):
     dim, n, L, r, k, lo, hi, bcu, bcp, hf = case
     rng = np.random.default_rng(seed)
     nc = n ** dim
@@ -64,7 +64,7 @@ def _pair(case, seed=0, coarse_op=0):
     prob = stfem.Problem(dim, n, L, r, k, tau, lo=lo, hi=hi, rho=1.3, alpha=0.8, c0=0.2,
                          lam_cell=lam, mu_cell=mu, kappa_cell=kap, bc_u=bcu, bc_p=bcp,
                          hf_mode=stfem.HF_MEASURE if hf == "measure" else stfem.HF_LENGTH,
-                         coarse_op=coarse_op)
+                         coarse_op=coarse_op, form=form)
     meshes = [BoxMesh(dim, lo, hi, [n] * dim, hf)]
     mats = [Material(1.3, 0.8, 0.2, lam, mu, kap)]
     for _ in range(L - 1):
@@ -74,13 +74,15 @@ def _pair(case, seed=0, coarse_op=0):
     return prob, ops, Temporal(k), tau
 
 
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
 @pytest.mark.parametrize("coarse", ["rediscretize", "galerkin"])
 @pytest.mark.parametrize("case", CASES)
-def test_level_matrices_match_oracle(case, coarse):
+def test_level_matrices_match_oracle(case, coarse, form):
     from oracle.gmg import slab_prolongation
     prob, ops, T, tau = _pair(case, coarse_op=stfem.COARSE_GALERKIN if coarse == "galerkin"
-                              else stfem.COARSE_REDISCRETIZE)
-    mats = [slab_matrix(o, T, tau) for o in ops]
+                              else stfem.COARSE_REDISCRETIZE,
+                              form=stfem.FORM_PROBLEM_3_1 if form == "3.1" else stfem.FORM_PROBLEM_B_1)
+    mats = [slab_matrix(o, T, tau, form) for o in ops]
     if coarse == "galerkin":
         for l in range(len(ops) - 1, 0, -1):
             P = slab_prolongation(ops[l - 1], ops[l], T)

@@ -67,12 +67,80 @@ def test_diffusion_constants_in_kernel_without_nitsche(dim, r):
     assert np.abs(ops.B @ np.ones(ops.S)).max() < 1e-11
 
 
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
 @pytest.mark.parametrize("k", [0, 1, 2])
-def test_kronecker_equals_direct_time_integration(k):
+def test_kronecker_equals_direct_time_integration(k, form):
     """Slab matrix from Dt/W (Radau) equals the block-by-block assembly with
     an independent Gauss rule in time (both exact)."""
     ops, _ = _ops(2, 2, 2, 0)
     T = Temporal(k)
-    A1 = slab_matrix(ops, T, 0.037)
-    A2 = slab_matrix_direct(ops, T, 0.037)
+    A1 = slab_matrix(ops, T, 0.037, form)
+    A2 = slab_matrix_direct(ops, T, 0.037, form=form)
     assert abs(A1 - A2).max() < 1e-10 * abs(A1).max()
+
+
+@pytest.mark.parametrize("dim,r", [(2, 2), (3, 2)])
+def test_volume_coupling_divergence_theorem(dim, r):
+    """Cvol(psi, 1) = -alpha int div psi whatever the boundary conditions, and
+    C - Cvol is the Dirichlet-face term alpha int_{Gamma_D} psi.n."""
+    opsD, mesh = _ops(dim, 2, r, 0)
+    X = opsD.Vs.node_coords()
+    u = np.zeros_like(X)
+    u[:, 0] = X[:, 0] ** 2 + X[:, 1]  # div u = 2 x, u.n = x^2 + y on the faces x = lo, hi
+    one = np.ones(opsD.S)
+    vol = float(np.prod(mesh.hi - mesh.lo))
+    int_div = (mesh.lo[0] + mesh.hi[0]) * vol  # int 2 x over the box
+    assert abs(one @ (opsD.Cvol @ u.reshape(-1)) + 0.9 * int_div) < 1e-11
+    # faces x = hi (n = +e_0) and x = lo (n = -e_0): int (x^2 + y) over each
+    side = vol / (mesh.hi[0] - mesh.lo[0])
+    ybar = 0.5 * (mesh.lo[1] + mesh.hi[1])
+    flux = (mesh.hi[0] ** 2 + ybar) * side - (mesh.lo[0] ** 2 + ybar) * side
+    assert abs(one @ ((opsD.C - opsD.Cvol) @ u.reshape(-1)) - 0.9 * flux) < 1e-11
+
+
+def _poly_case(dim, k):
+    """A solution in the discrete space: Q_2 in space and P_k in time for
+    u (so v = d_t u too), Q_1 and P_k for p; nonzero traces."""
+    import sympy as sy
+    from oracle.problems import Problem
+    X = sy.symbols("x0:%d" % dim, real=True)
+    t = sy.symbols("t", real=True)
+    T = sum(sy.Rational(1, j + 2) * t ** j for j in range(k + 1))  # degree k in time
+    x, y = X[0], X[1]
+    z = X[2] if dim == 3 else sy.Integer(1)
+    u = [T * (x ** 2 * y + x * y ** 2 / 2 - y * z), (1 - 2 * t if k else 1) * (x * y ** 2 + x ** 2 - sy.Rational(3, 10))]
+    if dim == 3:
+        u.append(T * (x * z + y ** 2 * z - 1))
+    p = (2 - t if k else 2) * (1 + x - y / 2 + x * y * z)
+    return Problem("poly", dim, 1.0, 0.9, 0.5, u, p)
+
+
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (3, 1)])
+def test_discrete_space_solution_is_exact(dim, k, form):
+    """Consistency: an exact solution lying in the discrete space satisfies the
+    slab system of either form to rounding (Dirichlet and Neumann faces with
+    nonzero data), and fails the other form's system."""
+    from oracle.slab import slab_rhs, interpolate_state, FORMS
+    prob = _poly_case(dim, k)
+    lo, hi = [0.0, 0.0, 0.0][:dim], [1.0, 2.0, 0.5][:dim]
+    mesh = BoxMesh(dim, lo, hi, [2] * dim)
+    mat = Material.uniform(mesh, 1.0, 0.9, 0.5, 2.0, 1.0, 0.7)
+    bcu = [0, 1, 0, 0, 1, 0][:2 * dim]
+    bcp = [1, 0, 0, 1, 0, 0][:2 * dim]
+    ops = SpatialOps(mesh, 2, mat, bcu, bcp)
+    T = Temporal(k)
+    tau, t_prev = 0.1, 0.3
+    state = interpolate_state(ops, prob, t_prev)
+    X = np.concatenate([np.concatenate(interpolate_state(ops, prob, t_prev + 0.5 * tau * (ta + 1.0)))
+                        for ta in T.t])
+
+    def rel_residual(mat_form, rhs_form):
+        A = slab_matrix(ops, T, tau, mat_form)
+        b = slab_rhs(ops, T, tau, t_prev, prob, state, rhs_form)
+        scale = abs(A) @ np.abs(X) + np.abs(b)
+        return np.max(np.abs(A @ X - b) / scale)
+
+    assert rel_residual(form, form) < 1e-12
+    other = [f for f in FORMS if f != form][0]
+    assert rel_residual(form, other) > 1e-6
