@@ -55,10 +55,19 @@ def _axis_range(a_lo, a_hi, at_lo_bdry, at_hi_bdry):
     return range(lo, hi + 1)
 
 
+def _patch_cells(mesh, vertex):
+    """Cells whose closure holds lattice vertex ``vertex``, x fastest."""
+    rng = [range(max(vertex[i] - 1, 0), min(vertex[i], mesh.n[i] - 1) + 1) for i in range(mesh.dim)]
+    return [c[::-1] for c in itertools.product(*rng[::-1])]
+
+
 def patch_nodes(space, vertex, support=True):
     """Global node indices of the scalar space ``space`` belonging to the
-    vertex patch at lattice vertex ``vertex`` (multi-index)."""
+    vertex patch at lattice vertex ``vertex`` (multi-index).  A broken space:
+    the dofs of every cell of the patch (each supported in its cell)."""
     mesh, m = space.mesh, space.m
+    if getattr(space, "disc", False):
+        return np.concatenate([space.cell_nodes(c) for c in _patch_cells(mesh, vertex)])
     ranges = []
     for i in range(mesh.dim):
         c0 = max(vertex[i] - 1, 0)
@@ -93,6 +102,8 @@ def patch_dofs(ops, temporal, vertex, support=True):
 
 def cell_patch_nodes(space, cell):
     """Every node of the scalar space ``space`` on the closed cell ``cell``."""
+    if getattr(space, "disc", False):
+        return space.cell_nodes(cell)
     m = space.m
     ranges = [range(m * cell[i], m * (cell[i] + 1) + 1) for i in range(space.mesh.dim)]
     return np.array([space.node_index(a[::-1]) for a in itertools.product(*ranges[::-1])], int)
@@ -133,9 +144,36 @@ def vertices(mesh):
         yield tuple(v)
 
 
+def prolongation_disc(coarse, fine):
+    """Embedding of the broken coarse P_m space into the nested fine one: on
+    each fine cell the coarse basis function, an exact member of the fine
+    cell's P_m, expanded in the fine basis (L2 projection on the cell, exact)."""
+    cm_, fm_ = coarse.mesh, fine.mesh
+    from .space import cell_rule
+    X, w = cell_rule(fm_.dim, fine.m + 2)
+    phi_f, _ = fine.basis(X)
+    gram = np.einsum("q,qi,qj->ij", w, phi_f, phi_f)
+    rows, cols, vals = [], [], []
+    for c, cf in fm_.cells():
+        cc = tuple(ci // 2 for ci in cf)
+        off = np.array([cf[i] - 2 * cc[i] for i in range(fm_.dim)], float)
+        phi_c, _ = coarse.basis((X + off[None, :]) / 2.0)  # fine reference points in the coarse cell
+        coef = np.linalg.solve(gram, np.einsum("q,qj,qi->ji", w, phi_f, phi_c))
+        fr, cr = fine.cell_nodes(cf), coarse.cell_nodes(cc)
+        for j in range(fine.nloc):
+            for i in range(coarse.nloc):
+                if abs(coef[j, i]) > 1e-14:
+                    rows.append(fr[j])
+                    cols.append(cr[i])
+                    vals.append(coef[j, i])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(fine.nnodes, coarse.nnodes))
+
+
 def prolongation_scalar(coarse, fine):
     """Interpolation of the coarse Q_m space into the nested fine one:
     P[f, c] = coarse basis function c evaluated at fine node f."""
+    if getattr(fine, "disc", False):
+        return prolongation_disc(coarse, fine)
     xf = fine.node_coords()
     cm_ = coarse.mesh
     rows, cols, vals = [], [], []
@@ -218,7 +256,7 @@ class Hierarchy:
 
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material_fine, bc_u, bc_p, tau,
                  omega=0.7, nsweeps=1, support=True, hf="measure", coarse="galerkin",
-                 patches="vertex", averaging=True, form="3.1"):
+                 patches="vertex", averaging=True, form="3.1", pressure="cont"):
         self.temporal = Temporal(k)
         self.omega, self.nsweeps = omega, nsweeps
         self.averaging = averaging
@@ -230,7 +268,7 @@ class Hierarchy:
         meshes, mats = meshes[::-1], mats[::-1]  # level 0 = coarsest
         self.levels = []
         for mesh, mat in zip(meshes, mats):
-            ops = SpatialOps(mesh, r, mat, bc_u, bc_p)
+            ops = SpatialOps(mesh, r, mat, bc_u, bc_p, pressure)
             A = slab_matrix(ops, self.temporal, tau, form)
             self.levels.append(Level(ops, A, self.temporal, support, patches))
         self.P = [None] + [slab_prolongation(self.levels[l - 1].ops, self.levels[l].ops,

@@ -187,12 +187,12 @@ def end_state(ops, temporal, X):
 
 
 def interpolate_state(ops, prob, t):
-    """Nodal interpolation of (v, u, p) at time t (reading for u_{0,h} etc.)."""
+    """Nodal interpolation of (v, u, p) at time t (reading for u_{0,h} etc.;
+    a broken pressure space takes the L2 projection on each cell)."""
     xu = ops.Vs.node_coords()
-    xp = ops.Qs.node_coords()
     V = prob.v(xu, t).reshape(-1)
     U = prob.u(xu, t).reshape(-1)
-    P = prob.p(xp, t).reshape(-1)
+    P = ops.Qs.interpolate(lambda X: prob.p(X, t))
     return V, U, P
 
 

@@ -19,9 +19,9 @@ class Instance:
     def __init__(self, dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
                  problem, t0=0.0, omega=0.7, nsweeps=1, support=True, hf="measure",
                  coarse="galerkin", patches="vertex", averaging=True, absolute=False,
-                 form="3.1"):
+                 form="3.1", pressure="cont"):
         self.h = Hierarchy(dim, lo, hi, n_fine, n_levels, r, k, material, bc_u, bc_p, tau,
-                           omega, nsweeps, support, hf, coarse, patches, averaging, form)
+                           omega, nsweeps, support, hf, coarse, patches, averaging, form, pressure)
         self.form = form
         self.absolute = absolute
         self.prob, self.tau, self.t0 = problem, tau, t0

@@ -1,9 +1,12 @@
-"""Box meshes, Taylor-Hood spaces and spatial forms (oracle; test infrastructure only).
+"""Box meshes, finite element spaces and spatial forms (oracle; test infrastructure only).
 
 Follows Sec. 2 (quasi-uniform hexahedral / quadrilateral levels, h_l = h_{l-1}/2,
-Eq. 2.5 with the continuous pressure space, i.e. the Taylor-Hood pair
-Q_r^d / Q_{r-1}) and Sec. 3, Eqs. 3.2-3.4 (the forms A_gamma, C, B_gamma with
-Nitsche's terms a_gamma, b_gamma and the functionals F_gamma, G_gamma).
+Eq. 2.5 with either pressure space: the continuous one, i.e. the Taylor-Hood
+pair Q_r^d / Q_{r-1} (default), or the broken one, the pair
+Q_r^d / P_{r-1}^disc) and Sec. 3, Eqs. 3.2-3.4 (the forms A_gamma, C, B_gamma
+with Nitsche's terms a_gamma, b_gamma, or for the broken pressure space the
+symmetric interior penalty form B_gamma, and the functionals F_gamma,
+G_gamma).
 
 Numbering used throughout the oracle:
 
@@ -31,6 +34,16 @@ Readings taken where the paper is silent or garbled:
   The permeability is isotropic, K = kappa I.
 * Quadrature: Gauss-Legendre with r+2 points per direction on cells and
   faces, for matrices and loads.
+* Broken pressure space P_{r-1}^disc (Sec. 2 names mapped and unmapped
+  versions; on axis-parallel boxes both are the polynomials of total degree
+  r-1 on each cell).  Basis: products of Legendre polynomials of the
+  reference cell, orthogonal per cell; dofs numbered cell by cell.  The
+  interior penalty terms run over the interior faces and the Dirichlet
+  faces of p (on a Neumann face the jump term would impose p = 0, which the
+  functional G_gamma, with its Neumann datum there, does not); h_F is the
+  mean of the two cells' h_F, which on these uniform meshes is the cell's
+  (the same reading as for Nitsche's terms); gamma = gamma_b.  The initial
+  pressure p_{0,h} is the L2 projection onto each cell (no nodal values).
 """
 import itertools
 import numpy as np
@@ -117,6 +130,10 @@ class NodalSpace:
                 out[idx, i] = self.mesh.lo[i] + self.mesh.h[i] * (c + self.ref[loc])
         return out
 
+    def interpolate(self, fun):
+        """Nodal interpolation of fun(X) (X: physical points, shape (n, d))."""
+        return np.asarray(fun(self.node_coords()), float).reshape(-1)
+
     def basis(self, X):
         """Reference basis values (npts, nloc) and gradients (npts, nloc, d)
         at reference points X in [0,1]^d (gradient w.r.t. reference coords)."""
@@ -141,6 +158,58 @@ class NodalSpace:
                     g = g * (ders[i][:, loc[i]] if i == j else vals[i][:, loc[i]])
                 dphi[:, li, j] = g
         return phi, dphi
+
+
+class DiscSpace:
+    """Broken scalar P_m space on a BoxMesh: on each cell the polynomials of
+    total degree <= m, with the basis prod_i L_{a_i}(2 x_i - 1) (Legendre
+    polynomials of the reference coordinates, sum a_i <= m)."""
+
+    disc = True
+
+    def __init__(self, mesh, m):
+        self.mesh = mesh
+        self.m = int(m)
+        d = mesh.dim
+        self.exps = [e[::-1] for e in itertools.product(range(self.m + 1), repeat=d) if sum(e) <= self.m]
+        self.nloc = len(self.exps)
+        self.nnodes = mesh.ncell * self.nloc
+
+    def cell_nodes(self, cm):
+        c, stride = 0, 1
+        for i in range(self.mesh.dim):
+            c += cm[i] * stride
+            stride *= self.mesh.n[i]
+        return c * self.nloc + np.arange(self.nloc)
+
+    def basis(self, X):
+        """Reference basis values (npts, nloc) and gradients (npts, nloc, d)."""
+        from numpy.polynomial import legendre as L
+        d = self.mesh.dim
+        npts = X.shape[0]
+        vals = [[L.legval(2 * X[:, i] - 1, np.eye(self.m + 1)[a]) for a in range(self.m + 1)] for i in range(d)]
+        ders = [[2 * L.legval(2 * X[:, i] - 1, L.legder(np.eye(self.m + 1)[a])) for a in range(self.m + 1)]
+                for i in range(d)]
+        phi = np.zeros((npts, self.nloc))
+        dphi = np.zeros((npts, self.nloc, d))
+        for li, e in enumerate(self.exps):
+            phi[:, li] = np.prod([vals[i][e[i]] for i in range(d)], axis=0)
+            for j in range(d):
+                dphi[:, li, j] = np.prod([ders[i][e[i]] if i == j else vals[i][e[i]] for i in range(d)], axis=0)
+        return phi, dphi
+
+    def interpolate(self, fun):
+        """L2 projection of fun(X) (X: physical points, shape (n, d)) onto each cell."""
+        mesh = self.mesh
+        X, w = cell_rule(mesh.dim, self.m + 4)
+        phi, _ = self.basis(X)
+        gram = np.einsum("q,qi,qj->ij", w, phi, phi)
+        out = np.zeros(self.nnodes)
+        for c, cm in mesh.cells():
+            x0 = mesh.lo + mesh.h * np.array(cm)
+            f = fun(x0[None, :] + X * mesh.h[None, :])
+            out[self.cell_nodes(cm)] = np.linalg.solve(gram, np.einsum("q,qi,q->i", w, phi, f))
+        return out
 
 
 def cell_rule(dim, nq):
@@ -222,11 +291,14 @@ class SpatialOps:
     Row index = test function, column index = trial function.
     """
 
-    def __init__(self, mesh, r, mat, bc_u, bc_p):
+    def __init__(self, mesh, r, mat, bc_u, bc_p, pressure="cont"):
+        if pressure not in ("cont", "disc"):
+            raise ValueError("pressure must be 'cont' or 'disc'")
         self.mesh, self.r, self.mat = mesh, int(r), mat
         self.bc_u, self.bc_p = list(bc_u), list(bc_p)
+        self.pressure = pressure
         self.Vs = NodalSpace(mesh, r)
-        self.Qs = NodalSpace(mesh, r - 1)
+        self.Qs = NodalSpace(mesh, r - 1) if pressure == "cont" else DiscSpace(mesh, r - 1)
         self.d = mesh.dim
         self.nu = self.Vs.nnodes
         self.np_ = self.Qs.nnodes
@@ -353,6 +425,8 @@ class SpatialOps:
             add("Mu", un, un, Mu)
             add("B", pn, pn, B)
             add("Mp", pn, pn, Mp)
+        if self.pressure == "disc":
+            self._interior_faces(add)
         shapes = {"K": (self.R, self.R), "C": (self.S, self.R), "Cvol": (self.S, self.R),
                   "Mu": (self.nu, self.nu),
                   "B": (self.S, self.S), "Mp": (self.S, self.S)}
@@ -362,6 +436,43 @@ class SpatialOps:
             M.sum_duplicates()
             setattr(self, key, M)
         self.M = sp.kron(self.Mu, sp.identity(d), format="csr")  # vector mass, node-major
+
+    def _interior_faces(self, add):
+        """Interior face terms of the interior penalty form B_gamma (Def. of
+        B_gamma, broken pressure space): for the face between the cell K+
+        below and K- above along an axis, n the unit normal out of K+,
+        [w] = w+ - w-, {w} = (w+ + w-)/2:
+        -<{K grad q}.n, [psi]> - <[q], {K grad psi}.n> + gamma/h_F <[q], [psi]>."""
+        mesh, d = self.mesh, self.d
+        hF, gam = mesh.hF, self.gamma_b
+        for ax in range(d):
+            Xm, wf = face_rule(d, self.nq, ax, 1)  # on K+ (its upper face)
+            Xp, _ = face_rule(d, self.nq, ax, 0)   # on K- (its lower face)
+            wf = wf * (mesh.vol / mesh.h[ax])
+            pa, dpa = self.Qs.basis(Xm)
+            pb, dpb = self.Qs.basis(Xp)
+            dna = dpa[:, :, ax] / mesh.h[ax]  # grad . n, n = +e_ax
+            dnb = dpb[:, :, ax] / mesh.h[ax]
+            for c, cm in mesh.cells():
+                if cm[ax] == mesh.n[ax] - 1:
+                    continue
+                cn = list(cm)
+                cn[ax] += 1
+                cn = tuple(cn)
+                c2 = 0
+                stride = 1
+                for i in range(d):
+                    c2 += cn[i] * stride
+                    stride *= mesh.n[i]
+                ka, kb = self.mat.kappa[c], self.mat.kappa[c2]
+                # trial/test functions of both cells: jump and flux-average values
+                jump = np.concatenate([pa, -pb], axis=1)                       # (nq, 2 nloc)
+                flux = np.concatenate([0.5 * ka * dna, 0.5 * kb * dnb], axis=1)
+                Bf = (-np.einsum("q,qs,qr->rs", wf, flux, jump)
+                      - np.einsum("q,qs,qr->rs", wf, jump, flux)
+                      + (gam / hF) * np.einsum("q,qs,qr->rs", wf, jump, jump))
+                idx = np.concatenate([self.Qs.cell_nodes(cm), self.Qs.cell_nodes(cn)])
+                add("B", idx, idx, Bf)
 
     # -- loads (Eq. 3.4) -------------------------------------------------------
     def loads(self, prob, t):

@@ -257,3 +257,41 @@ def test_elementwise_vanka_is_weaker_under_pressure_coupling():
         _, its[patches], rel, _ = fgmres(lambda v: H.fine.A @ v, b, repeat_state(ops, T, st), H.vcycle, 1e-8)
         assert rel <= 1e-8
     assert its["cell"] >= 1.5 * its["vertex"]
+
+
+@pytest.mark.parametrize("dim,m", [(2, 1), (2, 2), (3, 1)])
+def test_broken_prolongation_reproduces_polynomials(dim, m):
+    """The embedding of the broken coarse P_m space into the fine one (nested
+    spaces, Sec. 2) maps the coarse L2 projection of a degree-m polynomial to
+    the fine one exactly, and each fine cell sees only its parent's dofs."""
+    from oracle.space import DiscSpace
+    cm = BoxMesh(dim, [0.0] * dim, [1.0, 0.5, 2.0][:dim], [2] * dim)
+    fm = BoxMesh(dim, [0.0] * dim, [1.0, 0.5, 2.0][:dim], [4] * dim)
+    sc, sf = DiscSpace(cm, m), DiscSpace(fm, m)
+    f = lambda X: 1.0 + X[:, 0] ** m - 0.7 * X[:, dim - 1] + 0.2 * X[:, 0] * X[:, 1] ** (m - 1)
+    P = prolongation_scalar(sc, sf)
+    assert np.abs(P @ sc.interpolate(f) - sf.interpolate(f)).max() < 1e-12
+    nnz_rows = np.diff(P.indptr)
+    assert nnz_rows.max() <= sc.nloc
+
+
+def test_gmg_fgmres_broken_pressure_matches_direct_solve():
+    """The GMG-FGMRES solve of the pair Q2^2 / P1^disc (interior penalty
+    pressure form) reaches the dense direct solution of a slab; the vertex
+    patches hold the pressure dofs of their cells."""
+    mat = Material.uniform(BoxMesh(2, [0, 0], [1, 1], [8, 8]), 1, 1, 1, 1, 1, 1)
+    H = Hierarchy(2, [0, 0], [1, 1], [8, 8], 3, 2, 1, mat, [0] * 4, [0] * 4, 0.01, pressure="disc")
+    prob = sin_problem(2, 1.0, 1.0, 1.0)
+    ops, T = H.fine.ops, H.temporal
+    assert ops.S == 64 * 3
+    sizes = [len(p) for p in H.fine.patches]
+    # the 5 x 5 vertices away from boundary cells: 3 x 3 Q2 nodes x 2 fields x 2
+    # components + 4 cells x 3 P1 dofs, at q time nodes
+    assert sizes.count(T.q * (2 * 2 * 9 + 4 * 3)) == 25
+    st = interpolate_state(ops, prob, 0.0)
+    b = slab_rhs(ops, T, 0.01, 0.0, prob, st)
+    xd = np.linalg.solve(H.fine.A.toarray(), b)
+    x0 = repeat_state(ops, T, st)
+    x, it, rel, hist = fgmres(lambda v: H.fine.A @ v, b, x0, H.vcycle, 1e-10)
+    assert rel <= 1e-10 and it <= 30
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)

@@ -144,3 +144,60 @@ def test_discrete_space_solution_is_exact(dim, k, form):
     assert rel_residual(form, form) < 1e-12
     other = [f for f in FORMS if f != form][0]
     assert rel_residual(form, other) > 1e-6
+
+
+@pytest.mark.parametrize("dim,r", [(2, 2), (2, 3), (3, 2)])
+def test_interior_penalty_form(dim, r):
+    """The broken pressure form B_gamma (interior penalty): symmetric, and
+    constants in its kernel without Dirichlet faces (jumps of a constant
+    vanish); the pressure mass is block diagonal by cell.  (Coercivity needs
+    gamma large enough; with gamma = r (r-1) / 2 it fails on some coarse
+    meshes, so it is not asserted.)"""
+    lo, hi = [0.0, 0.0, 0.0][:dim], [1.0, 2.0, 0.5][:dim]
+    mesh = BoxMesh(dim, lo, hi, [2] * dim)
+    mat = Material.uniform(mesh, 1.1, 0.9, 0.3, 1.3, 0.7, 1.7)
+    opsN = SpatialOps(mesh, r, mat, [1] * (2 * dim), [1] * (2 * dim), "disc")
+    opsD = SpatialOps(mesh, r, mat, [0] * (2 * dim), [0] * (2 * dim), "disc")
+    for o in (opsN, opsD):
+        assert abs(o.B - o.B.T).max() < 1e-12 * abs(o.B).max()
+    one = opsN.Qs.interpolate(lambda X: np.ones(X.shape[0]))
+    assert np.abs(opsN.B @ one).max() < 1e-11 * abs(opsN.B).max()
+    nl = opsN.Qs.nloc
+    Mp = opsN.Mp.toarray()
+    for c in range(mesh.ncell):
+        Mp[c * nl:(c + 1) * nl, c * nl:(c + 1) * nl] = 0.0
+    assert np.abs(Mp).max() == 0.0
+
+
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
+@pytest.mark.parametrize("dim,r,k", [(2, 3, 1), (2, 3, 2), (3, 2, 1)])
+def test_broken_pressure_solution_is_exact(dim, r, k, form):
+    """Consistency of the pair Q_r^d / P_{r-1}^disc: a solution in the discrete
+    space (u in Q_r, P_k in time; p a global polynomial of total degree
+    r - 1) satisfies either slab system to rounding, with Dirichlet and
+    Neumann faces for both fields and nonzero data."""
+    import sympy as sy
+    from oracle.problems import Problem
+    from oracle.slab import slab_rhs, interpolate_state
+    X = sy.symbols("x0:%d" % dim, real=True)
+    t = sy.symbols("t", real=True)
+    T = sum(sy.Rational(1, j + 2) * t ** j for j in range(k + 1))
+    x, y = X[0], X[1]
+    z = X[2] if dim == 3 else sy.Integer(1)
+    u = [T * (x ** 2 * y - y * z + x), (1 - 2 * t) * (x * y + x ** 2 - sy.Rational(3, 10))]
+    if dim == 3:
+        u.append(T * (x * z + y * z - 1))
+    p = (2 - t) * (1 + x - y / 2 + (x * y if r >= 3 else 0) + (z / 3 if dim == 3 else 0))
+    prob = Problem("poly", dim, 1.0, 0.9, 0.5, u, p)
+    lo, hi = [0.0, 0.0, 0.0][:dim], [1.0, 2.0, 0.5][:dim]
+    mesh = BoxMesh(dim, lo, hi, [2] * dim)
+    mat = Material.uniform(mesh, 1.0, 0.9, 0.5, 2.0, 1.0, 0.7)
+    ops = SpatialOps(mesh, r, mat, [0, 1, 0, 0, 1, 0][:2 * dim], [1, 0, 0, 1, 0, 0][:2 * dim], "disc")
+    Tm = Temporal(k)
+    tau, t_prev = 0.1, 0.3
+    state = interpolate_state(ops, prob, t_prev)
+    Xs = np.concatenate([np.concatenate(interpolate_state(ops, prob, t_prev + 0.5 * tau * (ta + 1.0)))
+                         for ta in Tm.t])
+    A = slab_matrix(ops, Tm, tau, form)
+    b = slab_rhs(ops, Tm, tau, t_prev, prob, state, form)
+    assert np.max(np.abs(A @ Xs - b) / (abs(A) @ np.abs(Xs) + np.abs(b))) < 1e-12

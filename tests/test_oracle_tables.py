@@ -20,10 +20,10 @@ LAM = E * NU / ((1 + NU) * (1 - 2 * NU))
 MU = E / (2 * (1 + NU))
 
 
-def _march_errors(prob, n, r, k, tau, t0, T, m_inf=0, form="3.1"):
+def _march_errors(prob, n, r, k, tau, t0, T, m_inf=0, form="3.1", pressure="cont"):
     mesh = BoxMesh(2, [0, 0], [1, 1], [n, n])
     mat = Material.uniform(mesh, 1.0, 0.9, 0.01, LAM, MU, 1.0)
-    ops = SpatialOps(mesh, r, mat, [0] * 4, [0] * 4)
+    ops = SpatialOps(mesh, r, mat, [0] * 4, [0] * 4, pressure)
     tmp = Temporal(k)
     lu = spla.splu(slab_matrix(ops, tmp, tau, form).tocsc())
     acc = ErrorAccumulator(ops, tmp, prob, m_inf=m_inf)
@@ -61,5 +61,18 @@ def test_table_5_3_superconvergence_rate():
 def test_table_5_1_displacement_velocity(row, n, tau, form):
     ref = read_golden("table_5_1_row%d.txt" % row)
     l2, _, _ = _march_errors(paper_eoc_problem(), n, 3, 2, tau, 1.0, 1.0, form=form)
+    assert abs(l2["gu"] - ref["L2_grad_u"]) <= 1e-4 * ref["L2_grad_u"]
+    assert abs(l2["v"] - ref["L2_v"]) <= 2e-4 * ref["L2_v"]
+
+
+@pytest.mark.parametrize("row,n,tau", [(1, 4, 0.1), (2, 8, 0.05)])
+def test_table_5_1_broken_pressure_pair(row, n, tau):
+    """Table 5.1 is printed for the pair Q3^2 / P2^disc itself: its
+    displacement and velocity errors, with the interior penalty pressure form.
+    (Its pressure errors are not matched: this oracle's are 1.7-1.8x the
+    printed ones, and no reading of h_F or gamma tried brings them within
+    40%.)"""
+    ref = read_golden("table_5_1_row%d.txt" % row)
+    l2, _, _ = _march_errors(paper_eoc_problem(), n, 3, 2, tau, 1.0, 1.0, pressure="disc")
     assert abs(l2["gu"] - ref["L2_grad_u"]) <= 1e-4 * ref["L2_grad_u"]
     assert abs(l2["v"] - ref["L2_v"]) <= 2e-4 * ref["L2_v"]
