@@ -254,7 +254,9 @@ int stfem_initial_state(stfem_h h, double *state);
 
 /* Right-hand side F_n of slab n (0-based, I_n = (t0 + n tau, t0 + (n+1) tau])
  * from the problem's data at the Radau nodes and the previous end state
- * prev_state (device, 2R+S) (Eq. 3.5, Eq. 4.5).  rhs: device, n_slab. */
+ * prev_state (device, 2R+S) (Eq. 3.5, Eq. 4.5; for STFEM_FORM_PROBLEM_B_1 the
+ * pressure rows take the coupling of Problem B.1, see stfem_degrees).
+ * rhs: device, n_slab. */
 int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs);
 
 /* March n_slabs slabs from slab index first_slab: for each slab, build F_n,
