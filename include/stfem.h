@@ -94,13 +94,24 @@ typedef struct {
 #define STFEM_FORM_PROBLEM_3_1 0
 #define STFEM_FORM_PROBLEM_B_1 1
 
-/* r: displacement degree (Q_r^d / Q_{r-1} Taylor-Hood, r >= 2, Eq. 2.5);
+/* Pressure space (Sec. 2, Eq. 2.5):
+ * CONTINUOUS: Q_{r-1}, the Taylor-Hood pair Q_r^d / Q_{r-1} (default).
+ * BROKEN: P_{r-1}^disc, polynomials of total degree r-1 on each cell, with the
+ *   interior penalty form B_gamma over interior faces and Dirichlet faces of p
+ *   (gamma = r (r-1) / 2).  Host setup only (stfem_host_* inspection calls):
+ *   stfem_setup and stfem_estimate_bytes return STFEM_ERR_ARG for it. */
+#define STFEM_PRESSURE_CONTINUOUS 0
+#define STFEM_PRESSURE_BROKEN 1
+
+/* r: displacement degree (Q_r^d, r >= 2, Eq. 2.5);
  * k: temporal degree of dG(k) (k+1 right Gauss-Radau nodes, Eq. 2.4), 0..4;
- * form: STFEM_FORM_PROBLEM_3_1 (0, default) or STFEM_FORM_PROBLEM_B_1. */
+ * form: STFEM_FORM_PROBLEM_3_1 (0, default) or STFEM_FORM_PROBLEM_B_1;
+ * pressure: STFEM_PRESSURE_CONTINUOUS (0, default) or STFEM_PRESSURE_BROKEN. */
 typedef struct {
   int r;
   int k;
   int form;
+  int pressure;
 } stfem_degrees;
 
 /* Coefficients of Eq. 1.1 with isotropic C (lambda, mu) and K = kappa I.

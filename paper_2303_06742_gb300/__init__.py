@@ -26,6 +26,7 @@ FP64, MIXED = 0, 1
 HF_MEASURE, HF_LENGTH = 0, 1
 COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
 FORM_PROBLEM_3_1, FORM_PROBLEM_B_1 = 0, 1
+PRESSURE_CONTINUOUS, PRESSURE_BROKEN = 0, 1
 PATCH_AUTO, PATCH_DENSE, PATCH_TIME_DIAGONAL = 0, 1, 2
 PATCHES_VERTEX, PATCHES_CELL = 0, 1
 UPDATE_AVERAGE, UPDATE_OVERWRITE = 0, 1
@@ -46,7 +47,7 @@ class Mesh(C.Structure):
 
 
 class Degrees(C.Structure):
-    _fields_ = [("r", C.c_int), ("k", C.c_int), ("form", C.c_int)]
+    _fields_ = [("r", C.c_int), ("k", C.c_int), ("form", C.c_int), ("pressure", C.c_int)]
 
 
 class Material(C.Structure):
@@ -162,7 +163,7 @@ class Problem:
     def __init__(self, dim, n_cells, n_levels, r, k, tau, lo=None, hi=None, rho=1.0, alpha=1.0, c0=1.0,
                  lam=1.0, mu=1.0, kappa=1.0, lam_cell=None, mu_cell=None, kappa_cell=None,
                  bc_u=None, bc_p=None, problem=PROBLEM_NONE, t0=0.0, hf_mode=HF_MEASURE,
-                 coarse_op=COARSE_GALERKIN, form=FORM_PROBLEM_3_1):
+                 coarse_op=COARSE_GALERKIN, form=FORM_PROBLEM_3_1, pressure=PRESSURE_CONTINUOUS):
         self.dim = dim
         lo = list(lo) if lo is not None else [0.0] * dim
         hi = list(hi) if hi is not None else [1.0] * dim
@@ -170,7 +171,7 @@ class Problem:
         self.mesh = Mesh(dim, (C.c_double * 3)(*(lo + [0.0] * (3 - dim))),
                          (C.c_double * 3)(*(hi + [1.0] * (3 - dim))),
                          (C.c_int * 3)(*(n_cells + [1] * (3 - dim))), n_levels, hf_mode, coarse_op)
-        self.deg = Degrees(r, k, form)
+        self.deg = Degrees(r, k, form, pressure)
         self._cells = []
 
         def arr(a):

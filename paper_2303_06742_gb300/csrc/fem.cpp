@@ -358,6 +358,51 @@ RefData ref_data(const Lattice &L, const Box &b, const std::vector<std::array<do
   return R;
 }
 
+// Exponents of the broken P_m basis: total degree <= m, x exponent fastest.
+std::vector<std::array<int, 3>> disc_exponents(int m, int dim) {
+  std::vector<std::array<int, 3>> e;
+  const int ez = dim > 2 ? m : 0, ey = dim > 1 ? m : 0;
+  for (int z = 0; z <= ez; ++z)
+    for (int y = 0; y <= ey; ++y)
+      for (int x = 0; x <= m; ++x)
+        if (x + y + z <= m) e.push_back({x, y, z});
+  return e;
+}
+
+// Reference data of the broken P_m space: products of Legendre polynomials
+// L_a(2 xi - 1) of the reference coordinates.
+RefData ref_data_disc(int m, const Box &b, const std::vector<std::array<double, 3>> &pts) {
+  RefData R;
+  R.dim = b.dim;
+  const auto ex = disc_exponents(m, b.dim);
+  R.nloc = (int)ex.size();
+  R.npts = (int)pts.size();
+  R.loc.assign(R.nloc * 3, 0);
+  R.phi.assign((size_t)R.npts * R.nloc, 0.0);
+  R.dphi.assign((size_t)R.npts * R.nloc * b.dim, 0.0);
+  for (int q = 0; q < R.npts; ++q) {
+    double vals[3][16] = {}, ders[3][16] = {};
+    for (int i = 0; i < b.dim; ++i)
+      for (int a = 0; a <= m; ++a) {
+        double p, dp;
+        legendre(a, 2.0 * pts[q][i] - 1.0, &p, &dp);
+        vals[i][a] = p;
+        ders[i][a] = 2.0 * dp / b.h[i];
+      }
+    for (int l = 0; l < R.nloc; ++l) {
+      double v = 1.0;
+      for (int i = 0; i < b.dim; ++i) v *= vals[i][ex[l][i]];
+      R.phi[(size_t)q * R.nloc + l] = v;
+      for (int j = 0; j < b.dim; ++j) {
+        double g = 1.0;
+        for (int i = 0; i < b.dim; ++i) g *= (i == j) ? ders[i][ex[l][i]] : vals[i][ex[l][i]];
+        R.dphi[((size_t)q * R.nloc + l) * b.dim + j] = g;
+      }
+    }
+  }
+  return R;
+}
+
 std::vector<std::array<double, 3>> cell_points(const Box &b, int nq, std::vector<double> *w) {
   Rule g = gauss01(nq);
   std::vector<std::array<double, 3>> pts;
@@ -395,17 +440,189 @@ std::vector<std::array<double, 3>> face_points(const Box &b, int nq, int ax, int
   return pts;
 }
 
+struct Entry {
+  int col;
+  double v1, v2;
+};
+
+// Spatial system CSR of a level with the broken pressure space.  u- and
+// v-rows take the node-level UU values; the pressure couplings come from the
+// cell-private blocks (C per cell: np x du; (Mp, B) per cell: np x np pairs)
+// and the interior penalty faces between neighbouring cells.
+void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, const std::vector<double> &cellMB,
+                 const RefData &RU, double gam, const BCs &bc, bool b1) {
+  (void)bc;
+  const Box &b = L.box;
+  const int d = b.dim, r = L.r, np = L.pnloc, nu = RU.nloc, du = nu * d;
+  const double rho = L.coef.rho, c0 = L.coef.c0;
+  const long R = L.R, S = L.S, ns = L.ns;
+  std::vector<std::vector<Entry>> rows(ns);
+  // interior penalty faces: block (2 np x 2 np) per face, rows test, cols trial
+  std::vector<std::vector<double>> FB(d); // per axis, for unit kappa split below
+  struct FaceRef {
+    RefData a, b;
+    std::vector<double> w;
+  };
+  std::vector<FaceRef> fr(d);
+  for (int ax = 0; ax < d; ++ax) {
+    std::vector<double> wa, wb;
+    auto pa = face_points(b, r + 2, ax, 1, &wa); // on K+ (the lower cell's upper face)
+    auto pb = face_points(b, r + 2, ax, 0, &wb); // on K- (the upper cell's lower face)
+    fr[ax].a = ref_data_disc(r - 1, b, pa);
+    fr[ax].b = ref_data_disc(r - 1, b, pb);
+    fr[ax].w = wa;
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long row = 0; row < ns; ++row) {
+    std::vector<Entry> &E = rows[row];
+    int a[3];
+    if (row < 2 * R) {
+      const bool vrow = row >= R;
+      const long I = (row % R) / d;
+      const int c = (int)((row % R) % d);
+      unflatten(I, L.U.dims, d, a);
+      NbrBox nbu = nbr_box(a, r, r, b);
+      const double *uu = &UU.val[UU.rowptr[I] * UU.nvals];
+      long t = 0;
+      for (int z = 0; z < nbu.ext[2]; ++z)
+        for (int y = 0; y < nbu.ext[1]; ++y)
+          for (int x = 0; x < nbu.ext[0]; ++x, ++t) {
+            int aj[3] = {nbu.lo[0] + x, nbu.lo[1] + y, nbu.lo[2] + z};
+            const long J = flatten(aj, L.U.dims);
+            const double m = uu[t * UU.nvals];
+            if (!vrow) {
+              E.push_back({(int)(J * d + c), 0.0, -rho * m});
+              E.push_back({(int)(R + J * d + c), rho * m, 0.0});
+            } else {
+              E.push_back({(int)(J * d + c), rho * m, 0.0});
+              for (int cp = 0; cp < d; ++cp) E.push_back({(int)(R + J * d + cp), 0.0, uu[t * UU.nvals + 1 + c * d + cp]});
+            }
+          }
+      if (vrow) {
+        // C^T from every cell holding node I
+        int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) cells_of(a[i], r, b.n[i], &clo[i], &chi[i]);
+        for (int cz = clo[2]; cz <= chi[2]; ++cz)
+          for (int cy = clo[1]; cy <= chi[1]; ++cy)
+            for (int cx = clo[0]; cx <= chi[0]; ++cx) {
+              const int cc[3] = {cx, cy, cz};
+              int l = 0, stride = 1;
+              for (int i = 0; i < d; ++i) {
+                l += (a[i] - r * cc[i]) * stride;
+                stride *= r + 1;
+              }
+              const long cell = flatten(cc, b.n);
+              const double *Cc = cellC.data() + (size_t)cell * np * du;
+              for (int s2 = 0; s2 < np; ++s2) E.push_back({(int)(2 * R + cell * np + s2), 0.0, Cc[s2 * du + l * d + c]});
+            }
+      }
+    } else {
+      const long sI = row - 2 * R, cell = sI / np;
+      const int s2 = (int)(sI % np);
+      int cm[3];
+      unflatten(cell, b.n, d, cm);
+      const double *Cc = cellC.data() + (size_t)cell * np * du;
+      for (int j = 0; j < nu; ++j) {
+        int aj[3];
+        for (int i = 0; i < 3; ++i) aj[i] = i < d ? r * cm[i] + RU.loc[j * 3 + i] : 0;
+        const long J = flatten(aj, L.U.dims);
+        for (int cp = 0; cp < d; ++cp) {
+          const double v = -Cc[s2 * du + j * d + cp];
+          if (b1)
+            E.push_back({(int)(R + J * d + cp), v, 0.0});
+          else
+            E.push_back({(int)(J * d + cp), 0.0, v});
+        }
+      }
+      const double *mb = cellMB.data() + (size_t)cell * np * np * 2;
+      for (int t2 = 0; t2 < np; ++t2)
+        E.push_back({(int)(2 * R + cell * np + t2), c0 * mb[2 * (s2 * np + t2)], mb[2 * (s2 * np + t2) + 1]});
+      // interior faces of this cell: as K+ (neighbour above) and as K- (below)
+      for (int ax = 0; ax < d; ++ax)
+        for (int side = 0; side < 2; ++side) {
+          int cn[3] = {cm[0], cm[1], cm[2]};
+          cn[ax] += side ? 1 : -1;
+          if (cn[ax] < 0 || cn[ax] >= b.n[ax]) continue;
+          const long nb_cell = flatten(cn, b.n);
+          const long lower = side ? cell : nb_cell, upper = side ? nb_cell : cell;
+          const double ka = L.coef.kap[lower], kb = L.coef.kap[upper];
+          const FaceRef &F = fr[ax];
+          const int nq = F.a.npts;
+          // this row's test function is in the lower (side 1) or upper cell
+          for (int q = 0; q < nq; ++q) {
+            const double W = F.w[q];
+            const double *pa = &F.a.phi[(size_t)q * np], *pb = &F.b.phi[(size_t)q * np];
+            const double *ga = &F.a.dphi[(size_t)q * np * d], *gb = &F.b.dphi[(size_t)q * np * d];
+            // test values: jump and flux average of psi_row
+            const double jr = side ? pa[s2] : -pb[s2];
+            const double fr_ = side ? 0.5 * ka * ga[s2 * d + ax] : 0.5 * kb * gb[s2 * d + ax];
+            for (int t2 = 0; t2 < np; ++t2) {
+              // trial functions of the lower cell, then of the upper cell
+              const double js[2] = {pa[t2], -pb[t2]};
+              const double fs[2] = {0.5 * ka * ga[t2 * d + ax], 0.5 * kb * gb[t2 * d + ax]};
+              const long cl[2] = {lower, upper};
+              for (int k = 0; k < 2; ++k) {
+                const double v = W * (-fs[k] * jr - js[k] * fr_ + (gam / b.hF) * js[k] * jr);
+                E.push_back({(int)(2 * R + cl[k] * np + t2), 0.0, v});
+              }
+            }
+          }
+        }
+    }
+    // merge duplicate columns (the own-cell block meets the face blocks)
+    std::sort(E.begin(), E.end(), [](const Entry &x, const Entry &y) { return x.col < y.col; });
+    size_t o = 0;
+    for (size_t i = 0; i < E.size(); ++i) {
+      if (o > 0 && E[o - 1].col == E[i].col) {
+        E[o - 1].v1 += E[i].v1;
+        E[o - 1].v2 += E[i].v2;
+      } else {
+        E[o++] = E[i];
+      }
+    }
+    E.resize(o);
+  }
+  L.rowptr.assign(ns + 1, 0);
+  for (long i = 0; i < ns; ++i) L.rowptr[i + 1] = L.rowptr[i] + (int)rows[i].size();
+  const long nnz = L.rowptr[ns];
+  L.col.resize(nnz);
+  L.v1.resize(nnz);
+  L.v2.resize(nnz);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long i = 0; i < ns; ++i) {
+    long e = L.rowptr[i];
+    for (const Entry &x : rows[i]) {
+      L.col[e] = x.col;
+      L.v1[e] = x.v1;
+      L.v2[e] = x.v2;
+      ++e;
+    }
+  }
+  (void)S;
+  (void)FB;
+}
+
 } // namespace
 
-Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int form) {
+Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int form, int pressure) {
   Level L;
   L.form = form;
   L.box = b;
   L.r = r;
   L.coef = coef;
   L.U = make_lattice(b, r);
-  L.P = make_lattice(b, r - 1);
   const int d = b.dim;
+  const bool disc = pressure == STFEM_PRESSURE_BROKEN;
+  L.pdisc = disc;
+  if (disc) {
+    L.pnloc = (int)disc_exponents(r - 1, d).size();
+    L.P = Lattice();
+    L.P.dim = d;
+    L.P.m = r - 1;
+    L.P.nnodes = b.ncell * L.pnloc;
+  } else {
+    L.P = make_lattice(b, r - 1);
+  }
   L.R = (long)d * L.U.nnodes;
   L.S = L.P.nnodes;
   L.ns = 2 * L.R + L.S;
@@ -415,7 +632,7 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
   // reference element data
   std::vector<double> wq;
   auto pts = cell_points(b, r + 2, &wq);
-  RefData RU = ref_data(L.U, b, pts), RP = ref_data(L.P, b, pts);
+  RefData RU = ref_data(L.U, b, pts), RP = disc ? ref_data_disc(r - 1, b, pts) : ref_data(L.P, b, pts);
   const int nu = RU.nloc, np = RP.nloc, nq = RU.npts, du = nu * d;
   // unit-coefficient element matrices
   std::vector<double> Mu(nu * nu, 0), Kmu(du * du, 0), Klam(du * du, 0), Cv(np * du, 0), Bv(np * np, 0),
@@ -463,7 +680,7 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
       fm.Bpen.assign(np * np, 0);
       std::vector<double> wf;
       auto fp = face_points(b, r + 2, ax, side, &wf);
-      RefData FU = ref_data(L.U, b, fp), FP = ref_data(L.P, b, fp);
+      RefData FU = ref_data(L.U, b, fp), FP = disc ? ref_data_disc(r - 1, b, fp) : ref_data(L.P, b, fp);
       double n[3] = {0, 0, 0};
       n[ax] = side ? 1.0 : -1.0;
       for (int q = 0; q < (int)fp.size(); ++q) {
@@ -506,12 +723,20 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
 
   // node-level matrices
   NodeMat UU = make_nodemat(L.U, L.U, b, 1 + d * d); // M, K[c][c']
-  NodeMat UP = make_nodemat(L.U, L.P, b, d);         // C^T: C[s][(I,c)]
-  NodeMat PU = make_nodemat(L.P, L.U, b, d);         // C[s][(J,c')]
-  NodeMat PP = make_nodemat(L.P, L.P, b, 2);         // Mp, B
+  NodeMat UP, PU, PP;                               // C^T: C[s][(I,c)]; C[s][(J,c')]; Mp, B
   const bool b1 = form == STFEM_FORM_PROBLEM_B_1;
   NodeMat PUv; // volume part of C (Problem B.1 only)
-  if (b1) PUv = make_nodemat(L.P, L.U, b, d);
+  // broken pressure space: the cell-local blocks C (np x du) and (Mp, B)
+  std::vector<double> cellC, cellMB;
+  if (disc) {
+    cellC.assign((size_t)b.ncell * np * du, 0.0);
+    cellMB.assign((size_t)b.ncell * np * np * 2, 0.0);
+  } else {
+    UP = make_nodemat(L.U, L.P, b, d);
+    PU = make_nodemat(L.P, L.U, b, d);
+    PP = make_nodemat(L.P, L.P, b, 2);
+    if (b1) PUv = make_nodemat(L.P, L.U, b, d);
+  }
   // cells in 2^d colour classes by the parity of their coordinates: cells of
   // one class share no node, so a class is scattered in parallel
   std::vector<std::vector<long>> colour(1 << d);
@@ -556,12 +781,13 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
       for (int i = 0; i < 3; ++i) gu_[l][i] = (i < d) ? r * cm[i] + RU.loc[l * 3 + i] : 0;
       giu[l] = flatten(gu_[l], L.U.dims);
     }
-    for (int l = 0; l < np; ++l) {
-      for (int i = 0; i < 3; ++i) gp_[l][i] = (i < d) ? (r - 1) * cm[i] + RP.loc[l * 3 + i] : 0;
-      gip[l] = flatten(gp_[l], L.P.dims);
-    }
+    if (!disc)
+      for (int l = 0; l < np; ++l) {
+        for (int i = 0; i < 3; ++i) gp_[l][i] = (i < d) ? (r - 1) * cm[i] + RP.loc[l * 3 + i] : 0;
+        gip[l] = flatten(gp_[l], L.P.dims);
+      }
     for (int i = 0; i < nu; ++i) {
-      NbrBox nbu = nbr_box(gu_[i], r, r, b), nbp = nbr_box(gu_[i], r, r - 1, b);
+      NbrBox nbu = nbr_box(gu_[i], r, r, b);
       for (int j = 0; j < nu; ++j) {
         long e = UU.rowptr[giu[i]] + nbr_pos(nbu, gu_[j]);
         double *v = &UU.val[e * UU.nvals];
@@ -569,10 +795,21 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
         for (int c = 0; c < d; ++c)
           for (int cp = 0; cp < d; ++cp) v[1 + c * d + cp] += Ke[(i * d + c) * du + j * d + cp];
       }
+      if (disc) continue;
+      NbrBox nbp = nbr_box(gu_[i], r, r - 1, b);
       for (int s = 0; s < np; ++s) {
         long e = UP.rowptr[giu[i]] + nbr_pos(nbp, gp_[s]);
         for (int c = 0; c < d; ++c) UP.val[e * d + c] += Ce[s * du + i * d + c];
       }
+    }
+    if (disc) { // cell-private blocks: no scatter
+      std::copy(Ce.begin(), Ce.end(), cellC.begin() + (size_t)c * np * du);
+      double *mb = cellMB.data() + (size_t)c * np * np * 2;
+      for (int i = 0; i < np * np; ++i) {
+        mb[2 * i] = Mp[i];
+        mb[2 * i + 1] = Be[i];
+      }
+      continue;
     }
     for (int s = 0; s < np; ++s) {
       NbrBox nbu = nbr_box(gp_[s], r - 1, r, b), nbp = nbr_box(gp_[s], r - 1, r - 1, b);
@@ -595,6 +832,10 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
   // expand to the spatial system CSR (rows u-eq, v-eq, p-eq; cols V, U, P)
   const double rho = coef.rho, c0 = coef.c0;
   const long R = L.R, S = L.S, ns = L.ns;
+  if (disc) {
+    expand_disc(L, UU, cellC, cellMB, RU, gam_b, bc, b1);
+    return L;
+  }
   L.rowptr.assign(ns + 1, 0);
   int a[3];
   for (long I = 0; I < L.U.nnodes; ++I) {
@@ -751,6 +992,63 @@ CSR prolongation(const Lattice &cl, const Box &cb, const Lattice &fl, const Box 
     P.rowptr[f + 1] = (int)P.col.size();
   }
   (void)cb;
+  return P;
+}
+
+CSR prolongation_disc(int m, const Box &cb, const Box &fb) {
+  // on each fine cell, the parent's basis function (a polynomial of degree m
+  // there) expanded in the fine cell's orthogonal Legendre basis:
+  // coef_j = <phi_i^coarse, phi_j^fine> / <phi_j^fine, phi_j^fine>, by
+  // Gauss quadrature exact for the products
+  const int d = fb.dim;
+  const auto ex = disc_exponents(m, d);
+  const int nl = (int)ex.size();
+  const Rule g = gauss01(m + 2);
+  const int nq = (int)g.x.size();
+  CSR P;
+  P.nrows = fb.ncell * nl;
+  P.ncols = cb.ncell * nl;
+  P.rowptr.assign(P.nrows + 1, 0);
+  // 1D tables: fine Legendre values at the nodes, coarse values at the
+  // matching coarse points for offset o in {0, 1}
+  std::vector<double> lf((size_t)(m + 1) * nq), lc[2];
+  for (int o = 0; o < 2; ++o) lc[o].resize((size_t)(m + 1) * nq);
+  for (int a = 0; a <= m; ++a)
+    for (int k = 0; k < nq; ++k) {
+      double p, dp;
+      legendre(a, 2.0 * g.x[k] - 1.0, &p, &dp);
+      lf[a * nq + k] = p;
+      for (int o = 0; o < 2; ++o) {
+        legendre(a, 2.0 * ((o + g.x[k]) / 2.0) - 1.0, &p, &dp);
+        lc[o][a * nq + k] = p;
+      }
+    }
+  // the expansion separates by axis: coef = prod_i <Lc_{e_i}, Lf_{f_i}>_i / <Lf_{f_i}, Lf_{f_i}>_i
+  auto c1 = [&](int o, int ec, int ef) {
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < nq; ++k) {
+      num += g.w[k] * lc[o][ec * nq + k] * lf[ef * nq + k];
+      den += g.w[k] * lf[ef * nq + k] * lf[ef * nq + k];
+    }
+    return num / den;
+  };
+  int cf[3], cc[3];
+  for (long f = 0; f < fb.ncell; ++f) {
+    unflatten(f, fb.n, d, cf);
+    for (int i = 0; i < 3; ++i) cc[i] = i < d ? cf[i] / 2 : 0;
+    const long ccell = flatten(cc, cb.n);
+    for (int j = 0; j < nl; ++j) {
+      const long row = f * nl + j;
+      for (int i = 0; i < nl; ++i) {
+        double w = 1.0;
+        for (int ax = 0; ax < d; ++ax) w *= c1(cf[ax] - 2 * cc[ax], ex[i][ax], ex[j][ax]);
+        if (std::fabs(w) <= 1e-14) continue;
+        P.col.push_back((int)(ccell * nl + i));
+        P.val.push_back(w);
+      }
+      P.rowptr[row + 1] = (int)P.col.size();
+    }
+  }
   return P;
 }
 
@@ -1375,12 +1673,28 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
           int a[3] = {x, y, z};
           un.push_back(flatten(a, L.U.dims));
         }
-    for (int z = plo[2]; z <= phi[2]; ++z)
-      for (int y = plo[1]; y <= phi[1]; ++y)
-        for (int x = plo[0]; x <= phi[0]; ++x) {
-          int a[3] = {x, y, z};
-          pn.push_back(flatten(a, L.P.dims));
-        }
+    if (L.pdisc) {
+      // the dofs of every cell of the patch (each supported in its cell)
+      int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+      for (int i = 0; i < d; ++i) {
+        clo[i] = kind == 1 ? v[i] : std::max(v[i] - 1, 0);
+        chi[i] = kind == 1 ? v[i] : std::min(v[i], b.n[i] - 1);
+      }
+      for (int z = clo[2]; z <= chi[2]; ++z)
+        for (int y = clo[1]; y <= chi[1]; ++y)
+          for (int x = clo[0]; x <= chi[0]; ++x) {
+            int cc[3] = {x, y, z};
+            const long cell = flatten(cc, b.n);
+            for (int l = 0; l < L.pnloc; ++l) pn.push_back(cell * L.pnloc + l);
+          }
+    } else {
+      for (int z = plo[2]; z <= phi[2]; ++z)
+        for (int y = plo[1]; y <= phi[1]; ++y)
+          for (int x = plo[0]; x <= phi[0]; ++x) {
+            int a[3] = {x, y, z};
+            pn.push_back(flatten(a, L.P.dims));
+          }
+    }
     std::vector<int> &sp = spatial[p];
     for (long I : un)
       for (int c = 0; c < d; ++c) sp.push_back((int)(I * d + c));
@@ -1588,6 +1902,10 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
     *err = "invalid form";
     return STFEM_ERR_ARG;
   }
+  if (deg->pressure != STFEM_PRESSURE_CONTINUOUS && deg->pressure != STFEM_PRESSURE_BROKEN) {
+    *err = "invalid pressure space";
+    return STFEM_ERR_ARG;
+  }
   for (int i = 0; i < d; ++i) {
     if (mesh->n_cells[i] < 1 || (mesh->n_cells[i] % (1 << (mesh->n_levels - 1))) != 0 ||
         !(mesh->hi[i] > mesh->lo[i])) {
@@ -1651,19 +1969,30 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
       Lv.form = deg->form;
       Lv.coef = coefs[l];
       Lv.U = make_lattice(boxes[l], deg->r);
-      Lv.P = make_lattice(boxes[l], deg->r - 1);
+      if (deg->pressure == STFEM_PRESSURE_BROKEN) {
+        Lv.pdisc = true;
+        Lv.pnloc = (int)disc_exponents(deg->r - 1, d).size();
+        Lv.P = Lattice();
+        Lv.P.dim = d;
+        Lv.P.m = deg->r - 1;
+        Lv.P.nnodes = boxes[l].ncell * Lv.pnloc;
+      } else {
+        Lv.P = make_lattice(boxes[l], deg->r - 1);
+      }
       Lv.R = (long)d * Lv.U.nnodes;
       Lv.S = Lv.P.nnodes;
       Lv.ns = 2 * Lv.R + Lv.S;
     } else {
-      (*levels)[l] = assemble_level(boxes[l], deg->r, coefs[l], bc, deg->form);
+      (*levels)[l] = assemble_level(boxes[l], deg->r, coefs[l], bc, deg->form, deg->pressure);
     }
   }
   Pu->assign(nlev, CSR());
   Pp->assign(nlev, CSR());
   for (int l = 1; l < nlev; ++l) {
     (*Pu)[l] = prolongation((*levels)[l - 1].U, boxes[l - 1], (*levels)[l].U, boxes[l]);
-    (*Pp)[l] = prolongation((*levels)[l - 1].P, boxes[l - 1], (*levels)[l].P, boxes[l]);
+    (*Pp)[l] = deg->pressure == STFEM_PRESSURE_BROKEN
+                   ? prolongation_disc(deg->r - 1, boxes[l - 1], boxes[l])
+                   : prolongation((*levels)[l - 1].P, boxes[l - 1], (*levels)[l].P, boxes[l]);
   }
   if (galerkin_ops)
     for (int l = nlev - 1; l >= 1; --l) galerkin((*levels)[l], (*Pu)[l], (*Pp)[l], &(*levels)[l - 1]);

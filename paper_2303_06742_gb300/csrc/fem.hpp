@@ -100,10 +100,19 @@ struct Level {
   // p-rows' entries): the previous-slab coupling of Problem B.1 uses it.
   int form = 0;
   std::vector<double> cvol;
+  // STFEM_PRESSURE_BROKEN: P is P_{r-1}^disc, numbered cell by cell (cells x
+  // fastest, pnloc dofs each: Legendre products of total degree <= r-1, x
+  // exponent fastest); P.nnodes counts its dofs and P.dims is unused.
+  bool pdisc = false;
+  int pnloc = 0;
   // per lattice node: spatial position, for initial values and loads
 };
 
-Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc, int form = 0);
+Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc, int form = 0, int pressure = 0);
+// Embedding of the broken P_m space of the coarse box into that of the fine
+// box (nested; fine rows, coarse columns).
+struct CSR;
+CSR prolongation_disc(int m, const Box &cb, const Box &fb);
 
 // Scalar interpolation coarse Q_m -> fine Q_m (fine rows), CSR.
 struct CSR {

@@ -144,6 +144,10 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
     g_host_err = "invalid sizes";
     return STFEM_ERR_ARG;
   }
+  if (deg->pressure != STFEM_PRESSURE_CONTINUOUS) {
+    g_host_err = "the broken pressure pair has no device path";
+    return STFEM_ERR_ARG;
+  }
   const bool mixed = gmg->precision == STFEM_MIXED;
   int form = gmg->patch_form;
   if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;

@@ -3519,6 +3519,10 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
     return STFEM_ERR_ARG;
   }
   *out = nullptr;
+  if (deg && deg->pressure != STFEM_PRESSURE_CONTINUOUS) {
+    g_setup_err = "the broken pressure pair has a host setup only (no device path)";
+    return STFEM_ERR_ARG;
+  }
   stfem_h h = new stfem_ctx();
   cudaGetDevice(&h->device);
   {

@@ -53,7 +53,7 @@ CASES = [
 ]
 
 
-def _pair(case, seed=0, coarse_op=0, form=0):
+def _pair(case, seed=0, coarse_op=0, form=0, pressure="cont"):
     dim, n, L, r, k, lo, hi, bcu, bcp, hf = case
     rng = np.random.default_rng(seed)
     nc = n ** dim
@@ -64,24 +64,27 @@ def _pair(case, seed=0, coarse_op=0, form=0):
     prob = stfem.Problem(dim, n, L, r, k, tau, lo=lo, hi=hi, rho=1.3, alpha=0.8, c0=0.2,
                          lam_cell=lam, mu_cell=mu, kappa_cell=kap, bc_u=bcu, bc_p=bcp,
                          hf_mode=stfem.HF_MEASURE if hf == "measure" else stfem.HF_LENGTH,
-                         coarse_op=coarse_op, form=form)
+                         coarse_op=coarse_op, form=form,
+                         pressure=stfem.PRESSURE_BROKEN if pressure == "disc" else stfem.PRESSURE_CONTINUOUS)
     meshes = [BoxMesh(dim, lo, hi, [n] * dim, hf)]
     mats = [Material(1.3, 0.8, 0.2, lam, mu, kap)]
     for _ in range(L - 1):
         mats.append(mats[-1].coarsen(meshes[-1]))
         meshes.append(meshes[-1].coarsen())
-    ops = [SpatialOps(m, r, mt, bcu, bcp) for m, mt in zip(meshes[::-1], mats[::-1])]
+    ops = [SpatialOps(m, r, mt, bcu, bcp, pressure) for m, mt in zip(meshes[::-1], mats[::-1])]
     return prob, ops, Temporal(k), tau
 
 
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("form", ["3.1", "B.1"])
 @pytest.mark.parametrize("coarse", ["rediscretize", "galerkin"])
 @pytest.mark.parametrize("case", CASES)
-def test_level_matrices_match_oracle(case, coarse, form):
+def test_level_matrices_match_oracle(case, coarse, form, pressure):
     from oracle.gmg import slab_prolongation
     prob, ops, T, tau = _pair(case, coarse_op=stfem.COARSE_GALERKIN if coarse == "galerkin"
                               else stfem.COARSE_REDISCRETIZE,
-                              form=stfem.FORM_PROBLEM_3_1 if form == "3.1" else stfem.FORM_PROBLEM_B_1)
+                              form=stfem.FORM_PROBLEM_3_1 if form == "3.1" else stfem.FORM_PROBLEM_B_1,
+                              pressure=pressure)
     mats = [slab_matrix(o, T, tau, form) for o in ops]
     if coarse == "galerkin":
         for l in range(len(ops) - 1, 0, -1):
@@ -102,9 +105,10 @@ def test_level_matrices_match_oracle(case, coarse, form):
         assert abs(D @ (abs(A) - abs(B))).max() <= 1e-12
 
 
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("case", CASES)
-def test_patch_sets_match_oracle(case):
-    prob, ops, T, tau = _pair(case)
+def test_patch_sets_match_oracle(case, pressure):
+    prob, ops, T, tau = _pair(case, pressure=pressure)
     for level in range(1, len(ops)):
         host = stfem.host_patch_dofs(prob, level)
         ora = [patch_dofs(ops[level], T, v) for v in vertices(ops[level].mesh)]
@@ -113,9 +117,10 @@ def test_patch_sets_match_oracle(case):
             assert np.array_equal(np.sort(a), np.sort(b))
 
 
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("case", CASES)
-def test_cell_patch_sets_match_oracle(case):
-    prob, ops, T, tau = _pair(case)
+def test_cell_patch_sets_match_oracle(case, pressure):
+    prob, ops, T, tau = _pair(case, pressure=pressure)
     for level in range(1, len(ops)):
         host = stfem.host_patch_dofs(prob, level, stfem.PATCHES_CELL)
         ora = [cell_patch_dofs(ops[level], T, c) for c in cells(ops[level].mesh)]
@@ -124,9 +129,10 @@ def test_cell_patch_sets_match_oracle(case):
             assert np.array_equal(np.sort(a), np.sort(b))
 
 
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("case", CASES)
-def test_prolongations_match_oracle(case):
-    prob, ops, T, tau = _pair(case)
+def test_prolongations_match_oracle(case, pressure):
+    prob, ops, T, tau = _pair(case, pressure=pressure)
     for level in range(1, len(ops)):
         for field, (sc, sf) in enumerate([(ops[level - 1].Vs, ops[level].Vs), (ops[level - 1].Qs, ops[level].Qs)]):
             rp, ci, va, shape = stfem.host_prolongation(prob, level, field)
@@ -183,3 +189,13 @@ def test_coarse_inverse_rejects_singular():
     A = np.ones((600, 600))
     with pytest.raises(stfem.StfemError):
         stfem.host_invert(A)
+
+
+def test_broken_pressure_has_no_device_path():
+    """The broken pair is host setup only: the footprint estimate (and so the
+    serving admission) refuses it, as stfem_setup does."""
+    prob = stfem.Problem(2, 4, 2, 2, 1, 0.01, pressure=stfem.PRESSURE_BROKEN)
+    with pytest.raises(stfem.StfemError):
+        stfem.estimate_bytes(prob, stfem.MIXED)
+    rp, ci, va, n = stfem.host_level_matrix(prob, -1)
+    assert n == 2 * (2 * 2 * 9 * 9 + 16 * 3)  # q (2 d (2n+1)^2 + cells x dim P1)
