@@ -450,15 +450,13 @@ struct Entry {
 // cell-private blocks (C per cell: np x du; (Mp, B) per cell: np x np pairs)
 // and the interior penalty faces between neighbouring cells.
 void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, const std::vector<double> &cellMB,
-                 const RefData &RU, double gam, const BCs &bc, bool b1) {
-  (void)bc;
+                 const RefData &RU, double gam, bool b1) {
   const Box &b = L.box;
   const int d = b.dim, r = L.r, np = L.pnloc, nu = RU.nloc, du = nu * d;
   const double rho = L.coef.rho, c0 = L.coef.c0;
-  const long R = L.R, S = L.S, ns = L.ns;
+  const long R = L.R, ns = L.ns;
   std::vector<std::vector<Entry>> rows(ns);
-  // interior penalty faces: block (2 np x 2 np) per face, rows test, cols trial
-  std::vector<std::vector<double>> FB(d); // per axis, for unit kappa split below
+  // reference data of the broken basis on both sides of a face, per axis
   struct FaceRef {
     RefData a, b;
     std::vector<double> w;
@@ -598,8 +596,6 @@ void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, 
       ++e;
     }
   }
-  (void)S;
-  (void)FB;
 }
 
 } // namespace
@@ -833,7 +829,7 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
   const double rho = coef.rho, c0 = coef.c0;
   const long R = L.R, S = L.S, ns = L.ns;
   if (disc) {
-    expand_disc(L, UU, cellC, cellMB, RU, gam_b, bc, b1);
+    expand_disc(L, UU, cellC, cellMB, RU, gam_b, b1);
     return L;
   }
   L.rowptr.assign(ns + 1, 0);
