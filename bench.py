@@ -156,7 +156,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, watts = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         rows = [l for ts, l in self.lines if t0 - 0.25 <= ts <= t1 + 0.25] or [l for _, l in self.lines]
         for line in rows:
@@ -168,11 +168,28 @@ class ClockSampler:
                 smax = float(parts[1])
             except ValueError:
                 continue
+            try:
+                watts.append(float(parts[2]))
+            except ValueError:
+                pass
             for nm, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(watts) if watts else None}
+
+
+def energy_per_step(clk, ms_per_step):
+    """Board energy per step: the median board power sampled during the timed
+    region times the device time of a step (the GPU analogue of the paper's
+    energy figures; coarse when the region holds few 200 ms samples)."""
+    w = clk.get("power_w")
+    if w is None:
+        return None
+    return {"j_per_step": w * ms_per_step / 1000.0, "power_w": w, "samples": clk.get("samples"),
+            "method": "median nvidia-smi power.draw of this rank's GPU during the timed region x device time "
+                      "per step"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -427,6 +444,7 @@ def gpu_arm(args):
         "speedup_mixed_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
         "gpu_launches": launches,
         "clocks": clk,
+        "energy": energy_per_step(clk, total_ms / K),
     }
     print(json.dumps(out))
 
@@ -606,6 +624,7 @@ def batch_arm(args):
                      "traffic": None, "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
                      "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"]},
         "breakdown": breakdown, "gpu_launches": launches, "clocks": clk,
+        "energy": energy_per_step(clk, total_ms / K),
     }))
 
 
