@@ -137,13 +137,15 @@ def test_gmg_fgmres_matches_direct_solve():
     assert all(e2 < 0.9 * e1 for e1, e2 in zip(errs, errs[1:]))
 
 
-def test_energy_decays_without_data():
+@pytest.mark.parametrize("pressure,r", [("cont", 2), ("disc", 3)])
+def test_energy_decays_without_data(pressure, r):
     """Lemma 3.2's argument applied with zero data: testing Eq. 3.5 with
     (A_gamma u, v, p) gives E(t_n) + 2 Q_n(B_gamma(p,p)) <= E(t_{n-1}),
-    E = A_gamma(u,u) + rho |v|^2 + c0 |p|^2, so E is non-increasing."""
+    E = A_gamma(u,u) + rho |v|^2 + c0 |p|^2, so E is non-increasing (for the
+    broken pressure pair too, where B_gamma is the interior penalty form)."""
     mesh = BoxMesh(2, [0, 0], [1, 1], [4, 4])
     mat = Material.uniform(mesh, 1.0, 0.9, 0.1, 2.0, 1.0, 0.5)
-    ops = SpatialOps(mesh, 2, mat, [0] * 4, [0] * 4)
+    ops = SpatialOps(mesh, r, mat, [0] * 4, [0] * 4, pressure)
     T = Temporal(1)
     lu = spla.splu(slab_matrix(ops, T, 0.05).tocsc())
     rng = np.random.default_rng(4)
