@@ -470,6 +470,13 @@ int stfem_host_invert(int n, double *a_host);
 const char *stfem_last_error(stfem_h h);
 
 /* Message of the last failed stfem_host_* call on this thread. */
+/* y = A_n x (Eq. 4.7) of a level, computed on the host from the node-block
+ * arrays the device operator reads (either pressure space, either slab
+ * form): a CPU check of that layout.  x, y: host, n_slab of the level.
+ * STFEM_ERR_STATE if the level matrix does not fit the layout. */
+int stfem_host_block_apply(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                           const stfem_bcs *bcs, double tau, int level, const double *x_host, double *y_host);
+
 const char *stfem_host_last_error(void);
 
 /* Frees every resource of the handle.  NULL is ignored. */

@@ -111,6 +111,8 @@ def _load():
         "stfem_initial_state_at": [P, D, P],
         "stfem_host_level_matrix": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                     C.POINTER(BCs), D, I, pLL, pLL, pLL, pI, pD],
+        "stfem_host_block_apply": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material), C.POINTER(BCs), D,
+                                   I, pD, pD],
         "stfem_host_patch_dofs": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                   C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pI],
         "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
@@ -210,6 +212,14 @@ def host_level_matrix(prob, level=-1):
                                             rp.ctypes.data_as(C.POINTER(C.c_longlong)),
                                             ci.ctypes.data_as(C.POINTER(C.c_int)), _dptr(va)))
     return rp, ci, va, n.value
+
+
+def host_block_apply(prob, x, level=-1):
+    """A_n x of a level from the device layout of the level operator, on the host."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    _host_check(lib.stfem_host_block_apply(*prob.args(), level, _dptr(x), _dptr(y)))
+    return y
 
 
 def host_patch_dofs(prob, level=-1, patch_kind=PATCHES_VERTEX):

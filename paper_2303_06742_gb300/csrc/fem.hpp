@@ -174,6 +174,12 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
 void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, hvec<double> *out,
                           std::vector<long long> *off);
 
+// y = A_n x of a level (q time nodes; Dt and W of Eq. 4.7) computed on the
+// host from the node-block arrays the device operator reads (defined with the
+// kernels): a CPU check of that layout.  x, y: host, q * ns.
+int block_apply_level(const Level &L, int q, const double *Dt, const double *W, const double *x, double *y,
+                      std::string *err);
+
 // Dense row-major slab matrix of a level (for the coarse solve).
 std::vector<double> dense_slab(const Level &L, const Temporal &T, double tau);
 // In-place Gauss-Jordan inverse with partial pivoting of a row-major n x n

@@ -104,6 +104,27 @@ int stfem_host_patch_dofs(const stfem_mesh *mesh, const stfem_degrees *deg, cons
   return STFEM_OK;
 }
 
+int stfem_host_block_apply(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                           const stfem_bcs *bcs, double tau, int level, const double *x, double *y) {
+  if (!x || !y) {
+    g_host_err = "null argument";
+    return STFEM_ERR_ARG;
+  }
+  std::vector<stfem::Level> L;
+  std::vector<stfem::CSR> Pu, Pp;
+  int rc = build(mesh, deg, mat, bcs, tau, &L, &Pu, &Pp);
+  if (rc < 0) return rc;
+  if (level == -1) level = (int)L.size() - 1;
+  if (level < 0 || level >= (int)L.size()) {
+    g_host_err = "level out of range";
+    return STFEM_ERR_ARG;
+  }
+  const stfem::Temporal T = stfem::make_temporal(deg->k);
+  std::vector<double> W(T.q);
+  for (int b = 0; b < T.q; ++b) W[b] = 0.5 * tau * T.w[b];
+  return stfem::block_apply_level(L[level], T.q, T.Dt.data(), W.data(), x, y, &g_host_err);
+}
+
 int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
                             const stfem_bcs *bcs, double tau, int level, int field, long long *nrows,
                             long long *ncols, long long *nnz, long long *rowptr, int *col, double *val) {

@@ -1792,6 +1792,13 @@ struct NodeBlockHost {
   long nu = 0, np = 0;
   std::vector<int> uu_ptr, up_ptr, pu_ptr, pp_ptr;
   std::vector<double> uu_m, uu_k, up_c, pu_c, pp_m, pp_b;
+  // broken pressure space: the "pressure nodes" are the pnl dofs of each cell;
+  // up_c runs over the cells holding a displacement node (x fastest) times
+  // pnl, pu_c over the (r+1)^d nodes of the dof's cell, pp_* over 2d+1 cell
+  // slots (own cell, then the lower and upper neighbour along each axis; a
+  // missing neighbour keeps zeros) times pnl
+  bool pdisc = false;
+  int pnl = 0;
 };
 
 struct HostBox {
@@ -1834,6 +1841,22 @@ static long box_pos(const HostBox &b, long j, const int *dims, int dim) {
   return pos;
 }
 
+// flat index of box element e (x fastest) in lattice dims
+static long box_node_host(const HostBox &b, long e, const int *dims) {
+  const long ex = e % b.ext[0], t = e / b.ext[0];
+  const long ey = t % b.ext[1], ez = t / b.ext[1];
+  return (b.lo[0] + ex) + (long)dims[0] * ((b.lo[1] + ey) + (long)dims[1] * (b.lo[2] + ez));
+}
+
+static long stfem_flat(const int *a, const int *dims, int dim) {
+  long idx = 0, stride = 1;
+  for (int i = 0; i < dim; ++i) {
+    idx += a[i] * stride;
+    stride *= dims[i];
+  }
+  return idx;
+}
+
 static void coords_of(long idx, const int *dims, int dim, int *a) {
   for (int i = 0; i < 3; ++i) {
     if (i < dim) {
@@ -1845,14 +1868,40 @@ static void coords_of(long idx, const int *dims, int dim, int *a) {
   }
 }
 
+// Cells holding lattice node a of degree m: a box of cells, as a HostBox
+// over the cell grid.
+static HostBox cell_box(const int *a, int m, const int *ncell, int dim) {
+  HostBox b;
+  b.size = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      int clo, chi;
+      stfem::cells_of(a[i], m, ncell[i], &clo, &chi);
+      b.lo[i] = clo;
+      b.ext[i] = chi - clo + 1;
+    } else {
+      b.lo[i] = 0;
+      b.ext[i] = 1;
+    }
+    b.size *= b.ext[i];
+  }
+  return b;
+}
+
 int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *err) {
   NodeBlockHost &H = *out;
   const long R = L.R, S = L.S, nu = R / d, np = S;
   const int r = L.r;
   const bool b1 = L.form == STFEM_FORM_PROBLEM_B_1;
+  const bool disc = L.pdisc;
+  const int pnl = L.pnloc;
+  int nuloc = 1;
+  for (int i = 0; i < d; ++i) nuloc *= r + 1;
   const int *ud = L.U.dims, *pd = L.P.dims, *nc = L.box.n;
   H.nu = nu;
   H.np = np;
+  H.pdisc = disc;
+  H.pnl = pnl;
   H.uu_ptr.assign(nu + 1, 0);
   H.up_ptr.assign(nu + 1, 0);
   H.pu_ptr.assign(np + 1, 0);
@@ -1861,9 +1910,14 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
   for (long I = 0; I < nu; ++I) {
     coords_of(I, ud, d, a);
     H.uu_ptr[I + 1] = H.uu_ptr[I] + (int)host_box(a, r, r, nc, d).size;
-    H.up_ptr[I + 1] = H.up_ptr[I] + (int)host_box(a, r, r - 1, nc, d).size;
+    H.up_ptr[I + 1] = H.up_ptr[I] + (int)(disc ? cell_box(a, r, nc, d).size * pnl : host_box(a, r, r - 1, nc, d).size);
   }
   for (long sI = 0; sI < np; ++sI) {
+    if (disc) {
+      H.pu_ptr[sI + 1] = H.pu_ptr[sI] + nuloc;
+      H.pp_ptr[sI + 1] = H.pp_ptr[sI] + (2 * d + 1) * pnl;
+      continue;
+    }
     coords_of(sI, pd, d, a);
     H.pu_ptr[sI + 1] = H.pu_ptr[sI] + (int)host_box(a, r - 1, r, nc, d).size;
     H.pp_ptr[sI + 1] = H.pp_ptr[sI] + (int)host_box(a, r - 1, r - 1, nc, d).size;
@@ -1884,7 +1938,8 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
   };
   for (long I = 0; I < nu; ++I) {
     coords_of(I, ud, d, a);
-    const HostBox bu = host_box(a, r, r, nc, d), bp = host_box(a, r, r - 1, nc, d);
+    const HostBox bu = host_box(a, r, r, nc, d);
+    const HostBox bp = disc ? HostBox{} : host_box(a, r, r - 1, nc, d), cb = disc ? cell_box(a, r, nc, d) : HostBox{};
     for (int c = 0; c < d; ++c) {
       // u-equation row (I, c): V block -rho M (W), U block rho M (Dt), same component
       const long ru = I * d + c;
@@ -1929,6 +1984,11 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
           const long pos = box_pos(bu, (col - R) / d, ud, d);
           if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("elasticity entry outside the box");
           H.uu_k[((size_t)H.uu_ptr[I] + pos) * d * d + c * d + (col - R) % d] = L.v2[e];
+        } else if (disc) {
+          const long cell = (col - 2 * R) / pnl, sl = (col - 2 * R) % pnl;
+          const long pos = box_pos(cb, cell, nc, d);
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("coupling entry outside the cells of the node");
+          H.up_c[((size_t)H.up_ptr[I] + pos * pnl + sl) * d + c] = L.v2[e];
         } else {
           const long pos = box_pos(bp, col - 2 * R, pd, d);
           if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("coupling entry outside the box");
@@ -1937,7 +1997,48 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
       }
     }
   }
-  for (long sI = 0; sI < np; ++sI) {
+  for (long sI = 0; disc && sI < np; ++sI) {
+    // broken pressure dof s of cell `cell`
+    const long cell = sI / pnl;
+    int cm[3];
+    coords_of(cell, nc, d, cm);
+    const long rp = 2 * R + sI;
+    for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
+      const long col = L.col[e];
+      if ((!b1 && col < R) || (b1 && col >= R && col < 2 * R)) {
+        const long rem = b1 ? col - R : col, J = rem / d;
+        int aj[3];
+        coords_of(J, ud, d, aj);
+        int j = 0, stride = 1;
+        bool in = true;
+        for (int i = 0; i < d; ++i) {
+          const int o = aj[i] - r * cm[i];
+          in = in && o >= 0 && o <= r;
+          j += o * stride;
+          stride *= r + 1;
+        }
+        if (!in || std::fabs(b1 ? L.v2[e] : L.v1[e]) > tol) return bad("p-equation displacement entry outside its cell");
+        H.pu_c[((size_t)H.pu_ptr[sI] + j) * d + rem % d] = b1 ? L.v1[e] : L.v2[e];
+      } else if (col >= 2 * R) {
+        const long cell2 = (col - 2 * R) / pnl, t = (col - 2 * R) % pnl;
+        int c2[3];
+        coords_of(cell2, nc, d, c2);
+        int slot = -1, diff = 0;
+        for (int i = 0; i < d; ++i) diff += std::abs(c2[i] - cm[i]);
+        if (diff == 0) slot = 0;
+        else if (diff == 1)
+          for (int i = 0; i < d; ++i)
+            if (c2[i] != cm[i]) slot = 1 + 2 * i + (c2[i] > cm[i] ? 1 : 0);
+        if (slot < 0) return bad("p-equation pressure entry outside the face neighbours");
+        const size_t at = (size_t)H.pp_ptr[sI] + (size_t)slot * pnl + t;
+        H.pp_m[at] = L.v1[e];
+        H.pp_b[at] = L.v2[e];
+      } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
+        return bad(b1 ? "p-equation couples to V" : "p-equation couples to U");
+      }
+    }
+  }
+  for (long sI = 0; !disc && sI < np; ++sI) {
     coords_of(sI, pd, d, a);
     const HostBox bu = host_box(a, r - 1, r, nc, d), bp = host_box(a, r - 1, r - 1, nc, d);
     const long rp = 2 * R + sI;
@@ -1962,6 +2063,112 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
     }
   }
   return 0;
+}
+
+// Host model of the node-block product y = (Dt (x) S1 + W (x) S2) x of
+// k_spmv_nb on the arrays node_block builds (FP64, one node after another;
+// neighbour addresses from the boxes, as the kernel computes them).  It
+// checks the layout on the CPU, for either pressure space.
+static void block_apply_host(const NodeBlockHost &H, const stfem::Level &L, int d, int q, const double *Dt,
+                             const double *W, const double *x, double *y) {
+  const long R = L.R, ns = L.ns, nu = H.nu;
+  const int r = L.r, pnl = H.pnl;
+  const bool b1 = L.form == STFEM_FORM_PROBLEM_B_1;
+  const int *ud = L.U.dims, *pd = L.P.dims, *nc = L.box.n;
+  int a[3];
+  for (long I = 0; I < nu; ++I) {
+    coords_of(I, ud, d, a);
+    const HostBox bu = host_box(a, r, r, nc, d);
+    // per time node: rho M U, rho M V, K U, C^T P, each d components
+    std::vector<double> mu(q * d, 0.0), mv(q * d, 0.0), ku(q * d, 0.0), cp(q * d, 0.0);
+    for (int e = H.uu_ptr[I]; e < H.uu_ptr[I + 1]; ++e) {
+      const long J = box_node_host(bu, e - H.uu_ptr[I], ud);
+      for (int t = 0; t < q; ++t)
+        for (int c = 0; c < d; ++c) {
+          mu[t * d + c] += H.uu_m[e] * x[t * ns + R + J * d + c];
+          mv[t * d + c] += H.uu_m[e] * x[t * ns + J * d + c];
+          for (int c2 = 0; c2 < d; ++c2) ku[t * d + c] += H.uu_k[((size_t)e * d + c) * d + c2] * x[t * ns + R + J * d + c2];
+        }
+    }
+    for (int e = H.up_ptr[I]; e < H.up_ptr[I + 1]; ++e) {
+      long sI;
+      if (H.pdisc) {
+        const HostBox cb = cell_box(a, r, nc, d);
+        const int k = e - H.up_ptr[I];
+        sI = box_node_host(cb, k / pnl, nc) * pnl + k % pnl;
+      } else {
+        sI = box_node_host(host_box(a, r, r - 1, nc, d), e - H.up_ptr[I], pd);
+      }
+      for (int t = 0; t < q; ++t)
+        for (int c = 0; c < d; ++c) cp[t * d + c] += H.up_c[(size_t)e * d + c] * x[t * ns + 2 * R + sI];
+    }
+    for (int b = 0; b < q; ++b)
+      for (int c = 0; c < d; ++c) {
+        double vu = 0.0, vv = 0.0;
+        for (int t = 0; t < q; ++t) {
+          vu += Dt[b * q + t] * mu[t * d + c];
+          vv += Dt[b * q + t] * mv[t * d + c];
+        }
+        y[b * ns + I * d + c] = vu - W[b] * mv[b * d + c];
+        y[b * ns + R + I * d + c] = vv + W[b] * (ku[b * d + c] + cp[b * d + c]);
+      }
+  }
+  const long uoff = b1 ? R : 0;
+  for (long sI = 0; sI < H.np; ++sI) {
+    std::vector<double> mp(q, 0.0), bp(q, 0.0), cn(q, 0.0);
+    if (H.pdisc) {
+      const long cell = sI / pnl;
+      int cm[3];
+      coords_of(cell, nc, d, cm);
+      for (int e = H.pu_ptr[sI]; e < H.pu_ptr[sI + 1]; ++e) {
+        const int j = e - H.pu_ptr[sI];
+        int aj[3] = {0, 0, 0}, t = j;
+        for (int i = 0; i < d; ++i) {
+          aj[i] = r * cm[i] + t % (r + 1);
+          t /= r + 1;
+        }
+        const long J = stfem_flat(aj, ud, d);
+        for (int tt = 0; tt < q; ++tt)
+          for (int c = 0; c < d; ++c) cn[tt] += H.pu_c[(size_t)e * d + c] * x[tt * ns + uoff + J * d + c];
+      }
+      for (int slot = 0; slot < 2 * d + 1; ++slot) {
+        int c2[3] = {cm[0], cm[1], cm[2]};
+        if (slot > 0) c2[(slot - 1) / 2] += (slot - 1) % 2 ? 1 : -1;
+        bool in = true;
+        for (int i = 0; i < d; ++i) in = in && c2[i] >= 0 && c2[i] < nc[i];
+        if (!in) continue;
+        const long cell2 = stfem_flat(c2, nc, d);
+        for (int tl = 0; tl < pnl; ++tl) {
+          const size_t e = (size_t)H.pp_ptr[sI] + (size_t)slot * pnl + tl;
+          for (int tt = 0; tt < q; ++tt) {
+            const double pv = x[tt * ns + 2 * R + cell2 * pnl + tl];
+            mp[tt] += H.pp_m[e] * pv;
+            bp[tt] += H.pp_b[e] * pv;
+          }
+        }
+      }
+    } else {
+      coords_of(sI, pd, d, a);
+      const HostBox bpx = host_box(a, r - 1, r - 1, nc, d), bux = host_box(a, r - 1, r, nc, d);
+      for (int e = H.pp_ptr[sI]; e < H.pp_ptr[sI + 1]; ++e) {
+        const long s2 = box_node_host(bpx, e - H.pp_ptr[sI], pd);
+        for (int tt = 0; tt < q; ++tt) {
+          mp[tt] += H.pp_m[e] * x[tt * ns + 2 * R + s2];
+          bp[tt] += H.pp_b[e] * x[tt * ns + 2 * R + s2];
+        }
+      }
+      for (int e = H.pu_ptr[sI]; e < H.pu_ptr[sI + 1]; ++e) {
+        const long J = box_node_host(bux, e - H.pu_ptr[sI], ud);
+        for (int tt = 0; tt < q; ++tt)
+          for (int c = 0; c < d; ++c) cn[tt] += H.pu_c[(size_t)e * d + c] * x[tt * ns + uoff + J * d + c];
+      }
+    }
+    for (int b = 0; b < q; ++b) {
+      double v = W[b] * (bp[b] + (b1 ? 0.0 : cn[b]));
+      for (int t = 0; t < q; ++t) v += Dt[b * q + t] * (mp[t] + (b1 ? cn[t] : 0.0));
+      y[b * ns + 2 * R + sI] = v;
+    }
+  }
 }
 
 template <typename T>
@@ -3426,6 +3633,15 @@ int fail_setup(stfem_h h, int rc) {
 }
 
 } // namespace
+
+int stfem::block_apply_level(const stfem::Level &L, int q, const double *Dt, const double *W, const double *x,
+                             double *y, std::string *err) {
+  NodeBlockHost H;
+  const int d = L.box.dim;
+  if (node_block(L, d, &H, err) < 0) return STFEM_ERR_STATE;
+  block_apply_host(H, L, d, q, Dt, W, x, y);
+  return STFEM_OK;
+}
 
 // ---------------------------------------------------------------- allocation-free smoothing
 // Scratch of stfem_smooth_noalloc: one static array per device that loads the

@@ -106,6 +106,29 @@ def test_level_matrices_match_oracle(case, coarse, form, pressure):
 
 
 @pytest.mark.parametrize("pressure", ["cont", "disc"])
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
+@pytest.mark.parametrize("case", CASES)
+def test_device_layout_reproduces_the_oracle_operator(case, form, pressure):
+    """The node-block arrays the device SpMV reads (neighbour addresses from
+    boxes; cell boxes and face slots for the broken pressure space), applied on
+    the host with the kernel's arithmetic, give the oracle's A_n x on every
+    level (Galerkin coarse levels included)."""
+    from oracle.gmg import slab_prolongation
+    prob, ops, T, tau = _pair(case, form=stfem.FORM_PROBLEM_3_1 if form == "3.1" else stfem.FORM_PROBLEM_B_1,
+                              pressure=pressure)
+    mats = [slab_matrix(o, T, tau, form) for o in ops]
+    for l in range(len(ops) - 1, 0, -1):
+        P = slab_prolongation(ops[l - 1], ops[l], T)
+        mats[l - 1] = (P.T @ mats[l] @ P).tocsr()
+    rng = np.random.default_rng(17)
+    for level, A in enumerate(mats):
+        x = rng.standard_normal(A.shape[0])
+        y = stfem.host_block_apply(prob, x, level)
+        scale = abs(A) @ np.abs(x)
+        assert np.max(np.abs(y - A @ x) / np.maximum(scale, 1e-300)) < 1e-13, level
+
+
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("case", CASES)
 def test_patch_sets_match_oracle(case, pressure):
     prob, ops, T, tau = _pair(case, pressure=pressure)
