@@ -78,6 +78,7 @@ struct NodeBlockDev {
   long nu, np;
   int r;                       // displacement degree (pressure degree r - 1)
   int pcouple;                 // 0: Cn on V through W (3.1); 1: on U through Dt (B.1)
+  int pdisc, pnl;              // broken pressure space: pnl dofs per cell (see disc_* below)
   int n[3];                    // cells per axis of the level
   int udims[3], pdims[3];      // lattice sizes of Q_r and Q_{r-1}
   const int *uu_ptr, *up_ptr, *pu_ptr, *pp_ptr;
@@ -133,7 +134,53 @@ __device__ __forceinline__ void lattice_coords(long idx, const int *dims, int di
   }
 }
 
-template <typename T, int Q, int D, int G>
+// Broken pressure space (P_{r-1}^disc, pnl dofs per cell, numbered cell by
+// cell).  A displacement node couples to the dofs of the cells around it: a
+// box of cells (x fastest) times pnl.  A pressure dof couples to the (r+1)^D
+// nodes of its cell (x fastest) and to 2D+1 cell slots times pnl: its own
+// cell, then the lower and upper face neighbour along each axis.
+__device__ __forceinline__ Box3 disc_cell_box(const int *a, int r, const int *ncell, int dim) {
+  Box3 b;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < dim) {
+      int clo, chi;
+      if (a[i] % r == 0) {
+        clo = max(a[i] / r - 1, 0);
+        chi = min(a[i] / r, ncell[i] - 1);
+      } else {
+        clo = chi = a[i] / r;
+      }
+      b.lo[i] = clo;
+      b.ext[i] = chi - clo + 1;
+    } else {
+      b.lo[i] = 0;
+      b.ext[i] = 1;
+    }
+  }
+  return b;
+}
+
+// Cell of slot `slot` next to cell cm, or -1 past the boundary.
+__device__ __forceinline__ long disc_slot_cell(const int *cm, int slot, const int *ncell, int dim) {
+  int c2[3] = {cm[0], cm[1], cm[2]};
+  if (slot > 0) c2[(slot - 1) / 2] += ((slot - 1) % 2) ? 1 : -1;
+  for (int i = 0; i < dim; ++i)
+    if (c2[i] < 0 || c2[i] >= ncell[i]) return -1;
+  return (long)c2[0] + (long)ncell[0] * (c2[1] + (long)ncell[1] * c2[2]);
+}
+
+// Displacement node j (x fastest over (r+1)^dim) of cell cm.
+__device__ __forceinline__ long disc_cell_node(const int *cm, int j, int r, const int *udims, int dim) {
+  int aj[3] = {0, 0, 0};
+  for (int i = 0; i < dim; ++i) {
+    aj[i] = r * cm[i] + j % (r + 1);
+    j /= r + 1;
+  }
+  return (long)aj[0] + (long)udims[0] * (aj[1] + (long)udims[1] * aj[2]);
+}
+
+template <typename T, int Q, int D, int G, bool PD = false>
 __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
                                                  const T *__restrict__ x, const T *__restrict__ rhs,
                                                  T *__restrict__ y, int mode, int nb, long cstride) {
@@ -195,10 +242,11 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
           }
       }
     }
-    const Box3 bp = node_box(a, A.r, A.r - 1, A.n, D);
+    const Box3 bp = PD ? disc_cell_box(a, A.r, A.n, D) : node_box(a, A.r, A.r - 1, A.n, D);
     const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
     for (int e = f0 + lane; e < f1; e += G) {
-      const long sI = box_node(bp, e - f0, A.pdims);
+      const long sI = PD ? box_node(bp, (e - f0) / A.pnl, A.n) * A.pnl + (e - f0) % A.pnl
+                         : box_node(bp, e - f0, A.pdims);
       T ct[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
@@ -207,6 +255,39 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
         const T pv = x[(long)a * ns + 2 * R + sI];
 #pragma unroll
         for (int c = 0; c < D; ++c) acc[(3 * Q + a) * D + c] += ct[c] * pv;
+      }
+    }
+  } else if (PD && is_p) {
+    // broken pressure dof: acc layout as below
+    const long sI = node - A.nu, cell = sI / A.pnl;
+    int cm[3];
+    lattice_coords(cell, A.n, D, cm);
+    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
+    for (int e = e0p + lane; e < e1; e += G) {
+      const long c2 = disc_slot_cell(cm, (e - e0p) / A.pnl, A.n, D);
+      if (c2 < 0) continue;
+      const long s2 = c2 * A.pnl + (e - e0p) % A.pnl;
+      const T m = A.pp_m[e], bb = A.pp_b[e];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const T pv = x[(long)a * ns + 2 * R + s2];
+        acc[a] += m * pv;
+        acc[Q + a] += bb * pv;
+      }
+    }
+    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    const long uoff = A.pcouple ? R : 0;
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long J = disc_cell_node(cm, e - f0, A.r, A.udims, D);
+      T cn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        T t = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
+        acc[2 * Q + a] += t;
       }
     }
   } else if (is_p) {
@@ -340,7 +421,7 @@ struct TimeCoefDF {
   float2 Dt[MAXQ * MAXQ], W[MAXQ], mW[MAXQ];
 };
 
-template <int Q, int D, int G>
+template <int Q, int D, int G, bool PD = false>
 __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns, long R, TimeCoefDF tc,
                                                  const float *__restrict__ x, double *__restrict__ y, int nb,
                                                  long cstride) {
@@ -385,10 +466,11 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
         }
       }
     }
-    const Box3 bp = node_box(a, A.r, A.r - 1, A.n, D);
+    const Box3 bp = PD ? disc_cell_box(a, A.r, A.n, D) : node_box(a, A.r, A.r - 1, A.n, D);
     const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
     for (int e = f0 + lane; e < f1; e += G) {
-      const long sI = box_node(bp, e - f0, A.pdims);
+      const long sI = PD ? box_node(bp, (e - f0) / A.pnl, A.n) * A.pnl + (e - f0) % A.pnl
+                         : box_node(bp, e - f0, A.pdims);
       float2 ct[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
@@ -398,6 +480,36 @@ __global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns
 #pragma unroll
         for (int c = 0; c < D; ++c) df_madd(acc[(3 * Q + t) * D + c], ct[c], pv);
       }
+    }
+  } else if (PD && is_p) {
+    // broken pressure dof (see k_spmv_nb)
+    const long sI = node - A.nu, cell = sI / A.pnl;
+    int cm[3];
+    lattice_coords(cell, A.n, D, cm);
+    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
+    for (int e = e0p + lane; e < e1; e += G) {
+      const long c2 = disc_slot_cell(cm, (e - e0p) / A.pnl, A.n, D);
+      if (c2 < 0) continue;
+      const long s2 = c2 * A.pnl + (e - e0p) % A.pnl;
+      const float2 m = A.pp_m[e], bb = A.pp_b[e];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const float pv = x[(long)t * ns + 2 * R + s2];
+        df_madd(acc[t], m, pv);
+        df_madd(acc[Q + t], bb, pv);
+      }
+    }
+    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
+    const long uoff = A.pcouple ? R : 0;
+    for (int e = f0 + lane; e < f1; e += G) {
+      const long J = disc_cell_node(cm, e - f0, A.r, A.udims, D);
+      float2 cn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
+#pragma unroll
+      for (int t = 0; t < Q; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + uoff + J * D + c]);
     }
   } else if (is_p) {
     // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
@@ -1707,8 +1819,12 @@ void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, c
                     int mode, int nb) {
   constexpr int G = SpmvLanes<T, D>::G;
   const long threads = (L.nb.nu + L.nb.np) * G;
-  k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode, nb,
-                                                                    L.N);
+  if (D == 2 && L.nb.pdisc) // broken pressure space (2D)
+    k_spmv_nb<T, Q, D, G, D == 2><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode,
+                                                                              nb, L.N);
+  else
+    k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode, nb,
+                                                                      L.N);
 }
 
 template <typename T, int Q>
@@ -1760,7 +1876,10 @@ void launch_spmv_df_qd(cudaStream_t s, const DLevel<double> &L, const TimeCoef<d
     td.W[b] = pair(tc.W[b]);
     td.mW[b] = pair(-tc.W[b]);
   }
-  k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
+  if (D == 2 && L.nbdf.pdisc) // broken pressure space (2D)
+    k_spmv_df<Q, D, G, D == 2><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
+  else
+    k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
 }
 
 // y = A x on the finest FP64 level in double-float arithmetic, x FP32 (nb
@@ -2189,6 +2308,8 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
   nb.np = H.np;
   nb.r = L.r;
   nb.pcouple = L.form == STFEM_FORM_PROBLEM_B_1 ? 1 : 0;
+  nb.pdisc = H.pdisc ? 1 : 0;
+  nb.pnl = H.pnl;
   for (int i = 0; i < 3; ++i) {
     nb.n[i] = L.box.n[i];
     nb.udims[i] = L.U.dims[i];
@@ -2247,6 +2368,8 @@ int upload_level_df(stfem_h h, DLevel<double> &D, const stfem::Level &L) {
   nb.np = D.nb.np;
   nb.r = D.nb.r;
   nb.pcouple = D.nb.pcouple;
+  nb.pdisc = D.nb.pdisc;
+  nb.pnl = D.nb.pnl;
   for (int i = 0; i < 3; ++i) {
     nb.n[i] = D.nb.n[i];
     nb.udims[i] = D.nb.udims[i];
