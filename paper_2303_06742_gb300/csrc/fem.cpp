@@ -991,6 +991,27 @@ CSR prolongation(const Lattice &cl, const Box &cb, const Lattice &fl, const Box 
   return P;
 }
 
+int disc_basis(int m, int dim, const double *xi, int npts, std::vector<double> *phi) {
+  const auto ex = disc_exponents(m, dim);
+  const int nl = (int)ex.size();
+  phi->assign((size_t)npts * nl, 0.0);
+  for (int q = 0; q < npts; ++q) {
+    double vals[3][16] = {};
+    for (int i = 0; i < dim; ++i)
+      for (int a = 0; a <= m; ++a) {
+        double p, dp;
+        legendre(a, 2.0 * xi[3 * q + i] - 1.0, &p, &dp);
+        vals[i][a] = p;
+      }
+    for (int l = 0; l < nl; ++l) {
+      double v = 1.0;
+      for (int i = 0; i < dim; ++i) v *= vals[i][ex[l][i]];
+      (*phi)[(size_t)q * nl + l] = v;
+    }
+  }
+  return nl;
+}
+
 CSR prolongation_disc(int m, const Box &cb, const Box &fb) {
   // on each fine cell, the parent's basis function (a polynomial of degree m
   // there) expanded in the fine cell's orthogonal Legendre basis:

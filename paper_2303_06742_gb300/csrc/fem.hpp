@@ -174,6 +174,11 @@ int build_patches(const Level &L, const Temporal &T, double tau, int vec, Patche
 void extract_patch_blocks(const Level &L, const Patches &P, int q, long p0, long p1, hvec<double> *out,
                           std::vector<long long> *off);
 
+// Values of the broken P_m basis (Legendre products of total degree <= m,
+// x exponent fastest) at npts reference points xi[3 * i + axis] of the unit
+// cell: phi[i * nloc + l].  Returns nloc.
+int disc_basis(int m, int dim, const double *xi, int npts, std::vector<double> *phi);
+
 // y = A_n x of a level (q time nodes; Dt and W of Eq. 4.7) computed on the
 // host from the node-block arrays the device operator reads (defined with the
 // kernels): a CPU check of that layout.  x, y: host, q * ns.

@@ -42,6 +42,11 @@ struct LoadTables {
   const double *fphiU;
   const double *lam, *mu, *kap; // per fine cell
   int top_neumann;
+  // broken pressure space: phiP holds its basis at the load points (nlp
+  // dofs per cell), and the initial pressure is the L2 projection per cell
+  // with the rule (pqx, pqw) of npq points and the basis values phiPP
+  int pdisc, npq;
+  const double *pqx, *pqw, *phiPP;
 };
 
 struct CSRDev {

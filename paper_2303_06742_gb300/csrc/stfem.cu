@@ -1496,11 +1496,33 @@ __device__ double dev_top_traction(const ProbDev &P, const double *x, double t) 
   return 0.0;
 }
 
-// state = nodal interpolation of (v, u, p) at time t
-__global__ void k_interp(GeomDev g, ProbDev P, double t, long R, long S, double *__restrict__ state) {
+// state = nodal interpolation of (v, u, p) at time t; a broken pressure
+// space takes the L2 projection of p on each cell (orthogonal basis: one
+// quotient per dof)
+__global__ void k_interp(GeomDev g, ProbDev P, LoadTables L, double t, long R, long S, double *__restrict__ state) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * R + S) return;
   double x[3], u[3], v[3], p;
+  if (L.pdisc && i >= 2 * R) {
+    const long cell = (i - 2 * R) / L.nlp;
+    const int s = (int)((i - 2 * R) % L.nlp);
+    int cm[3] = {0, 0, 0};
+    long t2 = cell;
+    for (int k = 0; k < g.dim; ++k) {
+      cm[k] = (int)(t2 % g.n[k]);
+      t2 /= g.n[k];
+    }
+    double num = 0.0, den = 0.0;
+    for (int qq = 0; qq < L.npq; ++qq) {
+      for (int k = 0; k < 3; ++k) x[k] = k < g.dim ? g.lo[k] + g.h[k] * (cm[k] + L.pqx[qq * 3 + k]) : 0.0;
+      dev_fields(P, x, t, u, v, &p);
+      const double ph = L.phiPP[(long)qq * L.nlp + s];
+      num += L.pqw[qq] * p * ph;
+      den += L.pqw[qq] * ph * ph;
+    }
+    state[i] = num / den;
+    return;
+  }
   if (i < 2 * R) {
     const long rem = i % R;
     node_coord(g, g.r, g.udims, g.refU, rem / g.dim, x);
@@ -1560,6 +1582,17 @@ __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double
     const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
     const int d = g.dim;
     const bool urow = m < 2 * R;
+    if (!urow && L.pdisc) {
+      // broken pressure dof: the load of its own cell alone
+      const long ncell = (long)g.n[0] * g.n[1] * g.n[2];
+      const long cell = (m - 2 * R) / L.nlp;
+      const int li = (int)((m - 2 * R) % L.nlp);
+      const double *sv = src + (((long)b * ncell + cell) * L.nq) * 4 + 3;
+      double load = 0.0;
+      for (int qq = 0; qq < L.nq; ++qq) load += L.qw[qq] * sv[qq * 4] * L.phiP[(long)qq * L.nlp + li];
+      out[i] = val + tc.W[b] * load;
+      return;
+    }
     const int deg = urow ? g.r : g.r - 1;
     const int *dims = urow ? g.udims : g.pdims;
     const long node = urow ? (m - R) / d : m - 2 * R;
@@ -3723,7 +3756,7 @@ int build_load_tables(stfem_h h) {
     }
     return out;
   };
-  std::vector<double> phiU = tab(L.U, qx), phiP = tab(L.P, qx);
+  std::vector<double> phiU = tab(L.U, qx), phiP;
   std::vector<double> fphiU = d == 3 ? tab(L.U, fx) : std::vector<double>(1, 0.0);
   int nlu = 1, nlp = 1;
   for (int i = 0; i < d; ++i) {
@@ -3731,6 +3764,31 @@ int build_load_tables(stfem_h h) {
     nlp *= h->r;
   }
   LoadTables &lt = h->lt;
+  std::vector<double> pqx, pqw, phiPP;
+  if (L.pdisc) {
+    nlp = stfem::disc_basis(h->r - 1, d, qx.data(), (int)qw.size(), &phiP);
+    // projection rule: Gauss with r + 3 points per direction (weights of the
+    // reference cell: the cell measure cancels in the projection)
+    const int np1 = h->r + 3;
+    stfem::Rule gp = stfem::gauss01(np1);
+    const int pz = d > 2 ? np1 : 1, py = d > 1 ? np1 : 1;
+    for (int z = 0; z < pz; ++z)
+      for (int y = 0; y < py; ++y)
+        for (int x = 0; x < np1; ++x) {
+          pqx.push_back(gp.x[x]);
+          pqx.push_back(d > 1 ? gp.x[y] : 0.0);
+          pqx.push_back(d > 2 ? gp.x[z] : 0.0);
+          pqw.push_back(gp.w[x] * (d > 1 ? gp.w[y] : 1.0) * (d > 2 ? gp.w[z] : 1.0));
+        }
+    stfem::disc_basis(h->r - 1, d, pqx.data(), (int)pqw.size(), &phiPP);
+  } else {
+    phiP = tab(L.P, qx);
+    pqx.assign(3, 0.0);
+    pqw.assign(1, 0.0);
+    phiPP.assign(1, 0.0);
+  }
+  lt.pdisc = L.pdisc ? 1 : 0;
+  lt.npq = L.pdisc ? (int)pqw.size() : 0;
   lt.nq = (int)qw.size();
   lt.nlu = nlu;
   lt.nlp = nlp;
@@ -3746,6 +3804,9 @@ int build_load_tables(stfem_h h) {
   CKR(upload(h, &p, L.coef.lam)); lt.lam = p;
   CKR(upload(h, &p, L.coef.mu)); lt.mu = p;
   CKR(upload(h, &p, L.coef.kap)); lt.kap = p;
+  CKR(upload(h, &p, pqx)); lt.pqx = p;
+  CKR(upload(h, &p, pqw)); lt.pqw = p;
+  CKR(upload(h, &p, phiPP)); lt.phiPP = p;
   return 0;
 }
 
@@ -4231,7 +4292,7 @@ int stfem_initial_state_at(stfem_h h, double t, double *state) {
   const stfem::Level &F = h->hl.back();
   {
     Launch G_(h, STFEM_KCLASS_OTHER, F.ns * 8.0, 0.0);
-    k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, t, F.R, F.S, state);
+    k_interp<<<grid_for(F.ns, 256), 256, 0, h->stream>>>(h->geom, h->prob, h->lt, t, F.R, F.S, state);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
