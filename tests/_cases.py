@@ -10,7 +10,7 @@ def _cells(c):
     return n, int(np.prod(n))
 
 
-def gpu_problem(c, hf_mode=0, form=0):
+def gpu_problem(c, hf_mode=0, form=0, pressure=0):
     import paper_2303_06742_gb300 as st
     n, nc = _cells(c)
     pid = {"sin": st.PROBLEM_SIN, "pulse": st.PROBLEM_PULSE, "none": st.PROBLEM_NONE,
@@ -19,11 +19,11 @@ def gpu_problem(c, hf_mode=0, form=0):
                       rho=c["rho"], alpha=c["alpha"], c0=c["c0"], lam=c.get("lam", 1.0), mu=c.get("mu", 1.0),
                       kappa=c.get("kappa", 1.0), lam_cell=c.get("lam_cell"), mu_cell=c.get("mu_cell"),
                       kappa_cell=c.get("kappa_cell"), bc_u=c.get("bc_u"), bc_p=c.get("bc_p"), problem=pid,
-                      t0=c.get("t0", 0.0), hf_mode=hf_mode, form=form)
+                      t0=c.get("t0", 0.0), hf_mode=hf_mode, form=form, pressure=pressure)
 
 
 def oracle_instance(c, omega=0.7, nsweeps=1, hf="measure", **variant):
-    """``variant``: patches, averaging, absolute, form (oracle.solver.Instance)."""
+    """``variant``: patches, averaging, absolute, form, pressure (oracle.solver.Instance)."""
     from oracle.space import Material
     from oracle.solver import Instance
     from oracle import problems as P
