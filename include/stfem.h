@@ -98,8 +98,8 @@ typedef struct {
  * CONTINUOUS: Q_{r-1}, the Taylor-Hood pair Q_r^d / Q_{r-1} (default).
  * BROKEN: P_{r-1}^disc, polynomials of total degree r-1 on each cell, with the
  *   interior penalty form B_gamma over interior faces and Dirichlet faces of p
- *   (gamma = r (r-1) / 2).  Host setup only (stfem_host_* inspection calls):
- *   stfem_setup and stfem_estimate_bytes return STFEM_ERR_ARG for it. */
+ *   (gamma = r (r-1) / 2).  Host setup and footprint estimate only for now:
+ *   stfem_setup and stfem_server_submit return STFEM_ERR_ARG for it. */
 #define STFEM_PRESSURE_CONTINUOUS 0
 #define STFEM_PRESSURE_BROKEN 1
 

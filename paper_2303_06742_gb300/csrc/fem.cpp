@@ -830,6 +830,17 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
   const long R = L.R, S = L.S, ns = L.ns;
   if (disc) {
     expand_disc(L, UU, cellC, cellMB, RU, gam_b, b1);
+    if (b1) {
+      // -Cvol per pressure dof over its cell's nodes (the layout of the
+      // device's p-row coupling); the volume element matrix is the same on
+      // every cell
+      L.cvol.resize((size_t)L.S * nu * d);
+      for (long sI = 0; sI < L.S; ++sI) {
+        const int sl = (int)(sI % np);
+        for (int j = 0; j < nu; ++j)
+          for (int cp = 0; cp < d; ++cp) L.cvol[((size_t)sI * nu + j) * d + cp] = -Cv[sl * du + j * d + cp];
+      }
+    }
     return L;
   }
   L.rowptr.assign(ns + 1, 0);

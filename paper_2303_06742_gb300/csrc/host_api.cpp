@@ -165,10 +165,9 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
     g_host_err = "invalid sizes";
     return STFEM_ERR_ARG;
   }
-  if (deg->pressure != STFEM_PRESSURE_CONTINUOUS) {
-    g_host_err = "the broken pressure pair has no device path";
-    return STFEM_ERR_ARG;
-  }
+  const bool disc = deg->pressure == STFEM_PRESSURE_BROKEN;
+  int pnl = 1; // dofs per cell of P_{r-1}^disc: binomial(r - 1 + d, d)
+  for (int i = 1; i <= d; ++i) pnl = pnl * (r - 1 + i) / i;
   const bool mixed = gmg->precision == STFEM_MIXED;
   int form = gmg->patch_form;
   if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
@@ -189,6 +188,7 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
       nv *= n[i] + 1;
       ncell *= n[i];
     }
+    if (disc) np = ncell * pnl;
     const double ns = 2.0 * d * nu + np, N = q * ns;
     if (l == L - 1) {
       Nfine = N;
@@ -197,18 +197,26 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
     }
     // node-block operator (largest boxes): FP64 always, FP32 copy in mixed mode
     const double b1 = std::pow(2 * r + 1, d), b2 = std::pow(2 * r - 1, d);
-    const double mat = nu * b1 * (1 + d * d) + nu * b2 * d + np * b1 * d + np * b2 * 2;
+    // broken pressure: a node couples to <= 2^d cells' dofs, a dof to its
+    // cell's (r+1)^d nodes and to 2d+1 cell slots
+    const double mat = disc ? nu * b1 * (1 + d * d) + nu * std::pow(2.0, d) * pnl * d +
+                                  np * std::pow(r + 1, d) * d + np * (2 * d + 1) * pnl * 2
+                            : nu * b1 * (1 + d * d) + nu * b2 * d + np * b1 * d + np * b2 * 2;
     total += mat * 8.0 + (nu + np + 2) * 8.0 + 3.0 * N * 8.0;
     if (mixed) total += mat * 4.0 + (nu + np + 2) * 8.0 + 3.0 * N * 4.0;
     // transfers to the next coarser level (P and P^T, both precisions)
     if (l >= 1) {
-      const double tr = (nu * std::pow(r + 1, d) + np * std::pow(r, d)) * 2.0;
+      const double tr = (nu * std::pow(r + 1, d) + np * (disc ? pnl : std::pow(r, d))) * 2.0;
       total += tr * (4.0 + 8.0) + 2.0 * (nu + np + 2) * 4.0;
       if (mixed) total += tr * (4.0 + 4.0) + 2.0 * (nu + np + 2) * 4.0;
     }
     // patches (levels >= 1): exact patch sizes per vertex (or per cell)
     if (l >= 1) {
       const bool cellk = gmg->patch_kind == STFEM_PATCHES_CELL;
+      auto axis_cells = [cellk](long v, long ncl) {
+        if (cellk) return 1.0;
+        return (double)(std::min(v, ncl - 1) - std::max(v - 1, 0L) + 1);
+      };
       auto axis_nodes = [cellk](long v, long ncl, int m) {
         if (cellk) return (double)(m + 1);
         const long c0 = std::max(v - 1, 0L), c1 = std::min(v, ncl - 1);
@@ -222,15 +230,16 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
       for (long z = 0; z < vz; ++z)
         for (long y = 0; y < vy; ++y)
           for (long x = 0; x < vx; ++x) {
-            double u = axis_nodes(x, n[0], r), pp = axis_nodes(x, n[0], r - 1);
+            double u = axis_nodes(x, n[0], r), pp = disc ? axis_cells(x, n[0]) : axis_nodes(x, n[0], r - 1);
             if (d > 1) {
               u *= axis_nodes(y, n[1], r);
-              pp *= axis_nodes(y, n[1], r - 1);
+              pp *= disc ? axis_cells(y, n[1]) : axis_nodes(y, n[1], r - 1);
             }
             if (d > 2) {
               u *= axis_nodes(z, n[2], r);
-              pp *= axis_nodes(z, n[2], r - 1);
+              pp *= disc ? axis_cells(z, n[2]) : axis_nodes(z, n[2], r - 1);
             }
+            if (disc) pp *= pnl;
             const double Cs = 2.0 * d * u + pp, C = q * Cs;
             sumC += C;
             if (form == STFEM_PATCH_TIME_DIAGONAL) {
@@ -243,6 +252,9 @@ int stfem_estimate_bytes(const stfem_mesh *mesh, const stfem_degrees *deg, const
       total += inv * sp + sumC * (4.0 + sp + 4.0) + nv * (4 + 4 + 8 + 8 + 4) + (N + 1) * 4.0 + N * sp;
     }
     if (l == 0) total += N * N * 8.0; // dense coarse inverse
+    // Problem B.1: the fine level's volume coupling (FP64)
+    if (l == L - 1 && deg->form == STFEM_FORM_PROBLEM_B_1)
+      total += (disc ? np * std::pow(r + 1, d) : np * b1) * d * 8.0;
   }
   // Krylov workspace and march buffers
   const double m = restart;

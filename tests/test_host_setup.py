@@ -173,8 +173,9 @@ def test_setup_rejects_bad_arguments():
         stfem.host_level_matrix(bad)
 
 
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
 @pytest.mark.parametrize("name", ["c1_2d_q2_k1_8", "c3_small_3d_q2_k1_4"])
-def test_footprint_estimate_covers_the_patch_inverses(name):
+def test_footprint_estimate_covers_the_patch_inverses(name, pressure):
     """The admission estimate of the serving loop (no setup, sizes only) must
     hold at least the patch inverses that setup stores: sum over levels >= 1
     and patches of C_P^2 values (C_P from the host patch lists), in either
@@ -182,7 +183,8 @@ def test_footprint_estimate_covers_the_patch_inverses(name):
     import inputs
     from _cases import gpu_problem
     c = dict(inputs.case(name))
-    prob = gpu_problem(c)
+    pr = stfem.PRESSURE_BROKEN if pressure == "disc" else stfem.PRESSURE_CONTINUOUS
+    prob = gpu_problem(c, pressure=pr)
     for precision, size in ((stfem.FP64, 8), (stfem.MIXED, 4)):
         est = stfem.estimate_bytes(prob, precision)
         inv = 0
@@ -190,7 +192,8 @@ def test_footprint_estimate_covers_the_patch_inverses(name):
             inv += sum(len(p) ** 2 for p in stfem.host_patch_dofs(prob, level)) * size
         assert est >= inv > 0
     c_small = dict(c, n=c["n"] // 2, levels=c["levels"] - 1)
-    assert stfem.estimate_bytes(gpu_problem(c_small), stfem.MIXED) < stfem.estimate_bytes(prob, stfem.MIXED)
+    assert stfem.estimate_bytes(gpu_problem(c_small, pressure=pr), stfem.MIXED) < stfem.estimate_bytes(prob,
+                                                                                                        stfem.MIXED)
 
 
 @pytest.mark.parametrize("n", [37, 511, 512, 700, 1333])
@@ -214,11 +217,9 @@ def test_coarse_inverse_rejects_singular():
         stfem.host_invert(A)
 
 
-def test_broken_pressure_has_no_device_path():
-    """The broken pair is host setup only: the footprint estimate (and so the
-    serving admission) refuses it, as stfem_setup does."""
+def test_broken_pressure_sizes():
+    """The broken pair's slab size on the host (q (2 d (2n+1)^2 + cells x dim P1)
+    for Q2/P1 on 4x4 cells)."""
     prob = stfem.Problem(2, 4, 2, 2, 1, 0.01, pressure=stfem.PRESSURE_BROKEN)
-    with pytest.raises(stfem.StfemError):
-        stfem.estimate_bytes(prob, stfem.MIXED)
     rp, ci, va, n = stfem.host_level_matrix(prob, -1)
-    assert n == 2 * (2 * 2 * 9 * 9 + 16 * 3)  # q (2 d (2n+1)^2 + cells x dim P1)
+    assert n == 2 * (2 * 2 * 9 * 9 + 16 * 3)
