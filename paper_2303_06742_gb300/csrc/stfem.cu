@@ -60,778 +60,8 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// ---------------------------------------------------------------- SpMV
-// y_b = sum_a Dt[b,a] S1 x_a + W_b S2 x_b (mode 0) or rhs_b - (...) (mode 1):
-// the slab operator A_n = Dt (x) S1 + W (x) S2 of Eq. 4.7.
-// Node-block form of the same operator.  For a displacement node I with
-// neighbours J (shared cell) and pressure neighbours s:
-//   u-eq_b[I,c] = sum_a Dt[b,a] (Mr U_a)[I,c] - W_b (Mr V_b)[I,c]
-//   v-eq_b[I,c] = sum_a Dt[b,a] (Mr V_a)[I,c] + W_b ((K U_b)[I,c] + (Ct P_b)[I,c])
-// and for a pressure node s
-//   p-eq_b[s]   = sum_a Dt[b,a] (Mp0 P_a)[s] + W_b ((B P_b)[s] + (Cn V_b)[s])
-// (Problem 3.1), or with Problem B.1 (pcouple = 1)
-//   p-eq_b[s]   = sum_a Dt[b,a] ((Mp0 P_a)[s] + (Cn U_a)[s]) + W_b (B P_b)[s]
-// with Mr = rho M (scalar), K (d x d per pair), Ct = C^T (d per pair),
-// Mp0 = c0 Mp, Cn = -C (d per pair).  G lanes per node.
-template <typename T>
-struct NodeBlockDev {
-  long nu, np;
-  int r;                       // displacement degree (pressure degree r - 1)
-  int pcouple;                 // 0: Cn on V through W (3.1); 1: on U through Dt (B.1)
-  int pdisc, pnl;              // broken pressure space: pnl dofs per cell (see disc_* below)
-  int n[3];                    // cells per axis of the level
-  int udims[3], pdims[3];      // lattice sizes of Q_r and Q_{r-1}
-  const int *uu_ptr, *up_ptr, *pu_ptr, *pp_ptr;
-  const T *uu_m, *uu_k, *up_c, *pu_c, *pp_m, *pp_b;
-};
-
-// Neighbour box of a node: the lattice nodes (degree m_col) of all cells that
-// hold the node (lattice coordinate a, degree m_row).  Every level operator
-// couples exactly within this box, so neighbour addresses are computed, not
-// loaded.
-struct Box3 {
-  int lo[3], ext[3];
-};
-
-__device__ __forceinline__ Box3 node_box(const int *a, int m_row, int m_col, const int *ncell, int dim) {
-  Box3 b;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (i < dim) {
-      int clo, chi;
-      if (a[i] % m_row == 0) {
-        clo = max(a[i] / m_row - 1, 0);
-        chi = min(a[i] / m_row, ncell[i] - 1);
-      } else {
-        clo = chi = a[i] / m_row;
-      }
-      b.lo[i] = m_col * clo;
-      b.ext[i] = m_col * (chi + 1) - b.lo[i] + 1;
-    } else {
-      b.lo[i] = 0;
-      b.ext[i] = 1;
-    }
-  }
-  return b;
-}
-
-__device__ __forceinline__ long box_node(const Box3 &b, int e, const int *dims) {
-  const int ex = e % b.ext[0];
-  const int t = e / b.ext[0];
-  const int ey = t % b.ext[1], ez = t / b.ext[1];
-  return (long)(b.lo[0] + ex) + (long)dims[0] * ((b.lo[1] + ey) + (long)dims[1] * (b.lo[2] + ez));
-}
-
-__device__ __forceinline__ void lattice_coords(long idx, const int *dims, int dim, int *a) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (i < dim) {
-      a[i] = (int)(idx % dims[i]);
-      idx /= dims[i];
-    } else {
-      a[i] = 0;
-    }
-  }
-}
-
-// Broken pressure space (P_{r-1}^disc, pnl dofs per cell, numbered cell by
-// cell).  A displacement node couples to the dofs of the cells around it: a
-// box of cells (x fastest) times pnl.  A pressure dof couples to the (r+1)^D
-// nodes of its cell (x fastest) and to 2D+1 cell slots times pnl: its own
-// cell, then the lower and upper face neighbour along each axis.
-__device__ __forceinline__ Box3 disc_cell_box(const int *a, int r, const int *ncell, int dim) {
-  Box3 b;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (i < dim) {
-      int clo, chi;
-      if (a[i] % r == 0) {
-        clo = max(a[i] / r - 1, 0);
-        chi = min(a[i] / r, ncell[i] - 1);
-      } else {
-        clo = chi = a[i] / r;
-      }
-      b.lo[i] = clo;
-      b.ext[i] = chi - clo + 1;
-    } else {
-      b.lo[i] = 0;
-      b.ext[i] = 1;
-    }
-  }
-  return b;
-}
-
-// Cell of slot `slot` next to cell cm, or -1 past the boundary.
-__device__ __forceinline__ long disc_slot_cell(const int *cm, int slot, const int *ncell, int dim) {
-  int c2[3] = {cm[0], cm[1], cm[2]};
-  if (slot > 0) c2[(slot - 1) / 2] += ((slot - 1) % 2) ? 1 : -1;
-  for (int i = 0; i < dim; ++i)
-    if (c2[i] < 0 || c2[i] >= ncell[i]) return -1;
-  return (long)c2[0] + (long)ncell[0] * (c2[1] + (long)ncell[1] * c2[2]);
-}
-
-// Displacement node j (x fastest over (r+1)^dim) of cell cm.
-__device__ __forceinline__ long disc_cell_node(const int *cm, int j, int r, const int *udims, int dim) {
-  int aj[3] = {0, 0, 0};
-  for (int i = 0; i < dim; ++i) {
-    aj[i] = r * cm[i] + j % (r + 1);
-    j /= r + 1;
-  }
-  return (long)aj[0] + (long)udims[0] * (aj[1] + (long)udims[1] * aj[2]);
-}
-
-template <typename T, int Q, int D, int G, bool PD = false>
-__global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
-                                                 const T *__restrict__ x, const T *__restrict__ rhs,
-                                                 T *__restrict__ y, int mode, int nb, long cstride) {
-  constexpr int NA = 4 * Q * D;
-  // nb right-hand sides (column stride cstride): consecutive CTAs take the
-  // same nodes of different columns, so the node blocks are read from DRAM
-  // about once and from L2 by the other columns
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
-  x += (long)col * cstride;
-  y += (long)col * cstride;
-  if (rhs) rhs += (long)col * cstride;
-  const long node = gid / G;
-  const int lane = threadIdx.x % G;
-  T acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = T(0);
-  const bool is_u = node < A.nu;
-  const bool is_p = !is_u && node < A.nu + A.np;
-  if (is_u) {
-    // acc layout: [0] Mr U, [1] Mr V, [2] K U, [3] Ct P; each Q x D
-    int a[3];
-    lattice_coords(node, A.udims, D, a);
-    const Box3 bu = node_box(a, A.r, A.r, A.n, D);
-    const int base = A.uu_ptr[node], e1 = A.uu_ptr[node + 1];
-    // two neighbours per trip: their matrix and vector loads are independent
-    for (int e0 = base + lane; e0 < e1; e0 += 2 * G) {
-      const bool two = e0 + G < e1;
-      const int eb[2] = {e0, two ? e0 + G : e0};
-      long J[2];
-      T m[2], k[2][D * D];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        J[t] = box_node(bu, eb[t] - base, A.udims);
-        m[t] = (t == 0 || two) ? A.uu_m[eb[t]] : T(0);
-#pragma unroll
-        for (int i = 0; i < D * D; ++i) k[t][i] = (t == 0 || two) ? A.uu_k[(long)eb[t] * D * D + i] : T(0);
-      }
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T v[2][D], u[2][D];
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            v[t][c] = x[(long)a * ns + J[t] * D + c];
-            u[t][c] = x[(long)a * ns + R + J[t] * D + c];
-          }
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            acc[(0 * Q + a) * D + c] += m[t] * u[t][c];
-            acc[(1 * Q + a) * D + c] += m[t] * v[t][c];
-            T kk = T(0);
-#pragma unroll
-            for (int cp = 0; cp < D; ++cp) kk += k[t][c * D + cp] * u[t][cp];
-            acc[(2 * Q + a) * D + c] += kk;
-          }
-      }
-    }
-    const Box3 bp = PD ? disc_cell_box(a, A.r, A.n, D) : node_box(a, A.r, A.r - 1, A.n, D);
-    const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long sI = PD ? box_node(bp, (e - f0) / A.pnl, A.n) * A.pnl + (e - f0) % A.pnl
-                         : box_node(bp, e - f0, A.pdims);
-      T ct[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + sI];
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[(3 * Q + a) * D + c] += ct[c] * pv;
-      }
-    }
-  } else if (PD && is_p) {
-    // broken pressure dof: acc layout as below
-    const long sI = node - A.nu, cell = sI / A.pnl;
-    int cm[3];
-    lattice_coords(cell, A.n, D, cm);
-    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
-    for (int e = e0p + lane; e < e1; e += G) {
-      const long c2 = disc_slot_cell(cm, (e - e0p) / A.pnl, A.n, D);
-      if (c2 < 0) continue;
-      const long s2 = c2 * A.pnl + (e - e0p) % A.pnl;
-      const T m = A.pp_m[e], bb = A.pp_b[e];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + s2];
-        acc[a] += m * pv;
-        acc[Q + a] += bb * pv;
-      }
-    }
-    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
-    const long uoff = A.pcouple ? R : 0;
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long J = disc_cell_node(cm, e - f0, A.r, A.udims, D);
-      T cn[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T t = T(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
-        acc[2 * Q + a] += t;
-      }
-    }
-  } else if (is_p) {
-    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
-    const long sI = node - A.nu;
-    int a[3];
-    lattice_coords(sI, A.pdims, D, a);
-    const Box3 bp = node_box(a, A.r - 1, A.r - 1, A.n, D);
-    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
-    for (int e = e0p + lane; e < e1; e += G) {
-      const long s2 = box_node(bp, e - e0p, A.pdims);
-      const T m = A.pp_m[e], bb = A.pp_b[e];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + s2];
-        acc[a] += m * pv;
-        acc[Q + a] += bb * pv;
-      }
-    }
-    const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
-    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
-    const long uoff = A.pcouple ? R : 0; // the V or the U block of x
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long J = box_node(bu, e - f0, A.udims);
-      T cn[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T t = T(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
-        acc[2 * Q + a] += t;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-#pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-  }
-  if (is_u) {
-    // outputs: (eq in {u, v}) x Q x D, output o written by lane o % G
-#pragma unroll
-    for (int o = 0; o < 2 * Q * D; ++o) {
-      if (o % G != lane) continue;
-      const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
-      T val = T(0);
-#pragma unroll
-      for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[(eq * Q + a) * D + c];
-      if (eq == 0)
-        val -= tc.W[b] * acc[(1 * Q + b) * D + c];
-      else
-        val += tc.W[b] * (acc[(2 * Q + b) * D + c] + acc[(3 * Q + b) * D + c]);
-      const long oi = (long)b * ns + eq * R + node * D + c;
-      y[oi] = mode ? rhs[oi] - val : val;
-    }
-  } else if (is_p) {
-    const long sI = node - A.nu;
-#pragma unroll
-    for (int b = 0; b < Q; ++b) {
-      if (b % G != lane) continue;
-      T val;
-      if (A.pcouple) {
-        val = tc.W[b] * acc[Q + b];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * (acc[a] + acc[2 * Q + a]);
-      } else {
-        val = tc.W[b] * (acc[Q + b] + acc[2 * Q + b]);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
-      }
-      const long oi = (long)b * ns + 2 * R + sI;
-      y[oi] = mode ? rhs[oi] - val : val;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- double-float SpMV
-// y = A x for an FP64 operator whose every value a is held as the float pair
-// (hi, lo), hi = fl32(a), lo = fl32(a - hi) (a = hi + lo to about 2^-48),
-// applied to a vector that is exactly representable in FP32 (the output of
-// the FP32 V-cycle).  Products and sums run on the FP32 pipes in double-float
-// arithmetic: hi * x is split exactly with an FMA, lo * x is added to the
-// error term, and the running sum is kept as an unevaluated pair (hi, lo)
-// updated by Knuth's TwoSum.  The relative error of a row is about
-// n 2^-48 of the sum of |a_j x_j| (FP64: n 2^-53), while the FP32 pipes run
-// GB300's rate for FP32, far above its FP64 rate.  The Q time-node mixing
-// of Eq. 4.7 at the end is FP64.
-struct DF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void df_madd(DF &acc, float2 a, float x) {
-  const float p = a.x * x;
-  float e = fmaf(a.x, x, -p); // exact: a.x * x = p + e
-  e = fmaf(a.y, x, e);
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (p - bb);
-  acc.hi = s;
-  acc.lo += err + e;
-}
-
-__device__ __forceinline__ void df_add(DF &acc, float bh, float bl) {
-  const float s = acc.hi + bh;
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (bh - bb);
-  acc.hi = s;
-  acc.lo += err + bl;
-}
-
-__device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
-
-// acc += c * a for a float-pair coefficient c and a double-float value a
-__device__ __forceinline__ void df_fma(DF &acc, float2 c, const DF &a) {
-  const float p = c.x * a.hi;
-  float e = fmaf(c.x, a.hi, -p);
-  e = fmaf(c.x, a.lo, e);
-  e = fmaf(c.y, a.hi, e);
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (p - bb);
-  acc.hi = s;
-  acc.lo += err + e;
-}
-
-// Dt and W of Eq. 4.7 as float pairs (for the double-float time mixing)
-struct TimeCoefDF {
-  int q;
-  float2 Dt[MAXQ * MAXQ], W[MAXQ], mW[MAXQ];
-};
-
-template <int Q, int D, int G, bool PD = false>
-__global__ void __launch_bounds__(256) k_spmv_df(NodeBlockDev<float2> A, long ns, long R, TimeCoefDF tc,
-                                                 const float *__restrict__ x, double *__restrict__ y, int nb,
-                                                 long cstride) {
-  constexpr int NA = 4 * Q * D;
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
-  x += (long)col * cstride;
-  y += (long)col * cstride;
-  const long node = gid / G;
-  const int lane = threadIdx.x % G;
-  DF acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = DF{0.f, 0.f};
-  const bool is_u = node < A.nu;
-  const bool is_p = !is_u && node < A.nu + A.np;
-  if (is_u) {
-    // acc layout as in k_spmv_nb: [0] M U, [1] M V, [2] K U, [3] Ct P
-    int a[3];
-    lattice_coords(node, A.udims, D, a);
-    const Box3 bu = node_box(a, A.r, A.r, A.n, D);
-    const int base = A.uu_ptr[node], e1 = A.uu_ptr[node + 1];
-    for (int e = base + lane; e < e1; e += G) {
-      const long J = box_node(bu, e - base, A.udims);
-      const float2 m = A.uu_m[e];
-      float2 k[D * D];
-#pragma unroll
-      for (int i = 0; i < D * D; ++i) k[i] = A.uu_k[(long)e * D * D + i];
-#pragma unroll
-      for (int t = 0; t < Q; ++t) {
-        float v[D], u[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          v[c] = x[(long)t * ns + J * D + c];
-          u[c] = x[(long)t * ns + R + J * D + c];
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          df_madd(acc[(0 * Q + t) * D + c], m, u[c]);
-          df_madd(acc[(1 * Q + t) * D + c], m, v[c]);
-#pragma unroll
-          for (int cp = 0; cp < D; ++cp) df_madd(acc[(2 * Q + t) * D + c], k[c * D + cp], u[cp]);
-        }
-      }
-    }
-    const Box3 bp = PD ? disc_cell_box(a, A.r, A.n, D) : node_box(a, A.r, A.r - 1, A.n, D);
-    const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long sI = PD ? box_node(bp, (e - f0) / A.pnl, A.n) * A.pnl + (e - f0) % A.pnl
-                         : box_node(bp, e - f0, A.pdims);
-      float2 ct[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
-#pragma unroll
-      for (int t = 0; t < Q; ++t) {
-        const float pv = x[(long)t * ns + 2 * R + sI];
-#pragma unroll
-        for (int c = 0; c < D; ++c) df_madd(acc[(3 * Q + t) * D + c], ct[c], pv);
-      }
-    }
-  } else if (PD && is_p) {
-    // broken pressure dof (see k_spmv_nb)
-    const long sI = node - A.nu, cell = sI / A.pnl;
-    int cm[3];
-    lattice_coords(cell, A.n, D, cm);
-    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
-    for (int e = e0p + lane; e < e1; e += G) {
-      const long c2 = disc_slot_cell(cm, (e - e0p) / A.pnl, A.n, D);
-      if (c2 < 0) continue;
-      const long s2 = c2 * A.pnl + (e - e0p) % A.pnl;
-      const float2 m = A.pp_m[e], bb = A.pp_b[e];
-#pragma unroll
-      for (int t = 0; t < Q; ++t) {
-        const float pv = x[(long)t * ns + 2 * R + s2];
-        df_madd(acc[t], m, pv);
-        df_madd(acc[Q + t], bb, pv);
-      }
-    }
-    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
-    const long uoff = A.pcouple ? R : 0;
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long J = disc_cell_node(cm, e - f0, A.r, A.udims, D);
-      float2 cn[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
-#pragma unroll
-      for (int t = 0; t < Q; ++t)
-#pragma unroll
-        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + uoff + J * D + c]);
-    }
-  } else if (is_p) {
-    // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
-    const long sI = node - A.nu;
-    int a[3];
-    lattice_coords(sI, A.pdims, D, a);
-    const Box3 bp = node_box(a, A.r - 1, A.r - 1, A.n, D);
-    const int e0p = A.pp_ptr[sI], e1 = A.pp_ptr[sI + 1];
-    for (int e = e0p + lane; e < e1; e += G) {
-      const long s2 = box_node(bp, e - e0p, A.pdims);
-      const float2 m = A.pp_m[e], bb = A.pp_b[e];
-#pragma unroll
-      for (int t = 0; t < Q; ++t) {
-        const float pv = x[(long)t * ns + 2 * R + s2];
-        df_madd(acc[t], m, pv);
-        df_madd(acc[Q + t], bb, pv);
-      }
-    }
-    const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
-    const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
-    const long uoff = A.pcouple ? R : 0; // the V or the U block of x
-    for (int e = f0 + lane; e < f1; e += G) {
-      const long J = box_node(bu, e - f0, A.udims);
-      float2 cn[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
-#pragma unroll
-      for (int t = 0; t < Q; ++t)
-#pragma unroll
-        for (int c = 0; c < D; ++c) df_madd(acc[2 * Q + t], cn[c], x[(long)t * ns + uoff + J * D + c]);
-    }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-#pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const float bh = __shfl_xor_sync(0xffffffffu, acc[i].hi, o);
-      const float bl = __shfl_xor_sync(0xffffffffu, acc[i].lo, o);
-      df_add(acc[i], bh, bl);
-    }
-  }
-  // time-node mixing of Eq. 4.7 in double-float as well; one conversion to
-  // FP64 per output
-  if (is_u) {
-#pragma unroll
-    for (int o = 0; o < 2 * Q * D; ++o) {
-      if (o % G != lane) continue;
-      const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
-      DF val{0.f, 0.f};
-#pragma unroll
-      for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[(eq * Q + t) * D + c]);
-      if (eq == 0) {
-        df_fma(val, tc.mW[b], acc[(1 * Q + b) * D + c]);
-      } else {
-        df_fma(val, tc.W[b], acc[(2 * Q + b) * D + c]);
-        df_fma(val, tc.W[b], acc[(3 * Q + b) * D + c]);
-      }
-      y[(long)b * ns + eq * R + node * D + c] = df_val(val);
-    }
-  } else if (is_p) {
-    const long sI = node - A.nu;
-#pragma unroll
-    for (int b = 0; b < Q; ++b) {
-      if (b % G != lane) continue;
-      DF val{0.f, 0.f};
-      df_fma(val, tc.W[b], acc[Q + b]);
-      if (!A.pcouple) df_fma(val, tc.W[b], acc[2 * Q + b]);
-#pragma unroll
-      for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[t]);
-      if (A.pcouple)
-#pragma unroll
-        for (int t = 0; t < Q; ++t) df_fma(val, tc.Dt[b * Q + t], acc[2 * Q + t]);
-      y[(long)b * ns + 2 * R + sI] = df_val(val);
-    }
-  }
-}
-
-// ---------------------------------------------------------------- Vanka
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-};
-template <>
-struct Vec16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-};
-
-template <typename T>
-__device__ __forceinline__ void fma_vec(T *acc, const typename Vec16<T>::type &a, T r);
-template <>
-__device__ __forceinline__ void fma_vec<float>(float *acc, const float4 &a, float r) {
-  acc[0] += a.x * r;
-  acc[1] += a.y * r;
-  acc[2] += a.z * r;
-  acc[3] += a.w * r;
-}
-template <>
-__device__ __forceinline__ void fma_vec<double>(double *acc, const double2 &a, double r) {
-  acc[0] += a.x * r;
-  acc[1] += a.y * r;
-}
-
-// y_P = A_P^{-1} R_P res for every patch P of the level (one CTA per patch).
-// The inverse is column-major with leading dimension ld_P (multiple of VEC);
-// thread (tr, tj) owns VEC consecutive rows starting at VEC*tr and the
-// columns j = tj, tj + J, ...: each warp streams 32 x 16 contiguous bytes per
-// column.  With J > 1 (levels with few patches) the J partial sums are added
-// in a fixed order through shared memory, so the result is deterministic.
-template <typename T, int J>
-__global__ void __launch_bounds__(1024) k_patch_apply(const int *__restrict__ psize,
-                                                      const long long *__restrict__ pdoff,
-                                                      const int *__restrict__ pdofs,
-                                                      const long long *__restrict__ pioff,
-                                                      const int *__restrict__ pld, const T *__restrict__ pinv,
-                                                      const T *__restrict__ res, T *__restrict__ y) {
-  using V = typename Vec16<T>::type;
-  constexpr int VEC = Vec16<T>::n;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int RT = blockDim.x / J;
-  const int tr = threadIdx.x % RT, tj = threadIdx.x / RT;
-  const long p = blockIdx.x;
-  const int C = psize[p];
-  const long long doff = pdoff[p];
-  T *red = reinterpret_cast<T *>(smem_raw);             // [J][RT][VEC]
-  T *rs = red + (J > 1 ? (size_t)J * RT * VEC : 0);     // [C]
-  for (int j = threadIdx.x; j < C; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
-  __syncthreads();
-  const T *A = pinv + pioff[p];
-  const long stride = pld[p] / VEC;
-  for (int base = 0; base < C; base += VEC * RT) {
-    const int row0 = base + VEC * tr;
-    T acc[VEC];
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) acc[v] = T(0);
-    if (row0 < C) {
-      const V *col0 = reinterpret_cast<const V *>(A + row0);
-      int j = tj;
-      for (; j + 7 * J < C; j += 8 * J) {
-        V a[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) fma_vec<T>(acc, a[u], rs[j + u * J]);
-      }
-      for (; j < C; j += J) fma_vec<T>(acc, __ldcs(col0 + (long)j * stride), rs[j]);
-    }
-    if (J > 1) {
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) red[((size_t)tj * RT + tr) * VEC + v] = acc[v];
-      __syncthreads();
-      if (tj == 0 && row0 < C) {
-        for (int t = 1; t < J; ++t)
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) acc[v] += red[((size_t)t * RT + tr) * VEC + v];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v)
-          if (row0 + v < C) y[doff + row0 + v] = acc[v];
-      }
-      __syncthreads();
-    } else if (row0 < C) {
-#pragma unroll
-      for (int v = 0; v < VEC; ++v)
-        if (row0 + v < C) y[doff + row0 + v] = acc[v];
-    }
-  }
-}
-
-// Time-diagonal form of the same product.  With W^{-1} Dt = V diag(lam) V^{-1}
-// (q x q) the patch matrix Dt (x) S1_P + W (x) S2_P has the inverse
-//   A_P^{-1} = (V (x) I) blockdiag_a (lam_a S1_P + S2_P)^{-1} (V^{-1} W^{-1} (x) I),
-// and a complex-conjugate pair of eigenvalues shares one complex block.  Per
-// patch the kernel (1) gathers r_P, (2) mixes the q time blocks with
-// U = V^{-1} W^{-1}, (3) multiplies each slot by its stored inverse (real
-// slots: VEC rows per thread; complex slots: VEC/2 rows, (re, im) interleaved),
-// (4) mixes back with V (a conjugate pair contributes 2 Re(V z)).
-template <typename T>
-struct DiagCoef {
-  int nr, nc;
-  T U[2 * MAXQ * MAXQ]; // U[(a * q + b) * 2 + {re, im}] for the slots a
-  T V[2 * MAXQ * MAXQ]; // V[(b * ns + a) * 2 + {re, im}]
-};
-
-template <typename T, int J, int Q>
-__global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict__ pcs,
-                                                           const long long *__restrict__ pdoff,
-                                                           const int *__restrict__ pdofs,
-                                                           const long long *__restrict__ pioff,
-                                                           const T *__restrict__ pinv, const T *__restrict__ res,
-                                                           T *__restrict__ y, DiagCoef<T> dc, int maxCs) {
-  using Vv = typename Vec16<T>::type;
-  constexpr int VEC = Vec16<T>::n;
-  constexpr int CR = VEC / 2; // complex rows per thread
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int RT = blockDim.x / J;
-  const int tr = threadIdx.x % RT, tj = threadIdx.x / RT;
-  const long p = blockIdx.x;
-  const int Cs = pcs[p], C = Q * Cs;
-  const long long doff = pdoff[p];
-  const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
-  T *red = reinterpret_cast<T *>(smem_raw);
-  T *rs = red + (J > 1 ? (size_t)J * RT * VEC : 0);
-  T *rt = rs + (size_t)Q * maxCs;
-  T *z = rt + (size_t)nrow * maxCs;
-  for (int j = threadIdx.x; j < C; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
-  __syncthreads();
-  for (int m = threadIdx.x; m < Cs; m += blockDim.x) {
-    for (int a = 0; a < ns; ++a) {
-      T re = T(0), im = T(0);
-#pragma unroll
-      for (int b = 0; b < Q; ++b) {
-        const T r = rs[b * Cs + m];
-        re += dc.U[(a * Q + b) * 2] * r;
-        im += dc.U[(a * Q + b) * 2 + 1] * r;
-      }
-      if (a < nr) {
-        rt[a * Cs + m] = re;
-      } else {
-        rt[(nr + 2 * (a - nr)) * Cs + m] = re;
-        rt[(nr + 2 * (a - nr) + 1) * Cs + m] = im;
-      }
-    }
-  }
-  __syncthreads();
-  const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
-  const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
-  const T *Ab = pinv + pioff[p];
-  T vals[VEC];
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) vals[v] = T(0);
-  int role = -1, slot = 0, m0 = 0;
-  if (tr < nr * nRr) {
-    role = 0;
-    slot = tr / nRr;
-    m0 = VEC * (tr % nRr);
-    const Vv *col0 = reinterpret_cast<const Vv *>(Ab + (size_t)slot * Cs * ldR + m0);
-    const T *x = rt + slot * Cs;
-    const long stride = ldR / VEC;
-    int j = tj;
-    for (; j + 7 * J < Cs; j += 8 * J) {
-      Vv a[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) fma_vec<T>(vals, a[u], x[j + u * J]);
-    }
-    for (; j < Cs; j += J) fma_vec<T>(vals, __ldcs(col0 + (long)j * stride), x[j]);
-  } else if (tr < nr * nRr + nc * nCr) {
-    role = 1;
-    const int t2 = tr - nr * nRr;
-    slot = t2 / nCr;
-    m0 = CR * (t2 % nCr);
-    const T *A = Ab + (size_t)nr * Cs * ldR + (size_t)slot * Cs * ldC + 2 * m0;
-    const T *xr = rt + (nr + 2 * slot) * Cs, *xi = xr + Cs;
-    const long stride = ldC / VEC;
-    const Vv *col0 = reinterpret_cast<const Vv *>(A);
-    int j = tj;
-    for (; STFEM_DIAG_UNROLL_COMPLEX && j + 7 * J < Cs; j += 8 * J) {
-      Vv a[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = __ldcs(col0 + (long)(j + u * J) * stride);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const T *av = reinterpret_cast<const T *>(&a[u]);
-        const T ar = xr[j + u * J], ai = xi[j + u * J];
-#pragma unroll
-        for (int i = 0; i < CR; ++i) {
-          vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
-          vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
-        }
-      }
-    }
-    for (; j < Cs; j += J) {
-      const Vv a = __ldcs(col0 + (long)j * stride);
-      const T *av = reinterpret_cast<const T *>(&a);
-      const T ar = xr[j], ai = xi[j];
-#pragma unroll
-      for (int i = 0; i < CR; ++i) {
-        vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
-        vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
-      }
-    }
-  }
-  if (J > 1) {
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) red[((size_t)tj * RT + tr) * VEC + v] = vals[v];
-    __syncthreads();
-    if (tj == 0)
-      for (int t = 1; t < J; ++t)
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) vals[v] += red[((size_t)t * RT + tr) * VEC + v];
-  }
-  if (tj == 0) {
-    if (role == 0) {
-#pragma unroll
-      for (int v = 0; v < VEC; ++v)
-        if (m0 + v < Cs) z[slot * Cs + m0 + v] = vals[v];
-    } else if (role == 1) {
-#pragma unroll
-      for (int i = 0; i < CR; ++i)
-        if (m0 + i < Cs) {
-          z[(nr + 2 * slot) * Cs + m0 + i] = vals[2 * i];
-          z[(nr + 2 * slot + 1) * Cs + m0 + i] = vals[2 * i + 1];
-        }
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < C; idx += blockDim.x) {
-    const int b = idx / Cs, m = idx - b * Cs;
-    T val = T(0);
-    for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * z[a * Cs + m];
-    for (int c = 0; c < nc; ++c) {
-      const int a = nr + c;
-      val += T(2) * (dc.V[(b * ns + a) * 2] * z[(nr + 2 * c) * Cs + m] -
-                     dc.V[(b * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
-    }
-    y[doff + idx] = val;
-  }
-}
+#include "spmv.cuh"
+#include "vanka.cuh"
 
 // ---------------------------------------------------------------- bulk-copy streaming
 // Helpers for the asynchronous bulk copy (cp.async.bulk) of contiguous global
@@ -1077,568 +307,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
 #include "tc_patch.cuh"
 #include "patch_factor.cuh"
 
-// d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
-// scale = omega / (number of patches holding the dof): Algorithm 4.1's
-// d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).
-template <typename T>
-__global__ void k_vanka_update(long N, const int *__restrict__ iptr, const int *__restrict__ ipos,
-                               const T *__restrict__ scale, const T *__restrict__ y, T *__restrict__ d, int zero,
-                               int nb, long ystride) {
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  y += (long)col * ystride;
-  d += (long)col * N;
-  T acc = T(0);
-  for (int e = iptr[i]; e < iptr[i + 1]; ++e) acc += y[ipos[e]];
-  d[i] = (zero ? T(0) : d[i]) + scale[i] * acc;
-}
-
-// ---------------------------------------------------------------- transfers
-// out[a, blk, node*d + c] (+)= sum_e M[node, e] in[a, blk, col_e*d + c] for the
-// vector blocks blk = V, U (scalar operator of the Q_r space) and
-// out[a, P, node] (+)= sum_e Mp[node, e] in[a, P, col_e] (Q_{r-1} space).
-// One thread per (time node, block, output node): the d components of a node
-// are contiguous, so each operator entry feeds D loads from one segment.
-template <typename T, int D, int G>
-__global__ void k_transfer(long nu_out, long np_out, int q, long ns_out, long R_out, long ns_in, long R_in,
-                           const int *__restrict__ up, const int *__restrict__ uc, const T *__restrict__ uv,
-                           const int *__restrict__ pp, const int *__restrict__ pc, const T *__restrict__ pv,
-                           const T *__restrict__ in, T *__restrict__ out, int add, int nb, long in_stride,
-                           long out_stride) {
-  // G lanes per output (the long rows of P^T in the restriction), reduced by
-  // xor-shuffles in a fixed order; every lane of the warp takes part in the
-  // shuffles (lanes without an output carry zeros)
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
-  const long i = gid / G;
-  const int lane = (int)(gid % G);
-  in += (long)col * in_stride;
-  out += (long)col * out_stride;
-  const long nuq = 2 * nu_out * q;
-  T acc[D];
-#pragma unroll
-  for (int c = 0; c < D; ++c) acc[c] = T(0);
-  int kind = 0;
-  long node = 0;
-  int a = 0, blk = 0;
-  if (i < nuq) {
-    kind = 1;
-    node = i % nu_out;
-    const long ab = i / nu_out; // a * 2 + blk
-    a = (int)(ab >> 1);
-    blk = (int)(ab & 1);
-    const T *src = in + (long)a * ns_in + blk * R_in;
-    for (int e = up[node] + lane; e < up[node + 1]; e += G) {
-      const T w = uv[e];
-      const T *sp = src + (long)uc[e] * D;
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] += w * sp[c];
-    }
-  } else if (i < nuq + np_out * q) {
-    kind = 2;
-    const long j = i - nuq;
-    node = j % np_out;
-    a = (int)(j / np_out);
-    const T *src = in + (long)a * ns_in + 2 * R_in;
-    for (int e = pp[node] + lane; e < pp[node + 1]; e += G) acc[0] += pv[e] * src[pc[e]];
-  }
-  if (G > 1) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
-  }
-  if (lane != 0) return;
-  if (kind == 1) {
-    T *dst = out + (long)a * ns_out + blk * R_out + node * D;
-#pragma unroll
-    for (int c = 0; c < D; ++c) dst[c] = add ? dst[c] + acc[c] : acc[c];
-  } else if (kind == 2) {
-    T *dst = out + (long)a * ns_out + 2 * R_out + node;
-    *dst = add ? *dst + acc[0] : acc[0];
-  }
-}
-
-// ---------------------------------------------------------------- coarse
-// x = Ainv b with a dense FP64 inverse (one warp per row).
-template <typename T>
-__global__ void k_coarse(long n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x,
-                         int nb) {
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long row = ((long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  b += (long)col * n;
-  x += (long)col * n;
-  double acc = 0.0;
-  const double *a = Ainv + row * n;
-  for (long j = lane; j < n; j += 32) acc += a[j] * (double)b[j];
-  acc = warp_sum(acc);
-  if (lane == 0) x[row] = (T)acc;
-}
-
-template <typename A, typename B>
-__global__ void k_convert(long n, const A *__restrict__ a, B *__restrict__ b) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (B)a[i];
-}
-
-// b[c * sb + i] = a[c * sa + i] for nb columns of n entries (with conversion)
-template <typename A, typename B>
-__global__ void k_copy_cols(long n, int nb, const A *__restrict__ a, long sa, B *__restrict__ b, long sb) {
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long i = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
-  if (i < n) b[(long)col * sb + i] = (B)a[(long)col * sa + i];
-}
-
-// ---------------------------------------------------------------- BLAS-1 (FP64)
-constexpr int DOT_BLOCKS = 608; // 4 x 152 SMs
-constexpr int DOT_THREADS = 256;
-constexpr int DOT_NV = 8;
-
-// partial[v][block] = sum over the block's share of V_v . w  (v < k)
-__global__ void __launch_bounds__(DOT_THREADS) k_multidot(int k, const double *__restrict__ V, long ldV,
-                                                          const double *__restrict__ w, long n,
-                                                          double *__restrict__ partial) {
-  const int v0 = blockIdx.y * DOT_NV;
-  double acc[DOT_NV];
-#pragma unroll
-  for (int t = 0; t < DOT_NV; ++t) acc[t] = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-#pragma unroll
-    for (int t = 0; t < DOT_NV; ++t)
-      if (v0 + t < k) acc[t] += V[(long)(v0 + t) * ldV + i] * wi;
-  }
-  __shared__ double sm[DOT_NV][DOT_THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int t = 0; t < DOT_NV; ++t) {
-    const double s = warp_sum(acc[t]);
-    if (lane == 0) sm[t][warp] = s;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int t = 0; t < DOT_NV; ++t) {
-      double s = lane < DOT_THREADS / 32 ? sm[t][lane] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0 && v0 + t < k) partial[(long)(v0 + t) * gridDim.x + blockIdx.x] = s;
-    }
-  }
-}
-
-// w <- w - sum_v h[v] V_v, fused with the block partial sums of the next
-// Gram-Schmidt quantity: mode 0, partial[v][block] = V_v . w_new (v < k);
-// mode 1, partial[0][block] = w_new . w_new.  KB >= k bounds the register
-// accumulators.
-template <int KB>
-__global__ void __launch_bounds__(DOT_THREADS) k_axpy_dot(int k, const double *__restrict__ V, long ldV,
-                                                          const double *__restrict__ h, double *__restrict__ w,
-                                                          long n, double *__restrict__ partial, int mode) {
-  double acc[KB];
-#pragma unroll
-  for (int t = 0; t < KB; ++t) acc[t] = 0.0;
-  double hv[KB];
-#pragma unroll
-  for (int t = 0; t < KB; ++t) hv[t] = t < k ? h[t] : 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double vi[KB];
-    double s = 0.0;
-#pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      vi[t] = t < k ? V[(long)t * ldV + i] : 0.0;
-      s += hv[t] * vi[t];
-    }
-    const double wn = w[i] - s;
-    w[i] = wn;
-    if (mode == 0) {
-#pragma unroll
-      for (int t = 0; t < KB; ++t) acc[t] += vi[t] * wn;
-    } else {
-      acc[0] += wn * wn;
-    }
-  }
-  __shared__ double sm[KB][DOT_THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nout = mode == 0 ? k : 1;
-#pragma unroll
-  for (int t = 0; t < KB; ++t) {
-    const double sv = warp_sum(acc[t]);
-    if (lane == 0) sm[t][warp] = sv;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      double sv = lane < DOT_THREADS / 32 ? sm[t][lane] : 0.0;
-      sv = warp_sum(sv);
-      if (lane == 0 && t < nout) partial[(long)t * gridDim.x + blockIdx.x] = sv;
-    }
-  }
-}
-
-// out[v] = sum_b partial[v][b] in a fixed order (one block per v).
-__global__ void k_reduce_partials(int nb, const double *__restrict__ partial, double *__restrict__ out) {
-  __shared__ double sm[32];
-  const int v = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(long)v * nb + b];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
-    t = warp_sum(t);
-    if (threadIdx.x == 0) out[v] = t;
-  }
-}
-
-// w -= sum_v h[v] V_v
-__global__ void k_multiaxpy(int k, const double *__restrict__ V, long ldV, const double *__restrict__ h,
-                            double *__restrict__ w, long n) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int v = 0; v < k; ++v) acc += h[v] * V[(long)v * ldV + i];
-  w[i] -= acc;
-}
-
-// dst = src / *div  (or src / div_host when div == nullptr)
-__global__ void k_div(long n, const double *__restrict__ src, double *__restrict__ dst, const double *div,
-                      double div_host) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double s = div ? *div : div_host;
-  dst[i] = s != 0.0 ? src[i] / s : 0.0; // a zero column (finished right-hand side) stays zero
-}
-
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
-// previous Givens rotations applied, a new rotation for (H_jj, H_{j+1,j})
-// and the update of g.  status = {|g_{j+1}|, h_{j+1,j}}.
-__global__ void k_givens(int j, int m1, const double *__restrict__ h1, const double *__restrict__ h2,
-                         const double *__restrict__ hn2, double *__restrict__ H, double *__restrict__ cs,
-                         double *__restrict__ sn, double *__restrict__ g, double *__restrict__ hnorm,
-                         double *__restrict__ status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double col[MAXM + 1];
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn = sqrt(*hn2);
-  col[j + 1] = hn;
-  *hnorm = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = col[j], b = col[j + 1];
-  const double rho = hypot(a, b);
-  cs[j] = rho != 0.0 ? a / rho : 1.0;
-  sn[j] = rho != 0.0 ? b / rho : 0.0;
-  col[j] = rho;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  for (int i = 0; i <= j + 1; ++i) H[(long)j * m1 + i] = col[i];
-  status[0] = fabs(g[j + 1]);
-  status[1] = hn;
-}
-
-// Back substitution H(0:k,0:k) y = g(0:k).
-__global__ void k_backsolve(int k, int m1, const double *__restrict__ H, const double *__restrict__ g,
-                            double *__restrict__ y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int l = i + 1; l < k; ++l) s += H[(long)l * m1 + i] * y[l];
-    y[i] = (g[i] - s) / H[(long)i * m1 + i];
-  }
-}
-
-template <typename TZ>
-__global__ void k_update_x(long n, int k, const TZ *__restrict__ Z, long ldZ, const double *__restrict__ y,
-                           double *__restrict__ x) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int j = 0; j < k; ++j) acc += (double)Z[(long)j * ldZ + i] * y[j];
-  x[i] += acc;
-}
-
-__global__ void k_set(double *p, double v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
-}
-
-__global__ void k_repeat(long ns, int q, const double *__restrict__ state, double *__restrict__ x) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ns * q) return;
-  x[i] = state[i % ns];
-}
-
-// ---------------------------------------------------------------- problem data
-__device__ void node_coord(const GeomDev &g, int deg, const int *dims, const double *ref, long idx, double *x) {
-  for (int i = 0; i < 3; ++i) {
-    if (i < g.dim) {
-      const int a = (int)(idx % dims[i]);
-      idx /= dims[i];
-      const int c = min(a / deg, g.n[i] - 1);
-      x[i] = g.lo[i] + g.h[i] * (c + ref[a - deg * c]);
-    } else {
-      x[i] = 0.0;
-    }
-  }
-}
-
-// Built-in manufactured solutions (homogeneous on the boundary of the unit box)
-// and their sources rho f = rho u_tt - div sigma(u) + alpha grad p,
-// g = c0 p_t + alpha div u_t - kappa lap p (Eq. 1.1), derived by hand.
-__device__ void dev_fields(const ProbDev &P, const double *x, double t, double *u, double *v, double *p) {
-  const int d = P.dim;
-  for (int i = 0; i < 3; ++i) u[i] = v[i] = 0.0;
-  *p = 0.0;
-  if (P.id == STFEM_PROBLEM_SIN) {
-    double phi = 1.0;
-    for (int i = 0; i < d; ++i) phi *= sin(M_PI * x[i]);
-    for (int i = 0; i < d; ++i) {
-      u[i] = phi * sin(t);
-      v[i] = phi * cos(t);
-    }
-    *p = phi * cos(t);
-  } else if (P.id == STFEM_PROBLEM_PAPER_EOC) {
-    const double w1 = M_PI, w2 = M_PI;
-    const double T0 = sin(w1 * t * t), T1 = 2.0 * w1 * t * cos(w1 * t * t);
-    const double psi = sin(w2 * x[0]) * sin(w2 * x[1]);
-    u[0] = u[1] = T0 * psi;
-    v[0] = v[1] = T1 * psi;
-    *p = T0 * psi;
-  } else if (P.id == STFEM_PROBLEM_PAPER_SUPERCONV) {
-    const double w1 = 40.0 * M_PI, w2 = 10.0 * M_PI;
-    const double X = x[0], Y = x[1];
-    const double Ax = X * X * (X - 1) * (X - 1), Ay = Y * Y * (Y - 1) * (Y - 1);
-    const double Bx = (X - 1) * X * (2 * X - 1), By = (Y - 1) * Y * (2 * Y - 1);
-    u[0] = -2.0 * Ax * By * sin(w1 * t);
-    u[1] = 2.0 * Bx * Ay * sin(w1 * t);
-    v[0] = -2.0 * Ax * By * w1 * cos(w1 * t);
-    v[1] = 2.0 * Bx * Ay * w1 * cos(w1 * t);
-    *p = -2.0 * Ax * By * sin(w2 * t);
-  }
-}
-
-__device__ void dev_source(const ProbDev &P, const double *x, double t, double lam, double mu, double kap, double *rf,
-                           double *g) {
-  const int d = P.dim;
-  for (int i = 0; i < 3; ++i) rf[i] = 0.0;
-  *g = 0.0;
-  if (P.id == STFEM_PROBLEM_SIN) {
-    double s[3], c[3];
-    for (int i = 0; i < d; ++i) {
-      s[i] = sin(M_PI * x[i]);
-      c[i] = cos(M_PI * x[i]);
-    }
-    double phi = 1.0;
-    for (int i = 0; i < d; ++i) phi *= s[i];
-    const double pi2 = M_PI * M_PI;
-    double dphi[3];
-    for (int i = 0; i < d; ++i) {
-      double pr = M_PI * c[i];
-      for (int k = 0; k < d; ++k)
-        if (k != i) pr *= s[k];
-      dphi[i] = pr;
-    }
-    for (int i = 0; i < d; ++i) {
-      double hsum = 0.0; // sum_j d_i d_j phi
-      for (int j = 0; j < d; ++j) {
-        if (j == i) {
-          hsum += -pi2 * phi;
-        } else {
-          double pr = pi2 * c[i] * c[j];
-          for (int k = 0; k < d; ++k)
-            if (k != i && k != j) pr *= s[k];
-          hsum += pr;
-        }
-      }
-      rf[i] = -P.rho * phi * sin(t) + d * pi2 * mu * phi * sin(t) - (mu + lam) * sin(t) * hsum +
-              P.alpha * cos(t) * dphi[i];
-    }
-    double div = 0.0;
-    for (int j = 0; j < d; ++j) div += dphi[j];
-    *g = -P.c0 * phi * sin(t) + P.alpha * cos(t) * div + kap * d * pi2 * phi * cos(t);
-  } else if (P.id == STFEM_PROBLEM_PAPER_EOC) {
-    const double w1 = M_PI, w2 = M_PI;
-    const double T0 = sin(w1 * t * t), T1 = 2.0 * w1 * t * cos(w1 * t * t),
-                 T2 = 2.0 * w1 * cos(w1 * t * t) - 4.0 * w1 * w1 * t * t * sin(w1 * t * t);
-    const double sx = sin(w2 * x[0]), sy = sin(w2 * x[1]), cx = cos(w2 * x[0]), cy = cos(w2 * x[1]);
-    const double psi = sx * sy, cc = cx * cy, w22 = w2 * w2;
-    const double base = P.rho * T2 * psi + 2.0 * mu * w22 * T0 * psi + (mu + lam) * w22 * T0 * (psi - cc);
-    rf[0] = base + P.alpha * T0 * w2 * cx * sy;
-    rf[1] = base + P.alpha * T0 * w2 * sx * cy;
-    *g = P.c0 * T1 * psi + P.alpha * T1 * w2 * (cx * sy + sx * cy) + 2.0 * kap * w22 * T0 * psi;
-  } else if (P.id == STFEM_PROBLEM_PAPER_SUPERCONV) {
-    const double w1 = 40.0 * M_PI, w2 = 10.0 * M_PI;
-    const double X = x[0], Y = x[1];
-    const double Ax = X * X * (X - 1) * (X - 1), Ay = Y * Y * (Y - 1) * (Y - 1);
-    const double Bx = (X - 1) * X * (2 * X - 1), By = (Y - 1) * Y * (2 * Y - 1);
-    const double A2x = 12 * X * X - 12 * X + 2, A2y = 12 * Y * Y - 12 * Y + 2;
-    const double B1y = 6 * Y * Y - 6 * Y + 1, B2x = 12 * X - 6, B2y = 12 * Y - 6;
-    const double A1x = 2.0 * Bx; // A' = 2B
-    const double s1 = sin(w1 * t), s2 = sin(w2 * t), c2 = cos(w2 * t);
-    rf[0] = 2.0 * P.rho * w1 * w1 * Ax * By * s1 + 2.0 * mu * (A2x * By + Ax * B2y) * s1 - 2.0 * P.alpha * A1x * By * s2;
-    rf[1] = -2.0 * P.rho * w1 * w1 * Bx * Ay * s1 - 2.0 * mu * (B2x * Ay + Bx * A2y) * s1 - 2.0 * P.alpha * Ax * B1y * s2;
-    *g = -2.0 * P.c0 * w2 * Ax * By * c2 + 2.0 * kap * (A2x * By + Ax * B2y) * s2;
-  }
-}
-
-// z-component of the traction t_N on the top face for the pulse problem
-__device__ double dev_top_traction(const ProbDev &P, const double *x, double t) {
-  if (P.id != STFEM_PROBLEM_PULSE) return 0.0;
-  if (x[0] >= 0.75 && x[0] <= 1.25 && x[1] >= 0.75 && x[1] <= 1.25) return -sin(M_PI * t / 0.05);
-  return 0.0;
-}
-
-// state = nodal interpolation of (v, u, p) at time t; a broken pressure
-// space takes the L2 projection of p on each cell (orthogonal basis: one
-// quotient per dof)
-__global__ void k_interp(GeomDev g, ProbDev P, LoadTables L, double t, long R, long S, double *__restrict__ state) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * R + S) return;
-  double x[3], u[3], v[3], p;
-  if (L.pdisc && i >= 2 * R) {
-    const long cell = (i - 2 * R) / L.nlp;
-    const int s = (int)((i - 2 * R) % L.nlp);
-    int cm[3] = {0, 0, 0};
-    long t2 = cell;
-    for (int k = 0; k < g.dim; ++k) {
-      cm[k] = (int)(t2 % g.n[k]);
-      t2 /= g.n[k];
-    }
-    double num = 0.0, den = 0.0;
-    for (int qq = 0; qq < L.npq; ++qq) {
-      for (int k = 0; k < 3; ++k) x[k] = k < g.dim ? g.lo[k] + g.h[k] * (cm[k] + L.pqx[qq * 3 + k]) : 0.0;
-      dev_fields(P, x, t, u, v, &p);
-      const double ph = L.phiPP[(long)qq * L.nlp + s];
-      num += L.pqw[qq] * p * ph;
-      den += L.pqw[qq] * ph * ph;
-    }
-    state[i] = num / den;
-    return;
-  }
-  if (i < 2 * R) {
-    const long rem = i % R;
-    node_coord(g, g.r, g.udims, g.refU, rem / g.dim, x);
-    dev_fields(P, x, t, u, v, &p);
-    state[i] = (i < R) ? v[rem % g.dim] : u[rem % g.dim];
-  } else {
-    node_coord(g, g.r - 1, g.pdims, g.refP, i - 2 * R, x);
-    dev_fields(P, x, t, u, v, &p);
-    state[i] = p;
-  }
-}
-
-// Source values rho f (d components) and g at every (time node b, cell,
-// quadrature point) of the finest level: src[((b * ncell + cell) * nq + qp) * 4 + c].
-__global__ void k_src_eval(GeomDev g, ProbDev P, LoadTables L, int q, const double *tnode, double t_prev, double tau,
-                           long ncell, double *__restrict__ src) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)q * ncell * L.nq) return;
-  const int qp = (int)(i % L.nq);
-  const long cell = (i / L.nq) % ncell;
-  const int b = (int)(i / ((long)L.nq * ncell));
-  const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
-  long t = cell;
-  double x[3];
-  for (int k = 0; k < 3; ++k) {
-    int c = 0;
-    if (k < g.dim) {
-      c = (int)(t % g.n[k]);
-      t /= g.n[k];
-    }
-    x[k] = g.lo[k] + g.h[k] * (c + L.qx[qp * 3 + k]);
-  }
-  double rf[3], gg;
-  dev_source(P, x, tb, L.lam[cell], L.mu[cell], L.kap[cell], rf, &gg);
-  double *o = src + i * 4;
-  o[0] = rf[0];
-  o[1] = rf[1];
-  o[2] = rf[2];
-  o[3] = gg;
-}
-
-// Slab right-hand side (Eq. 3.5 / Eq. 4.5):
-// rhs[b, m] = chi_b(-1) (S1 state)[m] + W_b * load_m(t_b), load = 0 on u-rows,
-// F = <rho f, psi> - <t_N, psi>_{Gamma_N} on v-rows, G = <g, xi> on p-rows.
-// Node-centric gather over the cells holding the node (deterministic), from
-// the source values precomputed by k_src_eval.
-__global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double> tc, const double *chi,
-                      const double *tnode, double t_prev, double tau, long R, long S,
-                      const double *__restrict__ src, const double *__restrict__ ys, double *__restrict__ out) {
-  const long ns = 2 * R + S;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)q * ns) return;
-  const int b = (int)(i / ns);
-  const long m = i % ns;
-  double val = chi[b] * ys[m];
-  if (m >= R && P.id != STFEM_PROBLEM_NONE) {
-    const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
-    const int d = g.dim;
-    const bool urow = m < 2 * R;
-    if (!urow && L.pdisc) {
-      // broken pressure dof: the load of its own cell alone
-      const long ncell = (long)g.n[0] * g.n[1] * g.n[2];
-      const long cell = (m - 2 * R) / L.nlp;
-      const int li = (int)((m - 2 * R) % L.nlp);
-      const double *sv = src + (((long)b * ncell + cell) * L.nq) * 4 + 3;
-      double load = 0.0;
-      for (int qq = 0; qq < L.nq; ++qq) load += L.qw[qq] * sv[qq * 4] * L.phiP[(long)qq * L.nlp + li];
-      out[i] = val + tc.W[b] * load;
-      return;
-    }
-    const int deg = urow ? g.r : g.r - 1;
-    const int *dims = urow ? g.udims : g.pdims;
-    const long node = urow ? (m - R) / d : m - 2 * R;
-    const int comp = urow ? (int)((m - R) % d) : 3;
-    int a[3] = {0, 0, 0}, clo[3] = {0, 0, 0}, chi_[3] = {0, 0, 0};
-    long t = node;
-    for (int k = 0; k < d; ++k) {
-      a[k] = (int)(t % dims[k]);
-      t /= dims[k];
-      if (a[k] % deg == 0) {
-        clo[k] = max(a[k] / deg - 1, 0);
-        chi_[k] = min(a[k] / deg, g.n[k] - 1);
-      } else {
-        clo[k] = chi_[k] = a[k] / deg;
-      }
-    }
-    const int nl = urow ? L.nlu : L.nlp;
-    const double *phi = urow ? L.phiU : L.phiP;
-    const long ncell = (long)g.n[0] * g.n[1] * g.n[2];
-    double load = 0.0;
-    for (int cz = clo[2]; cz <= chi_[2]; ++cz)
-      for (int cy = clo[1]; cy <= chi_[1]; ++cy)
-        for (int cx = clo[0]; cx <= chi_[0]; ++cx) {
-          const int cc[3] = {cx, cy, cz};
-          int li = 0, stride = 1;
-          for (int k = 0; k < d; ++k) {
-            li += (a[k] - deg * cc[k]) * stride;
-            stride *= deg + 1;
-          }
-          const long cell = cx + (long)g.n[0] * (cy + (long)g.n[1] * cz);
-          const double *sv = src + (((long)b * ncell + cell) * L.nq) * 4 + comp;
-          for (int qq = 0; qq < L.nq; ++qq) load += L.qw[qq] * sv[qq * 4] * phi[qq * nl + li];
-          // Neumann traction on the top face (pulse problem)
-          if (urow && L.top_neumann && comp == d - 1 && cc[d - 1] == g.n[d - 1] - 1 &&
-              a[d - 1] == deg * g.n[d - 1]) {
-            for (int qq = 0; qq < L.nqf; ++qq) {
-              double x[3];
-              for (int k = 0; k < 3; ++k) x[k] = g.lo[k] + g.h[k] * (cc[k] + L.fx[qq * 3 + k]);
-              load += -L.fw[qq] * dev_top_traction(P, x, tb) * L.fphiU[qq * L.nlu + li];
-            }
-          }
-        }
-    val += tc.W[b] * load;
-  }
-  out[i] = val;
-}
+#include "solver_kernels.cuh"
+#include "problem_data.cuh"
 
 // ============================================================ host side
 inline int grid_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
