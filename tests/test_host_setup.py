@@ -50,6 +50,9 @@ CASES = [
     (2, 4, 2, 2, 1, [0, 0], [1, 2], [0, 1, 0, 0], [1, 0, 0, 1], "measure"),
     (2, 4, 2, 3, 2, [0, 0], [1, 1], [0, 0, 0, 0], [0, 0, 0, 0], "length"),
     (3, 2, 2, 2, 1, [0, 0, 0], [2, 2, 1], [0, 1, 1, 1, 0, 1], [1, 1, 1, 1, 1, 0], "measure"),
+    # the degrees of Tables 5.2 / C.1 (r = 4, k = 3) and 5.3 (r = 5, k = 2)
+    (2, 4, 2, 4, 3, [0, 0], [1, 1], [0, 0, 1, 0], [0, 1, 0, 0], "measure"),
+    (2, 2, 2, 5, 2, [0, 0], [1, 1], [0, 0, 0, 0], [0, 0, 0, 0], "measure"),
 ]
 
 
