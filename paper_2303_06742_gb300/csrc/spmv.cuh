@@ -30,20 +30,21 @@ struct NodeBlockDev {
 // Neighbour box of a node: the lattice nodes (degree m_col) of all cells that
 // hold the node (lattice coordinate a, degree m_row).  Every level operator
 // couples exactly within this box, so neighbour addresses are computed, not
-// loaded.
+// loaded.  These index helpers also run on the host, in the CPU model of the
+// product that checks the layout.
 struct Box3 {
   int lo[3], ext[3];
 };
 
-__device__ __forceinline__ Box3 node_box(const int *a, int m_row, int m_col, const int *ncell, int dim) {
+__host__ __device__ __forceinline__ Box3 node_box(const int *a, int m_row, int m_col, const int *ncell, int dim) {
   Box3 b;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < dim) {
       int clo, chi;
       if (a[i] % m_row == 0) {
-        clo = max(a[i] / m_row - 1, 0);
-        chi = min(a[i] / m_row, ncell[i] - 1);
+        clo = a[i] / m_row - 1 > 0 ? a[i] / m_row - 1 : 0;
+        chi = a[i] / m_row < ncell[i] - 1 ? a[i] / m_row : ncell[i] - 1;
       } else {
         clo = chi = a[i] / m_row;
       }
@@ -57,14 +58,14 @@ __device__ __forceinline__ Box3 node_box(const int *a, int m_row, int m_col, con
   return b;
 }
 
-__device__ __forceinline__ long box_node(const Box3 &b, int e, const int *dims) {
+__host__ __device__ __forceinline__ long box_node(const Box3 &b, int e, const int *dims) {
   const int ex = e % b.ext[0];
   const int t = e / b.ext[0];
   const int ey = t % b.ext[1], ez = t / b.ext[1];
   return (long)(b.lo[0] + ex) + (long)dims[0] * ((b.lo[1] + ey) + (long)dims[1] * (b.lo[2] + ez));
 }
 
-__device__ __forceinline__ void lattice_coords(long idx, const int *dims, int dim, int *a) {
+__host__ __device__ __forceinline__ void lattice_coords(long idx, const int *dims, int dim, int *a) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < dim) {
@@ -81,15 +82,15 @@ __device__ __forceinline__ void lattice_coords(long idx, const int *dims, int di
 // box of cells (x fastest) times pnl.  A pressure dof couples to the (r+1)^D
 // nodes of its cell (x fastest) and to 2D+1 cell slots times pnl: its own
 // cell, then the lower and upper face neighbour along each axis.
-__device__ __forceinline__ Box3 disc_cell_box(const int *a, int r, const int *ncell, int dim) {
+__host__ __device__ __forceinline__ Box3 disc_cell_box(const int *a, int r, const int *ncell, int dim) {
   Box3 b;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < dim) {
       int clo, chi;
       if (a[i] % r == 0) {
-        clo = max(a[i] / r - 1, 0);
-        chi = min(a[i] / r, ncell[i] - 1);
+        clo = a[i] / r - 1 > 0 ? a[i] / r - 1 : 0;
+        chi = a[i] / r < ncell[i] - 1 ? a[i] / r : ncell[i] - 1;
       } else {
         clo = chi = a[i] / r;
       }
@@ -104,7 +105,7 @@ __device__ __forceinline__ Box3 disc_cell_box(const int *a, int r, const int *nc
 }
 
 // Cell of slot `slot` next to cell cm, or -1 past the boundary.
-__device__ __forceinline__ long disc_slot_cell(const int *cm, int slot, const int *ncell, int dim) {
+__host__ __device__ __forceinline__ long disc_slot_cell(const int *cm, int slot, const int *ncell, int dim) {
   int c2[3] = {cm[0], cm[1], cm[2]};
   if (slot > 0) c2[(slot - 1) / 2] += ((slot - 1) % 2) ? 1 : -1;
   for (int i = 0; i < dim; ++i)
@@ -113,7 +114,7 @@ __device__ __forceinline__ long disc_slot_cell(const int *cm, int slot, const in
 }
 
 // Displacement node j (x fastest over (r+1)^dim) of cell cm.
-__device__ __forceinline__ long disc_cell_node(const int *cm, int j, int r, const int *udims, int dim) {
+__host__ __device__ __forceinline__ long disc_cell_node(const int *cm, int j, int r, const int *udims, int dim) {
   int aj[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) {
     aj[i] = r * cm[i] + j % (r + 1);

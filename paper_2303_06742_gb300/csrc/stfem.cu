@@ -663,22 +663,6 @@ static long box_pos(const HostBox &b, long j, const int *dims, int dim) {
   return pos;
 }
 
-// flat index of box element e (x fastest) in lattice dims
-static long box_node_host(const HostBox &b, long e, const int *dims) {
-  const long ex = e % b.ext[0], t = e / b.ext[0];
-  const long ey = t % b.ext[1], ez = t / b.ext[1];
-  return (b.lo[0] + ex) + (long)dims[0] * ((b.lo[1] + ey) + (long)dims[1] * (b.lo[2] + ez));
-}
-
-static long stfem_flat(const int *a, const int *dims, int dim) {
-  long idx = 0, stride = 1;
-  for (int i = 0; i < dim; ++i) {
-    idx += a[i] * stride;
-    stride *= dims[i];
-  }
-  return idx;
-}
-
 static void coords_of(long idx, const int *dims, int dim, int *a) {
   for (int i = 0; i < 3; ++i) {
     if (i < dim) {
@@ -888,9 +872,10 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
 }
 
 // Host model of the node-block product y = (Dt (x) S1 + W (x) S2) x of
-// k_spmv_nb on the arrays node_block builds (FP64, one node after another;
-// neighbour addresses from the boxes, as the kernel computes them).  It
-// checks the layout on the CPU, for either pressure space.
+// k_spmv_nb on the arrays node_block builds (FP64, one node after another),
+// with the kernels' own index helpers (node_box, box_node, lattice_coords,
+// disc_*): a CPU check of the layout and of the kernels' address arithmetic,
+// for either pressure space.
 static void block_apply_host(const NodeBlockHost &H, const stfem::Level &L, int d, int q, const double *Dt,
                              const double *W, const double *x, double *y) {
   const long R = L.R, ns = L.ns, nu = H.nu;
@@ -899,12 +884,13 @@ static void block_apply_host(const NodeBlockHost &H, const stfem::Level &L, int 
   const int *ud = L.U.dims, *pd = L.P.dims, *nc = L.box.n;
   int a[3];
   for (long I = 0; I < nu; ++I) {
-    coords_of(I, ud, d, a);
-    const HostBox bu = host_box(a, r, r, nc, d);
+    lattice_coords(I, ud, d, a);
+    const Box3 bu = node_box(a, r, r, nc, d);
+    const Box3 bp = H.pdisc ? disc_cell_box(a, r, nc, d) : node_box(a, r, r - 1, nc, d);
     // per time node: rho M U, rho M V, K U, C^T P, each d components
     std::vector<double> mu(q * d, 0.0), mv(q * d, 0.0), ku(q * d, 0.0), cp(q * d, 0.0);
     for (int e = H.uu_ptr[I]; e < H.uu_ptr[I + 1]; ++e) {
-      const long J = box_node_host(bu, e - H.uu_ptr[I], ud);
+      const long J = box_node(bu, e - H.uu_ptr[I], ud);
       for (int t = 0; t < q; ++t)
         for (int c = 0; c < d; ++c) {
           mu[t * d + c] += H.uu_m[e] * x[t * ns + R + J * d + c];
@@ -913,14 +899,8 @@ static void block_apply_host(const NodeBlockHost &H, const stfem::Level &L, int 
         }
     }
     for (int e = H.up_ptr[I]; e < H.up_ptr[I + 1]; ++e) {
-      long sI;
-      if (H.pdisc) {
-        const HostBox cb = cell_box(a, r, nc, d);
-        const int k = e - H.up_ptr[I];
-        sI = box_node_host(cb, k / pnl, nc) * pnl + k % pnl;
-      } else {
-        sI = box_node_host(host_box(a, r, r - 1, nc, d), e - H.up_ptr[I], pd);
-      }
+      const int k = e - H.up_ptr[I];
+      const long sI = H.pdisc ? box_node(bp, k / pnl, nc) * pnl + k % pnl : box_node(bp, k, pd);
       for (int t = 0; t < q; ++t)
         for (int c = 0; c < d; ++c) cp[t * d + c] += H.up_c[(size_t)e * d + c] * x[t * ns + 2 * R + sI];
     }
@@ -939,48 +919,35 @@ static void block_apply_host(const NodeBlockHost &H, const stfem::Level &L, int 
   for (long sI = 0; sI < H.np; ++sI) {
     std::vector<double> mp(q, 0.0), bp(q, 0.0), cn(q, 0.0);
     if (H.pdisc) {
-      const long cell = sI / pnl;
       int cm[3];
-      coords_of(cell, nc, d, cm);
+      lattice_coords(sI / pnl, nc, d, cm);
       for (int e = H.pu_ptr[sI]; e < H.pu_ptr[sI + 1]; ++e) {
-        const int j = e - H.pu_ptr[sI];
-        int aj[3] = {0, 0, 0}, t = j;
-        for (int i = 0; i < d; ++i) {
-          aj[i] = r * cm[i] + t % (r + 1);
-          t /= r + 1;
-        }
-        const long J = stfem_flat(aj, ud, d);
+        const long J = disc_cell_node(cm, e - H.pu_ptr[sI], r, ud, d);
         for (int tt = 0; tt < q; ++tt)
           for (int c = 0; c < d; ++c) cn[tt] += H.pu_c[(size_t)e * d + c] * x[tt * ns + uoff + J * d + c];
       }
-      for (int slot = 0; slot < 2 * d + 1; ++slot) {
-        int c2[3] = {cm[0], cm[1], cm[2]};
-        if (slot > 0) c2[(slot - 1) / 2] += (slot - 1) % 2 ? 1 : -1;
-        bool in = true;
-        for (int i = 0; i < d; ++i) in = in && c2[i] >= 0 && c2[i] < nc[i];
-        if (!in) continue;
-        const long cell2 = stfem_flat(c2, nc, d);
-        for (int tl = 0; tl < pnl; ++tl) {
-          const size_t e = (size_t)H.pp_ptr[sI] + (size_t)slot * pnl + tl;
-          for (int tt = 0; tt < q; ++tt) {
-            const double pv = x[tt * ns + 2 * R + cell2 * pnl + tl];
-            mp[tt] += H.pp_m[e] * pv;
-            bp[tt] += H.pp_b[e] * pv;
-          }
+      for (int e = H.pp_ptr[sI]; e < H.pp_ptr[sI + 1]; ++e) {
+        const long c2 = disc_slot_cell(cm, (e - H.pp_ptr[sI]) / pnl, nc, d);
+        if (c2 < 0) continue;
+        const long s2 = c2 * pnl + (e - H.pp_ptr[sI]) % pnl;
+        for (int tt = 0; tt < q; ++tt) {
+          const double pv = x[tt * ns + 2 * R + s2];
+          mp[tt] += H.pp_m[e] * pv;
+          bp[tt] += H.pp_b[e] * pv;
         }
       }
     } else {
-      coords_of(sI, pd, d, a);
-      const HostBox bpx = host_box(a, r - 1, r - 1, nc, d), bux = host_box(a, r - 1, r, nc, d);
+      lattice_coords(sI, pd, d, a);
+      const Box3 bpx = node_box(a, r - 1, r - 1, nc, d), bux = node_box(a, r - 1, r, nc, d);
       for (int e = H.pp_ptr[sI]; e < H.pp_ptr[sI + 1]; ++e) {
-        const long s2 = box_node_host(bpx, e - H.pp_ptr[sI], pd);
+        const long s2 = box_node(bpx, e - H.pp_ptr[sI], pd);
         for (int tt = 0; tt < q; ++tt) {
           mp[tt] += H.pp_m[e] * x[tt * ns + 2 * R + s2];
           bp[tt] += H.pp_b[e] * x[tt * ns + 2 * R + s2];
         }
       }
       for (int e = H.pu_ptr[sI]; e < H.pu_ptr[sI + 1]; ++e) {
-        const long J = box_node_host(bux, e - H.pu_ptr[sI], ud);
+        const long J = box_node(bux, e - H.pu_ptr[sI], ud);
         for (int tt = 0; tt < q; ++tt)
           for (int c = 0; c < d; ++c) cn[tt] += H.pu_c[(size_t)e * d + c] * x[tt * ns + uoff + J * d + c];
       }
