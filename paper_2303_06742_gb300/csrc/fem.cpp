@@ -1099,7 +1099,358 @@ CSR transpose(const CSR &a) {
   return t;
 }
 
+namespace {
+
+// A node-level matrix in CSR form with nv values per entry.
+struct NodeCSR {
+  long nrows = 0;
+  int nv = 1;
+  std::vector<long> ptr;
+  hvec<int> col;
+  hvec<double> val;
+};
+
+// C = Prow^T A Pcol for a node-level matrix (rows: fine row nodes, columns:
+// fine column nodes), every value slot at once; rows of C are coarse row
+// nodes, sorted columns.  Threaded like the scalar product below.
+NodeCSR node_rap(const NodeCSR &A, const CSR &Prow, const CSR &Pcol) {
+  const int nv = A.nv;
+  const long nfr = A.nrows, ncc = Pcol.ncols, ncr = Prow.ncols;
+  const int nt = n_threads();
+  struct Buf {
+    hvec<int> col;
+    hvec<double> val;
+  };
+  auto product = [&](long nrows, auto row_terms, std::vector<long> &ptr, hvec<int> &col, hvec<double> &val) {
+    // row_terms(i, emit): calls emit(J, weight, const double *v) for the terms of row i
+    std::vector<Buf> buf(nt);
+    std::vector<int> who(nrows), len(nrows);
+    std::vector<long> at(nrows);
+    std::atomic<long> next(0);
+    auto work = [&](int w) {
+      std::vector<double> acc((size_t)ncc * nv, 0.0);
+      std::vector<char> mark(ncc, 0);
+      std::vector<int> touched;
+      Buf &o = buf[w];
+      for (;;) {
+        const long i0 = next.fetch_add(128);
+        if (i0 >= nrows) break;
+        for (long i = i0; i < std::min(nrows, i0 + 128); ++i) {
+          touched.clear();
+          row_terms(i, [&](int J, double wgt, const double *v) {
+            if (!mark[J]) {
+              mark[J] = 1;
+              touched.push_back(J);
+              for (int k = 0; k < nv; ++k) acc[(size_t)J * nv + k] = 0.0;
+            }
+            for (int k = 0; k < nv; ++k) acc[(size_t)J * nv + k] += wgt * v[k];
+          });
+          std::sort(touched.begin(), touched.end());
+          who[i] = w;
+          at[i] = (long)o.col.size();
+          len[i] = (int)touched.size();
+          for (const int J : touched) {
+            o.col.push_back(J);
+            for (int k = 0; k < nv; ++k) o.val.push_back(acc[(size_t)J * nv + k]);
+            mark[J] = 0;
+          }
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
+    for (auto &t : th) t.join();
+    ptr.assign(nrows + 1, 0);
+    for (long i = 0; i < nrows; ++i) ptr[i + 1] = ptr[i] + len[i];
+    col.resize(ptr[nrows]);
+    val.resize((size_t)ptr[nrows] * nv);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long i = 0; i < nrows; ++i) {
+      const Buf &b = buf[who[i]];
+      std::copy(b.col.begin() + at[i], b.col.begin() + at[i] + len[i], col.begin() + ptr[i]);
+      std::copy(b.val.begin() + at[i] * nv, b.val.begin() + (at[i] + len[i]) * nv, val.begin() + ptr[i] * nv);
+    }
+  };
+  // AP = A Pcol (rows fine, columns coarse)
+  NodeCSR AP;
+  AP.nrows = nfr;
+  AP.nv = nv;
+  product(
+      nfr,
+      [&](long i, auto emit) {
+        for (long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+          const int j = A.col[e];
+          const double *v = A.val.data() + (size_t)e * nv;
+          for (int f = Pcol.rowptr[j]; f < Pcol.rowptr[j + 1]; ++f) emit(Pcol.col[f], Pcol.val[f], v);
+        }
+      },
+      AP.ptr, AP.col, AP.val);
+  // C = Prow^T AP (rows coarse)
+  const CSR Rt = transpose(Prow);
+  NodeCSR C;
+  C.nrows = ncr;
+  C.nv = nv;
+  product(
+      ncr,
+      [&](long I, auto emit) {
+        for (int e = Rt.rowptr[I]; e < Rt.rowptr[I + 1]; ++e) {
+          const int i = Rt.col[e];
+          const double wgt = Rt.val[e];
+          for (long f = AP.ptr[i]; f < AP.ptr[i + 1]; ++f) emit(AP.col[f], wgt, AP.val.data() + (size_t)f * nv);
+        }
+      },
+      C.ptr, C.col, C.val);
+  return C;
+}
+
+// The node-level blocks of a level's spatial system (rows u-eq, v-eq, p-eq;
+// columns V, U, P): rho M (from the u-rows' U columns), K (d x d, v-rows' U
+// columns), C^T (v-rows' P columns), the p-rows' displacement coupling (V
+// columns for Problem 3.1, U columns for B.1) and (c0 Mp, B).  False when the
+// level does not have exactly this structure.
+struct NodeBlocks {
+  NodeCSR MM, KK, UP, PU, PP;
+};
+
+bool split_nodes(const Level &L, NodeBlocks *out) {
+  const int d = L.box.dim;
+  const long R = L.R, nu = R / d, S = L.S;
+  const bool b1 = L.form == STFEM_FORM_PROBLEM_B_1;
+  NodeBlocks &B = *out;
+  auto init = [](NodeCSR &m, long n, int nv) {
+    m.nrows = n;
+    m.nv = nv;
+    m.ptr.assign(n + 1, 0);
+  };
+  init(B.MM, nu, 1);
+  init(B.KK, nu, d * d);
+  init(B.UP, nu, d);
+  init(B.PU, S, d);
+  init(B.PP, S, 2);
+  std::atomic<bool> ok(true);
+  // counts per node row (from component 0 rows)
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (long I = 0; I < nu; ++I) {
+    long nm = 0, nk = 0, np = 0;
+    for (int e = L.rowptr[I * d]; e < L.rowptr[I * d + 1]; ++e)
+      if (L.col[e] >= R && L.col[e] < 2 * R && (L.col[e] - R) % d == 0) ++nm;
+    for (int e = L.rowptr[R + I * d]; e < L.rowptr[R + I * d + 1]; ++e) {
+      const long c = L.col[e];
+      if (c >= R && c < 2 * R && (c - R) % d == 0) ++nk;
+      if (c >= 2 * R) ++np;
+    }
+    B.MM.ptr[I + 1] = nm;
+    B.KK.ptr[I + 1] = nk;
+    B.UP.ptr[I + 1] = np;
+  }
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (long s = 0; s < S; ++s) {
+    long nuc = 0, npp = 0;
+    for (int e = L.rowptr[2 * R + s]; e < L.rowptr[2 * R + s + 1]; ++e) {
+      const long c = L.col[e];
+      if (c >= 2 * R) ++npp;
+      else if ((b1 ? (c >= R) : (c < R)) && (c % d) == 0) ++nuc;
+    }
+    B.PU.ptr[s + 1] = nuc;
+    B.PP.ptr[s + 1] = npp;
+  }
+  for (NodeCSR *m : {&B.MM, &B.KK, &B.UP, &B.PU, &B.PP}) {
+    for (long i = 0; i < m->nrows; ++i) m->ptr[i + 1] += m->ptr[i];
+    m->col.resize(m->ptr[m->nrows]);
+    m->val.resize((size_t)m->ptr[m->nrows] * m->nv);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)m->val.size(); ++i) m->val[i] = 0.0;
+  }
+  // values; every row of every component must fit the node pattern of
+  // component 0 (checked by position)
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long I = 0; I < nu; ++I) {
+    for (int c = 0; c < d; ++c) {
+      long em = B.MM.ptr[I];
+      for (int e = L.rowptr[I * d + c]; e < L.rowptr[I * d + c + 1]; ++e) {
+        const long col = L.col[e];
+        if (col >= R && col < 2 * R) {
+          if ((col - R) % d != c || em >= B.MM.ptr[I + 1] || L.v2[e] != 0.0) { ok = false; continue; }
+          if (c == 0) {
+            B.MM.col[em] = (int)((col - R) / d);
+            B.MM.val[em] = L.v1[e];
+          } else if (B.MM.col[em] != (col - R) / d || B.MM.val[em] != L.v1[e]) {
+            ok = false;
+          }
+          ++em;
+        }
+      }
+      long ek = B.KK.ptr[I], ep = B.UP.ptr[I];
+      for (int e = L.rowptr[R + I * d + c]; e < L.rowptr[R + I * d + c + 1]; ++e) {
+        const long col = L.col[e];
+        if (col >= R && col < 2 * R) {
+          const long J = (col - R) / d;
+          const int cp = (int)((col - R) % d);
+          if (L.v1[e] != 0.0) ok = false;
+          if (cp == 0) {
+            if (ek >= B.KK.ptr[I + 1]) { ok = false; continue; }
+            if (c == 0) B.KK.col[ek] = (int)J;
+            else if (B.KK.col[ek] != J) ok = false;
+            ++ek;
+          }
+          if (ek == B.KK.ptr[I] || B.KK.col[ek - 1] != J) { ok = false; continue; }
+          B.KK.val[(size_t)(ek - 1) * d * d + c * d + cp] = L.v2[e];
+        } else if (col >= 2 * R) {
+          if (ep >= B.UP.ptr[I + 1] || L.v1[e] != 0.0) { ok = false; continue; }
+          if (c == 0) B.UP.col[ep] = (int)(col - 2 * R);
+          else if (B.UP.col[ep] != col - 2 * R) ok = false;
+          B.UP.val[(size_t)ep * d + c] = L.v2[e];
+          ++ep;
+        }
+      }
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long s = 0; s < S; ++s) {
+    long eu = B.PU.ptr[s], ep = B.PP.ptr[s];
+    for (int e = L.rowptr[2 * R + s]; e < L.rowptr[2 * R + s + 1]; ++e) {
+      const long col = L.col[e];
+      if (col >= 2 * R) {
+        B.PP.col[ep] = (int)(col - 2 * R);
+        B.PP.val[(size_t)ep * 2] = L.v1[e];
+        B.PP.val[(size_t)ep * 2 + 1] = L.v2[e];
+        ++ep;
+      } else if (b1 ? (col >= R) : (col < R)) {
+        const long rem = b1 ? col - R : col;
+        const int cp = (int)(rem % d);
+        if ((b1 ? L.v2[e] : L.v1[e]) != 0.0) ok = false;
+        if (cp == 0) {
+          if (eu >= B.PU.ptr[s + 1]) { ok = false; continue; }
+          B.PU.col[eu] = (int)(rem / d);
+          ++eu;
+        }
+        if (eu == B.PU.ptr[s] || B.PU.col[eu - 1] != rem / d) { ok = false; continue; }
+        B.PU.val[(size_t)(eu - 1) * d + cp] = b1 ? L.v1[e] : L.v2[e];
+      } else if (L.v1[e] != 0.0 || L.v2[e] != 0.0) {
+        ok = false;
+      }
+    }
+  }
+  // the u-rows' V columns must be -rho M and the v-rows' V columns rho M
+  // (checked through their counts and values)
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long I = 0; I < nu; ++I)
+    for (int c = 0; c < d; ++c) {
+      long em = B.MM.ptr[I];
+      for (int e = L.rowptr[I * d + c]; e < L.rowptr[I * d + c + 1]; ++e)
+        if (L.col[e] < R) {
+          if (em >= B.MM.ptr[I + 1] || L.col[e] != B.MM.col[em] * d + c || L.v2[e] != -B.MM.val[em] || L.v1[e] != 0.0)
+            ok = false;
+          ++em;
+        } else if (L.col[e] >= 2 * R && (L.v1[e] != 0.0 || L.v2[e] != 0.0)) {
+          ok = false;
+        }
+      em = B.MM.ptr[I];
+      for (int e = L.rowptr[R + I * d + c]; e < L.rowptr[R + I * d + c + 1]; ++e)
+        if (L.col[e] < R) {
+          if (em >= B.MM.ptr[I + 1] || L.col[e] != B.MM.col[em] * d + c || L.v1[e] != B.MM.val[em] || L.v2[e] != 0.0)
+            ok = false;
+          ++em;
+        }
+    }
+  return ok;
+}
+
+// Coarse spatial CSR from its node-level blocks (the layout of the fine
+// level's rows: u-rows V then U columns, v-rows V, U, P, p-rows the
+// displacement coupling then P).
+void join_nodes(const NodeBlocks &B, Level *L) {
+  const int d = L->box.dim;
+  const long R = L->R, nu = R / d, S = L->S, ns = L->ns;
+  const bool b1 = L->form == STFEM_FORM_PROBLEM_B_1;
+  L->rowptr.assign(ns + 1, 0);
+  for (long I = 0; I < nu; ++I) {
+    const long nm = B.MM.ptr[I + 1] - B.MM.ptr[I], nk = B.KK.ptr[I + 1] - B.KK.ptr[I];
+    const long np = B.UP.ptr[I + 1] - B.UP.ptr[I];
+    for (int c = 0; c < d; ++c) {
+      L->rowptr[I * d + c + 1] = (int)(2 * nm);
+      L->rowptr[R + I * d + c + 1] = (int)(nm + d * nk + np);
+    }
+  }
+  for (long s = 0; s < S; ++s)
+    L->rowptr[2 * R + s + 1] = (int)(d * (B.PU.ptr[s + 1] - B.PU.ptr[s]) + (B.PP.ptr[s + 1] - B.PP.ptr[s]));
+  for (long i = 0; i < ns; ++i) L->rowptr[i + 1] += L->rowptr[i];
+  const long nnz = L->rowptr[ns];
+  L->col.resize(nnz);
+  L->v1.resize(nnz);
+  L->v2.resize(nnz);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long I = 0; I < nu; ++I)
+    for (int c = 0; c < d; ++c) {
+      long e = L->rowptr[I * d + c];
+      for (long m = B.MM.ptr[I]; m < B.MM.ptr[I + 1]; ++m, ++e) {
+        L->col[e] = (int)(B.MM.col[m] * d + c);
+        L->v1[e] = 0.0;
+        L->v2[e] = -B.MM.val[m];
+      }
+      for (long m = B.MM.ptr[I]; m < B.MM.ptr[I + 1]; ++m, ++e) {
+        L->col[e] = (int)(R + B.MM.col[m] * d + c);
+        L->v1[e] = B.MM.val[m];
+        L->v2[e] = 0.0;
+      }
+      e = L->rowptr[R + I * d + c];
+      for (long m = B.MM.ptr[I]; m < B.MM.ptr[I + 1]; ++m, ++e) {
+        L->col[e] = (int)(B.MM.col[m] * d + c);
+        L->v1[e] = B.MM.val[m];
+        L->v2[e] = 0.0;
+      }
+      for (long k = B.KK.ptr[I]; k < B.KK.ptr[I + 1]; ++k)
+        for (int cp = 0; cp < d; ++cp, ++e) {
+          L->col[e] = (int)(R + B.KK.col[k] * d + cp);
+          L->v1[e] = 0.0;
+          L->v2[e] = B.KK.val[(size_t)k * d * d + c * d + cp];
+        }
+      for (long p = B.UP.ptr[I]; p < B.UP.ptr[I + 1]; ++p, ++e) {
+        L->col[e] = (int)(2 * R + B.UP.col[p]);
+        L->v1[e] = 0.0;
+        L->v2[e] = B.UP.val[(size_t)p * d + c];
+      }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long s = 0; s < S; ++s) {
+    long e = L->rowptr[2 * R + s];
+    for (long u = B.PU.ptr[s]; u < B.PU.ptr[s + 1]; ++u)
+      for (int cp = 0; cp < d; ++cp, ++e) {
+        const double v = B.PU.val[(size_t)u * d + cp];
+        L->col[e] = (int)((b1 ? R : 0) + B.PU.col[u] * d + cp);
+        L->v1[e] = b1 ? v : 0.0;
+        L->v2[e] = b1 ? 0.0 : v;
+      }
+    for (long p = B.PP.ptr[s]; p < B.PP.ptr[s + 1]; ++p, ++e) {
+      L->col[e] = (int)(2 * R + B.PP.col[p]);
+      L->v1[e] = B.PP.val[(size_t)p * 2];
+      L->v2[e] = B.PP.val[(size_t)p * 2 + 1];
+    }
+  }
+}
+
+} // namespace
+
+void galerkin_scalar(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl);
+
 void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
+  // node level: one product per block with vector values (d^2 fewer index
+  // operations for the elasticity block); the scalar product otherwise
+  NodeBlocks B;
+  if (split_nodes(F, &B)) {
+    NodeBlocks C;
+    C.MM = node_rap(B.MM, Pu, Pu);
+    C.KK = node_rap(B.KK, Pu, Pu);
+    C.UP = node_rap(B.UP, Pu, Pp);
+    C.PU = node_rap(B.PU, Pp, Pu);
+    C.PP = node_rap(B.PP, Pp, Pp);
+    join_nodes(C, Cl);
+    return;
+  }
+  galerkin_scalar(F, Pu, Pp, Cl);
+}
+
+void galerkin_scalar(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
   const int d = F.box.dim;
   const long Rf = F.R, Rc = Cl->R, nsf = F.ns, nsc = Cl->ns;
   // spatial prolongation P_s (rows fine, cols coarse)
