@@ -1431,180 +1431,19 @@ void join_nodes(const NodeBlocks &B, Level *L) {
 
 } // namespace
 
-void galerkin_scalar(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl);
-
-void galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
-  // node level: one product per block with vector values (d^2 fewer index
-  // operations for the elasticity block); the scalar product otherwise
+bool galerkin(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
+  // one product P^T A P per node-level block, with vector values (d^2 fewer
+  // index operations for the elasticity block than a scalar product)
   NodeBlocks B;
-  if (split_nodes(F, &B)) {
-    NodeBlocks C;
-    C.MM = node_rap(B.MM, Pu, Pu);
-    C.KK = node_rap(B.KK, Pu, Pu);
-    C.UP = node_rap(B.UP, Pu, Pp);
-    C.PU = node_rap(B.PU, Pp, Pu);
-    C.PP = node_rap(B.PP, Pp, Pp);
-    join_nodes(C, Cl);
-    return;
-  }
-  galerkin_scalar(F, Pu, Pp, Cl);
-}
-
-void galerkin_scalar(const Level &F, const CSR &Pu, const CSR &Pp, Level *Cl) {
-  const int d = F.box.dim;
-  const long Rf = F.R, Rc = Cl->R, nsf = F.ns, nsc = Cl->ns;
-  // spatial prolongation P_s (rows fine, cols coarse)
-  std::vector<long> pptr(nsf + 1, 0);
-  std::vector<int> pcol;
-  std::vector<double> pval;
-  for (long i = 0; i < nsf; ++i) {
-    if (i < 2 * Rf) {
-      const long blk = i / Rf, rem = i % Rf, node = rem / d;
-      const int comp = (int)(rem % d);
-      for (int e = Pu.rowptr[node]; e < Pu.rowptr[node + 1]; ++e) {
-        pcol.push_back((int)(blk * Rc + (long)Pu.col[e] * d + comp));
-        pval.push_back(Pu.val[e]);
-      }
-    } else {
-      const long node = i - 2 * Rf;
-      for (int e = Pp.rowptr[node]; e < Pp.rowptr[node + 1]; ++e) {
-        pcol.push_back((int)(2 * Rc + Pp.col[e]));
-        pval.push_back(Pp.val[e]);
-      }
-    }
-    pptr[i + 1] = (long)pcol.size();
-  }
-  // P_s^T (rows coarse)
-  std::vector<long> tptr(nsc + 1, 0);
-  for (int c : pcol) tptr[c + 1]++;
-  for (long i = 0; i < nsc; ++i) tptr[i + 1] += tptr[i];
-  std::vector<int> tcol(pcol.size());
-  std::vector<double> tval(pcol.size());
-  {
-    std::vector<long> fill(tptr.begin(), tptr.end() - 1);
-    for (long i = 0; i < nsf; ++i)
-      for (long e = pptr[i]; e < pptr[i + 1]; ++e) {
-        long p = fill[pcol[e]]++;
-        tcol[p] = (int)i;
-        tval[p] = pval[e];
-      }
-  }
-  // AP = S P_s (rows fine), two value arrays.  Each worker appends the rows
-  // it builds to buffers of its own; a row is found by (worker, offset).
-  const int nt = n_threads();
-  struct RowBuf {
-    hvec<int> col;
-    hvec<double> v1, v2;
-  };
-  std::vector<RowBuf> apb(nt);
-  std::vector<int> ap_who(nsf), ap_len(nsf);
-  std::vector<long> ap_at(nsf);
-  {
-    std::atomic<long> next(0);
-    auto work = [&](int w) {
-      std::vector<double> acc(2 * nsc, 0.0); // (S1, S2) parts side by side
-      std::vector<char> mark(nsc, 0);
-      std::vector<int> touched;
-      RowBuf &o = apb[w];
-      for (;;) {
-        const long i0 = next.fetch_add(256);
-        if (i0 >= nsf) break;
-        for (long i = i0; i < std::min(nsf, i0 + 256); ++i) {
-          touched.clear();
-          for (int e = F.rowptr[i]; e < F.rowptr[i + 1]; ++e) {
-            const int j = F.col[e];
-            const double x1 = F.v1[e], x2 = F.v2[e];
-            for (long f = pptr[j]; f < pptr[j + 1]; ++f) {
-              const int J = pcol[f];
-              if (!mark[J]) {
-                mark[J] = 1;
-                touched.push_back(J);
-                acc[2 * J] = acc[2 * J + 1] = 0.0;
-              }
-              acc[2 * J] += x1 * pval[f];
-              acc[2 * J + 1] += x2 * pval[f];
-            }
-          }
-          std::sort(touched.begin(), touched.end());
-          ap_who[i] = w;
-          ap_at[i] = (long)o.col.size();
-          ap_len[i] = (int)touched.size();
-          for (const int J : touched) {
-            o.col.push_back(J);
-            o.v1.push_back(acc[2 * J]);
-            o.v2.push_back(acc[2 * J + 1]);
-            mark[J] = 0;
-          }
-        }
-      }
-    };
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
-    for (auto &t : th) t.join();
-  }
-  // C = P_s^T AP (rows coarse), the same way
-  std::vector<RowBuf> cb(nt);
-  std::vector<int> c_who(nsc), c_len(nsc);
-  std::vector<long> c_at(nsc);
-  {
-    std::atomic<long> next(0);
-    auto work = [&](int w) {
-      std::vector<double> acc(2 * nsc, 0.0);
-      std::vector<char> mark(nsc, 0);
-      std::vector<int> touched;
-      RowBuf &o = cb[w];
-      for (;;) {
-        const long I0 = next.fetch_add(64);
-        if (I0 >= nsc) break;
-        for (long I = I0; I < std::min(nsc, I0 + 64); ++I) {
-          touched.clear();
-          for (long e = tptr[I]; e < tptr[I + 1]; ++e) {
-            const int i = tcol[e];
-            const double wgt = tval[e];
-            const RowBuf &a = apb[ap_who[i]];
-            const int *rc = a.col.data() + ap_at[i];
-            const double *r1 = a.v1.data() + ap_at[i], *r2 = a.v2.data() + ap_at[i];
-            for (int t = 0; t < ap_len[i]; ++t) {
-              const int J = rc[t];
-              if (!mark[J]) {
-                mark[J] = 1;
-                touched.push_back(J);
-                acc[2 * J] = acc[2 * J + 1] = 0.0;
-              }
-              acc[2 * J] += wgt * r1[t];
-              acc[2 * J + 1] += wgt * r2[t];
-            }
-          }
-          std::sort(touched.begin(), touched.end());
-          c_who[I] = w;
-          c_at[I] = (long)o.col.size();
-          c_len[I] = (int)touched.size();
-          for (const int J : touched) {
-            o.col.push_back(J);
-            o.v1.push_back(acc[2 * J]);
-            o.v2.push_back(acc[2 * J + 1]);
-            mark[J] = 0;
-          }
-        }
-      }
-    };
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
-    for (auto &t : th) t.join();
-  }
-  Cl->rowptr.assign(nsc + 1, 0);
-  for (long I = 0; I < nsc; ++I) Cl->rowptr[I + 1] = Cl->rowptr[I] + c_len[I];
-  Cl->col.resize(Cl->rowptr[nsc]);
-  Cl->v1.resize(Cl->rowptr[nsc]);
-  Cl->v2.resize(Cl->rowptr[nsc]);
-#pragma omp parallel for schedule(dynamic, 256)
-  for (long I = 0; I < nsc; ++I) {
-    const RowBuf &a = cb[c_who[I]];
-    const long at = c_at[I], to = Cl->rowptr[I];
-    std::copy(a.col.begin() + at, a.col.begin() + at + c_len[I], Cl->col.begin() + to);
-    std::copy(a.v1.begin() + at, a.v1.begin() + at + c_len[I], Cl->v1.begin() + to);
-    std::copy(a.v2.begin() + at, a.v2.begin() + at + c_len[I], Cl->v2.begin() + to);
-  }
+  if (!split_nodes(F, &B)) return false;
+  NodeBlocks C;
+  C.MM = node_rap(B.MM, Pu, Pu);
+  C.KK = node_rap(B.KK, Pu, Pu);
+  C.UP = node_rap(B.UP, Pu, Pp);
+  C.PU = node_rap(B.PU, Pp, Pu);
+  C.PP = node_rap(B.PP, Pp, Pp);
+  join_nodes(C, Cl);
+  return true;
 }
 
 // ---------------------------------------------------------------- patches
@@ -2374,7 +2213,11 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
                    : prolongation((*levels)[l - 1].P, boxes[l - 1], (*levels)[l].P, boxes[l]);
   }
   if (galerkin_ops)
-    for (int l = nlev - 1; l >= 1; --l) galerkin((*levels)[l], (*Pu)[l], (*Pp)[l], &(*levels)[l - 1]);
+    for (int l = nlev - 1; l >= 1; --l)
+      if (!galerkin((*levels)[l], (*Pu)[l], (*Pp)[l], &(*levels)[l - 1])) {
+        *err = "level " + std::to_string(l) + " does not have the node-block structure of the spatial system";
+        return STFEM_ERR_STATE;
+      }
   return STFEM_OK;
 }
 

@@ -124,8 +124,9 @@ CSR prolongation(const Lattice &coarse, const Box &cbox, const Lattice &fine, co
 CSR transpose(const CSR &a);
 // Galerkin product P_s^T S P_s of the spatial system of `fine` (both value
 // arrays), P_s = blockdiag(Pu (x) I_d, Pu (x) I_d, Pp); fills the matrix of
-// `coarse` (whose sizes must be set).
-void galerkin(const Level &fine, const CSR &Pu, const CSR &Pp, Level *coarse);
+// `coarse` (whose sizes must be set).  Works on the node-level blocks of the
+// system; false if `fine` does not have that block structure.
+bool galerkin(const Level &fine, const CSR &Pu, const CSR &Pp, Level *coarse);
 
 // Eigen-decomposition of W^{-1} Dt = V diag(lam) V^{-1} used by the
 // time-diagonal form of the patch inverses.  Slots: the nr real eigenvalues
