@@ -36,7 +36,7 @@ def commands():
         cmds.append(cxx[:-1] + [cuda_inc, "-c", os.path.join(CSRC, src), "-o", o])
         objs.append(o)
     o = os.path.join(OUT, "stfem.cu.o")
-    cmds.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", inc,
+    cmds.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", inc,
                  "-c", os.path.join(CSRC, "stfem.cu"), "-o", o])
     objs.append(o)
     link = [nvcc, ARCH, "-shared", "-o", LIB] + objs + ["-lpthread", "-lgomp"]

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -491,11 +492,23 @@ int dalloc(stfem_h h, T **p, size_t n) {
   return 0;
 }
 
-template <typename T, typename S>
-int upload(stfem_h h, T **p, const std::vector<S> &src) {
+// src: any contiguous container (std::vector, stfem::hvec); copied as is
+// when the element types agree, else converted on the host (threaded)
+template <typename T, typename V>
+int upload(stfem_h h, T **p, const V &src) {
+  using S = typename V::value_type;
   CKR(dalloc(h, p, src.size()));
   if (src.empty()) return 0;
-  std::vector<T> tmp(src.begin(), src.end());
+  if (std::is_same<T, S>::value) {
+    CK(cudaMemcpy(*p, (const void *)src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return 0;
+  }
+  stfem::hvec<T> tmp(src.size());
+  const long n = (long)src.size();
+  const S *in = src.data();
+  T *o = tmp.data();
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < n; ++i) o[i] = (T)in[i];
   CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
   return 0;
 }
@@ -613,7 +626,7 @@ void launch_spmv_df(stfem_h h, const DLevel<double> &L, const TimeCoef<double> &
 struct NodeBlockHost {
   long nu = 0, np = 0;
   std::vector<int> uu_ptr, up_ptr, pu_ptr, pp_ptr;
-  std::vector<double> uu_m, uu_k, up_c, pu_c, pp_m, pp_b;
+  stfem::hvec<double> uu_m, uu_k, up_c, pu_c, pp_m, pp_b;
   // broken pressure space: the "pressure nodes" are the pnl dofs of each cell;
   // up_c runs over the cells holding a displacement node (x fastest) times
   // pnl, pu_c over the (r+1)^d nodes of the dof's cell, pp_* over 2d+1 cell
@@ -712,37 +725,56 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
   H.up_ptr.assign(nu + 1, 0);
   H.pu_ptr.assign(np + 1, 0);
   H.pp_ptr.assign(np + 1, 0);
-  int a[3];
+  // sizes per node (threaded), then the offsets
+#pragma omp parallel for schedule(static)
   for (long I = 0; I < nu; ++I) {
+    int a[3];
     coords_of(I, ud, d, a);
-    H.uu_ptr[I + 1] = H.uu_ptr[I] + (int)host_box(a, r, r, nc, d).size;
-    H.up_ptr[I + 1] = H.up_ptr[I] + (int)(disc ? cell_box(a, r, nc, d).size * pnl : host_box(a, r, r - 1, nc, d).size);
+    H.uu_ptr[I + 1] = (int)host_box(a, r, r, nc, d).size;
+    H.up_ptr[I + 1] = (int)(disc ? cell_box(a, r, nc, d).size * pnl : host_box(a, r, r - 1, nc, d).size);
   }
+#pragma omp parallel for schedule(static)
   for (long sI = 0; sI < np; ++sI) {
     if (disc) {
-      H.pu_ptr[sI + 1] = H.pu_ptr[sI] + nuloc;
-      H.pp_ptr[sI + 1] = H.pp_ptr[sI] + (2 * d + 1) * pnl;
+      H.pu_ptr[sI + 1] = nuloc;
+      H.pp_ptr[sI + 1] = (2 * d + 1) * pnl;
       continue;
     }
+    int a[3];
     coords_of(sI, pd, d, a);
-    H.pu_ptr[sI + 1] = H.pu_ptr[sI] + (int)host_box(a, r - 1, r, nc, d).size;
-    H.pp_ptr[sI + 1] = H.pp_ptr[sI] + (int)host_box(a, r - 1, r - 1, nc, d).size;
+    H.pu_ptr[sI + 1] = (int)host_box(a, r - 1, r, nc, d).size;
+    H.pp_ptr[sI + 1] = (int)host_box(a, r - 1, r - 1, nc, d).size;
   }
-  H.uu_m.assign(H.uu_ptr[nu], 0.0);
-  H.uu_k.assign((size_t)H.uu_ptr[nu] * d * d, 0.0);
-  H.up_c.assign((size_t)H.up_ptr[nu] * d, 0.0);
-  H.pu_c.assign((size_t)H.pu_ptr[np] * d, 0.0);
-  H.pp_m.assign(H.pp_ptr[np], 0.0);
-  H.pp_b.assign(H.pp_ptr[np], 0.0);
-  double scale = 0.0;
-  for (double v : L.v1) scale = std::max(scale, std::fabs(v));
-  for (double v : L.v2) scale = std::max(scale, std::fabs(v));
-  const double tol = 1e-12 * scale;
-  auto bad = [&](const char *what) {
-    *err = std::string("level operator does not have the expected block/box structure: ") + what;
-    return STFEM_ERR_STATE;
-  };
   for (long I = 0; I < nu; ++I) {
+    H.uu_ptr[I + 1] += H.uu_ptr[I];
+    H.up_ptr[I + 1] += H.up_ptr[I];
+  }
+  for (long sI = 0; sI < np; ++sI) {
+    H.pu_ptr[sI + 1] += H.pu_ptr[sI];
+    H.pp_ptr[sI + 1] += H.pp_ptr[sI];
+  }
+  auto zeros = [](stfem::hvec<double> &v, size_t n) {
+    v.resize(n);
+    double *p = v.data();
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)n; ++i) p[i] = 0.0;
+  };
+  zeros(H.uu_m, H.uu_ptr[nu]);
+  zeros(H.uu_k, (size_t)H.uu_ptr[nu] * d * d);
+  zeros(H.up_c, (size_t)H.up_ptr[nu] * d);
+  zeros(H.pu_c, (size_t)H.pu_ptr[np] * d);
+  zeros(H.pp_m, H.pp_ptr[np]);
+  zeros(H.pp_b, H.pp_ptr[np]);
+  double scale = 0.0;
+  const long nnz = (long)L.v1.size();
+#pragma omp parallel for schedule(static) reduction(max : scale)
+  for (long e = 0; e < nnz; ++e) scale = std::max(scale, std::max(std::fabs(L.v1[e]), std::fabs(L.v2[e])));
+  const double tol = 1e-12 * scale;
+  // the nodes are independent (each writes its own ranges); the first
+  // structure violation found is reported
+  std::atomic<const char *> fault(nullptr);
+  auto node_u = [&](long I) -> const char * {
+    int a[3];
     coords_of(I, ud, d, a);
     const HostBox bu = host_box(a, r, r, nc, d);
     const HostBox bp = disc ? HostBox{} : host_box(a, r, r - 1, nc, d), cb = disc ? cell_box(a, r, nc, d) : HostBox{};
@@ -752,19 +784,19 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
       for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
         const long col = L.col[e];
         if (col >= 2 * R) {
-          if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) return bad("u-equation couples to P");
+          if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) return "u-equation couples to P";
           continue;
         }
         const long blk = col / R, rem = col % R, J = rem / d;
         const long pos = box_pos(bu, J, ud, d);
-        if (pos < 0 || rem % d != c) return bad("u-equation entry outside the box");
+        if (pos < 0 || rem % d != c) return "u-equation entry outside the box";
         const size_t at = (size_t)H.uu_ptr[I] + pos;
         if (blk == 1) {
           if (c == 0) H.uu_m[at] = L.v1[e];
-          else if (std::fabs(L.v1[e] - H.uu_m[at]) > tol) return bad("u-equation mass differs between components");
-          if (std::fabs(L.v2[e]) > tol) return bad("u-equation U block has a W part");
+          else if (std::fabs(L.v1[e] - H.uu_m[at]) > tol) return "u-equation mass differs between components";
+          if (std::fabs(L.v2[e]) > tol) return "u-equation U block has a W part";
         } else if (std::fabs(L.v1[e]) > tol) {
-          return bad("u-equation V block has a Dt part");
+          return "u-equation V block has a Dt part";
         }
       }
     }
@@ -774,7 +806,7 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
         const long col = L.col[e];
         if (col < R) {
           const size_t at = (size_t)H.uu_ptr[I] + box_pos(bu, col / d, ud, d);
-          if (std::fabs(L.v2[e] + H.uu_m[at]) > tol) return bad("u-equation V block is not -rho M");
+          if (std::fabs(L.v2[e] + H.uu_m[at]) > tol) return "u-equation V block is not -rho M";
         }
       }
       // v-equation row (I, c)
@@ -783,90 +815,111 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
         const long col = L.col[e];
         if (col < R) {
           const long pos = box_pos(bu, col / d, ud, d);
-          if (pos < 0 || col % d != c) return bad("v-equation V entry outside the box");
+          if (pos < 0 || col % d != c) return "v-equation V entry outside the box";
           if (std::fabs(L.v1[e] - H.uu_m[(size_t)H.uu_ptr[I] + pos]) > tol || std::fabs(L.v2[e]) > tol)
-            return bad("v-equation V block is not rho M");
+            return "v-equation V block is not rho M";
         } else if (col < 2 * R) {
           const long pos = box_pos(bu, (col - R) / d, ud, d);
-          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("elasticity entry outside the box");
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return "elasticity entry outside the box";
           H.uu_k[((size_t)H.uu_ptr[I] + pos) * d * d + c * d + (col - R) % d] = L.v2[e];
         } else if (disc) {
           const long cell = (col - 2 * R) / pnl, sl = (col - 2 * R) % pnl;
           const long pos = box_pos(cb, cell, nc, d);
-          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("coupling entry outside the cells of the node");
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return "coupling entry outside the cells of the node";
           H.up_c[((size_t)H.up_ptr[I] + pos * pnl + sl) * d + c] = L.v2[e];
         } else {
           const long pos = box_pos(bp, col - 2 * R, pd, d);
-          if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("coupling entry outside the box");
+          if (pos < 0 || std::fabs(L.v1[e]) > tol) return "coupling entry outside the box";
           H.up_c[((size_t)H.up_ptr[I] + pos) * d + c] = L.v2[e];
         }
       }
     }
-  }
-  for (long sI = 0; disc && sI < np; ++sI) {
-    // broken pressure dof s of cell `cell`
-    const long cell = sI / pnl;
-    int cm[3];
-    coords_of(cell, nc, d, cm);
+    return nullptr;
+  };
+  auto node_p = [&](long sI) -> const char * {
     const long rp = 2 * R + sI;
-    for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
-      const long col = L.col[e];
-      if ((!b1 && col < R) || (b1 && col >= R && col < 2 * R)) {
-        const long rem = b1 ? col - R : col, J = rem / d;
-        int aj[3];
-        coords_of(J, ud, d, aj);
-        int j = 0, stride = 1;
-        bool in = true;
-        for (int i = 0; i < d; ++i) {
-          const int o = aj[i] - r * cm[i];
-          in = in && o >= 0 && o <= r;
-          j += o * stride;
-          stride *= r + 1;
+    if (disc) {
+      // broken pressure dof of cell `cell`
+      const long cell = sI / pnl;
+      int cm[3];
+      coords_of(cell, nc, d, cm);
+      for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
+        const long col = L.col[e];
+        if ((!b1 && col < R) || (b1 && col >= R && col < 2 * R)) {
+          const long rem = b1 ? col - R : col, J = rem / d;
+          int aj[3];
+          coords_of(J, ud, d, aj);
+          int j = 0, stride = 1;
+          bool in = true;
+          for (int i = 0; i < d; ++i) {
+            const int o = aj[i] - r * cm[i];
+            in = in && o >= 0 && o <= r;
+            j += o * stride;
+            stride *= r + 1;
+          }
+          if (!in || std::fabs(b1 ? L.v2[e] : L.v1[e]) > tol) return "p-equation displacement entry outside its cell";
+          H.pu_c[((size_t)H.pu_ptr[sI] + j) * d + rem % d] = b1 ? L.v1[e] : L.v2[e];
+        } else if (col >= 2 * R) {
+          const long cell2 = (col - 2 * R) / pnl, t = (col - 2 * R) % pnl;
+          int c2[3];
+          coords_of(cell2, nc, d, c2);
+          int slot = -1, diff = 0;
+          for (int i = 0; i < d; ++i) diff += std::abs(c2[i] - cm[i]);
+          if (diff == 0) slot = 0;
+          else if (diff == 1)
+            for (int i = 0; i < d; ++i)
+              if (c2[i] != cm[i]) slot = 1 + 2 * i + (c2[i] > cm[i] ? 1 : 0);
+          if (slot < 0) return "p-equation pressure entry outside the face neighbours";
+          const size_t at = (size_t)H.pp_ptr[sI] + (size_t)slot * pnl + t;
+          H.pp_m[at] = L.v1[e];
+          H.pp_b[at] = L.v2[e];
+        } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
+          return b1 ? "p-equation couples to V" : "p-equation couples to U";
         }
-        if (!in || std::fabs(b1 ? L.v2[e] : L.v1[e]) > tol) return bad("p-equation displacement entry outside its cell");
-        H.pu_c[((size_t)H.pu_ptr[sI] + j) * d + rem % d] = b1 ? L.v1[e] : L.v2[e];
-      } else if (col >= 2 * R) {
-        const long cell2 = (col - 2 * R) / pnl, t = (col - 2 * R) % pnl;
-        int c2[3];
-        coords_of(cell2, nc, d, c2);
-        int slot = -1, diff = 0;
-        for (int i = 0; i < d; ++i) diff += std::abs(c2[i] - cm[i]);
-        if (diff == 0) slot = 0;
-        else if (diff == 1)
-          for (int i = 0; i < d; ++i)
-            if (c2[i] != cm[i]) slot = 1 + 2 * i + (c2[i] > cm[i] ? 1 : 0);
-        if (slot < 0) return bad("p-equation pressure entry outside the face neighbours");
-        const size_t at = (size_t)H.pp_ptr[sI] + (size_t)slot * pnl + t;
-        H.pp_m[at] = L.v1[e];
-        H.pp_b[at] = L.v2[e];
-      } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
-        return bad(b1 ? "p-equation couples to V" : "p-equation couples to U");
       }
+      return nullptr;
     }
-  }
-  for (long sI = 0; !disc && sI < np; ++sI) {
+    int a[3];
     coords_of(sI, pd, d, a);
     const HostBox bu = host_box(a, r - 1, r, nc, d), bp = host_box(a, r - 1, r - 1, nc, d);
-    const long rp = 2 * R + sI;
     for (int e = L.rowptr[rp]; e < L.rowptr[rp + 1]; ++e) {
       const long col = L.col[e];
       if (!b1 && col < R) { // Problem 3.1: -C on V through W
         const long pos = box_pos(bu, col / d, ud, d);
-        if (pos < 0 || std::fabs(L.v1[e]) > tol) return bad("p-equation V entry outside the box");
+        if (pos < 0 || std::fabs(L.v1[e]) > tol) return "p-equation V entry outside the box";
         H.pu_c[((size_t)H.pu_ptr[sI] + pos) * d + col % d] = L.v2[e];
       } else if (b1 && col >= R && col < 2 * R) { // Problem B.1: -C on U through Dt
         const long pos = box_pos(bu, (col - R) / d, ud, d);
-        if (pos < 0 || std::fabs(L.v2[e]) > tol) return bad("p-equation U entry outside the box");
+        if (pos < 0 || std::fabs(L.v2[e]) > tol) return "p-equation U entry outside the box";
         H.pu_c[((size_t)H.pu_ptr[sI] + pos) * d + (col - R) % d] = L.v1[e];
       } else if (col >= 2 * R) {
         const long pos = box_pos(bp, col - 2 * R, pd, d);
-        if (pos < 0) return bad("p-equation P entry outside the box");
+        if (pos < 0) return "p-equation P entry outside the box";
         H.pp_m[(size_t)H.pp_ptr[sI] + pos] = L.v1[e];
         H.pp_b[(size_t)H.pp_ptr[sI] + pos] = L.v2[e];
       } else if (std::fabs(L.v1[e]) > tol || std::fabs(L.v2[e]) > tol) {
-        return bad(b1 ? "p-equation couples to V" : "p-equation couples to U");
+        return b1 ? "p-equation couples to V" : "p-equation couples to U";
       }
     }
+    return nullptr;
+  };
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long I = 0; I < nu; ++I) {
+    if (fault.load(std::memory_order_relaxed)) continue;
+    const char *f = node_u(I);
+    const char *none = nullptr;
+    if (f) fault.compare_exchange_strong(none, f);
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long sI = 0; sI < np; ++sI) {
+    if (fault.load(std::memory_order_relaxed)) continue;
+    const char *f = node_p(sI);
+    const char *none = nullptr;
+    if (f) fault.compare_exchange_strong(none, f);
+  }
+  if (const char *f = fault.load()) {
+    *err = std::string("level operator does not have the expected block/box structure: ") + f;
+    return STFEM_ERR_STATE;
   }
   return 0;
 }
@@ -1025,9 +1078,11 @@ int upload_level_df(stfem_h h, DLevel<double> &D, const stfem::Level &L) {
     h->err = err;
     return STFEM_ERR_STATE;
   }
-  auto split = [](const std::vector<double> &v) {
-    std::vector<float2> o(v.size());
-    for (size_t i = 0; i < v.size(); ++i) {
+  auto split = [](const stfem::hvec<double> &v) {
+    stfem::hvec<float2> o(v.size());
+    const long n = (long)v.size();
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) {
       const float hi = (float)v[i];
       o[i] = make_float2(hi, (float)(v[i] - (double)hi));
     }
