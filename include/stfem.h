@@ -45,6 +45,7 @@ extern "C" {
 #define STFEM_ERR_BREAKDOWN (-4)
 #define STFEM_ERR_STATE (-5)
 #define STFEM_ERR_OOM (-6)
+#define STFEM_ERR_TIMEOUT (-7) /* a bounded wait inside a kernel ran out (see stfem_set_wait_limit) */
 
 #define STFEM_BC_DIRICHLET 0 /* homogeneous Dirichlet, imposed by Nitsche's method */
 #define STFEM_BC_NEUMANN 1   /* natural condition; data from the problem id */
@@ -98,8 +99,8 @@ typedef struct {
  * CONTINUOUS: Q_{r-1}, the Taylor-Hood pair Q_r^d / Q_{r-1} (default).
  * BROKEN: P_{r-1}^disc, polynomials of total degree r-1 on each cell, with the
  *   interior penalty form B_gamma over interior faces and Dirichlet faces of p
- *   (gamma = r (r-1) / 2).  Host setup and footprint estimate only for now:
- *   stfem_setup and stfem_server_submit return STFEM_ERR_ARG for it. */
+ *   (gamma = r (r-1) / 2).  Device path in 2D; stfem_setup and
+ *   stfem_server_submit return STFEM_ERR_ARG for it in 3D. */
 #define STFEM_PRESSURE_CONTINUOUS 0
 #define STFEM_PRESSURE_BROKEN 1
 
@@ -215,6 +216,29 @@ int stfem_set_stop(stfem_h h, int mode);
  * the legacy default stream). */
 int stfem_set_stream(stfem_h h, void *stream);
 
+/* Launch shape of the persistent patch-apply kernels (the streaming and the
+ * tensor-core apply of Algorithm 4.1): at most max_ctas CTAs per launch, each
+ * taking patches p = cta, cta + grid, ... (0, the default: as many as fit on
+ * the device's multiprocessors).  A cap leaves SMs to the kernels of other
+ * handles that run concurrently (the serving loop), and with a small cap every
+ * CTA walks many patches.  Results do not depend on it: a patch's arithmetic
+ * is the same in every CTA.  STFEM_ERR_ARG for max_ctas < 0. */
+int stfem_set_launch_cap(stfem_h h, int max_ctas);
+
+/* Longest a bounded wait of the streaming patch apply may take before the
+ * kernel gives up: its CTAs then leave at the next patch boundary (after the
+ * copies in flight have landed), and the call that launched it returns
+ * STFEM_ERR_TIMEOUT.  seconds in (0, 60]; default about 2 s.  The handle
+ * stays usable: the timeout flag is cleared when it is reported. */
+int stfem_set_wait_limit(stfem_h h, double seconds);
+
+/* Failure-detection check of the bounded waits: on != 0 makes the streaming
+ * patch apply's producer issue no copy, so that every consumer's wait runs out
+ * after the wait limit (nothing is in flight when the kernel leaves, nothing
+ * faults or hangs); 0 restores normal operation.  No counterpart in the
+ * paper. */
+int stfem_stall_copies(stfem_h h, int on);
+
 /* Sizes: *n_slab = q (2R+S) of level l (l = -1: finest), *n_state = 2R+S,
  * *n_patches of level l, *inv_bytes = bytes of the stored patch inverses of
  * level l in the current precision. */
@@ -250,10 +274,13 @@ int stfem_vcycle(stfem_h h, const double *b, double *d);
  * applied twice.  x: in = initial guess x0, out = solution.  Stops when the
  * least-squares residual satisfies |g_{j+1}| <= tol ||rhs - A x0|| and the
  * recomputed true residual confirms it, or after max_it iterations.
- * *iters: iterations done; *rel_res: final true ||rhs - A x|| / ||rhs - A x0||.
- * Returns STFEM_OK, STFEM_NOT_CONVERGED or STFEM_ERR_BREAKDOWN (NaN/Inf). */
+ * *iters: iterations done; *rel_res: final true ||rhs - A x|| / ||rhs - A x0||;
+ * *abs_res: final true ||rhs - A x|| (the quantity the paper's absolute
+ * stopping rule of Sec. 5 bounds).  iters, rel_res, abs_res: host, may be NULL.
+ * Returns STFEM_OK, STFEM_NOT_CONVERGED, STFEM_ERR_BREAKDOWN (NaN/Inf) or
+ * STFEM_ERR_TIMEOUT (a bounded device wait ran out). */
 int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart, int max_it,
-               int *iters, double *rel_res);
+               int *iters, double *rel_res, double *abs_res);
 
 /* History |g_j| / ||rhs - A x0|| of the last slab_solve (j = 0..iters) into
  * hist_host (capacity cap); *n = number of entries written. */
@@ -328,6 +355,12 @@ int march_batch(stfem_h h, int n_rhs, const double *t0_host, int first_slab, int
  * the paper beyond the product itself (Eq. 4.7). */
 int stfem_apply_krylov(stfem_h h, const double *x, double *y);
 
+/* n_sweeps smoothing steps of Algorithm 4.1 on level l >= 1 for n_rhs columns
+ * of b and d (column stride n_slab of the level), as stfem_smooth does for
+ * each column, with every patch inverse read once per sweep for all columns
+ * (on tensor cores on the FP32 levels of a mixed handle). */
+int stfem_smooth_batch(stfem_h h, int level, int n_rhs, const double *b, double *d, int n_sweeps, int zero_init);
+
 /* d = M^{-1} b for n_rhs columns (one batched V-cycle, as stfem_vcycle). */
 int stfem_vcycle_batch(stfem_h h, int n_rhs, const double *b, double *d);
 /* Nodal interpolant of the problem's exact state at time t (as
@@ -400,30 +433,37 @@ int stfem_server_result(stfem_server s, long long id, double timeout_s, stfem_re
 void stfem_server_destroy(stfem_server s);
 
 /* ---- Allocation-free smoothing ----
- * No counterpart in the paper: an interface for callers that must not
- * allocate device memory at call time, e.g. code that runs while a CUDA stream
- * is being captured into a graph (cudaMalloc is not allowed there), solvers
- * embedded in a host application that fixes its device-memory budget after
- * start-up, or latency-critical loops where an allocation would stall.
+ * No counterpart in the paper: an entry point for callers that cannot call
+ * cudaMalloc while they run.  Examples: a host application that reserves all
+ * the device memory it will ever use at start-up and hands the rest to a pool
+ * of its own (an allocation later would fail, or take memory the pool counts
+ * on), an allocator-less embedding such as a plug-in that may only touch the
+ * buffers its host passes in, and latency-critical loops where a cudaMalloc
+ * (which can synchronise the device) would stall the other streams.
  *
- * stfem_smooth_noalloc does exactly what stfem_smooth does (n_sweeps averaged
- * Vanka sweeps of Algorithm 4.1 on level l >= 1, in the level's precision),
- * but takes its scratch memory (the level-precision copies of b and d, the
+ * stfem_smooth_noalloc does what stfem_smooth does (n_sweeps averaged Vanka
+ * sweeps of Algorithm 4.1 on level l >= 1, in the level's precision, with the
+ * same kernels: on a tensor-core level of a handle set up for several
+ * right-hand sides it uses the tensor-core apply, as stfem_smooth does), but
+ * takes its scratch memory (the level-precision copies of b and d, the
  * residual and the patch results) from one static device array of
  * STFEM_NOALLOC_SCRATCH_BYTES bytes that is part of the library (every GPU
  * that loads the library holds it until the process exits).  It calls no
- * cudaMalloc or cudaFree.  The caller passes b and d (device, FP64, n_slab of
- * the level) as for stfem_smooth; the handle's setup data are only read.
+ * cudaMalloc, cudaFree or allocating library routine.  The caller passes b
+ * and d (device, FP64, n_slab of the level) as for stfem_smooth; the handle's
+ * setup data are only read.
  *
  * Needs (3 n_slab + sum of patch sizes) * (4 in STFEM_MIXED, 8 in STFEM_FP64)
- * bytes of scratch; larger levels are rejected with STFEM_ERR_ARG and a
- * message naming the sizes.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  The current device must be the one
- * the handle was set up on.  Every call, from every handle, shares the one
- * array and it keeps the last call's contents: calls that may overlap on the
- * GPU (other streams, other host threads) race and must be serialised by the
- * caller.  Profiling (stfem_profile) must be off, since it creates events. */
+ * bytes of scratch (each part rounded up to 256 bytes); larger levels are
+ * rejected with STFEM_ERR_ARG and a message naming the sizes.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current.  The current device must be the one the handle was set
+ * up on.  Every call, from every handle, shares the one array and it keeps the
+ * last call's contents (each call overwrites what it reads before reading
+ * it): calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  The call synchronises the
+ * handle's stream before it returns.  Profiling (stfem_profile) must be off,
+ * since it creates events. */
 #define STFEM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int stfem_smooth_noalloc(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init);
 

@@ -21,6 +21,9 @@ def case(name, seed=SEED):
     if name == "c1_2d_q2_k1_8":  # 2D unit square 8x8, Q2/Q1, k=1, 3 levels
         return dict(dim=2, n=8, levels=3, r=2, k=1, tau=0.01, slabs=10, rho=1.0, alpha=1.0, c0=1.0,
                     lam=1.0, mu=1.0, kappa=1.0, problem="sin", tol=1e-10)
+    if name == "c1_2d_q2_k1_32":  # the 8x8 recipe on 32x32, 4 levels (1,089 fine patches)
+        return dict(dim=2, n=32, levels=4, r=2, k=1, tau=0.01, slabs=2, rho=1.0, alpha=1.0, c0=1.0,
+                    lam=1.0, mu=1.0, kappa=1.0, problem="sin", tol=1e-10)
     if name == "c2_2d_q3_k2_64":  # 2D 64x64, 5 levels, Q3/Q2, k=2, random materials
         lam = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
         mu = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libstfem.so")
 
 OK = 0
 NOT_CONVERGED = 1
-ERR_ARG, ERR_CUDA, ERR_SINGULAR_PATCH, ERR_BREAKDOWN, ERR_STATE, ERR_OOM = -1, -2, -3, -4, -5, -6
+ERR_ARG, ERR_CUDA, ERR_SINGULAR_PATCH, ERR_BREAKDOWN, ERR_STATE, ERR_OOM, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 DIRICHLET, NEUMANN = 0, 1
 PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPERCONV = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
@@ -95,11 +95,15 @@ def _load():
         "stfem_apply": [P, I, P, P],
         "stfem_smooth": [P, I, P, P, I, I],
         "stfem_smooth_noalloc": [P, I, P, P, I, I],
+        "stfem_smooth_batch": [P, I, I, P, P, I, I],
         "stfem_restrict": [P, I, P, P],
         "stfem_prolongate_add": [P, I, P, P],
         "stfem_coarse_solve": [P, P, P],
         "stfem_vcycle": [P, P, P],
-        "slab_solve": [P, P, P, D, I, I, pI, pD],
+        "slab_solve": [P, P, P, D, I, I, pI, pD, pD],
+        "stfem_set_launch_cap": [P, I],
+        "stfem_set_wait_limit": [P, D],
+        "stfem_stall_copies": [P, I],
         "stfem_solve_history": [P, pD, I, pI],
         "stfem_initial_state": [P, P],
         "stfem_slab_rhs": [P, I, P, P],
@@ -319,6 +323,11 @@ class Solver:
     def smooth(self, level, b, d, n_sweeps=1, zero_init=True):
         self._check(lib.stfem_smooth(self.h, level, _ptr(b), _ptr(d), n_sweeps, int(bool(zero_init))))
 
+    def smooth_batch(self, level, n_rhs, b, d, n_sweeps=1, zero_init=True):
+        """n_rhs columns (column stride n_slab of the level) smoothed together."""
+        self._check(lib.stfem_smooth_batch(self.h, level, n_rhs, _ptr(b), _ptr(d), n_sweeps,
+                                           int(bool(zero_init))))
+
     def smooth_noalloc(self, level, b, d, n_sweeps=1, zero_init=True):
         """stfem_smooth_noalloc: the same sweeps with the library's static scratch array."""
         self._check(lib.stfem_smooth_noalloc(self.h, level, _ptr(b), _ptr(d), n_sweeps, int(bool(zero_init))))
@@ -336,10 +345,25 @@ class Solver:
         self._check(lib.stfem_vcycle(self.h, _ptr(b), _ptr(d)))
 
     def slab_solve(self, rhs, x, tol=1e-8, restart=30, max_it=500):
-        it, rr = C.c_int(), C.c_double()
+        """(status, iterations, relative true residual); the absolute true
+        residual of the same solve is kept in ``self.abs_res``."""
+        it, rr, ra = C.c_int(), C.c_double(), C.c_double()
         rc = self._check(lib.slab_solve(self.h, _ptr(rhs), _ptr(x), tol, restart, max_it, C.byref(it),
-                                        C.byref(rr)))
+                                        C.byref(rr), C.byref(ra)))
+        self.abs_res = ra.value
         return rc, it.value, rr.value
+
+    def set_launch_cap(self, max_ctas):
+        """At most max_ctas CTAs per persistent patch-apply launch (0: as many as fit)."""
+        self._check(lib.stfem_set_launch_cap(self.h, int(max_ctas)))
+
+    def set_wait_limit(self, seconds):
+        """Longest bounded wait of the streaming patch apply before it reports ERR_TIMEOUT."""
+        self._check(lib.stfem_set_wait_limit(self.h, float(seconds)))
+
+    def stall_copies(self, on):
+        """Failure-detection check: the streaming patch apply issues no copy while on."""
+        self._check(lib.stfem_stall_copies(self.h, int(bool(on))))
 
     def history(self, cap=4096):
         buf = np.zeros(cap)

@@ -1280,6 +1280,7 @@ bool split_nodes(const Level &L, NodeBlocks *out) {
           ++em;
         }
       }
+      if (em != B.MM.ptr[I + 1]) ok = false; // a strict prefix of component 0's pattern
       long ek = B.KK.ptr[I], ep = B.UP.ptr[I];
       for (int e = L.rowptr[R + I * d + c]; e < L.rowptr[R + I * d + c + 1]; ++e) {
         const long col = L.col[e];
@@ -1303,6 +1304,7 @@ bool split_nodes(const Level &L, NodeBlocks *out) {
           ++ep;
         }
       }
+      if (ek != B.KK.ptr[I + 1] || ep != B.UP.ptr[I + 1]) ok = false;
     }
   }
 #pragma omp parallel for schedule(dynamic, 256)
@@ -1330,6 +1332,7 @@ bool split_nodes(const Level &L, NodeBlocks *out) {
         ok = false;
       }
     }
+    if (eu != B.PU.ptr[s + 1] || ep != B.PP.ptr[s + 1]) ok = false;
   }
   // the u-rows' V columns must be -rho M and the v-rows' V columns rho M
   // (checked through their counts and values)
@@ -1345,6 +1348,7 @@ bool split_nodes(const Level &L, NodeBlocks *out) {
         } else if (L.col[e] >= 2 * R && (L.v1[e] != 0.0 || L.v2[e] != 0.0)) {
           ok = false;
         }
+      if (em != B.MM.ptr[I + 1]) ok = false;
       em = B.MM.ptr[I];
       for (int e = L.rowptr[R + I * d + c]; e < L.rowptr[R + I * d + c + 1]; ++e)
         if (L.col[e] < R) {
@@ -1352,6 +1356,7 @@ bool split_nodes(const Level &L, NodeBlocks *out) {
             ok = false;
           ++em;
         }
+      if (em != B.MM.ptr[I + 1]) ok = false;
     }
   return ok;
 }

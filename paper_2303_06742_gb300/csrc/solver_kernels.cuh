@@ -100,7 +100,7 @@ __global__ void k_copy_cols(long n, int nb, const A *__restrict__ a, long sa, B 
 }
 
 // ---------------------------------------------------------------- BLAS-1 (FP64)
-constexpr int DOT_BLOCKS = 608; // 4 x 152 SMs
+// (the dot products run 4 blocks per SM: stfem_ctx::dot_blocks)
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_NV = 8;
 

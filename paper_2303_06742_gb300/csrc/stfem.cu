@@ -108,7 +108,9 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 
 constexpr int STREAM_STAGES = 4;                    // most stages of the ring (runtime: nst)
 constexpr int STREAM_CHUNK = 16384;                 // bytes per shared-memory stage
-constexpr long long STREAM_WAIT_LIMIT = 4000000000LL; // clock cycles (about 2 s)
+// clock cycles a drain of copies in flight may wait (about 2 s at 2 GHz);
+// the other waits take the handle's limit (stfem_set_wait_limit)
+constexpr long long STREAM_WAIT_LIMIT = 4000000000LL;
 // shared-memory bytes before the per-patch vectors: the ring, the barriers
 __host__ __device__ constexpr int stream_header(int nst) { return nst * STREAM_CHUNK + 2 * STREAM_STAGES * 8 + 16; }
 
@@ -119,8 +121,11 @@ __host__ __device__ constexpr int stream_header(int nst) { return nst * STREAM_C
 // 16-byte aligned, a multiple of 16 bytes) into a ring of nst <= STREAM_STAGES
 // shared stages.  The other warps gather and mix the residual, consume the
 // chunks of their slot rows from shared memory, and mix the result back.
-// Every wait is bounded; on a timeout the CTA sets *err, the producer waits
-// (bounded) for its copies still in flight, and the CTA returns.
+// Every wait is bounded by `wait` clock cycles; on a timeout the CTA sets
+// *err, the producer waits (bounded by STREAM_WAIT_LIMIT) for its copies still
+// in flight, and the CTA returns.  stall != 0 makes the producer issue no copy
+// at all, so that every consumer's first wait runs out (the failure-detection
+// test of the bounded waits: nothing is in flight when the CTA leaves).
 template <typename T, int Q>
 __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const int *__restrict__ pcs,
                                                              const long long *__restrict__ pdoff,
@@ -128,7 +133,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
                                                              const long long *__restrict__ pioff,
                                                              const T *__restrict__ pinv, const T *__restrict__ res,
                                                              T *__restrict__ y, DiagCoef<T> dc, int maxCs,
-                                                             int *__restrict__ err, int nst) {
+                                                             int *__restrict__ err, int nst, long long wait,
+                                                             int stall) {
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
 
   if (warp == nwc) {
     // ---------------- producer
-    if (lane != 0) return;
+    if (lane != 0 || stall) return;
     long long it = 0;
     bool ok = true;
     for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
         const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
         for (int j0 = 0; j0 < Cs; j0 += K) {
           const int st = (int)(it % nst);
-          if (it >= nst && !mbar_wait(&empty[st], (uint32_t)(((it / nst) - 1) & 1), STREAM_WAIT_LIMIT)) {
+          if (it >= nst && !mbar_wait(&empty[st], (uint32_t)(((it / nst) - 1) & 1), wait)) {
             ok = false;
             break;
           }
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
       for (int j0 = 0; j0 < Cs; j0 += K) {
         const int st = (int)(it % nst);
         bool ready = !*abort_flag;
-        if (ready && !mbar_wait(&full[st], (uint32_t)((it / nst) & 1), STREAM_WAIT_LIMIT)) {
+        if (ready && !mbar_wait(&full[st], (uint32_t)((it / nst) & 1), wait)) {
           atomicExch(err, 2);
           *abort_flag = 1;
           ready = false;
@@ -366,6 +372,15 @@ struct stfem_ctx {
   std::string err;
   cudaStream_t stream = 0;
   int device = 0;
+  // streaming multiprocessors of the device (grid sizes of the persistent
+  // kernels and of the dot products) and its SM clock (kHz)
+  int nsm = 152, clock_khz = 2070000, dot_blocks = 4 * 152;
+  // most CTAs of the persistent patch-apply kernels (0: as many as fit)
+  int launch_cap = 0;
+  // clock cycles a bounded wait of the streaming patch apply may take before
+  // it reports a timeout; stall_copies != 0 makes its producer issue no copy
+  long long wait_cycles = 4000000000LL;
+  int stall_copies = 0;
   int dim = 2, r = 2, k = 1, q = 2, nlev = 1;
   double tau = 0.01, t0 = 0.0;
   int problem = 0;
@@ -805,7 +820,9 @@ int node_block(const stfem::Level &L, int d, NodeBlockHost *out, std::string *er
       for (int e = L.rowptr[ru]; e < L.rowptr[ru + 1]; ++e) {
         const long col = L.col[e];
         if (col < R) {
-          const size_t at = (size_t)H.uu_ptr[I] + box_pos(bu, col / d, ud, d);
+          const long pos = box_pos(bu, col / d, ud, d);
+          if (pos < 0) return "u-equation V entry outside the box";
+          const size_t at = (size_t)H.uu_ptr[I] + pos;
           if (std::fabs(L.v2[e] + H.uu_m[at]) > tol) return "u-equation V block is not -rho M";
         }
       }
@@ -1497,7 +1514,8 @@ void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t sme
 // consumer warps per CTA) run best with 2 stages and up to 5 CTAs per SM,
 // 3D patches with 4 stages and up to 3.
 template <typename T>
-void stream_shape(const DLevel<T> &L, int q, int dim, int *threads, size_t *smem, int *grid, int *nst) {
+void stream_shape(stfem_h h, const DLevel<T> &L, int *threads, size_t *smem, int *grid, int *nst) {
+  const int q = h->q, dim = h->dim;
   constexpr int VEC = Vec16<T>::n;
   const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
   const int nwc = std::max(1, (rows + 31) / 32);
@@ -1510,16 +1528,18 @@ void stream_shape(const DLevel<T> &L, int q, int dim, int *threads, size_t *smem
   }
   *smem = (size_t)stream_header(*nst) + (size_t)(q + 2 * (L.dc.nr + 2 * L.dc.nc)) * L.maxCs * sizeof(T);
   const int per_sm = std::max(1, std::min(cap, (int)((227u * 1024u) / *smem)));
-  *grid = (int)std::min<long>(L.npatch, 152L * per_sm);
+  *grid = (int)std::min<long>(L.npatch, (long)h->nsm * per_sm);
+  if (h->launch_cap > 0) *grid = std::min(*grid, h->launch_cap);
 }
 
 template <typename T, int Q>
 void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   int threads, grid, nst;
   size_t smem;
-  stream_shape(L, Q, h->dim, &threads, &smem, &grid, &nst);
+  stream_shape(h, L, &threads, &smem, &grid, &nst);
   k_patch_apply_stream<T, Q><<<grid, threads, smem, h->stream>>>((int)L.npatch, L.pcs, L.pdoff, L.pdofs, L.pioff,
-                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err, nst);
+                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err, nst,
+                                                                 h->wait_cycles, h->stall_copies);
 }
 
 template <typename T>
@@ -1534,7 +1554,7 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   // time-diagonal one needs every row block resident (checked at setup)
   const int RT = L.form == 1 ? std::max((rows + 31) / 32 * 32, 32) : std::min(std::max((rows + 31) / 32 * 32, 32), 512);
   int J = 1;
-  const double target = 152.0 * STFEM_PATCH_THREADS_PER_SM;
+  const double target = (double)h->nsm * STFEM_PATCH_THREADS_PER_SM;
   while (J < 8 && (double)L.npatch * RT * J < target && RT * J * 2 <= 1024) J *= 2;
   size_t smem = (J > 1 ? (size_t)J * RT * VEC * sizeof(T) : 0);
   cudaStream_t s = h->stream;
@@ -1610,7 +1630,7 @@ int autotune_stream(stfem_h h, DLevel<T> &L) {
     L.tune_cap = c[1];
     int threads, grid, nst;
     size_t smem;
-    stream_shape(L, h->q, h->dim, &threads, &smem, &grid, &nst);
+    stream_shape(h, L, &threads, &smem, &grid, &nst);
     if (smem > 227u * 1024u) continue;
     for (int w = 0; w < 2; ++w) launch_patch_apply_to<T>(h, L, L.r, L.ybuf);
     cudaEventRecord(e0, ts);
@@ -1646,7 +1666,7 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
   const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
   int threads, grid, nst;
   size_t smem;
-  stream_shape(L, h->q, h->dim, &threads, &smem, &grid, &nst);
+  stream_shape(h, L, &threads, &smem, &grid, &nst);
   const size_t widest_column = (size_t)2 * ((L.maxCs + 1) / 2 * 2) * sizeof(T); // complex slot column
   if (rows > 992 || smem > 227u * 1024u || widest_column > (size_t)STREAM_CHUNK) {
     h->err = "patches too large for the time-diagonal form (" + std::to_string(rows) + " row threads, " +
@@ -1656,13 +1676,26 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
   return 0;
 }
 
+// y: nb columns of sumC patch results (column stride L.sumC)
 template <int Q>
-void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, int nb) {
+void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, float *y, int nb) {
   const size_t smem = tcp::smem_bytes(L.tc_nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
-  const int grid = (int)std::min<long>(L.npatch, 152L * STFEM_TC_CTAS_PER_SM);
+  int grid = (int)std::min<long>(L.npatch, (long)h->nsm * STFEM_TC_CTAS_PER_SM);
+  if (h->launch_cap > 0) grid = std::min(grid, h->launch_cap);
   k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)L.npatch, nb, L.pcs, L.pdoff, L.pdofs, L.ptoff,
-                                                             L.ptile, res, L.N, L.ybuf, L.sumC, L.dc, L.maxCs,
+                                                             L.ptile, res, L.N, y, L.sumC, L.dc, L.maxCs,
                                                              L.tc_nst, L.tc_cols, h->dev_err);
+}
+
+// the tensor-core apply of a level into y (nb columns)
+void launch_patch_tc(stfem_h h, DLevel<float> &L, const float *res, float *y, int nb) {
+  switch (h->q) {
+  case 1: launch_patch_tc_q<1>(h, L, res, y, nb); break;
+  case 2: launch_patch_tc_q<2>(h, L, res, y, nb); break;
+  case 3: launch_patch_tc_q<3>(h, L, res, y, nb); break;
+  case 4: launch_patch_tc_q<4>(h, L, res, y, nb); break;
+  default: launch_patch_tc_q<5>(h, L, res, y, nb); break;
+  }
 }
 
 // nb columns: res with column stride L.N, results with column stride
@@ -1675,13 +1708,7 @@ void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res, int nb = 1) {
             L.patch_flops * nb);
   if constexpr (std::is_same<T, float>::value) {
     if (L.tc) {
-      switch (h->q) {
-      case 1: launch_patch_tc_q<1>(h, L, res, nb); break;
-      case 2: launch_patch_tc_q<2>(h, L, res, nb); break;
-      case 3: launch_patch_tc_q<3>(h, L, res, nb); break;
-      case 4: launch_patch_tc_q<4>(h, L, res, nb); break;
-      default: launch_patch_tc_q<5>(h, L, res, nb); break;
-      }
+      launch_patch_tc(h, L, res, L.ybuf, nb);
       return;
     }
   }
@@ -1799,14 +1826,15 @@ int precondition(stfem_h h, const double *v, double *zd, float *zf) {
 
 // dots out[0..k) = V_v . w on device (deterministic two-stage reduction)
 void multidot(stfem_h h, int k, const double *V, long ldV, const double *w, long n, double *out) {
-  dim3 grid(DOT_BLOCKS, (k + DOT_NV - 1) / DOT_NV);
+  const int nbk = h->dot_blocks;
+  dim3 grid(nbk, (k + DOT_NV - 1) / DOT_NV);
   {
     Launch G_(h, STFEM_KCLASS_BLAS1, (double)(k + 1) * n * 8.0, 2.0 * k * n);
     k_multidot<<<grid, DOT_THREADS, 0, h->stream>>>(k, V, ldV, w, n, h->partial);
   }
   {
-    Launch G_(h, STFEM_KCLASS_OTHER, (double)k * DOT_BLOCKS * 8.0, (double)k * DOT_BLOCKS);
-    k_reduce_partials<<<k, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)k * nbk * 8.0, (double)k * nbk);
+    k_reduce_partials<<<k, 256, 0, h->stream>>>(nbk, h->partial, out);
   }
 }
 
@@ -1814,21 +1842,22 @@ void multidot(stfem_h h, int k, const double *V, long ldV, const double *w, long
 // out = w . w (mode 1): one pass over V and w, fixed-order reduction.
 void axpy_dot(stfem_h h, int k, const double *V, long ldV, const double *hvec, double *w, long n, double *out,
               int mode) {
+  const int nbk = h->dot_blocks;
   {
     Launch G_(h, STFEM_KCLASS_BLAS1, (double)(k + 2) * n * 8.0, 2.0 * k * n * (mode == 0 ? 2 : 1) + 2.0 * n);
     if (k <= 8)
-      k_axpy_dot<8><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+      k_axpy_dot<8><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
     else if (k <= 16)
-      k_axpy_dot<16><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+      k_axpy_dot<16><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
     else if (k <= 24)
-      k_axpy_dot<24><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+      k_axpy_dot<24><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
     else
-      k_axpy_dot<32><<<DOT_BLOCKS, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+      k_axpy_dot<32><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
   }
   {
     const int nout = mode == 0 ? k : 1;
-    Launch G_(h, STFEM_KCLASS_OTHER, (double)nout * DOT_BLOCKS * 8.0, (double)nout * DOT_BLOCKS);
-    k_reduce_partials<<<nout, 256, 0, h->stream>>>(DOT_BLOCKS, h->partial, out);
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)nout * nbk * 8.0, (double)nout * nbk);
+    k_reduce_partials<<<nout, 256, 0, h->stream>>>(nbk, h->partial, out);
   }
 }
 
@@ -1967,7 +1996,8 @@ int run_iteration(stfem_h h, int j, int m1) {
   return run_captured(h, h->graphs, j, [&]() { return enqueue_iteration(h, j, m1); });
 }
 
-int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it, int *iters, double *relres) {
+int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it, int *iters, double *relres,
+           double *absres) {
   CKR(ensure_workspace(h, m));
   DLevel<double> &F = h->L64.back();
   const long N = F.N;
@@ -1977,11 +2007,13 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
   h->hist.clear();
   *iters = 0;
   *relres = 0.0;
+  *absres = 0.0;
   launch_spmv<double>(h, F, tc, x, b, h->rvec, 1);
   multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
   double beta0sq;
   CKR(read_scalar(h, h->hn2, &beta0sq));
   const double beta0 = std::sqrt(beta0sq);
+  *absres = beta0;
   h->hist.push_back(1.0);
   if (!std::isfinite(beta0)) {
     h->err = "initial residual is not finite";
@@ -2044,6 +2076,7 @@ int fgmres(stfem_h h, const double *b, double *x, double tol, int m, int max_it,
     const double res = std::sqrt(rr);
     *iters = it;
     *relres = res / beta0;
+    *absres = res;
     if (!std::isfinite(res)) {
       h->err = "FGMRES breakdown: non-finite residual";
       return STFEM_ERR_BREAKDOWN;
@@ -2313,16 +2346,33 @@ int fgmres_batch(stfem_h h, int nb, const double *b, double *x, double tol, int 
   return worst;
 }
 
-// A bounded wait inside a kernel timed out (reported through h->dev_err).
+// A bounded wait inside a kernel timed out (reported through h->dev_err):
+// the flag is cleared again, so that the handle's next call starts clean.
 int check_dev_err(stfem_h h) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (e) {
-    h->err = "a bounded wait in the streaming patch apply timed out (code " + std::to_string(e) + ")";
-    return STFEM_ERR_CUDA;
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const char *who = e == 1 ? "streaming patch apply, producer" : e == 2 ? "streaming patch apply, consumer"
+                                                                         : "tensor-core patch apply";
+    h->err = std::string("a bounded wait timed out (") + who + ", code " + std::to_string(e) + ")";
+    return STFEM_ERR_TIMEOUT;
   }
   return 0;
+}
+
+// Drops the captured per-iteration graphs (their kernels hold launch
+// parameters that a setting of the handle has changed); they are captured
+// again on their next use.
+void drop_graphs(stfem_h h) {
+  for (auto &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.assign(h->graphs.size(), stfem_ctx::GraphRec());
+  for (auto &g : h->bt.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->bt.graphs.assign(h->bt.graphs.size(), stfem_ctx::GraphRec());
 }
 
 int check_level(stfem_h h, int level, bool allow_fine_alias) {
@@ -2366,13 +2416,25 @@ int apply_t(stfem_h h, int level, const double *x, double *y) {
   return 0;
 }
 
+// nb columns of b and d (column stride N of the level)
 template <typename T>
-int smooth_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init) {
+int smooth_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init, int nb = 1) {
   DLevel<T> &L = levels<T>(h)[level];
-  to_level<T>(h, b, L.b, L.N);
-  if (!zero_init) to_level<T>(h, d, L.d, L.N);
-  smooth<T>(h, level, nsw, zero_init != 0);
-  from_level<T>(h, L.d, d, L.N);
+  if (nb == 1) {
+    to_level<T>(h, b, L.b, L.N);
+    if (!zero_init) to_level<T>(h, d, L.d, L.N);
+  } else {
+    Launch G_(h, STFEM_KCLASS_OTHER, L.N * (8.0 + sizeof(T)) * nb * (zero_init ? 1 : 2), 0.0);
+    k_copy_cols<double, T><<<grid_for(L.N, 256) * nb, 256, 0, h->stream>>>(L.N, nb, b, L.N, L.b, L.N);
+    if (!zero_init) k_copy_cols<double, T><<<grid_for(L.N, 256) * nb, 256, 0, h->stream>>>(L.N, nb, d, L.N, L.d, L.N);
+  }
+  smooth<T>(h, level, nsw, zero_init != 0, nb);
+  if (nb == 1) {
+    from_level<T>(h, L.d, d, L.N);
+  } else {
+    Launch G_(h, STFEM_KCLASS_OTHER, L.N * (8.0 + sizeof(T)) * nb, 0.0);
+    k_copy_cols<T, double><<<grid_for(L.N, 256) * nb, 256, 0, h->stream>>>(L.N, nb, L.d, L.N, d, L.N);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   CKR(check_dev_err(h));
@@ -2588,7 +2650,14 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
       launch_spmv<T>(h, L, tc, dT, bT, rT, 1);
       res = rT;
     }
-    launch_patch_apply_to<T>(h, L, res, yT);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.tc) { // the tensor-core apply that stfem_smooth uses on this level
+        launch_patch_tc(h, L, res, yT, 1);
+        done = true;
+      }
+    }
+    if (!done) launch_patch_apply_to<T>(h, L, res, yT);
     k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0, 1,
                                                          L.sumC);
   }
@@ -2611,12 +2680,18 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
     return STFEM_ERR_ARG;
   }
   *out = nullptr;
-  if (deg && deg->pressure != STFEM_PRESSURE_CONTINUOUS) {
-    g_setup_err = "the broken pressure pair has a host setup only (no device path)";
+  if (deg && mesh && deg->pressure != STFEM_PRESSURE_CONTINUOUS && mesh->dim != 2) {
+    g_setup_err = "the broken pressure pair has a device path in 2D only";
     return STFEM_ERR_ARG;
   }
   stfem_h h = new stfem_ctx();
   cudaGetDevice(&h->device);
+  if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->nsm < 1 ||
+      cudaDeviceGetAttribute(&h->clock_khz, cudaDevAttrClockRate, h->device) != cudaSuccess || h->clock_khz < 1) {
+    h->err = "cannot query the device's multiprocessor count and clock";
+    return fail_setup(h, STFEM_ERR_CUDA);
+  }
+  h->dot_blocks = 4 * h->nsm;
   {
     int rc0 = stfem::build_hierarchy(mesh, deg, mat, bcs, tau, &h->hl, &h->Pu, &h->Pp, &h->err);
     if (rc0 < 0) return fail_setup(h, rc0);
@@ -2669,7 +2744,7 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
       (rc = dalloc(h, &h->src, (size_t)h->q * F.box.ncell * h->lt.nq * 4)) < 0 ||
       (rc = dalloc(h, &h->hnorm, 1)) < 0 || (rc = dalloc(h, &h->status, 4)) < 0 ||
       (rc = dalloc(h, &h->dev_err, 1)) < 0 ||
-      (rc = dalloc(h, &h->partial, (size_t)DOT_BLOCKS * (MAXM + 1))) < 0 ||
+      (rc = dalloc(h, &h->partial, (size_t)h->dot_blocks * (MAXM + 1))) < 0 ||
       (rc = upload(h, &h->chi, h->T.chi_m1)) < 0 || (rc = upload(h, &h->tnode, h->T.t)) < 0)
     return fail_setup(h, rc);
   if (cudaHostAlloc((void **)&h->status_host, 4 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
@@ -2793,6 +2868,31 @@ int stfem_set_stop(stfem_h h, int mode) {
   return STFEM_OK;
 }
 
+int stfem_set_launch_cap(stfem_h h, int max_ctas) {
+  if (!h || max_ctas < 0) return STFEM_ERR_ARG;
+  if (max_ctas != h->launch_cap) drop_graphs(h);
+  h->launch_cap = max_ctas;
+  return STFEM_OK;
+}
+
+int stfem_set_wait_limit(stfem_h h, double seconds) {
+  if (!h || !(seconds > 0.0) || seconds > 60.0) {
+    if (h) h->err = "wait limit must lie in (0, 60] seconds";
+    return STFEM_ERR_ARG;
+  }
+  const long long cyc = std::max(1LL, (long long)(seconds * 1e3 * (double)h->clock_khz));
+  if (cyc != h->wait_cycles) drop_graphs(h);
+  h->wait_cycles = cyc;
+  return STFEM_OK;
+}
+
+int stfem_stall_copies(stfem_h h, int on) {
+  if (!h) return STFEM_ERR_ARG;
+  if ((on != 0) != (h->stall_copies != 0)) drop_graphs(h);
+  h->stall_copies = on != 0;
+  return STFEM_OK;
+}
+
 int stfem_set_stream(stfem_h h, void *stream) {
   if (!h) return STFEM_ERR_ARG;
   h->stream = (cudaStream_t)stream;
@@ -2837,6 +2937,22 @@ int stfem_smooth(stfem_h h, int level, const double *b, double *d, int n_sweeps,
   }
   if (h->precision == STFEM_MIXED) return smooth_t<float>(h, level, b, d, n_sweeps, zero_init);
   return smooth_t<double>(h, level, b, d, n_sweeps, zero_init);
+}
+
+int stfem_smooth_batch(stfem_h h, int level, int n_rhs, const double *b, double *d, int n_sweeps, int zero_init) {
+  if (!h || !b || !d || n_sweeps < 1) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  CKR(check_level(h, level, false));
+  if (level < 1) {
+    h->err = "smoothing is defined on levels >= 1";
+    return STFEM_ERR_ARG;
+  }
+  if (n_rhs < 1 || n_rhs > h->nrhs_cap) {
+    h->err = "n_rhs must be between 1 and the n_rhs given to stfem_gmg_setup";
+    return STFEM_ERR_ARG;
+  }
+  if (h->precision == STFEM_MIXED) return smooth_t<float>(h, level, b, d, n_sweeps, zero_init, n_rhs);
+  return smooth_t<double>(h, level, b, d, n_sweeps, zero_init, n_rhs);
 }
 
 int stfem_smooth_noalloc(stfem_h h, int level, const double *b, double *d, int n_sweeps, int zero_init) {
@@ -2890,14 +3006,15 @@ int stfem_vcycle(stfem_h h, const double *b, double *d) {
 }
 
 int slab_solve(stfem_h h, const double *rhs, double *x, double tol, int restart, int max_it, int *iters,
-               double *rel_res) {
+               double *rel_res, double *abs_res) {
   if (!h || !rhs || !x || restart < 1 || max_it < 0 || !(tol >= 0.0)) return STFEM_ERR_ARG;
   CKR(require_gmg(h));
   int it = 0;
-  double rr = 0.0;
-  int rc = fgmres(h, rhs, x, tol, restart, max_it, &it, &rr);
+  double rr = 0.0, ra = 0.0;
+  int rc = fgmres(h, rhs, x, tol, restart, max_it, &it, &rr, &ra);
   if (iters) *iters = it;
   if (rel_res) *rel_res = rr;
+  if (abs_res) *abs_res = ra;
   CKR(check_dev_err(h));
   return rc;
 }
@@ -3052,8 +3169,8 @@ int march(stfem_h h, int first_slab, int n_slabs, double *state, double tol, int
       k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, state, h->xs);
     }
     int it = 0;
-    double rr = 0.0;
-    int rc = fgmres(h, h->rhs, h->xs, tol, restart, max_it, &it, &rr);
+    double rr = 0.0, ra = 0.0;
+    int rc = fgmres(h, h->rhs, h->xs, tol, restart, max_it, &it, &rr, &ra);
     if (iters_host) iters_host[n] = it;
     if (rc < 0) return rc;
     if (rc > worst) worst = rc;

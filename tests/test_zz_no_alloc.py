@@ -1,14 +1,18 @@
 """stfem_smooth_noalloc against stfem_smooth (needs a GPU).
 
-The allocation-free entry point exists for callers that must not allocate
-device memory while they run: code issued during CUDA stream capture (where
-cudaMalloc is not allowed), host programs that fix their device-memory budget
-after start-up, and latency-critical loops.  It takes its scratch from a
-static device array inside the library, which keeps the previous call's
-contents, so two calls in a row are checked.  Its result must equal
-stfem_smooth's within the smoother parity tolerance (1e-11 in FP64; the FP32
-level of the mixed mode is held to 1e-6), and levels whose scratch does not
-fit the static array must be rejected with an error.
+The allocation-free entry point serves callers that cannot call cudaMalloc
+while they run: a host application that reserved its device memory at
+start-up and hands out the rest from its own pool, a plug-in that may only
+touch the buffers its host passes in, or a latency-critical loop where an
+allocation could synchronise the device.  It takes its scratch from a static
+device array inside the library, which keeps the previous call's contents,
+so two calls in a row are checked.  Its result must equal stfem_smooth's
+within the smoother parity tolerance (1e-11 in FP64; the FP32 level of the
+mixed mode is held to 1e-6, and a handle set up for eight right-hand sides,
+whose FP32 levels apply the patches on tensor cores, to the same bound), and
+levels whose scratch does not fit the static array must be rejected with an
+error.  This file is collected last, so that a failure here stops a run only
+after every other test has run.
 """
 import numpy as np
 import pytest
@@ -23,11 +27,11 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-6)])
-def test_noalloc_smooth_matches_smooth_twice(precision, tol):
+@pytest.mark.parametrize("precision,tol,n_rhs", [(0, 1e-11, 0), (1, 1e-6, 0), (1, 1e-6, 8)])
+def test_noalloc_smooth_matches_smooth_twice(precision, tol, n_rhs):
     import paper_2303_06742_gb300 as st
     c = case("c2_small_2d_q3_k2_8")
-    S = st.Solver(gpu_problem(c), precision=precision)
+    S = st.Solver(gpu_problem(c), precision=precision, n_rhs=n_rhs)
     rng = np.random.default_rng(11)
     for level in range(1, c["levels"]):
         n = S.level_info(level)["n_slab"]
