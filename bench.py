@@ -83,29 +83,54 @@ def oracle_leg(workload, out_path, mode, steps=0, warmup=0, form="3.1"):
     b = O.rhs(0, st0)
     x0 = repeat_state(O.ops, O.tmp, st0)
     t0 = time.perf_counter()
+    c0 = time.process_time()
     x, it, rel, _ = O.solve(b, x0, c["tol"])
     t_solve = time.perf_counter() - t0
-    res = dict(setup_s=t_setup, solve_s=t_solve, iters=it, rel=rel)
+    cpu_s = time.process_time() - c0
+    res = dict(setup_s=t_setup, solve_s=t_solve, iters=it, rel=rel, cpu_s=cpu_s,
+               threads_used=cpu_s / max(t_solve, 1e-9))
     if mode == "solve":
         np.save(out_path + ".npy", x)
     else:
-        samples = []
+        samples, steps_s = [], []
         for i in range(warmup + steps):
             t0 = time.perf_counter()
             O.solve(b, x0, 0.0, restart=30, max_it=2)
             if i >= warmup:
-                samples.append((time.perf_counter() - t0) / 2.0)
+                steps_s.append(time.perf_counter() - t0)
+                samples.append(steps_s[-1] / 2.0)
         res["per_iter_s"] = samples
+        res["step_s"] = steps_s
     with open(out_path, "w") as f:
         json.dump(res, f)
 
 
-def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1"):
+def host_cpu():
+    """(logical cores, CPU model) of the host the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1", threads=1):
+    """The oracle in a subprocess with `threads` BLAS/OpenMP threads (the
+    oracle's library calls are the only parallel part of it)."""
     fd, path = tempfile.mkstemp(suffix=".json")
     os.close(fd)
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[v] = "1"
+        env[v] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", path, "--workload", workload,
            "--steps", str(steps), "--warmup", str(warmup), "--impl", "reference" if mode == "reference" else "ours",
@@ -403,12 +428,23 @@ def gpu_arm(args):
     cpu = None
     err_vs_oracle = None
     if not args.no_cpu_baseline:
+        nproc, model = host_cpu()
         res, sol = run_oracle_subprocess(args.workload, "solve", form=args.form)
         cpu = {"value": 1.0 / res["solve_s"], "unit": "slab solves/s", "cores": 1, "kind": "oracle",
+               "nproc": nproc, "cpu_model": model,
                "sample": "one full slab solve (slab 0, FGMRES-GMG to %g, %d iterations) of the same workload; "
-                         "oracle setup (%.1f s) excluded as on the GPU" % (tol, res["iters"], res["setup_s"])}
+                         "oracle setup (%.1f s) excluded as on the GPU; BLAS/OpenMP threads pinned to 1"
+                         % (tol, res["iters"], res["setup_s"])}
         if sol is not None:
             err_vs_oracle = float(np.abs(x_slab0_host - sol).max() / np.abs(sol).max())
+        # the same oracle with its library calls free to use every host core
+        resa, _ = run_oracle_subprocess(args.workload, "solve", form=args.form, threads=nproc)
+        cpu["all_cores"] = {
+            "value": 1.0 / resa["solve_s"], "unit": "slab solves/s", "cores": round(resa["threads_used"], 2),
+            "threads_allowed": nproc, "nproc": nproc, "cpu_model": model, "kind": "oracle",
+            "sample": "the same slab solve with BLAS/OpenMP threads = nproc; cores = process CPU time / wall "
+                      "time of the solve (the oracle's sparse products and patch loops are single-threaded, "
+                      "only its dense library calls use more cores)"}
 
     out = {
         "metric": "slab solves/s",
@@ -425,13 +461,10 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload),
-                   "precision": "FP32 V-cycle inside FP64 FGMRES",
-                   "form": "Problem %s" % args.form,
-                   "tol": tol, "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
-                   "l2": "inputs larger than L2: %.2f GB of FP32 patch inverses streamed per sweep set"
-                         % (sum(v["inv_bytes"] for v in info.values()) / 1e9),
-                   "levels": info, "parallelism": "replicas" if world > 1 else "single"},
+        "config": bench_config(args, world),
+        "precision": "FP32 V-cycle inside FP64 FGMRES",
+        "levels": info,
+        "inverse_bytes_per_sweep_set": sum(v["inv_bytes"] for v in info.values()),
         "iters_per_slab": iters,
         "first_slab": {"iters": it0, "rel_res": rel0, "err_vs_fp64_oracle": err_vs_oracle},
         "setup_s": setup_s,
@@ -449,6 +482,16 @@ def gpu_arm(args):
     print(json.dumps(out))
 
 
+def bench_config(args, world):
+    """The `config` of the JSON line: the workload, identical for both arms."""
+    import inputs
+    c = inputs.case(args.workload)
+    return {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "form": "Problem %s" % args.form,
+            "tol": c["tol"], "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
+            "l2": "inputs larger than L2: the patch inverses streamed per sweep set exceed the 129 MB L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -463,6 +506,7 @@ def reference_arm(args):
     t_slab = statistics.mean(per_iter) * iters
     value = 1.0 / t_slab
     samples_ms = [p * iters * 1000.0 for p in per_iter]
+    nproc, model = host_cpu()
     out = {
         "impl": "reference",
         "metric": "slab solves/s",
@@ -471,7 +515,10 @@ def reference_arm(args):
         "n_gpus": 0,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": t_slab * 1000.0,
+        # the timed steps themselves: each is a bounded sample (two FGMRES-GMG
+        # iterations); `value` scales the mean iteration time to a slab solve
+        "ms_per_step": statistics.mean(res["step_s"]) * 1000.0,
+        "ms_per_slab_solve": t_slab * 1000.0,
         "p50_ms": pct(samples_ms, 50),
         "p99_ms": pct(samples_ms, 99),
         "higher_is_better": True,
@@ -479,12 +526,13 @@ def reference_arm(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "precision": "FP64 (oracle)",
-                   "form": "Problem %s" % args.form,
-                   "tol": c["tol"]},
+        "config": bench_config(args, 1),
+        "precision": "FP64 (oracle)",
         "cpu_baseline": {"value": value, "unit": "slab solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: 2 FGMRES-GMG iterations of slab 0, scaled by the %d iterations "
-                                   "of a full slab solve; oracle setup (%.1f s) excluded" % (iters, res["setup_s"])},
+                         "nproc": nproc, "cpu_model": model,
+                         "sample": "each step: 2 FGMRES-GMG iterations of slab 0 (ms_per_step); value = 1 / "
+                                   "(mean iteration time x the %d iterations of a full slab solve, whose time is "
+                                   "ms_per_slab_solve); oracle setup (%.1f s) excluded" % (iters, res["setup_s"])},
         "e2e": {"value": value, "unit": "slab solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
