@@ -99,8 +99,7 @@ typedef struct {
  * CONTINUOUS: Q_{r-1}, the Taylor-Hood pair Q_r^d / Q_{r-1} (default).
  * BROKEN: P_{r-1}^disc, polynomials of total degree r-1 on each cell, with the
  *   interior penalty form B_gamma over interior faces and Dirichlet faces of p
- *   (gamma = r (r-1) / 2).  Device path in 2D; stfem_setup and
- *   stfem_server_submit return STFEM_ERR_ARG for it in 3D. */
+ *   (gamma = r (r-1) / 2). */
 #define STFEM_PRESSURE_CONTINUOUS 0
 #define STFEM_PRESSURE_BROKEN 1
 
@@ -225,6 +224,21 @@ int stfem_set_stream(stfem_h h, void *stream);
  * is the same in every CTA.  STFEM_ERR_ARG for max_ctas < 0. */
 int stfem_set_launch_cap(stfem_h h, int max_ctas);
 
+/* Patch-apply kernel of the time-diagonal levels (Algorithm 4.1's local
+ * solves).  STREAM: a persistent grid whose CTAs each stream their patches'
+ * inverses through a shared-memory ring (bulk copies); WIDE: one CTA per
+ * (patch, slot) that requests the slot's whole inverse in one wave of loads
+ * (lower latency where a level has few patches); AUTO (default): WIDE for
+ * levels with at most 4 patches per multiprocessor, STREAM for the others.
+ * The two kernels sum in different orders, so their results differ by
+ * rounding; for a given choice and device every result is deterministic.
+ * Tensor-core levels (several right-hand sides) are not affected.  Needs
+ * stfem_gmg_setup first; may allocate the wide kernel's buffers. */
+#define STFEM_PATCH_KERNEL_AUTO 0
+#define STFEM_PATCH_KERNEL_STREAM 1
+#define STFEM_PATCH_KERNEL_WIDE 2
+int stfem_set_patch_kernel(stfem_h h, int choice);
+
 /* Longest a bounded wait of the streaming patch apply may take before the
  * kernel gives up: its CTAs then leave at the next patch boundary (after the
  * copies in flight have landed), and the call that launched it returns
@@ -269,7 +283,8 @@ int stfem_coarse_solve(stfem_h h, const double *b, double *x);
  * preconditioner of each FGMRES iteration, Sec. 4). */
 int stfem_vcycle(stfem_h h, const double *b, double *d);
 
-/* Flexible GMRES(restart) for A_n x = rhs (Sec. 4) on the finest level,
+/* Flexible GMRES(restart) for A_n x = rhs (Sec. 4) on the finest level
+ * (1 <= restart <= 32; STFEM_ERR_ARG above),
  * right-preconditioned by one V-cycle per iteration, classical Gram-Schmidt
  * applied twice.  x: in = initial guess x0, out = solution.  Stops when the
  * least-squares residual satisfies |g_{j+1}| <= tol ||rhs - A x0|| and the

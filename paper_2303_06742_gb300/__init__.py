@@ -29,6 +29,7 @@ FORM_PROBLEM_3_1, FORM_PROBLEM_B_1 = 0, 1
 PRESSURE_CONTINUOUS, PRESSURE_BROKEN = 0, 1
 PATCH_AUTO, PATCH_DENSE, PATCH_TIME_DIAGONAL = 0, 1, 2
 PATCHES_VERTEX, PATCHES_CELL = 0, 1
+PATCH_KERNEL_AUTO, PATCH_KERNEL_STREAM, PATCH_KERNEL_WIDE = 0, 1, 2
 UPDATE_AVERAGE, UPDATE_OVERWRITE = 0, 1
 STOP_RELATIVE, STOP_ABSOLUTE = 0, 1
 KCLASSES = ["spmv", "patch_apply", "update", "transfer", "coarse", "blas1", "rhs", "other"]
@@ -102,6 +103,7 @@ def _load():
         "stfem_vcycle": [P, P, P],
         "slab_solve": [P, P, P, D, I, I, pI, pD, pD],
         "stfem_set_launch_cap": [P, I],
+        "stfem_set_patch_kernel": [P, I],
         "stfem_set_wait_limit": [P, D],
         "stfem_stall_copies": [P, I],
         "stfem_solve_history": [P, pD, I, pI],
@@ -356,6 +358,10 @@ class Solver:
     def set_launch_cap(self, max_ctas):
         """At most max_ctas CTAs per persistent patch-apply launch (0: as many as fit)."""
         self._check(lib.stfem_set_launch_cap(self.h, int(max_ctas)))
+
+    def set_patch_kernel(self, choice):
+        """PATCH_KERNEL_AUTO (default), PATCH_KERNEL_STREAM or PATCH_KERNEL_WIDE."""
+        self._check(lib.stfem_set_patch_kernel(self.h, int(choice)))
 
     def set_wait_limit(self, seconds):
         """Longest bounded wait of the streaming patch apply before it reports ERR_TIMEOUT."""

@@ -6,7 +6,7 @@
 namespace stfem_dev {
 
 constexpr int MAXQ = 5;    // at most k = 4 (five Radau nodes)
-constexpr int MAXM = 64;   // FGMRES restart length bound
+constexpr int MAXM = 32;   // FGMRES restart length bound (the Gram-Schmidt kernels block k <= 32 vectors)
 
 template <typename T>
 struct TimeCoef {

@@ -171,9 +171,6 @@ int stfem_server_create(long long hbm_budget, int n_workers, stfem_server *out) 
 
 int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id) {
   if (!s || !req || !id || req->n_slabs < 0) return STFEM_ERR_ARG;
-  // the broken pressure pair has a device path in 2D only: refuse it here
-  // rather than fail in a worker
-  if (req->deg.pressure != STFEM_PRESSURE_CONTINUOUS && req->mesh.dim != 2) return STFEM_ERR_ARG;
   auto R = std::make_shared<Request>();
   R->req = *req;
   long ncell = 1;

@@ -349,6 +349,11 @@ struct DLevel {
   // ring shape of the streaming patch apply picked by autotune_stream (0: by
   // dimension)
   int tune_nst = 0, tune_cap = 0;
+  // levels with few patches use k_patch_apply_wide: its slot results (sumC
+  // per column) and per-patch ticket counters
+  int wide = 0;
+  T *zbuf = nullptr;
+  int *ticket = nullptr;
   uint32_t tc_cols = 0;
   long long *ptoff = nullptr;
   float *ptile = nullptr;
@@ -381,6 +386,8 @@ struct stfem_ctx {
   // it reports a timeout; stall_copies != 0 makes its producer issue no copy
   long long wait_cycles = 4000000000LL;
   int stall_copies = 0;
+  // patch-apply kernel of the time-diagonal levels (STFEM_PATCH_KERNEL_*)
+  int patch_kernel = 0;
   int dim = 2, r = 2, k = 1, q = 2, nlev = 1;
   double tau = 0.01, t0 = 0.0;
   int problem = 0;
@@ -545,26 +552,44 @@ struct SpmvLanes {
   static constexpr int G = sizeof(T) == 8 ? 2 : (D == 3 ? 8 : 4);
 };
 
-template <typename T, int Q, int D>
-void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
-                    int mode, int nb) {
-  constexpr int G = SpmvLanes<T, D>::G;
+// A level whose nodes fill at most about two waves of the GPU with a warp
+// per node (the coarse levels of the V-cycle) takes 32 lanes per node: each
+// lane then walks one or two neighbours instead of a dependent chain of ten
+// or more.  A fixed rule on the level's size, so a level's arithmetic never
+// depends on the run.
+template <typename T>
+bool spmv_wide_lanes(const DLevel<T> &L, int nsm) {
+  return (L.nb.nu + L.nb.np) * 32 <= (long)nsm * 1024;
+}
+
+template <typename T, int Q, int D, int G>
+void launch_spmv_qdg(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+                     int mode, int nb) {
   const long threads = (L.nb.nu + L.nb.np) * G;
-  if (D == 2 && L.nb.pdisc) // broken pressure space (2D)
-    k_spmv_nb<T, Q, D, G, D == 2><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode,
-                                                                              nb, L.N);
+  if (L.nb.pdisc) // broken pressure space
+    k_spmv_nb<T, Q, D, G, true><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode,
+                                                                            nb, L.N);
   else
     k_spmv_nb<T, Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode, nb,
                                                                       L.N);
 }
 
+template <typename T, int Q, int D>
+void launch_spmv_qd(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
+                    int mode, int nb, int nsm) {
+  if (spmv_wide_lanes(L, nsm))
+    launch_spmv_qdg<T, Q, D, 32>(s, L, tc, x, rhs, y, mode, nb);
+  else
+    launch_spmv_qdg<T, Q, D, SpmvLanes<T, D>::G>(s, L, tc, x, rhs, y, mode, nb);
+}
+
 template <typename T, int Q>
 void launch_spmv_q(cudaStream_t s, int d, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs,
-                   T *y, int mode, int nb) {
+                   T *y, int mode, int nb, int nsm) {
   if (d == 2)
-    launch_spmv_qd<T, Q, 2>(s, L, tc, x, rhs, y, mode, nb);
+    launch_spmv_qd<T, Q, 2>(s, L, tc, x, rhs, y, mode, nb, nsm);
   else
-    launch_spmv_qd<T, Q, 3>(s, L, tc, x, rhs, y, mode, nb);
+    launch_spmv_qd<T, Q, 3>(s, L, tc, x, rhs, y, mode, nb, nsm);
 }
 
 // algorithmic bytes of one Kronecker SpMV: the node-block operator once, x and y
@@ -582,12 +607,13 @@ void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *
             L.nb_flops * tc.q * nb);
   cudaStream_t s = h->stream;
   const int d = h->dim;
+  const int nsm = h->nsm;
   switch (tc.q) {
-  case 1: launch_spmv_q<T, 1>(s, d, L, tc, x, rhs, y, mode, nb); break;
-  case 2: launch_spmv_q<T, 2>(s, d, L, tc, x, rhs, y, mode, nb); break;
-  case 3: launch_spmv_q<T, 3>(s, d, L, tc, x, rhs, y, mode, nb); break;
-  case 4: launch_spmv_q<T, 4>(s, d, L, tc, x, rhs, y, mode, nb); break;
-  default: launch_spmv_q<T, 5>(s, d, L, tc, x, rhs, y, mode, nb); break;
+  case 1: launch_spmv_q<T, 1>(s, d, L, tc, x, rhs, y, mode, nb, nsm); break;
+  case 2: launch_spmv_q<T, 2>(s, d, L, tc, x, rhs, y, mode, nb, nsm); break;
+  case 3: launch_spmv_q<T, 3>(s, d, L, tc, x, rhs, y, mode, nb, nsm); break;
+  case 4: launch_spmv_q<T, 4>(s, d, L, tc, x, rhs, y, mode, nb, nsm); break;
+  default: launch_spmv_q<T, 5>(s, d, L, tc, x, rhs, y, mode, nb, nsm); break;
   }
 }
 
@@ -607,8 +633,8 @@ void launch_spmv_df_qd(cudaStream_t s, const DLevel<double> &L, const TimeCoef<d
     td.W[b] = pair(tc.W[b]);
     td.mW[b] = pair(-tc.W[b]);
   }
-  if (D == 2 && L.nbdf.pdisc) // broken pressure space (2D)
-    k_spmv_df<Q, D, G, D == 2><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
+  if (L.nbdf.pdisc) // broken pressure space
+    k_spmv_df<Q, D, G, true><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
   else
     k_spmv_df<Q, D, G><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nbdf, L.ns, L.R, td, x, y, nb, L.N);
 }
@@ -1506,6 +1532,37 @@ void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t sme
   }
 }
 
+// Threads per CTA of k_patch_apply_wide; a level takes that kernel when it has
+// at most STFEM_WIDE_MAX_PATCHES_PER_SM patches per multiprocessor (a fixed
+// rule, not a timing, so that the arithmetic of a level never depends on the
+// run) and each slot's row groups fit one CTA.
+constexpr int WIDE_THREADS = 512;
+#ifndef STFEM_WIDE_MAX_PATCHES_PER_SM
+#define STFEM_WIDE_MAX_PATCHES_PER_SM 4
+#endif
+
+template <typename T>
+size_t wide_smem(const DLevel<T> &L, int q) {
+  return ((size_t)(q + 2) * L.maxCs + (size_t)WIDE_THREADS * Vec16<T>::n) * sizeof(T);
+}
+
+// the level's patches fit k_patch_apply_wide (time-diagonal form, FP32 or
+// FP64 CUDA cores, every slot's row groups in one CTA)
+template <typename T>
+bool wide_possible(const DLevel<T> &L) {
+  constexpr int CR = Vec16<T>::n / 2;
+  return L.form == 1 && !L.tc && L.npatch > 0 && (L.maxCs + CR - 1) / CR <= WIDE_THREADS &&
+         wide_smem(L, MAXQ) <= 227u * 1024u;
+}
+
+// kernel choice of a level: STFEM_PATCH_KERNEL_AUTO takes the wide kernel for
+// levels with few patches, the streaming kernel for the others
+template <typename T>
+bool wide_chosen(const DLevel<T> &L, int nsm, int choice) {
+  if (!wide_possible(L) || choice == STFEM_PATCH_KERNEL_STREAM) return false;
+  return choice == STFEM_PATCH_KERNEL_WIDE || L.npatch <= (long)STFEM_WIDE_MAX_PATCHES_PER_SM * nsm;
+}
+
 // Shape of the streaming time-diagonal patch apply: one consumer thread per
 // row block of the largest patch (rounded to warps) plus a producer warp;
 // shared memory = stages + the per-patch vectors; as many CTAs per SM as
@@ -1542,9 +1599,31 @@ void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
                                                                  h->wait_cycles, h->stall_copies);
 }
 
+template <typename T, int Q>
+void launch_patch_wide_q(stfem_h h, DLevel<T> &L, const T *res, T *y, T *zb, int *tk) {
+  const size_t smem = wide_smem<T>(L, Q);
+  const int ns = L.dc.nr + L.dc.nc;
+  k_patch_apply_wide<T, Q><<<(unsigned)(L.npatch * ns), WIDE_THREADS, smem, h->stream>>>(
+      L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, zb, tk, L.dc);
+}
+
+// zb, tk: slot results and ticket counters of the wide kernel (nullptr: the
+// level's own)
 template <typename T>
-void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y) {
+void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y, T *zb = nullptr, int *tk = nullptr) {
   constexpr int VEC = Vec16<T>::n;
+  if (L.form == 1 && L.wide) {
+    if (!zb) zb = L.zbuf;
+    if (!tk) tk = L.ticket;
+    switch (h->q) {
+    case 1: launch_patch_wide_q<T, 1>(h, L, res, y, zb, tk); break;
+    case 2: launch_patch_wide_q<T, 2>(h, L, res, y, zb, tk); break;
+    case 3: launch_patch_wide_q<T, 3>(h, L, res, y, zb, tk); break;
+    case 4: launch_patch_wide_q<T, 4>(h, L, res, y, zb, tk); break;
+    default: launch_patch_wide_q<T, 5>(h, L, res, y, zb, tk); break;
+    }
+    return;
+  }
   int rows;
   if (L.form == 1)
     rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
@@ -1599,6 +1678,13 @@ int prepare_stream_kernels(stfem_h h) {
   STFEM_SMEM_ATTR(double, 1); STFEM_SMEM_ATTR(double, 2); STFEM_SMEM_ATTR(double, 3);
   STFEM_SMEM_ATTR(double, 4); STFEM_SMEM_ATTR(double, 5);
 #undef STFEM_SMEM_ATTR
+#define STFEM_SMEM_ATTR_W(T, Q)                                                                          \
+  CK(cudaFuncSetAttribute(k_patch_apply_wide<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
+  STFEM_SMEM_ATTR_W(float, 1); STFEM_SMEM_ATTR_W(float, 2); STFEM_SMEM_ATTR_W(float, 3);
+  STFEM_SMEM_ATTR_W(float, 4); STFEM_SMEM_ATTR_W(float, 5);
+  STFEM_SMEM_ATTR_W(double, 1); STFEM_SMEM_ATTR_W(double, 2); STFEM_SMEM_ATTR_W(double, 3);
+  STFEM_SMEM_ATTR_W(double, 4); STFEM_SMEM_ATTR_W(double, 5);
+#undef STFEM_SMEM_ATTR_W
   CK(cudaFuncSetAttribute(k_patch_apply_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -1612,8 +1698,18 @@ int prepare_stream_kernels(stfem_h h) {
 // fastest.  The shape changes only how patches are spread over CTAs, never
 // the arithmetic of a patch, so results do not depend on the choice.
 template <typename T>
+int prepare_wide(stfem_h h, DLevel<T> &L) {
+  L.wide = wide_chosen(L, h->nsm, h->patch_kernel) ? 1 : 0;
+  if (!L.wide || L.zbuf) return 0;
+  CKR(dalloc(h, &L.zbuf, (size_t)L.sumC));
+  CKR(dalloc(h, &L.ticket, (size_t)L.npatch));
+  CK(cudaMemset(L.ticket, 0, (size_t)L.npatch * sizeof(int)));
+  return 0;
+}
+
+template <typename T>
 int autotune_stream(stfem_h h, DLevel<T> &L) {
-  if (L.form != 1 || L.tc || L.npatch == 0) return 0;
+  if (L.form != 1 || L.tc || L.wide || L.npatch == 0) return 0;
   static const int cand[][2] = {{2, 5}, {3, 4}, {4, 3}};
   cudaStream_t ts = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1748,12 +1844,23 @@ void restrict_to(stfem_h h, int l, const T *rf, T *bc, int nb = 1) {
   // restriction: rows of P^T are long, STFEM_RESTRICT_LANES lanes per output
   const long nu = C.R / h->dim, np = C.S, nt = (2 * nu + np) * h->q;
   constexpr int GR = STFEM_RESTRICT_LANES;
-  if (h->dim == 2)
-    k_transfer<T, 2, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
-        nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
-  else
-    k_transfer<T, 3, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
-        nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
+  // small coarse levels: a warp per output (fewer dependent trips per lane)
+  const bool wide = nt * 32 <= (long)h->nsm * 1024;
+  if (h->dim == 2) {
+    if (wide)
+      k_transfer<T, 2, 32><<<grid_for(nt * 32, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
+    else
+      k_transfer<T, 2, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
+  } else {
+    if (wide)
+      k_transfer<T, 3, 32><<<grid_for(nt * 32, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
+    else
+      k_transfer<T, 3, GR><<<grid_for(nt * GR, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, C.ns, C.R, F.ns, F.R, F.Ru_p, F.Ru_c, F.Ru_v, F.Rp_p, F.Rp_c, F.Rp_v, rf, bc, 0, nb, F.N, C.N);
+  }
 }
 
 template <typename T>
@@ -1764,12 +1871,23 @@ void prolongate_add(stfem_h h, int l, const T *dc, T *df, int nb = 1) {
             2.0 * F.transfer_nnz * nb);
   const long nu = F.R / h->dim, np = F.S, nt = (2 * nu + np) * h->q;
   constexpr int GP = STFEM_PROLONG_LANES;
-  if (h->dim == 2)
-    k_transfer<T, 2, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
-        nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
-  else
-    k_transfer<T, 3, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
-        nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
+  // small fine levels: 8 lanes per output (rows of P hold up to (r+1)^d entries)
+  const bool wide = nt * 8 <= (long)h->nsm * 1024;
+  if (h->dim == 2) {
+    if (wide)
+      k_transfer<T, 2, 8><<<grid_for(nt * 8, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
+    else
+      k_transfer<T, 2, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
+  } else {
+    if (wide)
+      k_transfer<T, 3, 8><<<grid_for(nt * 8, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
+    else
+      k_transfer<T, 3, GP><<<grid_for(nt * GP, 128) * nb, 128, 0, h->stream>>>(
+          nu, np, h->q, F.ns, F.R, C.ns, C.R, F.Pu_p, F.Pu_c, F.Pu_v, F.Pp_p, F.Pp_c, F.Pp_v, dc, df, 1, nb, C.N, F.N);
+  }
 }
 
 template <typename T>
@@ -1845,14 +1963,18 @@ void axpy_dot(stfem_h h, int k, const double *V, long ldV, const double *hvec, d
   const int nbk = h->dot_blocks;
   {
     Launch G_(h, STFEM_KCLASS_BLAS1, (double)(k + 2) * n * 8.0, 2.0 * k * n * (mode == 0 ? 2 : 1) + 2.0 * n);
-    if (k <= 8)
-      k_axpy_dot<8><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
-    else if (k <= 16)
-      k_axpy_dot<16><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
-    else if (k <= 24)
-      k_axpy_dot<24><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
-    else
-      k_axpy_dot<32><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode);
+    // the register blocks run KB >= k multiply-adds per entry: KB in steps of 4
+#define STFEM_AXPY_DOT(KB)                                                                                \
+  k_axpy_dot<KB><<<nbk, DOT_THREADS, 0, h->stream>>>(k, V, ldV, hvec, w, n, h->partial, mode)
+    if (k <= 4) STFEM_AXPY_DOT(4);
+    else if (k <= 8) STFEM_AXPY_DOT(8);
+    else if (k <= 12) STFEM_AXPY_DOT(12);
+    else if (k <= 16) STFEM_AXPY_DOT(16);
+    else if (k <= 20) STFEM_AXPY_DOT(20);
+    else if (k <= 24) STFEM_AXPY_DOT(24);
+    else if (k <= 28) STFEM_AXPY_DOT(28);
+    else STFEM_AXPY_DOT(32);
+#undef STFEM_AXPY_DOT
   }
   {
     const int nout = mode == 0 ? k : 1;
@@ -2619,7 +2741,10 @@ int noalloc_scratch(stfem_h h, unsigned char **out) {
 template <typename T>
 int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, int zero_init) {
   DLevel<T> &L = levels<T>(h)[level];
-  const size_t need = (3 * (size_t)L.N + (size_t)L.sumC) * sizeof(T);
+  // a level on the wide patch kernel also needs its slot results and ticket
+  // counters
+  const size_t wz = L.wide ? (size_t)L.sumC * sizeof(T) + (size_t)L.npatch * sizeof(int) : 0;
+  const size_t need = (3 * (size_t)L.N + (size_t)L.sumC) * sizeof(T) + wz;
   if (need > STFEM_NOALLOC_SCRATCH_BYTES) {
     h->err = "stfem_smooth_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
              " bytes of scratch, more than the " + std::to_string((size_t)STFEM_NOALLOC_SCRATCH_BYTES) +
@@ -2628,10 +2753,12 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   }
   unsigned char *base = nullptr;
   CKR(noalloc_scratch(h, &base));
-  // layout: b_T | d_T | r_T | y_T (each 256-byte aligned)
+  // layout: b_T | d_T | r_T | y_T [| z_T | tickets] (each 256-byte aligned)
   auto align = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t vb = align((size_t)L.N * sizeof(T));
-  if (3 * vb + (size_t)L.sumC * sizeof(T) > STFEM_NOALLOC_SCRATCH_BYTES) {
+  const size_t yb = align((size_t)L.sumC * sizeof(T));
+  const size_t total = 3 * vb + (L.wide ? 2 * yb + (size_t)L.npatch * sizeof(int) : (size_t)L.sumC * sizeof(T));
+  if (total > STFEM_NOALLOC_SCRATCH_BYTES) {
     h->err = "stfem_smooth_noalloc: level does not fit the static array after alignment";
     return STFEM_ERR_ARG;
   }
@@ -2639,8 +2766,12 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   T *dT = reinterpret_cast<T *>(base + vb);
   T *rT = reinterpret_cast<T *>(base + 2 * vb);
   T *yT = reinterpret_cast<T *>(base + 3 * vb);
+  T *zT = L.wide ? reinterpret_cast<T *>(base + 3 * vb + yb) : nullptr;
+  int *tT = L.wide ? reinterpret_cast<int *>(base + 3 * vb + 2 * yb) : nullptr;
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
   cudaStream_t s = h->stream;
+  // the array keeps the last call's contents: the tickets must start at zero
+  if (tT) CK(cudaMemsetAsync(tT, 0, (size_t)L.npatch * sizeof(int), s));
   k_convert<double, T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, b, bT);
   if (!zero_init) k_convert<double, T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d, dT);
   for (int it = 0; it < nsw; ++it) {
@@ -2657,7 +2788,7 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
         done = true;
       }
     }
-    if (!done) launch_patch_apply_to<T>(h, L, res, yT);
+    if (!done) launch_patch_apply_to<T>(h, L, res, yT, zT, tT);
     k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, L.iptr, L.ipos, L.scale, yT, dT, zero ? 1 : 0, 1,
                                                          L.sumC);
   }
@@ -2680,10 +2811,6 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
     return STFEM_ERR_ARG;
   }
   *out = nullptr;
-  if (deg && mesh && deg->pressure != STFEM_PRESSURE_CONTINUOUS && mesh->dim != 2) {
-    g_setup_err = "the broken pressure pair has a device path in 2D only";
-    return STFEM_ERR_ARG;
-  }
   stfem_h h = new stfem_ctx();
   cudaGetDevice(&h->device);
   if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->nsm < 1 ||
@@ -2836,10 +2963,13 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
     }
   }
   for (int l = 1; l < h->nlev; ++l) {
-    if (mixed)
+    if (mixed) {
+      CKR(prepare_wide(h, h->L32[l]));
       CKR(autotune_stream(h, h->L32[l]));
-    else
+    } else {
+      CKR(prepare_wide(h, h->L64[l]));
       CKR(autotune_stream(h, h->L64[l]));
+    }
   }
   CKR(check_dev_err(h));
   if (!coarse.get()) {
@@ -2872,6 +3002,24 @@ int stfem_set_launch_cap(stfem_h h, int max_ctas) {
   if (!h || max_ctas < 0) return STFEM_ERR_ARG;
   if (max_ctas != h->launch_cap) drop_graphs(h);
   h->launch_cap = max_ctas;
+  return STFEM_OK;
+}
+
+int stfem_set_patch_kernel(stfem_h h, int choice) {
+  if (!h || choice < STFEM_PATCH_KERNEL_AUTO || choice > STFEM_PATCH_KERNEL_WIDE) {
+    if (h) h->err = "unknown patch-apply kernel choice";
+    return STFEM_ERR_ARG;
+  }
+  CKR(require_gmg(h));
+  if (choice != h->patch_kernel) drop_graphs(h);
+  h->patch_kernel = choice;
+  for (int l = 1; l < h->nlev; ++l) {
+    if (h->precision == STFEM_MIXED)
+      CKR(prepare_wide(h, h->L32[l]));
+    else
+      CKR(prepare_wide(h, h->L64[l]));
+  }
+  CK(cudaStreamSynchronize(0)); // the ticket counters were cleared on the legacy stream
   return STFEM_OK;
 }
 

@@ -249,6 +249,165 @@ __global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict
   }
 }
 
+// Time-diagonal patch apply for levels with few patches (latency-bound under
+// the streaming kernel, whose CTAs each walk one patch's inverse chunk by
+// chunk): one CTA per (patch, slot), whose threads split the slot's Cs
+// columns into G groups, so that every 16-byte word of the slot's inverse is
+// requested in one wave of independent loads.  Thread t owns row group
+// t % nrg (VEC rows of a real slot, VEC/2 complex rows) and the columns
+// t / nrg, t / nrg + G, ...; the G partial sums of a row group are added in
+// the order of the groups.  The slot's result z_a goes to zbuf (the patch's
+// C = q Cs entries hold the q slot rows, nr + 2 nc = q); the last CTA of the
+// patch to finish (a ticket counter, reset by that CTA) mixes the slots back
+// to the time nodes with V and writes y.  Every value is formed by one fixed
+// sequence of operations, so the result does not depend on which CTA
+// finishes last.
+template <typename T, int Q>
+__global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict__ pcs,
+                                                          const long long *__restrict__ pdoff,
+                                                          const int *__restrict__ pdofs,
+                                                          const long long *__restrict__ pioff,
+                                                          const T *__restrict__ pinv, const T *__restrict__ res,
+                                                          T *__restrict__ y, T *__restrict__ zbuf,
+                                                          int *__restrict__ ticket, DiagCoef<T> dc) {
+  using Vv = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int CR = VEC / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nr = dc.nr, nc = dc.nc, ns = nr + nc;
+  const long p = blockIdx.x / ns;
+  const int a = (int)(blockIdx.x % ns); // slot of this CTA
+  const int Cs = pcs[p];
+  const long long doff = pdoff[p];
+  const bool cplx = a >= nr;
+  const int nrg = cplx ? (Cs + CR - 1) / CR : (Cs + VEC - 1) / VEC; // row groups
+  const int G = max(1, (int)blockDim.x / nrg);
+  T *rs = reinterpret_cast<T *>(smem_raw); // [Q][Cs] gathered residual
+  T *xr = rs + (size_t)Q * Cs;             // [Cs] slot input, real part
+  T *xi = xr + Cs;                         // [Cs] imaginary part
+  T *red = xi + Cs;                        // [G * nrg][VEC] partial sums
+  for (int j = threadIdx.x; j < Q * Cs; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
+  __syncthreads();
+  for (int m = threadIdx.x; m < Cs; m += blockDim.x) {
+    T re = T(0), im = T(0);
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const T r = rs[b * Cs + m];
+      re += dc.U[(a * Q + b) * 2] * r;
+      im += dc.U[(a * Q + b) * 2 + 1] * r;
+    }
+    xr[m] = re;
+    xi[m] = im;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  T vals[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) vals[v] = T(0);
+  const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+  const T *Ab = pinv + pioff[p];
+  if (t < G * nrg) {
+    const int g = t % nrg, jg = t / nrg;
+    if (!cplx) {
+      const Vv *col0 = reinterpret_cast<const Vv *>(Ab + (size_t)a * Cs * ldR + VEC * g);
+      const long stride = ldR / VEC;
+      int j = jg;
+      for (; j + 7 * G < Cs; j += 8 * G) {
+        Vv v8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v8[u] = __ldcs(col0 + (long)(j + u * G) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) fma_vec<T>(vals, v8[u], xr[j + u * G]);
+      }
+      for (; j < Cs; j += G) fma_vec<T>(vals, __ldcs(col0 + (long)j * stride), xr[j]);
+    } else {
+      const Vv *col0 =
+          reinterpret_cast<const Vv *>(Ab + (size_t)nr * Cs * ldR + (size_t)(a - nr) * Cs * ldC + 2 * CR * g);
+      const long stride = ldC / VEC;
+      int j = jg;
+      for (; j + 7 * G < Cs; j += 8 * G) {
+        Vv v8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v8[u] = __ldcs(col0 + (long)(j + u * G) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const T *av = reinterpret_cast<const T *>(&v8[u]);
+          const T ar = xr[j + u * G], ai = xi[j + u * G];
+#pragma unroll
+          for (int i = 0; i < CR; ++i) {
+            vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+            vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+          }
+        }
+      }
+      for (; j < Cs; j += G) {
+        const Vv v1 = __ldcs(col0 + (long)j * stride);
+        const T *av = reinterpret_cast<const T *>(&v1);
+        const T ar = xr[j], ai = xi[j];
+#pragma unroll
+        for (int i = 0; i < CR; ++i) {
+          vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+          vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) red[(size_t)t * VEC + v] = vals[v];
+  }
+  __syncthreads();
+  // z rows of this slot: real slot a -> row a; complex slot -> rows
+  // nr + 2 (a - nr) (re) and the next (im)
+  T *z = zbuf + doff;
+  for (int g = t; g < nrg; g += blockDim.x) {
+    T acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = red[(size_t)g * VEC + v];
+    for (int k = 1; k < G; ++k)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[v] += red[((size_t)k * nrg + g) * VEC + v];
+    if (!cplx) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        if (VEC * g + v < Cs) z[(size_t)a * Cs + VEC * g + v] = acc[v];
+    } else {
+      const int row = nr + 2 * (a - nr);
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+        if (CR * g + i < Cs) {
+          z[(size_t)row * Cs + CR * g + i] = acc[2 * i];
+          z[(size_t)(row + 1) * Cs + CR * g + i] = acc[2 * i + 1];
+        }
+    }
+  }
+  if (ns > 1) {
+    // the last CTA of the patch combines the slots (the flag is broadcast by
+    // the barrier itself: no static shared memory beside the dynamic region)
+    __threadfence();
+    __syncthreads();
+    int is_last = 0;
+    if (t == 0) {
+      is_last = atomicAdd(&ticket[p], 1) == ns - 1;
+      if (is_last) ticket[p] = 0;
+    }
+    if (!__syncthreads_or(is_last)) return;
+    __threadfence();
+  } else {
+    __syncthreads();
+  }
+  const int C = Q * Cs;
+  for (int idx = t; idx < C; idx += blockDim.x) {
+    const int b = idx / Cs, m = idx - b * Cs;
+    T val = T(0);
+    for (int s2 = 0; s2 < nr; ++s2) val += dc.V[(b * ns + s2) * 2] * __ldcg(z + (size_t)s2 * Cs + m);
+    for (int c = 0; c < nc; ++c) {
+      const int s2 = nr + c;
+      val += T(2) * (dc.V[(b * ns + s2) * 2] * __ldcg(z + (size_t)(nr + 2 * c) * Cs + m) -
+                     dc.V[(b * ns + s2) * 2 + 1] * __ldcg(z + (size_t)(nr + 2 * c + 1) * Cs + m));
+    }
+    y[doff + idx] = val;
+  }
+}
+
 // d = (zero ? 0 : d) + scale * sum of the patch results holding each dof.
 // scale = omega / (number of patches holding the dof): Algorithm 4.1's
 // d = z / p written as d + omega D^{-1} sum_P E_P A_P^{-1} R_P (b - A d).

@@ -5,9 +5,8 @@ Every step that differs from Taylor-Hood is compared element by element:
 the level operators (cell boxes and face slots of the node-block layout),
 the initial state (L2-projected pressure), the slab right-hand side, the
 smoother (dense and time-diagonal patch inverses), whole solves and a march,
-in FP64 and in the mixed mode, for both slab forms.  Tolerances as in
-test_gpu_parity.  While stfem_setup refuses the broken pair (its device
-path has not been enabled), every test is skipped.
+in FP64 and in the mixed mode, for both slab forms, in 2D (Q2/P1disc,
+Q3/P2disc) and 3D (Q2/P1disc).  Tolerances as in test_gpu_parity.
 """
 import numpy as np
 import pytest
@@ -17,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 from _cases import case, gpu_problem, oracle_instance
 
-CASES = ["c1_2d_q2_k1_8", "c2_small_2d_q3_k2_8"]
+CASES = ["c1_2d_q2_k1_8", "c2_small_2d_q3_k2_8", "c3_small_3d_q2_k1_4"]
 FORMS = ["3.1", "B.1"]
 _cache = {}
 
@@ -41,13 +40,8 @@ def pair(name, form, precision=0, patch_form=0):
         import paper_2303_06742_gb300 as st
         c = case(name)
         f = st.FORM_PROBLEM_B_1 if form == "B.1" else st.FORM_PROBLEM_3_1
-        try:
-            S = st.Solver(gpu_problem(c, form=f, pressure=st.PRESSURE_BROKEN), precision=precision,
-                          patch_form=patch_form)
-        except st.StfemError as e:
-            if e.code == st.ERR_ARG:
-                pytest.skip("the broken pressure pair has no enabled device path: %s" % e)
-            raise
+        S = st.Solver(gpu_problem(c, form=f, pressure=st.PRESSURE_BROKEN), precision=precision,
+                      patch_form=patch_form)
         O = oracle_instance(c, form=form, pressure="disc")
         _cache[key] = (c, S, O)
     return _cache[key]

@@ -71,6 +71,7 @@ def test_streaming_apply_many_patches_per_cta(name, precision, tol):
     import paper_2303_06742_gb300 as st
     O = oracle(name)
     S = st.Solver(gpu_problem(case(name)), precision=precision, patch_form=st.PATCH_TIME_DIAGONAL)
+    S.set_patch_kernel(st.PATCH_KERNEL_STREAM)  # these small levels would take the wide kernel
     free = _smooth_all_levels(S, O, 71)
     for cap in CAPS:
         S.set_launch_cap(cap)
@@ -125,6 +126,7 @@ def test_capped_vcycle_and_solve_unchanged(precision):
     name = "c2_small_2d_q3_k2_8"
     O = oracle(name)
     S = st.Solver(gpu_problem(case(name)), precision=precision, patch_form=st.PATCH_TIME_DIAGONAL)
+    S.set_patch_kernel(st.PATCH_KERNEL_STREAM)
     st0 = O.initial_state()
     b = O.rhs(0, st0)
     x0 = repeat_state(O.ops, O.tmp, st0)
@@ -167,4 +169,28 @@ def test_default_grid_smaller_than_patch_count(precision, tol):
     err = _rel(host(d), O.h.vcycle(b))
     print(name, precision, "vcycle", err)
     assert err < (1e-10 if precision == 0 else 1e-4)
+    S.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+def test_wide_apply_every_level(name, precision, tol):
+    """The wide patch kernel (one CTA per patch and slot, the default on levels
+    with few patches) on every level: against the oracle, the same result on
+    a second call (its slot combine is ordered, whichever CTA finishes last),
+    and the streaming kernel's result to rounding."""
+    import paper_2303_06742_gb300 as st
+    O = oracle(name)
+    S = st.Solver(gpu_problem(case(name)), precision=precision, patch_form=st.PATCH_TIME_DIAGONAL)
+    S.set_patch_kernel(st.PATCH_KERNEL_WIDE)
+    a = _smooth_all_levels(S, O, 75)
+    b = _smooth_all_levels(S, O, 75)
+    S.set_patch_kernel(st.PATCH_KERNEL_STREAM)
+    c = _smooth_all_levels(S, O, 75)
+    for l, ((g, ref), (g2, _), (g3, _)) in enumerate(zip(a, b, c), start=1):
+        err = _rel(g, ref)
+        print(name, precision, "wide level", l, err, "vs stream", _rel(g, g3))
+        assert err < tol
+        assert np.array_equal(g, g2)
+        assert _rel(g, g3) < tol
     S.close()

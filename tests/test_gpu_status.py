@@ -66,6 +66,7 @@ def test_bounded_wait_runs_out_and_handle_recovers(precision):
     c = case("c2_small_2d_q3_k2_8")
     O = oracle_instance(c)
     S = st.Solver(gpu_problem(c), precision=precision, patch_form=st.PATCH_TIME_DIAGONAL)
+    S.set_patch_kernel(st.PATCH_KERNEL_STREAM)  # the kernel with the bounded waits
     lev = O.h.levels[-1]
     rng = np.random.default_rng(91)
     b = rng.standard_normal(lev.A.shape[0])

@@ -3,8 +3,7 @@ refuses what cannot run instead of failing later on the device.
 
 * A request whose footprint estimate exceeds the whole HBM budget is refused
   at submission (an allocation failure made on the host).
-* A request for the broken pressure pair in 3D, which has no device path,
-  is refused at submission too.
+* A request with a negative slab count is refused at submission too.
 """
 import pytest
 
@@ -23,8 +22,7 @@ def test_admission_refuses_oversized_and_device_less_requests():
         small.close()
     big = stfem.Server(1 << 40, 1)
     try:
-        disc = stfem.Problem(3, 4, 2, 2, 1, 0.01, problem=stfem.PROBLEM_SIN, pressure=stfem.PRESSURE_BROKEN)
         with pytest.raises(stfem.StfemError):
-            big.submit(disc, 2)
+            big.submit(prob, -1)
     finally:
         big.close()
