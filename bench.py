@@ -58,6 +58,8 @@ def parse():
                         "batched path with the tensor-core patch apply")
     p.add_argument("--form", default="3.1", choices=["3.1", "B.1"],
                    help="slab problem: Problem 3.1 (default) or Problem B.1 of Appendix B")
+    p.add_argument("--fine-operator", default="auto", choices=["auto", "assembled", "matrix-free"],
+                   help="operator of the finest level inside the mixed-precision V-cycle")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -277,12 +279,16 @@ def pct(vals, q):
 
 
 # ------------------------------------------------------------------ GPU arm
-def make_solver(c, precision, stream, sweeps=1, form="3.1"):
+FINE_OPERATORS = {"auto": 0, "assembled": 1, "matrix-free": 2}
+
+
+def make_solver(c, precision, stream, sweeps=1, form="3.1", fine_operator="auto"):
     import paper_2303_06742_gb300 as st
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from _cases import gpu_problem
     f = st.FORM_PROBLEM_B_1 if form == "B.1" else st.FORM_PROBLEM_3_1
-    return st.Solver(gpu_problem(c, form=f), precision=precision, stream=stream, n_sweeps=sweeps)
+    return st.Solver(gpu_problem(c, form=f), precision=precision, stream=stream, n_sweeps=sweeps,
+                     fine_operator=FINE_OPERATORS[fine_operator])
 
 
 def time_march(S, torch, stream, state, first, steps, tol, profile=False):
@@ -324,7 +330,7 @@ def gpu_arm(args):
 
     # ---- mixed precision (headline)
     t0 = time.perf_counter()
-    S = make_solver(c, st.MIXED, stream, args.sweeps, args.form)
+    S = make_solver(c, st.MIXED, stream, args.sweeps, args.form, args.fine_operator)
     setup_s = time.perf_counter() - t0
     state = torch.zeros(S.n_state, dtype=torch.float64, device="cuda")
     S.initial_state(state)

@@ -224,12 +224,28 @@ int stfem_set_stream(stfem_h h, void *stream);
  * is the same in every CTA.  STFEM_ERR_ARG for max_ctas < 0. */
 int stfem_set_launch_cap(stfem_h h, int max_ctas);
 
+/* Operator of the finest level inside the mixed-precision V-cycle (its FP32
+ * residuals, Eq. 4.7).  ASSEMBLED: the node-block form of the assembled
+ * spatial matrices; MATRIX_FREE: cell by cell from the unit-coefficient
+ * element matrices of the uniform mesh and the per-cell coefficients (no
+ * global matrix is read; Taylor-Hood pressure only, else the assembled form
+ * is kept); AUTO (default): ASSEMBLED, the faster form on GB300 at the
+ * workloads' degrees (measured: the assembled node-block product takes about
+ * half the time of the cell-by-cell one).  The two forms
+ * differ by FP32 rounding.  The FP64 products (FGMRES, true residuals) and
+ * the coarser levels always use the assembled form.  Must be called before
+ * stfem_gmg_setup (STFEM_ERR_STATE after it). */
+#define STFEM_OPERATOR_AUTO 0
+#define STFEM_OPERATOR_ASSEMBLED 1
+#define STFEM_OPERATOR_MATRIX_FREE 2
+int stfem_set_fine_operator(stfem_h h, int choice);
+
 /* Patch-apply kernel of the time-diagonal levels (Algorithm 4.1's local
  * solves).  STREAM: a persistent grid whose CTAs each stream their patches'
  * inverses through a shared-memory ring (bulk copies); WIDE: one CTA per
  * (patch, slot) that requests the slot's whole inverse in one wave of loads
  * (lower latency where a level has few patches); AUTO (default): WIDE for
- * levels with at most 4 patches per multiprocessor, STREAM for the others.
+ * levels with at most one patch per multiprocessor, STREAM for the others.
  * The two kernels sum in different orders, so their results differ by
  * rounding; for a given choice and device every result is deterministic.
  * Tensor-core levels (several right-hand sides) are not affected.  Needs
@@ -469,7 +485,10 @@ void stfem_server_destroy(stfem_server s);
  * setup data are only read.
  *
  * Needs (3 n_slab + sum of patch sizes) * (4 in STFEM_MIXED, 8 in STFEM_FP64)
- * bytes of scratch (each part rounded up to 256 bytes); larger levels are
+ * bytes of scratch, plus, on a level with the wide patch kernel, the slot
+ * results (sum of patch sizes) and a 4-byte counter per patch, and on a
+ * matrix-free level its per-cell results (each part rounded up to 256
+ * bytes); larger levels are
  * rejected with STFEM_ERR_ARG and a message naming the sizes.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current.  The current device must be the one the handle was set

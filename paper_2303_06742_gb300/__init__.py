@@ -30,6 +30,7 @@ PRESSURE_CONTINUOUS, PRESSURE_BROKEN = 0, 1
 PATCH_AUTO, PATCH_DENSE, PATCH_TIME_DIAGONAL = 0, 1, 2
 PATCHES_VERTEX, PATCHES_CELL = 0, 1
 PATCH_KERNEL_AUTO, PATCH_KERNEL_STREAM, PATCH_KERNEL_WIDE = 0, 1, 2
+OPERATOR_AUTO, OPERATOR_ASSEMBLED, OPERATOR_MATRIX_FREE = 0, 1, 2
 UPDATE_AVERAGE, UPDATE_OVERWRITE = 0, 1
 STOP_RELATIVE, STOP_ABSOLUTE = 0, 1
 KCLASSES = ["spmv", "patch_apply", "update", "transfer", "coarse", "blas1", "rhs", "other"]
@@ -104,6 +105,7 @@ def _load():
         "slab_solve": [P, P, P, D, I, I, pI, pD, pD],
         "stfem_set_launch_cap": [P, I],
         "stfem_set_patch_kernel": [P, I],
+        "stfem_set_fine_operator": [P, I],
         "stfem_set_wait_limit": [P, D],
         "stfem_stall_copies": [P, I],
         "stfem_solve_history": [P, pD, I, pI],
@@ -272,7 +274,8 @@ class Solver:
     """Handle of one problem instance on the current CUDA device."""
 
     def __init__(self, prob, omega=0.7, n_sweeps=1, precision=FP64, stream=None, patch_form=PATCH_AUTO,
-                 patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE, stop=STOP_RELATIVE, n_rhs=0, factor_host=0):
+                 patch_kind=PATCHES_VERTEX, update=UPDATE_AVERAGE, stop=STOP_RELATIVE, n_rhs=0, factor_host=0,
+                 fine_operator=OPERATOR_AUTO):
         self.prob = prob
         h = C.c_void_p()
         rc = lib.stfem_setup(*prob.args(), C.byref(h))
@@ -281,6 +284,7 @@ class Solver:
         self.h = h
         if stream is not None:
             self.set_stream(stream)
+        self._check(lib.stfem_set_fine_operator(self.h, int(fine_operator)))
         self._check(lib.stfem_gmg_setup(self.h, C.byref(GmgParams(omega, n_sweeps, precision, patch_form,
                                                                   patch_kind, update, n_rhs, factor_host))))
         self.set_stop(stop)

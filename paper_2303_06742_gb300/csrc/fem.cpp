@@ -717,6 +717,29 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
       }
     }
 
+  L.bc = bc;
+  if (!disc) {
+    Level::Elem &E = L.elem;
+    E.nu = nu;
+    E.np = np;
+    E.locu = RU.loc;
+    E.locp = RP.loc;
+    E.Mu = Mu;
+    E.Kmu = Kmu;
+    E.Klam = Klam;
+    E.Cv = Cv;
+    E.Bv = Bv;
+    E.Mp = Mp;
+    for (int f = 0; f < 2 * d; ++f) {
+      E.fKmu[f] = F[f].Kmu;
+      E.fKlam[f] = F[f].Klam;
+      E.fKpen[f] = F[f].Kpen;
+      E.fC[f] = F[f].C;
+      E.fB[f] = F[f].B;
+      E.fBpen[f] = F[f].Bpen;
+    }
+  }
+
   // node-level matrices
   NodeMat UU = make_nodemat(L.U, L.U, b, 1 + d * d); // M, K[c][c']
   NodeMat UP, PU, PP;                               // C^T: C[s][(I,c)]; C[s][(J,c')]; Mp, B

@@ -105,7 +105,22 @@ struct Level {
   // exponent fastest); P.nnodes counts its dofs and P.dims is unused.
   bool pdisc = false;
   int pnloc = 0;
-  // per lattice node: spatial position, for initial values and loads
+  // Unit-coefficient element matrices of the level's cells (uniform mesh, so
+  // one set serves every cell), kept for the matrix-free operator (continuous
+  // pressure only).  Row-major; u dofs i * d + c (i < nu local Q_r nodes),
+  // p dofs s (np local Q_{r-1} nodes); local nodes lexicographic, x fastest,
+  // with lattice offsets locu / locp (3 per node).  A cell with lambda, mu,
+  // kappa has K = lam Klam + mu Kmu (+ per Dirichlet-u face f:
+  // lam fKlam[f] + mu fKmu[f] + fKpen[f]), C = Cv (+ fC[f]), the mass rho Mu
+  // (per component) and c0 Mp, B = kap Bv (+ per Dirichlet-p face:
+  // kap fB[f] + fBpen[f]); f = 2 axis + side.  alpha is part of Cv and fC.
+  struct Elem {
+    int nu = 0, np = 0;
+    std::vector<int> locu, locp;
+    std::vector<double> Mu, Kmu, Klam, Cv, Bv, Mp;
+    std::vector<double> fKmu[6], fKlam[6], fKpen[6], fC[6], fB[6], fBpen[6];
+  } elem;
+  BCs bc;
 };
 
 Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc, int form = 0, int pressure = 0);

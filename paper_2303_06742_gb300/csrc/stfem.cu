@@ -62,6 +62,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 #include "spmv.cuh"
+#include "matfree.cuh"
 #include "vanka.cuh"
 
 // ---------------------------------------------------------------- bulk-copy streaming
@@ -330,6 +331,11 @@ struct DLevel {
   NodeBlockDev<float2> nbdf{};
   // Problem B.1: -Cvol in the layout of nb.pu_c (assembled levels)
   const T *pu_cvol = nullptr;
+  // matrix-free form of the same operator (finest FP32 level; see
+  // matfree.cuh) and whether the level's single-column products use it
+  bool has_mf = false, use_mf = false;
+  MfDev mf{};
+  double mf_bytes = 0.0, mf_flops = 0.0;
   bool has_df = false;
   double nb_bytes = 0.0, nb_flops = 0.0;
   // patches
@@ -388,6 +394,8 @@ struct stfem_ctx {
   int stall_copies = 0;
   // patch-apply kernel of the time-diagonal levels (STFEM_PATCH_KERNEL_*)
   int patch_kernel = 0;
+  // operator of the finest FP32 level (STFEM_OPERATOR_*)
+  int fine_op = 0;
   int dim = 2, r = 2, k = 1, q = 2, nlev = 1;
   double tau = 0.01, t0 = 0.0;
   int problem = 0;
@@ -600,9 +608,62 @@ double spmv_bytes(const DLevel<T> &L, int q, int mode) {
 }
 
 // nb > 1: nb columns of x, rhs, y with column stride L.N
+template <int Q, int D>
+void launch_mf_qd(stfem_h h, const DLevel<float> &L, const TimeCoef<float> &tc, const float *x, const float *rhs,
+                  float *y, int mode, float *scratch) {
+  MfDev A = L.mf;
+  if (scratch) A.scratch = scratch;
+  const size_t smem = (size_t)MF_CELLS * Q * (2 * A.du + A.np) * sizeof(float);
+  const long ntile = (A.ncell + MF_CELLS - 1) / MF_CELLS;
+  const int per_sm = std::max(1, std::min(16, (int)((227u * 1024u) / smem)));
+  const long tiles = std::min<long>(ntile, std::max<long>(1, (long)h->nsm * per_sm / MF_PARTS));
+  k_mf_cells<Q, D><<<(unsigned)(tiles * MF_PARTS), 32 * MF_WARPS, smem, h->stream>>>(A, tc, x);
+  const long nnode = A.R / D + A.S;
+  k_mf_gather<Q, D><<<grid_for((long)Q * nnode, 256), 256, 0, h->stream>>>(A, rhs, y, mode);
+}
+
+template <int Q>
+void launch_mf_q(stfem_h h, const DLevel<float> &L, const TimeCoef<float> &tc, const float *x, const float *rhs,
+                 float *y, int mode, float *scratch) {
+  if (L.mf.d == 2)
+    launch_mf_qd<Q, 2>(h, L, tc, x, rhs, y, mode, scratch);
+  else
+    launch_mf_qd<Q, 3>(h, L, tc, x, rhs, y, mode, scratch);
+}
+
+// y = A x (mode 0) or rhs - A x (mode 1) on a level with the matrix-free form
+// (scratch: the per-cell results, nullptr = the level's own buffer)
+void launch_mf(stfem_h h, const DLevel<float> &L, const TimeCoef<float> &tc, const float *x, const float *rhs,
+               float *y, int mode, float *scratch = nullptr) {
+  Launch G_(h, STFEM_KCLASS_SPMV, L.mf_bytes + (double)tc.q * L.ns * sizeof(float) * (mode ? 3 : 2), L.mf_flops);
+  switch (tc.q) {
+  case 1: launch_mf_q<1>(h, L, tc, x, rhs, y, mode, scratch); break;
+  case 2: launch_mf_q<2>(h, L, tc, x, rhs, y, mode, scratch); break;
+  case 3: launch_mf_q<3>(h, L, tc, x, rhs, y, mode, scratch); break;
+  case 4: launch_mf_q<4>(h, L, tc, x, rhs, y, mode, scratch); break;
+  default: launch_mf_q<5>(h, L, tc, x, rhs, y, mode, scratch); break;
+  }
+}
+
+// floats of per-cell results the matrix-free form of a level needs
+template <typename T>
+size_t mf_scratch_floats(const DLevel<T> &L, int q) {
+  if (!L.use_mf) return 0;
+  return (size_t)L.mf.n[0] * L.mf.n[1] * L.mf.n[2] * q * (2 * L.mf.du + L.mf.np);
+}
+
+// mf_scratch: per-cell results of the matrix-free form (nullptr = the level's)
 template <typename T>
 void launch_spmv(stfem_h h, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
-                 int mode, int nb = 1) {
+                 int mode, int nb = 1, T *mf_scratch = nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.use_mf) {
+      for (int c = 0; c < nb; ++c)
+        launch_mf(h, L, tc, x + (long)c * L.N, rhs ? rhs + (long)c * L.N : nullptr, y + (long)c * L.N, mode,
+                  mf_scratch);
+      return;
+    }
+  }
   Launch G_(h, STFEM_KCLASS_SPMV, L.nb_bytes + (spmv_bytes(L, tc.q, mode) - L.nb_bytes) * nb,
             L.nb_flops * tc.q * nb);
   cudaStream_t s = h->stream;
@@ -1114,6 +1175,71 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
 
 // Float-pair copy (hi = fl32(a), lo = fl32(a - hi)) of the node-block values
 // of an FP64 level, for the double-float SpMV.
+// Matrix-free form of an FP32 level (continuous pressure): the unit element
+// matrices in FP32, the per-cell coefficients and the per-cell result buffer.
+int upload_matfree(stfem_h h, DLevel<float> &D, const stfem::Level &L) {
+  const stfem::Level::Elem &E = L.elem;
+  if (L.pdisc || E.nu == 0) return 0;
+  const int d = L.box.dim, nu = E.nu, np = E.np, du = nu * d;
+  MfDev &A = D.mf;
+  A.d = d;
+  A.r = L.r;
+  A.nu = nu;
+  A.np = np;
+  A.du = du;
+  A.q = h->q;
+  for (int i = 0; i < 3; ++i) {
+    A.n[i] = L.box.n[i];
+    A.udims[i] = L.U.dims[i];
+    A.pdims[i] = L.P.dims[i];
+  }
+  A.R = L.R;
+  A.S = L.S;
+  A.ns = L.ns;
+  A.pcouple = L.form == STFEM_FORM_PROBLEM_B_1 ? 1 : 0;
+  A.bc_u = A.bc_p = 0;
+  for (int f = 0; f < 2 * d; ++f) {
+    if (L.bc.bc_u[f] == STFEM_BC_DIRICHLET) A.bc_u |= 1 << f;
+    if (L.bc.bc_p[f] == STFEM_BC_DIRICHLET) A.bc_p |= 1 << f;
+  }
+  A.rho = (float)L.coef.rho;
+  A.c0 = (float)L.coef.c0;
+  float *p = nullptr;
+  CKR(upload(h, &p, E.Mu)); A.Mu = p;
+  CKR(upload(h, &p, E.Klam)); A.Klam = p;
+  CKR(upload(h, &p, E.Kmu)); A.Kmu = p;
+  CKR(upload(h, &p, E.Cv)); A.Cv = p;
+  CKR(upload(h, &p, E.Bv)); A.Bv = p;
+  CKR(upload(h, &p, E.Mp)); A.Mp = p;
+  std::vector<double> fK((size_t)6 * 3 * du * du, 0.0), fC((size_t)6 * np * du, 0.0),
+      fB((size_t)6 * 2 * np * np, 0.0);
+  for (int f = 0; f < 2 * d; ++f) {
+    std::copy(E.fKlam[f].begin(), E.fKlam[f].end(), fK.begin() + (size_t)f * 3 * du * du);
+    std::copy(E.fKmu[f].begin(), E.fKmu[f].end(), fK.begin() + (size_t)f * 3 * du * du + (size_t)du * du);
+    std::copy(E.fKpen[f].begin(), E.fKpen[f].end(), fK.begin() + (size_t)f * 3 * du * du + 2 * (size_t)du * du);
+    std::copy(E.fC[f].begin(), E.fC[f].end(), fC.begin() + (size_t)f * np * du);
+    std::copy(E.fB[f].begin(), E.fB[f].end(), fB.begin() + (size_t)f * 2 * np * np);
+    std::copy(E.fBpen[f].begin(), E.fBpen[f].end(), fB.begin() + (size_t)f * 2 * np * np + (size_t)np * np);
+  }
+  CKR(upload(h, &p, fK)); A.fK = p;
+  CKR(upload(h, &p, fC)); A.fC = p;
+  CKR(upload(h, &p, fB)); A.fB = p;
+  CKR(upload(h, &p, L.coef.lam)); A.lam = p;
+  CKR(upload(h, &p, L.coef.mu)); A.mu = p;
+  CKR(upload(h, &p, L.coef.kap)); A.kap = p;
+  const long ncell = L.box.ncell;
+  A.ncell = ncell;
+  float *sc = nullptr;
+  CKR(dalloc(h, &sc, (size_t)ncell * h->q * (2 * du + np)));
+  A.scratch = sc;
+  // algorithmic bytes beyond x and y: the per-cell results written and read
+  // back, and the per-cell coefficients
+  D.mf_bytes = (double)ncell * h->q * (2 * du + np) * 8.0 + ncell * 12.0;
+  D.mf_flops = 2.0 * ncell * h->q * ((double)nu * nu * 2 * d + 2.0 * du * du + 2.0 * np * du + 2.0 * np * np);
+  D.has_mf = true;
+  return 0;
+}
+
 int upload_level_df(stfem_h h, DLevel<double> &D, const stfem::Level &L) {
   NodeBlockHost H;
   std::string err;
@@ -1538,7 +1664,7 @@ void launch_patch_diag_q(cudaStream_t s, DLevel<T> &L, int RT, int J, size_t sme
 // run) and each slot's row groups fit one CTA.
 constexpr int WIDE_THREADS = 512;
 #ifndef STFEM_WIDE_MAX_PATCHES_PER_SM
-#define STFEM_WIDE_MAX_PATCHES_PER_SM 4
+#define STFEM_WIDE_MAX_PATCHES_PER_SM 1
 #endif
 
 template <typename T>
@@ -1685,6 +1811,11 @@ int prepare_stream_kernels(stfem_h h) {
   STFEM_SMEM_ATTR_W(double, 1); STFEM_SMEM_ATTR_W(double, 2); STFEM_SMEM_ATTR_W(double, 3);
   STFEM_SMEM_ATTR_W(double, 4); STFEM_SMEM_ATTR_W(double, 5);
 #undef STFEM_SMEM_ATTR_W
+#define STFEM_SMEM_ATTR_MF(Q)                                                                            \
+  CK(cudaFuncSetAttribute(k_mf_cells<Q, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));   \
+  CK(cudaFuncSetAttribute(k_mf_cells<Q, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
+  STFEM_SMEM_ATTR_MF(1); STFEM_SMEM_ATTR_MF(2); STFEM_SMEM_ATTR_MF(3); STFEM_SMEM_ATTR_MF(4); STFEM_SMEM_ATTR_MF(5);
+#undef STFEM_SMEM_ATTR_MF
   CK(cudaFuncSetAttribute(k_patch_apply_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   CK(cudaFuncSetAttribute(k_patch_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -2744,7 +2875,9 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   // a level on the wide patch kernel also needs its slot results and ticket
   // counters
   const size_t wz = L.wide ? (size_t)L.sumC * sizeof(T) + (size_t)L.npatch * sizeof(int) : 0;
-  const size_t need = (3 * (size_t)L.N + (size_t)L.sumC) * sizeof(T) + wz;
+  // and a matrix-free level its per-cell results
+  const size_t mz = mf_scratch_floats(L, h->q) * sizeof(T);
+  const size_t need = (3 * (size_t)L.N + (size_t)L.sumC) * sizeof(T) + wz + mz;
   if (need > STFEM_NOALLOC_SCRATCH_BYTES) {
     h->err = "stfem_smooth_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
              " bytes of scratch, more than the " + std::to_string((size_t)STFEM_NOALLOC_SCRATCH_BYTES) +
@@ -2753,11 +2886,13 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   }
   unsigned char *base = nullptr;
   CKR(noalloc_scratch(h, &base));
-  // layout: b_T | d_T | r_T | y_T [| z_T | tickets] (each 256-byte aligned)
+  // layout: b_T | d_T | r_T | y_T [| z_T | tickets] [| per-cell results]
+  // (each 256-byte aligned)
   auto align = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t vb = align((size_t)L.N * sizeof(T));
   const size_t yb = align((size_t)L.sumC * sizeof(T));
-  const size_t total = 3 * vb + (L.wide ? 2 * yb + (size_t)L.npatch * sizeof(int) : (size_t)L.sumC * sizeof(T));
+  const size_t tb = align((size_t)L.npatch * sizeof(int));
+  const size_t total = 3 * vb + (L.wide ? 2 * yb + tb : yb) + mz;
   if (total > STFEM_NOALLOC_SCRATCH_BYTES) {
     h->err = "stfem_smooth_noalloc: level does not fit the static array after alignment";
     return STFEM_ERR_ARG;
@@ -2768,6 +2903,7 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   T *yT = reinterpret_cast<T *>(base + 3 * vb);
   T *zT = L.wide ? reinterpret_cast<T *>(base + 3 * vb + yb) : nullptr;
   int *tT = L.wide ? reinterpret_cast<int *>(base + 3 * vb + 2 * yb) : nullptr;
+  T *mT = mz ? reinterpret_cast<T *>(base + 3 * vb + (L.wide ? 2 * yb + tb : yb)) : nullptr;
   const TimeCoef<T> tc = time_coef<T>(h->T, h->tau);
   cudaStream_t s = h->stream;
   // the array keeps the last call's contents: the tickets must start at zero
@@ -2778,7 +2914,7 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
     const bool zero = zero_init && it == 0;
     const T *res = bT;
     if (!zero) {
-      launch_spmv<T>(h, L, tc, dT, bT, rT, 1);
+      launch_spmv<T>(h, L, tc, dT, bT, rT, 1, 1, mT);
       res = rT;
     }
     bool done = false;
@@ -2917,6 +3053,10 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
       if (l >= 1) CKR(upload_transfer(h, h->L32[l], h->Pu[l], h->Pp[l]));
     }
     CKR(upload_level_df(h, h->L64.back(), h->hl.back()));
+    if (h->fine_op == STFEM_OPERATOR_MATRIX_FREE) {
+      CKR(upload_matfree(h, h->L32.back(), h->hl.back()));
+      h->L32.back().use_mf = h->L32.back().has_mf;
+    }
   }
   int form = p->patch_form;
   if (form == STFEM_PATCH_AUTO) form = mixed ? STFEM_PATCH_TIME_DIAGONAL : STFEM_PATCH_DENSE;
@@ -3002,6 +3142,19 @@ int stfem_set_launch_cap(stfem_h h, int max_ctas) {
   if (!h || max_ctas < 0) return STFEM_ERR_ARG;
   if (max_ctas != h->launch_cap) drop_graphs(h);
   h->launch_cap = max_ctas;
+  return STFEM_OK;
+}
+
+int stfem_set_fine_operator(stfem_h h, int choice) {
+  if (!h || choice < STFEM_OPERATOR_AUTO || choice > STFEM_OPERATOR_MATRIX_FREE) {
+    if (h) h->err = "unknown operator choice";
+    return STFEM_ERR_ARG;
+  }
+  if (h->precision >= 0) {
+    h->err = "stfem_set_fine_operator must be called before stfem_gmg_setup";
+    return STFEM_ERR_STATE;
+  }
+  h->fine_op = choice;
   return STFEM_OK;
 }
 

@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict_
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
+  constexpr int PF = 8; // loads of the inverse a thread keeps in flight
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nr = dc.nr, nc = dc.nc, ns = nr + nc;
   const long p = blockIdx.x / ns;
@@ -286,9 +287,24 @@ __global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict_
   T *xr = rs + (size_t)Q * Cs;             // [Cs] slot input, real part
   T *xi = xr + Cs;                         // [Cs] imaginary part
   T *red = xi + Cs;                        // [G * nrg][VEC] partial sums
-  for (int j = threadIdx.x; j < Q * Cs; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
+  const int t = threadIdx.x;
+  const bool active = t < G * nrg;
+  const int g = t % nrg, jg = t / nrg;
+  const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+  const T *Ab = pinv + pioff[p];
+  const Vv *col0 = cplx ? reinterpret_cast<const Vv *>(Ab + (size_t)nr * Cs * ldR + (size_t)(a - nr) * Cs * ldC +
+                                                       2 * CR * g)
+                        : reinterpret_cast<const Vv *>(Ab + (size_t)a * Cs * ldR + VEC * g);
+  const long stride = (cplx ? ldC : ldR) / VEC;
+  // the first PF columns of this thread are requested before the residual is
+  // gathered, so that the two chains of loads overlap
+  Vv buf[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u)
+    if (active && jg + u * G < Cs) buf[u] = __ldcs(col0 + (long)(jg + u * G) * stride);
+  for (int j = t; j < Q * Cs; j += blockDim.x) rs[j] = res[pdofs[doff + j]];
   __syncthreads();
-  for (int m = threadIdx.x; m < Cs; m += blockDim.x) {
+  for (int m = t; m < Cs; m += blockDim.x) {
     T re = T(0), im = T(0);
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
@@ -300,54 +316,32 @@ __global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict_
     xi[m] = im;
   }
   __syncthreads();
-  const int t = threadIdx.x;
   T vals[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) vals[v] = T(0);
-  const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
-  const T *Ab = pinv + pioff[p];
-  if (t < G * nrg) {
-    const int g = t % nrg, jg = t / nrg;
-    if (!cplx) {
-      const Vv *col0 = reinterpret_cast<const Vv *>(Ab + (size_t)a * Cs * ldR + VEC * g);
-      const long stride = ldR / VEC;
-      int j = jg;
-      for (; j + 7 * G < Cs; j += 8 * G) {
-        Vv v8[8];
+  if (active) {
+    for (int j0 = jg; j0 < Cs; j0 += PF * G) {
+      Vv cur[PF];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v8[u] = __ldcs(col0 + (long)(j + u * G) * stride);
+      for (int u = 0; u < PF; ++u) cur[u] = buf[u];
+      // next PF columns in flight while these are used
 #pragma unroll
-        for (int u = 0; u < 8; ++u) fma_vec<T>(vals, v8[u], xr[j + u * G]);
-      }
-      for (; j < Cs; j += G) fma_vec<T>(vals, __ldcs(col0 + (long)j * stride), xr[j]);
-    } else {
-      const Vv *col0 =
-          reinterpret_cast<const Vv *>(Ab + (size_t)nr * Cs * ldR + (size_t)(a - nr) * Cs * ldC + 2 * CR * g);
-      const long stride = ldC / VEC;
-      int j = jg;
-      for (; j + 7 * G < Cs; j += 8 * G) {
-        Vv v8[8];
+      for (int u = 0; u < PF; ++u)
+        if (j0 + (PF + u) * G < Cs) buf[u] = __ldcs(col0 + (long)(j0 + (PF + u) * G) * stride);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v8[u] = __ldcs(col0 + (long)(j + u * G) * stride);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const T *av = reinterpret_cast<const T *>(&v8[u]);
-          const T ar = xr[j + u * G], ai = xi[j + u * G];
+      for (int u = 0; u < PF; ++u) {
+        const int j = j0 + u * G;
+        if (j >= Cs) break;
+        if (!cplx) {
+          fma_vec<T>(vals, cur[u], xr[j]);
+        } else {
+          const T *av = reinterpret_cast<const T *>(&cur[u]);
+          const T ar = xr[j], ai = xi[j];
 #pragma unroll
           for (int i = 0; i < CR; ++i) {
             vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
             vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
           }
-        }
-      }
-      for (; j < Cs; j += G) {
-        const Vv v1 = __ldcs(col0 + (long)j * stride);
-        const T *av = reinterpret_cast<const T *>(&v1);
-        const T ar = xr[j], ai = xi[j];
-#pragma unroll
-        for (int i = 0; i < CR; ++i) {
-          vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
-          vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
         }
       }
     }
@@ -358,24 +352,24 @@ __global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict_
   // z rows of this slot: real slot a -> row a; complex slot -> rows
   // nr + 2 (a - nr) (re) and the next (im)
   T *z = zbuf + doff;
-  for (int g = t; g < nrg; g += blockDim.x) {
+  for (int rg = t; rg < nrg; rg += blockDim.x) {
     T acc[VEC];
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) acc[v] = red[(size_t)g * VEC + v];
+    for (int v = 0; v < VEC; ++v) acc[v] = red[(size_t)rg * VEC + v];
     for (int k = 1; k < G; ++k)
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) acc[v] += red[((size_t)k * nrg + g) * VEC + v];
+      for (int v = 0; v < VEC; ++v) acc[v] += red[((size_t)k * nrg + rg) * VEC + v];
     if (!cplx) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v)
-        if (VEC * g + v < Cs) z[(size_t)a * Cs + VEC * g + v] = acc[v];
+        if (VEC * rg + v < Cs) z[(size_t)a * Cs + VEC * rg + v] = acc[v];
     } else {
       const int row = nr + 2 * (a - nr);
 #pragma unroll
       for (int i = 0; i < CR; ++i)
-        if (CR * g + i < Cs) {
-          z[(size_t)row * Cs + CR * g + i] = acc[2 * i];
-          z[(size_t)(row + 1) * Cs + CR * g + i] = acc[2 * i + 1];
+        if (CR * rg + i < Cs) {
+          z[(size_t)row * Cs + CR * rg + i] = acc[2 * i];
+          z[(size_t)(row + 1) * Cs + CR * rg + i] = acc[2 * i + 1];
         }
     }
   }
