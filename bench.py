@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--sweeps", type=int, default=1, help="pre- and post-smoothing sweeps per level")
     p.add_argument("--requests", type=int, default=64, help="requests of the serving workload")
     p.add_argument("--workers", type=int, default=8, help="concurrent requests of the serving workload")
+    p.add_argument("--batched", action="store_true",
+                   help="serving: lockstep groups with fused smoother launches (continuous batching)")
+    p.add_argument("--members", type=int, default=16, help="serving, batched: most members of a group")
     p.add_argument("--rhs", type=int, default=1,
                    help="right-hand sides solved together (marches from t0 = 0, 0.1, ...): >1 times the "
                         "batched path with the tensor-core patch apply")
@@ -697,7 +700,7 @@ def serving_arm(args):
     probs = [gpu_problem(c) for c in reqs]
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    S = st.Server(hbm_budget=budget, n_workers=args.workers)
+    S = st.Server(hbm_budget=budget, n_workers=args.workers, batched=args.batched, max_members=args.members)
     t0 = time.perf_counter()
     ids = []
     for p, c in zip(probs, reqs):
@@ -719,7 +722,9 @@ def serving_arm(args):
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving stream: %d 2D requests, Poisson arrivals (mean 2 ms), meshes "
                                "{16,32,64,128}^2, (Q2/Q1,k=1) or (Q3/Q2,k=2), 5-50 slabs, random materials; "
-                               "%d workers, HBM budget %.0f GB" % (len(reqs), args.workers, budget / 1e9)},
+                               "%d workers, HBM budget %.0f GB" % (len(reqs), args.workers, budget / 1e9),
+                   "mode": ("batched: lockstep groups of up to %d requests per class with fused smoother "
+                            "launches" % args.members) if args.batched else "independent: one march per worker"},
         "requests": len(reqs), "slabs": slabs, "makespan_s": makespan,
         "request_latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
         "slab_latency_ms": {"p50": pct(slab_ms, 50), "p99": pct(slab_ms, 99)},

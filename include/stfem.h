@@ -451,6 +451,14 @@ typedef struct {
 
 /* n_workers concurrent requests at most; hbm_budget bytes of footprint. */
 int stfem_server_create(long long hbm_budget, int n_workers, stfem_server *out);
+/* Batched mode (continuous batching): n_workers threads set requests up
+ * (admitted as above); a stepper thread per class of requests (temporal
+ * degree, precision) keeps up to max_members of them resident in a group
+ * (stfem_group_*) and advances them in lockstep, the patch applies of each
+ * V-cycle stage of all members in one fused launch; a request joins between
+ * two steps as soon as its setup is done and a place is free, and leaves
+ * when its march ends.  Results are bitwise those of the request run alone. */
+int stfem_server_create_batched(long long hbm_budget, int n_workers, int max_members, stfem_server *out);
 /* Queues a request; *id identifies it.  STFEM_ERR_ARG if its footprint
  * estimate exceeds the whole budget. */
 int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id);
@@ -462,6 +470,45 @@ int stfem_server_result(stfem_server s, long long id, double timeout_s, stfem_re
                         double *end_state_host, double *slab_ms_host);
 /* Waits for all requests, stops the workers and frees everything. */
 void stfem_server_destroy(stfem_server s);
+
+/* ---- Groups of handles advanced together ----
+ * No counterpart in the paper: the batching side of serving.  Handles of
+ * different problems (meshes, spatial degrees, materials, time steps) with
+ * the same temporal degree and precision march in lockstep: every
+ * stfem_group_step advances every member by one FGMRES-GMG step (the start of
+ * a slab, one iteration, or the end of a restart cycle), and the patch
+ * applies of each V-cycle stage (Algorithm 4.1's local solves) of all members
+ * run as one launch of the persistent smoother kernel over a table of the
+ * members' levels (uneven sizes packed together; launch shapes tuned on the
+ * first use of each kind of stage, which never changes a result).  A member's
+ * other kernels run on its own stream (stfem_set_stream; members should have
+ * distinct non-default streams) and the fused launch on the group's stream
+ * between events, so members still overlap.  Each member marches exactly as
+ * march() would: the same kernels in the same order, so its results are the
+ * same as alone.  Host memory of the group is owned by it; the handles and
+ * the state vectors stay the caller's and must outlive their membership. */
+typedef struct stfem_group_ctx *stfem_group;
+int stfem_group_create(stfem_group *out);
+/* Adds a march of n_slabs slabs from slab first_slab for handle h, starting
+ * from and updating `state` (device, n_state), with the solve parameters of
+ * march().  *member identifies it.  STFEM_ERR_ARG if the handle is already a
+ * live member or differs from the live members in temporal degree or
+ * precision. */
+int stfem_group_add(stfem_group g, stfem_h h, int first_slab, int n_slabs, double *state, double tol, int restart,
+                    int max_it, long long *member);
+/* One step of every live member; *n_active: members still marching. */
+int stfem_group_step(stfem_group g, int *n_active);
+/* *done, *status (worst slab status, as march() returns), and per finished
+ * slab the FGMRES iterations and the host time of the slab solve in ms
+ * (host arrays of at least n_slabs entries, may be NULL). */
+int stfem_group_member(stfem_group g, long long member, int *done, int *status, int *iters_host,
+                       double *slab_ms_host);
+/* Removes a member (after it is done, or to abandon it). */
+int stfem_group_remove(stfem_group g, long long member);
+/* Fused patch-apply launches so far and the levels they held. */
+int stfem_group_stats(stfem_group g, long long *fused_launches, long long *fused_jobs);
+const char *stfem_group_last_error(stfem_group g);
+void stfem_group_destroy(stfem_group g);
 
 /* ---- Allocation-free smoothing ----
  * No counterpart in the paper: an entry point for callers that cannot call

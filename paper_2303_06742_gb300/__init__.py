@@ -132,9 +132,16 @@ def _load():
         "stfem_footprint_bytes": [P, pLL],
         "stfem_estimate_bytes": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(GmgParams), I, pLL],
         "stfem_server_create": [LL, I, C.POINTER(P)],
+        "stfem_server_create_batched": [LL, I, I, C.POINTER(P)],
         "stfem_server_submit": [P, C.POINTER(Request), pLL],
         "stfem_server_result": [P, LL, D, C.POINTER(Result), pD, pD],
         "stfem_profile_read": [P, I, pLL, pD, pD, pD],
+        "stfem_group_create": [C.POINTER(P)],
+        "stfem_group_add": [P, P, I, I, P, D, I, I, pLL],
+        "stfem_group_step": [P, pI],
+        "stfem_group_member": [P, LL, pI, pI, pI, pD],
+        "stfem_group_remove": [P, LL],
+        "stfem_group_stats": [P, pLL, pLL],
         "stfem_launch_count": [P, pLL],
     }
     for name, args in sig.items():
@@ -149,6 +156,10 @@ def _load():
     lib.stfem_destroy.restype = None
     lib.stfem_server_destroy.argtypes = [P]
     lib.stfem_server_destroy.restype = None
+    lib.stfem_group_destroy.argtypes = [P]
+    lib.stfem_group_destroy.restype = None
+    lib.stfem_group_last_error.argtypes = [P]
+    lib.stfem_group_last_error.restype = C.c_char_p
     return lib
 
 
@@ -451,13 +462,83 @@ def estimate_bytes(prob, precision=FP64, patch_form=PATCH_AUTO, restart=30, n_sw
     return n.value
 
 
+class Group:
+    """Handles advanced in lockstep with fused patch-apply launches
+    (stfem_group_*): each member marches as Solver.march would."""
+
+    def __init__(self):
+        g = C.c_void_p()
+        rc = lib.stfem_group_create(C.byref(g))
+        if rc < 0:
+            raise StfemError(rc, "group creation failed")
+        self.g = g
+        self._keep = {}
+
+    def _check(self, rc):
+        if rc < 0:
+            raise StfemError(rc, lib.stfem_group_last_error(self.g).decode())
+        return rc
+
+    def add(self, solver, first_slab, n_slabs, state, tol=1e-8, restart=30, max_it=500):
+        mid = C.c_longlong()
+        self._check(lib.stfem_group_add(self.g, solver.h, first_slab, n_slabs, _ptr(state), tol, restart, max_it,
+                                        C.byref(mid)))
+        self._keep[mid.value] = (solver, state, n_slabs)
+        return mid.value
+
+    def step(self):
+        n = C.c_int()
+        self._check(lib.stfem_group_step(self.g, C.byref(n)))
+        return n.value
+
+    def run(self):
+        steps = 0
+        while self.step() > 0:
+            steps += 1
+        return steps
+
+    def member(self, mid):
+        """(done, status, per-slab iterations, per-slab ms)."""
+        n_slabs = self._keep[mid][2]
+        done, status = C.c_int(), C.c_int()
+        it = (C.c_int * max(n_slabs, 1))()
+        ms = (C.c_double * max(n_slabs, 1))()
+        self._check(lib.stfem_group_member(self.g, mid, C.byref(done), C.byref(status), it, ms))
+        return bool(done.value), status.value, list(it)[:n_slabs], list(ms)[:n_slabs]
+
+    def remove(self, mid):
+        self._check(lib.stfem_group_remove(self.g, mid))
+        self._keep.pop(mid, None)
+
+    def stats(self):
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(lib.stfem_group_stats(self.g, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "g", None):
+            lib.stfem_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """The serving loop: requests (marches) admitted by HBM footprint and run
     concurrently by `n_workers` threads, each with its own handle and stream."""
 
-    def __init__(self, hbm_budget, n_workers):
+    def __init__(self, hbm_budget, n_workers, batched=False, max_members=8):
+        """batched: set-up workers hand requests to lockstep groups with fused
+        smoother launches (stfem_server_create_batched)."""
         s = C.c_void_p()
-        rc = lib.stfem_server_create(int(hbm_budget), int(n_workers), C.byref(s))
+        if batched:
+            rc = lib.stfem_server_create_batched(int(hbm_budget), int(n_workers), int(max_members), C.byref(s))
+        else:
+            rc = lib.stfem_server_create(int(hbm_budget), int(n_workers), C.byref(s))
         if rc < 0:
             raise StfemError(rc, "server creation failed")
         self.s = s

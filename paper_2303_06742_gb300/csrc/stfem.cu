@@ -24,7 +24,12 @@
 #include <string>
 #include <type_traits>
 #include <climits>
+#include <array>
+#include <chrono>
 #include <future>
+#include <map>
+#include <memory>
+#include <tuple>
 #include <vector>
 
 using namespace stfem_dev;
@@ -115,27 +120,49 @@ constexpr long long STREAM_WAIT_LIMIT = 4000000000LL;
 // shared-memory bytes before the per-patch vectors: the ring, the barriers
 __host__ __device__ constexpr int stream_header(int nst) { return nst * STREAM_CHUNK + 2 * STREAM_STAGES * 8 + 16; }
 
+// Patch sets processed by one launch of a patch-apply kernel: `njobs` levels
+// (of one handle, or of several handles that advance together), job j holding
+// the global patches [first[j], first[j + 1]).  Passed by value
+// (__grid_constant__): the launch carries it, so a captured graph replays it.
+// All jobs have the same number of time nodes (hence the same slot structure
+// nr, nc); their U, V factors may differ (they depend on tau).
+template <typename T, int MAXJ>
+struct PatchJobs {
+  int njobs;
+  long first[MAXJ + 1];
+  const int *pcs[MAXJ];
+  const long long *pdoff[MAXJ];
+  const int *pdofs[MAXJ];
+  const long long *pioff[MAXJ];
+  const T *pinv[MAXJ];
+  const T *res[MAXJ];
+  T *y[MAXJ];
+  T *zbuf[MAXJ];  // wide kernel: slot results
+  int *ticket[MAXJ];
+  DiagCoef<T> dc[MAXJ];
+};
+constexpr int MAXJOBS = 16; // levels one fused launch takes
+
 // Time-diagonal patch apply (see k_patch_apply_diag) with the inverse blocks
-// streamed by bulk copies.  Persistent CTAs take patches p = blockIdx.x,
-// blockIdx.x + gridDim.x, ...  The last warp is the producer: one lane walks
-// the (patch, slot, column chunk) sequence and copies each chunk (contiguous,
-// 16-byte aligned, a multiple of 16 bytes) into a ring of nst <= STREAM_STAGES
-// shared stages.  The other warps gather and mix the residual, consume the
-// chunks of their slot rows from shared memory, and mix the result back.
+// streamed by bulk copies.  Persistent CTAs take tiles of `tile` consecutive
+// patches: patches b * tile .. b * tile + tile - 1, then the same plus
+// gridDim.x * tile, ... over the patches of all jobs (so one launch may serve
+// the levels of several handles).  The last warp is the producer: one lane
+// walks the (patch, slot, column chunk) sequence and copies each chunk
+// (contiguous, 16-byte aligned, a multiple of 16 bytes) into a ring of
+// nst <= STREAM_STAGES shared stages.  The other warps gather and mix the
+// residual, consume the chunks of their slot rows from shared memory, and mix
+// the result back.  A patch's arithmetic does not depend on the CTA, the tile
+// or the other jobs of the launch.
 // Every wait is bounded by `wait` clock cycles; on a timeout the CTA sets
 // *err, the producer waits (bounded by STREAM_WAIT_LIMIT) for its copies still
 // in flight, and the CTA returns.  stall != 0 makes the producer issue no copy
 // at all, so that every consumer's first wait runs out (the failure-detection
 // test of the bounded waits: nothing is in flight when the CTA leaves).
-template <typename T, int Q>
-__global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const int *__restrict__ pcs,
-                                                             const long long *__restrict__ pdoff,
-                                                             const int *__restrict__ pdofs,
-                                                             const long long *__restrict__ pioff,
-                                                             const T *__restrict__ pinv, const T *__restrict__ res,
-                                                             T *__restrict__ y, DiagCoef<T> dc, int maxCs,
-                                                             int *__restrict__ err, int nst, long long wait,
-                                                             int stall) {
+template <typename T, int Q, int MAXJ>
+__global__ void __launch_bounds__(1024) k_patch_apply_stream(const __grid_constant__ PatchJobs<T, MAXJ> J, int maxCs,
+                                                             int tile, int *__restrict__ err, int nst,
+                                                             long long wait, int stall) {
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
@@ -144,7 +171,8 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_stream + nst * STREAM_CHUNK);
   uint64_t *empty = full + STREAM_STAGES;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + STREAM_STAGES);
-  const int nr = dc.nr, nc = dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
+  const int nr = J.dc[0].nr, nc = J.dc[0].nc, ns = nr + nc, nrow = nr + 2 * nc;
+  const long npatch = J.first[J.njobs];
   T *rs = reinterpret_cast<T *>(smem_stream + stream_header(nst));
   T *rt = rs + (size_t)Q * maxCs;
   T *z = rt + (size_t)nrow * maxCs;
@@ -160,37 +188,44 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  const long step = (long)gridDim.x * tile;
 
   if (warp == nwc) {
     // ---------------- producer
     if (lane != 0 || stall) return;
     long long it = 0;
     bool ok = true;
-    for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
-      const int Cs = pcs[p];
-      const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
-      const T *base = pinv + pioff[p];
-      for (int sl = 0; sl < ns && ok; ++sl) {
-        const int ld = sl < nr ? ldR : ldC;
-        const T *sb = base + (sl < nr ? (size_t)sl * Cs * ldR : (size_t)nr * Cs * ldR + (size_t)(sl - nr) * Cs * ldC);
-        const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
-        for (int j0 = 0; j0 < Cs; j0 += K) {
-          const int st = (int)(it % nst);
-          if (it >= nst && !mbar_wait(&empty[st], (uint32_t)(((it / nst) - 1) & 1), wait)) {
-            ok = false;
-            break;
+    int j = 0;
+    for (long b = (long)blockIdx.x * tile; b < npatch && ok; b += step)
+      for (long p = b; p < b + tile && p < npatch && ok; ++p) {
+        if (MAXJ > 1)
+          while (p >= J.first[j + 1]) ++j;
+        const long lp = p - J.first[j];
+        const int Cs = J.pcs[j][lp];
+        const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+        const T *base = J.pinv[j] + J.pioff[j][lp];
+        for (int sl = 0; sl < ns && ok; ++sl) {
+          const int ld = sl < nr ? ldR : ldC;
+          const T *sb =
+              base + (sl < nr ? (size_t)sl * Cs * ldR : (size_t)nr * Cs * ldR + (size_t)(sl - nr) * Cs * ldC);
+          const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
+          for (int j0 = 0; j0 < Cs; j0 += K) {
+            const int st = (int)(it % nst);
+            if (it >= nst && !mbar_wait(&empty[st], (uint32_t)(((it / nst) - 1) & 1), wait)) {
+              ok = false;
+              break;
+            }
+            if (*abort_flag) {
+              ok = false;
+              break;
+            }
+            const uint32_t bytes = (uint32_t)(min(K, Cs - j0) * ld * (int)sizeof(T));
+            mbar_arrive_expect_tx(&full[st], bytes);
+            bulk_copy_g2s(stage + (size_t)st * STREAM_CHUNK, sb + (size_t)j0 * ld, bytes, &full[st]);
+            ++it;
           }
-          if (*abort_flag) {
-            ok = false;
-            break;
-          }
-          const uint32_t bytes = (uint32_t)(min(K, Cs - j0) * ld * (int)sizeof(T));
-          mbar_arrive_expect_tx(&full[st], bytes);
-          bulk_copy_g2s(stage + (size_t)st * STREAM_CHUNK, sb + (size_t)j0 * ld, bytes, &full[st]);
-          ++it;
         }
       }
-    }
     if (!ok) {
       atomicExch(err, 1);
       *abort_flag = 1;
@@ -204,112 +239,121 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(int npatch, const i
   // ---------------- consumers (threads 0 .. nct-1)
   const int tid = threadIdx.x;
   long long it = 0;
-  for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
-    // all consumers pass the same barriers, so they all see the flag and
-    // leave together (no barrier is left waiting)
-    consumer_sync(nct);
-    if (*abort_flag) return;
-    const int Cs = pcs[p], C = Q * Cs;
-    const long long doff = pdoff[p];
-    for (int j = tid; j < C; j += nct) rs[j] = res[pdofs[doff + j]];
-    consumer_sync(nct);
-    for (int m = tid; m < Cs; m += nct) {
-      for (int a = 0; a < ns; ++a) {
-        T re = T(0), im = T(0);
+  int j = 0;
+  for (long b = (long)blockIdx.x * tile; b < npatch; b += step)
+    for (long p = b; p < b + tile && p < npatch; ++p) {
+      // all consumers pass the same barriers, so they all see the flag and
+      // leave together (no barrier is left waiting)
+      consumer_sync(nct);
+      if (*abort_flag) return;
+      if (MAXJ > 1) // one job: j stays 0 and the factors are launch constants
+        while (p >= J.first[j + 1]) ++j;
+      const long lp = p - J.first[j];
+      const DiagCoef<T> &dc = J.dc[j];
+      const int Cs = J.pcs[j][lp], C = Q * Cs;
+      const long long doff = J.pdoff[j][lp];
+      const int *__restrict__ pdofs = J.pdofs[j];
+      const T *__restrict__ res = J.res[j];
+      T *__restrict__ y = J.y[j];
+      for (int jj = tid; jj < C; jj += nct) rs[jj] = res[pdofs[doff + jj]];
+      consumer_sync(nct);
+      for (int m = tid; m < Cs; m += nct) {
+        for (int a = 0; a < ns; ++a) {
+          T re = T(0), im = T(0);
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-          const T r = rs[b * Cs + m];
-          re += dc.U[(a * Q + b) * 2] * r;
-          im += dc.U[(a * Q + b) * 2 + 1] * r;
-        }
-        if (a < nr) {
-          rt[a * Cs + m] = re;
-        } else {
-          rt[(nr + 2 * (a - nr)) * Cs + m] = re;
-          rt[(nr + 2 * (a - nr) + 1) * Cs + m] = im;
+          for (int bq = 0; bq < Q; ++bq) {
+            const T r = rs[bq * Cs + m];
+            re += dc.U[(a * Q + bq) * 2] * r;
+            im += dc.U[(a * Q + bq) * 2 + 1] * r;
+          }
+          if (a < nr) {
+            rt[a * Cs + m] = re;
+          } else {
+            rt[(nr + 2 * (a - nr)) * Cs + m] = re;
+            rt[(nr + 2 * (a - nr) + 1) * Cs + m] = im;
+          }
         }
       }
-    }
-    consumer_sync(nct);
-    const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
-    const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
-    int role = -1, slot = 0, m0 = 0;
-    if (tid < nr * nRr) {
-      role = 0;
-      slot = tid / nRr;
-      m0 = VEC * (tid % nRr);
-    } else if (tid < nr * nRr + nc * nCr) {
-      role = 1;
-      const int t2 = tid - nr * nRr;
-      slot = t2 / nCr;
-      m0 = CR * (t2 % nCr);
-    }
-    T vals[VEC];
+      consumer_sync(nct);
+      const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
+      const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
+      int role = -1, slot = 0, m0 = 0;
+      if (tid < nr * nRr) {
+        role = 0;
+        slot = tid / nRr;
+        m0 = VEC * (tid % nRr);
+      } else if (tid < nr * nRr + nc * nCr) {
+        role = 1;
+        const int t2 = tid - nr * nRr;
+        slot = t2 / nCr;
+        m0 = CR * (t2 % nCr);
+      }
+      T vals[VEC];
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) vals[v] = T(0);
-    for (int sl = 0; sl < ns; ++sl) {
-      const int ld = sl < nr ? ldR : ldC;
-      const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
-      for (int j0 = 0; j0 < Cs; j0 += K) {
-        const int st = (int)(it % nst);
-        bool ready = !*abort_flag;
-        if (ready && !mbar_wait(&full[st], (uint32_t)((it / nst) & 1), wait)) {
-          atomicExch(err, 2);
-          *abort_flag = 1;
-          ready = false;
-        }
-        const int ncol = ready ? min(K, Cs - j0) : 0;
-        const T *sbuf = reinterpret_cast<const T *>(stage + (size_t)st * STREAM_CHUNK);
-        if (sl < nr) {
-          if (role == 0 && slot == sl) {
-            const T *x = rt + sl * Cs + j0;
-            for (int j = 0; j < ncol; ++j)
-              fma_vec<T>(vals, *reinterpret_cast<const Vv *>(sbuf + (size_t)j * ld + m0), x[j]);
+      for (int v = 0; v < VEC; ++v) vals[v] = T(0);
+      for (int sl = 0; sl < ns; ++sl) {
+        const int ld = sl < nr ? ldR : ldC;
+        const int K = max(1, STREAM_CHUNK / (ld * (int)sizeof(T)));
+        for (int j0 = 0; j0 < Cs; j0 += K) {
+          const int st = (int)(it % nst);
+          bool ready = !*abort_flag;
+          if (ready && !mbar_wait(&full[st], (uint32_t)((it / nst) & 1), wait)) {
+            atomicExch(err, 2);
+            *abort_flag = 1;
+            ready = false;
           }
-        } else if (role == 1 && slot == sl - nr) {
-          const T *xr = rt + (nr + 2 * slot) * Cs + j0, *xi = xr + Cs;
-          for (int j = 0; j < ncol; ++j) {
-            const Vv a = *reinterpret_cast<const Vv *>(sbuf + (size_t)j * ld + 2 * m0);
-            const T *av = reinterpret_cast<const T *>(&a);
-            const T ar = xr[j], ai = xi[j];
+          const int ncol = ready ? min(K, Cs - j0) : 0;
+          const T *sbuf = reinterpret_cast<const T *>(stage + (size_t)st * STREAM_CHUNK);
+          if (sl < nr) {
+            if (role == 0 && slot == sl) {
+              const T *x = rt + sl * Cs + j0;
+              for (int jc = 0; jc < ncol; ++jc)
+                fma_vec<T>(vals, *reinterpret_cast<const Vv *>(sbuf + (size_t)jc * ld + m0), x[jc]);
+            }
+          } else if (role == 1 && slot == sl - nr) {
+            const T *xr = rt + (nr + 2 * slot) * Cs + j0, *xi = xr + Cs;
+            for (int jc = 0; jc < ncol; ++jc) {
+              const Vv a = *reinterpret_cast<const Vv *>(sbuf + (size_t)jc * ld + 2 * m0);
+              const T *av = reinterpret_cast<const T *>(&a);
+              const T ar = xr[jc], ai = xi[jc];
 #pragma unroll
-            for (int i = 0; i < CR; ++i) {
-              vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
-              vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+              for (int i = 0; i < CR; ++i) {
+                vals[2 * i] += av[2 * i] * ar - av[2 * i + 1] * ai;
+                vals[2 * i + 1] += av[2 * i] * ai + av[2 * i + 1] * ar;
+              }
             }
           }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[st]);
+          ++it;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
-        ++it;
       }
-    }
-    if (role == 0) {
+      if (role == 0) {
 #pragma unroll
-      for (int v = 0; v < VEC; ++v)
-        if (m0 + v < Cs) z[slot * Cs + m0 + v] = vals[v];
-    } else if (role == 1) {
+        for (int v = 0; v < VEC; ++v)
+          if (m0 + v < Cs) z[slot * Cs + m0 + v] = vals[v];
+      } else if (role == 1) {
 #pragma unroll
-      for (int i = 0; i < CR; ++i)
-        if (m0 + i < Cs) {
-          z[(nr + 2 * slot) * Cs + m0 + i] = vals[2 * i];
-          z[(nr + 2 * slot + 1) * Cs + m0 + i] = vals[2 * i + 1];
+        for (int i = 0; i < CR; ++i)
+          if (m0 + i < Cs) {
+            z[(nr + 2 * slot) * Cs + m0 + i] = vals[2 * i];
+            z[(nr + 2 * slot + 1) * Cs + m0 + i] = vals[2 * i + 1];
+          }
+      }
+      consumer_sync(nct);
+      for (int idx = tid; idx < C; idx += nct) {
+        const int bq = idx / Cs, m = idx - bq * Cs;
+        T val = T(0);
+        for (int a = 0; a < nr; ++a) val += dc.V[(bq * ns + a) * 2] * z[a * Cs + m];
+        for (int c = 0; c < nc; ++c) {
+          const int a = nr + c;
+          val += T(2) * (dc.V[(bq * ns + a) * 2] * z[(nr + 2 * c) * Cs + m] -
+                         dc.V[(bq * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
         }
-    }
-    consumer_sync(nct);
-    for (int idx = tid; idx < C; idx += nct) {
-      const int b = idx / Cs, m = idx - b * Cs;
-      T val = T(0);
-      for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * z[a * Cs + m];
-      for (int c = 0; c < nc; ++c) {
-        const int a = nr + c;
-        val += T(2) * (dc.V[(b * ns + a) * 2] * z[(nr + 2 * c) * Cs + m] -
-                       dc.V[(b * ns + a) * 2 + 1] * z[(nr + 2 * c + 1) * Cs + m]);
+        y[doff + idx] = val;
       }
-      y[doff + idx] = val;
+      consumer_sync(nct);
     }
-    consumer_sync(nct);
-  }
 }
 
 #include "tc_patch.cuh"
@@ -354,7 +398,7 @@ struct DLevel {
   int tc = 0, tc_nst = 0;
   // ring shape of the streaming patch apply picked by autotune_stream (0: by
   // dimension)
-  int tune_nst = 0, tune_cap = 0;
+  int tune_nst = 0, tune_cap = 0, tune_tile = 0;
   // levels with few patches use k_patch_apply_wide: its slot results (sumC
   // per column) and per-patch ticket counters
   int wide = 0;
@@ -392,6 +436,8 @@ struct stfem_ctx {
   // it reports a timeout; stall_copies != 0 makes its producer issue no copy
   long long wait_cycles = 4000000000LL;
   int stall_copies = 0;
+  // recorded on the handle's stream before a fused launch of a group
+  cudaEvent_t grp_ev = nullptr;
   // patch-apply kernel of the time-diagonal levels (STFEM_PATCH_KERNEL_*)
   int patch_kernel = 0;
   // operator of the finest FP32 level (STFEM_OPERATOR_*)
@@ -1715,22 +1761,47 @@ void stream_shape(stfem_h h, const DLevel<T> &L, int *threads, size_t *smem, int
   if (h->launch_cap > 0) *grid = std::min(*grid, h->launch_cap);
 }
 
+// Appends a level's patches (input res, results y; slot results zb and
+// tickets tk for the wide kernel) to a job table.
+template <typename T, int MAXJ>
+void add_job(PatchJobs<T, MAXJ> &J, const DLevel<T> &L, const T *res, T *y, T *zb = nullptr, int *tk = nullptr) {
+  const int j = J.njobs++;
+  if (j == 0) J.first[0] = 0;
+  J.first[j + 1] = J.first[j] + L.npatch;
+  J.pcs[j] = L.pcs;
+  J.pdoff[j] = L.pdoff;
+  J.pdofs[j] = L.pdofs;
+  J.pioff[j] = L.pioff;
+  J.pinv[j] = L.pinv;
+  J.res[j] = res;
+  J.y[j] = y;
+  J.zbuf[j] = zb;
+  J.ticket[j] = tk;
+  J.dc[j] = L.dc;
+}
+
 template <typename T, int Q>
 void launch_patch_stream_q(stfem_h h, DLevel<T> &L, const T *res, T *y) {
   int threads, grid, nst;
   size_t smem;
   stream_shape(h, L, &threads, &smem, &grid, &nst);
-  k_patch_apply_stream<T, Q><<<grid, threads, smem, h->stream>>>((int)L.npatch, L.pcs, L.pdoff, L.pdofs, L.pioff,
-                                                                 L.pinv, res, y, L.dc, L.maxCs, h->dev_err, nst,
-                                                                 h->wait_cycles, h->stall_copies);
+  PatchJobs<T, 1> J;
+  J.njobs = 0;
+  add_job(J, L, res, y);
+  const int tile = L.tune_tile > 0 ? L.tune_tile : 1;
+  grid = std::max(1, std::min<int>(grid, (int)((L.npatch + tile - 1) / tile)));
+  k_patch_apply_stream<T, Q, 1><<<grid, threads, smem, h->stream>>>(J, L.maxCs, tile, h->dev_err, nst,
+                                                                    h->wait_cycles, h->stall_copies);
 }
 
 template <typename T, int Q>
 void launch_patch_wide_q(stfem_h h, DLevel<T> &L, const T *res, T *y, T *zb, int *tk) {
   const size_t smem = wide_smem<T>(L, Q);
   const int ns = L.dc.nr + L.dc.nc;
-  k_patch_apply_wide<T, Q><<<(unsigned)(L.npatch * ns), WIDE_THREADS, smem, h->stream>>>(
-      L.pcs, L.pdoff, L.pdofs, L.pioff, L.pinv, res, y, zb, tk, L.dc);
+  PatchJobs<T, 1> J;
+  J.njobs = 0;
+  add_job(J, L, res, y, zb, tk);
+  k_patch_apply_wide<T, Q, PatchJobs<T, 1>><<<(unsigned)(L.npatch * ns), WIDE_THREADS, smem, h->stream>>>(J);
 }
 
 // zb, tk: slot results and ticket counters of the wide kernel (nullptr: the
@@ -1798,14 +1869,19 @@ void launch_patch_apply_to(stfem_h h, DLevel<T> &L, const T *res, T *y, T *zb = 
 // setup, never during a graph capture).
 int prepare_stream_kernels(stfem_h h) {
 #define STFEM_SMEM_ATTR(T, Q)                                                                            \
-  CK(cudaFuncSetAttribute(k_patch_apply_stream<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
+  CK(cudaFuncSetAttribute(k_patch_apply_stream<T, Q, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)); \
+  CK(cudaFuncSetAttribute(k_patch_apply_stream<T, Q, MAXJOBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                          227 * 1024))
   STFEM_SMEM_ATTR(float, 1); STFEM_SMEM_ATTR(float, 2); STFEM_SMEM_ATTR(float, 3);
   STFEM_SMEM_ATTR(float, 4); STFEM_SMEM_ATTR(float, 5);
   STFEM_SMEM_ATTR(double, 1); STFEM_SMEM_ATTR(double, 2); STFEM_SMEM_ATTR(double, 3);
   STFEM_SMEM_ATTR(double, 4); STFEM_SMEM_ATTR(double, 5);
 #undef STFEM_SMEM_ATTR
 #define STFEM_SMEM_ATTR_W(T, Q)                                                                          \
-  CK(cudaFuncSetAttribute(k_patch_apply_wide<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
+  CK(cudaFuncSetAttribute(k_patch_apply_wide<T, Q, PatchJobs<T, 1>>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                          227 * 1024));                                                                        \
+  CK(cudaFuncSetAttribute(k_patch_apply_wide<T, Q, PatchJobs<T, MAXJOBS>>,                                     \
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))
   STFEM_SMEM_ATTR_W(float, 1); STFEM_SMEM_ATTR_W(float, 2); STFEM_SMEM_ATTR_W(float, 3);
   STFEM_SMEM_ATTR_W(float, 4); STFEM_SMEM_ATTR_W(float, 5);
   STFEM_SMEM_ATTR_W(double, 1); STFEM_SMEM_ATTR_W(double, 2); STFEM_SMEM_ATTR_W(double, 3);
@@ -1824,10 +1900,6 @@ int prepare_stream_kernels(stfem_h h) {
   return 0;
 }
 
-// Autotuner of the streaming patch apply: times the candidate ring shapes
-// (stages per CTA x CTAs per SM) on the level's own inverses and keeps the
-// fastest.  The shape changes only how patches are spread over CTAs, never
-// the arithmetic of a patch, so results do not depend on the choice.
 template <typename T>
 int prepare_wide(stfem_h h, DLevel<T> &L) {
   L.wide = wide_chosen(L, h->nsm, h->patch_kernel) ? 1 : 0;
@@ -1838,10 +1910,15 @@ int prepare_wide(stfem_h h, DLevel<T> &L) {
   return 0;
 }
 
+// Autotuner of the streaming patch apply: times the candidate ring shapes
+// (stages per CTA x CTAs per SM) and patch tiles (consecutive patches a CTA
+// takes per step) on the level's own inverses and keeps the fastest.  The
+// shape and the tile change only how patches are spread over CTAs, never the
+// arithmetic of a patch, so results do not depend on the choice.
 template <typename T>
 int autotune_stream(stfem_h h, DLevel<T> &L) {
   if (L.form != 1 || L.tc || L.wide || L.npatch == 0) return 0;
-  static const int cand[][2] = {{2, 5}, {3, 4}, {4, 3}};
+  static const int cand[][3] = {{2, 5, 1}, {3, 4, 1}, {4, 3, 1}, {2, 5, 2}, {4, 3, 2}, {4, 3, 4}};
   cudaStream_t ts = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
@@ -1851,10 +1928,11 @@ int autotune_stream(stfem_h h, DLevel<T> &L) {
   h->stream = ts;
   cudaMemsetAsync(L.r, 0, (size_t)L.N * sizeof(T), ts);
   float best = 1e30f;
-  int bn = 0, bc = 0;
+  int bn = 0, bc = 0, bt = 0;
   for (const auto &c : cand) {
     L.tune_nst = c[0];
     L.tune_cap = c[1];
+    L.tune_tile = c[2];
     int threads, grid, nst;
     size_t smem;
     stream_shape(h, L, &threads, &smem, &grid, &nst);
@@ -1870,11 +1948,13 @@ int autotune_stream(stfem_h h, DLevel<T> &L) {
       best = ms;
       bn = c[0];
       bc = c[1];
+      bt = c[2];
     }
   }
   h->stream = saved;
   L.tune_nst = bn;
   L.tune_cap = bc;
+  L.tune_tile = bt;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const cudaError_t e = cudaStreamSynchronize(ts);
@@ -2148,33 +2228,53 @@ int ensure_workspace(stfem_h h, int m) {
   return 0;
 }
 
-// All work of FGMRES iteration j (Sec. 4): z_j = M^{-1} v_j (one V-cycle),
-// w = A z_j, classical Gram-Schmidt twice, Givens update, copy of the status
+// The two halves of FGMRES iteration j around its V-cycle.  iter_pre: the
+// V-cycle input v_j in the GMG precision.  iter_post: z_j = the V-cycle
+// output kept for the solution update, w = A z_j, classical Gram-Schmidt
+// twice (h1 = V^T w; w -= V h1 and h2 = V^T w in one pass; w -= V h2 and
+// ||w||^2 in one pass), the Givens update, a copy of the status
 // {|g_{j+1}|, h_{j+1,j}} to pinned host memory, and v_{j+1} = w / h_{j+1,j}
-// (unused when the host stops at j).  Only stream-ordered work: it can be
-// captured into a graph.
-int enqueue_iteration(stfem_h h, int j, int m1) {
+// (unused when the host stops at j).
+int iter_pre(stfem_h h, int j) {
+  const int L = h->nlev - 1;
+  const long N = h->L64.back().N;
+  const double *vj = h->V + (long)j * N;
+  cudaStream_t s = h->stream;
+  if (h->precision == STFEM_FP64) {
+    CK(cudaMemcpyAsync(h->L64[L].b, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0, 0.0);
+    k_convert<double, float><<<grid_for(N, 256), 256, 0, s>>>(N, vj, h->L32[L].b);
+  }
+  return 0;
+}
+
+int iter_post(stfem_h h, int j, int m1) {
   DLevel<double> &F = h->L64.back();
   const long N = F.N;
+  const int L = h->nlev - 1;
   const TimeCoef<double> tc = time_coef<double>(h->T, h->tau);
   cudaStream_t s = h->stream;
   const int nb = grid_for(N, 256);
-  double *vj = h->V + (long)j * N;
   double *w = h->w;
   if (h->precision == STFEM_FP64) {
     double *zj = h->Zd + (long)j * N;
-    CKR(precondition(h, vj, zj, nullptr));
+    CK(cudaMemcpyAsync(zj, h->L64[L].d, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     launch_spmv<double>(h, F, tc, zj, nullptr, w, 0);
-  } else if (F.has_df) {
-    // z_j is the FP32 V-cycle output: exact in FP32, so A z_j in double-float
-    CKR(precondition(h, vj, nullptr, h->Zf + (long)j * N));
-    launch_spmv_df(h, F, tc, h->Zf + (long)j * N, w);
   } else {
-    CKR(precondition(h, vj, h->zt, h->Zf + (long)j * N));
-    launch_spmv<double>(h, F, tc, h->zt, nullptr, w, 0);
+    float *zf = h->Zf + (long)j * N;
+    CK(cudaMemcpyAsync(zf, h->L32[L].d, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (F.has_df) {
+      // z_j is the FP32 V-cycle output: exact in FP32, so A z_j in double-float
+      launch_spmv_df(h, F, tc, zf, w);
+    } else {
+      {
+        Launch G_(h, STFEM_KCLASS_OTHER, N * 12.0, 0.0);
+        k_convert<float, double><<<grid_for(N, 256), 256, 0, s>>>(N, h->L32[L].d, h->zt);
+      }
+      launch_spmv<double>(h, F, tc, h->zt, nullptr, w, 0);
+    }
   }
-  // classical Gram-Schmidt, applied twice: h1 = V^T w; w -= V h1 and
-  // h2 = V^T w in one pass; w -= V h2 and ||w||^2 in one pass
   multidot(h, j + 1, h->V, N, w, N, h->h1);
   axpy_dot(h, j + 1, h->V, N, h->h1, w, N, h->h2, 0);
   axpy_dot(h, j + 1, h->V, N, h->h2, w, N, h->hn2, 1);
@@ -2187,7 +2287,20 @@ int enqueue_iteration(stfem_h h, int j, int m1) {
     Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
     k_div<<<nb, 256, 0, s>>>(N, w, h->V + (long)(j + 1) * N, h->hnorm, 0.0);
   }
+  CK(cudaGetLastError());
   return 0;
+}
+
+// All work of FGMRES iteration j (Sec. 4): z_j = M^{-1} v_j (one V-cycle) and
+// the rest of iter_post.  Only stream-ordered work: it can be captured into a
+// graph.
+int enqueue_iteration(stfem_h h, int j, int m1) {
+  CKR(iter_pre(h, j));
+  if (h->precision == STFEM_FP64)
+    vcycle<double>(h, h->nlev - 1);
+  else
+    vcycle<float>(h, h->nlev - 1);
+  return iter_post(h, j, m1);
 }
 
 // Runs the work enqueue() issues from its captured graph gv[j] (captured on
@@ -3575,7 +3688,592 @@ void stfem_destroy(stfem_h h) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->status_host) cudaFreeHost(h->status_host);
   if (h->bt.host) cudaFreeHost(h->bt.host);
+  if (h->grp_ev) cudaEventDestroy(h->grp_ev);
   delete h;
+}
+
+} // extern "C"
+
+// ============================================================ groups of handles
+// Several handles (problems of different meshes, degrees, materials: uneven
+// instances) advanced in lockstep, one FGMRES step per member per group step,
+// with the patch applies of each V-cycle stage fused across members: one
+// launch of the streaming (or wide) patch kernel takes the patches of every
+// member at that stage from a job table.  Every other kernel of a member runs
+// on the member's own stream, as in the single-handle path; the fused launch
+// runs on the group's stream between events, so members still overlap.  A
+// member's arithmetic is the single-handle path's: the same kernels in the
+// same order, a patch computed the same way in any launch.
+
+namespace {
+
+struct GroupMember {
+  stfem_h h = nullptr;
+  long long id = 0;
+  int first = 0, n_slabs = 0, slab = 0;
+  double *state = nullptr; // device, n_state
+  double tol = 1e-8;
+  int restart = 30, max_it = 500;
+  // FGMRES state of the current slab solve
+  enum Phase { START, INIT, ITER, FIN, DONE } phase = START;
+  int j = 0, it = 0, jlast = -1;
+  double beta0 = 0.0, bound = 0.0, beta = 0.0;
+  int status = STFEM_OK;
+  std::vector<int> iters;
+  std::vector<double> slab_ms;
+  std::chrono::steady_clock::time_point t_slab;
+  cudaEvent_t ev = nullptr;
+};
+
+// Fused launch shapes picked by timing (ring stages, CTAs per SM, patch tile),
+// keyed by the precision, the time nodes, the largest patch and the patch
+// count (in powers of two): the candidates only spread patches differently
+// over CTAs, so the choice never changes a result.
+struct GroupTune {
+  std::map<std::tuple<int, int, int, int>, std::array<int, 3>> shape;
+};
+
+} // namespace
+
+struct stfem_group_ctx {
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  long long next_id = 1;
+  std::vector<std::unique_ptr<GroupMember>> members;
+  GroupTune tune;
+  long long fused_launches = 0, fused_jobs = 0;
+};
+
+namespace {
+
+// Patch applies of one V-cycle stage for a set of (member, level, input)
+// items: time-diagonal levels are fused into job tables (streaming and wide
+// kernels apart, at most MAXJOBS levels per launch); other levels (dense
+// inverses, tensor-core levels) are applied on the member's stream.
+template <typename T, int Q>
+int fused_stage_q(stfem_group g, const std::vector<std::pair<stfem_h, int>> &items, bool use_r) {
+  std::vector<std::pair<stfem_h, int>> stream_items, wide_items;
+  for (const auto &it : items) {
+    DLevel<T> &L = levels<T>(it.first)[it.second];
+    const T *res = use_r ? L.r : L.b;
+    if (L.form == 1 && !L.tc && L.wide)
+      wide_items.push_back(it);
+    else if (L.form == 1 && !L.tc)
+      stream_items.push_back(it);
+    else
+      launch_patch_apply<T>(it.first, L, res);
+  }
+  auto join_in = [&](const std::vector<std::pair<stfem_h, int>> &v, size_t a, size_t b) -> int {
+    for (size_t i = a; i < b; ++i) {
+      stfem_h h = v[i].first;
+      if (cudaEventRecord(h->grp_ev, h->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(g->stream, h->grp_ev, 0) != cudaSuccess) {
+        g->err = "event record/wait failed";
+        return STFEM_ERR_CUDA;
+      }
+    }
+    return 0;
+  };
+  auto join_out = [&](const std::vector<std::pair<stfem_h, int>> &v, size_t a, size_t b) -> int {
+    if (cudaEventRecord(g->ev, g->stream) != cudaSuccess) {
+      g->err = "event record failed";
+      return STFEM_ERR_CUDA;
+    }
+    for (size_t i = a; i < b; ++i)
+      if (cudaStreamWaitEvent(v[i].first->stream, g->ev, 0) != cudaSuccess) {
+        g->err = "stream wait failed";
+        return STFEM_ERR_CUDA;
+      }
+    return 0;
+  };
+  for (size_t a = 0; a < stream_items.size(); a += MAXJOBS) {
+    const size_t b = std::min(stream_items.size(), a + MAXJOBS);
+    PatchJobs<T, MAXJOBS> J;
+    J.njobs = 0;
+    int maxCs = 0, nst = 0, cap = 0, tile = 1;
+    size_t smem = 0;
+    double bytes = 0.0, flops = 0.0;
+    for (size_t i = a; i < b; ++i) {
+      stfem_h h = stream_items[i].first;
+      DLevel<T> &L = levels<T>(h)[stream_items[i].second];
+      add_job(J, L, use_r ? L.r : L.b, L.ybuf);
+      maxCs = std::max(maxCs, L.maxCs);
+      bytes += L.patch_bytes;
+      flops += L.patch_flops;
+      h->launches++;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].launches++;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].bytes += L.patch_bytes;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].flops += L.patch_flops;
+    }
+    const long total = J.first[J.njobs];
+    // launch shape: the largest level's autotuned ring, or the group's own
+    // tuning of this kind of stage
+    stfem_h h0 = stream_items[a].first;
+    const int dim = h0->dim;
+    constexpr int VEC = Vec16<T>::n;
+    int rows = 0;
+    for (size_t i = a; i < b; ++i) {
+      const DLevel<T> &L = levels<T>(stream_items[i].first)[stream_items[i].second];
+      rows = std::max(rows, L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2)));
+    }
+    const int nwc = std::max(1, (rows + 31) / 32);
+    const int threads = 32 * (nwc + 1);
+    int lg = 0;
+    while ((1L << lg) < total) ++lg;
+    const auto key = std::make_tuple((int)sizeof(T), Q, maxCs, lg);
+    auto shape_of = [&](int st, int cp, int tl, size_t *sm, int *grid) {
+      *sm = (size_t)stream_header(st) + (size_t)(Q + 2 * Q) * maxCs * sizeof(T);
+      const int per_sm = std::max(1, std::min(cp, (int)((227u * 1024u) / *sm)));
+      *grid = (int)std::min<long>((total + tl - 1) / tl, (long)h0->nsm * per_sm);
+    };
+    CKR(join_in(stream_items, a, b));
+    auto found = g->tune.shape.find(key);
+    if (found == g->tune.shape.end()) {
+      static const int cand[][3] = {{2, 5, 1}, {3, 4, 1}, {4, 3, 1}, {2, 5, 2}, {4, 3, 2}, {4, 3, 4}};
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      std::array<int, 3> pick = {dim == 2 ? 2 : 4, dim == 2 ? 5 : 3, 1};
+      for (const auto &c : cand) {
+        int grid;
+        shape_of(c[0], c[1], c[2], &smem, &grid);
+        if (smem > 227u * 1024u) continue;
+        cudaEventRecord(e0, g->stream);
+        for (int t = 0; t < 3; ++t)
+          k_patch_apply_stream<T, Q, MAXJOBS><<<grid, threads, smem, g->stream>>>(
+              J, maxCs, c[2], h0->dev_err, c[0], h0->wait_cycles, h0->stall_copies);
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          pick = {c[0], c[1], c[2]};
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      found = g->tune.shape.emplace(key, pick).first;
+    }
+    nst = found->second[0];
+    cap = found->second[1];
+    tile = found->second[2];
+    int grid;
+    shape_of(nst, cap, tile, &smem, &grid);
+    if (smem > 227u * 1024u) {
+      g->err = "fused patch apply: patches too large for the streaming kernel";
+      return STFEM_ERR_ARG;
+    }
+    k_patch_apply_stream<T, Q, MAXJOBS><<<grid, threads, smem, g->stream>>>(J, maxCs, tile, h0->dev_err, nst,
+                                                                          h0->wait_cycles, h0->stall_copies);
+    g->fused_launches++;
+    g->fused_jobs += J.njobs;
+    (void)bytes;
+    (void)flops;
+    CKR(join_out(stream_items, a, b));
+  }
+  for (size_t a = 0; a < wide_items.size(); a += MAXJOBS) {
+    const size_t b = std::min(wide_items.size(), a + MAXJOBS);
+    PatchJobs<T, MAXJOBS> J;
+    J.njobs = 0;
+    size_t smem = 0;
+    long ctas = 0;
+    for (size_t i = a; i < b; ++i) {
+      stfem_h h = wide_items[i].first;
+      DLevel<T> &L = levels<T>(h)[wide_items[i].second];
+      add_job(J, L, use_r ? L.r : L.b, L.ybuf, L.zbuf, L.ticket);
+      smem = std::max(smem, wide_smem<T>(L, Q));
+      ctas += L.npatch * (L.dc.nr + L.dc.nc);
+      h->launches++;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].launches++;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].bytes += L.patch_bytes;
+      h->kstat[STFEM_KCLASS_PATCH_APPLY].flops += L.patch_flops;
+    }
+    CKR(join_in(wide_items, a, b));
+    k_patch_apply_wide<T, Q, PatchJobs<T, MAXJOBS>><<<(unsigned)ctas, WIDE_THREADS, smem, g->stream>>>(J);
+    g->fused_launches++;
+    g->fused_jobs += J.njobs;
+    CKR(join_out(wide_items, a, b));
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    g->err = "fused patch apply launch failed";
+    return STFEM_ERR_CUDA;
+  }
+  return 0;
+}
+
+template <typename T>
+int fused_stage(stfem_group g, int q, const std::vector<std::pair<stfem_h, int>> &items, bool use_r) {
+  if (items.empty()) return 0;
+  switch (q) {
+  case 1: return fused_stage_q<T, 1>(g, items, use_r);
+  case 2: return fused_stage_q<T, 2>(g, items, use_r);
+  case 3: return fused_stage_q<T, 3>(g, items, use_r);
+  case 4: return fused_stage_q<T, 4>(g, items, use_r);
+  default: return fused_stage_q<T, 5>(g, items, use_r);
+  }
+}
+
+// One V-cycle (from d = 0 on each member's finest level) for every handle of
+// hs, stage by stage from the top: stage k smooths level nlev - 1 - k of each
+// member that has it.  Per member the kernels and their order are those of
+// vcycle(); the patch applies of a stage are fused.
+template <typename T>
+int group_vcycle(stfem_group g, const std::vector<stfem_h> &hs) {
+  int K = 0, S = 0;
+  for (stfem_h h : hs) {
+    K = std::max(K, h->nlev - 1);
+    S = std::max(S, h->nsweeps);
+  }
+  const int q = hs.empty() ? 1 : hs[0]->q;
+  auto smooth_stage = [&](int k, bool pre) -> int {
+    for (int sw = 0; sw < S; ++sw) {
+      std::vector<std::pair<stfem_h, int>> items;
+      for (stfem_h h : hs) {
+        const int l = h->nlev - 1 - k;
+        if (l < 1 || sw >= h->nsweeps) continue;
+        DLevel<T> &L = levels<T>(h)[l];
+        const bool zero = pre && sw == 0;
+        if (!zero) launch_spmv<T>(h, L, time_coef<T>(h->T, h->tau), L.d, L.b, L.r, 1);
+        items.push_back({h, l});
+      }
+      CKR(fused_stage<T>(g, q, items, !(pre && sw == 0)));
+      for (const auto &it : items) {
+        stfem_h h = it.first;
+        DLevel<T> &L = levels<T>(h)[it.second];
+        const bool zero = pre && sw == 0;
+        Launch G_(h, STFEM_KCLASS_UPDATE, (double)L.N * (4.0 + 3.0 * sizeof(T)) + (double)L.sumC * (4.0 + sizeof(T)),
+                  (double)L.sumC + 2.0 * L.N);
+        k_vanka_update<T><<<grid_for(L.N, 256), 256, 0, h->stream>>>(L.N, L.iptr, L.ipos, L.scale, L.ybuf, L.d,
+                                                                      zero ? 1 : 0, 1, L.sumC);
+      }
+    }
+    return 0;
+  };
+  for (int k = 0; k < K; ++k) {
+    CKR(smooth_stage(k, true));
+    for (stfem_h h : hs) {
+      const int l = h->nlev - 1 - k;
+      if (l < 1) continue;
+      std::vector<DLevel<T>> &Ls = levels<T>(h);
+      DLevel<T> &L = Ls[l];
+      launch_spmv<T>(h, L, time_coef<T>(h->T, h->tau), L.d, L.b, L.r, 1);
+      restrict_to<T>(h, l, L.r, Ls[l - 1].b);
+      if (l - 1 == 0) coarse<T>(h, Ls[0].b, Ls[0].d);
+    }
+  }
+  for (stfem_h h : hs)
+    if (h->nlev == 1) coarse<T>(h, levels<T>(h)[0].b, levels<T>(h)[0].d);
+  for (int k = K - 1; k >= 0; --k) {
+    for (stfem_h h : hs) {
+      const int l = h->nlev - 1 - k;
+      if (l < 1) continue;
+      std::vector<DLevel<T>> &Ls = levels<T>(h);
+      prolongate_add<T>(h, l, Ls[l - 1].d, Ls[l].d);
+    }
+    CKR(smooth_stage(k, false));
+  }
+  return 0;
+}
+
+// Enqueues the start of member m's next slab: right-hand side, initial guess
+// (the previous end state at every time node) and the initial residual norm.
+int member_start(GroupMember &m) {
+  stfem_h h = m.h;
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  m.t_slab = std::chrono::steady_clock::now();
+  CKR(ensure_workspace(h, m.restart));
+  CKR(slab_rhs_async(h, m.first + m.slab, m.state, h->rhs, h->t0));
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, F.N * 8.0 + F.ns * 8.0, 0.0);
+    k_repeat<<<grid_for(F.N, 256), 256, 0, h->stream>>>(F.ns, h->q, m.state, h->xs);
+  }
+  h->hist.clear();
+  launch_spmv<double>(h, F, time_coef<double>(h->T, h->tau), h->xs, h->rhs, h->rvec, 1);
+  multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
+  CK(cudaMemcpyAsync(h->status_host + 2, h->hn2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  m.phase = GroupMember::INIT;
+  return 0;
+}
+
+// Enqueues the start of a restart cycle (v_0 = r / beta, g = beta e_1).
+void member_cycle(GroupMember &m) {
+  stfem_h h = m.h;
+  const long N = h->L64.back().N;
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, N * 16.0, (double)N);
+    k_div<<<grid_for(N, 256), 256, 0, h->stream>>>(N, h->rvec, h->V, nullptr, m.beta);
+  }
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, 8.0, 0.0);
+    k_set<<<1, 1, 0, h->stream>>>(h->g, m.beta);
+  }
+  m.j = 0;
+  m.jlast = -1;
+}
+
+// Enqueues the end of a cycle: y from the triangular system, x += Z y, and the
+// true residual norm.
+int member_finish(GroupMember &m) {
+  stfem_h h = m.h;
+  DLevel<double> &F = h->L64.back();
+  const long N = F.N;
+  const int kk = m.jlast + 1, m1 = m.restart + 1;
+  cudaStream_t s = h->stream;
+  {
+    Launch G_(h, STFEM_KCLASS_OTHER, (double)kk * kk * 8.0, (double)kk * kk);
+    k_backsolve<<<1, 1, 0, s>>>(kk, m1, h->H, h->g, h->y);
+  }
+  {
+    Launch G_(h, STFEM_KCLASS_BLAS1, (double)N * (16.0 + kk * (h->precision == STFEM_FP64 ? 8.0 : 4.0)),
+              2.0 * kk * N);
+    if (h->precision == STFEM_FP64)
+      k_update_x<double><<<grid_for(N, 256), 256, 0, s>>>(N, kk, h->Zd, N, h->y, h->xs);
+    else
+      k_update_x<float><<<grid_for(N, 256), 256, 0, s>>>(N, kk, h->Zf, N, h->y, h->xs);
+  }
+  launch_spmv<double>(h, F, time_coef<double>(h->T, h->tau), h->xs, h->rhs, h->rvec, 1);
+  multidot(h, 1, h->rvec, N, h->rvec, N, h->hn2);
+  CK(cudaMemcpyAsync(h->status_host + 2, h->hn2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  m.phase = GroupMember::FIN;
+  return 0;
+}
+
+// The slab converged (or ran out of iterations): keep its end state, move on.
+int member_next_slab(GroupMember &m, int rc) {
+  stfem_h h = m.h;
+  DLevel<double> &F = h->L64.back();
+  CK(cudaMemcpyAsync(m.state, h->xs + (long)(h->q - 1) * F.ns, F.ns * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->stream));
+  m.iters.push_back(m.it);
+  m.slab_ms.push_back(
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - m.t_slab).count());
+  m.status = std::max(m.status, rc);
+  ++m.slab;
+  m.phase = m.slab < m.n_slabs ? GroupMember::START : GroupMember::DONE;
+  return 0;
+}
+
+// One step of every member: members at the start of a slab or at the end of
+// a cycle enqueue that work, the iterating members one FGMRES iteration with
+// a shared, fused V-cycle; then every member's stream is synchronised once
+// and each member's host state advances as in fgmres() and march().
+int group_step(stfem_group g) {
+  std::vector<GroupMember *> live;
+  for (auto &up : g->members)
+    if (up->phase != GroupMember::DONE && up->status >= 0) live.push_back(up.get());
+  if (live.empty()) return 0;
+  for (GroupMember *m : live)
+    if (m->phase == GroupMember::START) {
+      const int rc = member_start(*m);
+      if (rc < 0) {
+        m->status = rc;
+        m->phase = GroupMember::DONE;
+      }
+    }
+  std::vector<GroupMember *> iter;
+  for (GroupMember *m : live)
+    if (m->phase == GroupMember::ITER) iter.push_back(m);
+  if (!iter.empty()) {
+    std::vector<stfem_h> hs;
+    for (GroupMember *m : iter) {
+      CKR(iter_pre(m->h, m->j));
+      hs.push_back(m->h);
+    }
+    const int rc = iter[0]->h->precision == STFEM_FP64 ? group_vcycle<double>(g, hs) : group_vcycle<float>(g, hs);
+    if (rc < 0) return rc;
+    for (GroupMember *m : iter) CKR(iter_post(m->h, m->j, m->restart + 1));
+  }
+  for (GroupMember *m : live)
+    if (cudaStreamSynchronize(m->h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      g->err = "device error in a group step";
+      return STFEM_ERR_CUDA;
+    }
+  for (GroupMember *m : live) {
+    stfem_h h = m->h;
+    if (m->phase == GroupMember::INIT) {
+      const double beta0 = std::sqrt(h->status_host[2]);
+      h->hist.push_back(1.0);
+      m->it = 0;
+      if (!std::isfinite(beta0)) {
+        h->err = "initial residual is not finite";
+        m->status = STFEM_ERR_BREAKDOWN;
+        m->phase = GroupMember::DONE;
+        continue;
+      }
+      m->beta0 = beta0;
+      m->bound = h->stop == STFEM_STOP_ABSOLUTE ? m->tol : m->tol * beta0;
+      if (beta0 == 0.0 || beta0 <= m->bound) {
+        CKR(member_next_slab(*m, STFEM_OK));
+        continue;
+      }
+      m->beta = beta0;
+      member_cycle(*m);
+      m->phase = GroupMember::ITER;
+    } else if (m->phase == GroupMember::ITER) {
+      const double res = h->status_host[0], hn = h->status_host[1];
+      if (!std::isfinite(res) || !std::isfinite(hn)) {
+        h->err = "FGMRES breakdown: non-finite Hessenberg entry";
+        m->status = STFEM_ERR_BREAKDOWN;
+        m->phase = GroupMember::DONE;
+        continue;
+      }
+      ++m->it;
+      m->jlast = m->j;
+      h->hist.push_back(res / m->beta0);
+      if (res <= m->bound || m->it >= m->max_it || hn == 0.0 || m->j + 1 >= m->restart)
+        CKR(member_finish(*m));
+      else
+        ++m->j;
+    } else if (m->phase == GroupMember::FIN) {
+      const double res = std::sqrt(h->status_host[2]);
+      if (!std::isfinite(res)) {
+        h->err = "FGMRES breakdown: non-finite residual";
+        m->status = STFEM_ERR_BREAKDOWN;
+        m->phase = GroupMember::DONE;
+        continue;
+      }
+      if (res <= m->bound) {
+        CKR(member_next_slab(*m, STFEM_OK));
+      } else if (m->it >= m->max_it) {
+        CKR(member_next_slab(*m, STFEM_NOT_CONVERGED));
+      } else {
+        m->beta = res;
+        member_cycle(*m);
+        m->phase = GroupMember::ITER;
+      }
+    }
+  }
+  return 0;
+}
+
+} // namespace
+
+extern "C" {
+
+int stfem_group_create(stfem_group *out) {
+  if (!out) return STFEM_ERR_ARG;
+  stfem_group g = new stfem_group_ctx();
+  cudaGetDevice(&g->device);
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete g;
+    return STFEM_ERR_CUDA;
+  }
+  *out = g;
+  return STFEM_OK;
+}
+
+int stfem_group_add(stfem_group g, stfem_h h, int first_slab, int n_slabs, double *state, double tol, int restart,
+                    int max_it, long long *member) {
+  if (!g || !h || !state || !member || first_slab < 0 || n_slabs < 0 || restart < 1 || max_it < 0 ||
+      !(tol >= 0.0))
+    return STFEM_ERR_ARG;
+  if (h->precision < 0) {
+    g->err = "stfem_gmg_setup has not been called on the handle";
+    return STFEM_ERR_STATE;
+  }
+  if (restart > MAXM) {
+    g->err = "restart length above the supported maximum";
+    return STFEM_ERR_ARG;
+  }
+  for (auto &m : g->members) {
+    if (m->phase == GroupMember::DONE) continue;
+    if (m->h == h) {
+      g->err = "the handle is already a member of the group";
+      return STFEM_ERR_ARG;
+    }
+    if (m->h->q != h->q || m->h->precision != h->precision) {
+      g->err = "group members share the temporal degree and the precision";
+      return STFEM_ERR_ARG;
+    }
+  }
+  if (!h->grp_ev && cudaEventCreateWithFlags(&h->grp_ev, cudaEventDisableTiming) != cudaSuccess) {
+    g->err = "cudaEventCreate failed";
+    return STFEM_ERR_CUDA;
+  }
+  auto m = std::make_unique<GroupMember>();
+  m->h = h;
+  m->id = g->next_id++;
+  m->first = first_slab;
+  m->n_slabs = n_slabs;
+  m->state = state;
+  m->tol = tol;
+  m->restart = restart;
+  m->max_it = max_it;
+  m->phase = n_slabs > 0 ? GroupMember::START : GroupMember::DONE;
+  *member = m->id;
+  g->members.push_back(std::move(m));
+  return STFEM_OK;
+}
+
+int stfem_group_step(stfem_group g, int *n_active) {
+  if (!g) return STFEM_ERR_ARG;
+  const int rc = group_step(g);
+  int n = 0;
+  for (auto &m : g->members) n += m->phase != GroupMember::DONE && m->status >= 0;
+  if (n_active) *n_active = n;
+  return rc;
+}
+
+int stfem_group_member(stfem_group g, long long member, int *done, int *status, int *iters_host,
+                       double *slab_ms_host) {
+  if (!g) return STFEM_ERR_ARG;
+  for (auto &m : g->members) {
+    if (m->id != member) continue;
+    const bool fin = m->phase == GroupMember::DONE || m->status < 0;
+    if (done) *done = fin ? 1 : 0;
+    if (status) *status = m->status;
+    if (fin && m->status >= 0) {
+      const int rc = check_dev_err(m->h);
+      if (rc < 0) {
+        m->status = rc;
+        if (status) *status = rc;
+      }
+    }
+    for (size_t i = 0; i < m->iters.size(); ++i) {
+      if (iters_host) iters_host[i] = m->iters[i];
+      if (slab_ms_host) slab_ms_host[i] = m->slab_ms[i];
+    }
+    return STFEM_OK;
+  }
+  g->err = "unknown group member";
+  return STFEM_ERR_ARG;
+}
+
+int stfem_group_remove(stfem_group g, long long member) {
+  if (!g) return STFEM_ERR_ARG;
+  for (size_t i = 0; i < g->members.size(); ++i)
+    if (g->members[i]->id == member) {
+      if (cudaStreamSynchronize(g->members[i]->h->stream) != cudaSuccess) return STFEM_ERR_CUDA;
+      g->members.erase(g->members.begin() + i);
+      return STFEM_OK;
+    }
+  g->err = "unknown group member";
+  return STFEM_ERR_ARG;
+}
+
+int stfem_group_stats(stfem_group g, long long *fused_launches, long long *fused_jobs) {
+  if (!g) return STFEM_ERR_ARG;
+  if (fused_launches) *fused_launches = g->fused_launches;
+  if (fused_jobs) *fused_jobs = g->fused_jobs;
+  return STFEM_OK;
+}
+
+const char *stfem_group_last_error(stfem_group g) { return g ? g->err.c_str() : ""; }
+
+void stfem_group_destroy(stfem_group g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  for (auto &m : g->members)
+    if (m->h) cudaStreamSynchronize(m->h->stream);
+  cudaEventDestroy(g->ev);
+  cudaStreamDestroy(g->stream);
+  delete g;
 }
 
 } // extern "C"

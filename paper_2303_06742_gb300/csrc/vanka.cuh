@@ -262,24 +262,29 @@ __global__ void __launch_bounds__(1024) k_patch_apply_diag(const int *__restrict
 // to the time nodes with V and writes y.  Every value is formed by one fixed
 // sequence of operations, so the result does not depend on which CTA
 // finishes last.
-template <typename T, int Q>
-__global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict__ pcs,
-                                                          const long long *__restrict__ pdoff,
-                                                          const int *__restrict__ pdofs,
-                                                          const long long *__restrict__ pioff,
-                                                          const T *__restrict__ pinv, const T *__restrict__ res,
-                                                          T *__restrict__ y, T *__restrict__ zbuf,
-                                                          int *__restrict__ ticket, DiagCoef<T> dc) {
+template <typename T, int Q, typename JOBS>
+__global__ void __launch_bounds__(512) k_patch_apply_wide(const __grid_constant__ JOBS J) {
   using Vv = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int CR = VEC / 2;
   constexpr int PF = 8; // loads of the inverse a thread keeps in flight
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nr = dc.nr, nc = dc.nc, ns = nr + nc;
-  const long p = blockIdx.x / ns;
+  const int nr = J.dc[0].nr, nc = J.dc[0].nc, ns = nr + nc;
+  // CTA -> (job, patch of the job, slot)
+  const long gp = blockIdx.x / ns;
+  int jb = 0;
+  if (sizeof(J.first) > 2 * sizeof(long)) // several jobs (a one-job table keeps jb = 0)
+    while (gp >= J.first[jb + 1]) ++jb;
+  const long p = gp - J.first[jb];
   const int a = (int)(blockIdx.x % ns); // slot of this CTA
-  const int Cs = pcs[p];
-  const long long doff = pdoff[p];
+  const DiagCoef<T> &dc = J.dc[jb];
+  const int *__restrict__ pdofs = J.pdofs[jb];
+  const T *__restrict__ res = J.res[jb];
+  T *__restrict__ y = J.y[jb];
+  T *__restrict__ zbuf = J.zbuf[jb];
+  int *__restrict__ ticket = J.ticket[jb];
+  const int Cs = J.pcs[jb][p];
+  const long long doff = J.pdoff[jb][p];
   const bool cplx = a >= nr;
   const int nrg = cplx ? (Cs + CR - 1) / CR : (Cs + VEC - 1) / VEC; // row groups
   const int G = max(1, (int)blockDim.x / nrg);
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(512) k_patch_apply_wide(const int *__restrict_
   const bool active = t < G * nrg;
   const int g = t % nrg, jg = t / nrg;
   const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
-  const T *Ab = pinv + pioff[p];
+  const T *Ab = J.pinv[jb] + J.pioff[jb][p];
   const Vv *col0 = cplx ? reinterpret_cast<const Vv *>(Ab + (size_t)nr * Cs * ldR + (size_t)(a - nr) * Cs * ldC +
                                                        2 * CR * g)
                         : reinterpret_cast<const Vv *>(Ab + (size_t)a * Cs * ldR + VEC * g);

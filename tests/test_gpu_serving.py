@@ -1,8 +1,10 @@
 """The serving loop (needs a GPU): requests admitted by HBM footprint run
-concurrently, one handle and stream per worker; every result must be bitwise
-the same as the request run alone and as the direct march of the same
-problem, and the footprint estimate used for admission must bound the bytes
-the handle actually allocated."""
+concurrently, one handle and stream per request, either marched by their own
+worker (independent mode) or in lockstep groups with fused smoother launches
+(batched mode, continuous batching); every result must be bitwise the same as
+the request run alone and as the direct march of the same problem, and the
+footprint estimate used for admission must bound the bytes the handle
+actually allocated."""
 import numpy as np
 import pytest
 
@@ -20,11 +22,12 @@ def _requests():
     return reqs
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("batched", [False, True])
+def test_results_alone_equal_results_in_the_mix(batched):
     import paper_2303_06742_gb300 as st
     reqs = _requests()
     probs = [gpu_problem(c) for c in reqs]
-    S = st.Server(hbm_budget=8 << 30, n_workers=3)
+    S = st.Server(hbm_budget=8 << 30, n_workers=3, batched=batched)
     ids = [S.submit(p, c["slabs"], tol=c["tol"]) for p, c in zip(probs, reqs)]
     mix = [S.result(i) for i in ids]
     S.close()
@@ -38,7 +41,7 @@ def test_results_alone_equal_results_in_the_mix():
     ends = sorted(m[0]["t_done"] for m in mix)
     assert starts[1] < ends[0]
     for p, c, (info, state, _) in zip(probs, reqs, mix):
-        A = st.Server(hbm_budget=8 << 30, n_workers=1)
+        A = st.Server(hbm_budget=8 << 30, n_workers=1, batched=batched)
         alone = A.result(A.submit(p, c["slabs"], tol=c["tol"]))
         A.close()
         assert np.array_equal(alone[1], state)
