@@ -453,7 +453,8 @@ typedef struct {
 int stfem_server_create(long long hbm_budget, int n_workers, stfem_server *out);
 /* Batched mode (continuous batching): n_workers threads set requests up
  * (admitted as above); a stepper thread per class of requests (temporal
- * degree, precision) keeps up to max_members of them resident in a group
+ * degree, precision, spatial degree, mesh size: members of a group then cost
+ * about the same per step) keeps up to max_members of them resident in a group
  * (stfem_group_*) and advances them in lockstep, the patch applies of each
  * V-cycle stage of all members in one fused launch; a request joins between
  * two steps as soon as its setup is done and a place is free, and leaves

@@ -2,7 +2,7 @@
 // admitted by HBM footprint and run concurrently, one handle and one CUDA
 // stream per request.  Independent mode: each worker thread sets up and
 // marches its request.  Batched mode: workers set requests up and hand them
-// to a stepper thread per class (temporal degree, precision), whose group
+// to a stepper thread per class (temporal and spatial degree, precision, mesh), whose group
 // marches its members in lockstep with fused smoother launches; requests join
 // the group between steps as they become ready and leave when done.
 #include "../../include/stfem.h"
@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <condition_variable>
@@ -44,7 +45,7 @@ struct Ready {
   long long member = 0;
 };
 
-// The requests of one class (temporal degree, precision) marching in lockstep
+// The requests of one class (temporal and spatial degree, precision, mesh) marching in lockstep
 // on one stepper thread.
 struct Lane {
   std::deque<Ready> queue;    // set up, waiting for a place in the group
@@ -63,7 +64,9 @@ struct stfem_server_ctx {
   // batched mode: set-up workers hand handles to per-class groups
   bool batched = false;
   int max_members = 8;
-  std::map<std::pair<int, int>, std::unique_ptr<Lane>> lanes;
+  // lanes by class: temporal degree, precision, spatial degree and mesh size,
+  // so that the members of a group cost about the same per step
+  std::map<std::array<int, 5>, std::unique_ptr<Lane>> lanes;
   long long next_id = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -143,6 +146,13 @@ void run_request(stfem_server s, Request &R) {
   R.info.status = status;
   R.info.n_slabs = q.n_slabs;
   R.info.n_state = n_state;
+}
+
+// The lane of a request in batched mode: requests of one lane share the
+// temporal degree and the precision (a group's requirement), the spatial
+// degree and the mesh (so they advance at about the same pace).
+std::array<int, 5> lane_class(const stfem_request &q) {
+  return {q.deg.k, q.gmg.precision, q.deg.r, q.mesh.n_cells[0], q.mesh.dim == 3 ? q.mesh.n_cells[2] : 1};
 }
 
 // Batched mode, set-up part: handle, stream and initial state of a request.
@@ -316,7 +326,7 @@ void worker(stfem_server s) {
       // set up here, march in the lockstep group of the request's class
       Ready rd;
       if (setup_request(s, R, &rd)) {
-        const std::pair<int, int> cls(R->req.deg.k, R->req.gmg.precision);
+        const std::array<int, 5> cls = lane_class(R->req);
         std::lock_guard<std::mutex> lock(s->mu);
         Lane *lane = s->lanes.at(cls).get();
         lane->queue.push_back(rd);
@@ -385,7 +395,7 @@ int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id)
     std::lock_guard<std::mutex> lock(s->mu);
     if (R->footprint > s->budget) return STFEM_ERR_ARG;
     if (s->batched) { // the stepper of the request's class
-      const std::pair<int, int> cls(req->deg.k, req->gmg.precision);
+      const std::array<int, 5> cls = lane_class(*req);
       if (!s->lanes.count(cls)) {
         auto lane = std::make_unique<Lane>();
         lane->thread = std::thread(stepper, s, lane.get());
