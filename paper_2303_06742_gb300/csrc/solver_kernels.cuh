@@ -112,11 +112,18 @@ __global__ void __launch_bounds__(DOT_THREADS) k_multidot(int k, const double *_
   double acc[DOT_NV];
 #pragma unroll
   for (int t = 0; t < DOT_NV; ++t) acc[t] = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const double wi = w[i];
+  // two entries per trip: twice the independent loads in flight
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const long i2 = i + stride;
+    const bool two = i2 < n;
+    const double wi = w[i], wi2 = two ? w[i2] : 0.0;
 #pragma unroll
     for (int t = 0; t < DOT_NV; ++t)
-      if (v0 + t < k) acc[t] += V[(long)(v0 + t) * ldV + i] * wi;
+      if (v0 + t < k) {
+        const double a = V[(long)(v0 + t) * ldV + i], a2 = two ? V[(long)(v0 + t) * ldV + i2] : 0.0;
+        acc[t] += a * wi + a2 * wi2;
+      }
   }
   __shared__ double sm[DOT_NV][DOT_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -150,21 +157,33 @@ __global__ void __launch_bounds__(DOT_THREADS) k_axpy_dot(int k, const double *_
   double hv[KB];
 #pragma unroll
   for (int t = 0; t < KB; ++t) hv[t] = t < k ? h[t] : 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double vi[KB];
-    double s = 0.0;
+  // small blocks take two entries per trip (more independent loads in flight)
+  constexpr int UN = KB <= 8 ? 2 : 1;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += UN * stride) {
+    double vi[UN][KB], wn[UN];
 #pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      vi[t] = t < k ? V[(long)t * ldV + i] : 0.0;
-      s += hv[t] * vi[t];
+    for (int u = 0; u < UN; ++u) {
+      const long i = i0 + u * stride;
+      const bool in = i < n;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        vi[u][t] = (t < k && in) ? V[(long)t * ldV + i] : 0.0;
+        s += hv[t] * vi[u][t];
+      }
+      wn[u] = in ? w[i] - s : 0.0;
     }
-    const double wn = w[i] - s;
-    w[i] = wn;
-    if (mode == 0) {
 #pragma unroll
-      for (int t = 0; t < KB; ++t) acc[t] += vi[t] * wn;
-    } else {
-      acc[0] += wn * wn;
+    for (int u = 0; u < UN; ++u) {
+      const long i = i0 + u * stride;
+      if (i < n) w[i] = wn[u];
+      if (mode == 0) {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) acc[t] += vi[u][t] * wn[u];
+      } else {
+        acc[0] += wn[u] * wn[u];
+      }
     }
   }
   __shared__ double sm[KB][DOT_THREADS / 32];

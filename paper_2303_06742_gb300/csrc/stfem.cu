@@ -240,6 +240,26 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(const __grid_consta
   const int tid = threadIdx.x;
   long long it = 0;
   int j = 0;
+  // The first PFK gather entries of a thread for the CTA's next patch are
+  // loaded into registers while the current patch streams, so the gather's two
+  // dependent loads overlap the copies (the values are the same as a direct
+  // gather's).
+  constexpr int PFK = 4;
+  T pre[PFK];
+  bool have_pre = false;
+  auto prefetch = [&](long pn) {
+    int jn = j;
+    if (MAXJ > 1)
+      while (pn >= J.first[jn + 1]) ++jn;
+    const long lpn = pn - J.first[jn];
+    const int Cn = Q * J.pcs[jn][lpn];
+    const long long dn = J.pdoff[jn][lpn];
+    const int *__restrict__ pd = J.pdofs[jn];
+    const T *__restrict__ rr = J.res[jn];
+#pragma unroll
+    for (int k = 0; k < PFK; ++k)
+      if (tid + k * nct < Cn) pre[k] = rr[pd[dn + tid + k * nct]];
+  };
   for (long b = (long)blockIdx.x * tile; b < npatch; b += step)
     for (long p = b; p < b + tile && p < npatch; ++p) {
       // all consumers pass the same barriers, so they all see the flag and
@@ -255,7 +275,15 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(const __grid_consta
       const int *__restrict__ pdofs = J.pdofs[j];
       const T *__restrict__ res = J.res[j];
       T *__restrict__ y = J.y[j];
-      for (int jj = tid; jj < C; jj += nct) rs[jj] = res[pdofs[doff + jj]];
+      {
+        int jj = tid;
+        if (have_pre) {
+#pragma unroll
+          for (int k = 0; k < PFK; ++k, jj += nct)
+            if (jj < C) rs[jj] = pre[k];
+        }
+        for (; jj < C; jj += nct) rs[jj] = res[pdofs[doff + jj]];
+      }
       consumer_sync(nct);
       for (int m = tid; m < Cs; m += nct) {
         for (int a = 0; a < ns; ++a) {
@@ -275,6 +303,12 @@ __global__ void __launch_bounds__(1024) k_patch_apply_stream(const __grid_consta
         }
       }
       consumer_sync(nct);
+      {
+        long pn = p + 1;
+        if (!(pn < b + tile && pn < npatch)) pn = b + step;
+        have_pre = pn < npatch;
+        if (have_pre) prefetch(pn);
+      }
       const int nRr = (Cs + VEC - 1) / VEC, nCr = (Cs + CR - 1) / CR;
       const int ldR = (Cs + 3) / 4 * 4, ldC = 2 * ((Cs + 1) / 2 * 2);
       int role = -1, slot = 0, m0 = 0;
