@@ -4,11 +4,12 @@ Sources are derived symbolically (sympy) from the model Eq. 1.1:
 
     rho f = rho u_tt - div(sigma(u)) + alpha grad p,
     sigma(u) = 2 mu eps(u) + lam tr(eps(u)) I,
-    g     = c0 p_t + alpha div(u_t) - div(kappa grad p),
+    g     = c0 p_t + alpha div(u_t) - div(K grad p),
 
-with lam, mu, kappa constant on each cell (so the derivatives do not act on
-them).  Boundary data u_D, v_D = d/dt u_D, p_D are the exact solution's
-traces; Neumann data follow from Eq. 1.1e/g.
+with lam, mu and the permeability K (kappa I, or a symmetric d x d tensor)
+constant on each cell (so the derivatives do not act on them).  Boundary
+data u_D, v_D = d/dt u_D, p_D are the exact solution's traces; Neumann data
+follow from Eq. 1.1e/g.
 
 Problems:
 
@@ -18,6 +19,8 @@ Problems:
 * ``paper_superconv`` Eq. 5.3 with w1 = 40 pi, w2 = 10 pi (2D; polynomial in space)
 * ``pulse``      f = g = 0 and a traction t_N = (0, 0, -sin(pi t / 0.05)) on the
                  top-face square [0.75, 1.25]^2 (zero elsewhere), no exact solution
+* ``trace``      u = sin(2t + 1/2) Phi (1, -7/10, 2/5), p = cos(t) Phi,
+                 Phi = prod cos((1 + i/2) x_i + 3/10 + i/5): nonzero traces
 * ``zero``       no sources and zero data
 """
 import numpy as np
@@ -37,7 +40,7 @@ class Problem:
         self.zero_trace = zero_trace
         self.rho, self.alpha, self.c0 = rho, alpha, c0
         X = s.symbols("x0:%d" % dim, real=True)
-        t, lam, mu, kap = s.symbols("t lam mu kap", real=True)
+        t, lam, mu = s.symbols("t lam mu", real=True)
         self._X, self._t = X, t
         if u is None:
             u = [s.Integer(0)] * dim
@@ -52,8 +55,10 @@ class Problem:
         rho_f = [rho * s.diff(u[b], t, 2) - sum(s.diff(sig[b][a], X[a]) for a in range(dim))
                  + alpha * s.diff(p, X[b]) for b in range(dim)]
         div_ut = sum(s.diff(u[a], t, X[a]) for a in range(dim))
-        lap_p = sum(s.diff(p, X[a], 2) for a in range(dim))
-        g = c0 * s.diff(p, t) + alpha * div_ut - kap * lap_p
+        # -div(K grad p) for K constant on the cell, K = (k_ab)
+        Ks = [[s.Symbol("k%d%d" % (a, b), real=True) for b in range(dim)] for a in range(dim)]
+        div_Kgrad = sum(Ks[a][b] * s.diff(p, X[a], X[b]) for a in range(dim) for b in range(dim))
+        g = c0 * s.diff(p, t) + alpha * div_ut - div_Kgrad
         v = [s.diff(ui, t) for ui in u]
         self.sym = dict(u=u, v=v, p=p, rho_f=rho_f, g=g, grad=grad, sig=sig)
         args = list(X) + [t]
@@ -62,10 +67,10 @@ class Problem:
         self._p = s.lambdify(args, p, "numpy")
         self._grad = [[s.lambdify(args, grad[b][a], "numpy") for a in range(dim)] for b in range(dim)]
         self._rho_f = [s.lambdify(args + [lam, mu], e, "numpy") for e in rho_f]
-        self._g = s.lambdify(args + [kap], g, "numpy")
+        self._g = s.lambdify(args + [Ks[a][b] for a in range(dim) for b in range(dim)], g, "numpy")
         self._sig = [[s.lambdify(args + [lam, mu], sig[b][a], "numpy") for a in range(dim)]
                      for b in range(dim)]
-        self._flux = [s.lambdify(args + [kap], -kap * s.diff(p, X[a]), "numpy") for a in range(dim)]
+        self._dp = [s.lambdify(args, s.diff(p, X[a]), "numpy") for a in range(dim)]
 
     @staticmethod
     def _ev(f, X, t, *extra):
@@ -93,8 +98,15 @@ class Problem:
     def rho_f(self, X, t, lam, mu):
         return np.stack([self._ev(f, X, t, lam, mu) for f in self._rho_f], axis=1)
 
+    @staticmethod
+    def _tensor(kappa, d):
+        return kappa * np.eye(d) if np.ndim(kappa) == 0 else np.asarray(kappa, float)
+
     def g(self, X, t, kappa):
-        return self._ev(self._g, X, t, kappa)
+        """g of Eq. 1.1 for the cell's permeability (kappa: a scalar, K =
+        kappa I, or the d x d tensor K)."""
+        K = self._tensor(kappa, self.dim)
+        return self._ev(self._g, X, t, *K.ravel())
 
     def traction(self, X, t, n, lam=None, mu=None):
         """t_N = -(sigma(u) - alpha p I) n (Eq. 1.1e); needs lam, mu of the cell
@@ -111,13 +123,13 @@ class Problem:
         return out
 
     def p_flux(self, X, t, n, kappa=None):
-        """p_N = -kappa grad p . n (Eq. 1.1g)."""
+        """p_N = -(K grad p) . n (Eq. 1.1g); kappa: a scalar (K = kappa I) or
+        the d x d tensor K of the cell."""
         if kappa is None:
             raise ValueError("flux of a manufactured solution needs kappa")
-        out = np.zeros(X.shape[0])
-        for a in range(self.dim):
-            out += self._ev(self._flux[a], X, t, kappa) * n[a]
-        return out
+        K = self._tensor(kappa, self.dim)
+        gp = np.stack([self._ev(f, X, t) for f in self._dp], axis=1)  # (n, d)
+        return -np.einsum("qb,ab,a->q", gp, K, np.asarray(n, float))
 
 
 def sin_problem(dim, rho, alpha, c0):
@@ -127,6 +139,22 @@ def sin_problem(dim, rho, alpha, c0):
     for xi in X:
         phi = phi * s.sin(s.pi * xi)
     return Problem("sin", dim, rho, alpha, c0, u=[phi * s.sin(t)] * dim, p=phi * s.cos(t), zero_trace=True)
+
+
+def trace_problem(dim, rho, alpha, c0):
+    """A smooth solution that does not vanish on the boundary, so that the
+    Dirichlet data u_D, v_D, p_D and the Neumann data of Eq. 3.4 are nonzero:
+    u = sin(2t + 1/2) Phi(x) (1, -7/10, 2/5), p = cos(t) Phi(x),
+    Phi = prod_i cos((1 + i/2) x_i + 3/10 + i/5).  Its sources come from the
+    symbolic derivatives of Problem."""
+    X = s.symbols("x0:%d" % dim, real=True)
+    t = s.Symbol("t", real=True)
+    phi = s.Integer(1)
+    for i, xi in enumerate(X):
+        phi = phi * s.cos((1 + s.Rational(i, 2)) * xi + s.Rational(3, 10) + s.Rational(i, 5))
+    w = [s.Integer(1), s.Rational(-7, 10), s.Rational(2, 5)][:dim]
+    T = s.sin(2 * t + s.Rational(1, 2))
+    return Problem("trace", dim, rho, alpha, c0, u=[wc * T * phi for wc in w], p=s.cos(t) * phi)
 
 
 def paper_eoc_problem(rho=1.0, alpha=0.9, c0=0.01, w1=s.pi, w2=s.pi):

@@ -30,8 +30,12 @@ Readings taken where the paper is silent or garbled:
 * Source scaling: Eq. 1.1a has rho f on the right, the functional F_gamma
   tests f.  Reading: the load tested is rho f (consistent with the PDE).
 * Coefficients on coarse levels (rediscretised operators): a coarse cell's
-  lambda, mu and kappa are the arithmetic mean over its fine descendants.
-  The permeability is isotropic, K = kappa I.
+  lambda, mu and K are the arithmetic mean over its fine descendants (entry
+  by entry for a tensor K).
+* Permeability: K = kappa I per cell (``kappa`` of shape (ncell,)), or a
+  symmetric positive definite d x d tensor per cell (shape (ncell, d, d)),
+  the K of Eq. 1.1; it enters B_gamma through (K grad p, grad xi) and the
+  normal fluxes (K grad p) . n of the Nitsche and interior penalty terms.
 * Quadrature: Gauss-Legendre with r+2 points per direction on cells and
   faces, for matrices and loads.
 * Broken pressure space P_{r-1}^disc (Sec. 2 names mapped and unmapped
@@ -234,13 +238,20 @@ def face_rule(dim, nq, axis, side):
 
 
 class Material:
-    """rho, alpha, c0 scalars; lam, mu, kappa per cell of the mesh it belongs to."""
+    """rho, alpha, c0 scalars; lam, mu per cell of the mesh it belongs to; the
+    permeability per cell as kappa (K = kappa I, shape (ncell,)) or as the
+    tensor K itself (shape (ncell, d, d))."""
 
     def __init__(self, rho, alpha, c0, lam, mu, kappa):
         self.rho, self.alpha, self.c0 = float(rho), float(alpha), float(c0)
         self.lam = np.asarray(lam, float)
         self.mu = np.asarray(mu, float)
         self.kappa = np.asarray(kappa, float)
+
+    def K(self, c, d):
+        """The permeability tensor of cell c (d x d)."""
+        k = self.kappa[c]
+        return k * np.eye(d) if np.ndim(k) == 0 else np.array(k, float)
 
     @staticmethod
     def uniform(mesh, rho, alpha, c0, lam, mu, kappa):
@@ -252,7 +263,7 @@ class Material:
         coarse = fine_mesh.coarsen()
         out = []
         for arr in (self.lam, self.mu, self.kappa):
-            a = np.zeros(coarse.ncell)
+            a = np.zeros((coarse.ncell,) + arr.shape[1:])
             for c, cm in coarse.cells():
                 acc = 0.0
                 for off in itertools.product((0, 1), repeat=fine_mesh.dim):
@@ -369,13 +380,17 @@ class SpatialOps:
             C += self.mat.alpha * np.einsum("q,qs,qj->sj", wf, ps, pn)
         return K, C, Cvol, Mu
 
-    def _elem_p(self, kappa, faces_D):
+    def _elem_p(self, K, faces_D):
+        """Cell matrices of B_gamma and the pressure mass for the permeability
+        tensor K: (K grad psi_s, grad psi_r) plus, on Dirichlet faces of p,
+        -<(K grad psi_s) . n, psi_r> - <psi_s, (K grad psi_r) . n>
+        + gamma_b / h_F <psi_s, psi_r>."""
         mesh, d = self.mesh, self.d
         X, w = cell_rule(d, self.nq)
         w = w * mesh.vol
         psi, dpsi = self.Qs.basis(X)
         dpsi = dpsi / mesh.h[None, None, :]
-        B = kappa * np.einsum("q,qsa,qra->rs", w, dpsi, dpsi)
+        B = np.einsum("q,qsb,ab,qra->rs", w, dpsi, K, dpsi)
         Mp = np.einsum("q,qr,qs->rs", w, psi, psi)
         for ax, side, fid in faces_D:
             Xf, wf = face_rule(d, self.nq, ax, side)
@@ -384,7 +399,7 @@ class SpatialOps:
             n[ax] = 1.0 if side == 1 else -1.0
             ps, dps = self.Qs.basis(Xf)
             dps = dps / mesh.h[None, None, :]
-            dn = kappa * np.einsum("qsa,a->qs", dps, n)
+            dn = np.einsum("qsb,ab,a->qs", dps, K, n)
             B += -np.einsum("q,qs,qr->rs", wf, dn, ps)
             B += -np.einsum("q,qs,qr->rs", wf, ps, dn)
             B += (self.gamma_b / mesh.hF) * np.einsum("q,qs,qr->rs", wf, ps, ps)
@@ -407,13 +422,13 @@ class SpatialOps:
             bf = boundary_faces(mesh, cm)
             fu = tuple((a, s, f) for a, s, f in bf if self.bc_u[f] == DIRICHLET)
             fp = tuple((a, s, f) for a, s, f in bf if self.bc_p[f] == DIRICHLET)
-            lam, mu, kap = self.mat.lam[c], self.mat.mu[c], self.mat.kappa[c]
+            lam, mu, Kc = self.mat.lam[c], self.mat.mu[c], self.mat.K(c, d)
             ku = (lam, mu, fu)
             if ku not in cache_u:
                 cache_u[ku] = self._elem_u(lam, mu, fu)
-            kp = (kap, fp)
+            kp = (tuple(Kc.ravel()), fp)
             if kp not in cache_p:
-                cache_p[kp] = self._elem_p(kap, fp)
+                cache_p[kp] = self._elem_p(Kc, fp)
             K, C, Cvol, Mu = cache_u[ku]
             B, Mp = cache_p[kp]
             un = self.Vs.cell_nodes(cm)
@@ -451,8 +466,8 @@ class SpatialOps:
             wf = wf * (mesh.vol / mesh.h[ax])
             pa, dpa = self.Qs.basis(Xm)
             pb, dpb = self.Qs.basis(Xp)
-            dna = dpa[:, :, ax] / mesh.h[ax]  # grad . n, n = +e_ax
-            dnb = dpb[:, :, ax] / mesh.h[ax]
+            dpa = dpa / mesh.h[None, None, :]
+            dpb = dpb / mesh.h[None, None, :]
             for c, cm in mesh.cells():
                 if cm[ax] == mesh.n[ax] - 1:
                     continue
@@ -464,10 +479,13 @@ class SpatialOps:
                 for i in range(d):
                     c2 += cn[i] * stride
                     stride *= mesh.n[i]
-                ka, kb = self.mat.kappa[c], self.mat.kappa[c2]
+                Ka, Kb = self.mat.K(c, d), self.mat.K(c2, d)
+                # (K grad psi) . n with n = +e_ax on either side
+                fa = np.einsum("qsb,b->qs", dpa, Ka[ax])
+                fb = np.einsum("qsb,b->qs", dpb, Kb[ax])
                 # trial/test functions of both cells: jump and flux-average values
                 jump = np.concatenate([pa, -pb], axis=1)                       # (nq, 2 nloc)
-                flux = np.concatenate([0.5 * ka * dna, 0.5 * kb * dnb], axis=1)
+                flux = np.concatenate([0.5 * fa, 0.5 * fb], axis=1)
                 Bf = (-np.einsum("q,qs,qr->rs", wf, flux, jump)
                       - np.einsum("q,qs,qr->rs", wf, jump, flux)
                       + (gam / hF) * np.einsum("q,qs,qr->rs", wf, jump, jump))
@@ -500,9 +518,9 @@ class SpatialOps:
         for c, cm in mesh.cells():
             x0 = mesh.lo + mesh.h * np.array(cm)
             Xp = x0[None, :] + X * mesh.h[None, :]
-            lam, mu, kap = self.mat.lam[c], self.mat.mu[c], self.mat.kappa[c]
+            lam, mu, Kc = self.mat.lam[c], self.mat.mu[c], self.mat.K(c, d)
             rf = prob.rho_f(Xp, t, lam, mu)  # (nq, d)
-            gg = prob.g(Xp, t, kap)  # (nq,)
+            gg = prob.g(Xp, t, Kc)  # (nq,)
             un = self.Vs.cell_nodes(cm)
             pn = self.Qs.cell_nodes(cm)
             Fe = np.einsum("q,qi,qc->ic", w, phi, rf)
@@ -534,11 +552,11 @@ class SpatialOps:
                     F[uvec] += Fa
                     G[pn] += -self.mat.alpha * np.einsum("q,q,qr->r", wf, vD @ n, ps)
                 if self.bc_p[fid] == NEUMANN:
-                    pN = prob.p_flux(Xfp, t, n, kap)
+                    pN = prob.p_flux(Xfp, t, n, Kc)
                     G[pn] += -np.einsum("q,q,qr->r", wf, pN, ps)
                 elif not prob.zero_trace:
                     pD = prob.p(Xfp, t)
-                    dn = kap * np.einsum("qsa,a->qs", dps, n)
+                    dn = np.einsum("qsb,ab,a->qs", dps, Kc, n)
                     G[pn] += -np.einsum("q,q,qs->s", wf, pD, dn)
                     G[pn] += (self.gamma_b / mesh.hF) * np.einsum("q,q,qs->s", wf, pD, ps)
         return F, G

@@ -201,3 +201,64 @@ def test_broken_pressure_solution_is_exact(dim, r, k, form):
     A = slab_matrix(ops, Tm, tau, form)
     b = slab_rhs(ops, Tm, tau, t_prev, prob, state, form)
     assert np.max(np.abs(A @ Xs - b) / (abs(A) @ np.abs(Xs) + np.abs(b))) < 1e-12
+
+
+ANISO = {2: np.array([[1.3, 0.45], [0.45, 0.8]]),
+         3: np.array([[1.3, 0.45, -0.2], [0.45, 0.8, 0.3], [-0.2, 0.3, 1.1]])}
+
+
+@pytest.mark.parametrize("pressure,r", [("cont", 2), ("disc", 3)])
+@pytest.mark.parametrize("form", ["3.1", "B.1"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_anisotropic_permeability_solution_is_exact(dim, form, pressure, r):
+    """A full permeability tensor K (Eq. 1.1, off-diagonal entries nonzero)
+    with a pressure whose mixed derivatives do not vanish (x y, x y z): the
+    discrete-space solution satisfies the slab system to rounding, with
+    Dirichlet and Neumann faces for p.  This holds only if every place where
+    K enters agrees: (K grad p, grad xi), the fluxes (K grad p) . n of the
+    Nitsche (and, for the broken space, interior penalty) terms, the Neumann
+    flux -(K grad p) . n and the source -div(K grad p); a dropped off-diagonal
+    entry or a wrong row of K on a face leaves a residual of order one.  The
+    operator or the loads alone taken with the diagonal of K must fail."""
+    import sympy as sy
+    from oracle.problems import Problem
+    from oracle.slab import slab_rhs, interpolate_state
+    k = 1
+    X = sy.symbols("x0:%d" % dim, real=True)
+    t = sy.symbols("t", real=True)
+    T = sum(sy.Rational(1, j + 2) * t ** j for j in range(k + 1))
+    x, y = X[0], X[1]
+    z = X[2] if dim == 3 else sy.Integer(1)
+    u = [T * (x ** 2 * y - y * z + x), (1 - 2 * t) * (x * y + x ** 2 - sy.Rational(3, 10))]
+    if dim == 3:
+        u.append(T * (x * z + y * z - 1))
+    p = (2 - t) * (1 + x - y / 2 + x * y + (y * z / 3 if dim == 3 else 0))
+    prob = Problem("poly", dim, 1.0, 0.9, 0.5, u, p)
+    lo, hi = [0.0, 0.0, 0.0][:dim], [1.0, 2.0, 0.5][:dim]
+    mesh = BoxMesh(dim, lo, hi, [2] * dim)
+    K = ANISO[dim]
+    bcu = [0, 1, 0, 0, 1, 0][:2 * dim]
+    bcp = [1, 0, 0, 1, 0, 0][:2 * dim]
+    Tm = Temporal(k)
+    tau, t_prev = 0.1, 0.3
+
+    def ops_for(Kc):
+        mat = Material(1.0, 0.9, 0.5, 2.0 * np.ones(mesh.ncell), np.ones(mesh.ncell),
+                       np.broadcast_to(Kc, (mesh.ncell, dim, dim)).copy())
+        return SpatialOps(mesh, r, mat, bcu, bcp, pressure)
+
+    def residual(K_matrix, K_data):
+        # the operator assembled with K_matrix, the loads (source, fluxes,
+        # Dirichlet data terms) with K_data
+        opsA, opsb = ops_for(K_matrix), ops_for(K_data)
+        state = interpolate_state(opsb, prob, t_prev)
+        Xs = np.concatenate([np.concatenate(interpolate_state(opsb, prob, t_prev + 0.5 * tau * (ta + 1.0)))
+                             for ta in Tm.t])
+        A = slab_matrix(opsA, Tm, tau, form)
+        b = slab_rhs(opsb, Tm, tau, t_prev, prob, state, form)
+        return np.max(np.abs(A @ Xs - b) / (abs(A) @ np.abs(Xs) + np.abs(b)))
+
+    D = np.diag(np.diag(K))
+    assert residual(K, K) < 1e-12
+    assert residual(D, K) > 1e-6  # the operator's off-diagonal terms matter
+    assert residual(K, D) > 1e-6  # and so do the loads'
