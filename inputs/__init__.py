@@ -24,6 +24,39 @@ def case(name, seed=SEED):
     if name == "c1_2d_q2_k1_32":  # the 8x8 recipe on 32x32, 4 levels (1,089 fine patches)
         return dict(dim=2, n=32, levels=4, r=2, k=1, tau=0.01, slabs=2, rho=1.0, alpha=1.0, c0=1.0,
                     lam=1.0, mu=1.0, kappa=1.0, problem="sin", tol=1e-10)
+    if name == "bd_2d_q2_k1_8":  # nonzero boundary data: Dirichlet and Neumann faces, random cells
+        return dict(dim=2, n=8, levels=3, r=2, k=1, tau=0.01, slabs=2, rho=1.0, alpha=0.9, c0=0.5,
+                    lo=[0.0, -0.25], hi=[1.0, 1.25], lam_cell=np.exp(rng.uniform(0.0, 1.5, 64)),
+                    mu_cell=np.exp(rng.uniform(-0.5, 0.5, 64)), kappa_cell=np.exp(rng.standard_normal(64)),
+                    bc_u=[0, 1, 0, 0], bc_p=[1, 0, 0, 0], problem="trace", tol=1e-10)
+    if name == "bd_2d_q3_k2_8":
+        return dict(dim=2, n=8, levels=3, r=3, k=2, tau=1e-3, slabs=2, rho=1.0, alpha=1.0, c0=1e-2,
+                    lam=3.0, mu=1.5, kappa_cell=np.exp(rng.standard_normal(64)),
+                    bc_u=[0, 0, 1, 0], bc_p=[0, 1, 0, 0], problem="trace", tol=1e-10)
+    if name == "bd_3d_q2_k1_4":
+        return dict(dim=3, n=4, levels=2, r=2, k=1, tau=1e-2, slabs=2, rho=1.0, alpha=0.5, c0=1.0,
+                    lam=2.0, mu=1.0, kappa=0.1, bc_u=[0, 1, 0, 0, 0, 1], bc_p=[1, 0, 0, 0, 0, 0],
+                    problem="trace", tol=1e-10)
+    if name == "bd_sin_neumann_2d_q2_k1_8":  # zero traces, Neumann data of the exact solution
+        return dict(dim=2, n=8, levels=3, r=2, k=1, tau=0.01, slabs=2, rho=1.0, alpha=1.0, c0=1.0,
+                    lam=1.0, mu=1.0, kappa=1.0, bc_u=[1, 0, 0, 1], bc_p=[0, 0, 1, 0], problem="sin", tol=1e-10)
+    if name in ("aniso_2d_q3_k2_8", "aniso_bd_2d_q2_k1_8", "aniso_3d_q2_k1_4"):
+        # a symmetric positive definite permeability tensor per cell, with
+        # off-diagonal entries as large as the diagonal ones (K = A A^T + 0.3 I)
+        dim = 3 if name.startswith("aniso_3d") else 2
+        n = 4 if dim == 3 else 8
+        A = rng.standard_normal((n ** dim, dim, dim))
+        K = np.einsum("cij,ckj->cik", A, A) + 0.3 * np.eye(dim)[None]
+        if name == "aniso_2d_q3_k2_8":
+            return dict(dim=2, n=8, levels=3, r=3, k=2, tau=1e-3, slabs=2, rho=1.0, alpha=1.0, c0=1e-2,
+                        lam=3.0, mu=1.5, K_cell=K, problem="sin", tol=1e-10)
+        if name == "aniso_bd_2d_q2_k1_8":
+            return dict(dim=2, n=8, levels=3, r=2, k=1, tau=0.01, slabs=2, rho=1.0, alpha=0.9, c0=0.5,
+                        lam=2.0, mu=1.0, K_cell=K, bc_u=[0, 1, 0, 0], bc_p=[1, 0, 0, 1], problem="trace",
+                        tol=1e-10)
+        return dict(dim=3, n=4, levels=2, r=2, k=1, tau=1e-2, slabs=2, rho=1.0, alpha=0.5, c0=1.0,
+                    lam=2.0, mu=1.0, K_cell=K, bc_u=[0, 0, 0, 1, 0, 0], bc_p=[0, 0, 0, 0, 1, 0],
+                    problem="trace", tol=1e-10)
     if name == "c2_2d_q3_k2_64":  # 2D 64x64, 5 levels, Q3/Q2, k=2, random materials
         lam = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
         mu = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
