@@ -63,6 +63,9 @@ def parse():
                    help="slab problem: Problem 3.1 (default) or Problem B.1 of Appendix B")
     p.add_argument("--fine-operator", default="auto", choices=["auto", "assembled", "matrix-free"],
                    help="operator of the finest level inside the mixed-precision V-cycle")
+    p.add_argument("--stream-shapes", default=None,
+                   help="pin the streaming patch apply's shape per level, 'level:stages,ctas_per_sm,tile;...' "
+                        "(default: the setup's autotuned shapes, printed in the roofline object)")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -341,6 +344,11 @@ def gpu_arm(args):
     t0 = time.perf_counter()
     S = make_solver(c, st.MIXED, stream, args.sweeps, args.form, args.fine_operator)
     setup_s = time.perf_counter() - t0
+    if args.stream_shapes:
+        for item in args.stream_shapes.split(";"):
+            lev, shape = item.split(":")
+            S.set_stream_shape(int(lev), *[int(v) for v in shape.split(",")])
+    shapes = {str(l): list(S.stream_shape(l)) for l in range(1, S.n_levels)}
     state = torch.zeros(S.n_state, dtype=torch.float64, device="cuda")
     S.initial_state(state)
     # slab 0 solution for the error against the oracle
@@ -435,7 +443,8 @@ def gpu_arm(args):
             "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
             "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"],
             "measured": "per-launch CUDA events on the solver stream over %d profiled slabs after the timed "
-                        "region (same kernels, eager launches)" % KP}
+                        "region (same kernels, eager launches)" % KP,
+            "stream_shapes": shapes}
     breakdown = {k: {"ms": v["ms"], "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-30),
                      "launches": v["launches"],
                      "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}

@@ -47,14 +47,28 @@ extern "C" {
 #define STFEM_ERR_OOM (-6)
 #define STFEM_ERR_TIMEOUT (-7) /* a bounded wait inside a kernel ran out (see stfem_set_wait_limit) */
 
-#define STFEM_BC_DIRICHLET 0 /* homogeneous Dirichlet, imposed by Nitsche's method */
-#define STFEM_BC_NEUMANN 1   /* natural condition; data from the problem id */
+/* Boundary conditions (Eq. 1.1, Sec. 3).  The data come from the problem id:
+ * DIRICHLET: imposed by Nitsche's method; the traces u_D, v_D = d_t u_D, p_D
+ *   are those of the problem's exact solution (zero for NONE, SIN, PULSE,
+ *   PAPER_EOC, PAPER_SUPERCONV; nonzero for TRACE), and the data terms
+ *   a_gamma(u_D, .), -alpha <v_D . n, .> and b_gamma(p_D, .) of Eq. 3.4 enter
+ *   the right-hand side.
+ * NEUMANN: natural condition with the traction t_N = -(sigma(u) - alpha p I) n
+ *   and the flux p_N = -(K grad p) . n of the exact solution (SIN, TRACE;
+ *   zero for NONE; PULSE: its top-face traction, zero flux).  PAPER_EOC and
+ *   PAPER_SUPERCONV take Dirichlet conditions on every face. */
+#define STFEM_BC_DIRICHLET 0
+#define STFEM_BC_NEUMANN 1
 
 #define STFEM_PROBLEM_NONE 0            /* f = g = 0, zero boundary data */
 #define STFEM_PROBLEM_SIN 1             /* u = phi sin t (1,..,1), p = phi cos t, phi = prod sin(pi x_i) */
 #define STFEM_PROBLEM_PULSE 2           /* 3D: traction (0,0,-sin(pi t/0.05)) on [0.75,1.25]^2 of the top face */
 #define STFEM_PROBLEM_PAPER_EOC 3       /* Eq. 5.1, omega_1 = omega_2 = pi (2D) */
 #define STFEM_PROBLEM_PAPER_SUPERCONV 4 /* Eq. 5.3, omega_1 = 40 pi, omega_2 = 10 pi (2D) */
+/* 2D and 3D, nonzero on the boundary: u = sin(2t + 1/2) Phi(x) (1, -0.7, 0.4),
+ * p = cos(t) Phi(x), Phi = prod_i cos(om_i x_i + be_i), om_i = 1 + i/2,
+ * be_i = 0.3 + 0.2 i (i = 0, 1, 2). */
+#define STFEM_PROBLEM_TRACE 5
 
 #define STFEM_FP64 0  /* every step in FP64 */
 #define STFEM_MIXED 1 /* V-cycle (level operators, patch inverses, transfers) in FP32 inside FP64 FGMRES */
@@ -90,8 +104,8 @@ typedef struct {
  *   jump of alpha div u, less its normal trace on Gamma_D^u, at t_{n-1}: the
  *   pressure row couples -C to U through Dt).  Its previous-slab coupling takes
  *   the volume part -alpha <div u^-, xi> alone plus the data term
- *   -alpha <u_D(t_{n-1}) . n, xi>_{Gamma_D^u}, which is zero for every built-in
- *   problem (all have homogeneous traces). */
+ *   -alpha <u_D(t_{n-1}) . n, xi>_{Gamma_D^u} (nonzero for STFEM_PROBLEM_TRACE
+ *   alone). */
 #define STFEM_FORM_PROBLEM_3_1 0
 #define STFEM_FORM_PROBLEM_B_1 1
 
@@ -114,16 +128,22 @@ typedef struct {
   int pressure;
 } stfem_degrees;
 
-/* Coefficients of Eq. 1.1 with isotropic C (lambda, mu) and K = kappa I.
+/* Coefficients of Eq. 1.1: isotropic C (lambda, mu) and the permeability K.
  * The *_cell arrays (host, may be NULL) give per-cell values on the finest
  * mesh, cells numbered lexicographically with x fastest; coarse cells take
- * the arithmetic mean of their children. */
+ * the arithmetic mean of their children (entry by entry for K).
+ * K_cell_host (may be NULL): K as a dim x dim tensor per cell (row-major,
+ * dim*dim values per cell), symmetric positive definite (STFEM_ERR_ARG
+ * otherwise); it replaces kappa and kappa_cell_host.  NULL: K = kappa I.
+ * With a tensor K the finest operator stays in the assembled form
+ * (stfem_set_fine_operator). */
 typedef struct {
   double rho, alpha, c0;
   double lambda, mu, kappa;
   const double *lambda_cell_host;
   const double *mu_cell_host;
   const double *kappa_cell_host;
+  const double *K_cell_host;
 } stfem_material;
 
 /* Boundary conditions per box face f = 2*axis + side (side 0: x_axis = lo,
@@ -224,12 +244,26 @@ int stfem_set_stream(stfem_h h, void *stream);
  * is the same in every CTA.  STFEM_ERR_ARG for max_ctas < 0. */
 int stfem_set_launch_cap(stfem_h h, int max_ctas);
 
+/* Ring shape of the streaming patch apply (Algorithm 4.1's local solves) on
+ * a V-cycle level l (1 .. n_levels-1) of a set-up handle: nst shared-memory
+ * stages per CTA, at most per_sm CTAs per multiprocessor, tile consecutive
+ * patches taken by a CTA per step.  stfem_gmg_setup picks each level's shape
+ * by timing candidates on the level's own inverses; the choice depends on
+ * timing, so two runs may pick differently.  get: the level's current shape
+ * (all 0 for a level that runs another patch kernel).  set: pins it
+ * (reproducible runs and profiles); STFEM_ERR_ARG for a level without the
+ * streaming kernel, 2 <= nst <= 12, 1 <= per_sm <= 8, 1 <= tile <= 64
+ * violated, or a shape whose shared memory exceeds a CTA's.  The shape
+ * changes only how patches are spread over CTAs, never a result. */
+int stfem_get_stream_shape(stfem_h h, int level, int *nst, int *per_sm, int *tile);
+int stfem_set_stream_shape(stfem_h h, int level, int nst, int per_sm, int tile);
+
 /* Operator of the finest level inside the mixed-precision V-cycle (its FP32
  * residuals, Eq. 4.7).  ASSEMBLED: the node-block form of the assembled
  * spatial matrices; MATRIX_FREE: cell by cell from the unit-coefficient
  * element matrices of the uniform mesh and the per-cell coefficients (no
- * global matrix is read; Taylor-Hood pressure only, else the assembled form
- * is kept); AUTO (default): ASSEMBLED, the faster form on GB300 at the
+ * global matrix is read; Taylor-Hood pressure and K = kappa I only, else the
+ * assembled form is kept); AUTO (default): ASSEMBLED, the faster form on GB300 at the
  * workloads' degrees (measured: the assembled node-block product takes about
  * half the time of the cell-by-cell one).  The two forms
  * differ by FP32 rounding.  The FP64 products (FGMRES, true residuals) and
@@ -324,8 +358,10 @@ int stfem_initial_state(stfem_h h, double *state);
 /* Right-hand side F_n of slab n (0-based, I_n = (t0 + n tau, t0 + (n+1) tau])
  * from the problem's data at the Radau nodes and the previous end state
  * prev_state (device, 2R+S) (Eq. 3.5, Eq. 4.5; for STFEM_FORM_PROBLEM_B_1 the
- * pressure rows take the coupling of Problem B.1, see stfem_degrees).
- * rhs: device, n_slab. */
+ * pressure rows take the coupling of Problem B.1, see stfem_degrees).  The
+ * loads F_gamma, G_gamma (Eq. 3.4) hold the volume sources and the boundary
+ * data of the problem (see STFEM_BC_*), integrated with the cell and face
+ * rules of the matrices.  rhs: device, n_slab. */
 int stfem_slab_rhs(stfem_h h, int slab, const double *prev_state, double *rhs);
 
 /* March n_slabs slabs from slab index first_slab: for each slab, build F_n,

@@ -21,7 +21,7 @@ OK = 0
 NOT_CONVERGED = 1
 ERR_ARG, ERR_CUDA, ERR_SINGULAR_PATCH, ERR_BREAKDOWN, ERR_STATE, ERR_OOM, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 DIRICHLET, NEUMANN = 0, 1
-PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPERCONV = 0, 1, 2, 3, 4
+PROBLEM_NONE, PROBLEM_SIN, PROBLEM_PULSE, PROBLEM_PAPER_EOC, PROBLEM_PAPER_SUPERCONV, PROBLEM_TRACE = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
 HF_MEASURE, HF_LENGTH = 0, 1
 COARSE_GALERKIN, COARSE_REDISCRETIZE = 0, 1
@@ -56,7 +56,7 @@ class Material(C.Structure):
     _fields_ = [("rho", C.c_double), ("alpha", C.c_double), ("c0", C.c_double),
                 ("lambda_", C.c_double), ("mu", C.c_double), ("kappa", C.c_double),
                 ("lambda_cell_host", C.POINTER(C.c_double)), ("mu_cell_host", C.POINTER(C.c_double)),
-                ("kappa_cell_host", C.POINTER(C.c_double))]
+                ("kappa_cell_host", C.POINTER(C.c_double)), ("K_cell_host", C.POINTER(C.c_double))]
 
 
 class BCs(C.Structure):
@@ -104,6 +104,8 @@ def _load():
         "stfem_vcycle": [P, P, P],
         "slab_solve": [P, P, P, D, I, I, pI, pD, pD],
         "stfem_set_launch_cap": [P, I],
+        "stfem_get_stream_shape": [P, I, pI, pI, pI],
+        "stfem_set_stream_shape": [P, I, I, I, I],
         "stfem_set_patch_kernel": [P, I],
         "stfem_set_fine_operator": [P, I],
         "stfem_set_wait_limit": [P, D],
@@ -184,7 +186,8 @@ class Problem:
     def __init__(self, dim, n_cells, n_levels, r, k, tau, lo=None, hi=None, rho=1.0, alpha=1.0, c0=1.0,
                  lam=1.0, mu=1.0, kappa=1.0, lam_cell=None, mu_cell=None, kappa_cell=None,
                  bc_u=None, bc_p=None, problem=PROBLEM_NONE, t0=0.0, hf_mode=HF_MEASURE,
-                 coarse_op=COARSE_GALERKIN, form=FORM_PROBLEM_3_1, pressure=PRESSURE_CONTINUOUS):
+                 coarse_op=COARSE_GALERKIN, form=FORM_PROBLEM_3_1, pressure=PRESSURE_CONTINUOUS,
+                 K_cell=None):
         self.dim = dim
         lo = list(lo) if lo is not None else [0.0] * dim
         hi = list(hi) if hi is not None else [1.0] * dim
@@ -202,7 +205,9 @@ class Problem:
             self._cells.append(a)
             return _dptr(a)
 
-        self.mat = Material(rho, alpha, c0, lam, mu, kappa, arr(lam_cell), arr(mu_cell), arr(kappa_cell))
+        # K_cell: permeability tensors, shape (n_cells, dim, dim), or None (K = kappa I)
+        self.mat = Material(rho, alpha, c0, lam, mu, kappa, arr(lam_cell), arr(mu_cell), arr(kappa_cell),
+                            arr(None if K_cell is None else np.reshape(K_cell, -1)))
         bc_u = list(bc_u) if bc_u is not None else [DIRICHLET] * (2 * dim)
         bc_p = list(bc_p) if bc_p is not None else [DIRICHLET] * (2 * dim)
         self.bcs = BCs((C.c_int * 6)(*(bc_u + [0] * (6 - len(bc_u)))),
@@ -303,6 +308,7 @@ class Solver:
         n_slab, n_state = C.c_longlong(), C.c_longlong()
         self._check(lib.stfem_level_info(self.h, -1, C.byref(n_slab), C.byref(n_state), None, None))
         self.n_slab, self.n_state = n_slab.value, n_state.value
+        self.n_levels = prob.mesh.n_levels
 
     def _check(self, rc):
         if rc < 0:
@@ -373,6 +379,17 @@ class Solver:
     def set_launch_cap(self, max_ctas):
         """At most max_ctas CTAs per persistent patch-apply launch (0: as many as fit)."""
         self._check(lib.stfem_set_launch_cap(self.h, int(max_ctas)))
+
+    def stream_shape(self, level):
+        """(stages, CTAs per SM, patch tile) of the streaming patch apply on a
+        level; (0, 0, 0) for a level that runs another patch kernel."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib.stfem_get_stream_shape(self.h, int(level), C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_stream_shape(self, level, nst, per_sm, tile):
+        """Pins the streaming patch apply's shape on a level."""
+        self._check(lib.stfem_set_stream_shape(self.h, int(level), int(nst), int(per_sm), int(tile)))
 
     def set_patch_kernel(self, choice):
         """PATCH_KERNEL_AUTO (default), PATCH_KERNEL_STREAM or PATCH_KERNEL_WIDE."""

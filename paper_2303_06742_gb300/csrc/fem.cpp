@@ -194,6 +194,8 @@ Coef coarsen(const Coef &f, const Box &fb) {
   c.lam.assign(ncc, 0.0);
   c.mu.assign(ncc, 0.0);
   c.kap.assign(ncc, 0.0);
+  const int dd = fb.dim * fb.dim;
+  if (!f.K.empty()) c.K.assign((size_t)ncc * dd, 0.0);
   const int nchild = 1 << fb.dim;
   for (int z = 0; z < nc[2]; ++z)
     for (int y = 0; y < nc[1]; ++y)
@@ -206,6 +208,8 @@ Coef coarsen(const Coef &f, const Box &fb) {
           c.lam[ci] += f.lam[fi] / nchild;
           c.mu[ci] += f.mu[fi] / nchild;
           c.kap[ci] += f.kap[fi] / nchild;
+          if (!f.K.empty())
+            for (int e = 0; e < dd; ++e) c.K[(size_t)ci * dd + e] += f.K[(size_t)fi * dd + e] / nchild;
         }
       }
   return c;
@@ -543,7 +547,16 @@ void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, 
           if (cn[ax] < 0 || cn[ax] >= b.n[ax]) continue;
           const long nb_cell = flatten(cn, b.n);
           const long lower = side ? cell : nb_cell, upper = side ? nb_cell : cell;
+          // (K grad psi) . e_ax = sum_b K[ax][b] d_b psi on either side
           const double ka = L.coef.kap[lower], kb = L.coef.kap[upper];
+          const double *Ka = L.coef.K.empty() ? nullptr : &L.coef.K[(size_t)lower * d * d + ax * d];
+          const double *Kb = L.coef.K.empty() ? nullptr : &L.coef.K[(size_t)upper * d * d + ax * d];
+          auto kflux = [&](const double *g, const double *Krow, double kap) {
+            if (!Krow) return kap * g[ax];
+            double v = 0.0;
+            for (int bb = 0; bb < d; ++bb) v += Krow[bb] * g[bb];
+            return v;
+          };
           const FaceRef &F = fr[ax];
           const int nq = F.a.npts;
           // this row's test function is in the lower (side 1) or upper cell
@@ -553,11 +566,11 @@ void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, 
             const double *ga = &F.a.dphi[(size_t)q * np * d], *gb = &F.b.dphi[(size_t)q * np * d];
             // test values: jump and flux average of psi_row
             const double jr = side ? pa[s2] : -pb[s2];
-            const double fr_ = side ? 0.5 * ka * ga[s2 * d + ax] : 0.5 * kb * gb[s2 * d + ax];
+            const double fr_ = side ? 0.5 * kflux(&ga[s2 * d], Ka, ka) : 0.5 * kflux(&gb[s2 * d], Kb, kb);
             for (int t2 = 0; t2 < np; ++t2) {
               // trial functions of the lower cell, then of the upper cell
               const double js[2] = {pa[t2], -pb[t2]};
-              const double fs[2] = {0.5 * ka * ga[t2 * d + ax], 0.5 * kb * gb[t2 * d + ax]};
+              const double fs[2] = {0.5 * kflux(&ga[t2 * d], Ka, ka), 0.5 * kflux(&gb[t2 * d], Kb, kb)};
               const long cl[2] = {lower, upper};
               for (int k = 0; k < 2; ++k) {
                 const double v = W * (-fs[k] * jr - js[k] * fr_ + (gam / b.hF) * js[k] * jr);
@@ -599,6 +612,27 @@ void expand_disc(Level &L, const NodeMat &UU, const std::vector<double> &cellC, 
 }
 
 } // namespace
+
+void face_tables(const Level &L, FaceTables *out) {
+  const Box &b = L.box;
+  const int d = b.dim, r = L.r;
+  FaceTables &T = *out;
+  T = FaceTables();
+  for (int f = 0; f < 2 * d; ++f) {
+    std::vector<double> w;
+    auto pts = face_points(b, r + 2, f / 2, f % 2, &w);
+    RefData FU = ref_data(L.U, b, pts), FP = L.pdisc ? ref_data_disc(r - 1, b, pts) : ref_data(L.P, b, pts);
+    T.npts = (int)pts.size();
+    T.nu = FU.nloc;
+    T.np = FP.nloc;
+    for (const auto &x : pts) T.x.insert(T.x.end(), x.begin(), x.end());
+    T.w.insert(T.w.end(), w.begin(), w.end());
+    T.U.insert(T.U.end(), FU.phi.begin(), FU.phi.end());
+    T.dU.insert(T.dU.end(), FU.dphi.begin(), FU.dphi.end());
+    T.P.insert(T.P.end(), FP.phi.begin(), FP.phi.end());
+    T.dP.insert(T.dP.end(), FP.dphi.begin(), FP.dphi.end());
+  }
+}
 
 Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int form, int pressure) {
   Level L;
@@ -660,9 +694,29 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
         Mp[rr * np + s] += W * pp[rr] * pp[s];
       }
   }
+  // a permeability tensor per cell: (K grad psi_s, grad psi_r) =
+  // sum_ab K_ab BvK[a d + b], BvK[a d + b][r][s] = (d_b psi_s, d_a psi_r)
+  const bool ktensor = !coef.K.empty();
+  std::vector<double> BvK;
+  if (ktensor) {
+    BvK.assign((size_t)d * d * np * np, 0.0);
+    for (int q = 0; q < nq; ++q) {
+      const double W = wq[q];
+      const double *gp = &RP.dphi[(size_t)q * np * d];
+      for (int a = 0; a < d; ++a)
+        for (int bb = 0; bb < d; ++bb)
+          for (int rr = 0; rr < np; ++rr)
+            for (int s = 0; s < np; ++s)
+              BvK[((size_t)(a * d + bb) * np + rr) * np + s] += W * gp[s * d + bb] * gp[rr * d + a];
+    }
+  }
   // face matrices, per face id
+  // BK[b] (tensor K only): the face consistency terms of B_gamma split by
+  // the derivative direction b: with n = +-e_ax, (K grad psi) . n =
+  // n_ax sum_b K[ax][b] d_b psi, so the terms are sum_b K[ax][b] BK[b]
   struct FaceMats {
     std::vector<double> Kmu, Klam, Kpen, C, B, Bpen;
+    std::vector<double> BK[3];
   };
   std::vector<FaceMats> F(2 * d);
   for (int ax = 0; ax < d; ++ax)
@@ -712,6 +766,11 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
             for (int a = 0; a < d; ++a) dns += gp[s * d + a] * n[a];
             fm.B[rr * np + s] += -W * (dns * pp[rr] + pp[s] * dnr);
             fm.Bpen[rr * np + s] += (gam_b / b.hF) * W * pp[s] * pp[rr];
+            if (ktensor)
+              for (int bb = 0; bb < d; ++bb) {
+                if (fm.BK[bb].empty()) fm.BK[bb].assign((size_t)np * np, 0.0);
+                fm.BK[bb][rr * np + s] += -W * n[ax] * (gp[s * d + bb] * pp[rr] + pp[s] * gp[rr * d + bb]);
+              }
           }
         }
       }
@@ -778,9 +837,18 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
     const long c = cells[ci];
     unflatten(c, b.n, d, cm);
     const double lam = coef.lam[c], mu = coef.mu[c], kap = coef.kap[c];
+    const double *Kc = ktensor ? &coef.K[(size_t)c * d * d] : nullptr;
     for (int i = 0; i < du * du; ++i) Ke[i] = lam * Klam[i] + mu * Kmu[i];
     for (int i = 0; i < np * du; ++i) Ce[i] = Cv[i];
-    for (int i = 0; i < np * np; ++i) Be[i] = kap * Bv[i];
+    if (Kc) {
+      for (int i = 0; i < np * np; ++i) {
+        double v = 0.0;
+        for (int e = 0; e < d * d; ++e) v += Kc[e] * BvK[(size_t)e * np * np + i];
+        Be[i] = v;
+      }
+    } else {
+      for (int i = 0; i < np * np; ++i) Be[i] = kap * Bv[i];
+    }
     for (int ax = 0; ax < d; ++ax)
       for (int side = 0; side < 2; ++side) {
         bool on = side ? (cm[ax] == b.n[ax] - 1) : (cm[ax] == 0);
@@ -790,8 +858,17 @@ Level assemble_level(const Box &b, int r, const Coef &coef, const BCs &bc, int f
           for (int i = 0; i < du * du; ++i) Ke[i] += lam * F[f].Klam[i] + mu * F[f].Kmu[i] + F[f].Kpen[i];
           for (int i = 0; i < np * du; ++i) Ce[i] += F[f].C[i];
         }
-        if (bc.bc_p[f] == 0)
-          for (int i = 0; i < np * np; ++i) Be[i] += kap * F[f].B[i] + F[f].Bpen[i];
+        if (bc.bc_p[f] == 0) {
+          if (Kc) {
+            for (int i = 0; i < np * np; ++i) {
+              double v = F[f].Bpen[i];
+              for (int bb = 0; bb < d; ++bb) v += Kc[ax * d + bb] * F[f].BK[bb][i];
+              Be[i] += v;
+            }
+          } else {
+            for (int i = 0; i < np * np; ++i) Be[i] += kap * F[f].B[i] + F[f].Bpen[i];
+          }
+        }
       }
     // global lattice coordinates of local nodes
     int gu_[216][3], gp_[216][3];
@@ -2160,7 +2237,7 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
     }
   }
   const int pid = bcs->problem;
-  if (pid < 0 || pid > 4 || (pid == STFEM_PROBLEM_PULSE && d != 3) ||
+  if (pid < 0 || pid > STFEM_PROBLEM_TRACE || (pid == STFEM_PROBLEM_PULSE && d != 3) ||
       ((pid == STFEM_PROBLEM_PAPER_EOC || pid == STFEM_PROBLEM_PAPER_SUPERCONV) && d != 2)) {
     *err = "unsupported problem id for this dimension";
     return STFEM_ERR_ARG;
@@ -2174,8 +2251,8 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
         *err = "boundary condition flags must be 0 or 1";
         return STFEM_ERR_ARG;
       }
-      if (pid != STFEM_PROBLEM_NONE && pid != STFEM_PROBLEM_PULSE && (bc.bc_u[f] || bc.bc_p[f])) {
-        *err = "manufactured problems need Dirichlet conditions on every face";
+      if ((pid == STFEM_PROBLEM_PAPER_EOC || pid == STFEM_PROBLEM_PAPER_SUPERCONV) && (bc.bc_u[f] || bc.bc_p[f])) {
+        *err = "the problems of Eq. 5.1 and Eq. 5.3 need Dirichlet conditions on every face";
         return STFEM_ERR_ARG;
       }
     }
@@ -2195,6 +2272,32 @@ int build_hierarchy(const stfem_mesh *mesh, const stfem_degrees *deg, const stfe
     c.lam[i] = mat->lambda_cell_host ? mat->lambda_cell_host[i] : mat->lambda;
     c.mu[i] = mat->mu_cell_host ? mat->mu_cell_host[i] : mat->mu;
     c.kap[i] = mat->kappa_cell_host ? mat->kappa_cell_host[i] : mat->kappa;
+  }
+  if (mat->K_cell_host) {
+    // a symmetric positive definite tensor per cell (Sylvester's criterion)
+    const int dd = d * d;
+    c.K.assign(mat->K_cell_host, mat->K_cell_host + (size_t)fine.ncell * dd);
+    for (long i = 0; i < fine.ncell; ++i) {
+      const double *k = &c.K[(size_t)i * dd];
+      double scale = 0.0, tr = 0.0;
+      for (int e = 0; e < dd; ++e) scale = std::max(scale, std::fabs(k[e]));
+      bool ok = std::isfinite(scale) && scale > 0.0;
+      for (int a = 0; a < d && ok; ++a)
+        for (int b2 = a + 1; b2 < d; ++b2) ok = ok && std::fabs(k[a * d + b2] - k[b2 * d + a]) <= 1e-12 * scale;
+      const double m1 = k[0], m2 = k[0] * k[d + 1] - k[1] * k[d];
+      ok = ok && m1 > 0.0 && m2 > 0.0;
+      if (ok && d == 3) {
+        const double m3 = k[0] * (k[4] * k[8] - k[5] * k[7]) - k[1] * (k[3] * k[8] - k[5] * k[6]) +
+                          k[2] * (k[3] * k[7] - k[4] * k[6]);
+        ok = m3 > 0.0;
+      }
+      if (!ok) {
+        *err = "K_cell_host: the permeability of every cell must be a symmetric positive definite tensor";
+        return STFEM_ERR_ARG;
+      }
+      for (int a = 0; a < d; ++a) tr += k[a * d + a];
+      c.kap[i] = tr / d;
+    }
   }
   boxes[nlev - 1] = fine;
   coefs[nlev - 1] = c;

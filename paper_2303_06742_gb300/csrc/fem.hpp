@@ -62,6 +62,8 @@ Box make_box(int dim, const double *lo, const double *hi, const int *n, int hf_m
 struct Coef {
   double rho = 1, alpha = 1, c0 = 1;
   std::vector<double> lam, mu, kap; // per cell of the level
+  // permeability tensor per cell (dim x dim, row-major); empty: K = kap I
+  std::vector<double> K;
 };
 Coef coarsen(const Coef &fine, const Box &fine_box);
 
@@ -124,6 +126,20 @@ struct Level {
 };
 
 Level assemble_level(const Box &b, int r, const Coef &c, const BCs &bc, int form = 0, int pressure = 0);
+
+// Basis data of a level's two spaces at the quadrature points of each face
+// f = 2 * axis + side of a cell (Gauss-Legendre with r + 2 points per
+// direction, as for the matrices), for the boundary data terms of Eq. 3.4.
+// Arrays are face-major: reference points x [f][pt][3], weights w [f][pt]
+// (the face measure included), displacement values U [f][pt][nu] and
+// physical gradients dU [f][pt][nu][d], and the same (P, dP, np local
+// functions) for the pressure space, broken or continuous.  Local functions
+// are numbered as in the cell loads.
+struct FaceTables {
+  int npts = 0, nu = 0, np = 0;
+  std::vector<double> x, w, U, dU, P, dP;
+};
+void face_tables(const Level &L, FaceTables *out);
 // Embedding of the broken P_m space of the coarse box into that of the fine
 // box (nested; fine rows, coarse columns).
 struct CSR;

@@ -16,14 +16,70 @@ __device__ void node_coord(const GeomDev &g, int deg, const int *dims, const dou
   }
 }
 
-// Built-in manufactured solutions (homogeneous on the boundary of the unit box)
-// and their sources rho f = rho u_tt - div sigma(u) + alpha grad p,
-// g = c0 p_t + alpha div u_t - kappa lap p (Eq. 1.1), derived by hand.
+// Spatial factor of the TRACE problem, Phi(x) = prod_i cos(om_i x_i + be_i)
+// with om_i = 1 + i/2, be_i = 0.3 + 0.2 i: its value, gradient and Hessian.
+__device__ void trace_phi(int d, const double *x, double *phi, double *dphi, double H[3][3]) {
+  double c[3], s[3], om[3];
+  for (int i = 0; i < d; ++i) {
+    om[i] = 1.0 + 0.5 * i;
+    const double a = om[i] * x[i] + 0.3 + 0.2 * i;
+    c[i] = cos(a);
+    s[i] = sin(a);
+  }
+  double f = 1.0;
+  for (int i = 0; i < d; ++i) f *= c[i];
+  *phi = f;
+  for (int a = 0; a < d; ++a) {
+    double g = -om[a] * s[a];
+    for (int i = 0; i < d; ++i)
+      if (i != a) g *= c[i];
+    dphi[a] = g;
+    for (int b = 0; b < d; ++b) {
+      double h;
+      if (a == b) {
+        h = -om[a] * om[a] * f;
+      } else {
+        h = om[a] * om[b] * s[a] * s[b];
+        for (int i = 0; i < d; ++i)
+          if (i != a && i != b) h *= c[i];
+      }
+      H[a][b] = h;
+    }
+  }
+}
+
+// time factor and weights of the TRACE problem's displacement
+__device__ inline double trace_T(double t) { return sin(2.0 * t + 0.5); }
+__device__ inline double trace_T1(double t) { return 2.0 * cos(2.0 * t + 0.5); }
+__device__ inline double trace_T2(double t) { return -4.0 * sin(2.0 * t + 0.5); }
+__device__ inline double trace_w(int c) { return c == 0 ? 1.0 : (c == 1 ? -0.7 : 0.4); }
+
+// sum_ab K_ab H_ab over the first d axes (K: 3 x 3 row-major)
+__device__ inline double k_contract(int d, const double *K, const double H[3][3]) {
+  double v = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) v += K[a * 3 + b] * H[a][b];
+  return v;
+}
+
+// Built-in manufactured solutions and their sources
+// rho f = rho u_tt - div sigma(u) + alpha grad p,
+// g = c0 p_t + alpha div u_t - div(K grad p) (Eq. 1.1), derived by hand, with
+// -div(K grad p) = -sum_ab K_ab d_a d_b p for K constant on the cell.  All
+// but TRACE vanish on the boundary of the unit box.
 __device__ void dev_fields(const ProbDev &P, const double *x, double t, double *u, double *v, double *p) {
   const int d = P.dim;
   for (int i = 0; i < 3; ++i) u[i] = v[i] = 0.0;
   *p = 0.0;
-  if (P.id == STFEM_PROBLEM_SIN) {
+  if (P.id == STFEM_PROBLEM_TRACE) {
+    double f, df[3], H[3][3];
+    trace_phi(d, x, &f, df, H);
+    for (int i = 0; i < d; ++i) {
+      u[i] = trace_w(i) * trace_T(t) * f;
+      v[i] = trace_w(i) * trace_T1(t) * f;
+    }
+    *p = cos(t) * f;
+  } else if (P.id == STFEM_PROBLEM_SIN) {
     double phi = 1.0;
     for (int i = 0; i < d; ++i) phi *= sin(M_PI * x[i]);
     for (int i = 0; i < d; ++i) {
@@ -51,12 +107,29 @@ __device__ void dev_fields(const ProbDev &P, const double *x, double t, double *
   }
 }
 
-__device__ void dev_source(const ProbDev &P, const double *x, double t, double lam, double mu, double kap, double *rf,
-                           double *g) {
+__device__ void dev_source(const ProbDev &P, const double *x, double t, double lam, double mu, const double *K,
+                           double *rf, double *g) {
   const int d = P.dim;
   for (int i = 0; i < 3; ++i) rf[i] = 0.0;
   *g = 0.0;
-  if (P.id == STFEM_PROBLEM_SIN) {
+  if (P.id == STFEM_PROBLEM_TRACE) {
+    // u_b = w_b T Phi: div sigma(u)_b = mu lap u_b + (mu + lam) d_b div u
+    double f, df[3], H[3][3];
+    trace_phi(d, x, &f, df, H);
+    double lap = 0.0, divw = 0.0;
+    for (int a = 0; a < d; ++a) {
+      lap += H[a][a];
+      divw += trace_w(a) * df[a];
+    }
+    const double T = trace_T(t), T1 = trace_T1(t), T2 = trace_T2(t);
+    for (int b = 0; b < d; ++b) {
+      double gd = 0.0; // d_b sum_a w_a d_a Phi
+      for (int a = 0; a < d; ++a) gd += trace_w(a) * H[a][b];
+      rf[b] = P.rho * trace_w(b) * T2 * f - mu * trace_w(b) * T * lap - (mu + lam) * T * gd +
+              P.alpha * cos(t) * df[b];
+    }
+    *g = -P.c0 * sin(t) * f + P.alpha * T1 * divw - cos(t) * k_contract(d, K, H);
+  } else if (P.id == STFEM_PROBLEM_SIN) {
     double s[3], c[3];
     for (int i = 0; i < d; ++i) {
       s[i] = sin(M_PI * x[i]);
@@ -89,7 +162,19 @@ __device__ void dev_source(const ProbDev &P, const double *x, double t, double l
     }
     double div = 0.0;
     for (int j = 0; j < d; ++j) div += dphi[j];
-    *g = -P.c0 * phi * sin(t) + P.alpha * cos(t) * div + kap * d * pi2 * phi * cos(t);
+    double H[3][3]; // Hessian of phi
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        if (i == j) {
+          H[i][j] = -pi2 * phi;
+        } else {
+          double pr = pi2 * c[i] * c[j];
+          for (int k = 0; k < d; ++k)
+            if (k != i && k != j) pr *= s[k];
+          H[i][j] = pr;
+        }
+      }
+    *g = -P.c0 * phi * sin(t) + P.alpha * cos(t) * div - cos(t) * k_contract(d, K, H);
   } else if (P.id == STFEM_PROBLEM_PAPER_EOC) {
     const double w1 = M_PI, w2 = M_PI;
     const double T0 = sin(w1 * t * t), T1 = 2.0 * w1 * t * cos(w1 * t * t),
@@ -99,7 +184,8 @@ __device__ void dev_source(const ProbDev &P, const double *x, double t, double l
     const double base = P.rho * T2 * psi + 2.0 * mu * w22 * T0 * psi + (mu + lam) * w22 * T0 * (psi - cc);
     rf[0] = base + P.alpha * T0 * w2 * cx * sy;
     rf[1] = base + P.alpha * T0 * w2 * sx * cy;
-    *g = P.c0 * T1 * psi + P.alpha * T1 * w2 * (cx * sy + sx * cy) + 2.0 * kap * w22 * T0 * psi;
+    const double H[3][3] = {{-w22 * psi, w22 * cc, 0.0}, {w22 * cc, -w22 * psi, 0.0}, {0.0, 0.0, 0.0}};
+    *g = P.c0 * T1 * psi + P.alpha * T1 * w2 * (cx * sy + sx * cy) - T0 * k_contract(2, K, H);
   } else if (P.id == STFEM_PROBLEM_PAPER_SUPERCONV) {
     const double w1 = 40.0 * M_PI, w2 = 10.0 * M_PI;
     const double X = x[0], Y = x[1];
@@ -111,8 +197,45 @@ __device__ void dev_source(const ProbDev &P, const double *x, double t, double l
     const double s1 = sin(w1 * t), s2 = sin(w2 * t), c2 = cos(w2 * t);
     rf[0] = 2.0 * P.rho * w1 * w1 * Ax * By * s1 + 2.0 * mu * (A2x * By + Ax * B2y) * s1 - 2.0 * P.alpha * A1x * By * s2;
     rf[1] = -2.0 * P.rho * w1 * w1 * Bx * Ay * s1 - 2.0 * mu * (B2x * Ay + Bx * A2y) * s1 - 2.0 * P.alpha * Ax * B1y * s2;
-    *g = -2.0 * P.c0 * w2 * Ax * By * c2 + 2.0 * kap * (A2x * By + Ax * B2y) * s2;
+    // p = -2 A(x) B(y) sin(w2 t): Hessian of the spatial factor -2 A B
+    const double H[3][3] = {{-2.0 * A2x * By, -2.0 * A1x * B1y, 0.0}, {-2.0 * A1x * B1y, -2.0 * Ax * B2y, 0.0},
+                            {0.0, 0.0, 0.0}};
+    *g = -2.0 * P.c0 * w2 * Ax * By * c2 - s2 * k_contract(2, K, H);
   }
+}
+
+// Gradients of the exact solution (SIN and TRACE): gu[b][a] = d_a u_b,
+// gp[a] = d_a p, and p, for the Neumann data of Eq. 3.4.
+__device__ void dev_grads(const ProbDev &P, const double *x, double t, double gu[3][3], double *gp, double *p) {
+  const int d = P.dim;
+  double f = 0.0, df[3] = {0.0, 0.0, 0.0}, tu = 0.0, tp = 0.0, w[3] = {1.0, 1.0, 1.0};
+  if (P.id == STFEM_PROBLEM_TRACE) {
+    double H[3][3];
+    trace_phi(d, x, &f, df, H);
+    tu = trace_T(t);
+    tp = cos(t);
+    for (int c = 0; c < d; ++c) w[c] = trace_w(c);
+  } else if (P.id == STFEM_PROBLEM_SIN) {
+    double s[3], c[3];
+    for (int i = 0; i < d; ++i) {
+      s[i] = sin(M_PI * x[i]);
+      c[i] = cos(M_PI * x[i]);
+    }
+    f = 1.0;
+    for (int i = 0; i < d; ++i) f *= s[i];
+    for (int a = 0; a < d; ++a) {
+      double g = M_PI * c[a];
+      for (int i = 0; i < d; ++i)
+        if (i != a) g *= s[i];
+      df[a] = g;
+    }
+    tu = sin(t);
+    tp = cos(t);
+  }
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) gu[b][a] = (a < d && b < d) ? w[b] * tu * df[a] : 0.0;
+  for (int a = 0; a < 3; ++a) gp[a] = a < d ? tp * df[a] : 0.0;
+  *p = tp * f;
 }
 
 // z-component of the traction t_N on the top face for the pulse problem
@@ -182,7 +305,7 @@ __global__ void k_src_eval(GeomDev g, ProbDev P, LoadTables L, int q, const doub
     x[k] = g.lo[k] + g.h[k] * (c + L.qx[qp * 3 + k]);
   }
   double rf[3], gg;
-  dev_source(P, x, tb, L.lam[cell], L.mu[cell], L.kap[cell], rf, &gg);
+  dev_source(P, x, tb, L.lam[cell], L.mu[cell], L.Kt + cell * 9, rf, &gg);
   double *o = src + i * 4;
   o[0] = rf[0];
   o[1] = rf[1];
@@ -264,4 +387,149 @@ __global__ void k_rhs(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double
     val += tc.W[b] * load;
   }
   out[i] = val;
+}
+
+// Boundary data terms of the loads (Eq. 3.4), added to the slab right-hand
+// side at every Radau node t_b (times W_b, as the volume loads):
+//   v-rows: -<t_N, psi> on Neumann faces of u; on Dirichlet faces of u the
+//           Nitsche terms of a_gamma(u_D, psi): -<u_D, sigma(psi) n>
+//           + gamma_a / h_F <u_D, psi>;
+//   p-rows: -alpha <v_D . n, xi> on Dirichlet faces of u; -<p_N, xi> on
+//           Neumann faces of p; on Dirichlet faces of p the terms of
+//           b_gamma(p_D, xi): -<p_D, (K grad xi) . n> + gamma_b / h_F <p_D, xi>;
+// and for Problem B.1 the previous-slab data term
+// -chi_b(-1) alpha <u_D(t_{n-1}) . n, xi> on Dirichlet faces of u.  One thread
+// per (node b, v- or p-row); it visits the cells holding the row's function
+// and their faces on the boundary (deterministic).
+__global__ void k_rhs_data(GeomDev g, ProbDev P, LoadTables L, int q, TimeCoef<double> tc, const double *chi,
+                           const double *tnode, double t_prev, double tau, long R, long S,
+                           double *__restrict__ out) {
+  const long nrow = R + S, ns = 2 * R + S;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)q * nrow) return;
+  const int b = (int)(i / nrow);
+  const long m = R + i % nrow;
+  const double tb = t_prev + 0.5 * tau * (tnode[b] + 1.0);
+  const int d = g.dim;
+  const bool vrow = m < 2 * R;
+  const bool trace = P.id == STFEM_PROBLEM_TRACE;
+  const bool exact_flux = trace || P.id == STFEM_PROBLEM_SIN;
+  const int nl = vrow ? L.nlu : L.nlp;
+  const int comp = vrow ? (int)((m - R) % d) : 0;
+  // the cells holding the row's function: a box of lattice cells, or the
+  // dof's own cell for the broken pressure space
+  int clo[3] = {0, 0, 0}, chi_[3] = {0, 0, 0}, a[3] = {0, 0, 0};
+  int deg = 1;
+  long own = -1;
+  if (!vrow && L.pdisc) {
+    own = (m - 2 * R) / L.nlp;
+    long t2 = own;
+    for (int k = 0; k < d; ++k) {
+      clo[k] = chi_[k] = (int)(t2 % g.n[k]);
+      t2 /= g.n[k];
+    }
+  } else {
+    deg = vrow ? g.r : g.r - 1;
+    const int *dims = vrow ? g.udims : g.pdims;
+    long t2 = vrow ? (m - R) / d : m - 2 * R;
+    for (int k = 0; k < d; ++k) {
+      a[k] = (int)(t2 % dims[k]);
+      t2 /= dims[k];
+      if (a[k] % deg == 0) {
+        clo[k] = max(a[k] / deg - 1, 0);
+        chi_[k] = min(a[k] / deg, g.n[k] - 1);
+      } else {
+        clo[k] = chi_[k] = a[k] / deg;
+      }
+    }
+  }
+  double acc = 0.0, acc0 = 0.0;
+  for (int cz = clo[2]; cz <= chi_[2]; ++cz)
+    for (int cy = clo[1]; cy <= chi_[1]; ++cy)
+      for (int cx = clo[0]; cx <= chi_[0]; ++cx) {
+        const int cc[3] = {cx, cy, cz};
+        const long cell = cx + (long)g.n[0] * (cy + (long)g.n[1] * cz);
+        int li = 0;
+        if (own >= 0) {
+          li = (int)((m - 2 * R) % L.nlp);
+        } else {
+          int stride = 1;
+          for (int k = 0; k < d; ++k) {
+            li += (a[k] - deg * cc[k]) * stride;
+            stride *= deg + 1;
+          }
+        }
+        const double lam = L.lam[cell], mu = L.mu[cell];
+        for (int f = 0; f < 2 * d; ++f) {
+          const int ax = f >> 1, side = f & 1;
+          if (cc[ax] != (side ? g.n[ax] - 1 : 0)) continue;
+          double n[3] = {0.0, 0.0, 0.0};
+          n[ax] = side ? 1.0 : -1.0;
+          // (K g) . n = n_ax sum_b K[ax][b] g_b
+          const double *Kn = L.Kt + cell * 9 + ax * 3;
+          const bool dir_u = P.bc_u[f] == 0, dir_p = P.bc_p[f] == 0;
+          if (vrow && (dir_u ? !trace : !exact_flux)) continue;
+          if (!vrow && !(dir_u && trace) && (dir_p ? !trace : !exact_flux)) continue;
+          for (int qq = 0; qq < L.nqd; ++qq) {
+            const long fq = (long)f * L.nqd + qq;
+            const double w = L.dfw[fq];
+            double x[3];
+            for (int k = 0; k < 3; ++k) x[k] = k < d ? g.lo[k] + g.h[k] * (cc[k] + L.dfx[fq * 3 + k]) : 0.0;
+            const double *gph = (vrow ? L.dfdU : L.dfdP) + (fq * nl + li) * d;
+            const double ph = (vrow ? L.dfU : L.dfP)[fq * nl + li];
+            if (vrow) {
+              if (!dir_u) {
+                double gu[3][3], gp[3], p;
+                dev_grads(P, x, tb, gu, gp, &p);
+                // t_N[c] = -(sigma(u) n)[c] + alpha p n[c]
+                double divu = 0.0, sn = 0.0;
+                for (int k = 0; k < d; ++k) divu += gu[k][k];
+                for (int k = 0; k < d; ++k) sn += mu * (gu[comp][k] + gu[k][comp]) * n[k];
+                sn += lam * divu * n[comp];
+                acc += -w * (-sn + P.alpha * p * n[comp]) * ph;
+              } else {
+                double u[3], v[3], p;
+                dev_fields(P, x, tb, u, v, &p);
+                // u_D . sigma(psi) n for psi = phi e_comp
+                double dn = 0.0, gdu = 0.0, un = 0.0;
+                for (int k = 0; k < d; ++k) {
+                  dn += gph[k] * n[k];
+                  gdu += gph[k] * u[k];
+                  un += u[k] * n[k];
+                }
+                const double usn = mu * (u[comp] * dn + n[comp] * gdu) + lam * gph[comp] * un;
+                acc += -w * usn + (P.gam_a / P.hF) * w * u[comp] * ph;
+              }
+            } else {
+              if (dir_u && trace) {
+                double u[3], v[3], p;
+                dev_fields(P, x, tb, u, v, &p);
+                double vn = 0.0;
+                for (int k = 0; k < d; ++k) vn += v[k] * n[k];
+                acc += -P.alpha * w * vn * ph;
+                if (P.b1) {
+                  dev_fields(P, x, t_prev, u, v, &p);
+                  double un = 0.0;
+                  for (int k = 0; k < d; ++k) un += u[k] * n[k];
+                  acc0 += -P.alpha * w * un * ph;
+                }
+              }
+              if (!dir_p && exact_flux) {
+                double gu[3][3], gp[3], p;
+                dev_grads(P, x, tb, gu, gp, &p);
+                double pN = 0.0;
+                for (int k = 0; k < d; ++k) pN += -n[ax] * Kn[k] * gp[k];
+                acc += -w * pN * ph;
+              } else if (dir_p && trace) {
+                double u[3], v[3], p;
+                dev_fields(P, x, tb, u, v, &p);
+                double dn = 0.0;
+                for (int k = 0; k < d; ++k) dn += n[ax] * Kn[k] * gph[k];
+                acc += -w * p * dn + (P.gam_b / P.hF) * w * p * ph;
+              }
+            }
+          }
+        }
+      }
+  out[(long)b * ns + m] += tc.W[b] * acc + chi[b] * acc0;
 }

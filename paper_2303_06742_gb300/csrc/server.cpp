@@ -27,7 +27,7 @@ namespace {
 struct Request {
   long long id = 0;
   stfem_request req{};
-  std::vector<double> lam, mu, kap; // copies of the per-cell arrays
+  std::vector<double> lam, mu, kap, K; // copies of the per-cell arrays
   long long footprint = 0;
   stfem_result info{};
   std::vector<double> end_state;
@@ -88,6 +88,7 @@ void run_request(stfem_server s, Request &R) {
   q.mat.lambda_cell_host = R.lam.empty() ? nullptr : R.lam.data();
   q.mat.mu_cell_host = R.mu.empty() ? nullptr : R.mu.data();
   q.mat.kappa_cell_host = R.kap.empty() ? nullptr : R.kap.data();
+  q.mat.K_cell_host = R.K.empty() ? nullptr : R.K.data();
   int status = STFEM_OK;
   cudaStream_t stream = nullptr;
   stfem_h h = nullptr;
@@ -163,6 +164,7 @@ bool setup_request(stfem_server s, const std::shared_ptr<Request> &Rp, Ready *ou
   q.mat.lambda_cell_host = R.lam.empty() ? nullptr : R.lam.data();
   q.mat.mu_cell_host = R.mu.empty() ? nullptr : R.mu.data();
   q.mat.kappa_cell_host = R.kap.empty() ? nullptr : R.kap.data();
+  q.mat.K_cell_host = R.K.empty() ? nullptr : R.K.data();
   Ready rd;
   rd.R = Rp;
   int status = STFEM_OK;
@@ -388,6 +390,8 @@ int stfem_server_submit(stfem_server s, const stfem_request *req, long long *id)
   if (req->mat.lambda_cell_host) R->lam.assign(req->mat.lambda_cell_host, req->mat.lambda_cell_host + ncell);
   if (req->mat.mu_cell_host) R->mu.assign(req->mat.mu_cell_host, req->mat.mu_cell_host + ncell);
   if (req->mat.kappa_cell_host) R->kap.assign(req->mat.kappa_cell_host, req->mat.kappa_cell_host + ncell);
+  if (req->mat.K_cell_host)
+    R->K.assign(req->mat.K_cell_host, req->mat.K_cell_host + ncell * req->mesh.dim * req->mesh.dim);
   const int rc = stfem_estimate_bytes(&req->mesh, &req->deg, &req->gmg, req->restart, &R->footprint);
   if (rc < 0) return rc;
   R->info.footprint = R->footprint;

@@ -112,8 +112,14 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-constexpr int STREAM_STAGES = 4;                    // most stages of the ring (runtime: nst)
+constexpr int STREAM_STAGES = 12;                   // most stages of the ring (runtime: nst)
 constexpr int STREAM_CHUNK = 16384;                 // bytes per shared-memory stage
+// Ring shapes {stages, CTAs per SM, patch tile} the autotuners time: shallow
+// rings with many CTAs per SM for levels with many patches, deep rings (up to
+// the whole of a patch's inverses in flight) with one or two CTAs per SM for
+// levels with a few patches per SM, where a CTA's own latency bounds the level.
+#define STREAM_SHAPE_CANDIDATES                                                                                    \
+  {{2, 5, 1}, {3, 4, 1}, {4, 3, 1}, {2, 5, 2}, {4, 3, 2}, {4, 3, 4}, {6, 3, 1}, {8, 2, 1}, {12, 1, 1}}
 // clock cycles a drain of copies in flight may wait (about 2 s at 2 GHz);
 // the other waits take the handle's limit (stfem_set_wait_limit)
 constexpr long long STREAM_WAIT_LIMIT = 4000000000LL;
@@ -1259,7 +1265,8 @@ int upload_level_matrix(stfem_h h, DLevel<T> &D, const stfem::Level &L, int q) {
 // matrices in FP32, the per-cell coefficients and the per-cell result buffer.
 int upload_matfree(stfem_h h, DLevel<float> &D, const stfem::Level &L) {
   const stfem::Level::Elem &E = L.elem;
-  if (L.pdisc || E.nu == 0) return 0;
+  // the cell-by-cell form covers the Taylor-Hood pair with K = kappa I
+  if (L.pdisc || E.nu == 0 || !L.coef.K.empty()) return 0;
   const int d = L.box.dim, nu = E.nu, np = E.np, du = nu * d;
   MfDev &A = D.mf;
   A.d = d;
@@ -1783,7 +1790,7 @@ void stream_shape(stfem_h h, const DLevel<T> &L, int *threads, size_t *smem, int
   const int rows = L.dc.nr * ((L.maxCs + VEC - 1) / VEC) + L.dc.nc * ((L.maxCs + VEC / 2 - 1) / (VEC / 2));
   const int nwc = std::max(1, (rows + 31) / 32);
   *threads = 32 * (nwc + 1);
-  *nst = dim == 2 ? 2 : STREAM_STAGES;
+  *nst = dim == 2 ? 2 : 4;
   int cap = dim == 2 ? 5 : 3;
   if (L.tune_nst > 0) {
     *nst = L.tune_nst;
@@ -1952,7 +1959,7 @@ int prepare_wide(stfem_h h, DLevel<T> &L) {
 template <typename T>
 int autotune_stream(stfem_h h, DLevel<T> &L) {
   if (L.form != 1 || L.tc || L.wide || L.npatch == 0) return 0;
-  static const int cand[][3] = {{2, 5, 1}, {3, 4, 1}, {4, 3, 1}, {2, 5, 2}, {4, 3, 2}, {4, 3, 4}};
+  static const int cand[][3] = STREAM_SHAPE_CANDIDATES;
   cudaStream_t ts = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
@@ -2957,10 +2964,33 @@ int build_load_tables(stfem_h h) {
   CKR(upload(h, &p, fphiU)); lt.fphiU = p;
   CKR(upload(h, &p, L.coef.lam)); lt.lam = p;
   CKR(upload(h, &p, L.coef.mu)); lt.mu = p;
-  CKR(upload(h, &p, L.coef.kap)); lt.kap = p;
+  {
+    std::vector<double> Kt((size_t)L.box.ncell * 9, 0.0);
+    for (long c = 0; c < L.box.ncell; ++c)
+      for (int a = 0; a < d; ++a)
+        for (int b2 = 0; b2 < d; ++b2)
+          Kt[(size_t)c * 9 + a * 3 + b2] = L.coef.K.empty() ? (a == b2 ? L.coef.kap[c] : 0.0)
+                                                            : L.coef.K[((size_t)c * d + a) * d + b2];
+    CKR(upload(h, &p, Kt));
+    lt.Kt = p;
+  }
   CKR(upload(h, &p, pqx)); lt.pqx = p;
   CKR(upload(h, &p, pqw)); lt.pqw = p;
   CKR(upload(h, &p, phiPP)); lt.phiPP = p;
+  // face rule and basis data of the boundary data terms
+  stfem::FaceTables ft;
+  stfem::face_tables(L, &ft);
+  if (ft.nu != nlu || ft.np != nlp) {
+    h->err = "face tables do not match the load tables";
+    return STFEM_ERR_STATE;
+  }
+  lt.nqd = ft.npts;
+  CKR(upload(h, &p, ft.x)); lt.dfx = p;
+  CKR(upload(h, &p, ft.w)); lt.dfw = p;
+  CKR(upload(h, &p, ft.U)); lt.dfU = p;
+  CKR(upload(h, &p, ft.dU)); lt.dfdU = p;
+  CKR(upload(h, &p, ft.P)); lt.dfP = p;
+  CKR(upload(h, &p, ft.dP)); lt.dfdP = p;
   return 0;
 }
 
@@ -3082,6 +3112,62 @@ int smooth_noalloc_t(stfem_h h, int level, const double *b, double *d, int nsw, 
   return 0;
 }
 
+// Ring shape of the streaming patch apply of one V-cycle level: read, or pin
+// (set != 0).  Only levels that run the streaming kernel have one.
+template <typename T>
+int stream_shape_io(stfem_h h, int level, int set, int *nst, int *per_sm, int *tile) {
+  std::vector<DLevel<T>> &Ls = levels<T>(h);
+  DLevel<T> &L = Ls[level];
+  if (L.form != 1 || L.tc || L.wide || L.npatch == 0) {
+    if (set) {
+      h->err = "the level does not run the streaming patch apply";
+      return STFEM_ERR_ARG;
+    }
+    *nst = *per_sm = *tile = 0;
+    return STFEM_OK;
+  }
+  if (!set) {
+    int threads, grid, n;
+    size_t smem;
+    stream_shape(h, L, &threads, &smem, &grid, &n);
+    *nst = n;
+    *per_sm = L.tune_nst > 0 ? L.tune_cap : (h->dim == 2 ? 5 : 3);
+    *tile = std::max(1, L.tune_tile);
+    return STFEM_OK;
+  }
+  if (*nst < 2 || *nst > STREAM_STAGES || *per_sm < 1 || *per_sm > 8 || *tile < 1 || *tile > 64) {
+    h->err = "stream shape out of range (2 <= nst <= 12, 1 <= per_sm <= 8, 1 <= tile <= 64)";
+    return STFEM_ERR_ARG;
+  }
+  const int o_nst = L.tune_nst, o_cap = L.tune_cap, o_tile = L.tune_tile;
+  L.tune_nst = *nst;
+  L.tune_cap = *per_sm;
+  L.tune_tile = *tile;
+  int threads, grid, n;
+  size_t smem;
+  stream_shape(h, L, &threads, &smem, &grid, &n);
+  if (smem > 227u * 1024u) {
+    L.tune_nst = o_nst;
+    L.tune_cap = o_cap;
+    L.tune_tile = o_tile;
+    h->err = "stream shape needs more shared memory than a CTA has";
+    return STFEM_ERR_ARG;
+  }
+  drop_graphs(h);
+  return STFEM_OK;
+}
+
+int stream_shape_call(stfem_h h, int level, int set, int *nst, int *per_sm, int *tile) {
+  if (!h || !nst || !per_sm || !tile) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  if (level < 1 || level >= h->nlev) {
+    h->err = "level out of range (levels 1 .. n_levels-1 have patches)";
+    return STFEM_ERR_ARG;
+  }
+  return h->precision == STFEM_MIXED ? stream_shape_io<float>(h, level, set, nst, per_sm, tile)
+                                     : stream_shape_io<double>(h, level, set, nst, per_sm, tile);
+}
+
 } // namespace
 
 // ============================================================ C ABI
@@ -3145,6 +3231,20 @@ int stfem_setup(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_ma
   h->prob.rho = mat->rho;
   h->prob.alpha = mat->alpha;
   h->prob.c0 = mat->c0;
+  h->prob.b1 = deg->form == STFEM_FORM_PROBLEM_B_1 ? 1 : 0;
+  h->prob.hF = F.box.hF;
+  h->prob.gam_a = 5.0e4 * h->r * (h->r + 1);
+  h->prob.gam_b = 0.5 * h->r * (h->r - 1);
+  {
+    bool neumann = false;
+    for (int f = 0; f < 6; ++f) {
+      h->prob.bc_u[f] = f < 2 * d ? bcs->bc_u[f] : 0;
+      h->prob.bc_p[f] = f < 2 * d ? bcs->bc_p[f] : 0;
+      neumann = neumann || h->prob.bc_u[f] != 0 || h->prob.bc_p[f] != 0;
+    }
+    // nonzero traces, or Neumann data of an exact solution
+    h->prob.data = (pid == STFEM_PROBLEM_TRACE || (pid == STFEM_PROBLEM_SIN && neumann)) ? 1 : 0;
+  }
   if ((rc = build_load_tables(h)) < 0) return fail_setup(h, rc);
   h->lt.top_neumann = (d == 3 && bcs->bc_u[5] == 1) ? 1 : 0;
   const long N = h->L64.back().N;
@@ -3290,6 +3390,14 @@ int stfem_set_launch_cap(stfem_h h, int max_ctas) {
   if (max_ctas != h->launch_cap) drop_graphs(h);
   h->launch_cap = max_ctas;
   return STFEM_OK;
+}
+
+int stfem_get_stream_shape(stfem_h h, int level, int *nst, int *per_sm, int *tile) {
+  return stream_shape_call(h, level, 0, nst, per_sm, tile);
+}
+
+int stfem_set_stream_shape(stfem_h h, int level, int nst, int per_sm, int tile) {
+  return stream_shape_call(h, level, 1, &nst, &per_sm, &tile);
 }
 
 int stfem_set_fine_operator(stfem_h h, int choice) {
@@ -3568,8 +3676,8 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs, 
   if (F.nb.pcouple) {
     // Problem B.1: the pressure row couples to the previous state through
     // c0 Mp P^- + alpha <div u^-, xi>, i.e. the volume part of -C alone (the
-    // data term -alpha <u_D . n, xi> is zero for the built-in problems); the
-    // launch takes its arguments by value, so the swap lasts for it alone
+    // data term -alpha <u_D . n, xi> is added by k_rhs_data); the launch
+    // takes its arguments by value, so the swap lasts for it alone
     if (!F.pu_cvol) {
       h->err = "Problem B.1 needs the volume coupling of the finest level";
       return STFEM_ERR_STATE;
@@ -3590,9 +3698,17 @@ static int slab_rhs_async(stfem_h h, int slab, const double *prev, double *rhs, 
     k_src_eval<<<grid_for(nsrc, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, h->tnode, t_prev, h->tau,
                                                            ncell, h->src);
   }
-  Launch G_(h, STFEM_KCLASS_RHS, (double)F.N * 16.0 + (double)nsrc * 32.0, 0.0);
-  k_rhs<<<grid_for(F.N, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode, t_prev,
-                                                   h->tau, HF.R, HF.S, h->src, h->ys, rhs);
+  {
+    Launch G_(h, STFEM_KCLASS_RHS, (double)F.N * 16.0 + (double)nsrc * 32.0, 0.0);
+    k_rhs<<<grid_for(F.N, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode, t_prev,
+                                                     h->tau, HF.R, HF.S, h->src, h->ys, rhs);
+  }
+  if (h->prob.data) {
+    const long nrow = (long)h->q * (HF.R + HF.S);
+    Launch G2_(h, STFEM_KCLASS_RHS, (double)nrow * 16.0, 0.0);
+    k_rhs_data<<<grid_for(nrow, 128), 128, 0, h->stream>>>(h->geom, h->prob, h->lt, h->q, tc, h->chi, h->tnode,
+                                                           t_prev, h->tau, HF.R, HF.S, rhs);
+  }
   CK(cudaGetLastError());
   return 0;
 }
@@ -3865,7 +3981,7 @@ int fused_stage_q(stfem_group g, const std::vector<std::pair<stfem_h, int>> &ite
     CKR(join_in(stream_items, a, b));
     auto found = g->tune.shape.find(key);
     if (found == g->tune.shape.end()) {
-      static const int cand[][3] = {{2, 5, 1}, {3, 4, 1}, {4, 3, 1}, {2, 5, 2}, {4, 3, 2}, {4, 3, 4}};
+      static const int cand[][3] = STREAM_SHAPE_CANDIDATES;
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);

@@ -194,3 +194,36 @@ def test_wide_apply_every_level(name, precision, tol):
         assert np.array_equal(g, g2)
         assert _rel(g, g3) < tol
     S.close()
+
+
+def test_pinned_stream_shapes_change_nothing():
+    """stfem_get/set_stream_shape: the autotuned shape of every streaming
+    level is readable; pinning other shapes (stages, CTAs per SM, tile, deep
+    rings included) leaves the smoothing result bitwise unchanged;
+    out-of-range shapes and levels without the streaming kernel are refused."""
+    import paper_2303_06742_gb300 as st
+    name = "c1_2d_q2_k1_32"
+    O = oracle(name)
+    S = st.Solver(gpu_problem(case(name)), precision=st.MIXED, patch_form=st.PATCH_TIME_DIAGONAL)
+    shapes = {l: S.stream_shape(l) for l in range(1, S.n_levels)}
+    print("autotuned", shapes)
+    stream_levels = [l for l, sh in shapes.items() if sh[0] > 0]
+    assert stream_levels and all(2 <= shapes[l][0] <= 12 and shapes[l][2] >= 1 for l in stream_levels)
+    base = _smooth_all_levels(S, O, 76)
+    for g, ref in base:
+        assert _rel(g, ref) < 1e-4
+    for nst, per_sm, tile in [(2, 5, 1), (4, 3, 4), (3, 1, 2), (12, 1, 1), (8, 2, 3)]:
+        for l in stream_levels:
+            S.set_stream_shape(l, nst, per_sm, tile)
+            assert S.stream_shape(l) == (nst, per_sm, tile)
+        got = _smooth_all_levels(S, O, 76)
+        for (g, _), (g0, _) in zip(got, base):
+            assert np.array_equal(g, g0), (nst, per_sm, tile)
+    with pytest.raises(st.StfemError):
+        S.set_stream_shape(stream_levels[0], 13, 1, 1)
+    with pytest.raises(st.StfemError):
+        S.set_stream_shape(stream_levels[0], 2, 0, 1)
+    for l in [l for l, sh in shapes.items() if sh[0] == 0]:
+        with pytest.raises(st.StfemError):
+            S.set_stream_shape(l, 2, 5, 1)
+    S.close()

@@ -56,21 +56,30 @@ CASES = [
 ]
 
 
-def _pair(case, seed=0, coarse_op=0, form=0, pressure="cont"):
+def _spd_tensors(rng, nc, dim):
+    """Random symmetric positive definite permeability tensors, one per cell,
+    with off-diagonal entries of the size of the diagonal ones."""
+    A = rng.standard_normal((nc, dim, dim))
+    return np.einsum("cij,ckj->cik", A, A) + 0.3 * np.eye(dim)[None]
+
+
+def _pair(case, seed=0, coarse_op=0, form=0, pressure="cont", aniso=False):
     dim, n, L, r, k, lo, hi, bcu, bcp, hf = case
     rng = np.random.default_rng(seed)
     nc = n ** dim
     lam = rng.uniform(0.5, 5.0, nc)
     mu = rng.uniform(0.5, 5.0, nc)
     kap = np.exp(rng.standard_normal(nc))
+    K = _spd_tensors(rng, nc, dim) if aniso else None
     tau = 0.013
     prob = stfem.Problem(dim, n, L, r, k, tau, lo=lo, hi=hi, rho=1.3, alpha=0.8, c0=0.2,
                          lam_cell=lam, mu_cell=mu, kappa_cell=kap, bc_u=bcu, bc_p=bcp,
                          hf_mode=stfem.HF_MEASURE if hf == "measure" else stfem.HF_LENGTH,
                          coarse_op=coarse_op, form=form,
-                         pressure=stfem.PRESSURE_BROKEN if pressure == "disc" else stfem.PRESSURE_CONTINUOUS)
+                         pressure=stfem.PRESSURE_BROKEN if pressure == "disc" else stfem.PRESSURE_CONTINUOUS,
+                         K_cell=K)
     meshes = [BoxMesh(dim, lo, hi, [n] * dim, hf)]
-    mats = [Material(1.3, 0.8, 0.2, lam, mu, kap)]
+    mats = [Material(1.3, 0.8, 0.2, lam, mu, kap if K is None else K)]
     for _ in range(L - 1):
         mats.append(mats[-1].coarsen(meshes[-1]))
         meshes.append(meshes[-1].coarsen())
@@ -106,6 +115,38 @@ def test_level_matrices_match_oracle(case, coarse, form, pressure):
         assert diff <= 1e-12, (level, diff)
         # and the sparsity patterns agree up to exact zeros
         assert abs(D @ (abs(A) - abs(B))).max() <= 1e-12
+
+
+@pytest.mark.parametrize("pressure", ["cont", "disc"])
+@pytest.mark.parametrize("coarse", ["rediscretize", "galerkin"])
+@pytest.mark.parametrize("case", CASES)
+def test_level_matrices_match_oracle_anisotropic_permeability(case, coarse, pressure):
+    """A symmetric positive definite permeability tensor per cell (K_cell):
+    every level's matrix against the oracle's, as above; the coarse cells
+    average the tensors entry by entry."""
+    from oracle.gmg import slab_prolongation
+    prob, ops, T, tau = _pair(case, seed=3, coarse_op=stfem.COARSE_GALERKIN if coarse == "galerkin"
+                              else stfem.COARSE_REDISCRETIZE, pressure=pressure, aniso=True)
+    mats = [slab_matrix(o, T, tau, "3.1") for o in ops]
+    if coarse == "galerkin":
+        for l in range(len(ops) - 1, 0, -1):
+            P = slab_prolongation(ops[l - 1], ops[l], T)
+            mats[l - 1] = (P.T @ mats[l] @ P).tocsr()
+    for level, o in enumerate(ops):
+        rp, ci, va, n = stfem.host_level_matrix(prob, level)
+        A = sp.csr_matrix((va, ci, rp), shape=(n, n))
+        B = mats[level]
+        scale = np.asarray(abs(B).max(axis=1).todense()).ravel()
+        diff = abs(sp.diags(1.0 / scale) @ (A - B)).max()
+        assert diff <= 1e-12, (level, diff)
+
+
+def test_setup_rejects_a_permeability_that_is_not_spd():
+    for K in ([[1.0, 0.2], [0.3, 1.0]], [[1.0, 2.0], [2.0, 1.0]], [[-1.0, 0.0], [0.0, 1.0]]):
+        bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, K_cell=np.tile(np.asarray(K), (16, 1, 1)))
+        with pytest.raises(stfem.StfemError):
+            stfem.host_level_matrix(bad)
+    stfem.host_level_matrix(stfem.Problem(2, 4, 2, 2, 1, 0.01, K_cell=np.tile([[1.0, 0.2], [0.2, 1.0]], (16, 1, 1))))
 
 
 @pytest.mark.parametrize("pressure", ["cont", "disc"])
@@ -171,9 +212,15 @@ def test_setup_rejects_bad_arguments():
     bad = stfem.Problem(2, 6, 3, 2, 1, 0.01)  # 6 not divisible by 4
     with pytest.raises(stfem.StfemError):
         stfem.host_level_matrix(bad)
-    bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, bc_u=[1, 0, 0, 0], problem=stfem.PROBLEM_SIN)
+    bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, bc_u=[1, 0, 0, 0], problem=stfem.PROBLEM_PAPER_EOC)
+    with pytest.raises(stfem.StfemError):  # Eq. 5.1's problem takes Dirichlet faces only
+        stfem.host_level_matrix(bad)
+    bad = stfem.Problem(2, 4, 2, 2, 1, 0.01, problem=6)
     with pytest.raises(stfem.StfemError):
         stfem.host_level_matrix(bad)
+    for pid in (stfem.PROBLEM_SIN, stfem.PROBLEM_TRACE):  # Neumann data of an exact solution
+        stfem.host_level_matrix(stfem.Problem(2, 4, 2, 2, 1, 0.01, bc_u=[1, 0, 0, 0], bc_p=[0, 0, 1, 0],
+                                              problem=pid))
 
 
 @pytest.mark.parametrize("pressure", ["cont", "disc"])
