@@ -435,7 +435,9 @@ struct DLevel {
   double patch_inv_bytes = 0.0;                 // the inverse part of patch_bytes
   // tensor-core layout of the time-diagonal inverses (FP32 levels of
   // handles set up for several right-hand sides)
-  int tc = 0, tc_nst = 0;
+  // tc_nst_deep: the ring of a level with at most one patch per SM, which
+  // runs one CTA per SM and so has the SM's shared memory to itself
+  int tc = 0, tc_nst = 0, tc_nst_deep = 0;
   // ring shape of the streaming patch apply picked by autotune_stream (0: by
   // dimension)
   int tune_nst = 0, tune_cap = 0, tune_tile = 0;
@@ -1478,8 +1480,8 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
 #ifndef STFEM_TC_CTAS_PER_SM
 #define STFEM_TC_CTAS_PER_SM 2
 #endif
-static int tc_stages(size_t fixed) {
-  const size_t per_cta = (227u * 1024u) / STFEM_TC_CTAS_PER_SM - 1024u;
+static int tc_stages(size_t fixed, int ctas_per_sm = STFEM_TC_CTAS_PER_SM) {
+  const size_t per_cta = (227u * 1024u) / ctas_per_sm - 1024u;
   if (fixed >= per_cta) return 0;
   return (int)std::min<size_t>(tcp::MAXSTAGES, (per_cta - fixed) / tcp::STAGE);
 }
@@ -1641,6 +1643,7 @@ int build_tc_tiles_device(stfem_h h, DLevel<float> &D, const stfem::Patches &P) 
   CK(cudaStreamSynchronize(0));
   D.tc = 1;
   D.tc_nst = nst;
+  D.tc_nst_deep = tc_stages(fixed, 1);
   D.tc_cols = cols;
   return 0;
 }
@@ -1714,6 +1717,7 @@ int upload_tc_tiles(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
   CKR(upload(h, &D.ptile, tile));
   D.tc = 1;
   D.tc_nst = nst;
+  D.tc_nst_deep = tc_stages(fixed, 1);
   D.tc_cols = cols;
   return 0;
 }
@@ -2027,12 +2031,16 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
 // y: nb columns of sumC patch results (column stride L.sumC)
 template <int Q>
 void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, float *y, int nb) {
-  const size_t smem = tcp::smem_bytes(L.tc_nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
+  // a level with at most one patch per SM: one CTA per patch with a deep ring
+  // (a CTA's bytes in flight bound such a level), else the shared ring of
+  // STFEM_TC_CTAS_PER_SM CTAs per SM
+  const int nst = (L.npatch <= h->nsm && L.tc_nst_deep > L.tc_nst) ? L.tc_nst_deep : L.tc_nst;
+  const size_t smem = tcp::smem_bytes(nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
   int grid = (int)std::min<long>(L.npatch, (long)h->nsm * STFEM_TC_CTAS_PER_SM);
   if (h->launch_cap > 0) grid = std::min(grid, h->launch_cap);
   k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)L.npatch, nb, L.pcs, L.pdoff, L.pdofs, L.ptoff,
                                                              L.ptile, res, L.N, y, L.sumC, L.dc, L.maxCs,
-                                                             L.tc_nst, L.tc_cols, h->dev_err);
+                                                             nst, L.tc_cols, h->dev_err);
 }
 
 // the tensor-core apply of a level into y (nb columns)
