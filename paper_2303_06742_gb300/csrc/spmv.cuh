@@ -123,24 +123,29 @@ __host__ __device__ __forceinline__ long disc_cell_node(const int *cm, int j, in
   return (long)aj[0] + (long)udims[0] * (aj[1] + (long)udims[1] * aj[2]);
 }
 
-template <typename T, int Q, int D, int G, bool PD = false>
+template <typename T, int Q, int D, int G, bool PD = false, int CB = 1>
 __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, long R, TimeCoef<T> tc,
                                                  const T *__restrict__ x, const T *__restrict__ rhs,
                                                  T *__restrict__ y, int mode, int nb, long cstride) {
   constexpr int NA = 4 * Q * D;
-  // nb right-hand sides (column stride cstride): consecutive CTAs take the
-  // same nodes of different columns, so the node blocks are read from DRAM
-  // about once and from L2 by the other columns
-  const int col = (int)(blockIdx.x % (unsigned)nb);
-  const long gid = (long)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
+  // nb right-hand sides (column stride cstride), CB of them per thread: a
+  // node block loaded once serves CB columns.  Consecutive CTAs take the same
+  // nodes of different column groups, so the node blocks are read from DRAM
+  // about once and from L2 by the other groups.  Each column's sums run in
+  // the same order for every CB.
+  const int ngrp = nb / CB;
+  const int col = (int)(blockIdx.x % (unsigned)ngrp) * CB;
+  const long gid = (long)(blockIdx.x / (unsigned)ngrp) * blockDim.x + threadIdx.x;
   x += (long)col * cstride;
   y += (long)col * cstride;
   if (rhs) rhs += (long)col * cstride;
   const long node = gid / G;
   const int lane = threadIdx.x % G;
-  T acc[NA];
+  T acc[CB][NA];
 #pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = T(0);
+  for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[cb][i] = T(0);
   const bool is_u = node < A.nu;
   const bool is_p = !is_u && node < A.nu + A.np;
   if (is_u) {
@@ -163,27 +168,29 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
         for (int i = 0; i < D * D; ++i) k[t][i] = (t == 0 || two) ? A.uu_k[(long)eb[t] * D * D + i] : T(0);
       }
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T v[2][D], u[2][D];
+      for (int cb = 0; cb < CB; ++cb)
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int a = 0; a < Q; ++a) {
+          T v[2][D], u[2][D];
 #pragma unroll
-          for (int c = 0; c < D; ++c) {
-            v[t][c] = x[(long)a * ns + J[t] * D + c];
-            u[t][c] = x[(long)a * ns + R + J[t] * D + c];
-          }
+          for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+            for (int c = 0; c < D; ++c) {
+              v[t][c] = x[(long)cb * cstride + (long)a * ns + J[t] * D + c];
+              u[t][c] = x[(long)cb * cstride + (long)a * ns + R + J[t] * D + c];
+            }
 #pragma unroll
-          for (int c = 0; c < D; ++c) {
-            acc[(0 * Q + a) * D + c] += m[t] * u[t][c];
-            acc[(1 * Q + a) * D + c] += m[t] * v[t][c];
-            T kk = T(0);
+          for (int t = 0; t < 2; ++t)
 #pragma unroll
-            for (int cp = 0; cp < D; ++cp) kk += k[t][c * D + cp] * u[t][cp];
-            acc[(2 * Q + a) * D + c] += kk;
-          }
-      }
+            for (int c = 0; c < D; ++c) {
+              acc[cb][(0 * Q + a) * D + c] += m[t] * u[t][c];
+              acc[cb][(1 * Q + a) * D + c] += m[t] * v[t][c];
+              T kk = T(0);
+#pragma unroll
+              for (int cp = 0; cp < D; ++cp) kk += k[t][c * D + cp] * u[t][cp];
+              acc[cb][(2 * Q + a) * D + c] += kk;
+            }
+        }
     }
     const Box3 bp = PD ? disc_cell_box(a, A.r, A.n, D) : node_box(a, A.r, A.r - 1, A.n, D);
     const int f0 = A.up_ptr[node], f1 = A.up_ptr[node + 1];
@@ -194,11 +201,13 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
 #pragma unroll
       for (int c = 0; c < D; ++c) ct[c] = A.up_c[(long)e * D + c];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + sI];
+      for (int cb = 0; cb < CB; ++cb)
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[(3 * Q + a) * D + c] += ct[c] * pv;
-      }
+        for (int a = 0; a < Q; ++a) {
+          const T pv = x[(long)cb * cstride + (long)a * ns + 2 * R + sI];
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[cb][(3 * Q + a) * D + c] += ct[c] * pv;
+        }
     }
   } else if (PD && is_p) {
     // broken pressure dof: acc layout as below
@@ -212,11 +221,13 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
       const long s2 = c2 * A.pnl + (e - e0p) % A.pnl;
       const T m = A.pp_m[e], bb = A.pp_b[e];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + s2];
-        acc[a] += m * pv;
-        acc[Q + a] += bb * pv;
-      }
+      for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          const T pv = x[(long)cb * cstride + (long)a * ns + 2 * R + s2];
+          acc[cb][a] += m * pv;
+          acc[cb][Q + a] += bb * pv;
+        }
     }
     const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
     const long uoff = A.pcouple ? R : 0;
@@ -226,12 +237,14 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
 #pragma unroll
       for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T t = T(0);
+      for (int cb = 0; cb < CB; ++cb)
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
-        acc[2 * Q + a] += t;
-      }
+        for (int a = 0; a < Q; ++a) {
+          T t = T(0);
+#pragma unroll
+          for (int c = 0; c < D; ++c) t += cn[c] * x[(long)cb * cstride + (long)a * ns + uoff + J * D + c];
+          acc[cb][2 * Q + a] += t;
+        }
     }
   } else if (is_p) {
     // acc layout: [0..Q) Mp0 P, [Q..2Q) B P, [2Q..3Q) Cn V (Cn U with pcouple)
@@ -244,11 +257,13 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
       const long s2 = box_node(bp, e - e0p, A.pdims);
       const T m = A.pp_m[e], bb = A.pp_b[e];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const T pv = x[(long)a * ns + 2 * R + s2];
-        acc[a] += m * pv;
-        acc[Q + a] += bb * pv;
-      }
+      for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          const T pv = x[(long)cb * cstride + (long)a * ns + 2 * R + s2];
+          acc[cb][a] += m * pv;
+          acc[cb][Q + a] += bb * pv;
+        }
     }
     const Box3 bu = node_box(a, A.r - 1, A.r, A.n, D);
     const int f0 = A.pu_ptr[sI], f1 = A.pu_ptr[sI + 1];
@@ -259,52 +274,61 @@ __global__ void __launch_bounds__(256) k_spmv_nb(NodeBlockDev<T> A, long ns, lon
 #pragma unroll
       for (int c = 0; c < D; ++c) cn[c] = A.pu_c[(long)e * D + c];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        T t = T(0);
+      for (int cb = 0; cb < CB; ++cb)
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += cn[c] * x[(long)a * ns + uoff + J * D + c];
-        acc[2 * Q + a] += t;
-      }
+        for (int a = 0; a < Q; ++a) {
+          T t = T(0);
+#pragma unroll
+          for (int c = 0; c < D; ++c) t += cn[c] * x[(long)cb * cstride + (long)a * ns + uoff + J * D + c];
+          acc[cb][2 * Q + a] += t;
+        }
     }
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+      for (int i = 0; i < NA; ++i) acc[cb][i] += __shfl_xor_sync(0xffffffffu, acc[cb][i], o);
   }
-  if (is_u) {
-    // outputs: (eq in {u, v}) x Q x D, output o written by lane o % G
 #pragma unroll
-    for (int o = 0; o < 2 * Q * D; ++o) {
-      if (o % G != lane) continue;
-      const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
-      T val = T(0);
+  for (int cb = 0; cb < CB; ++cb) {
+    T *__restrict__ yc = y + (long)cb * cstride;
+    const T *__restrict__ rc = rhs ? rhs + (long)cb * cstride : nullptr;
+    if (is_u) {
+      // outputs: (eq in {u, v}) x Q x D, output o written by lane o % G
 #pragma unroll
-      for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[(eq * Q + a) * D + c];
-      if (eq == 0)
-        val -= tc.W[b] * acc[(1 * Q + b) * D + c];
-      else
-        val += tc.W[b] * (acc[(2 * Q + b) * D + c] + acc[(3 * Q + b) * D + c]);
-      const long oi = (long)b * ns + eq * R + node * D + c;
-      y[oi] = mode ? rhs[oi] - val : val;
-    }
-  } else if (is_p) {
-    const long sI = node - A.nu;
+      for (int o = 0; o < 2 * Q * D; ++o) {
+        if (o % G != lane) continue;
+        const int eq = o / (Q * D), b = (o / D) % Q, c = o % D;
+        T val = T(0);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) {
-      if (b % G != lane) continue;
-      T val;
-      if (A.pcouple) {
-        val = tc.W[b] * acc[Q + b];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * (acc[a] + acc[2 * Q + a]);
-      } else {
-        val = tc.W[b] * (acc[Q + b] + acc[2 * Q + b]);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[a];
+        for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[cb][(eq * Q + a) * D + c];
+        if (eq == 0)
+          val -= tc.W[b] * acc[cb][(1 * Q + b) * D + c];
+        else
+          val += tc.W[b] * (acc[cb][(2 * Q + b) * D + c] + acc[cb][(3 * Q + b) * D + c]);
+        const long oi = (long)b * ns + eq * R + node * D + c;
+        yc[oi] = mode ? rc[oi] - val : val;
       }
-      const long oi = (long)b * ns + 2 * R + sI;
-      y[oi] = mode ? rhs[oi] - val : val;
+    } else if (is_p) {
+      const long sI = node - A.nu;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        if (b % G != lane) continue;
+        T val;
+        if (A.pcouple) {
+          val = tc.W[b] * acc[cb][Q + b];
+#pragma unroll
+          for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * (acc[cb][a] + acc[cb][2 * Q + a]);
+        } else {
+          val = tc.W[b] * (acc[cb][Q + b] + acc[cb][2 * Q + b]);
+#pragma unroll
+          for (int a = 0; a < Q; ++a) val += tc.Dt[b * Q + a] * acc[cb][a];
+        }
+        const long oi = (long)b * ns + 2 * R + sI;
+        yc[oi] = mode ? rc[oi] - val : val;
+      }
     }
   }
 }

@@ -662,6 +662,19 @@ template <typename T, int Q, int D, int G>
 void launch_spmv_qdg(cudaStream_t s, const DLevel<T> &L, const TimeCoef<T> &tc, const T *x, const T *rhs, T *y,
                      int mode, int nb) {
   const long threads = (L.nb.nu + L.nb.np) * G;
+  // several FP32 columns: two per thread (a node block loaded once serves
+  // both; per column the same sums in the same order)
+  if constexpr (std::is_same<T, float>::value && Q <= 3) {
+    if (nb % 2 == 0) {
+      if (L.nb.pdisc)
+        k_spmv_nb<T, Q, D, G, true, 2><<<grid_for(threads, 256) * (nb / 2), 256, 0, s>>>(L.nb, L.ns, L.R, tc, x,
+                                                                                        rhs, y, mode, nb, L.N);
+      else
+        k_spmv_nb<T, Q, D, G, false, 2><<<grid_for(threads, 256) * (nb / 2), 256, 0, s>>>(L.nb, L.ns, L.R, tc, x,
+                                                                                         rhs, y, mode, nb, L.N);
+      return;
+    }
+  }
   if (L.nb.pdisc) // broken pressure space
     k_spmv_nb<T, Q, D, G, true><<<grid_for(threads, 256) * nb, 256, 0, s>>>(L.nb, L.ns, L.R, tc, x, rhs, y, mode,
                                                                             nb, L.N);

@@ -76,3 +76,30 @@ def test_admission_by_footprint():
     with pytest.raises(st.StfemError):
         T.submit(probs[0], 1)
     T.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_served_requests_with_boundary_data_and_permeability_tensors(batched):
+    """Requests with nonzero boundary data and per-cell permeability tensors:
+    the server copies the tensors at submit (the caller's arrays are freed
+    right after), and each served result is bitwise the direct march."""
+    import paper_2303_06742_gb300 as st
+    names = ["aniso_bd_2d_q2_k1_8", "bd_2d_q3_k2_8", "aniso_2d_q3_k2_8", "bd_3d_q2_k1_4"]
+    cases = [inputs.case(n) for n in names]
+    S = st.Server(hbm_budget=8 << 30, n_workers=2, batched=batched)
+    ids = []
+    for c in cases:
+        p = gpu_problem(c)
+        ids.append(S.submit(p, 2, tol=1e-10))
+        del p  # the per-cell arrays must have been copied
+    res = [S.result(i) for i in ids]
+    S.close()
+    for c, (info, state, _) in zip(cases, res):
+        assert info["status"] == 0, info
+        D = st.Solver(gpu_problem(c), precision=st.MIXED)
+        s = torch.zeros(D.n_state, dtype=torch.float64, device="cuda")
+        D.initial_state(s)
+        rc, _ = D.march(0, 2, s, tol=1e-10)
+        torch.cuda.synchronize()
+        assert rc == 0 and np.array_equal(s.cpu().numpy(), state)
+        D.close()
