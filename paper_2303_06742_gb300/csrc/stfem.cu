@@ -1490,9 +1490,6 @@ int upload_patches(stfem_h h, DLevel<T> &D, const stfem::Patches &P, double omeg
 
 // Stages of the tensor-core kernel's ring: as many as fit next to the fixed
 // shared memory when STFEM_TC_CTAS_PER_SM CTAs share an SM (at most 8).
-#ifndef STFEM_TC_CTAS_PER_SM
-#define STFEM_TC_CTAS_PER_SM 2
-#endif
 static int tc_stages(size_t fixed, int ctas_per_sm = STFEM_TC_CTAS_PER_SM) {
   const size_t per_cta = (227u * 1024u) / ctas_per_sm - 1024u;
   if (fixed >= per_cta) return 0;

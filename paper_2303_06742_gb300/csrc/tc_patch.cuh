@@ -24,6 +24,12 @@
 // sets *err and every role leaves at its next uniform decision point after
 // draining its own copies / MMAs.
 
+// CTAs of the tensor-core kernel resident per SM (the registers per thread
+// are bounded to fit them).
+#ifndef STFEM_TC_CTAS_PER_SM
+#define STFEM_TC_CTAS_PER_SM 2
+#endif
+
 namespace tcp {
 
 constexpr int THREADS = 320;
@@ -120,7 +126,7 @@ __host__ __device__ inline size_t smem_bytes(int nst, int maxCs, int nrow) {
 } // namespace tcp
 
 template <int Q>
-__global__ void __launch_bounds__(tcp::THREADS, 1)
+__global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
     k_patch_apply_tc(int npatch, int nb, const int *__restrict__ pcs, const long long *__restrict__ pdoff,
                      const int *__restrict__ pdofs, const long long *__restrict__ ptoff,
                      const float *__restrict__ ptile, const float *__restrict__ res, long rstride,
@@ -245,28 +251,35 @@ __global__ void __launch_bounds__(tcp::THREADS, 1)
     const int quarter = warp & 3;     // tensor-memory lanes 32 quarter .. +31
     const int group = cw >> 2;        // tiles mt = group, group + 2, ...
     // gather the nb residual columns of patch p and transform them to the
-    // slots: xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot
+    // slots: xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot.
+    // A thread takes one patch row m: its Q slab indices are loaded once and
+    // the 8 Q residual values behind them are all requested before the first
+    // is used (one dependent load pair per row instead of one per column).
     auto gather = [&](int p) {
       const int Cs = pcs[p];
       const long long doff = pdoff[p];
-      for (int idx = tid; idx < 8 * Cs; idx += NCONS) {
-        const int c = idx / Cs, m = idx - c * Cs;
-        float r[Q];
+      for (int m = tid; m < Cs; m += NCONS) {
+        int g[Q];
 #pragma unroll
-        for (int b = 0; b < Q; ++b) r[b] = c < nb ? res[(long)c * rstride + pdofs[doff + b * Cs + m]] : 0.f;
+        for (int b = 0; b < Q; ++b) g[b] = pdofs[doff + b * Cs + m];
+        float r[8][Q];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int b = 0; b < Q; ++b) r[c][b] = c < nb ? res[(long)c * rstride + g[b]] : 0.f;
         for (int a = 0; a < ns; ++a) {
-          float re = 0.f, im = 0.f;
+          const bool cplx = a >= nr;
+          const int row = cplx ? nr + 2 * (a - nr) : a;
 #pragma unroll
-          for (int b = 0; b < Q; ++b) {
-            re += dc.U[(a * Q + b) * 2] * r[b];
-            im += dc.U[(a * Q + b) * 2 + 1] * r[b];
-          }
-          if (a < nr) {
-            S.xt[((size_t)a * 8 + c) * maxCs + m] = re;
-          } else {
-            const int row = nr + 2 * (a - nr);
+          for (int c = 0; c < 8; ++c) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+              re += dc.U[(a * Q + b) * 2] * r[c][b];
+              im += dc.U[(a * Q + b) * 2 + 1] * r[c][b];
+            }
             S.xt[((size_t)row * 8 + c) * maxCs + m] = re;
-            S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m] = im;
+            if (cplx) S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m] = im;
           }
         }
       }
@@ -276,21 +289,28 @@ __global__ void __launch_bounds__(tcp::THREADS, 1)
       const int K = kext(a, nr, c8);
       const bool cplx = a >= nr;
       const int row = cplx ? nr + 2 * (a - nr) : a;
-      for (int idx = tid; idx < 16 * K; idx += NCONS) {
-        const int k = idx >> 4, n = idx & 15;
-        float v = 0.f;
-        if (!cplx) {
-          if (n < 8 && k < Cs) v = S.xt[((size_t)row * 8 + n) * maxCs + k];
-        } else {
-          const int kk = k < c8 ? k : k - c8;
-          if (kk < Cs) {
-            const float xr = S.xt[((size_t)row * 8 + (n & 7)) * maxCs + kk];
-            const float xi = S.xt[((size_t)(row + 1) * 8 + (n & 7)) * maxCs + kk];
-            v = k < c8 ? (n < 8 ? xr : xi) : (n < 8 ? -xi : xr);
+      // a thread writes one 16-byte core row: k0 .. k0 + 3 of column n
+      for (int idx = tid; idx < 4 * K; idx += NCONS) {
+        const int k0 = (idx >> 4) * 4, n = idx & 15;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = k0 + e;
+          v[e] = 0.f;
+          if (!cplx) {
+            if (n < 8 && k < Cs) v[e] = S.xt[((size_t)row * 8 + n) * maxCs + k];
+          } else {
+            const int kk = k < c8 ? k : k - c8;
+            if (kk < Cs) {
+              const float xr = S.xt[((size_t)row * 8 + (n & 7)) * maxCs + kk];
+              const float xi = S.xt[((size_t)(row + 1) * 8 + (n & 7)) * maxCs + kk];
+              v[e] = k < c8 ? (n < 8 ? xr : xi) : (n < 8 ? -xi : xr);
+            }
           }
         }
-        const int kb = k >> 3, kc = (k >> 2) & 1, e = k & 3, ng = n >> 3, rr = n & 7;
-        S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4 + e] = v;
+        const int kb = k0 >> 3, kc = (k0 >> 2) & 1, ng = n >> 3, rr = n & 7;
+        *reinterpret_cast<float4 *>(&S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4]) =
+            make_float4(v[0], v[1], v[2], v[3]);
       }
     };
     long long nslot = 0;
