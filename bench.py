@@ -66,6 +66,10 @@ def parse():
     p.add_argument("--stream-shapes", default=None,
                    help="pin the streaming patch apply's shape per level, 'level:stages,ctas_per_sm,tile;...' "
                         "(default: the setup's autotuned shapes, printed in the roofline object)")
+    p.add_argument("--tc-shapes", default=None,
+                   help="with --rhs > 1: pin the tensor-core patch apply's shape per level, "
+                        "'level:split,deep;...' (default: the setup's autotuned shapes, printed in the "
+                        "roofline object)")
     p.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -591,6 +595,11 @@ def batch_arm(args):
     ts = time.perf_counter()
     S = st.Solver(gpu_problem(c), precision=st.MIXED, stream=stream, n_sweeps=args.sweeps, n_rhs=nb)
     setup_s = time.perf_counter() - ts
+    if args.tc_shapes:
+        for item in args.tc_shapes.split(";"):
+            lev, shape = item.split(":")
+            S.set_tc_shape(int(lev), *[int(v) for v in shape.split(",")])
+    tc_shapes = {str(l): list(S.tc_shape(l)) for l in range(1, S.n_levels)}
     states = torch.zeros((nb, S.n_state), dtype=torch.float64, device="cuda")
     for k, t0 in enumerate(t0s):
         S.initial_state_at(t0, states[k])
@@ -696,7 +705,8 @@ def batch_arm(args):
         "roofline": {"kernel": "k_patch_apply_tc", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
                      "traffic": None, "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
-                     "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"]},
+                     "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"],
+                     "tc_shapes": tc_shapes},
         "breakdown": breakdown, "gpu_launches": launches, "clocks": clk,
         "energy": energy_per_step(clk, total_ms / K),
     }))

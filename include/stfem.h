@@ -258,6 +258,22 @@ int stfem_set_launch_cap(stfem_h h, int max_ctas);
 int stfem_get_stream_shape(stfem_h h, int level, int *nst, int *per_sm, int *tile);
 int stfem_set_stream_shape(stfem_h h, int level, int nst, int per_sm, int tile);
 
+/* Shape of the tensor-core patch apply (the local solves of Algorithm 4.1
+ * for several right-hand sides, on the FP32 levels of a STFEM_MIXED handle
+ * set up for n_rhs > 1) on a V-cycle level l (1 .. n_levels-1): split = 0
+ * gives each CTA whole patches, split = 1 single 128-row tiles of a patch's
+ * inverse (a patch then spreads over several CTAs); deep = 0 runs
+ * two CTAs per multiprocessor with the ring that fits them,
+ * deep = 1 one CTA per multiprocessor with the deepest ring that fits.
+ * stfem_gmg_setup picks each level's shape by timing the candidates on the
+ * level's own inverses, so two runs may pick differently.  get: the level's
+ * current shape (-1, -1 for a level without the tensor-core apply).  set:
+ * pins it; STFEM_ERR_ARG for a level without the tensor-core apply, values
+ * other than 0 and 1, or deep = 1 where no deeper ring fits.  The shape
+ * changes only how rows are spread over CTAs, never a result. */
+int stfem_get_tc_shape(stfem_h h, int level, int *split, int *deep);
+int stfem_set_tc_shape(stfem_h h, int level, int split, int deep);
+
 /* Operator of the finest level inside the mixed-precision V-cycle (its FP32
  * residuals, Eq. 4.7).  ASSEMBLED: the node-block form of the assembled
  * spatial matrices; MATRIX_FREE: cell by cell from the unit-coefficient

@@ -106,6 +106,8 @@ def _load():
         "stfem_set_launch_cap": [P, I],
         "stfem_get_stream_shape": [P, I, pI, pI, pI],
         "stfem_set_stream_shape": [P, I, I, I, I],
+        "stfem_get_tc_shape": [P, I, pI, pI],
+        "stfem_set_tc_shape": [P, I, I, I],
         "stfem_set_patch_kernel": [P, I],
         "stfem_set_fine_operator": [P, I],
         "stfem_set_wait_limit": [P, D],
@@ -390,6 +392,17 @@ class Solver:
     def set_stream_shape(self, level, nst, per_sm, tile):
         """Pins the streaming patch apply's shape on a level."""
         self._check(lib.stfem_set_stream_shape(self.h, int(level), int(nst), int(per_sm), int(tile)))
+
+    def tc_shape(self, level):
+        """(split, deep) of the tensor-core patch apply on a level; (-1, -1)
+        for a level that runs another patch kernel."""
+        a, b = C.c_int(), C.c_int()
+        self._check(lib.stfem_get_tc_shape(self.h, int(level), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_tc_shape(self, level, split, deep):
+        """Pins the tensor-core patch apply's shape on a level."""
+        self._check(lib.stfem_set_tc_shape(self.h, int(level), int(split), int(deep)))
 
     def set_patch_kernel(self, choice):
         """PATCH_KERNEL_AUTO (default), PATCH_KERNEL_STREAM or PATCH_KERNEL_WIDE."""

@@ -449,6 +449,13 @@ struct DLevel {
   uint32_t tc_cols = 0;
   long long *ptoff = nullptr;
   float *ptile = nullptr;
+  // work items of the tensor-core apply (see tc_patch.cuh): [0] whole
+  // patches, [1] single 128-row M tiles, each list largest first; which list
+  // and which ring (tc_deep: one CTA per SM with the deepest ring) a launch
+  // uses is picked by autotune_tc
+  int2 *tc_items[2] = {nullptr, nullptr};
+  long tc_nitem[2] = {0, 0};
+  int tc_split = 0, tc_deep = 0;
   int form = 0;       // 0 dense inverses, 1 time-diagonal form
   int *pcs = nullptr; // spatial patch size Cs (form 1)
   int maxCs = 0;
@@ -1623,6 +1630,39 @@ int factor_on_device(stfem_h h, DLevel<T> &D, const stfem::Level &L, const stfem
   return rc;
 }
 
+// Work-item lists of the tensor-core apply of a level: whole patches, and
+// single M tiles (128 rows of a patch's A, the last one possibly shorter),
+// each sorted by the bytes of A it streams, largest first (ties in patch and
+// tile order), so that the round-robin assignment of items to CTAs starts
+// every CTA on a large item.  The default shape is whole patches, with the
+// deep ring on levels of at most one patch per SM.
+int build_tc_items(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
+  const int nr = D.dc.nr, ns = D.dc.nr + D.dc.nc;
+  for (int split = 0; split < 2; ++split) {
+    std::vector<std::pair<long long, int2>> it;
+    for (long p = 0; p < P.npatch; ++p) {
+      const int c8 = tcp::cs8(P.cs[p]), nt = (c8 + 127) / 128;
+      long long kt = 0;
+      for (int a = 0; a < ns; ++a) kt += tcp::kext(a, nr, c8);
+      if (!split) {
+        it.push_back({(long long)c8 * kt, make_int2((int)p, nt << 16)});
+      } else {
+        for (int t = 0; t < nt; ++t)
+          it.push_back({(long long)(std::min((t + 1) * 128, c8) - t * 128) * kt, make_int2((int)p, t | ((t + 1) << 16))});
+      }
+    }
+    std::stable_sort(it.begin(), it.end(), [](const std::pair<long long, int2> &x,
+                                              const std::pair<long long, int2> &y) { return x.first > y.first; });
+    std::vector<int2> v(it.size());
+    for (size_t i = 0; i < it.size(); ++i) v[i] = it[i].second;
+    CKR(upload(h, &D.tc_items[split], v));
+    D.tc_nitem[split] = (long)v.size();
+  }
+  D.tc_split = 0;
+  D.tc_deep = (D.npatch <= h->nsm && D.tc_nst_deep > D.tc_nst) ? 1 : 0;
+  return 0;
+}
+
 // Tensor-core tiles from device-resident FP32 inverses.
 int build_tc_tiles_device(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
   const int nr = D.dc.nr, nc = D.dc.nc, ns = nr + nc, nrow = nr + 2 * nc;
@@ -1655,7 +1695,7 @@ int build_tc_tiles_device(stfem_h h, DLevel<float> &D, const stfem::Patches &P) 
   D.tc_nst = nst;
   D.tc_nst_deep = tc_stages(fixed, 1);
   D.tc_cols = cols;
-  return 0;
+  return build_tc_items(h, D, P);
 }
 
 // Level work vectors with nb columns (b, d, r of N; the patch results of sumC).
@@ -1729,7 +1769,7 @@ int upload_tc_tiles(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
   D.tc_nst = nst;
   D.tc_nst_deep = tc_stages(fixed, 1);
   D.tc_cols = cols;
-  return 0;
+  return build_tc_items(h, D, P);
 }
 
 // ---------------------------------------------------------------- V-cycle
@@ -2041,16 +2081,19 @@ int check_patch_shape(stfem_h h, const DLevel<T> &L) {
 // y: nb columns of sumC patch results (column stride L.sumC)
 template <int Q>
 void launch_patch_tc_q(stfem_h h, DLevel<float> &L, const float *res, float *y, int nb) {
-  // a level with at most one patch per SM: one CTA per patch with a deep ring
-  // (a CTA's bytes in flight bound such a level), else the shared ring of
-  // STFEM_TC_CTAS_PER_SM CTAs per SM
-  const int nst = (L.npatch <= h->nsm && L.tc_nst_deep > L.tc_nst) ? L.tc_nst_deep : L.tc_nst;
+  // the level's shape (autotune_tc): whole patches or single M tiles as work
+  // items; the shared ring of STFEM_TC_CTAS_PER_SM CTAs per SM, or one CTA per
+  // SM with the deepest ring (where a CTA's bytes in flight bound the level)
+  const int split = L.tc_split, deep = L.tc_deep && L.tc_nst_deep > L.tc_nst;
+  const int nst = deep ? L.tc_nst_deep : L.tc_nst;
+  const long nitem = L.tc_nitem[split];
   const size_t smem = tcp::smem_bytes(nst, L.maxCs, L.dc.nr + 2 * L.dc.nc);
-  int grid = (int)std::min<long>(L.npatch, (long)h->nsm * STFEM_TC_CTAS_PER_SM);
+  int grid = (int)std::min<long>(nitem, (long)h->nsm * (deep ? 1 : STFEM_TC_CTAS_PER_SM));
   if (h->launch_cap > 0) grid = std::min(grid, h->launch_cap);
-  k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)L.npatch, nb, L.pcs, L.pdoff, L.pdofs, L.ptoff,
-                                                             L.ptile, res, L.N, y, L.sumC, L.dc, L.maxCs,
-                                                             nst, L.tc_cols, h->dev_err);
+  if (grid <= 0) return;
+  k_patch_apply_tc<Q><<<grid, tcp::THREADS, smem, h->stream>>>((int)nitem, L.tc_items[split], nb, L.pcs, L.pdoff,
+                                                             L.pdofs, L.ptoff, L.ptile, res, L.N, y, L.sumC, L.dc,
+                                                             L.maxCs, nst, L.tc_cols, h->dev_err);
 }
 
 // the tensor-core apply of a level into y (nb columns)
@@ -2068,6 +2111,55 @@ void launch_patch_tc(stfem_h h, DLevel<float> &L, const float *res, float *y, in
 // L.sumC.  Algorithmic bytes: the inverses once, the per-row traffic per
 // column (the tensor-core kernel reads each inverse once for all columns;
 // without it the columns are applied one after another).
+// Autotuner of the tensor-core patch apply (FP32 levels of handles set up for
+// several right-hand sides): times whole-patch and single-tile work items,
+// each with the shared ring and (where one fits) the deeper one-CTA-per-SM
+// ring, on the level's own tiles with the handle's column count, and keeps
+// the fastest.  Items and rings change only how rows are spread over CTAs,
+// never the arithmetic of a row, so results do not depend on the choice.
+int autotune_tc(stfem_h h, DLevel<float> &L) {
+  if (!L.tc || L.npatch == 0) return 0;
+  const int nb = std::max(1, std::min(h->nrhs_cap, L.ncols));
+  cudaStream_t ts = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStream_t saved = h->stream;
+  h->stream = ts;
+  cudaMemsetAsync(L.r, 0, (size_t)nb * L.N * sizeof(float), ts);
+  float best = 1e30f;
+  int bs = L.tc_split, bd = L.tc_deep;
+  for (int split = 0; split < 2; ++split)
+    for (int deep = 0; deep < 2; ++deep) {
+      if (deep && L.tc_nst_deep <= L.tc_nst) continue;
+      L.tc_split = split;
+      L.tc_deep = deep;
+      for (int w = 0; w < 2; ++w) launch_patch_tc(h, L, L.r, L.ybuf, nb);
+      cudaEventRecord(e0, ts);
+      for (int t = 0; t < 5; ++t) launch_patch_tc(h, L, L.r, L.ybuf, nb);
+      cudaEventRecord(e1, ts);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bs = split;
+        bd = deep;
+      }
+    }
+  h->stream = saved;
+  L.tc_split = bs;
+  L.tc_deep = bd;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
+  CK(e);
+  CK(cudaGetLastError());
+  return 0;
+}
+
 template <typename T>
 void launch_patch_apply(stfem_h h, DLevel<T> &L, const T *res, int nb = 1) {
   Launch G_(h, STFEM_KCLASS_PATCH_APPLY, L.patch_inv_bytes + (L.patch_bytes - L.patch_inv_bytes) * nb,
@@ -3186,6 +3278,42 @@ int stream_shape_call(stfem_h h, int level, int set, int *nst, int *per_sm, int 
                                      : stream_shape_io<double>(h, level, set, nst, per_sm, tile);
 }
 
+// Shape of the tensor-core patch apply of one level: read, or pin (set != 0).
+int tc_shape_call(stfem_h h, int level, int set, int *split, int *deep) {
+  if (!h || !split || !deep) return STFEM_ERR_ARG;
+  CKR(require_gmg(h));
+  if (level < 1 || level >= h->nlev) {
+    h->err = "level out of range (levels 1 .. n_levels-1 have patches)";
+    return STFEM_ERR_ARG;
+  }
+  if (h->precision != STFEM_MIXED || !h->L32[level].tc) {
+    if (set) {
+      h->err = "the level does not run the tensor-core patch apply";
+      return STFEM_ERR_ARG;
+    }
+    *split = *deep = -1;
+    return STFEM_OK;
+  }
+  DLevel<float> &L = h->L32[level];
+  if (!set) {
+    *split = L.tc_split;
+    *deep = L.tc_deep && L.tc_nst_deep > L.tc_nst ? 1 : 0;
+    return STFEM_OK;
+  }
+  if ((*split != 0 && *split != 1) || (*deep != 0 && *deep != 1)) {
+    h->err = "tensor-core shape out of range (split and deep are 0 or 1)";
+    return STFEM_ERR_ARG;
+  }
+  if (*deep && L.tc_nst_deep <= L.tc_nst) {
+    h->err = "no deeper ring fits next to this level's patches";
+    return STFEM_ERR_ARG;
+  }
+  L.tc_split = *split;
+  L.tc_deep = *deep;
+  drop_graphs(h);
+  return STFEM_OK;
+}
+
 } // namespace
 
 // ============================================================ C ABI
@@ -3382,13 +3510,17 @@ int stfem_gmg_setup(stfem_h h, const stfem_gmg_params *p) {
     return STFEM_ERR_SINGULAR_PATCH;
   }
   CKR(upload(h, &h->coarse_inv, A0));
-  if (h->nrhs_cap > 1)
+  if (h->nrhs_cap > 1) {
     for (int l = 0; l < h->nlev; ++l) {
       if (mixed)
         CKR(ensure_columns(h, h->L32[l], h->nrhs_cap));
       else
         CKR(ensure_columns(h, h->L64[l], h->nrhs_cap));
     }
+    if (mixed)
+      for (int l = 1; l < h->nlev; ++l) CKR(autotune_tc(h, h->L32[l]));
+    CKR(check_dev_err(h));
+  }
   CK(cudaStreamSynchronize(0)); // uploads of the legacy stream (see stfem_setup)
   return STFEM_OK;
 }
@@ -3416,6 +3548,14 @@ int stfem_get_stream_shape(stfem_h h, int level, int *nst, int *per_sm, int *til
 
 int stfem_set_stream_shape(stfem_h h, int level, int nst, int per_sm, int tile) {
   return stream_shape_call(h, level, 1, &nst, &per_sm, &tile);
+}
+
+int stfem_get_tc_shape(stfem_h h, int level, int *split, int *deep) {
+  return tc_shape_call(h, level, 0, split, deep);
+}
+
+int stfem_set_tc_shape(stfem_h h, int level, int split, int deep) {
+  return tc_shape_call(h, level, 1, &split, &deep);
 }
 
 int stfem_set_fine_operator(stfem_h h, int choice) {

@@ -16,6 +16,15 @@
 // bulk copy lands in shared memory ready for the MMA descriptors: rows padded
 // to Cs8 = 8 ceil(Cs / 8), K to Cs8 (real) or 2 Cs8 (complex), with zeros.
 //
+// Work items: a CTA takes items (patch p, M tiles t0 .. t1-1) from a table,
+// item i = blockIdx.x, blockIdx.x + gridDim.x, ...  An item is a whole patch
+// (t0 = 0, t1 = its tile count) or a single 128-row M tile of one; the rows of
+// D, and so of the patch result (the time mixing with V acts row by row), are
+// independent of one another, so a patch's tiles may go to different CTAs.
+// An item computes its rows with the same MMA sequence as a whole patch
+// (K blocks in ascending order into the same accumulator), so the result does
+// not depend on how patches are cut into items or spread over CTAs.
+//
 // Warp roles (320 threads): warp 0 streams A through a ring of stages
 // (cp.async.bulk, mbarrier transaction counts); warp 1 owns the tensor
 // memory and one lane issues the MMAs; warps 2..9 gather and transform the
@@ -127,7 +136,7 @@ __host__ __device__ inline size_t smem_bytes(int nst, int maxCs, int nrow) {
 
 template <int Q>
 __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
-    k_patch_apply_tc(int npatch, int nb, const int *__restrict__ pcs, const long long *__restrict__ pdoff,
+    k_patch_apply_tc(int nitem, const int2 *__restrict__ items, int nb, const int *__restrict__ pcs, const long long *__restrict__ pdoff,
                      const int *__restrict__ pdofs, const long long *__restrict__ ptoff,
                      const float *__restrict__ ptile, const float *__restrict__ res, long rstride,
                      float *__restrict__ y, long ystride, DiagCoef<float> dc, int maxCs, int nst, uint32_t tcols,
@@ -166,9 +175,15 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
     if (lane == 0) {
       long long it = 0;
       bool ok = true;
-      for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
-        const int c8 = cs8(pcs[p]), per = kpb(c8);
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(ptile + ptoff[p]);
+      for (int i = blockIdx.x; i < nitem && ok; i += gridDim.x) {
+        const int2 w = items[i];
+        const int p = w.x, t0 = w.y & 0xffff, t1 = w.y >> 16;
+        const int c8 = cs8(pcs[p]);
+        // bytes of the item's rows in one K block; a whole patch's K blocks
+        // are contiguous, a tile's rows are a 4 KB-aligned piece of each
+        const int rb = (min(t1 * 128, c8) - t0 * 128) * 32, per = STAGE / rb;
+        const bool whole = rb == c8 * 32;
+        const unsigned char *slot = reinterpret_cast<const unsigned char *>(ptile + ptoff[p]);
         for (int a = 0; a < ns && ok; ++a) {
           const int nkb = kext(a, nr, c8) / 8;
           for (int kb = 0; kb < nkb; kb += per) {
@@ -181,12 +196,19 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
               ok = false;
               break;
             }
-            const uint32_t bytes = (uint32_t)(min(per, nkb - kb) * c8 * 32);
-            mbar_arrive_expect_tx(&S.full[st], bytes);
-            bulk_copy_g2s(S.stage + (size_t)st * STAGE, src, bytes, &S.full[st]);
-            src += bytes;
+            const int nk = min(per, nkb - kb);
+            unsigned char *dst = S.stage + (size_t)st * STAGE;
+            mbar_arrive_expect_tx(&S.full[st], (uint32_t)(nk * rb));
+            if (whole) {
+              bulk_copy_g2s(dst, slot + (size_t)kb * c8 * 32, (uint32_t)(nk * rb), &S.full[st]);
+            } else {
+              for (int j = 0; j < nk; ++j)
+                bulk_copy_g2s(dst + (size_t)j * rb, slot + ((size_t)(kb + j) * c8 + (size_t)t0 * 128) * 32,
+                              (uint32_t)rb, &S.full[st]);
+            }
             ++it;
           }
+          slot += (size_t)nkb * c8 * 32;
         }
       }
       if (!ok) {
@@ -202,8 +224,11 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
       long long it = 0, nslot = 0;
       bool ok = true;
       const uint32_t bbase = smem_addr(S.B);
-      for (int p = blockIdx.x; p < npatch && ok; p += gridDim.x) {
-        const int c8 = cs8(pcs[p]), per = kpb(c8), ntile = (c8 + 127) / 128;
+      for (int i = blockIdx.x; i < nitem && ok; i += gridDim.x) {
+        const int2 w = items[i];
+        const int p = w.x, t0 = w.y & 0xffff, t1 = w.y >> 16;
+        const int c8 = cs8(pcs[p]), ntl = t1 - t0;
+        const int rb = (min(t1 * 128, c8) - t0 * 128) * 32, per = STAGE / rb;
         for (int a = 0; a < ns && ok; ++a, ++nslot) {
           // B of this slot written; D free (its previous contents read back)
           if (!mbar_wait(S.bfull, (uint32_t)(nslot & 1), WAIT) ||
@@ -224,8 +249,8 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
             const int nk = min(per, nkb - kb);
             for (int j = 0; j < nk; ++j) {
               const uint64_t bd = sdesc(bbase + (uint32_t)(kb + j) * 512u, 128u, 256u);
-              for (int mt = 0; mt < ntile; ++mt) {
-                const uint64_t ad = sdesc(sbase + (uint32_t)(j * c8 * 32 + mt * 4096), 128u, 256u);
+              for (int mt = 0; mt < ntl; ++mt) {
+                const uint64_t ad = sdesc(sbase + (uint32_t)(j * rb + mt * 4096), 128u, 256u);
                 mma_tf32(tbase + (uint32_t)(mt * 16), ad, bd, (kb + j) > 0 ? 1u : 0u);
               }
             }
@@ -319,19 +344,21 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
       // the MMAs of this one run, and the epilogue mixes D straight back to
       // the time nodes (y = V z, complex: 2 Re(V z)).
       const bool cplx = nc == 1;
-      if (blockIdx.x < npatch) gather(blockIdx.x);
-      for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++nslot) {
-        cons_sync(); // xt of patch p complete
+      if (blockIdx.x < nitem) gather(items[blockIdx.x].x);
+      for (int i = blockIdx.x; i < nitem; i += gridDim.x, ++nslot) {
+        cons_sync(); // xt of the item's patch complete
         if (tid == 0) S.flag[1] = S.flag[0];
         cons_sync();
         if (S.flag[1]) break;
-        const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+        const int2 w = items[i];
+        const int p = w.x, t0 = w.y & 0xffff, ntl = (w.y >> 16) - t0;
+        const int Cs = pcs[p], c8 = cs8(Cs);
         const long long doff = pdoff[p];
         write_b(0, Cs, c8);
         fence_async_smem();
         cons_sync();
         if (tid == 0) mbar_arrive(S.bfull);
-        if (p + (int)gridDim.x < npatch) gather(p + gridDim.x);
+        if (i + (int)gridDim.x < nitem) gather(items[i + gridDim.x].x);
         if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nslot & 1), WAIT) ? 0 : 1;
         cons_sync();
         if (S.flag[1]) {
@@ -342,11 +369,11 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
           break;
         }
         fence_after();
-        for (int mt = group; mt < ntile; mt += 2) {
+        for (int mt = group; mt < ntl; mt += 2) {
           float v[16];
           __syncwarp();
           ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
-          const int m = mt * 128 + quarter * 32 + lane;
+          const int m = (t0 + mt) * 128 + quarter * 32 + lane;
           if (m < Cs)
             for (int c = 0; c < nb; ++c)
 #pragma unroll
@@ -360,13 +387,15 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
         if (tid == 0) mbar_arrive(S.aempty);
       }
     } else
-    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+    for (int i = blockIdx.x; i < nitem; i += gridDim.x) {
       // uniform decision to go on
       cons_sync();
       if (tid == 0) S.flag[1] = S.flag[0];
       cons_sync();
       if (S.flag[1]) break;
-      const int Cs = pcs[p], c8 = cs8(Cs), ntile = (c8 + 127) / 128;
+      const int2 w = items[i];
+      const int p = w.x, t0 = w.y & 0xffff, ntl = (w.y >> 16) - t0;
+      const int Cs = pcs[p], c8 = cs8(Cs);
       const long long doff = pdoff[p];
       gather(p);
       cons_sync();
@@ -391,11 +420,11 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
           break;
         }
         fence_after();
-        for (int mt = group; mt < ntile; mt += 2) {
+        for (int mt = group; mt < ntl; mt += 2) {
           float v[16];
           __syncwarp();
           ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
-          const int m = mt * 128 + quarter * 32 + lane;
+          const int m = (t0 + mt) * 128 + quarter * 32 + lane;
           if (m < Cs) {
             if (!cplx) {
               for (int c = 0; c < nb; ++c) S.xt[((size_t)row * 8 + c) * maxCs + m] = v[c];
@@ -412,9 +441,10 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
         if (tid == 0) mbar_arrive(S.aempty);
       }
       if (stop) break;
-      // back to the time nodes: y[c][b][m]
-      for (int idx = tid; idx < nb * Q * Cs; idx += NCONS) {
-        const int c = idx / (Q * Cs), rem = idx - c * Q * Cs, b = rem / Cs, m = rem - b * Cs;
+      // back to the time nodes: y[c][b][m] for the item's rows m0 <= m < m0 + nm
+      const int m0 = t0 * 128, nm = min((t0 + ntl) * 128, Cs) - m0;
+      for (int idx = tid; idx < nb * Q * nm; idx += NCONS) {
+        const int c = idx / (Q * nm), rem = idx - c * Q * nm, b = rem / nm, m = m0 + rem - b * nm;
         float val = 0.f;
         for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * S.xt[((size_t)a * 8 + c) * maxCs + m];
         for (int cc = 0; cc < nc; ++cc) {
@@ -422,7 +452,7 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
           val += 2.f * (dc.V[(b * ns + a) * 2] * S.xt[((size_t)row * 8 + c) * maxCs + m] -
                         dc.V[(b * ns + a) * 2 + 1] * S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m]);
         }
-        y[(long)c * ystride + doff + rem] = val;
+        y[(long)c * ystride + doff + b * Cs + m] = val;
       }
     }
   }

@@ -116,6 +116,59 @@ def test_tensor_core_apply_many_patches_per_cta(name):
     S.close()
 
 
+@pytest.mark.parametrize("name", ["c2_small_2d_q3_k2_8", "c3_small_3d_q2_k1_4"])
+def test_tensor_core_apply_every_shape(name):
+    """Every shape of the tensor-core apply: whole patches or single 128-row
+    tiles as work items (a patch's tiles then go to different CTAs), two CTAs
+    per SM or one with the deepest ring, each at the default grid and with the
+    grid capped so that CTAs walk many items.  Each column against the
+    oracle's smoother, and bitwise the shape the setup picked (Q3/Q2 dG(2):
+    two time slots per patch; Q2/Q1 dG(1) in 3D: one complex slot, patches of
+    up to four tiles)."""
+    import paper_2303_06742_gb300 as st
+    from oracle.gmg import smooth
+    O = oracle(name)
+    S = st.Solver(gpu_problem(case(name)), precision=st.MIXED, n_rhs=8)
+    rng = np.random.default_rng(73)
+    n_split = 0
+    for l in range(1, len(O.h.levels)):
+        chosen = S.tc_shape(l)
+        assert chosen[0] in (0, 1) and chosen[1] in (0, 1), chosen
+        lev = O.h.levels[l]
+        n = lev.A.shape[0]
+        B = rng.standard_normal((8, n))
+        D0 = rng.standard_normal((8, n))
+        refs = [smooth(lev, B[k], D0[k].copy(), 0.7, 2) for k in range(8)]
+        d = dev(D0)
+        S.smooth_batch(l, 8, dev(B), d, n_sweeps=2, zero_init=False)
+        base = host(d)
+        for split in (0, 1):
+            for deep in (0, 1):
+                try:
+                    S.set_tc_shape(l, split, deep)
+                except st.StfemError:
+                    assert deep == 1  # no deeper ring fits next to these patches
+                    continue
+                assert S.tc_shape(l) == (split, deep)
+                n_split += split
+                for cap in (0, 3):
+                    S.set_launch_cap(cap)
+                    d = dev(D0)
+                    S.smooth_batch(l, 8, dev(B), d, n_sweeps=2, zero_init=False)
+                    D = host(d)
+                    for k in range(8):
+                        err = _rel(D[k], refs[k])
+                        assert err < 2.5e-3, (split, deep, cap, l, k, err)
+                    assert np.array_equal(D, base), (split, deep, cap, l)
+                S.set_launch_cap(0)
+        S.set_tc_shape(l, *chosen)
+        print(name, "tc level", l, "picked", chosen, "every shape ok")
+    assert n_split > 0
+    with pytest.raises(st.StfemError):
+        S.set_tc_shape(1, 2, 0)
+    S.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_capped_vcycle_and_solve_unchanged(precision):
     """A whole V-cycle and slab solve with every persistent launch capped at
