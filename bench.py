@@ -272,6 +272,28 @@ def dram_traffic(workload, precision):
     return r.get("bytes_per_launch")
 
 
+def tc_source_hash():
+    """Hash of the tensor-core patch apply's source (tc_patch.cuh)."""
+    with open(os.path.join(ROOT, "paper_2303_06742_gb300", "csrc", "tc_patch.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def dram_traffic_tc(workload, nb):
+    """Per-launch DRAM bytes of the tensor-core patch apply with nb columns from
+    the committed ncu summary, if it was taken on the current kernel source;
+    else None."""
+    p = os.path.join(ROOT, "profiles", "traffic_k_patch_apply_tc_%s.json" % workload)
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    r = rec.get("%s/tc%d/patch_apply" % (workload, nb))
+    if not r or r.get("source_hash") != tc_source_hash():
+        return None
+    return r.get("bytes_per_launch")
+
+
 def job_throughput(units_per_rank, total_ms, world, dist=None, device="cuda"):
     """Whole-job throughput of independent replicas: every rank processed
     units_per_rank units in its own total_ms; the job took the slowest rank's
@@ -704,7 +726,8 @@ def batch_arm(args):
                                "note": "same operator, one march at a time, FP32 CUDA-core patch apply"},
         "roofline": {"kernel": "k_patch_apply_tc", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
-                     "traffic": None, "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
+                     "traffic": dram_traffic_tc(args.workload, nb),
+                     "algorithmic_bytes_per_launch": pa["bytes"] / max(pa["launches"], 1),
                      "avg_launch_ms": pa["ms"] / max(pa["launches"], 1), "launches": pa["launches"],
                      "tc_shapes": tc_shapes},
         "breakdown": breakdown, "gpu_launches": launches, "clocks": clk,
