@@ -1677,8 +1677,12 @@ int build_tc_tiles_device(stfem_h h, DLevel<float> &D, const stfem::Patches &P) 
     h->err = "patches too large for the tensor-core patch apply (shared memory)";
     return STFEM_ERR_ARG;
   }
-  uint32_t cols = 32;
-  while (cols < (uint32_t)(16 * ((c8max + 127) / 128))) cols *= 2;
+  // one accumulator per slot and M tile; two CTAs per SM share its 512 columns
+  const uint32_t cols = tcp::tmem_cols(ns, c8max);
+  if (cols > 512u / STFEM_TC_CTAS_PER_SM) {
+    h->err = "patches too large for the tensor-core patch apply (tensor memory)";
+    return STFEM_ERR_ARG;
+  }
   std::vector<long long> off(P.npatch + 1, 0);
   for (long p = 0; p < P.npatch; ++p) {
     const long long c8 = tcp::cs8(P.cs[p]);
@@ -1727,9 +1731,12 @@ int upload_tc_tiles(stfem_h h, DLevel<float> &D, const stfem::Patches &P) {
     h->err = "patches too large for the tensor-core patch apply (shared memory)";
     return STFEM_ERR_ARG;
   }
-  const int ntile = (c8max + 127) / 128;
-  uint32_t cols = 32;
-  while (cols < (uint32_t)(16 * ntile)) cols *= 2;
+  // one accumulator per slot and M tile; two CTAs per SM share its 512 columns
+  const uint32_t cols = tcp::tmem_cols(ns, c8max);
+  if (cols > 512u / STFEM_TC_CTAS_PER_SM) {
+    h->err = "patches too large for the tensor-core patch apply (tensor memory)";
+    return STFEM_ERR_ARG;
+  }
   std::vector<long long> off(P.npatch + 1, 0);
   for (long p = 0; p < P.npatch; ++p) {
     const long long c8 = tcp::cs8(P.cs[p]);

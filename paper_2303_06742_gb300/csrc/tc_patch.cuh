@@ -25,13 +25,19 @@
 // (K blocks in ascending order into the same accumulator), so the result does
 // not depend on how patches are cut into items or spread over CTAs.
 //
+// Every slot of an item has its own B operand in shared memory and its own
+// accumulator in tensor memory (slot a, tile t at column 16 (a ntl + t)), so
+// the MMAs of all slots run back to back, and the epilogue mixes the slots
+// back to the time nodes straight from tensor memory.
+//
 // Warp roles (320 threads): warp 0 streams A through a ring of stages
 // (cp.async.bulk, mbarrier transaction counts); warp 1 owns the tensor
 // memory and one lane issues the MMAs; warps 2..9 gather and transform the
-// residual columns, write B, read D back (tcgen05.ld) and mix the result back
-// to the time nodes.  Every wait is bounded (clock64); on a timeout the CTA
-// sets *err and every role leaves at its next uniform decision point after
-// draining its own copies / MMAs.
+// residual columns (the next item's while the MMAs of this one run), write
+// B, read D back (tcgen05.ld) and mix the result back to the time nodes.
+// Every wait is bounded (clock64); on a timeout the CTA sets *err and every
+// role leaves at its next uniform decision point after draining its own
+// copies / MMAs.
 
 // CTAs of the tensor-core kernel resident per SM (the registers per thread
 // are bounded to fit them).
@@ -92,13 +98,20 @@ __device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 2, %0;" ::"
 __host__ __device__ __forceinline__ int cs8(int cs) { return (cs + 7) / 8 * 8; }
 // K extent of slot a (real slots first)
 __host__ __device__ __forceinline__ int kext(int a, int nr, int c8) { return a < nr ? c8 : 2 * c8; }
-// K blocks per stage copy
-__host__ __device__ __forceinline__ int kpb(int c8) { return STAGE / (c8 * 32); }
+// first K row of slot a in the slots' stacked K extents (units of Cs8)
+__host__ __device__ __forceinline__ int krow(int a, int nr) { return a < nr ? a : nr + 2 * (a - nr); }
+// tensor-memory columns of the accumulators: ns slots x ntile tiles x 16,
+// allocated as a power of two >= 32
+__host__ __device__ inline uint32_t tmem_cols(int ns, int c8max) {
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(16 * ns * ((c8max + 127) / 128))) cols *= 2;
+  return cols;
+}
 
 struct Smem {
   unsigned char *stage; // MAXSTAGES * STAGE + SLACK (nst used)
-  float *B;             // 16 x Kmax, core layout [kb][n group][k core]
-  float *xt;            // [slot rows (nr + 2 nc)][8][maxCs]: transformed residual, then z
+  float *B;             // per slot 16 x K_a, core layout [kb][n group][k core]; slots stacked
+  float *xt;            // [slot rows (nr + 2 nc)][8][maxCs]: transformed residual
   uint64_t *full, *empty, *bfull, *afull, *aempty, *drain;
   uint32_t *tmem;
   volatile int *flag; // [0] abort, [1] consumer decision
@@ -110,7 +123,7 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int nst, int maxCs, i
   s.stage = base + o;
   o += (size_t)nst * STAGE + SLACK;
   s.B = reinterpret_cast<float *>(base + o);
-  o += (size_t)16 * 2 * cs8(maxCs) * sizeof(float);
+  o += (size_t)16 * nrow * cs8(maxCs) * sizeof(float);
   s.xt = reinterpret_cast<float *>(base + o);
   o += (size_t)nrow * 8 * maxCs * sizeof(float);
   o = (o + 7) / 8 * 8;
@@ -126,7 +139,7 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int nst, int maxCs, i
 }
 
 __host__ __device__ inline size_t smem_bytes(int nst, int maxCs, int nrow) {
-  size_t o = (size_t)nst * STAGE + SLACK + (size_t)16 * 2 * cs8(maxCs) * sizeof(float) +
+  size_t o = (size_t)nst * STAGE + SLACK + (size_t)16 * nrow * cs8(maxCs) * sizeof(float) +
              (size_t)nrow * 8 * maxCs * sizeof(float);
   o = (o + 7) / 8 * 8;
   return o + (2 * MAXSTAGES + 4) * 8 + 16;
@@ -221,23 +234,25 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      long long it = 0, nslot = 0;
+      long long it = 0, nph = 0;
       bool ok = true;
       const uint32_t bbase = smem_addr(S.B);
-      for (int i = blockIdx.x; i < nitem && ok; i += gridDim.x) {
+      for (int i = blockIdx.x; i < nitem && ok; i += gridDim.x, ++nph) {
         const int2 w = items[i];
         const int p = w.x, t0 = w.y & 0xffff, t1 = w.y >> 16;
         const int c8 = cs8(pcs[p]), ntl = t1 - t0;
         const int rb = (min(t1 * 128, c8) - t0 * 128) * 32, per = STAGE / rb;
-        for (int a = 0; a < ns && ok; ++a, ++nslot) {
-          // B of this slot written; D free (its previous contents read back)
-          if (!mbar_wait(S.bfull, (uint32_t)(nslot & 1), WAIT) ||
-              (nslot > 0 && !mbar_wait(S.aempty, (uint32_t)((nslot - 1) & 1), WAIT)) || S.flag[0]) {
-            ok = false;
-            break;
-          }
-          fence_after();
+        // the item's B operands written; D free (the previous item's read back)
+        if (!mbar_wait(S.bfull, (uint32_t)(nph & 1), WAIT) ||
+            (nph > 0 && !mbar_wait(S.aempty, (uint32_t)((nph - 1) & 1), WAIT)) || S.flag[0]) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        for (int a = 0; a < ns && ok; ++a) {
           const int nkb = kext(a, nr, c8) / 8;
+          const uint32_t bslot = bbase + (uint32_t)(16 * c8 * krow(a, nr)) * 4u;
+          const uint32_t dslot = tbase + (uint32_t)(a * ntl * 16);
           for (int kb = 0; kb < nkb; kb += per) {
             const int st = (int)(it % nst);
             if (!mbar_wait(&S.full[st], (uint32_t)((it / nst) & 1), WAIT)) {
@@ -248,18 +263,18 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
             const uint32_t sbase = smem_addr(S.stage + (size_t)st * STAGE);
             const int nk = min(per, nkb - kb);
             for (int j = 0; j < nk; ++j) {
-              const uint64_t bd = sdesc(bbase + (uint32_t)(kb + j) * 512u, 128u, 256u);
+              const uint64_t bd = sdesc(bslot + (uint32_t)(kb + j) * 512u, 128u, 256u);
               for (int mt = 0; mt < ntl; ++mt) {
                 const uint64_t ad = sdesc(sbase + (uint32_t)(j * rb + mt * 4096), 128u, 256u);
-                mma_tf32(tbase + (uint32_t)(mt * 16), ad, bd, (kb + j) > 0 ? 1u : 0u);
+                mma_tf32(dslot + (uint32_t)(mt * 16), ad, bd, (kb + j) > 0 ? 1u : 0u);
               }
             }
             commit(&S.empty[st]); // stage free once these MMAs have read it
             ++it;
           }
-          if (!ok) break;
-          commit(S.afull);
         }
+        if (!ok) break;
+        commit(S.afull); // every slot's D of the item complete
       }
       if (!ok) {
         atomicExch(err, 4);
@@ -309,11 +324,13 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
         }
       }
     };
-    // B operand of slot a from xt (see the layout above)
+    // B operand of slot a from xt (see the layout above), at its place in the
+    // stacked slots
     auto write_b = [&](int a, int Cs, int c8) {
       const int K = kext(a, nr, c8);
       const bool cplx = a >= nr;
-      const int row = cplx ? nr + 2 * (a - nr) : a;
+      const int row = krow(a, nr);
+      float *Bs = S.B + (size_t)16 * c8 * row;
       // a thread writes one 16-byte core row: k0 .. k0 + 3 of column n
       for (int idx = tid; idx < 4 * K; idx += NCONS) {
         const int k0 = (idx >> 4) * 4, n = idx & 15;
@@ -334,62 +351,17 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
           }
         }
         const int kb = k0 >> 3, kc = (k0 >> 2) & 1, ng = n >> 3, rr = n & 7;
-        *reinterpret_cast<float4 *>(&S.B[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4]) =
+        *reinterpret_cast<float4 *>(&Bs[(size_t)kb * 128 + (ng * 2 + kc) * 32 + rr * 4]) =
             make_float4(v[0], v[1], v[2], v[3]);
       }
     };
-    long long nslot = 0;
-    if (ns == 1) {
-      // One slot per patch (dG(0) or dG(1)): the next patch is gathered while
-      // the MMAs of this one run, and the epilogue mixes D straight back to
-      // the time nodes (y = V z, complex: 2 Re(V z)).
-      const bool cplx = nc == 1;
-      if (blockIdx.x < nitem) gather(items[blockIdx.x].x);
-      for (int i = blockIdx.x; i < nitem; i += gridDim.x, ++nslot) {
-        cons_sync(); // xt of the item's patch complete
-        if (tid == 0) S.flag[1] = S.flag[0];
-        cons_sync();
-        if (S.flag[1]) break;
-        const int2 w = items[i];
-        const int p = w.x, t0 = w.y & 0xffff, ntl = (w.y >> 16) - t0;
-        const int Cs = pcs[p], c8 = cs8(Cs);
-        const long long doff = pdoff[p];
-        write_b(0, Cs, c8);
-        fence_async_smem();
-        cons_sync();
-        if (tid == 0) mbar_arrive(S.bfull);
-        if (i + (int)gridDim.x < nitem) gather(items[i + gridDim.x].x);
-        if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nslot & 1), WAIT) ? 0 : 1;
-        cons_sync();
-        if (S.flag[1]) {
-          if (tid == 0) {
-            atomicExch(err, 5);
-            S.flag[0] = 1;
-          }
-          break;
-        }
-        fence_after();
-        for (int mt = group; mt < ntl; mt += 2) {
-          float v[16];
-          __syncwarp();
-          ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
-          const int m = (t0 + mt) * 128 + quarter * 32 + lane;
-          if (m < Cs)
-            for (int c = 0; c < nb; ++c)
-#pragma unroll
-              for (int b = 0; b < Q; ++b) {
-                const float vr = dc.V[b * 2], vi = dc.V[b * 2 + 1];
-                y[(long)c * ystride + doff + b * Cs + m] = cplx ? 2.f * (vr * v[c] - vi * v[8 + c]) : vr * v[c];
-              }
-        }
-        fence_before();
-        cons_sync();
-        if (tid == 0) mbar_arrive(S.aempty);
-      }
-    } else
-    for (int i = blockIdx.x; i < nitem; i += gridDim.x) {
-      // uniform decision to go on
-      cons_sync();
+    // The next item's patch is gathered while the MMAs of this one run; the
+    // epilogue mixes every slot's D straight back to the time nodes:
+    // y_b = sum over real slots V_ba z_a + sum over complex slots 2 Re(V_ba z_a).
+    long long nph = 0;
+    if (blockIdx.x < nitem) gather(items[blockIdx.x].x);
+    for (int i = blockIdx.x; i < nitem; i += gridDim.x, ++nph) {
+      cons_sync(); // xt of the item's patch complete
       if (tid == 0) S.flag[1] = S.flag[0];
       cons_sync();
       if (S.flag[1]) break;
@@ -397,63 +369,58 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
       const int p = w.x, t0 = w.y & 0xffff, ntl = (w.y >> 16) - t0;
       const int Cs = pcs[p], c8 = cs8(Cs);
       const long long doff = pdoff[p];
-      gather(p);
+      for (int a = 0; a < ns; ++a) write_b(a, Cs, c8);
+      fence_async_smem();
       cons_sync();
-      bool stop = false;
-      for (int a = 0; a < ns; ++a, ++nslot) {
-        // B of slot a (the previous slot's MMAs have completed: afull waited)
-        const bool cplx = a >= nr;
-        const int row = cplx ? nr + 2 * (a - nr) : a;
-        write_b(a, Cs, c8);
-        fence_async_smem();
-        cons_sync();
-        if (tid == 0) mbar_arrive(S.bfull);
-        // D of slot a complete
-        if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nslot & 1), WAIT) ? 0 : 1;
-        cons_sync();
-        if (S.flag[1]) {
-          if (tid == 0) {
-            atomicExch(err, 5);
-            S.flag[0] = 1;
-          }
-          stop = true;
-          break;
+      if (tid == 0) mbar_arrive(S.bfull);
+      if (i + (int)gridDim.x < nitem) gather(items[i + gridDim.x].x);
+      if (tid == 0) S.flag[1] = mbar_wait(S.afull, (uint32_t)(nph & 1), WAIT) ? 0 : 1;
+      cons_sync();
+      if (S.flag[1]) {
+        if (tid == 0) {
+          atomicExch(err, 5);
+          S.flag[0] = 1;
         }
-        fence_after();
-        for (int mt = group; mt < ntl; mt += 2) {
+        break;
+      }
+      fence_after();
+      for (int mt = group; mt < ntl; mt += 2) {
+        float o[8][Q];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int b = 0; b < Q; ++b) o[c][b] = 0.f;
+        for (int a = 0; a < ns; ++a) {
           float v[16];
           __syncwarp();
-          ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), v);
-          const int m = (t0 + mt) * 128 + quarter * 32 + lane;
-          if (m < Cs) {
-            if (!cplx) {
-              for (int c = 0; c < nb; ++c) S.xt[((size_t)row * 8 + c) * maxCs + m] = v[c];
-            } else {
-              for (int c = 0; c < nb; ++c) {
-                S.xt[((size_t)row * 8 + c) * maxCs + m] = v[c];
-                S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m] = v[8 + c];
-              }
+          ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((a * ntl + mt) * 16), v);
+          if (a < nr) {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+              const float vr = dc.V[(b * ns + a) * 2];
+#pragma unroll
+              for (int c = 0; c < 8; ++c) o[c][b] += vr * v[c];
+            }
+          } else {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+              const float vr = dc.V[(b * ns + a) * 2], vi = dc.V[(b * ns + a) * 2 + 1];
+#pragma unroll
+              for (int c = 0; c < 8; ++c) o[c][b] += 2.f * (vr * v[c] - vi * v[8 + c]);
             }
           }
         }
-        fence_before();
-        cons_sync();
-        if (tid == 0) mbar_arrive(S.aempty);
+        const int m = (t0 + mt) * 128 + quarter * 32 + lane;
+        if (m < Cs)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < nb)
+#pragma unroll
+              for (int b = 0; b < Q; ++b) y[(long)c * ystride + doff + b * Cs + m] = o[c][b];
       }
-      if (stop) break;
-      // back to the time nodes: y[c][b][m] for the item's rows m0 <= m < m0 + nm
-      const int m0 = t0 * 128, nm = min((t0 + ntl) * 128, Cs) - m0;
-      for (int idx = tid; idx < nb * Q * nm; idx += NCONS) {
-        const int c = idx / (Q * nm), rem = idx - c * Q * nm, b = rem / nm, m = m0 + rem - b * nm;
-        float val = 0.f;
-        for (int a = 0; a < nr; ++a) val += dc.V[(b * ns + a) * 2] * S.xt[((size_t)a * 8 + c) * maxCs + m];
-        for (int cc = 0; cc < nc; ++cc) {
-          const int a = nr + cc, row = nr + 2 * cc;
-          val += 2.f * (dc.V[(b * ns + a) * 2] * S.xt[((size_t)row * 8 + c) * maxCs + m] -
-                        dc.V[(b * ns + a) * 2 + 1] * S.xt[((size_t)(row + 1) * 8 + c) * maxCs + m]);
-        }
-        y[(long)c * ystride + doff + b * Cs + m] = val;
-      }
+      fence_before();
+      cons_sync();
+      if (tid == 0) mbar_arrive(S.aempty);
     }
   }
   fence_before();
