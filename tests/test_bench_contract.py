@@ -28,3 +28,31 @@ def test_job_throughput_alone():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.job_throughput(20, 1000.0, 1) == (20.0, 1000.0)
+
+
+def test_traffic_records_follow_the_kernel_source(tmp_path, monkeypatch):
+    """The committed ncu DRAM traffic enters the bench line only while the
+    kernel source it was taken on is unchanged: a record with another hash
+    gives None, one with the current hash gives its bytes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2303_06742_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in ("stfem.cu", "vanka.cuh", "tc_patch.cuh"):
+        with open(os.path.join(ROOT, "paper_2303_06742_gb300", "csrc", name), "rb") as f:
+            (csrc / name).write_bytes(f.read())
+    key_s, key_t = "w/mixed/patch_apply", "w/tc8/patch_apply"
+    (prof / "traffic_k_patch_apply_stream_w.json").write_text(
+        json.dumps({key_s: {"bytes_per_launch": 123, "source_hash": bench.kernel_source_hash()}}))
+    (prof / "traffic_k_patch_apply_tc_w.json").write_text(
+        json.dumps({key_t: {"bytes_per_launch": 456, "source_hash": bench.tc_source_hash()}}))
+    assert bench.dram_traffic("w", "mixed") == 123
+    assert bench.dram_traffic_tc("w", 8) == 456
+    assert bench.dram_traffic_tc("w", 4) is None
+    # a changed kernel invalidates its record, and only its own
+    (csrc / "tc_patch.cuh").write_bytes((csrc / "tc_patch.cuh").read_bytes() + b"\n// changed\n")
+    assert bench.dram_traffic_tc("w", 8) is None
+    assert bench.dram_traffic("w", "mixed") == 123
