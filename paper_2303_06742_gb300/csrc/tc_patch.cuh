@@ -292,9 +292,9 @@ __global__ void __launch_bounds__(tcp::THREADS, STFEM_TC_CTAS_PER_SM)
     const int group = cw >> 2;        // tiles mt = group, group + 2, ...
     // gather the nb residual columns of patch p and transform them to the
     // slots: xt[row][c][m], row = real slot a, or 2 rows (re, im) per complex slot.
-    // A thread takes one patch row m: its Q slab indices are loaded once and
-    // the 8 Q residual values behind them are all requested before the first
-    // is used (one dependent load pair per row instead of one per column).
+    // A thread takes one patch row m: its Q slab indices are loaded once for
+    // all columns, and the 8 Q residual values behind them are all requested
+    // before the first is used.
     auto gather = [&](int p) {
       const int Cs = pcs[p];
       const long long doff = pdoff[p];
