@@ -31,4 +31,13 @@ Modules and what they follow:
 
 Where the paper is silent or garbled, the reading taken is stated in the
 docstring of the function that depends on it.
+
+Parity unpinned: one term, the boundary part of Problem B.1's previous-slab
+coupling with nonzero displacement traces (``slab.slab_rhs``, form "B.1").
+The oracle takes the data u_D(t_{n-1}), as printed.  With u^- in its place
+the errors of Table 5.1 agree to 1e-11, and the paper's other printed
+problems also have zero traces, so no printed value decides it.
+Every other function is pinned by the tests under ``tests/test_oracle_*``.
+The broken pair's pressure and the k = 3, r = 4 tables are pinned by their
+convergence orders, not by their printed digits.
 """
