@@ -61,6 +61,9 @@ def parse():
                         "batched path with the tensor-core patch apply")
     p.add_argument("--form", default="3.1", choices=["3.1", "B.1"],
                    help="slab problem: Problem 3.1 (default) or Problem B.1 of Appendix B")
+    p.add_argument("--pressure", default="continuous", choices=["continuous", "broken"],
+                   help="pressure space: Taylor-Hood Q_{r-1} (default) or the broken pair's P_{r-1}^disc "
+                        "with the interior penalty form")
     p.add_argument("--fine-operator", default="auto", choices=["auto", "assembled", "matrix-free"],
                    help="operator of the finest level inside the mixed-precision V-cycle")
     p.add_argument("--stream-shapes", default=None,
@@ -75,7 +78,7 @@ def parse():
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_leg(workload, out_path, mode, steps=0, warmup=0, form="3.1"):
+def oracle_leg(workload, out_path, mode, steps=0, warmup=0, form="3.1", pressure="continuous"):
     """Runs the oracle (test infrastructure) in this process on the host cores.
 
     mode "solve": set up, time one full slab solve (slab 0), save the solution.
@@ -89,7 +92,7 @@ def oracle_leg(workload, out_path, mode, steps=0, warmup=0, form="3.1"):
     from oracle.slab import repeat_state
     c = inputs.case(workload)
     t0 = time.perf_counter()
-    O = oracle_instance(c, form=form)
+    O = oracle_instance(c, form=form, pressure="disc" if pressure == "broken" else "cont")
     t_setup = time.perf_counter() - t0
     st0 = O.initial_state()
     b = O.rhs(0, st0)
@@ -135,7 +138,7 @@ def host_cpu():
     return os.cpu_count() or 1, model
 
 
-def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1", threads=1):
+def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1", threads=1, pressure="continuous"):
     """The oracle in a subprocess with `threads` BLAS/OpenMP threads (the
     oracle's library calls are the only parallel part of it)."""
     fd, path = tempfile.mkstemp(suffix=".json")
@@ -146,7 +149,7 @@ def run_oracle_subprocess(workload, mode, steps=0, warmup=0, form="3.1", threads
     env["CUDA_VISIBLE_DEVICES"] = ""
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", path, "--workload", workload,
            "--steps", str(steps), "--warmup", str(warmup), "--impl", "reference" if mode == "reference" else "ours",
-           "--form", form]
+           "--form", form, "--pressure", pressure]
     subprocess.run(cmd, check=True, env=env)
     with open(path) as f:
         res = json.load(f)
@@ -320,12 +323,13 @@ def pct(vals, q):
 FINE_OPERATORS = {"auto": 0, "assembled": 1, "matrix-free": 2}
 
 
-def make_solver(c, precision, stream, sweeps=1, form="3.1", fine_operator="auto"):
+def make_solver(c, precision, stream, sweeps=1, form="3.1", fine_operator="auto", pressure="continuous"):
     import paper_2303_06742_gb300 as st
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from _cases import gpu_problem
     f = st.FORM_PROBLEM_B_1 if form == "B.1" else st.FORM_PROBLEM_3_1
-    return st.Solver(gpu_problem(c, form=f), precision=precision, stream=stream, n_sweeps=sweeps,
+    pr = st.PRESSURE_BROKEN if pressure == "broken" else st.PRESSURE_CONTINUOUS
+    return st.Solver(gpu_problem(c, form=f, pressure=pr), precision=precision, stream=stream, n_sweeps=sweeps,
                      fine_operator=FINE_OPERATORS[fine_operator])
 
 
@@ -368,7 +372,7 @@ def gpu_arm(args):
 
     # ---- mixed precision (headline)
     t0 = time.perf_counter()
-    S = make_solver(c, st.MIXED, stream, args.sweeps, args.form, args.fine_operator)
+    S = make_solver(c, st.MIXED, stream, args.sweeps, args.form, args.fine_operator, args.pressure)
     setup_s = time.perf_counter() - t0
     if args.stream_shapes:
         for item in args.stream_shapes.split(";"):
@@ -443,7 +447,7 @@ def gpu_arm(args):
     fp64 = None
     if not args.no_fp64:
         t0 = time.perf_counter()
-        S64 = make_solver(c, st.FP64, stream, args.sweeps, args.form)
+        S64 = make_solver(c, st.FP64, stream, args.sweeps, args.form, pressure=args.pressure)
         setup64 = time.perf_counter() - t0
         st64 = torch.zeros(S64.n_state, dtype=torch.float64, device="cuda")
         S64.initial_state(st64)
@@ -481,7 +485,7 @@ def gpu_arm(args):
     err_vs_oracle = None
     if not args.no_cpu_baseline:
         nproc, model = host_cpu()
-        res, sol = run_oracle_subprocess(args.workload, "solve", form=args.form)
+        res, sol = run_oracle_subprocess(args.workload, "solve", form=args.form, pressure=args.pressure)
         cpu = {"value": 1.0 / res["solve_s"], "unit": "slab solves/s", "cores": 1, "kind": "oracle",
                "nproc": nproc, "cpu_model": model,
                "sample": "one full slab solve (slab 0, FGMRES-GMG to %g, %d iterations) of the same workload; "
@@ -490,7 +494,8 @@ def gpu_arm(args):
         if sol is not None:
             err_vs_oracle = float(np.abs(x_slab0_host - sol).max() / np.abs(sol).max())
         # the same oracle with its library calls free to use every host core
-        resa, _ = run_oracle_subprocess(args.workload, "solve", form=args.form, threads=nproc)
+        resa, _ = run_oracle_subprocess(args.workload, "solve", form=args.form, threads=nproc,
+                                        pressure=args.pressure)
         cpu["all_cores"] = {
             "value": 1.0 / resa["solve_s"], "unit": "slab solves/s", "cores": round(resa["threads_used"], 2),
             "threads_allowed": nproc, "nproc": nproc, "cpu_model": model, "kind": "oracle",
@@ -538,10 +543,13 @@ def bench_config(args, world):
     """The `config` of the JSON line: the workload, identical for both arms."""
     import inputs
     c = inputs.case(args.workload)
-    return {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "form": "Problem %s" % args.form,
-            "tol": c["tol"], "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
-            "l2": "inputs larger than L2: the patch inverses streamed per sweep set exceed the 129 MB L2",
-            "parallelism": "replicas" if world > 1 else "single"}
+    cfg = {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "form": "Problem %s" % args.form,
+           "tol": c["tol"], "restart": 30, "omega": 0.7, "sweeps": args.sweeps,
+           "l2": "inputs larger than L2: the patch inverses streamed per sweep set exceed the 129 MB L2",
+           "parallelism": "replicas" if world > 1 else "single"}
+    if args.pressure == "broken":
+        cfg["pressure_space"] = "broken P_{r-1}^disc with the interior penalty form (instead of Q_{r-1})"
+    return cfg
 
 
 # ------------------------------------------------------------------ reference arm
@@ -552,7 +560,7 @@ def reference_arm(args):
     import inputs
     c = inputs.case(args.workload)
     res, _ = run_oracle_subprocess(args.workload, "reference", steps=args.steps, warmup=args.warmup,
-                                   form=args.form)
+                                   form=args.form, pressure=args.pressure)
     per_iter = res["per_iter_s"]
     iters = res["iters"]
     t_slab = statistics.mean(per_iter) * iters
@@ -851,7 +859,7 @@ def main():
         return
     if args.cpu_leg:
         oracle_leg(args.workload, args.cpu_leg, "reference" if args.impl == "reference" else "solve",
-                   args.steps, args.warmup, args.form)
+                   args.steps, args.warmup, args.form, args.pressure)
         return
     if args.impl == "reference":
         reference_arm(args)
