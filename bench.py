@@ -259,16 +259,17 @@ def kernel_source_hash():
     return hashlib.sha256(src[a:b] + van[c:d]).hexdigest()[:16]
 
 
-def dram_traffic(workload, precision):
+def dram_traffic(workload, precision, pressure="continuous"):
     """Per-launch DRAM bytes of the patch-apply kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    summary of this workload and pressure space, if it was taken on the
+    current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "traffic_k_patch_apply_stream_%s.json" % workload)
     try:
         with open(p) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    key = "%s/%s/patch_apply" % (workload, precision)
+    key = "%s/%s/patch_apply" % (workload, precision if pressure == "continuous" else precision + "-broken")
     r = rec.get(key)
     if not r or r.get("source_hash") != kernel_source_hash():
         return None
@@ -464,7 +465,7 @@ def gpu_arm(args):
     pa = prof["patch_apply"]
     peak, peak_kind = peak_hbm()
     achieved = pa["bytes"] / (pa["ms"] / 1000.0) / 1e9 if pa["ms"] > 0 else None
-    traffic = dram_traffic(args.workload, "mixed")
+    traffic = dram_traffic(args.workload, "mixed", args.pressure)
     roof = {"kernel": "patch apply: k_patch_apply_stream<float> (levels with more than one patch per SM), "
                       "k_patch_apply_wide<float> (the others)",
             "workload": args.workload, "bound": "hbm", "achieved": achieved, "peak": peak,

@@ -50,6 +50,7 @@ def test_traffic_records_follow_the_kernel_source(tmp_path, monkeypatch):
     (prof / "traffic_k_patch_apply_tc_w.json").write_text(
         json.dumps({key_t: {"bytes_per_launch": 456, "source_hash": bench.tc_source_hash()}}))
     assert bench.dram_traffic("w", "mixed") == 123
+    assert bench.dram_traffic("w", "mixed", "broken") is None  # another pressure space
     assert bench.dram_traffic_tc("w", 8) == 456
     assert bench.dram_traffic_tc("w", 4) is None
     # a changed kernel invalidates its record, and only its own
