@@ -651,6 +651,18 @@ const char *stfem_last_error(stfem_h h);
 int stfem_host_block_apply(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
                            const stfem_bcs *bcs, double tau, int level, const double *x_host, double *y_host);
 
+/* CPU check of the structure test of the node-level Galerkin product
+ * P^T A_l P (the coarse operators): level l (1 .. n_levels-1, or -1 for the
+ * finest) of the host hierarchy goes through the product, with the first
+ * (drop_last = 0) or last (drop_last = 1) entry of its spatial row drop_row
+ * removed first when drop_row >= 0 (rows: u-equations d*node+c, then
+ * v-equations, then p-equations).  STFEM_OK if the level has the node-block
+ * structure the product needs; STFEM_ERR_STATE, with the message in
+ * stfem_host_last_error(), if not; STFEM_ERR_ARG for a level or row out of
+ * range. */
+int stfem_host_galerkin_check(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                              const stfem_bcs *bcs, double tau, int level, long long drop_row, int drop_last);
+
 const char *stfem_host_last_error(void);
 
 /* Frees every resource of the handle.  NULL is ignored. */

@@ -125,6 +125,8 @@ def _load():
                                     C.POINTER(BCs), D, I, pLL, pLL, pLL, pI, pD],
         "stfem_host_block_apply": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material), C.POINTER(BCs), D,
                                    I, pD, pD],
+        "stfem_host_galerkin_check": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material), C.POINTER(BCs),
+                                      D, I, C.c_longlong, I],
         "stfem_host_patch_dofs": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
                                   C.POINTER(BCs), D, I, I, pLL, pLL, pLL, pI],
         "stfem_host_prolongation": [C.POINTER(Mesh), C.POINTER(Degrees), C.POINTER(Material),
@@ -246,6 +248,13 @@ def host_block_apply(prob, x, level=-1):
     y = np.zeros_like(x)
     _host_check(lib.stfem_host_block_apply(*prob.args(), level, _dptr(x), _dptr(y)))
     return y
+
+
+def host_galerkin_check(prob, level=-1, drop_row=-1, drop_last=True):
+    """Runs the Galerkin product's structure test on a level of the host
+    hierarchy, optionally with the first or last entry of one spatial row
+    removed; raises StfemError (ERR_STATE) if the test rejects the level."""
+    _host_check(lib.stfem_host_galerkin_check(*prob.args(), int(level), int(drop_row), int(bool(drop_last))))
 
 
 def host_patch_dofs(prob, level=-1, patch_kind=PATCHES_VERTEX):

@@ -125,6 +125,38 @@ int stfem_host_block_apply(const stfem_mesh *mesh, const stfem_degrees *deg, con
   return stfem::block_apply_level(L[level], T.q, T.Dt.data(), W.data(), x, y, &g_host_err);
 }
 
+int stfem_host_galerkin_check(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
+                              const stfem_bcs *bcs, double tau, int level, long long drop_row, int drop_last) {
+  std::vector<stfem::Level> L;
+  std::vector<stfem::CSR> Pu, Pp;
+  int rc = build(mesh, deg, mat, bcs, tau, &L, &Pu, &Pp);
+  if (rc < 0) return rc;
+  if (level == -1) level = (int)L.size() - 1;
+  if (level < 1 || level >= (int)L.size()) {
+    g_host_err = "level out of range (levels 1 .. n_levels-1 have a coarser level)";
+    return STFEM_ERR_ARG;
+  }
+  stfem::Level F = L[level];
+  if (drop_row >= 0) {
+    const long nrows = (long)F.rowptr.size() - 1;
+    if (drop_row >= nrows || F.rowptr[drop_row] == F.rowptr[drop_row + 1]) {
+      g_host_err = "drop_row out of range or empty";
+      return STFEM_ERR_ARG;
+    }
+    const long e = drop_last ? F.rowptr[drop_row + 1] - 1 : F.rowptr[drop_row];
+    F.col.erase(F.col.begin() + e);
+    F.v1.erase(F.v1.begin() + e);
+    F.v2.erase(F.v2.begin() + e);
+    for (long i = drop_row + 1; i <= nrows; ++i) --F.rowptr[i];
+  }
+  stfem::Level C = L[level - 1];
+  if (!stfem::galerkin(F, Pu[level], Pp[level], &C)) {
+    g_host_err = "level " + std::to_string(level) + " does not have the node-block structure of the Galerkin product";
+    return STFEM_ERR_STATE;
+  }
+  return STFEM_OK;
+}
+
 int stfem_host_prolongation(const stfem_mesh *mesh, const stfem_degrees *deg, const stfem_material *mat,
                             const stfem_bcs *bcs, double tau, int level, int field, long long *nrows,
                             long long *ncols, long long *nnz, long long *rowptr, int *col, double *val) {

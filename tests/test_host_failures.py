@@ -26,3 +26,26 @@ def test_admission_refuses_oversized_and_device_less_requests():
             big.submit(prob, -1)
     finally:
         big.close()
+
+
+@pytest.mark.parametrize("dim,r,form", [(2, 2, 0), (2, 3, 1), (3, 2, 0)])
+def test_galerkin_structure_rejects_a_dropped_entry(dim, r, form):
+    """The coarse operators are node-level Galerkin products P^T A_l P: each
+    node's blocks are read from the rows of its displacement component 0 and
+    every other component's rows must repeat that pattern.  A level with one
+    entry removed from a u- or v-equation row (component 1's first or last
+    entry: a shifted pattern or a strict prefix of component 0's; or
+    component 0's own last entry) is rejected with ERR_STATE, instead of
+    giving a coarse operator that is no longer P^T A_l P."""
+    n = 4
+    prob = stfem.Problem(dim, n, 2, r, 1, 0.01, problem=stfem.PROBLEM_SIN, form=form)
+    stfem.host_galerkin_check(prob, level=1)  # the level as assembled passes
+    R = dim * (r * n + 1) ** dim  # u-equation rows: d per Q_r node
+    for row, last in [(1, True), (1, False), (0, True), (R + 1, True), (R + 1, False)]:
+        with pytest.raises(stfem.StfemError) as e:
+            stfem.host_galerkin_check(prob, level=1, drop_row=row, drop_last=last)
+        assert e.value.code == stfem.ERR_STATE, (row, last)
+        assert "node-block structure" in str(e.value)
+    with pytest.raises(stfem.StfemError) as e:
+        stfem.host_galerkin_check(prob, level=0)
+    assert e.value.code == stfem.ERR_ARG
